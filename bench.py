@@ -1,0 +1,448 @@
+#!/usr/bin/env python3
+"""Benchmark of the PNOF7 energy + orbital-Lagrangian build on GB300.
+
+One step = one build (E, lambda, dE/dgamma) plus its adjoint (dE/dC) of the large
+workload: nbf 1200, naux 4800, 50 pairs, Ncwo 2 (150 active orbitals), packed B,
+mixed precision, inputs resident in HBM (the 27.6 GB split copy of B that each build
+streams is far larger than L2).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lagrangian builds/sec & TFLOP/s, mixed vs FP64 GPU path at ≤1e-6 Eh"
+UNIT = "builds/s"
+WORKLOADS = {
+    "large": dict(nbf=1200, naux=4800, npair=50, ncwo=2, packed=True),
+    "precision": dict(nbf=500, naux=2000, npair=20, ncwo=3, packed=False),
+}
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-slices", type=int, default=480)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def flops_build(N, Q, A):
+    """Algorithmic flops of one build: X = B C (2QN^2A), b = C^T X (2QNA^2),
+    G += X Y (2QNA^2), h C and lambda = C^T G (2N^2A each)."""
+    return 2.0 * Q * N * A * (N + 2 * A) + 4.0 * N * N * A
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(w, seed, dev):
+    import numpy as np
+    import torch
+
+    import synth
+    N, Q = w["nbf"], w["naux"]
+    prob = synth.Problem(N, Q, w["npair"], w["ncwo"], seed)
+    d = synth.generate(prob, with_B=False)
+    npk = N * (N + 1) // 2
+    B = torch.empty((Q, npk) if w["packed"] else (Q, N, N), dtype=torch.float64, device=dev)
+    chunk = 160
+    for p0 in range(0, Q, chunk):
+        p1 = min(Q, p0 + chunk)
+        host = synth.gen_B(seed, Q, N, packed=w["packed"], p0=p0, p1=p1)
+        B[p0:p1].copy_(torch.from_numpy(host))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    return prob, d, dict(B=B, h=t(d["h"]), C=t(d["C"]), gamma=t(d["gamma"]),
+                         pair_map=t(d["pair_map"].astype(np.int32)))
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(w, seed, slices):
+    """The FP64 oracle on the large workload with `slices` of its naux auxiliary slices:
+    the naux-dependent part (AO operators) is scaled linearly to the full naux, the rest
+    (MO integrals, energy, G, lambda, dE/dgamma) is timed once.  Returns seconds per build."""
+    import numpy as np
+
+    import synth
+    from oracle import pnof
+    N, Q = w["nbf"], w["naux"]
+    prob = synth.Problem(N, Q, w["npair"], w["ncwo"], seed)
+    d = synth.generate(prob, with_B=False)
+    B = synth.gen_B(seed, Q, N, packed=False, p0=0, p1=slices)
+    pm = d["pair_map"]
+    C_act = d["C"][:, : prob.nact]
+    t0 = time.perf_counter()
+    occ = pnof.occupations(d["gamma"], pm, prob.npair, prob.ncwo)
+    Jq, Kq = pnof.ao_operators(B, C_act)
+    t1 = time.perf_counter()
+    J, K = pnof.mo_jk(C_act, Jq, Kq)
+    Hd = np.einsum("mp,mn,np->p", C_act, d["h"], C_act)
+    pnof.energy(Hd, J, K, occ, pm, prob.npair, pnof.PNOF7)
+    G = pnof.generalized_fock_action(d["h"], C_act, Jq, Kq, occ, pm, prob.npair, pnof.PNOF7)
+    _ = d["C"].T @ G
+    pnof.occupation_gradient(Hd, J, K, occ, pm, prob.npair, pnof.PNOF7)
+    t2 = time.perf_counter()
+    per_build = (t1 - t0) * (Q / slices) + (t2 - t1)
+    return per_build, (t2 - t0)
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- traffic record
+def recorded_traffic(kernel_src):
+    """Per-launch DRAM bytes of the half-transform kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "half_transform_large.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    slices = max(8, min(args.cpu_slices, 96))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, args.seed, slices)
+    times = []
+    for _ in range(args.steps):
+        per_build, _wall = cpu_oracle_sample(w, args.seed, slices)
+        times.append(per_build)
+    value = len(times) / sum(times)
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: nbf={w['nbf']}, naux={w['naux']}, npair={w['npair']}, "
+                               f"ncwo={w['ncwo']}, PNOF7, FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{slices} of {w['naux']} auxiliary slices per step; the "
+                                   "naux-dependent part scaled linearly to the full naux"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2004_06142_gb300 import build as libbuild
+    libbuild.build()
+    import paper_2004_06142_gb300 as dn
+
+    w = WORKLOADS[args.workload]
+    N, Q = w["nbf"], w["naux"]
+    prob, host, x = make_inputs(w, args.seed, dev)
+    A = prob.nact
+    layout = dn.B_PACKED if w["packed"] else dn.B_DENSE
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+
+    mixed = dn.Builder(N, Q, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.MIXED, device=dev)
+    mixed.prepare(x["B"])
+    Ebar = torch.ones(1, dtype=torch.float64, device=dev)
+
+    def step():
+        E, lam, dEdg = mixed.forward(x["h"], x["C"], x["gamma"], x["pair_map"])
+        dC, dg = mixed.backward(Ebar)
+        return E, lam, dEdg, dC
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert mixed.status() == 0, "device status after warm-up"
+
+    # ---------------- timed region (device resident inputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    dn.donof_profile_enable(True)
+    launches0 = dn.donof_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = dn.donof_launch_count() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    phases = {}
+    for i, nm in enumerate(dn.PHASES):
+        t, n = dn.donof_profile_read(i)
+        if n:
+            phases[nm] = {"ms_per_launch": t / n, "intervals": n}
+    dn.donof_profile_enable(False)
+    ms_all = torch.tensor([ms], device=dev)
+    if ws > 1:
+        tdist.all_reduce(ms_all, op=tdist.ReduceOp.MAX)
+    ms_max = ms_all.item()
+    value = ws * 1e3 / ms_max
+    E_mixed = out[0].item()
+    res_mixed = [t.detach().cpu().numpy() for t in out]
+
+    # ---------------- end to end through the public API with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hC, hg = pin(host["C"]), pin(host["gamma"])
+    oE = torch.empty(1, dtype=torch.float64).pin_memory()
+    olam = torch.empty(N, N, dtype=torch.float64).pin_memory()
+    odg = torch.empty(prob.ngamma, dtype=torch.float64).pin_memory()
+    odC = torch.empty(N, N, dtype=torch.float64).pin_memory()
+    Cd, gd = torch.empty_like(x["C"]), torch.empty_like(x["gamma"])
+    h2d = hC.numel() * 8 + hg.numel() * 8
+    d2h = (oE.numel() + olam.numel() + odg.numel() + odC.numel()) * 8
+
+    def e2e_step():
+        Cd.copy_(hC, non_blocking=True)
+        gd.copy_(hg, non_blocking=True)
+        E, lam, dEdg = mixed.forward(x["h"], Cd, gd, x["pair_map"])
+        dC, _ = mixed.backward(Ebar)
+        oE.copy_(E, non_blocking=True)
+        olam.copy_(lam, non_blocking=True)
+        odg.copy_(dEdg, non_blocking=True)
+        odC.copy_(dC, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record()
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1) / args.steps
+    assert abs(oE.item() - E_mixed) < 1e-9
+
+    # ---------------- the plain FP64 GPU path on the same inputs
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        del mixed
+        torch.cuda.empty_cache()
+        b64 = dn.Builder(N, Q, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.FP64,
+                         x_budget_bytes=16 << 30, device=dev)
+        b64.prepare(x["B"])
+
+        def step64():
+            E, lam, dEdg = b64.forward(x["h"], x["C"], x["gamma"], x["pair_map"])
+            dC, _ = b64.backward(Ebar)
+            return E, lam, dEdg, dC
+
+        step64()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(args.fp64_steps):
+            o64 = step64()
+        g1.record()
+        torch.cuda.synchronize()
+        ms64 = g0.elapsed_time(g1) / args.fp64_steps
+        r64 = [t.detach().cpu().numpy() for t in o64]
+        fp64 = {
+            "builds_per_s": 1e3 / ms64, "ms_per_build": ms64,
+            "tflops_algorithmic": flops_build(N, Q, A) / (ms64 * 1e-3) / 1e12,
+            "speedup_mixed_over_fp64": ms64 / ms,
+            "mixed_minus_fp64": {
+                "E_abs": float(abs(res_mixed[0][0] - r64[0][0])),
+                "lambda_maxabs": float(np.abs(res_mixed[1] - r64[1]).max()),
+                "dE_dgamma_maxabs": float(np.abs(res_mixed[2] - r64[2]).max()),
+                "dE_dC_maxabs": float(np.abs(res_mixed[3] - r64[3]).max()),
+            },
+            "status": b64.status(),
+        }
+
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        per_build, wall = cpu_oracle_sample(w, args.seed, args.cpu_slices)
+        cpu = {"value": 1.0 / per_build, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{args.cpu_slices} of {Q} auxiliary slices ({wall:.1f} s wall); "
+                         "naux-dependent part scaled linearly to the full naux"}
+
+    # ---------------- roofline of the dominant kernel (half transform X = B C)
+    pk, src = peaks()
+    peak_f16 = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    half = phases.get("half_transform", {}).get("ms_per_launch")
+    roof = None
+    if half:
+        flops_half = 2.0 * Q * N * N * A
+        achieved = flops_half / (half * 1e-3) / 1e12
+        peak_eff = peak_f16 / 3.0
+        traffic = recorded_traffic(os.path.join(ROOT, "paper_2004_06142_gb300", "csrc", "tc.cu"))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_eff, "unit": "TFLOP/s",
+                "frac": achieved / peak_eff, "traffic": traffic,
+                "kernel": "k_tc_gemm<64> (half transform X = B C_act)",
+                "peak_note": f"{src} dense fp16 sustained {peak_f16} TFLOP/s / 3 tensor products per "
+                             "algorithmic product (hi*hi + hi*lo + lo*hi)",
+                "issued_tflops": 3 * 2.0 * Q * N * N * ((A + 15) // 16 * 16) / (half * 1e-3) / 1e12,
+                "hbm_gbs_split_B_read": Q * N * (N + (-N) % 8) * 4 / (half * 1e-3) / 1e9,
+                "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 hi+lo split (3 products), f32 tensor accumulation, f64 reductions",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: nbf={N}, naux={Q}, npair={prob.npair}, "
+                                   f"ncwo={prob.ncwo} (nact {A}), "
+                                   f"{'packed' if w['packed'] else 'dense'} B, PNOF7, "
+                                   "E + lambda + dE/dgamma + dE/dC per step",
+                       "l2": "inputs larger than L2 (split B of "
+                             f"{Q * N * (N + (-N) % 8) * 4 / 1e9:.1f} GB streamed per build)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "tflops_algorithmic": flops_build(N, Q, A) * ws / (ms_max * 1e-3) / 1e12,
+            "phases_ms": {k: v["ms_per_launch"] for k, v in phases.items()},
+            "fp64_path": fp64,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "note": "per step: C and gamma host->device, E, lambda, dE/dgamma, dE/dC "
+                            "device->host; B and h stay resident (fixed across orbital "
+                            "iterations)"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "peaks_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

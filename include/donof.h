@@ -1,0 +1,150 @@
+/*
+ * donof.h -- C ABI of the GB300 library for the PNOF5 / PNOF7 / PNOF7s energy and
+ * orbital-Lagrangian build (one "build" = E, lambda, dE/dgamma for one set of
+ * natural orbitals C and occupation variables gamma).
+ *
+ * What is computed (paper sections and equations of arXiv:2004.06142):
+ *   occupations n_p(gamma) ............ Sec. III.A, Eqs. soo, woo
+ *   J_pq, K_pq (L = K, real orbitals) . Sec. III.D, Eqs. JKpq, Gpmn, with
+ *                                       density-fitted integrals
+ *                                       (mu nu|eta delta) = sum_P B[P][mu][nu] B[P][eta][delta]
+ *   E ................................. Sec. II, Eqs. EPNOF7, Eg, Efg (PNOF7), Efg with
+ *                                       Phi = 0 (PNOF5), Sec. V Eq. Efg_s (PNOF7s)
+ *   lambda_qp = n_p H_qp + g_pq ....... Sec. III.B, Eqs. lowdin, Vee-s, Vee-d, lag, gval,
+ *                                       normalised so that lambda = C^T G with
+ *                                       G = (1/4) dE/dC (Eq. lowdin carries the 4)
+ *   dE/dgamma, dE/dC .................. derivatives of the energy above
+ *
+ * Conventions shared by every entry point
+ *   - Every array is row-major.  Floating point arrays are IEEE double.
+ *   - Pointers marked (device) must be CUDA device pointers on the current device;
+ *     pointers marked (host) are host pointers.  The library never frees caller memory.
+ *   - h[nbf*nbf]   one-electron matrix, symmetric.
+ *   - B            DONOF_B_DENSE : [naux][nbf][nbf], each slice symmetric;
+ *                  DONOF_B_PACKED: [naux][nbf*(nbf+1)/2], element (mu >= nu) at
+ *                                  mu*(mu+1)/2 + nu.
+ *   - C[nbf*nbf]   MO coefficients, column p is orbital p (Eq. lcao): C[mu*nbf + p].
+ *   - gamma[npair*ncwo]  gamma[0..npair) strong (Eq. soo), then (ncwo-1) weak gammas
+ *                  per pair, pair-major (Eq. woo).
+ *   - pair_map[nact], nact = npair*(1+ncwo) <= nbf: subspace of each active orbital.
+ *                  pair_map[g] == g for g < npair (strong orbital g sits at index g);
+ *                  every pair owns exactly ncwo weak orbitals with index >= npair; the
+ *                  weak orbitals of a pair, in increasing index, are p_1..p_Ng of Eq. woo.
+ *                  Orbitals p >= nact are empty (n_p = 0).
+ *   - lam[nbf*nbf] lam[q*nbf + p] = lambda_qp (column p is the differentiated orbital);
+ *                  columns p >= nact are zero.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, 0 = legacy default stream).
+ *   - Return value: DONOF_OK (0) or a negative DONOF_ERR_* code; on error the outputs
+ *     are undefined.  Checks that need device data (pair_map contents, non-finite
+ *     inputs, kernel wait limits) write a status word into the workspace that
+ *     donof_read_status() returns.
+ *   - Workspace: caller-allocated device memory of donof_workspace_size() bytes,
+ *     256-byte aligned.  A workspace belongs to one problem description; the forward
+ *     state that donof_energy_backward() and donof_get_jk() read lives there, so those
+ *     calls must use the same workspace and stream as the forward call.  Calls that
+ *     share a workspace must not overlap in time.
+ */
+#ifndef DONOF_H
+#define DONOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { DONOF_PNOF5 = 5, DONOF_PNOF7 = 7, DONOF_PNOF7S = 8 };
+enum { DONOF_B_DENSE = 0, DONOF_B_PACKED = 1 };
+/* DONOF_FP64: every contraction in IEEE double on the CUDA cores.
+ * DONOF_MIXED: the three large contractions (X = B C, b = C^T X, G += X Y) on the
+ * tensor cores with fp16 hi+lo split operands (three products, fp32 accumulation,
+ * power-of-two scaling); J, K, E, dE/dgamma, lambda and every cross-tile sum in double. */
+enum { DONOF_FP64 = 0, DONOF_MIXED = 1 };
+
+enum {
+  DONOF_OK = 0,
+  DONOF_ERR_INVALID_ARG = -1,   /* bad size, null pointer, unknown enum */
+  DONOF_ERR_PAIR_MAP = -2,      /* pair_map violates the layout rules above */
+  DONOF_ERR_NONFINITE = -3,     /* gamma or a reduced quantity is NaN / Inf */
+  DONOF_ERR_WORKSPACE = -4,     /* workspace too small or misaligned */
+  DONOF_ERR_CUDA = -5,          /* a CUDA runtime / driver call failed */
+  DONOF_ERR_TIMEOUT = -6,       /* a bounded device-side wait ran out */
+  DONOF_ERR_UNSUPPORTED = -7,   /* shape outside the supported range (e.g. nact > 256 mixed) */
+  DONOF_ERR_NOT_PREPARED = -8   /* donof_prepare_B was not called for this workspace / B */
+};
+
+typedef struct {
+  int32_t nbf;         /* N_B, number of AO basis functions, >= 1 */
+  int32_t naux;        /* number of auxiliary (fitting) functions P, >= 1 */
+  int32_t npair;       /* N_II / 2, electron pairs, >= 1 */
+  int32_t ncwo;        /* N_g, weak orbitals per pair, >= 1 */
+  int32_t functional;  /* DONOF_PNOF5 | DONOF_PNOF7 | DONOF_PNOF7S */
+  int32_t b_layout;    /* DONOF_B_DENSE | DONOF_B_PACKED */
+  int32_t precision;   /* DONOF_FP64 | DONOF_MIXED */
+  int32_t reserved;    /* must be 0 */
+  /* Upper bound, in bytes, on the per-pass intermediate X[P][mu][q] (and its
+   * companions) held in the workspace; the auxiliary index is streamed in blocks that
+   * fit.  0 = hold every P at once. */
+  uint64_t x_budget_bytes;
+} donof_problem;
+
+/* Bytes of device workspace needed by `prob` (writes *bytes). */
+int donof_workspace_size(const donof_problem* prob, size_t* bytes);
+
+/* Register B (device) with the workspace.  DONOF_MIXED: converts B once into the
+ * scaled fp16 hi/lo copy that every later build streams (B is fixed across orbital
+ * iterations, Sec. III.D).  DONOF_FP64: records B only.  Must be called again when B
+ * changes; the build calls must then pass the same B pointer. */
+int donof_prepare_B(const donof_problem* prob, const double* B, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* One build.  Inputs h, B, C, gamma, pair_map (device).  Outputs (device):
+ * E[1], lam[nbf*nbf], dE_dgamma[npair*ncwo]; lam and dE_dgamma may be NULL. */
+int donof_energy_lagrangian(const donof_problem* prob, const double* h, const double* B,
+                            const double* C, const double* gamma, const int32_t* pair_map,
+                            void* workspace, size_t workspace_bytes, double* E, double* lam,
+                            double* dE_dgamma, void* stream);
+
+/* Adjoint of the last build in `workspace`: given the upstream gradient Ebar (device,
+ * one double), writes dE_dC[nbf*nbf] = Ebar * dE/dC = 4 Ebar G (zero columns p >= nact)
+ * and dE_dgamma[npair*ncwo] = Ebar * dE/dgamma (device; either may be NULL). */
+int donof_energy_backward(const donof_problem* prob, const double* Ebar, const void* workspace,
+                          size_t workspace_bytes, double* dE_dC, double* dE_dgamma, void* stream);
+
+/* Copies J[nact*nact] and K[nact*nact] (device) of the last build in `workspace`. */
+int donof_get_jk(const donof_problem* prob, const void* workspace, size_t workspace_bytes,
+                 double* J, double* K, void* stream);
+
+/* Synchronises `stream`, then returns in *status (host) the device status word of the
+ * last call on `workspace` (DONOF_OK or a DONOF_ERR_* code) and clears it. */
+int donof_read_status(const void* workspace, int32_t* status, void* stream);
+
+/* Tracing.  While enabled, every call records a pair of CUDA events on its stream around
+ * each phase of the build; donof_profile_read() waits for them and returns the summed
+ * device time (ms) and the number of timed intervals of one phase.  Enabling clears the
+ * previous record.  The launch counter counts every kernel the library has launched in
+ * this process (tracing on or off). */
+enum {
+  DONOF_PHASE_PREP = 0,            /* occupations, coefficients, h C, operand splits */
+  DONOF_PHASE_HALF_TRANSFORM = 1,  /* X = B C_act (the dominant contraction) */
+  DONOF_PHASE_MO_3INDEX = 2,       /* b^P = C_act^T X^P */
+  DONOF_PHASE_JK_Y = 3,            /* J, K accumulation and the Y^P operands */
+  DONOF_PHASE_G_BUILD = 4,         /* G += sum_P X^P Y^P */
+  DONOF_PHASE_ENERGY_LAMBDA = 5,   /* E, dE/dgamma, lambda = C^T G */
+  DONOF_PHASE_BACKWARD = 6,        /* donof_energy_backward */
+  DONOF_PHASE_PREPARE_B = 7,       /* donof_prepare_B */
+  DONOF_NUM_PHASES = 8
+};
+int donof_profile_enable(int32_t enable);
+int donof_profile_read(int32_t phase, double* total_ms, int32_t* intervals);
+int64_t donof_launch_count(void);
+
+/* Human-readable text for a status code (static storage). */
+const char* donof_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DONOF_H */

@@ -1,0 +1,35 @@
+/*
+ * donof_testing.h -- test hooks of libdonof (not needed to use the library).
+ *
+ * They expose the tensor-core building block of the mixed-precision build so that its
+ * arithmetic can be checked in isolation against exact products on the host.  The paper
+ * has no counterpart; these hooks exist for verification only.
+ */
+#ifndef DONOF_TESTING_H
+#define DONOF_TESTING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* D[m*N + n] = sum_k A_hi[m][k] B_hi[n][k] + A_hi[m][k] B_lo[n][k] + A_lo[m][k] B_hi[n][k]
+ * on the tensor cores (fp16 operands given as raw IEEE half bits, fp32 accumulation).
+ * All pointers are device pointers; A_* are [M][K], B_* are [N][K] (row-major, K
+ * contiguous), D is [M][N] fp32.  K must be a multiple of 8; N a multiple of 16 in
+ * [16, 256]; M >= 1.  Returns DONOF_OK or a DONOF_ERR_* code; the call is asynchronous on
+ * `stream` and device wait time-outs are reported by the return of the next call's
+ * status word (see donof_testing_status). */
+int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo, const uint16_t* B_hi,
+                          const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
+                          void* stream);
+
+/* Synchronises `stream` and returns (then clears) the status word of the test hooks. */
+int donof_testing_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DONOF_TESTING_H */

@@ -151,13 +151,14 @@ def ao_operators(B: np.ndarray, C_act: np.ndarray):
 
 
 def mo_jk(C_act: np.ndarray, Jq: np.ndarray, Kq: np.ndarray):
-    """Eq. JKpq: J_pq = sum Gamma^p J^q, K_pq = sum Gamma^p K^q with Gamma^p = C_p C_p^T."""
+    """Eq. JKpq: J_pq = sum Gamma^p J^q, K_pq = sum Gamma^p K^q with Gamma^p = C_p C_p^T,
+    i.e. J_pq = C_p^T J^q C_p (and the same for K)."""
     nact = C_act.shape[1]
     J = np.empty((nact, nact))
     K = np.empty((nact, nact))
     for q in range(nact):
-        J[:, q] = np.einsum("mp,mn,np->p", C_act, Jq[q], C_act)
-        K[:, q] = np.einsum("mp,mn,np->p", C_act, Kq[q], C_act)
+        J[:, q] = np.sum(C_act * (Jq[q] @ C_act), axis=0)
+        K[:, q] = np.sum(C_act * (Kq[q] @ C_act), axis=0)
     return J, K
 
 
@@ -206,28 +207,32 @@ def energy(Hdiag, J, K, occ, pair_map, npair, functional):
 def generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional):
     """G[:, p] = (1/4) dE/dphi_p expanded in the AO basis (Eqs. lowdin, Vee-s, Vee-d):
 
-    G_p = n_p h C_p
-        + sum_{q not in Omega_g(p)} [n_q n_p (2 J^q - K^q) - Phi_q Phi_p K^q] C_p   (PNOF7)
-        + sum_{q in Omega_g(p)} Pi_qp K^q C_p
-    (PNOF5: no Phi term; PNOF7s: -4 Phi_q^2 Phi_p^2 K^q instead.)
+    G_p = F_p C_p,  F_p = n_p h
+        + sum_{q not in Omega_g(p)} [n_q n_p (2 J^q - K^q) - Phi_q Phi_p K^q]   (PNOF7)
+        + sum_{q in Omega_g(p)} Pi_qp K^q
+    (PNOF5: no Phi term; PNOF7s: -4 Phi_q^2 Phi_p^2 K^q instead.)  F_p is applied to C_p
+    term by term: G_p = n_p h C_p + sum_q [a_pq (J^q C)_p + c_pq (K^q C)_p].
     """
     n, sq, phi = occ["n"], occ["sqrt_n"], occ["phi"]
     nbf, nact = C_act.shape
-    G = np.zeros((nbf, nact))
+    a = np.zeros((nact, nact))      # coefficient of J^q in F_p
+    c = np.zeros((nact, nact))      # coefficient of K^q in F_p
     for p in range(nact):
         gp = int(pair_map[p])
-        Fp = n[p] * h
         for q in range(nact):
             gq = int(pair_map[q])
             if gq == gp:
-                Fp = Fp + _pi(p, q, gp, sq) * Kq[q]
+                c[p, q] = _pi(p, q, gp, sq)
             else:
-                Fp = Fp + n[q] * n[p] * (2.0 * Jq[q] - Kq[q])
+                a[p, q] = 2.0 * n[q] * n[p]
+                c[p, q] = -n[q] * n[p]
                 if functional == PNOF7:
-                    Fp = Fp - phi[q] * phi[p] * Kq[q]
+                    c[p, q] -= phi[q] * phi[p]
                 elif functional == PNOF7S:
-                    Fp = Fp - 4.0 * phi[q] ** 2 * phi[p] ** 2 * Kq[q]
-        G[:, p] = Fp @ C_act[:, p]
+                    c[p, q] -= 4.0 * phi[q] ** 2 * phi[p] ** 2
+    G = n[None, :] * (h @ C_act)
+    for q in range(nact):
+        G += a[:, q][None, :] * (Jq[q] @ C_act) + c[:, q][None, :] * (Kq[q] @ C_act)
     return G
 
 

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libdonof (include/donof.h): same names, argument marshalling only.
+
+Every step of a build runs in the library's CUDA kernels.  PyTorch provides device
+memory and the current CUDA stream; nothing here computes on the host.  The library
+must have been built (``paper_2004_06142_gb300.build.build()``); loading fails loudly
+otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdonof.so")
+
+PNOF5, PNOF7, PNOF7S = 5, 7, 8
+B_DENSE, B_PACKED = 0, 1
+FP64, MIXED = 0, 1
+
+STATUS = {
+    0: "ok", -1: "invalid argument", -2: "pair_map violates the subspace layout",
+    -3: "non-finite input or result", -4: "workspace too small or misaligned",
+    -5: "CUDA call failed", -6: "device wait limit exceeded", -7: "unsupported problem size",
+    -8: "donof_prepare_B not called for this workspace and B",
+}
+
+
+class DonofError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, 'unknown status')} ({code})")
+        self.code = code
+
+
+class donof_problem(ctypes.Structure):
+    _fields_ = [("nbf", ctypes.c_int32), ("naux", ctypes.c_int32), ("npair", ctypes.c_int32),
+                ("ncwo", ctypes.c_int32), ("functional", ctypes.c_int32),
+                ("b_layout", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("x_budget_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdonof.so is not built ({LIB_PATH}); run "
+                               "paper_2004_06142_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(donof_problem)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        L.donof_workspace_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_prepare_B.argtypes = [P, vp, vp, sz, vp]
+        L.donof_energy_lagrangian.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp]
+        L.donof_energy_backward.argtypes = [P, vp, vp, sz, vp, vp, vp]
+        L.donof_get_jk.argtypes = [P, vp, sz, vp, vp, vp]
+        L.donof_read_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
+        L.donof_status_string.argtypes = [ctypes.c_int]
+        L.donof_status_string.restype = ctypes.c_char_p
+        L.donof_profile_enable.argtypes = [ctypes.c_int32]
+        L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32)]
+        L.donof_launch_count.argtypes = []
+        L.donof_launch_count.restype = ctypes.c_int64
+        for f in ("donof_workspace_size", "donof_prepare_B", "donof_energy_lagrangian",
+                  "donof_energy_backward", "donof_get_jk", "donof_read_status",
+                  "donof_profile_enable", "donof_profile_read"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def make_problem(nbf, naux, npair, ncwo, functional=PNOF7, b_layout=B_DENSE, precision=FP64,
+                 x_budget_bytes=0) -> donof_problem:
+    return donof_problem(nbf, naux, npair, ncwo, functional, b_layout, precision, 0,
+                         x_budget_bytes)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise DonofError(rc, where)
+
+
+def donof_workspace_size(prob: donof_problem) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().donof_workspace_size(ctypes.byref(prob), ctypes.byref(n)), "donof_workspace_size")
+    return n.value
+
+
+def donof_prepare_B(prob, B, ws, stream=None):
+    _check(lib().donof_prepare_B(ctypes.byref(prob), _ptr(B), _ptr(ws), ws.numel(), _stream(stream)),
+           "donof_prepare_B")
+
+
+def donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, E, lam=None, dE_dgamma=None,
+                            stream=None):
+    _check(lib().donof_energy_lagrangian(ctypes.byref(prob), _ptr(h), _ptr(B), _ptr(C), _ptr(gamma),
+                                         _ptr(pair_map), _ptr(ws), ws.numel(), _ptr(E), _ptr(lam),
+                                         _ptr(dE_dgamma), _stream(stream)),
+           "donof_energy_lagrangian")
+
+
+def donof_energy_backward(prob, Ebar, ws, dE_dC=None, dE_dgamma=None, stream=None):
+    _check(lib().donof_energy_backward(ctypes.byref(prob), _ptr(Ebar), _ptr(ws), ws.numel(),
+                                       _ptr(dE_dC), _ptr(dE_dgamma), _stream(stream)),
+           "donof_energy_backward")
+
+
+def donof_get_jk(prob, ws, J=None, K=None, stream=None):
+    _check(lib().donof_get_jk(ctypes.byref(prob), _ptr(ws), ws.numel(), _ptr(J), _ptr(K),
+                              _stream(stream)), "donof_get_jk")
+
+
+def donof_read_status(ws, stream=None) -> int:
+    st = ctypes.c_int32(0)
+    _check(lib().donof_read_status(_ptr(ws), ctypes.byref(st), _stream(stream)), "donof_read_status")
+    return st.value
+
+
+PHASES = ["prep", "half_transform", "mo_3index", "jk_y", "g_build", "energy_lambda",
+          "backward", "prepare_B"]
+
+
+def donof_profile_enable(enable: bool):
+    _check(lib().donof_profile_enable(1 if enable else 0), "donof_profile_enable")
+
+
+def donof_profile_read(phase: int):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int32(0)
+    _check(lib().donof_profile_read(phase, ctypes.byref(ms), ctypes.byref(n)), "donof_profile_read")
+    return ms.value, n.value
+
+
+def donof_launch_count() -> int:
+    return int(lib().donof_launch_count())
+
+
+def donof_status_string(code: int) -> str:
+    return lib().donof_status_string(code).decode()
+
+
+# ---------------------------------------------------------------------------
+class Builder:
+    """Owns a workspace for one problem and one prepared B (device tensors)."""
+
+    def __init__(self, nbf, naux, npair, ncwo, functional=PNOF7, b_layout=B_DENSE,
+                 precision=FP64, x_budget_bytes=0, device="cuda"):
+        self.prob = make_problem(nbf, naux, npair, ncwo, functional, b_layout, precision,
+                                 x_budget_bytes)
+        self.nbf, self.naux, self.npair, self.ncwo = nbf, naux, npair, ncwo
+        self.nact = npair * (1 + ncwo)
+        self.ngamma = npair * ncwo
+        self.device = torch.device(device)
+        self.ws = torch.empty(donof_workspace_size(self.prob), dtype=torch.uint8, device=self.device)
+        self.B = None
+
+    def prepare(self, B: torch.Tensor):
+        self.B = B
+        donof_prepare_B(self.prob, B, self.ws)
+
+    def forward(self, h, C, gamma, pair_map, want_lam=True):
+        dev, f64 = self.device, torch.float64
+        E = torch.empty(1, dtype=f64, device=dev)
+        lam = torch.empty(self.nbf, self.nbf, dtype=f64, device=dev) if want_lam else None
+        dEdg = torch.empty(self.ngamma, dtype=f64, device=dev)
+        donof_energy_lagrangian(self.prob, h, self.B, C, gamma, pair_map, self.ws, E, lam, dEdg)
+        return E, lam, dEdg
+
+    def backward(self, Ebar):
+        dev, f64 = self.device, torch.float64
+        dC = torch.empty(self.nbf, self.nbf, dtype=f64, device=dev)
+        dg = torch.empty(self.ngamma, dtype=f64, device=dev)
+        donof_energy_backward(self.prob, Ebar, self.ws, dC, dg)
+        return dC, dg
+
+    def jk(self):
+        J = torch.empty(self.nact, self.nact, dtype=torch.float64, device=self.device)
+        K = torch.empty_like(J)
+        donof_get_jk(self.prob, self.ws, J, K)
+        return J, K
+
+    def status(self) -> int:
+        return donof_read_status(self.ws)
+
+
+class DonofEnergy(torch.autograd.Function):
+    """E(C, gamma) with the library's adjoint: dE/dC = 4 Ebar G, dE/dgamma = Ebar dE/dgamma.
+    lambda is returned as a non-differentiable output."""
+
+    @staticmethod
+    def forward(ctx, C, gamma, builder: Builder, h, pair_map):
+        E, lam, _ = builder.forward(h, C.contiguous(), gamma.contiguous(), pair_map)
+        ctx.builder = builder
+        ctx.mark_non_differentiable(lam)
+        return E.reshape(()), lam
+
+    @staticmethod
+    def backward(ctx, gE, glam):
+        Ebar = gE.reshape(1).to(torch.float64).contiguous()
+        dC, dg = ctx.builder.backward(Ebar)
+        return dC, dg, None, None, None
+
+
+def energy(C, gamma, builder: Builder, h, pair_map):
+    """Differentiable energy (and lambda) of one build."""
+    return DonofEnergy.apply(C, gamma, builder, h, pair_map)

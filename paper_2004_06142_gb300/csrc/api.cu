@@ -1,0 +1,431 @@
+// C ABI entry points of libdonof (declared in include/donof.h): argument checks,
+// workspace carving and the launch sequence of one build.
+//
+// One build streams the auxiliary index P in blocks (Sec. III.D: the AO -> MO
+// transformation is redone every time the orbitals change).  Per block:
+//   X = B C_act  ->  b^P = C_act^T X^P  ->  J, K += ...,  Y^P  ->  G += sum_P X^P Y^P
+// and, after the last block, E and dE/dgamma from J, K (Eqs. EPNOF7, Eg, Efg, Efg_s) and
+// lambda = C^T G (Eqs. lowdin, lag).  The coefficients of Y depend only on the
+// occupations, so G needs no second pass over B.
+#include <atomic>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace donof {
+
+Dims make_dims(const donof_problem* p) {
+  Dims d{};
+  d.N = p->nbf;
+  d.Q = p->naux;
+  d.npair = p->npair;
+  d.ncwo = p->ncwo;
+  d.A = p->npair * (1 + p->ncwo);
+  d.Ap = round_up_int(d.A, 16);
+  d.Np = round_up_int(d.N, 8);
+  d.ng = p->npair * p->ncwo;
+  d.functional = p->functional;
+  d.layout = p->b_layout;
+  d.precision = p->precision;
+  size_t perP;
+  if (d.precision == DONOF_FP64) {
+    perP = (size_t)d.N * d.A * 8 + 2 * (size_t)d.A * d.A * 8 +
+           (d.layout == DONOF_B_PACKED ? (size_t)d.N * d.N * 8 : 0);
+  } else {
+    perP = (size_t)d.N * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4);
+  }
+  long long pb = d.Q;
+  if (p->x_budget_bytes > 0) {
+    pb = (long long)(p->x_budget_bytes / perP);
+    if (pb < 1) pb = 1;
+    if (pb > d.Q) pb = d.Q;
+  }
+  if (pb > 65535) pb = 65535;  // batch index of the double GEMMs lives in gridDim.z
+  d.pb = (int)pb;
+  d.nblk = (d.Q + d.pb - 1) / d.pb;
+  // split-K of the G contraction: at most 32 slices per split, enough units for 2 waves
+  const int mt = (d.N + 127) / 128;
+  int sp = (d.pb + 31) / 32;
+  const int want = (2 * 152 + mt - 1) / mt;
+  if (sp < want) sp = want;
+  if (sp > d.pb) sp = d.pb;
+  d.splits = sp;
+  return d;
+}
+
+Layout make_layout(const Dims& d) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  };
+  const size_t N = d.N, A = d.A, Ap = d.Ap, Np = d.Np, ng = d.ng > 0 ? d.ng : 1, pb = d.pb;
+  L.header = take(sizeof(DevHeader));
+  L.n = take(A * 8);
+  L.sqn = take(A * 8);
+  L.phi = take(A * 8);
+  L.dn = take(A * ng * 8);
+  L.dsq = take(A * ng * 8);
+  L.dphi = take(A * ng * 8);
+  L.Acoef = take(A * A * 8);
+  L.Bcoef = take(A * A * 8);
+  L.Hd = take(A * 8);
+  L.hC = take(N * A * 8);
+  L.J = take(A * A * 8);
+  L.K = take(A * A * 8);
+  L.G = take(N * A * 8);
+  L.dEdg = take(ng * 8);
+  if (d.precision == DONOF_FP64) {
+    L.X64 = take(pb * N * A * 8);
+    L.b64 = take(pb * A * A * 8);
+    L.Y64 = take(pb * A * A * 8);
+    L.Bun = d.layout == DONOF_B_PACKED ? take(pb * N * N * 8) : 0;
+  } else {
+    const size_t Q = d.Q;
+    L.Bhi = take(Q * N * Np * 2);
+    L.Blo = take(Q * N * Np * 2);
+    L.Chi = take(Ap * Np * 2);
+    L.Clo = take(Ap * Np * 2);
+    L.Xhi = take(pb * N * Ap * 2);
+    L.Xlo = take(pb * N * Ap * 2);
+    L.Xthi = take(pb * Ap * Np * 2);
+    L.Xtlo = take(pb * Ap * Np * 2);
+    L.b32 = take(pb * Ap * Ap * 4);
+    L.Y32 = take(pb * Ap * Ap * 4);
+    L.Yhi = take(pb * Ap * Ap * 2);
+    L.Ylo = take(pb * Ap * Ap * 2);
+    L.Gpart = take((size_t)d.splits * N * Ap * 4);
+  }
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Tracing: CUDA-event pairs per phase, and a process-wide kernel launch counter.
+// ---------------------------------------------------------------------------
+namespace {
+std::atomic<long long> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct PhaseRec {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  bool open = false;
+};
+PhaseRec g_prof[DONOF_NUM_PHASES];
+
+void prof_clear_locked() {
+  for (auto& r : g_prof) {
+    for (auto& e : r.ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    r.ev.clear();
+    r.open = false;
+  }
+}
+}  // namespace
+
+void count_launch(int n) { g_launches += n; }
+
+void prof_begin(int phase, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES) return;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+  cudaEventRecord(a, s);
+  g_prof[phase].ev.emplace_back(a, b);
+  g_prof[phase].open = true;
+}
+
+void prof_end(int phase, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES) return;
+  PhaseRec& r = g_prof[phase];
+  if (!r.open || r.ev.empty()) return;
+  cudaEventRecord(r.ev.back().second, s);
+  r.open = false;
+}
+
+namespace {
+
+struct Registration {
+  const double* B;
+  donof_problem prob;
+};
+std::mutex g_mu;
+std::unordered_map<const void*, Registration> g_reg;
+
+bool same_problem(const donof_problem& a, const donof_problem& b) {
+  return a.nbf == b.nbf && a.naux == b.naux && a.npair == b.npair && a.ncwo == b.ncwo &&
+         a.b_layout == b.b_layout && a.precision == b.precision &&
+         a.x_budget_bytes == b.x_budget_bytes;
+}
+
+int check_problem(const donof_problem* p) {
+  if (!p) return DONOF_ERR_INVALID_ARG;
+  if (p->nbf < 1 || p->naux < 1 || p->npair < 1 || p->ncwo < 1 || p->reserved != 0)
+    return DONOF_ERR_INVALID_ARG;
+  if (p->functional != DONOF_PNOF5 && p->functional != DONOF_PNOF7 &&
+      p->functional != DONOF_PNOF7S)
+    return DONOF_ERR_INVALID_ARG;
+  if (p->b_layout != DONOF_B_DENSE && p->b_layout != DONOF_B_PACKED) return DONOF_ERR_INVALID_ARG;
+  if (p->precision != DONOF_FP64 && p->precision != DONOF_MIXED) return DONOF_ERR_INVALID_ARG;
+  const long long nact = (long long)p->npair * (1 + p->ncwo);
+  if (nact > p->nbf) return DONOF_ERR_INVALID_ARG;
+  if (p->nbf > 65536 || p->naux > (1 << 24)) return DONOF_ERR_UNSUPPORTED;
+  if (p->precision == DONOF_MIXED && round_up_int((int)nact, 16) > 256)
+    return DONOF_ERR_UNSUPPORTED;
+  return DONOF_OK;
+}
+
+int check_ws(const donof_problem* p, const void* ws, size_t bytes) {
+  if (!ws || ((uintptr_t)ws % kAlign) != 0) return DONOF_ERR_WORKSPACE;
+  const Layout L = make_layout(make_dims(p));
+  return bytes >= L.total ? DONOF_OK : DONOF_ERR_WORKSPACE;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    if ((x) != cudaSuccess) return DONOF_ERR_CUDA; \
+  } while (0)
+
+}  // namespace
+}  // namespace donof
+
+using namespace donof;
+
+extern "C" int donof_workspace_size(const donof_problem* prob, size_t* bytes) {
+  const int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  if (!bytes) return DONOF_ERR_INVALID_ARG;
+  *bytes = make_layout(make_dims(prob)).total;
+  return DONOF_OK;
+}
+
+extern "C" int donof_prepare_B(const donof_problem* prob, const double* B, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  if (!B) return DONOF_ERR_INVALID_ARG;
+  rc = check_ws(prob, workspace, workspace_bytes);
+  if (rc != DONOF_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d = make_dims(prob);
+  const Layout L = make_layout(d);
+  char* ws = (char*)workspace;
+  prof_begin(DONOF_PHASE_PREPARE_B, s);
+  CK(cudaMemsetAsync(ws + L.header, 0, sizeof(DevHeader), s));
+  if (d.precision == DONOF_MIXED) CK(launch_prepare_split_B(d, B, ws, L, s));
+  prof_end(DONOF_PHASE_PREPARE_B, s);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_reg[workspace] = Registration{B, *prob};
+  return DONOF_OK;
+}
+
+extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* h, const double* B,
+                                       const double* C, const double* gamma,
+                                       const int32_t* pair_map, void* workspace,
+                                       size_t workspace_bytes, double* E, double* lam,
+                                       double* dE_dgamma, void* stream) {
+  int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  if (!h || !B || !C || !gamma || !pair_map || !E) return DONOF_ERR_INVALID_ARG;
+  rc = check_ws(prob, workspace, workspace_bytes);
+  if (rc != DONOF_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(workspace);
+    if (it == g_reg.end() || it->second.B != B || !same_problem(it->second.prob, *prob))
+      return DONOF_ERR_NOT_PREPARED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d = make_dims(prob);
+  const Layout L = make_layout(d);
+  char* ws = (char*)workspace;
+  const int N = d.N, A = d.A;
+
+  prof_begin(DONOF_PHASE_PREP, s);
+  CK(cudaMemsetAsync(&((DevHeader*)(ws + L.header))->abort_flag, 0, sizeof(int32_t), s));
+  CK(launch_occupations(d, gamma, pair_map, ws, L, s));
+  CK(launch_coefficients(d, pair_map, ws, L, s));
+  // hC = h C_act, H_pp, G = n o hC
+  {
+    DgemmArgs a{};
+    a.M = N; a.N = A; a.K = N; a.KB = 1; a.batch = 1; a.ksplit = 1;
+    a.A = h; a.sAm = N; a.sAk = 1;
+    a.B = C; a.sBk = N; a.sBn = 1;
+    a.C = (double*)(ws + L.hC); a.sCm = A; a.sCn = 1;
+    a.alpha = 1.0; a.beta = 0.0;
+    CK(launch_dgemm(a, s));
+  }
+  CK(launch_hdiag_ginit(d, C, ws, L, s));
+  CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
+  CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
+  if (d.precision == DONOF_MIXED) CK(launch_split_C(d, C, ws, L, s));
+  prof_end(DONOF_PHASE_PREP, s);
+
+  for (int p0 = 0; p0 < d.Q; p0 += d.pb) {
+    const int np = (d.Q - p0) < d.pb ? (d.Q - p0) : d.pb;
+    if (d.precision == DONOF_MIXED) {
+      rc = run_tc_block(d, p0, np, ws, L, s);
+      if (rc != DONOF_OK) return rc;
+      continue;
+    }
+    // ---- FP64 path
+    const double* Bblk;
+    prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
+    if (d.layout == DONOF_B_PACKED) {
+      CK(launch_unpack_B(d, B, p0, np, (double*)(ws + L.Bun), s));
+      Bblk = (const double*)(ws + L.Bun);
+    } else {
+      Bblk = B + (size_t)p0 * N * N;
+    }
+    double* X = (double*)(ws + L.X64);
+    double* b = (double*)(ws + L.b64);
+    double* Y = (double*)(ws + L.Y64);
+    {  // X[P][mu][q] = sum_nu B[P][mu][nu] C[nu][q]
+      DgemmArgs a{};
+      a.M = np * N; a.N = A; a.K = N; a.KB = 1; a.batch = 1; a.ksplit = 1;
+      a.A = Bblk; a.sAm = N; a.sAk = 1;
+      a.B = C; a.sBk = N; a.sBn = 1;
+      a.C = X; a.sCm = A; a.sCn = 1;
+      a.alpha = 1.0;
+      CK(launch_dgemm(a, s));
+    }
+    prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
+    prof_begin(DONOF_PHASE_MO_3INDEX, s);
+    {  // b[P][p][q] = sum_mu C[mu][p] X[P][mu][q]
+      DgemmArgs a{};
+      a.M = A; a.N = A; a.K = N; a.KB = 1; a.batch = np; a.ksplit = 1;
+      a.A = C; a.sAm = 1; a.sAk = N;
+      a.B = X; a.sBb = (long long)N * A; a.sBk = A; a.sBn = 1;
+      a.C = b; a.sCb = (long long)A * A; a.sCm = A; a.sCn = 1;
+      a.alpha = 1.0;
+      CK(launch_dgemm(a, s));
+    }
+    prof_end(DONOF_PHASE_MO_3INDEX, s);
+    prof_begin(DONOF_PHASE_JK_Y, s);
+    CK(launch_jk_accumulate_f64(d, b, np, A, ws, L, s));
+    CK(launch_build_Y_f64(d, b, Y, np, ws, L, s));
+    prof_end(DONOF_PHASE_JK_Y, s);
+    prof_begin(DONOF_PHASE_G_BUILD, s);
+    {  // G[mu][p] += sum_P sum_q X[P][mu][q] Y[P][q][p]
+      DgemmArgs a{};
+      a.M = N; a.N = A; a.K = A; a.KB = np; a.batch = 1;
+      const long long tiles = (long long)((N + 63) / 64) * ((A + 63) / 64);
+      long long ks = (2 * 152 + tiles - 1) / tiles;
+      if (ks > np) ks = np;
+      a.ksplit = (int)ks;
+      a.A = X; a.sAm = A; a.sAk = 1; a.sAkb = (long long)N * A;
+      a.B = Y; a.sBk = A; a.sBn = 1; a.sBkb = (long long)A * A;
+      a.C = (double*)(ws + L.G); a.sCm = A; a.sCn = 1;
+      a.alpha = 1.0; a.beta = 1.0;
+      CK(launch_dgemm(a, s));
+    }
+    prof_end(DONOF_PHASE_G_BUILD, s);
+  }
+
+  prof_begin(DONOF_PHASE_ENERGY_LAMBDA, s);
+  CK(launch_energy(d, pair_map, ws, L, E, dE_dgamma, s));
+  if (lam) {  // lambda_qp = C_q^T G_p (q < N, p < nact), zero for p >= nact
+    DgemmArgs a{};
+    a.M = N; a.N = A; a.K = N; a.KB = 1; a.batch = 1; a.ksplit = 1;
+    a.A = C; a.sAm = 1; a.sAk = N;
+    a.B = (const double*)(ws + L.G); a.sBk = A; a.sBn = 1;
+    a.C = lam; a.sCm = N; a.sCn = 1;
+    a.alpha = 1.0;
+    CK(launch_dgemm(a, s));
+    CK(launch_zero_cols(lam, N, N, A, N, s));
+  }
+  prof_end(DONOF_PHASE_ENERGY_LAMBDA, s);
+  return DONOF_OK;
+}
+
+extern "C" int donof_energy_backward(const donof_problem* prob, const double* Ebar,
+                                     const void* workspace, size_t workspace_bytes, double* dE_dC,
+                                     double* dE_dgamma, void* stream) {
+  int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  if (!Ebar) return DONOF_ERR_INVALID_ARG;
+  rc = check_ws(prob, workspace, workspace_bytes);
+  if (rc != DONOF_OK) return rc;
+  const Dims d = make_dims(prob);
+  const Layout L = make_layout(d);
+  prof_begin(DONOF_PHASE_BACKWARD, (cudaStream_t)stream);
+  CK(launch_backward(d, Ebar, (const char*)workspace, L, dE_dC, dE_dgamma, (cudaStream_t)stream));
+  prof_end(DONOF_PHASE_BACKWARD, (cudaStream_t)stream);
+  return DONOF_OK;
+}
+
+extern "C" int donof_get_jk(const donof_problem* prob, const void* workspace,
+                            size_t workspace_bytes, double* J, double* K, void* stream) {
+  int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  rc = check_ws(prob, workspace, workspace_bytes);
+  if (rc != DONOF_OK) return rc;
+  const Dims d = make_dims(prob);
+  const Layout L = make_layout(d);
+  const size_t bytes = (size_t)d.A * d.A * 8;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (J) CK(cudaMemcpyAsync(J, (const char*)workspace + L.J, bytes, cudaMemcpyDeviceToDevice, s));
+  if (K) CK(cudaMemcpyAsync(K, (const char*)workspace + L.K, bytes, cudaMemcpyDeviceToDevice, s));
+  return DONOF_OK;
+}
+
+extern "C" int donof_read_status(const void* workspace, int32_t* status, void* stream) {
+  if (!workspace || !status) return DONOF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s));
+  int32_t v = 0;
+  CK(cudaMemcpy(&v, workspace, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const int32_t zero = 0;
+  CK(cudaMemcpy((void*)workspace, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
+  *status = v;
+  return DONOF_OK;
+}
+
+extern "C" int donof_profile_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (enable) prof_clear_locked();
+  g_prof_on = enable != 0;
+  return DONOF_OK;
+}
+
+extern "C" int donof_profile_read(int32_t phase, double* total_ms, int32_t* intervals) {
+  if (phase < 0 || phase >= DONOF_NUM_PHASES || !total_ms) return DONOF_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  double t = 0.0;
+  int n = 0;
+  for (auto& e : g_prof[phase].ev) {
+    if (cudaEventSynchronize(e.second) != cudaSuccess) return DONOF_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess) return DONOF_ERR_CUDA;
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  if (intervals) *intervals = n;
+  return DONOF_OK;
+}
+
+extern "C" int64_t donof_launch_count(void) { return (int64_t)g_launches.load(); }
+
+extern "C" const char* donof_status_string(int status) {
+  switch (status) {
+    case DONOF_OK: return "ok";
+    case DONOF_ERR_INVALID_ARG: return "invalid argument";
+    case DONOF_ERR_PAIR_MAP: return "pair_map violates the subspace layout";
+    case DONOF_ERR_NONFINITE: return "non-finite input or result";
+    case DONOF_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case DONOF_ERR_CUDA: return "CUDA call failed";
+    case DONOF_ERR_TIMEOUT: return "device wait limit exceeded";
+    case DONOF_ERR_UNSUPPORTED: return "unsupported problem size";
+    case DONOF_ERR_NOT_PREPARED: return "donof_prepare_B not called for this workspace and B";
+    default: return "unknown status";
+  }
+}

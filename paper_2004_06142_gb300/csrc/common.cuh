@@ -1,0 +1,126 @@
+// Internal declarations shared by the CUDA translation units of libdonof.
+// Nothing here is part of the C ABI (include/donof.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/donof.h"
+
+namespace donof {
+
+// ---------------------------------------------------------------------------
+// Device-resident header at the start of every workspace.
+// ---------------------------------------------------------------------------
+struct DevHeader {
+  int32_t status;        // DONOF_OK or the first DONOF_ERR_* raised on the device
+  int32_t sB, sC, sX, sY;  // power-of-two exponents of the fp16 split operands
+  int32_t e1, e2, e3;    // output exponents of the three tensor-core contractions
+  double maxB;           // max |B|                      (set by prepare)
+  double maxBrow;        // max_P,mu ||B[P][mu][:]||_2   (set by prepare)
+  unsigned long long maxB_bits, maxBrow_bits;  // atomicMax scratch (double bits, >= 0)
+  unsigned int maxY_bits;  // max |Y| of the current block (float bits)
+  int32_t zero_exp;       // always 0 (epilogue exponent of raw partial sums)
+  int32_t abort_flag;     // set when a bounded device wait gives up; cleared per build
+  int32_t pad1;
+  double E;              // energy of the last build
+};
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int round_up_int(int x, int a) { return (x + a - 1) / a * a; }
+
+// Derived sizes of one problem.
+struct Dims {
+  int N, Q, A, Ap, Np, npair, ncwo, ng, pb, nblk, functional, layout, precision;
+  int splits;  // split-K factor of the G contraction (mixed path)
+};
+
+// Byte offsets of every buffer inside the workspace.
+struct Layout {
+  size_t header;
+  // shared by both precisions
+  size_t n, sqn, phi, dn, dsq, dphi, Acoef, Bcoef, Hd, hC, J, K, G, dEdg;
+  // FP64 path
+  size_t X64, b64, Y64, Bun, W64;
+  // mixed path
+  size_t Bhi, Blo, Chi, Clo, Xhi, Xlo, Xthi, Xtlo, b32, Y32, Yhi, Ylo, Gpart;
+  size_t total;
+};
+
+Dims make_dims(const donof_problem* p);
+
+// Tracing (api.cu): no-ops unless donof_profile_enable(1) was called.
+void prof_begin(int phase, cudaStream_t s);
+void prof_end(int phase, cudaStream_t s);
+void count_launch(int n);
+Layout make_layout(const Dims& d);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ inline void set_status(DevHeader* h, int code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+// Exponent s such that |x| * 2^s < 2^14 for |x| <= bound (bound > 0); 0 for bound == 0.
+__host__ __device__ inline int split_exponent(double bound) {
+  if (!(bound > 0.0)) return 0;
+  int e;
+  frexp(bound, &e);  // bound < 2^e
+  return 14 - e;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (host side), implemented in fp64.cu and tc.cu.
+// All return a cudaError_t of the launch.
+// ---------------------------------------------------------------------------
+
+// C[b](m, n) = alpha * sum_{kb, k} A(m, kb, k) B(kb, k, n) + beta * C[b](m, n)
+// with A(m, kb, k) = A[b*sAb + m*sAm + kb*sAkb + k*sAk] and
+//      B(kb, k, n) = B[b*sBb + kb*sBkb + k*sBk + n*sBn];
+// ksplit > 1 splits the kb range over CTAs and accumulates with atomicAdd (beta must be 1).
+struct DgemmArgs {
+  int M, N, K, KB, batch, ksplit;
+  const double* A; long long sAb, sAm, sAk, sAkb;
+  const double* B; long long sBb, sBk, sBn, sBkb;
+  double* C; long long sCb, sCm, sCn;
+  double alpha, beta;
+};
+cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s);
+
+cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pair_map,
+                               char* ws, const Layout& L, cudaStream_t s);
+cudaError_t launch_coefficients(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
+                                cudaStream_t s);
+cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, double* out,
+                            cudaStream_t s);
+cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const Layout& L,
+                               cudaStream_t s);
+cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
+                                     const Layout& L, cudaStream_t s);
+cudaError_t launch_jk_accumulate_f32(const Dims& d, const float* b, int np, int ld, char* ws,
+                                     const Layout& L, cudaStream_t s);
+cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np, char* ws,
+                               const Layout& L, cudaStream_t s);
+cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
+                               const Layout& L, cudaStream_t s);
+cudaError_t launch_energy(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
+                          double* E_out, double* dEdg_out, cudaStream_t s);
+cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s);
+cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, const Layout& L,
+                            double* dE_dC, double* dE_dgamma, cudaStream_t s);
+
+// mixed path
+cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, const Layout& L,
+                                   cudaStream_t s);
+cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
+                           cudaStream_t s);
+cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cudaStream_t s);
+cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
+// The three tensor-core contractions of one block of np auxiliary slices starting at p0.
+int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaStream_t s);
+
+}  // namespace donof

@@ -1,0 +1,543 @@
+// FP64 kernels of the PNOF build: the strided batched DGEMM that carries every
+// contraction of the plain-double path (and the small double contractions of the
+// mixed path), and the per-orbital / per-pair kernels of both paths:
+//   occupations n(gamma) and Jacobians ........ Eqs. soo, woo
+//   coefficient matrices of E in J and K ........ Eqs. Eg, Efg, Efg_s
+//   J / K accumulation over P, the Y^P operands . Eqs. JKpq (density-fitted)
+//   energy and dE/dgamma ........................ Eqs. EPNOF7, Eg, Efg, Efg_s
+#include "common.cuh"
+
+namespace donof {
+
+// ---------------------------------------------------------------------------
+// Strided batched DGEMM, 64x64 output tile per CTA, 4x4 per thread, DFMA.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int DBM = 64, DBN = 64, DBK = 16;
+
+__global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
+  __shared__ double As[DBK][DBM + 1];
+  __shared__ double Bs[DBK][DBN + 1];
+  const int bz = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
+  const long long m0 = (long long)blockIdx.x * DBM;
+  const int n0 = blockIdx.y * DBN;
+  const double* A = a.A + (long long)bz * a.sAb;
+  const double* B = a.B + (long long)bz * a.sBb;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const bool a_m_fast = (a.sAm == 1);
+  const bool b_n_fast = (a.sBn == 1);
+  const int kb0 = (int)((long long)a.KB * ks / a.ksplit);
+  const int kb1 = (int)((long long)a.KB * (ks + 1) / a.ksplit);
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int kb = kb0; kb < kb1; ++kb) {
+    const double* Akb = A + (long long)kb * a.sAkb;
+    const double* Bkb = B + (long long)kb * a.sBkb;
+    for (int k0 = 0; k0 < a.K; k0 += DBK) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int idx = threadIdx.x + i * 256;
+        int mm, kk;
+        if (a_m_fast) { mm = idx % DBM; kk = idx / DBM; } else { kk = idx % DBK; mm = idx / DBK; }
+        const long long gm = m0 + mm;
+        const int gk = k0 + kk;
+        As[kk][mm] = (gm < a.M && gk < a.K) ? Akb[gm * a.sAm + (long long)gk * a.sAk] : 0.0;
+        int nn;
+        if (b_n_fast) { nn = idx % DBN; kk = idx / DBN; } else { kk = idx % DBK; nn = idx / DBK; }
+        const int gn = n0 + nn;
+        const int gk2 = k0 + kk;
+        Bs[kk][nn] = (gn < a.N && gk2 < a.K) ? Bkb[(long long)gk2 * a.sBk + (long long)gn * a.sBn] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < DBK; ++kk) {
+        double ra[4], rb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ra[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  double* C = a.C + (long long)bz * a.sCb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long gm = m0 + ty + 16 * i;
+    if (gm >= a.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= a.N) continue;
+      double* c = C + gm * a.sCm + (long long)gn * a.sCn;
+      if (a.ksplit > 1) {
+        atomicAdd(c, a.alpha * acc[i][j]);
+      } else {
+        *c = a.alpha * acc[i][j] + (a.beta != 0.0 ? a.beta * *c : 0.0);
+      }
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  const long long mt = (a.M + DBM - 1) / DBM;
+  dim3 grid((unsigned)mt, (unsigned)((a.N + DBN - 1) / DBN), (unsigned)(a.batch * a.ksplit));
+  k_dgemm<<<grid, 256, 0, s>>>(a);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Occupations (Eqs. soo, woo) and their Jacobians with respect to gamma.
+// One thread per pair g.  Also validates pair_map and gamma.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_occupations(Dims d, const double* __restrict__ gamma,
+                              const int32_t* __restrict__ pm, DevHeader* hdr, double* n,
+                              double* sqn, double* phi, double* dn, double* dsq, double* dphi) {
+  const int A = d.A, ng = d.ng, npair = d.npair, ncwo = d.ncwo;
+  // every orbital index p >= npair must name a valid pair
+  for (int p = threadIdx.x + blockIdx.x * blockDim.x; p < A; p += blockDim.x * gridDim.x) {
+    const int g = pm[p];
+    if (g < 0 || g >= npair || (p < npair && g != p)) set_status(hdr, DONOF_ERR_PAIR_MAP);
+  }
+  for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < ng; k += blockDim.x * gridDim.x)
+    if (!isfinite(gamma[k])) set_status(hdr, DONOF_ERR_NONFINITE);
+
+  const int g = threadIdx.x + blockIdx.x * blockDim.x;
+  if (g >= npair) return;
+  const double rs2 = 0.70710678118654752440;  // 1/sqrt(2)
+  const double tg = gamma[g];
+  const double cg = cos(tg), sg = sin(tg);
+  // strong orbital g
+  {
+    const double ng_ = 0.5 * (1.0 + cg * cg);
+    const double r = sqrt(ng_);
+    const double dng = -cg * sg;
+    const double sh = fabs(sg) * rs2;                 // sqrt(1 - n_g) = sqrt(h_g)
+    const double dsh = copysign(1.0, sg) * cg * rs2;
+    for (int k = 0; k < ng; ++k) {
+      dn[(size_t)g * ng + k] = 0.0; dsq[(size_t)g * ng + k] = 0.0; dphi[(size_t)g * ng + k] = 0.0;
+    }
+    n[g] = ng_; sqn[g] = r; phi[g] = r * sh;
+    dn[(size_t)g * ng + g] = dng;
+    dsq[(size_t)g * ng + g] = dng / (2.0 * r);
+    dphi[(size_t)g * ng + g] = dng / (2.0 * r) * sh + r * dsh;
+  }
+  // weak orbitals p_1..p_Ng of pair g, in increasing orbital index
+  const double sh = fabs(sg) * rs2;
+  const double dsh = copysign(1.0, sg) * cg * rs2;
+  int i = 0;
+  for (int p = npair; p < A; ++p) {
+    if (pm[p] != g) continue;
+    if (i >= ncwo) { set_status(hdr, DONOF_ERR_PAIR_MAP); break; }
+    const int wbase = npair + g * (ncwo - 1);
+    // sqrt(n_{p_i}) = sh * prod_{j<i} |cos gamma_j| * (|sin gamma_i| unless last)
+    double val = sh;
+    for (int j = 0; j < i; ++j) val *= fabs(cos(gamma[wbase + j]));
+    const bool has_sin = (i < ncwo - 1);
+    if (has_sin) val *= fabs(sin(gamma[wbase + i]));
+    double* dsq_row = dsq + (size_t)p * ng;
+    for (int k = 0; k < ng; ++k) dsq_row[k] = 0.0;
+    // derivative w.r.t. gamma_g
+    {
+      double rest = 1.0;
+      for (int j = 0; j < i; ++j) rest *= fabs(cos(gamma[wbase + j]));
+      if (has_sin) rest *= fabs(sin(gamma[wbase + i]));
+      dsq_row[g] = dsh * rest;
+    }
+    for (int j = 0; j <= i; ++j) {
+      if (j == i && !has_sin) break;
+      const double t = gamma[wbase + j];
+      const double df = (j < i) ? -copysign(1.0, cos(t)) * sin(t) : copysign(1.0, sin(t)) * cos(t);
+      double rest = sh;
+      for (int jj = 0; jj < i; ++jj)
+        if (jj != j) rest *= fabs(cos(gamma[wbase + jj]));
+      if (has_sin && j != i) rest *= fabs(sin(gamma[wbase + i]));
+      dsq_row[wbase + j] = df * rest;
+    }
+    const double nn = val * val;
+    const double om = sqrt(1.0 - nn);
+    n[p] = nn; sqn[p] = val; phi[p] = val * om;
+    for (int k = 0; k < ng; ++k) {
+      const double dnk = 2.0 * val * dsq_row[k];
+      dn[(size_t)p * ng + k] = dnk;
+      dphi[(size_t)p * ng + k] = dsq_row[k] * om - val * dnk / (2.0 * om);
+    }
+    ++i;
+  }
+  if (i != ncwo) set_status(hdr, DONOF_ERR_PAIR_MAP);
+}
+}  // namespace
+
+cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pm, char* ws,
+                               const Layout& L, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (d.npair + threads - 1) / threads;
+  k_occupations<<<blocks, threads, 0, s>>>(
+      d, gamma, pm, (DevHeader*)(ws + L.header), (double*)(ws + L.n), (double*)(ws + L.sqn),
+      (double*)(ws + L.phi), (double*)(ws + L.dn), (double*)(ws + L.dsq), (double*)(ws + L.dphi));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// E = 2 sum_p n_p H_pp + sum_pq (Acoef_pq J_pq + Bcoef_pq K_pq):
+//   same subspace:      Acoef = 0,         Bcoef = Pi_pq               (Eqs. Eg, intra)
+//   different subspace: Acoef = 2 n_p n_q, Bcoef = -n_p n_q - Phi_p Phi_q  (Eq. Efg)
+//                                          -n_p n_q                    (PNOF5)
+//                                          -n_p n_q - 4 Phi_p^2 Phi_q^2 (Eq. Efg_s)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+                               const double* __restrict__ sqn, const double* __restrict__ phi,
+                               double* Ac, double* Bc) {
+  const int A = d.A;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)A * A) return;
+  const int p = (int)(idx / A), q = (int)(idx % A);
+  double a = 0.0, b;
+  if (pm[p] == pm[q]) {
+    const bool p_strong = (p < d.npair), q_strong = (q < d.npair);
+    const double sgn = (p == q || (!p_strong && !q_strong)) ? 1.0 : -1.0;
+    b = sgn * sqn[p] * sqn[q];
+  } else {
+    a = 2.0 * n[p] * n[q];
+    b = -n[p] * n[q];
+    if (d.functional == DONOF_PNOF7) b -= phi[p] * phi[q];
+    else if (d.functional == DONOF_PNOF7S) b -= 4.0 * phi[p] * phi[p] * phi[q] * phi[q];
+  }
+  Ac[idx] = a;
+  Bc[idx] = b;
+}
+}  // namespace
+
+cudaError_t launch_coefficients(const Dims& d, const int32_t* pm, char* ws, const Layout& L,
+                                cudaStream_t s) {
+  const long long tot = (long long)d.A * d.A;
+  k_coefficients<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
+      (double*)(ws + L.Acoef), (double*)(ws + L.Bcoef));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Packed lower triangle -> dense symmetric slices (FP64 path, per block).
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_unpack(const double* __restrict__ Bp, long long np, int N, double* out) {
+  const long long npk = (long long)N * (N + 1) / 2;
+  const long long tot = np * N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long P = i / ((long long)N * N);
+    const int r = (int)((i / N) % N), c = (int)(i % N);
+    const int hi = r > c ? r : c, lo = r > c ? c : r;
+    out[i] = Bp[P * npk + (long long)hi * (hi + 1) / 2 + lo];
+  }
+}
+}  // namespace
+
+cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, double* out,
+                            cudaStream_t s) {
+  const long long npk = (long long)d.N * (d.N + 1) / 2;
+  k_unpack<<<152 * 8, 256, 0, s>>>(Bp + (long long)p0 * npk, np, d.N, out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// H_pp = C_p^T (h C)_p and G_p = n_p (h C)_p.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_hdiag(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
+                        double* Hd) {
+  // one warp per orbital p
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (p >= d.A) return;
+  double s = 0.0;
+  for (int mu = lane; mu < d.N; mu += 32) s += C[(size_t)mu * d.N + p] * hC[(size_t)mu * d.A + p];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Hd[p] = s;
+}
+__global__ void k_ginit(Dims d, const double* __restrict__ n, const double* __restrict__ hC,
+                        double* G) {
+  const long long tot = (long long)d.N * d.A;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x)
+    G[i] = n[i % d.A] * hC[i];
+}
+}  // namespace
+
+cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const Layout& L,
+                               cudaStream_t s) {
+  k_hdiag<<<(d.A + 7) / 8, 256, 0, s>>>(d, C, (const double*)(ws + L.hC), (double*)(ws + L.Hd));
+  k_ginit<<<152 * 4, 256, 0, s>>>(d, (const double*)(ws + L.n), (const double*)(ws + L.hC),
+                                  (double*)(ws + L.G));
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// J_pq += sum_P b[P][p][p] b[P][q][q],  K_pq += sum_P b[P][p][q]^2  (double sums).
+// Grid: x over (p, q), y over chunks of P.
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+__global__ void k_jk(Dims d, const T* __restrict__ b, int np, int ld, double* J, double* K) {
+  const int A = d.A;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)A * A) return;
+  const int p = (int)(idx / A), q = (int)(idx % A);
+  const int chunk = (np + gridDim.y - 1) / gridDim.y;
+  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
+  double sj = 0.0, sk = 0.0;
+  for (int P = P0; P < P1; ++P) {
+    const T* bp = b + (size_t)P * ld * ld;
+    const double dp = (double)bp[(size_t)p * ld + p], dq = (double)bp[(size_t)q * ld + q];
+    const double v = (double)bp[(size_t)p * ld + q];
+    sj = fma(dp, dq, sj);
+    sk = fma(v, v, sk);
+  }
+  if (P0 < P1) {
+    atomicAdd(J + idx, sj);
+    atomicAdd(K + idx, sk);
+  }
+}
+}  // namespace
+
+template <typename T>
+static cudaError_t launch_jk_t(const Dims& d, const T* b, int np, int ld, char* ws,
+                               const Layout& L, cudaStream_t s) {
+  const long long tot = (long long)d.A * d.A;
+  const unsigned gx = (unsigned)((tot + 255) / 256);
+  unsigned gy = (unsigned)((np + 31) / 32);
+  const unsigned want = 152u * 8u;
+  if (gx * gy > want) gy = want / gx > 0 ? want / gx : 1;
+  k_jk<T><<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
+                                     const Layout& L, cudaStream_t s) {
+  return launch_jk_t<double>(d, b, np, ld, ws, L, s);
+}
+cudaError_t launch_jk_accumulate_f32(const Dims& d, const float* b, int np, int ld, char* ws,
+                                     const Layout& L, cudaStream_t s) {
+  return launch_jk_t<float>(d, b, np, ld, ws, L, s);
+}
+
+// ---------------------------------------------------------------------------
+// Y^P[q][p] = Bcoef_qp b^P_qp + delta_qp w^P_p,  w^P_p = sum_r Acoef_pr b^P_rr.
+// G_p = n_p (hC)_p + sum_P X^P Y^P  is then (1/4) dE/dC (Eqs. lowdin, Vee-s, Vee-d).
+// One CTA per auxiliary slice; ld = leading dimension of b and Y (A or Ap), padding
+// entries (q or p >= A) are written as zero.  The float variant also records max |Y|.
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+__global__ void k_build_Y(Dims d, const T* __restrict__ b, T* Y, int np, int ld,
+                          const double* __restrict__ Ac, const double* __restrict__ Bc,
+                          DevHeader* hdr) {
+  extern __shared__ double sh[];  // d[ld], w[ld]
+  double* dv = sh;
+  double* wv = sh + ld;
+  __shared__ float red[32];
+  const int A = d.A;
+  float ymax = 0.f;
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    const T* bp = b + (size_t)P * ld * ld;
+    T* yp = Y + (size_t)P * ld * ld;
+    for (int r = threadIdx.x; r < A; r += blockDim.x) dv[r] = (double)bp[(size_t)r * ld + r];
+    __syncthreads();
+    for (int p = threadIdx.x; p < A; p += blockDim.x) {
+      double w = 0.0;
+      for (int r = 0; r < A; ++r) w = fma(Ac[(size_t)p * A + r], dv[r], w);
+      wv[p] = w;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) {
+      const int q = i / ld, p = i % ld;
+      double v = 0.0;
+      if (q < A && p < A) {
+        v = Bc[(size_t)q * A + p] * (double)bp[i];
+        if (q == p) v += wv[p];
+      }
+      yp[i] = (T)v;
+      ymax = fmaxf(ymax, fabsf((float)v));
+    }
+    __syncthreads();
+  }
+  if (sizeof(T) == 4) {
+    for (int o = 16; o > 0; o >>= 1) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = ymax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int i = 0; i < (int)blockDim.x / 32; ++i) m = fmaxf(m, red[i]);
+      atomicMax(&hdr->maxY_bits, __float_as_uint(m));
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np, char* ws,
+                               const Layout& L, cudaStream_t s) {
+  const int grid = np < 152 * 4 ? np : 152 * 4;
+  k_build_Y<double><<<grid, 256, 2 * d.A * sizeof(double), s>>>(
+      d, b, Y, np, d.A, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef),
+      (DevHeader*)(ws + L.header));
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
+                               const Layout& L, cudaStream_t s) {
+  const int grid = np < 152 * 4 ? np : 152 * 4;
+  k_build_Y<float><<<grid, 256, 2 * d.Ap * sizeof(double), s>>>(
+      d, b, Y, np, d.Ap, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef),
+      (DevHeader*)(ws + L.header));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Energy and occupation gradient (one CTA, double throughout).
+//   dE/dn_p     = 2 H_pp + 2 sum_{q not in g(p)} n_q (2 J_pq - K_pq)
+//                 [PNOF7s: - 8 (1 - 2 n_p) sum_{q not in g(p)} Phi_q^2 K_pq]
+//   dE/dsqrt_np = 2 sum_{q in g(p)} s_pq sqrt(n_q) K_pq   (s_pq the sign of Pi_pq)
+//   dE/dPhi_p   = -2 sum_{q not in g(p)} Phi_q K_pq       [PNOF7]
+//   dE/dgamma_k = sum_p (dE/dn_p dn_p/dgamma_k + dE/dsqrt_np dsqrt_np/dgamma_k
+//                        + dE/dPhi_p dPhi_p/dgamma_k)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) k_energy(Dims d, const int32_t* __restrict__ pm,
+                                                const double* __restrict__ n,
+                                                const double* __restrict__ sqn,
+                                                const double* __restrict__ phi,
+                                                const double* __restrict__ dn,
+                                                const double* __restrict__ dsq,
+                                                const double* __restrict__ dphi,
+                                                const double* __restrict__ Ac,
+                                                const double* __restrict__ Bc,
+                                                const double* __restrict__ Hd,
+                                                const double* __restrict__ J,
+                                                const double* __restrict__ K, DevHeader* hdr,
+                                                double* dEdg_ws, double* E_out, double* dEdg_out) {
+  extern __shared__ double sh[];  // 3 * A
+  double* gn = sh;
+  double* gs = sh + d.A;
+  double* gp = sh + 2 * d.A;
+  __shared__ double red[32];
+  const int A = d.A;
+  double e = 0.0;
+  for (int p = threadIdx.x; p < A; p += blockDim.x) {
+    e += 2.0 * n[p] * Hd[p];
+    double a_n = 2.0 * Hd[p], a_s = 0.0, a_p = 0.0, a_7s = 0.0;
+    const int g = pm[p];
+    for (int q = 0; q < A; ++q) {
+      const double kpq = K[(size_t)p * A + q];
+      e += Ac[(size_t)p * A + q] * J[(size_t)p * A + q] + Bc[(size_t)p * A + q] * kpq;
+      if (pm[q] == g) {
+        const bool sgnp = (p == q || (p >= d.npair && q >= d.npair));
+        a_s += (sgnp ? 2.0 : -2.0) * sqn[q] * kpq;
+      } else {
+        a_n += 2.0 * n[q] * (2.0 * J[(size_t)p * A + q] - kpq);
+        a_p -= 2.0 * phi[q] * kpq;
+        a_7s += phi[q] * phi[q] * kpq;
+      }
+    }
+    if (d.functional == DONOF_PNOF7S) a_n -= 8.0 * (1.0 - 2.0 * n[p]) * a_7s;
+    gn[p] = a_n;
+    gs[p] = a_s;
+    gp[p] = (d.functional == DONOF_PNOF7) ? a_p : 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x / 32; ++i) t += red[i];
+    hdr->E = t;
+    if (E_out) *E_out = t;
+    if (!isfinite(t)) set_status(hdr, DONOF_ERR_NONFINITE);
+  }
+  for (int k = threadIdx.x; k < d.ng; k += blockDim.x) {
+    double t = 0.0;
+    for (int p = 0; p < A; ++p) {
+      const size_t o = (size_t)p * d.ng + k;
+      t += gn[p] * dn[o] + gs[p] * dsq[o] + gp[p] * dphi[o];
+    }
+    dEdg_ws[k] = t;
+    if (dEdg_out) dEdg_out[k] = t;
+  }
+}
+}  // namespace
+
+cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layout& L,
+                          double* E_out, double* dEdg_out, cudaStream_t s) {
+  const size_t shm = 3 * (size_t)d.A * sizeof(double);
+  if (shm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shm);
+    if (e != cudaSuccess) return e;
+  }
+  k_energy<<<1, 256, shm, s>>>(
+      d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
+      (const double*)(ws + L.dn), (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
+      (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef), (const double*)(ws + L.Hd),
+      (const double*)(ws + L.J), (const double*)(ws + L.K), (DevHeader*)(ws + L.header),
+      (double*)(ws + L.dEdg), E_out, dEdg_out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_zero_cols(double* M, int rows, int ld, int c0, int c1) {
+  const int w = c1 - c0;
+  const long long tot = (long long)rows * w;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x)
+    M[(i / w) * ld + c0 + (i % w)] = 0.0;
+}
+__global__ void k_backward(Dims d, const double* __restrict__ Ebar, const double* __restrict__ G,
+                           const double* __restrict__ dEdg, double* dE_dC, double* dE_dgamma) {
+  const double eb = *Ebar;
+  const long long tot = (long long)d.N * d.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % d.N);
+    const long long mu = i / d.N;
+    if (dE_dC) dE_dC[i] = (p < d.A) ? 4.0 * eb * G[mu * d.A + p] : 0.0;
+    if (dE_dgamma && i < d.ng) dE_dgamma[i] = eb * dEdg[i];
+  }
+}
+}  // namespace
+
+cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0 || rows <= 0) return cudaSuccess;
+  k_zero_cols<<<152 * 4, 256, 0, s>>>(M, rows, ld, c0, c1);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, const Layout& L,
+                            double* dE_dC, double* dE_dgamma, cudaStream_t s) {
+  k_backward<<<152 * 4, 256, 0, s>>>(d, Ebar, (const double*)(ws + L.G),
+                                     (const double*)(ws + L.dEdg), dE_dC, dE_dgamma);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace donof

@@ -1,0 +1,745 @@
+// Tensor-core (tcgen05 + TMEM + TMA) contractions of the mixed-precision build.
+//
+// The three large contractions of one build (DF form of Eqs. JKpq / Gpmn and of the
+// orbital gradient of Eqs. lowdin, Vee-s, Vee-d):
+//   (1) X[P][mu][q] = sum_nu B[P][mu][nu] C[nu][q]         M = np*N, N = Ap, K = N
+//   (2) b[P][p][q]  = sum_mu C[mu][p] X[P][mu][q]          per P: M = Ap, N = Ap, K = N
+//   (3) G[mu][p]   += sum_P sum_q X[P][mu][q] Y[P][q][p]   M = N, N = Ap, K = np*Ap (split)
+// run on one kernel: D = A_hi B_hi + A_hi B_lo + A_lo B_hi, where every operand is an
+// fp16 hi/lo pair of a power-of-two-scaled double or float (error-free splitting in
+// the spirit of the published "3xTF32" / Ozaki splitting; fp16 keeps 11+11 bits), with
+// fp32 accumulation in tensor memory.  Both operands are K-major and staged by TMA with
+// 128-byte (BK = 64) or 64-byte (BK = 32) swizzling.
+//
+// CTA roles (256 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma,
+// warp 2 owns the TMEM allocation, warps 4..7 drain the accumulator (one TMEM lane per
+// thread).  Two accumulators in TMEM let the epilogue of one tile overlap the MMAs of the
+// next.  Persistent grid: one CTA per SM, tiles handed out round-robin.
+#include <cuda.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+namespace donof {
+namespace {
+
+constexpr int BM = 128;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: after kWaitLimitNs it raises the abort flag and DONOF_ERR_TIMEOUT and
+// returns false; it also returns false soon after another role raised the abort flag.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*(volatile int*)abort_flag != 0) return false;
+      if (globaltimer() - t0 > kWaitLimitNs) {
+        atomicExch(abort_flag, 1);
+        atomicCAS(status, 0, (int)DONOF_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile with rows of `swz` bytes
+// (swizzle 128B: layout 2, 64B: layout 4), 8-row core groups `8*swz` bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int swz) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused, K-major swz)
+  d |= (uint64_t)((8u * (uint32_t)swz) >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)(swz == 128 ? 2 : 4) << 61;       // swizzle mode
+  return d;
+}
+// Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ kernel
+struct TcArgs {
+  int mode;        // 1: split-store X (and X^T); 2: fp32 store
+  int M;           // valid output rows per z
+  int Nn;          // output columns = B box rows (multiple of 16, <= 256)
+  int m_tiles, z_count, splits;
+  int kt_per_kb, nkb;
+  int a_z_kb;      // A tile z coordinate = kb (else 0)
+  int b_z_mode;    // 0: 0, 1: z, 2: kb
+  int stages;
+  int acc_stride;  // TMEM columns per accumulator
+  int tmem_cols;
+  // mode 1
+  int Nmu, Ap, Np;
+  __half *xhi, *xlo, *xthi, *xtlo;
+  // mode 2
+  float* out;
+  long long out_ld, out_zstride;
+  const int* scale_exp;
+  int* status;
+  int* abort_flag;
+};
+
+template <int BK>
+__global__ void __launch_bounds__(256, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+              const TcArgs args) {
+  constexpr int SWZ = BK * 2;  // bytes per tile row
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = args.stages;
+  const uint32_t a_bytes = BM * BK * 2;
+  const uint32_t b_bytes = (uint32_t)args.Nn * BK * 2;
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  uint64_t* bars = (uint64_t*)(smem + (size_t)S * stage_bytes);
+  // bars: full[S], empty[S], tfull[2], tempty[2]; then the TMEM address slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int* status = args.status;
+  int* abort_flag = args.abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&bars[i]), 1);
+      mbar_init(smem_u32(&bars[S + i]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * S + 0]), 1);
+    mbar_init(smem_u32(&bars[2 * S + 1]), 1);
+    mbar_init(smem_u32(&bars[2 * S + 2]), 128);
+    mbar_init(smem_u32(&bars[2 * S + 3]), 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(args.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
+
+  const int units = args.z_count * args.m_tiles * args.splits;
+  auto decode = [&](int u, int& z, int& mt, int& sp) {
+    z = u / (args.m_tiles * args.splits);
+    const int r = u % (args.m_tiles * args.splits);
+    mt = r / args.splits;
+    sp = r % args.splits;
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      int z, mt, sp;
+      decode(u, z, mt, sp);
+      const int kb0 = (int)((long long)args.nkb * sp / args.splits);
+      const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
+      for (int kb = kb0; kb < kb1 && ok; ++kb) {
+        const int az = args.a_z_kb ? kb : 0;
+        const int bz = args.b_z_mode == 1 ? z : (args.b_z_mode == 2 ? kb : 0);
+        for (int kt = 0; kt < args.kt_per_kb; ++kt) {
+          const uint32_t eb = smem_u32(&bars[S + stage]);
+          if (!mbar_wait(eb, phase ^ 1u, status, abort_flag)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&bars[stage]);
+          mbar_expect_tx(fb, stage_bytes);
+          const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
+          tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
+          tma_load_3d(base + a_bytes, &mAl, fb, kt * BK, mt * BM, az);
+          tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, 0, bz);
+          tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, 0, bz);
+          if (++stage == S) { stage = 0; phase ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    const uint32_t idesc = idesc_f16(BM, args.Nn);
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    int local = 0;
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++local) {
+      int z, mt, sp;
+      decode(u, z, mt, sp);
+      const int acc = local & 1;
+      const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+      if (!mbar_wait(smem_u32(&bars[2 * S + 2 + acc]), acc_phase ^ 1u, status, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t dt = tmem_base + (uint32_t)(acc * args.acc_stride);
+      const int kb0 = (int)((long long)args.nkb * sp / args.splits);
+      const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
+      const int iters = (kb1 - kb0) * args.kt_per_kb;
+      for (int it = 0; it < iters; ++it) {
+        if (!mbar_wait(smem_u32(&bars[stage]), phase, status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ah = sdesc(base + k * 32, SWZ);
+          const uint64_t al = sdesc(base + a_bytes + k * 32, SWZ);
+          const uint64_t bh = sdesc(base + 2 * a_bytes + k * 32, SWZ);
+          const uint64_t bl = sdesc(base + 2 * a_bytes + b_bytes + k * 32, SWZ);
+          mma_f16(dt, ah, bh, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          mma_f16(dt, ah, bl, idesc, 1u);
+          mma_f16(dt, al, bh, idesc, 1u);
+        }
+        mma_commit(smem_u32(&bars[S + stage]));
+        if (++stage == S) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&bars[2 * S + acc]));
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------ epilogue: TMEM -> registers -> global
+    const int ew = warp - 4;
+    const float scale = ldexpf(1.0f, *args.scale_exp);
+    int local = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
+      int z, mt, sp;
+      decode(u, z, mt, sp);
+      const int acc = local & 1;
+      const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+      bool ok = mbar_wait(smem_u32(&bars[2 * S + acc]), acc_phase, status, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const int row = mt * BM + ew * 32 + lane;
+      const bool valid = row < args.M;
+      const uint32_t taddr =
+          tmem_base + (uint32_t)(acc * args.acc_stride) + ((uint32_t)(ew * 32) << 16);
+      for (int c0 = 0; c0 < args.Nn; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c0, r);
+        if (!valid) continue;
+        if (args.mode == 1) {
+          const int P = row / args.Nmu, mu = row % args.Nmu;
+          __align__(16) __half hi[16], lo[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float v = __uint_as_float(r[j]) * scale;
+            hi[j] = __float2half_rn(v);
+            lo[j] = __float2half_rn(v - __half2float(hi[j]));
+          }
+          const size_t xo = (size_t)row * args.Ap + c0;
+          uint4* dh = (uint4*)(args.xhi + xo);
+          uint4* dl = (uint4*)(args.xlo + xo);
+          dh[0] = ((uint4*)hi)[0]; dh[1] = ((uint4*)hi)[1];
+          dl[0] = ((uint4*)lo)[0]; dl[1] = ((uint4*)lo)[1];
+          const size_t to = ((size_t)P * args.Ap + c0) * args.Np + mu;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            args.xthi[to + (size_t)j * args.Np] = hi[j];
+            args.xtlo[to + (size_t)j * args.Np] = lo[j];
+          }
+        } else {
+          float* o = args.out + (long long)(z * args.splits + sp) * args.out_zstride +
+                     (long long)row * args.out_ld + c0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            float4 v = make_float4(__uint_as_float(r[j]) * scale, __uint_as_float(r[j + 1]) * scale,
+                                   __uint_as_float(r[j + 2]) * scale,
+                                   __uint_as_float(r[j + 3]) * scale);
+            *(float4*)(o + j) = v;
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(args.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host: tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3-D fp16 map: x (contiguous, extent dx), y (extent dy, pitch sy bytes), z (extent dz,
+// pitch sz bytes); box {bx, by, 1}.  Reads past an extent return zeros, so the x extent
+// of every map is the true contraction length (row padding is never read).
+bool make_map(CUtensorMap* m, const void* base, uint64_t dx, uint64_t dy, uint64_t dz, uint64_t sy,
+              uint64_t sz, uint32_t bx, uint32_t by) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {dx, dy, dz};
+  cuuint64_t strides[2] = {sy, sz};
+  cuuint32_t box[3] = {bx, by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUtensorMapSwizzle sw = (bx * 2 == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int BK>
+cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
+                      const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
+  const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)a.Nn * BK * 2;
+  const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const size_t budget = 200 * 1024;
+  int stages = (int)(budget / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) stages = 2;
+  a.stages = stages;
+  int cols = 32;
+  while (cols < a.Nn) cols *= 2;
+  a.acc_stride = cols;
+  a.tmem_cols = 2 * cols;
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 4) * 8 + 16;
+  if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int units = a.z_count * a.m_tiles * a.splits;
+  int grid = num_sms();
+  if (grid > units) grid = units;
+  k_tc_gemm<BK><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ split / scale kernels
+__device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// max |B| and max row norm over (P, mu); one warp per row.
+__global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
+                          DevHeader* hdr) {
+  const long long rows = Q * N;
+  const int lane = threadIdx.x % 32;
+  const long long npk = (long long)N * (N + 1) / 2;
+  double mx = 0.0, mr = 0.0;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; row < rows;
+       row += (long long)gridDim.x * blockDim.x / 32) {
+    const long long P = row / N;
+    const int mu = (int)(row % N);
+    double ss = 0.0, m = 0.0;
+    for (int nu = lane; nu < N; nu += 32) {
+      double v;
+      if (layout == DONOF_B_DENSE) {
+        v = B[row * N + nu];
+      } else {
+        const int hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+        v = B[P * npk + (long long)hi * (hi + 1) / 2 + lo];
+      }
+      ss = fma(v, v, ss);
+      m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    mx = fmax(mx, m);
+    mr = fmax(mr, sqrt(ss));
+  }
+  if (lane == 0) {
+    if (!isfinite(mx) || !isfinite(mr)) set_status(hdr, DONOF_ERR_NONFINITE);
+    atomic_max_nonneg(&hdr->maxB_bits, mx);
+    atomic_max_nonneg(&hdr->maxBrow_bits, mr);
+  }
+}
+
+// B (double, dense or packed) -> scaled fp16 hi/lo [Q][N][Np], columns >= N zero.
+__global__ void k_split_B(const double* __restrict__ B, int layout, long long Q, int N, int Np,
+                          DevHeader* hdr, __half* hi, __half* lo) {
+  const double maxB = __longlong_as_double((long long)hdr->maxB_bits);
+  const int sB = split_exponent(maxB);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hdr->sB = sB;
+    hdr->maxB = maxB;
+    hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
+  }
+  const long long npk = (long long)N * (N + 1) / 2;
+  const long long tot = Q * N * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int nu = (int)(i % Np);
+    const long long r = i / Np;
+    const int mu = (int)(r % N);
+    const long long P = r / N;
+    double v = 0.0;
+    if (nu < N) {
+      if (layout == DONOF_B_DENSE) {
+        v = B[r * N + nu];
+      } else {
+        const int a = mu > nu ? mu : nu, b = mu > nu ? nu : mu;
+        v = B[P * npk + (long long)a * (a + 1) / 2 + b];
+      }
+    }
+    const double x = ldexp(v, sB);
+    const __half h = __double2half(x);
+    hi[i] = h;
+    lo[i] = __double2half(x - (double)__half2float(h));
+  }
+}
+
+// Scale exponents of C_act and X from max |C_act| and max_q ||C_q||_2.
+__global__ void k_c_stats(const double* __restrict__ C, int N, int A, DevHeader* hdr) {
+  __shared__ double smx[256], snr[256];
+  double mx = 0.0, nr = 0.0;
+  for (int q = threadIdx.x; q < A; q += blockDim.x) {
+    double ss = 0.0;
+    for (int mu = 0; mu < N; ++mu) {
+      const double v = C[(size_t)mu * N + q];
+      ss = fma(v, v, ss);
+      mx = fmax(mx, fabs(v));
+    }
+    nr = fmax(nr, sqrt(ss));
+  }
+  smx[threadIdx.x] = mx;
+  snr[threadIdx.x] = nr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)blockDim.x; ++i) {
+      mx = fmax(mx, smx[i]);
+      nr = fmax(nr, snr[i]);
+    }
+    if (!isfinite(mx)) set_status(hdr, DONOF_ERR_NONFINITE);
+    const int sC = split_exponent(mx);
+    const int sX = split_exponent(hdr->maxBrow * nr);
+    hdr->sC = sC;
+    hdr->sX = sX;
+    hdr->e1 = sX - hdr->sB - sC;
+    hdr->e2 = -sC - sX;
+  }
+}
+
+// Ct[p][mu] = C[mu][p] * 2^sC as fp16 hi/lo, [Ap][Np], zero padding.
+__global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, int Np,
+                          const DevHeader* hdr, __half* hi, __half* lo) {
+  const int sC = hdr->sC;
+  const long long tot = (long long)Ap * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i / Np), mu = (int)(i % Np);
+    const double v = (p < A && mu < N) ? C[(size_t)mu * N + p] : 0.0;
+    const double x = ldexp(v, sC);
+    const __half h = __double2half(x);
+    hi[i] = h;
+    lo[i] = __double2half(x - (double)__half2float(h));
+  }
+}
+
+// Y (fp32) -> scaled fp16 hi/lo; exponent from max |Y| of the block.
+__global__ void k_split_Y(const float* __restrict__ Y, long long tot, DevHeader* hdr, __half* hi,
+                          __half* lo) {
+  const float maxY = __uint_as_float(hdr->maxY_bits);
+  const int sY = split_exponent((double)maxY);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hdr->sY = sY;
+    hdr->e3 = -hdr->sX - sY;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float x = ldexpf(Y[i], sY);
+    const __half h = __float2half_rn(x);
+    hi[i] = h;
+    lo[i] = __float2half_rn(x - __half2float(h));
+  }
+}
+
+// G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]   (double sums)
+__global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
+                           const DevHeader* hdr, double* G) {
+  const double sc = ldexp(1.0, hdr->e3);
+  const long long tot = (long long)N * A;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long mu = i / A;
+    const int p = (int)(i % A);
+    double s = 0.0;
+    for (int k = 0; k < S; ++k) s += (double)Gp[((long long)k * N + mu) * Ap + p];
+    G[i] += sc * s;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, const Layout& L,
+                                   cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->maxB_bits, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr);
+  k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, hdr,
+                                          (__half*)(ws + L.Bhi), (__half*)(ws + L.Blo));
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
+                           cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  k_c_stats<<<1, 256, 0, s>>>(C, d.N, d.A, hdr);
+  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, hdr, (__half*)(ws + L.Chi),
+                                      (__half*)(ws + L.Clo));
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  k_split_Y<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Y32), (long long)np * d.Ap * d.Ap,
+                                          hdr, (__half*)(ws + L.Yhi), (__half*)(ws + L.Ylo));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
+  k_reduce_G<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Gpart), d.splits, d.N, d.A, d.Ap,
+                                           (const DevHeader*)(ws + L.header), (double*)(ws + L.G));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// The tensor-core part of one block of np auxiliary slices (slices p0 .. p0+np-1).
+int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, Ap = d.Ap, Np = d.Np;
+  CUtensorMap ah, al, bh, bl;
+  const size_t h2 = sizeof(__half);
+  // (1) X = B C_act
+  prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
+  {
+    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
+    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * N * Np;
+    const uint64_t rows = (uint64_t)np * N;
+    if (!make_map(&ah, Bh, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
+        !make_map(&al, Bl, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
+        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+      return DONOF_ERR_CUDA;
+    TcArgs a{};
+    a.mode = 1; a.M = (int)rows; a.Nn = Ap;
+    a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
+    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.Nmu = N; a.Ap = Ap; a.Np = Np;
+    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
+    a.xthi = (__half*)(ws + L.Xthi); a.xtlo = (__half*)(ws + L.Xtlo);
+    a.scale_exp = &hdr->e1; a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<64>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  }
+  prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
+  // (2) b[P] = C_act^T X[P]
+  prof_begin(DONOF_PHASE_MO_3INDEX, s);
+  {
+    if (!make_map(&ah, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
+        !make_map(&al, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
+        !make_map(&bh, ws + L.Xthi, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+        !make_map(&bl, ws + L.Xtlo, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+      return DONOF_ERR_CUDA;
+    TcArgs a{};
+    a.mode = 2; a.M = Ap; a.Nn = Ap;
+    a.m_tiles = (Ap + BM - 1) / BM; a.z_count = np; a.splits = 1;
+    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 1;
+    a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = (long long)Ap * Ap;
+    a.scale_exp = &hdr->e2; a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<64>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  }
+  prof_end(DONOF_PHASE_MO_3INDEX, s);
+  // J, K and Y from b
+  prof_begin(DONOF_PHASE_JK_Y, s);
+  if (launch_jk_accumulate_f32(d, (const float*)(ws + L.b32), np, Ap, ws, L, s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (cudaMemsetAsync(&hdr->maxY_bits, 0, sizeof(unsigned int), s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (launch_build_Y_f32(d, (const float*)(ws + L.b32), (float*)(ws + L.Y32), np, ws, L, s) !=
+      cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (launch_split_Y(d, np, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  prof_end(DONOF_PHASE_JK_Y, s);
+  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]
+  prof_begin(DONOF_PHASE_G_BUILD, s);
+  {
+    if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
+        !make_map(&al, ws + L.Xlo, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
+        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, 32, Ap) ||
+        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, 32, Ap))
+      return DONOF_ERR_CUDA;
+    TcArgs a{};
+    a.mode = 2; a.M = N; a.Nn = Ap;
+    a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
+    a.splits = d.splits < np ? d.splits : np;
+    a.kt_per_kb = (Ap + 31) / 32; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
+    a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
+    a.scale_exp = &hdr->zero_exp;  // partials stay in scaled units
+    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<32>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    Dims d2 = d;
+    d2.splits = a.splits;
+    if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  }
+  prof_end(DONOF_PHASE_G_BUILD, s);
+  return DONOF_OK;
+}
+
+}  // namespace donof
+
+// ---------------------------------------------------------------------------
+// Test hook (include/donof_testing.h): one plain split-product GEMM.
+// ---------------------------------------------------------------------------
+#include "../../include/donof_testing.h"
+
+namespace donof {
+namespace {
+__device__ int g_test_words[4];  // [0] zero exponent, [1] status, [2] abort flag
+}  // namespace
+}  // namespace donof
+
+extern "C" int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo,
+                                     const uint16_t* B_hi, const uint16_t* B_lo, float* D,
+                                     int32_t M, int32_t N, int32_t K, void* stream) {
+  using namespace donof;
+  if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
+  if (M < 1 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
+    return DONOF_ERR_INVALID_ARG;
+  int* words = nullptr;
+  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
+  CUtensorMap ah, al, bh, bl;
+  const uint64_t h2 = 2;
+  if (!make_map(&ah, A_hi, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM) ||
+      !make_map(&al, A_lo, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM) ||
+      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
+      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
+    return DONOF_ERR_CUDA;
+  TcArgs a{};
+  a.mode = 2; a.M = M; a.Nn = N;
+  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
+  a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.out = D; a.out_ld = N; a.out_zstride = 0;
+  a.scale_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
+  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (launch_tc<64>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess) return DONOF_ERR_CUDA;
+  return DONOF_OK;
+}
+
+extern "C" int donof_testing_status(void* stream) {
+  using namespace donof;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DONOF_ERR_CUDA;
+  int* words = nullptr;
+  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, words + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpy(words + 1, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  return st;
+}

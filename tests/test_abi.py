@@ -1,0 +1,86 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared symbol, and the
+host-side argument checks behave (no compute call needs a GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "donof.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_06142_gb300 import build as b
+    b.build()
+    from paper_2004_06142_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(donof_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "donof_energy_lagrangian" in names and "donof_energy_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_enums_match_binding():
+    from paper_2004_06142_gb300 import binding
+    src = open(HEADER).read()
+    def val(name):
+        return int(re.search(rf"\b{name}\s*=\s*(-?\d+)", src).group(1))
+    assert val("DONOF_PNOF5") == binding.PNOF5
+    assert val("DONOF_PNOF7") == binding.PNOF7
+    assert val("DONOF_PNOF7S") == binding.PNOF7S
+    assert val("DONOF_B_PACKED") == binding.B_PACKED
+    assert val("DONOF_MIXED") == binding.MIXED
+    for code, text in binding.STATUS.items():
+        assert binding.donof_status_string(code) == text
+
+
+def test_struct_layout_matches_header(lib):
+    from paper_2004_06142_gb300 import binding
+    assert ctypes.sizeof(binding.donof_problem) == 8 * 4 + 8
+
+
+def test_workspace_size_and_argument_checks(lib):
+    from paper_2004_06142_gb300 import binding as b
+    small = b.donof_workspace_size(b.make_problem(24, 96, 5, 1))
+    assert small > 0
+    mixed = b.donof_workspace_size(b.make_problem(24, 96, 5, 1, precision=b.MIXED))
+    assert mixed > small
+    budget = b.donof_workspace_size(b.make_problem(500, 2000, 20, 3, x_budget_bytes=1 << 26))
+    full = b.donof_workspace_size(b.make_problem(500, 2000, 20, 3))
+    assert budget < full
+    bad = [
+        b.make_problem(0, 96, 5, 1),
+        b.make_problem(24, 96, 5, 1, functional=6),
+        b.make_problem(24, 96, 13, 1),           # nact > nbf
+        b.make_problem(24, 96, 5, 1, b_layout=3),
+        b.make_problem(24, 96, 5, 1, precision=2),
+    ]
+    for p in bad:
+        with pytest.raises(b.DonofError) as e:
+            b.donof_workspace_size(p)
+        assert e.value.code == -1
+    with pytest.raises(b.DonofError) as e:       # nact 300 > 256 on the tensor-core path
+        b.donof_workspace_size(b.make_problem(400, 100, 100, 2, precision=b.MIXED))
+    assert e.value.code == -7
+
+
+def test_entry_points_reject_null_workspace(lib):
+    from paper_2004_06142_gb300 import binding as b
+    p = b.make_problem(24, 96, 5, 1)
+    rc = lib.donof_prepare_B(ctypes.byref(p), ctypes.c_void_p(256), None, 0, None)
+    assert rc == -4
+    E = ctypes.c_void_p(256)
+    rc = lib.donof_energy_lagrangian(ctypes.byref(p), E, E, E, E, E, None, 0, E, None, None, None)
+    assert rc == -4
+    rc = lib.donof_energy_lagrangian(ctypes.byref(p), None, E, E, E, E, E, 0, E, None, None, None)
+    assert rc == -1

@@ -1,0 +1,90 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 path |dE| <= 1e-10 Eh and 1e-10 elementwise on lambda, dE/dgamma,
+dE/dC, J, K (double arithmetic with a different contraction order: the differences are
+rounding only).  Mixed path (fp16 hi+lo split operands, fp32 tensor-core accumulation,
+double cross-tile sums): |dE| <= 1e-6 Eh, gradients <= 1e-5 max-abs, lambda <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pnof
+
+from helpers import gpu_build
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+MIX_E, MIX_G = 1e-6, 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2004_06142_gb300.build as b
+    b.build()
+
+
+def oracle(prob, d, functional, packed=False):
+    return pnof.build(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], prob.npair, prob.ncwo,
+                      functional)
+
+
+def compare(out, ref, tol_e, tol_g, tol_lam, tol_jk=None):
+    assert out["status"] == 0
+    assert abs(out["E"] - ref["E"]) <= tol_e, (out["E"], ref["E"])
+    np.testing.assert_allclose(out["dE_dgamma"], ref["dE_dgamma"], rtol=0, atol=tol_g)
+    np.testing.assert_allclose(out["dE_dgamma_bwd"], ref["dE_dgamma"], rtol=0, atol=tol_g)
+    np.testing.assert_allclose(out["dE_dC"], ref["dE_dC"], rtol=0, atol=tol_g)
+    np.testing.assert_allclose(out["lam"], ref["lam"], rtol=0, atol=tol_lam)
+    tj = tol_jk if tol_jk is not None else tol_lam
+    np.testing.assert_allclose(out["J"], ref["J"], rtol=0, atol=tj)
+    np.testing.assert_allclose(out["K"], ref["K"], rtol=0, atol=tj)
+
+
+CASES = [
+    # name, nbf, naux, npair, ncwo
+    ("plain", 24, 96, 5, 1),
+    ("ragged", 41, 37, 3, 2),
+    ("ragged2", 97, 150, 4, 3),
+    ("differentiation", 120, 480, 8, 4),
+    ("tail", 130, 257, 6, 4),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("functional", [pnof.PNOF7, pnof.PNOF5, pnof.PNOF7S])
+def test_fp64_path(case, functional):
+    _, nbf, naux, npair, ncwo = case
+    prob = synth.Problem(nbf, naux, npair, ncwo, seed=1)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, functional)
+    out = gpu_build(prob, d, 0, functional)
+    compare(out, ref, F64_TOL, F64_TOL, F64_TOL)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("functional", [pnof.PNOF7, pnof.PNOF5, pnof.PNOF7S])
+def test_mixed_path(case, functional):
+    _, nbf, naux, npair, ncwo = case
+    prob = synth.Problem(nbf, naux, npair, ncwo, seed=2)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, functional)
+    out = gpu_build(prob, d, 1, functional)
+    compare(out, ref, MIX_E, MIX_G, MIX_G, tol_jk=MIX_G)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_packed_and_blocked(precision):
+    """Packed B and a budget that streams P in several blocks (with a ragged last one)."""
+    prob = synth.Problem(57, 203, 4, 2, seed=3)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, pnof.PNOF7)
+    budget = 40 * 57 * 16 * 8 if precision == 0 else 30 * (57 * 16 * 4 + 16 * 64 * 4 + 16 * 16 * 12)
+    tol = (F64_TOL, F64_TOL, F64_TOL) if precision == 0 else (MIX_E, MIX_G, MIX_G)
+    for packed in (False, True):
+        out = gpu_build(prob, d, precision, pnof.PNOF7, packed=packed, budget=budget)
+        compare(out, ref, *tol)
