@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--naux", type=int, default=0,
+                    help="override naux (profiling captures on a slice of the workload)")
     return ap.parse_args()
 
 
@@ -249,7 +251,9 @@ def run_ours(args):
     libbuild.build()
     import paper_2004_06142_gb300 as dn
 
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.naux:
+        w["naux"] = args.naux
     N, Q = w["nbf"], w["naux"]
     prob, host, x = make_inputs(w, args.seed, dev)
     A = prob.nact

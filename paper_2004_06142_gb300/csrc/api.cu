@@ -34,7 +34,8 @@ Dims make_dims(const donof_problem* p) {
     perP = (size_t)d.N * d.A * 8 + 2 * (size_t)d.A * d.A * 8 +
            (d.layout == DONOF_B_PACKED ? (size_t)d.N * d.N * 8 : 0);
   } else {
-    perP = (size_t)d.N * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4);
+    perP = (size_t)d.N * d.Ap * 8 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
+           (size_t)d.Ap * 4;
   }
   long long pb = d.Q;
   if (p->x_budget_bytes > 0) {
@@ -88,12 +89,16 @@ Layout make_layout(const Dims& d) {
     const size_t Q = d.Q;
     L.Bhi = take(Q * N * Np * 2);
     L.Blo = take(Q * N * Np * 2);
+    L.eB = take(Q * N * 4);
     L.Chi = take(Ap * Np * 2);
     L.Clo = take(Ap * Np * 2);
+    L.eC = take(Ap * 4);
     L.Xhi = take(pb * N * Ap * 2);
     L.Xlo = take(pb * N * Ap * 2);
+    L.X32 = take(pb * N * Ap * 4);
     L.Xthi = take(pb * Ap * Np * 2);
     L.Xtlo = take(pb * Ap * Np * 2);
+    L.eXt = take(pb * Ap * 4);
     L.b32 = take(pb * Ap * Ap * 4);
     L.Y32 = take(pb * Ap * Ap * 4);
     L.Yhi = take(pb * Ap * Ap * 2);
@@ -189,6 +194,26 @@ int check_ws(const donof_problem* p, const void* ws, size_t bytes) {
   return bytes >= L.total ? DONOF_OK : DONOF_ERR_WORKSPACE;
 }
 
+// C(m, n) += sum_k A(m, k) B(k, n) for an M x N output with a long contraction K: the
+// contraction is cut into 64-wide chunks shared by enough CTAs to fill the GPU (atomic
+// double accumulation, so C must be initialised).
+DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long long sAk,
+                       const double* B, long long sBk, long long sBn, double* C, long long sCm,
+                       long long sCn) {
+  DgemmArgs a{};
+  a.M = M; a.N = N; a.K = 64; a.KB = (K + 63) / 64; a.Ktot = K; a.batch = 1;
+  const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+  long long ks = (3 * 152 + tiles - 1) / tiles;
+  if (ks > a.KB) ks = a.KB;
+  if (ks < 1) ks = 1;
+  a.ksplit = (int)ks;
+  a.A = A; a.sAm = sAm; a.sAk = sAk; a.sAkb = 64 * sAk;
+  a.B = B; a.sBk = sBk; a.sBn = sBn; a.sBkb = 64 * sBk;
+  a.C = C; a.sCm = sCm; a.sCn = sCn;
+  a.alpha = 1.0; a.beta = 1.0;
+  return a;
+}
+
 #define CK(x)                                  \
   do {                                         \
     if ((x) != cudaSuccess) return DONOF_ERR_CUDA; \
@@ -254,15 +279,8 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(launch_occupations(d, gamma, pair_map, ws, L, s));
   CK(launch_coefficients(d, pair_map, ws, L, s));
   // hC = h C_act, H_pp, G = n o hC
-  {
-    DgemmArgs a{};
-    a.M = N; a.N = A; a.K = N; a.KB = 1; a.batch = 1; a.ksplit = 1;
-    a.A = h; a.sAm = N; a.sAk = 1;
-    a.B = C; a.sBk = N; a.sBn = 1;
-    a.C = (double*)(ws + L.hC); a.sCm = A; a.sCn = 1;
-    a.alpha = 1.0; a.beta = 0.0;
-    CK(launch_dgemm(a, s));
-  }
+  CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
+  CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1), s));
   CK(launch_hdiag_ginit(d, C, ws, L, s));
   CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
   CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
@@ -333,14 +351,8 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   prof_begin(DONOF_PHASE_ENERGY_LAMBDA, s);
   CK(launch_energy(d, pair_map, ws, L, E, dE_dgamma, s));
   if (lam) {  // lambda_qp = C_q^T G_p (q < N, p < nact), zero for p >= nact
-    DgemmArgs a{};
-    a.M = N; a.N = A; a.K = N; a.KB = 1; a.batch = 1; a.ksplit = 1;
-    a.A = C; a.sAm = 1; a.sAk = N;
-    a.B = (const double*)(ws + L.G); a.sBk = A; a.sBn = 1;
-    a.C = lam; a.sCm = N; a.sCn = 1;
-    a.alpha = 1.0;
-    CK(launch_dgemm(a, s));
-    CK(launch_zero_cols(lam, N, N, A, N, s));
+    CK(cudaMemsetAsync(lam, 0, (size_t)N * N * 8, s));
+    CK(launch_dgemm(split_k_args(N, A, N, C, 1, N, (const double*)(ws + L.G), A, 1, lam, N, 1), s));
   }
   prof_end(DONOF_PHASE_ENERGY_LAMBDA, s);
   return DONOF_OK;

@@ -21,6 +21,7 @@ struct DevHeader {
   double maxB;           // max |B|                      (set by prepare)
   double maxBrow;        // max_P,mu ||B[P][mu][:]||_2   (set by prepare)
   unsigned long long maxB_bits, maxBrow_bits;  // atomicMax scratch (double bits, >= 0)
+  unsigned long long maxCcol_bits;  // max column norm of C_act (double bits)
   unsigned int maxY_bits;  // max |Y| of the current block (float bits)
   int32_t zero_exp;       // always 0 (epilogue exponent of raw partial sums)
   int32_t abort_flag;     // set when a bounded device wait gives up; cleared per build
@@ -46,7 +47,9 @@ struct Layout {
   // FP64 path
   size_t X64, b64, Y64, Bun, W64;
   // mixed path
-  size_t Bhi, Blo, Chi, Clo, Xhi, Xlo, Xthi, Xtlo, b32, Y32, Yhi, Ylo, Gpart;
+  // Bhi/Blo, Chi/Clo, Xthi/Xtlo hold integer + fraction planes, Xhi/Xlo and Yhi/Ylo
+  // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
+  size_t Bhi, Blo, eB, Chi, Clo, eC, Xhi, Xlo, X32, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo, Gpart;
   size_t total;
 };
 
@@ -82,8 +85,10 @@ __host__ __device__ inline int split_exponent(double bound) {
 // with A(m, kb, k) = A[b*sAb + m*sAm + kb*sAkb + k*sAk] and
 //      B(kb, k, n) = B[b*sBb + kb*sBkb + k*sBk + n*sBn];
 // ksplit > 1 splits the kb range over CTAs and accumulates with atomicAdd (beta must be 1).
+// Ktot > 0 limits the flattened contraction index kb*K + k to [0, Ktot) (used to split one
+// long contraction into KB chunks of K that ksplit CTAs share).
 struct DgemmArgs {
-  int M, N, K, KB, batch, ksplit;
+  int M, N, K, KB, batch, ksplit, Ktot;
   const double* A; long long sAb, sAm, sAk, sAkb;
   const double* B; long long sBb, sBk, sBn, sBkb;
   double* C; long long sCb, sCm, sCn;

@@ -45,12 +45,14 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
         if (a_m_fast) { mm = idx % DBM; kk = idx / DBM; } else { kk = idx % DBK; mm = idx / DBK; }
         const long long gm = m0 + mm;
         const int gk = k0 + kk;
-        As[kk][mm] = (gm < a.M && gk < a.K) ? Akb[gm * a.sAm + (long long)gk * a.sAk] : 0.0;
+        const bool kin = gk < a.K && (a.Ktot <= 0 || kb * a.K + gk < a.Ktot);
+        As[kk][mm] = (gm < a.M && kin) ? Akb[gm * a.sAm + (long long)gk * a.sAk] : 0.0;
         int nn;
         if (b_n_fast) { nn = idx % DBN; kk = idx / DBN; } else { kk = idx % DBK; nn = idx / DBK; }
         const int gn = n0 + nn;
         const int gk2 = k0 + kk;
-        Bs[kk][nn] = (gn < a.N && gk2 < a.K) ? Bkb[(long long)gk2 * a.sBk + (long long)gn * a.sBn] : 0.0;
+        const bool kin2 = gk2 < a.K && (a.Ktot <= 0 || kb * a.K + gk2 < a.Ktot);
+        Bs[kk][nn] = (gn < a.N && kin2) ? Bkb[(long long)gk2 * a.sBk + (long long)gn * a.sBn] : 0.0;
       }
       __syncthreads();
 #pragma unroll

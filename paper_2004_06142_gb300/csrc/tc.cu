@@ -129,8 +129,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // ------------------------------------------------------------------ kernel
+// Operand numerics.
+//   kSplit3: every operand x is s * (hi + lo), hi = fp16(x / s), lo = fp16(x / s - hi), with one
+//            power-of-two s per matrix; D = hi*hi + hi*lo + lo*hi in one fp32 accumulator.
+//   kIntFrac: every operand row r is u_r * (h + f) with u_r = 2^e_r chosen from the row's
+//            L2 norm so that ||h||_2 < 2^12, h integer (|h| <= 2048, exact in fp16) and
+//            f = fp16(x / u_r - h) in [-1/2, 1/2].  For any two rows |sum_k h_a h_b| < 2^24
+//            (Cauchy-Schwarz, every partial sum included), so the integer products
+//            accumulate exactly in fp32 -- the tensor core's truncating accumulation
+//            cannot bias them.  h*h goes to accumulator 0, h*f + f*h + f*f to accumulator 1.
+constexpr int kSplit3 = 0;
+constexpr int kIntFrac = 1;
+constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
+
 struct TcArgs {
-  int mode;        // 1: split-store X (and X^T); 2: fp32 store
+  int mode;        // 1: X store (fp32 + hi/lo split for the G contraction); 2: fp32 store
   int M;           // valid output rows per z
   int Nn;          // output columns = B box rows (multiple of 16, <= 256)
   int m_tiles, z_count, splits;
@@ -138,20 +151,31 @@ struct TcArgs {
   int a_z_kb;      // A tile z coordinate = kb (else 0)
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
-  int acc_stride;  // TMEM columns per accumulator
+  int nbuf;        // TMEM accumulator sets (1 or 2)
+  int buf_stride;  // TMEM columns per accumulator set
   int tmem_cols;
-  // mode 1
-  int Nmu, Ap, Np;
-  __half *xhi, *xlo, *xthi, *xtlo;
-  // mode 2
+  // per-row / per-column exponents (kIntFrac): value = 2^(eA[row] + eB[col]) * acc
+  const int* eA; long long eA_zstride;
+  const int* eB; long long eB_zstride;
+  const int* glob_exp;  // extra power of two applied to every output (mode 2), or the
+                        // exponent of the hi/lo split written for the G contraction (mode 1)
+  // mode 1 outputs, X[row][c] with row = P * Nmu + mu
+  int Nmu, Ap;
+  __half *xhi, *xlo;
+  float* x32;
+  // mode 2 output
   float* out;
   long long out_ld, out_zstride;
-  const int* scale_exp;
   int* status;
   int* abort_flag;
 };
 
-template <int BK>
+__device__ __forceinline__ float pow2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((e + 127) << 23);
+}
+
+template <int BK, int NUM>
 __global__ void __launch_bounds__(256, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -170,6 +194,7 @@ __global__ void __launch_bounds__(256, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int* status = args.status;
   int* abort_flag = args.abort_flag;
+  const int nbuf = args.nbuf;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
@@ -240,11 +265,12 @@ __global__ void __launch_bounds__(256, 1)
     for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++local) {
       int z, mt, sp;
       decode(u, z, mt, sp);
-      const int acc = local & 1;
-      const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+      const int acc = local % nbuf;
+      const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
       if (!mbar_wait(smem_u32(&bars[2 * S + 2 + acc]), acc_phase ^ 1u, status, abort_flag)) break;
       tc_fence_after();
-      const uint32_t dt = tmem_base + (uint32_t)(acc * args.acc_stride);
+      const uint32_t d0 = tmem_base + (uint32_t)(acc * args.buf_stride);
+      const uint32_t d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
       const int kb0 = (int)((long long)args.nkb * sp / args.splits);
       const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
       const int iters = (kb1 - kb0) * args.kt_per_kb;
@@ -258,9 +284,17 @@ __global__ void __launch_bounds__(256, 1)
           const uint64_t al = sdesc(base + a_bytes + k * 32, SWZ);
           const uint64_t bh = sdesc(base + 2 * a_bytes + k * 32, SWZ);
           const uint64_t bl = sdesc(base + 2 * a_bytes + b_bytes + k * 32, SWZ);
-          mma_f16(dt, ah, bh, idesc, (it > 0 || k > 0) ? 1u : 0u);
-          mma_f16(dt, ah, bl, idesc, 1u);
-          mma_f16(dt, al, bh, idesc, 1u);
+          const uint32_t first = (it > 0 || k > 0) ? 1u : 0u;
+          if (NUM == kSplit3) {
+            mma_f16(d0, ah, bh, idesc, first);
+            mma_f16(d0, ah, bl, idesc, 1u);
+            mma_f16(d0, al, bh, idesc, 1u);
+          } else {
+            mma_f16(d0, ah, bh, idesc, first);  // integer x integer: exact
+            mma_f16(d1, ah, bl, idesc, first);
+            mma_f16(d1, al, bh, idesc, 1u);
+            mma_f16(d1, al, bl, idesc, 1u);
+          }
         }
         mma_commit(smem_u32(&bars[S + stage]));
         if (++stage == S) { stage = 0; phase ^= 1u; }
@@ -271,59 +305,102 @@ __global__ void __launch_bounds__(256, 1)
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue: TMEM -> registers -> global
     const int ew = warp - 4;
-    const float scale = ldexpf(1.0f, *args.scale_exp);
+    const int glob = args.glob_exp ? *args.glob_exp : 0;
     int local = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
       int z, mt, sp;
       decode(u, z, mt, sp);
-      const int acc = local & 1;
-      const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+      const int acc = local % nbuf;
+      const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
       bool ok = mbar_wait(smem_u32(&bars[2 * S + acc]), acc_phase, status, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
       const int row = mt * BM + ew * 32 + lane;
       const bool valid = row < args.M;
-      const uint32_t taddr =
-          tmem_base + (uint32_t)(acc * args.acc_stride) + ((uint32_t)(ew * 32) << 16);
-      for (int c0 = 0; c0 < args.Nn; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(taddr + (uint32_t)c0, r);
-        if (!valid) continue;
+      const uint32_t t0 =
+          tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
+      const uint32_t t1 = t0 + (uint32_t)args.Nn;
+      const int erow = (NUM == kIntFrac && valid) ? args.eA[z * args.eA_zstride + row] : 0;
+      const int* ecol = (NUM == kIntFrac) ? args.eB + z * args.eB_zstride : nullptr;
+
+      // one 16-column chunk: raw accumulator values -> outputs
+      auto emit = [&](int c0, const float (&a)[16]) {
+        if (!valid) return;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int e = (NUM == kIntFrac ? erow + ecol[c0 + j] : 0) + (args.mode == 2 ? glob : 0);
+          v[j] = a[j] * pow2f(e);
+        }
         if (args.mode == 1) {
-          const int P = row / args.Nmu, mu = row % args.Nmu;
+          float* xo = args.x32 + (size_t)row * args.Ap + c0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *(float4*)(xo + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          const float s = pow2f(glob);
           __align__(16) __half hi[16], lo[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float v = __uint_as_float(r[j]) * scale;
-            hi[j] = __float2half_rn(v);
-            lo[j] = __float2half_rn(v - __half2float(hi[j]));
+            const float w = v[j] * s;
+            hi[j] = __float2half_rn(w);
+            lo[j] = __float2half_rn(w - __half2float(hi[j]));
           }
-          const size_t xo = (size_t)row * args.Ap + c0;
-          uint4* dh = (uint4*)(args.xhi + xo);
-          uint4* dl = (uint4*)(args.xlo + xo);
+          const size_t o = (size_t)row * args.Ap + c0;
+          uint4* dh = (uint4*)(args.xhi + o);
+          uint4* dl = (uint4*)(args.xlo + o);
           dh[0] = ((uint4*)hi)[0]; dh[1] = ((uint4*)hi)[1];
           dl[0] = ((uint4*)lo)[0]; dl[1] = ((uint4*)lo)[1];
-          const size_t to = ((size_t)P * args.Ap + c0) * args.Np + mu;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            args.xthi[to + (size_t)j * args.Np] = hi[j];
-            args.xtlo[to + (size_t)j * args.Np] = lo[j];
-          }
         } else {
           float* o = args.out + (long long)(z * args.splits + sp) * args.out_zstride +
                      (long long)row * args.out_ld + c0;
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]) * scale, __uint_as_float(r[j + 1]) * scale,
-                                   __uint_as_float(r[j + 2]) * scale,
-                                   __uint_as_float(r[j + 3]) * scale);
-            *(float4*)(o + j) = v;
+          for (int j = 0; j < 16; j += 4) *(float4*)(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      };
+      auto load = [&](int c0, float (&a)[16]) {
+        uint32_t r[16];
+        tmem_ld16(t0 + (uint32_t)c0, r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] = __uint_as_float(r[j]);
+        if (NUM == kIntFrac) {
+          tmem_ld16(t1 + (uint32_t)c0, r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] += __uint_as_float(r[j]);
+        }
+      };
+
+      if (args.Nn <= kMaxRegCols) {
+        // drain the accumulators into registers, hand TMEM back, then write
+        float keep[kMaxRegCols];
+#pragma unroll
+        for (int cc = 0; cc < kMaxRegCols / 16; ++cc) {
+          if (cc * 16 < args.Nn) {
+            float a[16];
+            load(cc * 16, a);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) keep[cc * 16 + j] = a[j];
           }
         }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
+#pragma unroll
+        for (int cc = 0; cc < kMaxRegCols / 16; ++cc) {
+          if (cc * 16 < args.Nn) {
+            float a[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = keep[cc * 16 + j];
+            emit(cc * 16, a);
+          }
+        }
+      } else {
+        for (int c0 = 0; c0 < args.Nn; c0 += 16) {
+          float a[16];
+          load(c0, a);
+          emit(c0, a);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
       }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
     }
   }
   tc_fence_before();
@@ -385,7 +462,7 @@ int num_sms() {
   return n;
 }
 
-template <int BK>
+template <int BK, int NUM>
 cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)a.Nn * BK * 2;
@@ -395,19 +472,21 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
   a.stages = stages;
-  int cols = 32;
-  while (cols < a.Nn) cols *= 2;
-  a.acc_stride = cols;
-  a.tmem_cols = 2 * cols;
+  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart), two sets if they fit
+  const int per_set = (NUM == kIntFrac ? 2 : 1) * a.Nn;
+  a.tmem_cols = 512;
+  a.nbuf = (2 * per_set <= 512) ? 2 : 1;
+  a.buf_stride = (a.nbuf == 2) ? 256 : 0;
+  if (a.nbuf == 2 && per_set > 256) return cudaErrorInvalidValue;
   size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 4) * 8 + 16;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_gemm<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int units = a.z_count * a.m_tiles * a.splits;
   int grid = num_sms();
   if (grid > units) grid = units;
-  k_tc_gemm<BK><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
+  k_tc_gemm<BK, NUM><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -417,9 +496,26 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
-// max |B| and max row norm over (P, mu); one warp per row.
+// Exponent e of the integer + fraction split of a row with L2 norm `nrm`: the row is
+// 2^e (h + f) with ||x / 2^e||_2 <= 2^11, so |h| <= 2048 and ||h||_2 < 2^12.
+__host__ __device__ inline int intfrac_exponent(double nrm) {
+  if (!(nrm > 0.0)) return 0;
+  int e;
+  frexp(nrm, &e);  // nrm <= 2^e
+  return e - 11;
+}
+
+__device__ inline double load_B_elem(const double* __restrict__ B, int layout, long long P,
+                                     long long r, int mu, int nu, int N, long long npk) {
+  if (layout == DONOF_B_DENSE) return B[r * N + nu];
+  const int a = mu > nu ? mu : nu, b = mu > nu ? nu : mu;
+  return B[P * npk + (long long)a * (a + 1) / 2 + b];
+}
+
+// Per row (P, mu): norm -> exponent of its integer + fraction split; global max |B| and
+// max row norm (the latter bounds |X| for the hi/lo split of the G contraction).
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
-                          DevHeader* hdr) {
+                          DevHeader* hdr, int* eB) {
   const long long rows = Q * N;
   const int lane = threadIdx.x % 32;
   const long long npk = (long long)N * (N + 1) / 2;
@@ -430,13 +526,7 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
     const int mu = (int)(row % N);
     double ss = 0.0, m = 0.0;
     for (int nu = lane; nu < N; nu += 32) {
-      double v;
-      if (layout == DONOF_B_DENSE) {
-        v = B[row * N + nu];
-      } else {
-        const int hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-        v = B[P * npk + (long long)hi * (hi + 1) / 2 + lo];
-      }
+      const double v = load_B_elem(B, layout, P, row, mu, nu, N, npk);
       ss = fma(v, v, ss);
       m = fmax(m, fabs(v));
     }
@@ -444,8 +534,10 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
       ss += __shfl_xor_sync(0xffffffffu, ss, o);
       m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     }
+    const double nr = sqrt(ss);
+    if (lane == 0) eB[row] = intfrac_exponent(nr);
     mx = fmax(mx, m);
-    mr = fmax(mr, sqrt(ss));
+    mr = fmax(mr, nr);
   }
   if (lane == 0) {
     if (!isfinite(mx) || !isfinite(mr)) set_status(hdr, DONOF_ERR_NONFINITE);
@@ -454,14 +546,11 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
   }
 }
 
-// B (double, dense or packed) -> scaled fp16 hi/lo [Q][N][Np], columns >= N zero.
+// B (double, dense or packed) -> integer + fraction planes [Q][N][Np], columns >= N zero.
 __global__ void k_split_B(const double* __restrict__ B, int layout, long long Q, int N, int Np,
-                          DevHeader* hdr, __half* hi, __half* lo) {
-  const double maxB = __longlong_as_double((long long)hdr->maxB_bits);
-  const int sB = split_exponent(maxB);
+                          DevHeader* hdr, const int* __restrict__ eB, __half* H, __half* F) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    hdr->sB = sB;
-    hdr->maxB = maxB;
+    hdr->maxB = __longlong_as_double((long long)hdr->maxB_bits);
     hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
   }
   const long long npk = (long long)N * (N + 1) / 2;
@@ -472,66 +561,103 @@ __global__ void k_split_B(const double* __restrict__ B, int layout, long long Q,
     const long long r = i / Np;
     const int mu = (int)(r % N);
     const long long P = r / N;
-    double v = 0.0;
-    if (nu < N) {
-      if (layout == DONOF_B_DENSE) {
-        v = B[r * N + nu];
-      } else {
-        const int a = mu > nu ? mu : nu, b = mu > nu ? nu : mu;
-        v = B[P * npk + (long long)a * (a + 1) / 2 + b];
-      }
-    }
-    const double x = ldexp(v, sB);
-    const __half h = __double2half(x);
-    hi[i] = h;
-    lo[i] = __double2half(x - (double)__half2float(h));
+    const double v = nu < N ? load_B_elem(B, layout, P, r, mu, nu, N, npk) : 0.0;
+    const double y = ldexp(v, -eB[r]);
+    const double h = rint(y);
+    H[i] = __double2half(h);
+    F[i] = __double2half(y - h);
   }
 }
 
-// Scale exponents of C_act and X from max |C_act| and max_q ||C_q||_2.
-__global__ void k_c_stats(const double* __restrict__ C, int N, int A, DevHeader* hdr) {
-  __shared__ double smx[256], snr[256];
-  double mx = 0.0, nr = 0.0;
-  for (int q = threadIdx.x; q < A; q += blockDim.x) {
-    double ss = 0.0;
-    for (int mu = 0; mu < N; ++mu) {
+// Column norms of C_act -> exponents of the integer + fraction split of C_act^T (one warp
+// per column); max column norm for the bound on |X|.
+__global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, int* eC,
+                          DevHeader* hdr) {
+  const int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (q >= Ap) return;
+  double ss = 0.0;
+  if (q < A)
+    for (int mu = lane; mu < N; mu += 32) {
       const double v = C[(size_t)mu * N + q];
       ss = fma(v, v, ss);
-      mx = fmax(mx, fabs(v));
     }
-    nr = fmax(nr, sqrt(ss));
-  }
-  smx[threadIdx.x] = mx;
-  snr[threadIdx.x] = nr;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)blockDim.x; ++i) {
-      mx = fmax(mx, smx[i]);
-      nr = fmax(nr, snr[i]);
-    }
-    if (!isfinite(mx)) set_status(hdr, DONOF_ERR_NONFINITE);
-    const int sC = split_exponent(mx);
-    const int sX = split_exponent(hdr->maxBrow * nr);
-    hdr->sC = sC;
-    hdr->sX = sX;
-    hdr->e1 = sX - hdr->sB - sC;
-    hdr->e2 = -sC - sX;
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) {
+    const double nr = sqrt(ss);
+    if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
+    eC[q] = intfrac_exponent(nr);
+    atomicMax((unsigned long long*)&hdr->maxCcol_bits, (unsigned long long)__double_as_longlong(nr));
   }
 }
 
-// Ct[p][mu] = C[mu][p] * 2^sC as fp16 hi/lo, [Ap][Np], zero padding.
+// Exponent of the hi/lo split of X used by the G contraction: |X| <= maxBrow * max ||C_q||.
+__global__ void k_c_finish(DevHeader* hdr) {
+  const double nc = __longlong_as_double((long long)hdr->maxCcol_bits);
+  hdr->sX = split_exponent(hdr->maxBrow * nc);
+}
+
+// C_act^T -> integer + fraction planes [Ap][Np] (rows q >= A and columns mu >= N zero).
 __global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, int Np,
-                          const DevHeader* hdr, __half* hi, __half* lo) {
-  const int sC = hdr->sC;
+                          const int* __restrict__ eC, __half* H, __half* F) {
   const long long tot = (long long)Ap * Np;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     const int p = (int)(i / Np), mu = (int)(i % Np);
     const double v = (p < A && mu < N) ? C[(size_t)mu * N + p] : 0.0;
-    const double x = ldexp(v, sC);
-    const __half h = __double2half(x);
-    hi[i] = h;
-    lo[i] = __double2half(x - (double)__half2float(h));
+    const double y = ldexp(v, -eC[p]);
+    const double h = rint(y);
+    H[i] = __double2half(h);
+    F[i] = __double2half(y - h);
+  }
+}
+
+// X^T for the b contraction: X32[P][mu][q] (fp32) -> integer + fraction planes
+// XtH/XtF[P][q][mu] with one exponent per (P, q) from the column norm over mu.
+// One CTA per (P, 32 columns); pass 1 reduces the norms, pass 2 transposes through
+// shared memory (the strip is re-read from L2).
+__global__ void __launch_bounds__(256) k_quant_xt(const float* __restrict__ X32, int N, int Ap,
+                                                  int Np, __half* XtH, __half* XtF, int* eXt) {
+  __shared__ float tile[32][33];
+  __shared__ double red[8][32];
+  __shared__ int se[32];
+  const int P = blockIdx.x, q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const float* Xp = X32 + (size_t)P * N * Ap;
+  const bool qok = q0 + tx < Ap;
+  double ss = 0.0;
+  if (qok)
+    for (int mu = ty; mu < N; mu += 8) {
+      const double v = Xp[(size_t)mu * Ap + q0 + tx];
+      ss = fma(v, v, ss);
+    }
+  red[ty][tx] = ss;
+  __syncthreads();
+  if (ty == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i][tx];
+    const int e = intfrac_exponent(sqrt(t));
+    se[tx] = e;
+    if (qok) eXt[(size_t)P * Ap + q0 + tx] = e;
+  }
+  __syncthreads();
+  for (int mu0 = 0; mu0 < Np; mu0 += 32) {
+    for (int i = ty; i < 32; i += 8) {
+      const int mu = mu0 + i;
+      tile[i][tx] = (mu < N && qok) ? Xp[(size_t)mu * Ap + q0 + tx] : 0.f;
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+      const int q = q0 + j, mu = mu0 + tx;
+      if (q < Ap && mu < Np) {
+        const float y = tile[tx][j] * pow2f(-se[j]);
+        const float h = rintf(y);
+        const size_t o = ((size_t)P * Ap + q) * Np + mu;
+        XtH[o] = __float2half_rn(h);
+        XtF[o] = __float2half_rn(y - h);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -576,9 +702,10 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->maxB_bits, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr);
+  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB));
   k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, hdr,
-                                          (__half*)(ws + L.Bhi), (__half*)(ws + L.Blo));
+                                          (const int*)(ws + L.eB), (__half*)(ws + L.Bhi),
+                                          (__half*)(ws + L.Blo));
   count_launch(2);
   return cudaGetLastError();
 }
@@ -586,10 +713,13 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
 cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
                            cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  k_c_stats<<<1, 256, 0, s>>>(C, d.N, d.A, hdr);
-  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, hdr, (__half*)(ws + L.Chi),
-                                      (__half*)(ws + L.Clo));
-  count_launch(2);
+  cudaError_t e = cudaMemsetAsync(&hdr->maxCcol_bits, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, (int*)(ws + L.eC), hdr);
+  k_c_finish<<<1, 1, 0, s>>>(hdr);
+  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, (const int*)(ws + L.eC),
+                                      (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
+  count_launch(3);
   return cudaGetLastError();
 }
 
@@ -614,7 +744,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   const int N = d.N, Ap = d.Ap, Np = d.Np;
   CUtensorMap ah, al, bh, bl;
   const size_t h2 = sizeof(__half);
-  // (1) X = B C_act
+  // (1) X = B C_act  (integer + fraction operands; exact integer products)
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
@@ -629,16 +759,23 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.mode = 1; a.M = (int)rows; a.Nn = Ap;
     a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
     a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-    a.Nmu = N; a.Ap = Ap; a.Np = Np;
-    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
-    a.xthi = (__half*)(ws + L.Xthi); a.xtlo = (__half*)(ws + L.Xtlo);
-    a.scale_exp = &hdr->e1; a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<64>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
+    a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
+    a.glob_exp = &hdr->sX;
+    a.Nmu = N; a.Ap = Ap;
+    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo); a.x32 = (float*)(ws + L.X32);
+    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
-  // (2) b[P] = C_act^T X[P]
+  // (2) b[P] = C_act^T X[P]  (X^T re-split per (P, q), integer + fraction operands)
   prof_begin(DONOF_PHASE_MO_3INDEX, s);
   {
+    k_quant_xt<<<dim3(np, (Ap + 31) / 32), 256, 0, s>>>((const float*)(ws + L.X32), N, Ap, Np,
+                                                        (__half*)(ws + L.Xthi),
+                                                        (__half*)(ws + L.Xtlo), (int*)(ws + L.eXt));
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
     if (!make_map(&ah, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
         !make_map(&al, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
         !make_map(&bh, ws + L.Xthi, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
@@ -648,9 +785,12 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.mode = 2; a.M = Ap; a.Nn = Ap;
     a.m_tiles = (Ap + BM - 1) / BM; a.z_count = np; a.splits = 1;
     a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 1;
+    a.eA = (const int*)(ws + L.eC); a.eA_zstride = 0;
+    a.eB = (const int*)(ws + L.eXt); a.eB_zstride = Ap;
+    a.glob_exp = &hdr->zero_exp;
     a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = (long long)Ap * Ap;
-    a.scale_exp = &hdr->e2; a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<64>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
@@ -664,7 +804,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     return DONOF_ERR_CUDA;
   if (launch_split_Y(d, np, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
   prof_end(DONOF_PHASE_JK_Y, s);
-  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]
+  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]  (hi/lo split operands)
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
     if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
@@ -678,9 +818,9 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.splits = d.splits < np ? d.splits : np;
     a.kt_per_kb = (Ap + 31) / 32; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
     a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
-    a.scale_exp = &hdr->zero_exp;  // partials stay in scaled units
-    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<32>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    a.glob_exp = &hdr->zero_exp;  // partials stay in scaled units
+    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+    if (launch_tc<32, kSplit3>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
     if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
@@ -723,10 +863,11 @@ extern "C" int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo,
   a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
   a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
   a.out = D; a.out_ld = N; a.out_zstride = 0;
-  a.scale_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
+  a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
   if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
     return DONOF_ERR_CUDA;
-  if (launch_tc<64>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess) return DONOF_ERR_CUDA;
+  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
   return DONOF_OK;
 }
 
