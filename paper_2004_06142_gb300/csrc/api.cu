@@ -34,7 +34,7 @@ Dims make_dims(const donof_problem* p) {
     perP = (size_t)d.N * d.A * 8 + 2 * (size_t)d.A * d.A * 8 +
            (d.layout == DONOF_B_PACKED ? (size_t)d.N * d.N * 8 : 0);
   } else {
-    perP = (size_t)d.N * d.Ap * 8 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
+    perP = (size_t)d.N * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
            (size_t)d.Ap * 4;
   }
   long long pb = d.Q;
@@ -90,12 +90,13 @@ Layout make_layout(const Dims& d) {
     L.Bhi = take(Q * N * Np * 2);
     L.Blo = take(Q * N * Np * 2);
     L.eB = take(Q * N * 4);
+    L.L1max = take(Q * 8);
     L.Chi = take(Ap * Np * 2);
     L.Clo = take(Ap * Np * 2);
     L.eC = take(Ap * 4);
+    L.cnorm = take(Ap * 8);
     L.Xhi = take(pb * N * Ap * 2);
     L.Xlo = take(pb * N * Ap * 2);
-    L.X32 = take(pb * N * Ap * 4);
     L.Xthi = take(pb * Ap * Np * 2);
     L.Xtlo = take(pb * Ap * Np * 2);
     L.eXt = take(pb * Ap * 4);

@@ -49,7 +49,8 @@ struct Layout {
   // mixed path
   // Bhi/Blo, Chi/Clo, Xthi/Xtlo hold integer + fraction planes, Xhi/Xlo and Yhi/Ylo
   // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
-  size_t Bhi, Blo, eB, Chi, Clo, eC, Xhi, Xlo, X32, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo, Gpart;
+  size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo,
+      Gpart;
   size_t total;
 };
 
@@ -112,6 +113,9 @@ cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np
                                const Layout& L, cudaStream_t s);
 cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
                                const Layout& L, cudaStream_t s);
+// J, K accumulation and Y^P in one pass over b (fp32 b, mixed path).
+cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
+                           const Layout& L, cudaStream_t s);
 cudaError_t launch_energy(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
                           double* E_out, double* dEdg_out, cudaStream_t s);
 cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s);

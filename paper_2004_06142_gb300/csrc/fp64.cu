@@ -101,91 +101,89 @@ cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Occupations (Eqs. soo, woo) and their Jacobians with respect to gamma.
-// One thread per pair g.  Also validates pair_map and gamma.
+// One thread per active orbital; the Jacobians are zeroed by the caller and only their
+// nonzero entries are written.  Also validates pair_map and gamma.
 // ---------------------------------------------------------------------------
 namespace {
 __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
                               const int32_t* __restrict__ pm, DevHeader* hdr, double* n,
                               double* sqn, double* phi, double* dn, double* dsq, double* dphi) {
   const int A = d.A, ng = d.ng, npair = d.npair, ncwo = d.ncwo;
-  // every orbital index p >= npair must name a valid pair
-  for (int p = threadIdx.x + blockIdx.x * blockDim.x; p < A; p += blockDim.x * gridDim.x) {
-    const int g = pm[p];
-    if (g < 0 || g >= npair || (p < npair && g != p)) set_status(hdr, DONOF_ERR_PAIR_MAP);
-  }
   for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < ng; k += blockDim.x * gridDim.x)
     if (!isfinite(gamma[k])) set_status(hdr, DONOF_ERR_NONFINITE);
-
-  const int g = threadIdx.x + blockIdx.x * blockDim.x;
-  if (g >= npair) return;
+  const int p = threadIdx.x + blockIdx.x * blockDim.x;
+  if (p >= A) return;
+  const int g = pm[p];
+  if (g < 0 || g >= npair || (p < npair && g != p)) {
+    set_status(hdr, DONOF_ERR_PAIR_MAP);
+    return;
+  }
   const double rs2 = 0.70710678118654752440;  // 1/sqrt(2)
   const double tg = gamma[g];
   const double cg = cos(tg), sg = sin(tg);
-  // strong orbital g
-  {
+  const double sh = fabs(sg) * rs2;                 // sqrt(1 - n_g) = sqrt(h_g)
+  const double dsh = copysign(1.0, sg) * cg * rs2;
+  if (p < npair) {
+    // strong orbital g = p: n_g = (1 + cos^2 gamma_g) / 2
+    int cnt = 0;
+    for (int q = npair; q < A; ++q) cnt += (pm[q] == p);
+    if (cnt != ncwo) set_status(hdr, DONOF_ERR_PAIR_MAP);
     const double ng_ = 0.5 * (1.0 + cg * cg);
     const double r = sqrt(ng_);
     const double dng = -cg * sg;
-    const double sh = fabs(sg) * rs2;                 // sqrt(1 - n_g) = sqrt(h_g)
-    const double dsh = copysign(1.0, sg) * cg * rs2;
-    for (int k = 0; k < ng; ++k) {
-      dn[(size_t)g * ng + k] = 0.0; dsq[(size_t)g * ng + k] = 0.0; dphi[(size_t)g * ng + k] = 0.0;
-    }
-    n[g] = ng_; sqn[g] = r; phi[g] = r * sh;
-    dn[(size_t)g * ng + g] = dng;
-    dsq[(size_t)g * ng + g] = dng / (2.0 * r);
-    dphi[(size_t)g * ng + g] = dng / (2.0 * r) * sh + r * dsh;
+    n[p] = ng_; sqn[p] = r; phi[p] = r * sh;
+    dn[(size_t)p * ng + g] = dng;
+    dsq[(size_t)p * ng + g] = dng / (2.0 * r);
+    dphi[(size_t)p * ng + g] = dng / (2.0 * r) * sh + r * dsh;
+    return;
   }
-  // weak orbitals p_1..p_Ng of pair g, in increasing orbital index
-  const double sh = fabs(sg) * rs2;
-  const double dsh = copysign(1.0, sg) * cg * rs2;
+  // weak orbital p_i of pair g: i = its rank among the pair's weak orbitals
   int i = 0;
-  for (int p = npair; p < A; ++p) {
-    if (pm[p] != g) continue;
-    if (i >= ncwo) { set_status(hdr, DONOF_ERR_PAIR_MAP); break; }
-    const int wbase = npair + g * (ncwo - 1);
-    // sqrt(n_{p_i}) = sh * prod_{j<i} |cos gamma_j| * (|sin gamma_i| unless last)
-    double val = sh;
-    for (int j = 0; j < i; ++j) val *= fabs(cos(gamma[wbase + j]));
-    const bool has_sin = (i < ncwo - 1);
-    if (has_sin) val *= fabs(sin(gamma[wbase + i]));
-    double* dsq_row = dsq + (size_t)p * ng;
-    for (int k = 0; k < ng; ++k) dsq_row[k] = 0.0;
-    // derivative w.r.t. gamma_g
-    {
-      double rest = 1.0;
-      for (int j = 0; j < i; ++j) rest *= fabs(cos(gamma[wbase + j]));
-      if (has_sin) rest *= fabs(sin(gamma[wbase + i]));
-      dsq_row[g] = dsh * rest;
-    }
-    for (int j = 0; j <= i; ++j) {
-      if (j == i && !has_sin) break;
-      const double t = gamma[wbase + j];
-      const double df = (j < i) ? -copysign(1.0, cos(t)) * sin(t) : copysign(1.0, sin(t)) * cos(t);
-      double rest = sh;
-      for (int jj = 0; jj < i; ++jj)
-        if (jj != j) rest *= fabs(cos(gamma[wbase + jj]));
-      if (has_sin && j != i) rest *= fabs(sin(gamma[wbase + i]));
-      dsq_row[wbase + j] = df * rest;
-    }
-    const double nn = val * val;
-    const double om = sqrt(1.0 - nn);
-    n[p] = nn; sqn[p] = val; phi[p] = val * om;
-    for (int k = 0; k < ng; ++k) {
-      const double dnk = 2.0 * val * dsq_row[k];
-      dn[(size_t)p * ng + k] = dnk;
-      dphi[(size_t)p * ng + k] = dsq_row[k] * om - val * dnk / (2.0 * om);
-    }
-    ++i;
+  for (int q = npair; q < p; ++q) i += (pm[q] == g);
+  if (i >= ncwo) {
+    set_status(hdr, DONOF_ERR_PAIR_MAP);
+    return;
   }
-  if (i != ncwo) set_status(hdr, DONOF_ERR_PAIR_MAP);
+  const int wbase = npair + g * (ncwo - 1);
+  const bool has_sin = (i < ncwo - 1);
+  // sqrt(n_{p_i}) = sh * prod_{j<i} |cos gamma_j| * (|sin gamma_i| unless last)
+  double prodc = 1.0;
+  for (int j = 0; j < i; ++j) prodc *= fabs(cos(gamma[wbase + j]));
+  const double si = has_sin ? fabs(sin(gamma[wbase + i])) : 1.0;
+  const double val = sh * prodc * si;
+  const double nn = val * val;
+  const double om = sqrt(1.0 - nn);
+  n[p] = nn; sqn[p] = val; phi[p] = val * om;
+  auto put = [&](int k, double ds) {
+    const double dnk = 2.0 * val * ds;
+    dsq[(size_t)p * ng + k] = ds;
+    dn[(size_t)p * ng + k] = dnk;
+    dphi[(size_t)p * ng + k] = ds * om - val * dnk / (2.0 * om);
+  };
+  put(g, dsh * prodc * si);
+  for (int j = 0; j < i; ++j) {
+    const double t = gamma[wbase + j];
+    double rest = sh * si;
+    for (int jj = 0; jj < i; ++jj)
+      if (jj != j) rest *= fabs(cos(gamma[wbase + jj]));
+    put(wbase + j, -copysign(1.0, cos(t)) * sin(t) * rest);
+  }
+  if (has_sin) {
+    const double t = gamma[wbase + i];
+    put(wbase + i, copysign(1.0, sin(t)) * cos(t) * sh * prodc);
+  }
 }
 }  // namespace
 
 cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pm, char* ws,
                                const Layout& L, cudaStream_t s) {
+  const size_t jac = (size_t)d.A * d.ng * sizeof(double);
+  for (size_t off : {L.dn, L.dsq, L.dphi}) {
+    const cudaError_t e = cudaMemsetAsync(ws + off, 0, jac, s);
+    if (e != cudaSuccess) return e;
+  }
   const int threads = 128;
-  const int blocks = (d.npair + threads - 1) / threads;
+  const int blocks = (d.A + threads - 1) / threads;
   k_occupations<<<blocks, threads, 0, s>>>(
       d, gamma, pm, (DevHeader*)(ws + L.header), (double*)(ws + L.n), (double*)(ws + L.sqn),
       (double*)(ws + L.phi), (double*)(ws + L.dn), (double*)(ws + L.dsq), (double*)(ws + L.dphi));
@@ -410,6 +408,138 @@ cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, 
       d, b, Y, np, d.Ap, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef),
       (DevHeader*)(ws + L.header));
   count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mixed path: J, K accumulation and Y^P from fp32 b.
+//   k_jk_tiled: 4 (q, p) entries per thread, a chunk of P per CTA, double partial sums.
+//   k_y_smem:   one CTA per slice at a time; Acoef and Bcoef cached in shared memory as fp32.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) k_jk_tiled(Dims d, const float* __restrict__ b, int np,
+                                                  int ld, double* J, double* K) {
+  const int A = d.A;
+  const int ents = ld * ld;
+  const int chunk = (np + gridDim.y - 1) / gridDim.y;
+  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
+  int e[4], q[4], p[4];
+  bool act[4];
+  double sj[4], sk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    e[j] = blockIdx.x * 1024 + threadIdx.x + 256 * j;
+    q[j] = e[j] / ld;
+    p[j] = e[j] % ld;
+    act[j] = e[j] < ents && q[j] < A && p[j] < A;
+    sj[j] = 0.0;
+    sk[j] = 0.0;
+  }
+#pragma unroll 4
+  for (int P = P0; P < P1; ++P) {
+    const float* bp = b + (size_t)P * ents;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!act[j]) continue;
+      const double v = bp[e[j]];
+      const double dq = bp[q[j] * ld + q[j]], dp = bp[p[j] * ld + p[j]];
+      sj[j] = fma(dq, dp, sj[j]);
+      sk[j] = fma(v, v, sk[j]);
+    }
+  }
+  if (P0 >= P1) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!act[j]) continue;
+    atomicAdd(J + (size_t)q[j] * A + p[j], sj[j]);
+    atomicAdd(K + (size_t)q[j] * A + p[j], sk[j]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_y_smem(Dims d, const float* __restrict__ b, float* Y,
+                                                int np, int ld, const double* __restrict__ Ac,
+                                                const double* __restrict__ Bc, DevHeader* hdr) {
+  extern __shared__ float shf[];
+  const int A = d.A;
+  float* sA = shf;                 // A * A
+  float* sB = sA + A * A;          // A * A
+  float* dv = sB + A * A;          // ld
+  float* wv = dv + ld;             // ld
+  __shared__ float red[8];
+  for (int i = threadIdx.x; i < A * A; i += blockDim.x) {
+    sA[i] = (float)Ac[i];
+    sB[i] = (float)Bc[i];
+  }
+  __syncthreads();
+  float ymax = 0.f;
+  const int ents = ld * ld;
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    const float* bp = b + (size_t)P * ents;
+    float* yp = Y + (size_t)P * ents;
+    for (int r = threadIdx.x; r < A; r += blockDim.x) dv[r] = bp[r * ld + r];
+    __syncthreads();
+    for (int pp = threadIdx.x; pp < A; pp += blockDim.x) {
+      float w = 0.f;
+      for (int r = 0; r < A; ++r) w = fmaf(sA[pp * A + r], dv[r], w);
+      wv[pp] = w;
+    }
+    __syncthreads();
+    // four consecutive entries of one row per thread (ld is a multiple of 16)
+    const float4* b4 = (const float4*)bp;
+    float4* y4 = (float4*)yp;
+    const int n4 = ents / 4;
+#pragma unroll 4
+    for (int i4 = threadIdx.x; i4 < n4; i4 += blockDim.x) {
+      const int i = i4 * 4;
+      const int qq = i / ld, p0 = i % ld;
+      const float4 v = b4[i4];
+      float r[4] = {v.x, v.y, v.z, v.w};
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pp = p0 + j;
+        float t = 0.f;
+        if (qq < A && pp < A) {
+          t = sB[qq * A + pp] * r[j];
+          if (qq == pp) t += wv[pp];
+        }
+        o[j] = t;
+        ymax = fmaxf(ymax, fabsf(t));
+      }
+      y4[i4] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = ymax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int i = 0; i < (int)blockDim.x / 32; ++i) m = fmaxf(m, red[i]);
+    atomicMax(&hdr->maxY_bits, __float_as_uint(m));
+  }
+}
+}  // namespace
+
+cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
+                           const Layout& L, cudaStream_t s) {
+  const int ld = d.Ap;
+  const unsigned gx = (unsigned)((ld * ld + 1023) / 1024);
+  unsigned gy = (unsigned)((4 * 152 + gx - 1) / gx);
+  if (gy > (unsigned)np) gy = (unsigned)np;
+  k_jk_tiled<<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
+  const size_t shm = (2 * (size_t)d.A * d.A + 2 * (size_t)ld) * sizeof(float);
+  if (shm > 200 * 1024) {  // coefficient matrices too large for shared memory
+    count_launch(1);
+    return launch_build_Y_f32(d, b, Y, np, ws, L, s);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_y_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm);
+  if (e != cudaSuccess) return e;
+  const int grid = np < 152 ? np : 152;
+  k_y_smem<<<grid, 256, shm, s>>>(d, b, Y, np, ld, (const double*)(ws + L.Acoef),
+                                  (const double*)(ws + L.Bcoef), (DevHeader*)(ws + L.header));
+  count_launch(2);
   return cudaGetLastError();
 }
 

@@ -128,6 +128,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ kernel
 // Operand numerics.
 //   kSplit3: every operand x is s * (hi + lo), hi = fp16(x / s), lo = fp16(x / s - hi), with one
@@ -159,10 +180,11 @@ struct TcArgs {
   const int* eB; long long eB_zstride;
   const int* glob_exp;  // extra power of two applied to every output (mode 2), or the
                         // exponent of the hi/lo split written for the G contraction (mode 1)
-  // mode 1 outputs, X[row][c] with row = P * Nmu + mu
-  int Nmu, Ap;
-  __half *xhi, *xlo;
-  float* x32;
+  // mode 1 outputs, X[row][c] with row = P * Nmu + mu: hi/lo split X[P][mu][c] for the G
+  // contraction and integer + fraction X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X
+  int Nmu, Ap, Np;
+  __half *xhi, *xlo, *xth, *xtf;
+  const int* eXt;
   // mode 2 output
   float* out;
   long long out_ld, out_zstride;
@@ -334,9 +356,16 @@ __global__ void __launch_bounds__(256, 1)
           v[j] = a[j] * pow2f(e);
         }
         if (args.mode == 1) {
-          float* xo = args.x32 + (size_t)row * args.Ap + c0;
+          const int P = row / args.Nmu, mu = row % args.Nmu;
+          const size_t to = ((size_t)P * args.Ap + c0) * args.Np + mu;
+          const int* ex = args.eXt + (size_t)P * args.Ap + c0;
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) *(float4*)(xo + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          for (int j = 0; j < 16; ++j) {
+            const float y = v[j] * pow2f(-ex[j]);
+            const float h = rintf(y);
+            args.xth[to + (size_t)j * args.Np] = __float2half_rn(h);
+            args.xtf[to + (size_t)j * args.Np] = __float2half_rn(y - h);
+          }
           const float s = pow2f(glob);
           __align__(16) __half hi[16], lo[16];
 #pragma unroll
@@ -370,17 +399,23 @@ __global__ void __launch_bounds__(256, 1)
       };
 
       if (args.Nn <= kMaxRegCols) {
-        // drain the accumulators into registers, hand TMEM back, then write
+        // drain the accumulators into registers (32 columns per load, one wait per pair of
+        // loads), hand TMEM back, then write
         float keep[kMaxRegCols];
 #pragma unroll
-        for (int cc = 0; cc < kMaxRegCols / 16; ++cc) {
-          if (cc * 16 < args.Nn) {
-            float a[16];
-            load(cc * 16, a);
+        for (int cc = 0; cc < kMaxRegCols / 32; ++cc) {
+          if (cc * 32 < args.Nn) {
+            tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), keep + cc * 32);
+            if (NUM == kIntFrac) {
+              float tmp[32];
+              tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), tmp);
+              tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) keep[cc * 16 + j] = a[j];
+              for (int j = 0; j < 32; ++j) keep[cc * 32 + j] += tmp[j];
+            }
           }
         }
+        tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
 #pragma unroll
@@ -467,7 +502,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)a.Nn * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  const size_t budget = 200 * 1024;
+  const size_t budget = 232448 - 1024 - 512;  // the 227 KB opt-in limit, less alignment and barriers
   int stages = (int)(budget / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
@@ -515,7 +550,7 @@ __device__ inline double load_B_elem(const double* __restrict__ B, int layout, l
 // Per row (P, mu): norm -> exponent of its integer + fraction split; global max |B| and
 // max row norm (the latter bounds |X| for the hi/lo split of the G contraction).
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
-                          DevHeader* hdr, int* eB) {
+                          DevHeader* hdr, int* eB, unsigned long long* L1max_bits) {
   const long long rows = Q * N;
   const int lane = threadIdx.x % 32;
   const long long npk = (long long)N * (N + 1) / 2;
@@ -524,18 +559,23 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
        row += (long long)gridDim.x * blockDim.x / 32) {
     const long long P = row / N;
     const int mu = (int)(row % N);
-    double ss = 0.0, m = 0.0;
+    double ss = 0.0, m = 0.0, l1 = 0.0;
     for (int nu = lane; nu < N; nu += 32) {
       const double v = load_B_elem(B, layout, P, row, mu, nu, N, npk);
       ss = fma(v, v, ss);
       m = fmax(m, fabs(v));
+      l1 += fabs(v);
     }
     for (int o = 16; o > 0; o >>= 1) {
       ss += __shfl_xor_sync(0xffffffffu, ss, o);
       m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      l1 += __shfl_xor_sync(0xffffffffu, l1, o);
     }
     const double nr = sqrt(ss);
-    if (lane == 0) eB[row] = intfrac_exponent(nr);
+    if (lane == 0) {
+      eB[row] = intfrac_exponent(nr);
+      atomic_max_nonneg(L1max_bits + P, l1);
+    }
     mx = fmax(mx, m);
     mr = fmax(mr, nr);
   }
@@ -572,7 +612,7 @@ __global__ void k_split_B(const double* __restrict__ B, int layout, long long Q,
 // Column norms of C_act -> exponents of the integer + fraction split of C_act^T (one warp
 // per column); max column norm for the bound on |X|.
 __global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, int* eC,
-                          DevHeader* hdr) {
+                          double* cnorm, DevHeader* hdr) {
   const int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (q >= Ap) return;
@@ -587,6 +627,7 @@ __global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, in
     const double nr = sqrt(ss);
     if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
     eC[q] = intfrac_exponent(nr);
+    cnorm[q] = nr;
     atomicMax((unsigned long long*)&hdr->maxCcol_bits, (unsigned long long)__double_as_longlong(nr));
   }
 }
@@ -612,53 +653,14 @@ __global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, in
   }
 }
 
-// X^T for the b contraction: X32[P][mu][q] (fp32) -> integer + fraction planes
-// XtH/XtF[P][q][mu] with one exponent per (P, q) from the column norm over mu.
-// One CTA per (P, 32 columns); pass 1 reduces the norms, pass 2 transposes through
-// shared memory (the strip is re-read from L2).
-__global__ void __launch_bounds__(256) k_quant_xt(const float* __restrict__ X32, int N, int Ap,
-                                                  int Np, __half* XtH, __half* XtF, int* eXt) {
-  __shared__ float tile[32][33];
-  __shared__ double red[8][32];
-  __shared__ int se[32];
-  const int P = blockIdx.x, q0 = blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const float* Xp = X32 + (size_t)P * N * Ap;
-  const bool qok = q0 + tx < Ap;
-  double ss = 0.0;
-  if (qok)
-    for (int mu = ty; mu < N; mu += 8) {
-      const double v = Xp[(size_t)mu * Ap + q0 + tx];
-      ss = fma(v, v, ss);
-    }
-  red[ty][tx] = ss;
-  __syncthreads();
-  if (ty == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += red[i][tx];
-    const int e = intfrac_exponent(sqrt(t));
-    se[tx] = e;
-    if (qok) eXt[(size_t)P * Ap + q0 + tx] = e;
-  }
-  __syncthreads();
-  for (int mu0 = 0; mu0 < Np; mu0 += 32) {
-    for (int i = ty; i < 32; i += 8) {
-      const int mu = mu0 + i;
-      tile[i][tx] = (mu < N && qok) ? Xp[(size_t)mu * Ap + q0 + tx] : 0.f;
-    }
-    __syncthreads();
-    for (int j = ty; j < 32; j += 8) {
-      const int q = q0 + j, mu = mu0 + tx;
-      if (q < Ap && mu < Np) {
-        const float y = tile[tx][j] * pow2f(-se[j]);
-        const float h = rintf(y);
-        const size_t o = ((size_t)P * Ap + q) * Np + mu;
-        XtH[o] = __float2half_rn(h);
-        XtF[o] = __float2half_rn(y - h);
-      }
-    }
-    __syncthreads();
-  }
+// Exponents of the integer + fraction split of X^T rows (P, q): ||X[P][:][q]||_2 =
+// ||B^P C_q||_2 <= ||B^P||_inf ||C_q||_2 (B^P symmetric, so ||B^P||_2 <= ||B^P||_inf).
+__global__ void k_xt_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
+                               int np, int Ap, int* eXt) {
+  const long long tot = (long long)np * Ap;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x)
+    eXt[i] = intfrac_exponent(L1max[i / Ap] * cnorm[i % Ap]);
 }
 
 // Y (fp32) -> scaled fp16 hi/lo; exponent from max |Y| of the block.
@@ -702,7 +704,10 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->maxB_bits, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB));
+  e = cudaMemsetAsync(ws + L.L1max, 0, (size_t)d.Q * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB),
+                                          (unsigned long long*)(ws + L.L1max));
   k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, hdr,
                                           (const int*)(ws + L.eB), (__half*)(ws + L.Bhi),
                                           (__half*)(ws + L.Blo));
@@ -715,7 +720,8 @@ cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layou
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->maxCcol_bits, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, (int*)(ws + L.eC), hdr);
+  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, (int*)(ws + L.eC),
+                                           (double*)(ws + L.cnorm), hdr);
   k_c_finish<<<1, 1, 0, s>>>(hdr);
   k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, (const int*)(ws + L.eC),
                                       (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
@@ -746,6 +752,10 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   const size_t h2 = sizeof(__half);
   // (1) X = B C_act  (integer + fraction operands; exact integer products)
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
+  k_xt_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.L1max) + p0,
+                                           (const double*)(ws + L.cnorm), np, Ap,
+                                           (int*)(ws + L.eXt));
+  count_launch(1);
   {
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * N * Np;
@@ -762,20 +772,16 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->sX;
-    a.Nmu = N; a.Ap = Ap;
-    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo); a.x32 = (float*)(ws + L.X32);
+    a.Nmu = N; a.Ap = Ap; a.Np = Np;
+    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
+    a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
     if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
-  // (2) b[P] = C_act^T X[P]  (X^T re-split per (P, q), integer + fraction operands)
+  // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
   prof_begin(DONOF_PHASE_MO_3INDEX, s);
   {
-    k_quant_xt<<<dim3(np, (Ap + 31) / 32), 256, 0, s>>>((const float*)(ws + L.X32), N, Ap, Np,
-                                                        (__half*)(ws + L.Xthi),
-                                                        (__half*)(ws + L.Xtlo), (int*)(ws + L.eXt));
-    count_launch(1);
-    if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
     if (!make_map(&ah, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
         !make_map(&al, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
         !make_map(&bh, ws + L.Xthi, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
@@ -795,11 +801,9 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
   prof_begin(DONOF_PHASE_JK_Y, s);
-  if (launch_jk_accumulate_f32(d, (const float*)(ws + L.b32), np, Ap, ws, L, s) != cudaSuccess)
-    return DONOF_ERR_CUDA;
   if (cudaMemsetAsync(&hdr->maxY_bits, 0, sizeof(unsigned int), s) != cudaSuccess)
     return DONOF_ERR_CUDA;
-  if (launch_build_Y_f32(d, (const float*)(ws + L.b32), (float*)(ws + L.Y32), np, ws, L, s) !=
+  if (launch_jky_f32(d, (const float*)(ws + L.b32), (float*)(ws + L.Y32), np, ws, L, s) !=
       cudaSuccess)
     return DONOF_ERR_CUDA;
   if (launch_split_Y(d, np, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
