@@ -120,6 +120,28 @@ int donof_get_jk(const donof_problem* prob, const void* workspace, size_t worksp
  * last call on `workspace` (DONOF_OK or a DONOF_ERR_* code) and clears it. */
 int donof_read_status(const void* workspace, int32_t* status, void* stream);
 
+/* A build that allocates no device memory, for callers that cannot allocate at the time
+ * they need one (a host framework that owns the device memory pool, a loop where an
+ * allocation's synchronisation or failure is not acceptable).  The paper has no
+ * counterpart; this is a deployment convenience.
+ * Inputs h, B, C, gamma, pair_map and outputs E[1], lam (may be NULL), dE_dgamma (may be
+ * NULL) and dE_dC[nbf*nbf] (= dE/dC, may be NULL) are caller-owned device pointers as in
+ * donof_energy_lagrangian / donof_energy_backward; B is converted on every call (there is
+ * no separate prepare step).
+ * Scratch: a fixed 64 MiB array in device global memory, held by every GPU that loads the
+ * library until the process exits.  Problems whose donof_workspace_size exceeds it are
+ * rejected with DONOF_ERR_WORKSPACE before any device work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call on a device shares the
+ * array and leaves its contents behind: the call clears what must start at zero itself,
+ * and calls whose device work overlaps (other streams, other threads) race on it.
+ * Device-side status (pair_map / non-finite checks) is not reported by this entry point.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+int donof_energy_lagrangian_noalloc(const donof_problem* prob, const double* h, const double* B,
+                                    const double* C, const double* gamma,
+                                    const int32_t* pair_map, double* E, double* lam,
+                                    double* dE_dgamma, double* dE_dC, void* stream);
+
 /* Tracing.  While enabled, every call records a pair of CUDA events on its stream around
  * each phase of the build; donof_profile_read() waits for them and returns the summed
  * device time (ms) and the number of timed intervals of one phase.  Enabling clears the

@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
         L.donof_read_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
         L.donof_status_string.argtypes = [ctypes.c_int]
         L.donof_status_string.restype = ctypes.c_char_p
+        L.donof_energy_lagrangian_noalloc.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -67,7 +68,7 @@ def lib() -> ctypes.CDLL:
         L.donof_launch_count.restype = ctypes.c_int64
         for f in ("donof_workspace_size", "donof_prepare_B", "donof_energy_lagrangian",
                   "donof_energy_backward", "donof_get_jk", "donof_read_status",
-                  "donof_profile_enable", "donof_profile_read"):
+                  "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -122,6 +123,16 @@ def donof_energy_backward(prob, Ebar, ws, dE_dC=None, dE_dgamma=None, stream=Non
     _check(lib().donof_energy_backward(ctypes.byref(prob), _ptr(Ebar), _ptr(ws), ws.numel(),
                                        _ptr(dE_dC), _ptr(dE_dgamma), _stream(stream)),
            "donof_energy_backward")
+
+
+def donof_energy_lagrangian_noalloc(prob, h, B, C, gamma, pair_map, E, lam=None, dE_dgamma=None,
+                                    dE_dC=None, stream=None):
+    """One build (and optionally dE/dC) using the library's fixed device scratch: no device
+    memory is allocated.  Small problems only (see include/donof.h)."""
+    _check(lib().donof_energy_lagrangian_noalloc(ctypes.byref(prob), _ptr(h), _ptr(B), _ptr(C),
+                                                 _ptr(gamma), _ptr(pair_map), _ptr(E), _ptr(lam),
+                                                 _ptr(dE_dgamma), _ptr(dE_dC), _stream(stream)),
+           "donof_energy_lagrangian_noalloc")
 
 
 def donof_get_jk(prob, ws, J=None, K=None, stream=None):
