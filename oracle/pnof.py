@@ -162,6 +162,26 @@ def mo_jk(C_act: np.ndarray, Jq: np.ndarray, Kq: np.ndarray):
     return J, K
 
 
+def jk_entries(slices, C_act: np.ndarray, pairs):
+    """Selected J_pq, K_pq of Eq. JKpq computed slice by slice, for workloads too large to
+    hold B: J_pq = sum_P (C_p^T B^P C_p)(C_q^T B^P C_q) = C_p^T J^q C_p and
+    K_pq = sum_P (C_p^T B^P C_q)^2 = C_p^T K^q C_p (Eq. Gpmn with DF integrals).
+    `slices` yields dense symmetric B^P; `pairs` lists (p, q)."""
+    cols = sorted({i for pq in pairs for i in pq})
+    J = {pq: 0.0 for pq in pairs}
+    K = {pq: 0.0 for pq in pairs}
+    for BP in slices:
+        BC = BP @ C_act[:, cols]                      # B^P C_i for the sampled orbitals
+        loc = {c: k for k, c in enumerate(cols)}
+        for (p, q) in pairs:
+            dp = C_act[:, p] @ BC[:, loc[p]]
+            dq = C_act[:, q] @ BC[:, loc[q]]
+            bpq = C_act[:, p] @ BC[:, loc[q]]
+            J[(p, q)] += dp * dq
+            K[(p, q)] += bpq * bpq
+    return J, K
+
+
 # ----------------------------------------------------------------------------
 # energy (Sec. II)
 # ----------------------------------------------------------------------------

@@ -46,9 +46,11 @@ Dims make_dims(const donof_problem* p) {
   if (pb > 65535) pb = 65535;  // batch index of the double GEMMs lives in gridDim.z
   d.pb = (int)pb;
   d.nblk = (d.Q + d.pb - 1) / d.pb;
-  // split-K of the G contraction: at most 32 slices per split, enough units for 2 waves
+  // split-K of the G contraction: at most 8 slices per split (each split is one fp32
+  // tensor-core accumulation, whose truncation bias grows with its length), enough units
+  // for 2 waves
   const int mt = (d.N + 127) / 128;
-  int sp = (d.pb + 31) / 32;
+  int sp = (d.pb + 7) / 8;
   const int want = (2 * 152 + mt - 1) / mt;
   if (sp < want) sp = want;
   if (sp > d.pb) sp = d.pb;

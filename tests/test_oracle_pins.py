@@ -260,3 +260,13 @@ def test_invariances():
     out = run(prob, d, pnof.PNOF7, C=C2, pair_map=pm_new, gamma=gam_new)
     assert abs(out["E"] - ref["E"]) < 1e-12
     np.testing.assert_allclose(out["lam"], ref["lam"][np.ix_(perm, perm)], atol=1e-12)
+
+
+def test_jk_entries_streaming_matches_operator_route():
+    prob, d = tiny(nbf=9, naux=13, npair=2, ncwo=2, seed=15)
+    out = run(prob, d, pnof.PNOF7)
+    pairs = [(0, 0), (1, 4), (5, 2)]
+    J, K = pnof.jk_entries(iter(d["B"]), d["C"][:, : prob.nact], pairs)
+    for pq in pairs:
+        assert abs(J[pq] - out["J"][pq]) < 1e-13
+        assert abs(K[pq] - out["K"][pq]) < 1e-13
