@@ -35,7 +35,7 @@ Dims make_dims(const donof_problem* p) {
            (d.layout == DONOF_B_PACKED ? (size_t)d.N * d.N * 8 : 0);
   } else {
     perP = (size_t)d.N * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
-           (size_t)d.Ap * 4;
+           (size_t)d.Ap * 4 + (size_t)d.A * 8;
   }
   long long pb = d.Q;
   if (p->x_budget_bytes > 0) {
@@ -107,6 +107,7 @@ Layout make_layout(const Dims& d) {
     L.Yhi = take(pb * Ap * Ap * 2);
     L.Ylo = take(pb * Ap * Ap * 2);
     L.Gpart = take((size_t)d.splits * N * Ap * 4);
+    L.D = take(pb * A * 8);
   }
   L.total = off;
   return L;

@@ -50,7 +50,7 @@ struct Layout {
   // Bhi/Blo, Chi/Clo, Xthi/Xtlo hold integer + fraction planes, Xhi/Xlo and Yhi/Ylo
   // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
   size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo,
-      Gpart;
+      Gpart, D;
   size_t total;
 };
 

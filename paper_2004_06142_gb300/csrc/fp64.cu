@@ -411,61 +411,78 @@ cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, 
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Mixed path: J, K accumulation and Y^P from fp32 b.
-//   k_jk_tiled: 4 (q, p) entries per thread, a chunk of P per CTA, double partial sums.
-//   k_y_smem:   one CTA per slice at a time; Acoef and Bcoef cached in shared memory as fp32.
-// ---------------------------------------------------------------------------
+#define CK_RET(x)                    \
+  do {                               \
+    const cudaError_t e_ = (x);      \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
 namespace {
-__global__ void __launch_bounds__(256) k_jk_tiled(Dims d, const float* __restrict__ b, int np,
-                                                  int ld, double* J, double* K) {
-  const int A = d.A;
-  const int ents = ld * ld;
-  const int chunk = (np + gridDim.y - 1) / gridDim.y;
-  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
-  int e[4], q[4], p[4];
-  bool act[4];
-  double sj[4], sk[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    e[j] = blockIdx.x * 1024 + threadIdx.x + 256 * j;
-    q[j] = e[j] / ld;
-    p[j] = e[j] % ld;
-    act[j] = e[j] < ents && q[j] < A && p[j] < A;
-    sj[j] = 0.0;
-    sk[j] = 0.0;
-  }
-#pragma unroll 4
-  for (int P = P0; P < P1; ++P) {
-    const float* bp = b + (size_t)P * ents;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (!act[j]) continue;
-      const double v = bp[e[j]];
-      const double dq = bp[q[j] * ld + q[j]], dp = bp[p[j] * ld + p[j]];
-      sj[j] = fma(dq, dp, sj[j]);
-      sk[j] = fma(v, v, sk[j]);
-    }
-  }
-  if (P0 >= P1) return;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (!act[j]) continue;
-    atomicAdd(J + (size_t)q[j] * A + p[j], sj[j]);
-    atomicAdd(K + (size_t)q[j] * A + p[j], sk[j]);
+__global__ void k_diag(const float* __restrict__ b, int np, int ld, int A, double* D) {
+  const long long tot = (long long)np * A;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long P = i / A;
+    const int r = (int)(i % A);
+    D[i] = b[(size_t)P * ld * ld + (size_t)r * ld + r];
   }
 }
+}  // namespace
 
-__global__ void __launch_bounds__(256) k_y_smem(Dims d, const float* __restrict__ b, float* Y,
-                                                int np, int ld, const double* __restrict__ Ac,
-                                                const double* __restrict__ Bc, DevHeader* hdr) {
+static cudaError_t launch_diag(const Dims& d, const float* b, int np, int ld, double* D,
+                               cudaStream_t s) {
+  k_diag<<<152, 256, 0, s>>>(b, np, ld, d.A, D);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mixed path: J, K accumulation and Y^P from fp32 b.
+//   k_k_stream: K from the squares of b (streaming, no gathers);
+//   k_y_smem:   one CTA per slice at a time; Acoef and Bcoef cached in shared memory as fp32;
+//               also writes the diagonals D[P][p] = b^P_pp, from which J = D^T D.
+// ---------------------------------------------------------------------------
+namespace {
+// K_pq += sum_P b[P][q][p]^2: four consecutive entries of one row per thread, a chunk of
+// slices per CTA, double partial sums.
+__global__ void __launch_bounds__(256) k_k_stream(Dims d, const float* __restrict__ b, int np,
+                                                  int ld, double* K) {
+  const int A = d.A;
+  const int n4 = ld * ld / 4;
+  const int i4 = blockIdx.x * 256 + threadIdx.x;
+  const int chunk = (np + gridDim.y - 1) / gridDim.y;
+  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
+  if (i4 >= n4 || P0 >= P1) return;
+  const int q = (i4 * 4) / ld, p0 = (i4 * 4) % ld;
+  if (q >= A || p0 >= A) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const float4* b4 = (const float4*)b;
+#pragma unroll 4
+  for (int P = P0; P < P1; ++P) {
+    const float4 v = b4[(size_t)P * n4 + i4];
+    s0 = fma((double)v.x, (double)v.x, s0);
+    s1 = fma((double)v.y, (double)v.y, s1);
+    s2 = fma((double)v.z, (double)v.z, s2);
+    s3 = fma((double)v.w, (double)v.w, s3);
+  }
+  double* k = K + (size_t)q * A + p0;
+  atomicAdd(k, s0);
+  if (p0 + 1 < A) atomicAdd(k + 1, s1);
+  if (p0 + 2 < A) atomicAdd(k + 2, s2);
+  if (p0 + 3 < A) atomicAdd(k + 3, s3);
+}
+
+__global__ void __launch_bounds__(1024) k_y_smem(Dims d, const float* __restrict__ b, float* Y,
+                                                 int np, int ld, const double* __restrict__ Ac,
+                                                 const double* __restrict__ Bc, double* D,
+                                                 DevHeader* hdr) {
   extern __shared__ float shf[];
   const int A = d.A;
   float* sA = shf;                 // A * A
   float* sB = sA + A * A;          // A * A
   float* dv = sB + A * A;          // ld
   float* wv = dv + ld;             // ld
-  __shared__ float red[8];
+  __shared__ float red[32];
   for (int i = threadIdx.x; i < A * A; i += blockDim.x) {
     sA[i] = (float)Ac[i];
     sB[i] = (float)Bc[i];
@@ -476,7 +493,11 @@ __global__ void __launch_bounds__(256) k_y_smem(Dims d, const float* __restrict_
   for (int P = blockIdx.x; P < np; P += gridDim.x) {
     const float* bp = b + (size_t)P * ents;
     float* yp = Y + (size_t)P * ents;
-    for (int r = threadIdx.x; r < A; r += blockDim.x) dv[r] = bp[r * ld + r];
+    for (int r = threadIdx.x; r < A; r += blockDim.x) {
+      const float v = bp[r * ld + r];
+      dv[r] = v;
+      D[(size_t)P * A + r] = v;  // diagonal d^P for J = D^T D
+    }
     __syncthreads();
     for (int pp = threadIdx.x; pp < A; pp += blockDim.x) {
       float w = 0.f;
@@ -524,23 +545,40 @@ __global__ void __launch_bounds__(256) k_y_smem(Dims d, const float* __restrict_
 cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
                            const Layout& L, cudaStream_t s) {
   const int ld = d.Ap;
-  const unsigned gx = (unsigned)((ld * ld + 1023) / 1024);
-  unsigned gy = (unsigned)((4 * 152 + gx - 1) / gx);
+  // K
+  const unsigned gx = (unsigned)((ld * ld / 4 + 255) / 256);
+  unsigned gy = (unsigned)((6 * 152 + gx - 1) / gx);
   if (gy > (unsigned)np) gy = (unsigned)np;
-  k_jk_tiled<<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
+  k_k_stream<<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.K));
+  count_launch(1);
+  // Y and the diagonals D
+  double* D = (double*)(ws + L.D);
   const size_t shm = (2 * (size_t)d.A * d.A + 2 * (size_t)ld) * sizeof(float);
   if (shm > 200 * 1024) {  // coefficient matrices too large for shared memory
+    CK_RET(launch_build_Y_f32(d, b, Y, np, ws, L, s));
+    CK_RET(launch_diag(d, b, np, ld, D, s));
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_y_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shm);
+    if (e != cudaSuccess) return e;
+    const int grid = np < 152 ? np : 152;
+    k_y_smem<<<grid, 1024, shm, s>>>(d, b, Y, np, ld, (const double*)(ws + L.Acoef),
+                                     (const double*)(ws + L.Bcoef), D,
+                                     (DevHeader*)(ws + L.header));
     count_launch(1);
-    return launch_build_Y_f32(d, b, Y, np, ws, L, s);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_y_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)shm);
-  if (e != cudaSuccess) return e;
-  const int grid = np < 152 ? np : 152;
-  k_y_smem<<<grid, 256, shm, s>>>(d, b, Y, np, ld, (const double*)(ws + L.Acoef),
-                                  (const double*)(ws + L.Bcoef), (DevHeader*)(ws + L.header));
-  count_launch(2);
-  return cudaGetLastError();
+  // J += D^T D  (K = np slices, split across CTAs)
+  DgemmArgs a{};
+  a.M = d.A; a.N = d.A; a.K = 64; a.KB = (np + 63) / 64; a.Ktot = np; a.batch = 1;
+  const long long tiles = (long long)((d.A + 63) / 64) * ((d.A + 63) / 64);
+  long long ks = (3 * 152 + tiles - 1) / tiles;
+  if (ks > a.KB) ks = a.KB;
+  a.ksplit = (int)(ks < 1 ? 1 : ks);
+  a.A = D; a.sAm = 1; a.sAk = d.A; a.sAkb = 64LL * d.A;
+  a.B = D; a.sBk = d.A; a.sBn = 1; a.sBkb = 64LL * d.A;
+  a.C = (double*)(ws + L.J); a.sCm = d.A; a.sCn = 1;
+  a.alpha = 1.0; a.beta = 1.0;
+  return launch_dgemm(a, s);
 }
 
 // ---------------------------------------------------------------------------
