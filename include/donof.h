@@ -57,9 +57,12 @@ extern "C" {
 enum { DONOF_PNOF5 = 5, DONOF_PNOF7 = 7, DONOF_PNOF7S = 8 };
 enum { DONOF_B_DENSE = 0, DONOF_B_PACKED = 1 };
 /* DONOF_FP64: every contraction in IEEE double on the CUDA cores.
- * DONOF_MIXED: the three large contractions (X = B C, b = C^T X, G += X Y) on the
- * tensor cores with fp16 hi+lo split operands (three products, fp32 accumulation,
- * power-of-two scaling); J, K, E, dE/dgamma, lambda and every cross-tile sum in double. */
+ * DONOF_MIXED: the large contractions (X = B C, b = C^T X, G += X Y, lambda = C^T G) on the
+ * tensor cores.  Every operand row is stored as 2^e (h + f): h an fp16 integer with the
+ * row's L2 norm bounding ||h||_2 below 2^12, f the fp16 remainder.  The integer products
+ * h*h then accumulate exactly in fp32 (no partial sum reaches 2^24), and h*f + f*h + f*f
+ * go to a second accumulator.  h C_act, the energy, dE/dgamma, J, K and every cross-tile
+ * or cross-slice sum are in double. */
 enum { DONOF_FP64 = 0, DONOF_MIXED = 1 };
 
 enum {
@@ -93,7 +96,7 @@ typedef struct {
 int donof_workspace_size(const donof_problem* prob, size_t* bytes);
 
 /* Register B (device) with the workspace.  DONOF_MIXED: converts B once into the
- * scaled fp16 hi/lo copy that every later build streams (B is fixed across orbital
+ * integer + fraction fp16 copy that every later build streams (B is fixed across orbital
  * iterations, Sec. III.D).  DONOF_FP64: records B only.  Must be called again when B
  * changes; the build calls must then pass the same B pointer. */
 int donof_prepare_B(const donof_problem* prob, const double* B, void* workspace,

@@ -46,11 +46,9 @@ Dims make_dims(const donof_problem* p) {
   if (pb > 65535) pb = 65535;  // batch index of the double GEMMs lives in gridDim.z
   d.pb = (int)pb;
   d.nblk = (d.Q + d.pb - 1) / d.pb;
-  // split-K of the G contraction: at most 8 slices per split (each split is one fp32
-  // tensor-core accumulation, whose truncation bias grows with its length), enough units
-  // for 2 waves
+  // split-K of the G contraction: at most 32 slices per split, enough units for 2 waves
   const int mt = (d.N + 127) / 128;
-  int sp = (d.pb + 7) / 8;
+  int sp = (d.pb + 31) / 32;
   const int want = (2 * 152 + mt - 1) / mt;
   if (sp < want) sp = want;
   if (sp > d.pb) sp = d.pb;
@@ -107,7 +105,18 @@ Layout make_layout(const Dims& d) {
     L.Yhi = take(pb * Ap * Ap * 2);
     L.Ylo = take(pb * Ap * Ap * 2);
     L.Gpart = take((size_t)d.splits * N * Ap * 4);
-    L.D = take(pb * A * 8);
+    L.D = take(pb * A * 4);
+    L.rn2 = take(Q * N * 8);
+    L.spOf = take(pb * 4);
+    L.eX3 = take((size_t)d.splits * N * 4);
+    L.ssqY = take((size_t)d.splits * Ap * 4);
+    L.eY = take((size_t)d.splits * Ap * 4);
+    L.CfH = take(N * Np * 2);
+    L.CfF = take(N * Np * 2);
+    L.eCf = take(N * 4);
+    L.GtH = take(Ap * Np * 2);
+    L.GtF = take(Ap * Np * 2);
+    L.eG = take(Ap * 4);
   }
   L.total = off;
   return L;
@@ -207,7 +216,7 @@ DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long
   DgemmArgs a{};
   a.M = M; a.N = N; a.K = 64; a.KB = (K + 63) / 64; a.Ktot = K; a.batch = 1;
   const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
-  long long ks = (3 * 152 + tiles - 1) / tiles;
+  long long ks = (2 * 152 + tiles - 1) / tiles;
   if (ks > a.KB) ks = a.KB;
   if (ks < 1) ks = 1;
   a.ksplit = (int)ks;
@@ -288,7 +297,11 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(launch_hdiag_ginit(d, C, ws, L, s));
   CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
   CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
-  if (d.precision == DONOF_MIXED) CK(launch_split_C(d, C, ws, L, s));
+  if (d.precision == DONOF_MIXED) {
+    CK(launch_split_C(d, C, ws, L, s));
+    // bound on ||C_act||_2 for the exponents of X in the G contraction
+    CK(launch_gram_bound(d, C, ws, L, s));
+  }
   prof_end(DONOF_PHASE_PREP, s);
 
   for (int p0 = 0; p0 < d.Q; p0 += d.pb) {
@@ -356,7 +369,13 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(launch_energy(d, pair_map, ws, L, E, dE_dgamma, s));
   if (lam) {  // lambda_qp = C_q^T G_p (q < N, p < nact), zero for p >= nact
     CK(cudaMemsetAsync(lam, 0, (size_t)N * N * 8, s));
-    CK(launch_dgemm(split_k_args(N, A, N, C, 1, N, (const double*)(ws + L.G), A, 1, lam, N, 1), s));
+    if (d.precision == DONOF_MIXED) {
+      rc = run_lambda_tc(d, C, ws, L, lam, s);
+      if (rc != DONOF_OK) return rc;
+    } else {
+      CK(launch_dgemm(split_k_args(N, A, N, C, 1, N, (const double*)(ws + L.G), A, 1, lam, N, 1),
+                      s));
+    }
   }
   prof_end(DONOF_PHASE_ENERGY_LAMBDA, s);
   return DONOF_OK;

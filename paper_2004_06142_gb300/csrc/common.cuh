@@ -27,6 +27,7 @@ struct DevHeader {
   int32_t abort_flag;     // set when a bounded device wait gives up; cleared per build
   int32_t pad1;
   double E;              // energy of the last build
+  double sC2;            // bound on ||C_act||_2^2 (Gershgorin on C_act^T C_act)
 };
 
 constexpr size_t kAlign = 256;
@@ -50,7 +51,7 @@ struct Layout {
   // Bhi/Blo, Chi/Clo, Xthi/Xtlo hold integer + fraction planes, Xhi/Xlo and Yhi/Ylo
   // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
   size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo,
-      Gpart, D;
+      Gpart, D, rn2, spOf, eX3, ssqY, eY, CfH, CfF, eCf, GtH, GtF, eG;
   size_t total;
 };
 
@@ -129,7 +130,12 @@ cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layou
                            cudaStream_t s);
 cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
+cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
+                              cudaStream_t s);
 // The three tensor-core contractions of one block of np auxiliary slices starting at p0.
 int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaStream_t s);
+// lambda = C^T G on the tensor cores (mixed path).
+int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
+                  cudaStream_t s);
 
 }  // namespace donof

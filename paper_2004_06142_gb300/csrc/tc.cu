@@ -175,19 +175,27 @@ struct TcArgs {
   int nbuf;        // TMEM accumulator sets (1 or 2)
   int buf_stride;  // TMEM columns per accumulator set
   int tmem_cols;
-  // per-row / per-column exponents (kIntFrac): value = 2^(eA[row] + eB[col]) * acc
-  const int* eA; long long eA_zstride;
-  const int* eB; long long eB_zstride;
+  // per-row / per-column exponents (kIntFrac): value = 2^(eA[row] + eB[col]) * acc, with
+  // eA indexed by z * eA_zstride + split * eA_sstride + row (eB likewise by column)
+  const int* eA; long long eA_zstride, eA_sstride;
+  const int* eB; long long eB_zstride, eB_sstride;
   const int* glob_exp;  // extra power of two applied to every output (mode 2), or the
                         // exponent of the hi/lo split written for the G contraction (mode 1)
-  // mode 1 outputs, X[row][c] with row = P * Nmu + mu: hi/lo split X[P][mu][c] for the G
-  // contraction and integer + fraction X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X
+  // mode 1 outputs, X[row][c] with row = P * Nmu + mu: integer + fraction X[P][mu][c] for
+  // the G contraction (exponent eX3[spOf[P]][mu], common to the slices of one G split) and
+  // X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X
   int Nmu, Ap, Np;
   __half *xhi, *xlo, *xth, *xtf;
   const int* eXt;
+  const int* spOf;
+  const int* eX3;
   // mode 2 output
   float* out;
   long long out_ld, out_zstride;
+  // mode 3 output: double, columns c < ncols_valid only
+  double* out64;
+  long long out64_ld;
+  int ncols_valid;
   int* status;
   int* abort_flag;
 };
@@ -343,8 +351,21 @@ __global__ void __launch_bounds__(256, 1)
       const uint32_t t0 =
           tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
       const uint32_t t1 = t0 + (uint32_t)args.Nn;
-      const int erow = (NUM == kIntFrac && valid) ? args.eA[z * args.eA_zstride + row] : 0;
-      const int* ecol = (NUM == kIntFrac) ? args.eB + z * args.eB_zstride : nullptr;
+      const int erow =
+          (NUM == kIntFrac && valid) ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + row] : 0;
+      // mode 1: slice and AO index of this row, the exponent of its X row in the G
+      // contraction and the row of X^T exponents, looked up once per tile
+      int rP = 0, rmu = 0;
+      float sx3 = 1.f;
+      const int* exrow = nullptr;
+      if (args.mode == 1 && valid) {
+        rP = row / args.Nmu;
+        rmu = row % args.Nmu;
+        sx3 = pow2f(-args.eX3[(size_t)args.spOf[rP] * args.Nmu + rmu]);
+        exrow = args.eXt + (size_t)rP * args.Ap;
+      }
+      const int* ecol =
+          (NUM == kIntFrac) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
 
       // one 16-column chunk: raw accumulator values -> outputs
       auto emit = [&](int c0, const float (&a)[16]) {
@@ -352,13 +373,12 @@ __global__ void __launch_bounds__(256, 1)
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int e = (NUM == kIntFrac ? erow + ecol[c0 + j] : 0) + (args.mode == 2 ? glob : 0);
+          const int e = (NUM == kIntFrac ? erow + ecol[c0 + j] : 0) + (args.mode >= 2 ? glob : 0);
           v[j] = a[j] * pow2f(e);
         }
         if (args.mode == 1) {
-          const int P = row / args.Nmu, mu = row % args.Nmu;
-          const size_t to = ((size_t)P * args.Ap + c0) * args.Np + mu;
-          const int* ex = args.eXt + (size_t)P * args.Ap + c0;
+          const size_t to = ((size_t)rP * args.Ap + c0) * args.Np + rmu;
+          const int* ex = exrow + c0;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const float y = v[j] * pow2f(-ex[j]);
@@ -366,19 +386,24 @@ __global__ void __launch_bounds__(256, 1)
             args.xth[to + (size_t)j * args.Np] = __float2half_rn(h);
             args.xtf[to + (size_t)j * args.Np] = __float2half_rn(y - h);
           }
-          const float s = pow2f(glob);
           __align__(16) __half hi[16], lo[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float w = v[j] * s;
-            hi[j] = __float2half_rn(w);
-            lo[j] = __float2half_rn(w - __half2float(hi[j]));
+            const float w = v[j] * sx3;
+            const float h = rintf(w);
+            hi[j] = __float2half_rn(h);
+            lo[j] = __float2half_rn(w - h);
           }
           const size_t o = (size_t)row * args.Ap + c0;
           uint4* dh = (uint4*)(args.xhi + o);
           uint4* dl = (uint4*)(args.xlo + o);
           dh[0] = ((uint4*)hi)[0]; dh[1] = ((uint4*)hi)[1];
           dl[0] = ((uint4*)lo)[0]; dl[1] = ((uint4*)lo)[1];
+        } else if (args.mode == 3) {
+          double* o = args.out64 + (long long)row * args.out64_ld + c0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < args.ncols_valid) o[j] = (double)v[j];
         } else {
           float* o = args.out + (long long)(z * args.splits + sp) * args.out_zstride +
                      (long long)row * args.out_ld + c0;
@@ -550,7 +575,7 @@ __device__ inline double load_B_elem(const double* __restrict__ B, int layout, l
 // Per row (P, mu): norm -> exponent of its integer + fraction split; global max |B| and
 // max row norm (the latter bounds |X| for the hi/lo split of the G contraction).
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
-                          DevHeader* hdr, int* eB, unsigned long long* L1max_bits) {
+                          DevHeader* hdr, int* eB, unsigned long long* L1max_bits, double* rn2) {
   const long long rows = Q * N;
   const int lane = threadIdx.x % 32;
   const long long npk = (long long)N * (N + 1) / 2;
@@ -574,6 +599,7 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
     const double nr = sqrt(ss);
     if (lane == 0) {
       eB[row] = intfrac_exponent(nr);
+      rn2[row] = ss;
       atomic_max_nonneg(L1max_bits + P, l1);
     }
     mx = fmax(mx, m);
@@ -632,6 +658,39 @@ __global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, in
   }
 }
 
+// Integer + fraction split of the transpose of a double matrix S (N rows, leading dimension
+// ld): output row c < nrows_out holds column c of S (zero for c >= ncols), exponent from
+// the column's L2 norm.  One warp per column for the norms.
+__global__ void k_colnorm_exp(const double* __restrict__ S, long long ld, int N, int ncols,
+                              int nrows_out, int* e) {
+  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (c >= nrows_out) return;
+  double ss = 0.0;
+  if (c < ncols)
+    for (int mu = lane; mu < N; mu += 32) {
+      const double v = S[(size_t)mu * ld + c];
+      ss = fma(v, v, ss);
+    }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) e[c] = intfrac_exponent(sqrt(ss));
+}
+
+__global__ void k_split_rows(const double* __restrict__ S, long long ld, int N, int ncols,
+                             int nrows_out, int Np, const int* __restrict__ e, __half* H,
+                             __half* F) {
+  const long long tot = (long long)nrows_out * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Np), mu = (int)(i % Np);
+    const double v = (c < ncols && mu < N) ? S[(size_t)mu * ld + c] : 0.0;
+    const double y = ldexp(v, -e[c]);
+    const double h = rint(y);
+    H[i] = __double2half(h);
+    F[i] = __double2half(y - h);
+  }
+}
+
 // Exponent of the hi/lo split of X used by the G contraction: |X| <= maxBrow * max ||C_q||.
 __global__ void k_c_finish(DevHeader* hdr) {
   const double nc = __longlong_as_double((long long)hdr->maxCcol_bits);
@@ -661,6 +720,105 @@ __global__ void k_xt_exponents(const double* __restrict__ L1max, const double* _
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x)
     eXt[i] = intfrac_exponent(L1max[i / Ap] * cnorm[i % Ap]);
+}
+
+// s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
+// matrix, formed in fp32 (one CTA per row i) with a relative safety margin of 1e-4 far above
+// its rounding error.
+__global__ void __launch_bounds__(256) k_gram_rows(const double* __restrict__ C, int N, int A,
+                                                   DevHeader* hdr) {
+  // row i of the Gram matrix: warp w sums mu = w, w + 8, ...; lane l owns columns l + 32k
+  const int i = blockIdx.x;
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  constexpr int kCols = 8;  // A <= 256
+  __shared__ float part[8][256];
+  float g[kCols];
+#pragma unroll
+  for (int k = 0; k < kCols; ++k) g[k] = 0.f;
+  for (int mu = w; mu < N; mu += 8) {
+    const double* Cm = C + (size_t)mu * N;
+    const float ci = (float)Cm[i];
+#pragma unroll
+    for (int k = 0; k < kCols; ++k) {
+      const int j = lane + 32 * k;
+      if (j < A) g[k] = fmaf(ci, (float)Cm[j], g[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kCols; ++k) {
+    const int j = lane + 32 * k;
+    if (j < A) part[w][j] = g[k];
+  }
+  __syncthreads();
+  float rs = 0.f;
+  for (int j = threadIdx.x; j < A; j += blockDim.x) {
+    float t = 0.f;
+    for (int ww = 0; ww < 8; ++ww) t += part[ww][j];
+    rs += fabsf(t);
+  }
+  __shared__ float red[8];
+  for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+  if (lane == 0) red[w] = rs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int ww = 0; ww < 8; ++ww) t += red[ww];
+    atomic_max_nonneg((unsigned long long*)&hdr->sC2, (double)t * (1.0 + 1e-4));
+  }
+}
+
+// Slices P of a block belong to G split sp when nkb*sp/splits <= P < nkb*(sp+1)/splits (the
+// split of the G contraction).  spOf[P] = sp; eX3[sp][mu] is the exponent of the integer +
+// fraction split of X rows (P in sp, mu) over (P, q):
+//   sum_{P in sp} ||X[P][mu][:]||^2 <= ||C_act||_2^2 sum_{P in sp} ||B^P[mu][:]||^2.
+__global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* hdr, int np,
+                               int splits, int N, int* spOf, int* eX3) {
+  const double sC2 = hdr->sC2;
+  const long long tot = (long long)splits * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int sp = (int)(i / N), mu = (int)(i % N);
+    const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
+    double r2 = 0.0;
+    for (int P = P0; P < P1; ++P) {
+      r2 += rn2[(size_t)P * N + mu];
+      if (mu == 0) spOf[P] = sp;
+    }
+    eX3[i] = intfrac_exponent(sqrt(sC2 * r2) * (1.0 + 1e-12));
+  }
+}
+
+// eY[sp][r] from the accumulated squares of the Y rows of split sp.
+__global__ void k_y_exponents(const float* __restrict__ ssqY, int n, int* eY) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    eY[i] = intfrac_exponent(sqrt((double)ssqY[i]) * (1.0 + 1e-6));
+}
+
+// Y (fp32, [P][r][c], symmetric) -> integer + fraction planes with row exponent
+// eY[spOf[P]][r]; four consecutive entries of one row per thread.
+__global__ void k_quant_Y(const float* __restrict__ Y, int np, int Ap, const int* __restrict__ spOf,
+                          const int* __restrict__ eY, __half* H, __half* F, DevHeader* hdr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->e3 = 0;  // G partials are in true units
+  const int r4 = Ap / 4;                                  // float4 per row
+  const long long tot4 = (long long)np * Ap * r4;
+  const float4* Y4 = (const float4*)Y;
+  for (long long i4 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i4 < tot4;
+       i4 += (long long)gridDim.x * blockDim.x) {
+    const long long row = i4 / r4;  // P * Ap + r
+    const int P = (int)(row / Ap), r = (int)(row % Ap);
+    const float sc = pow2f(-eY[(size_t)spOf[P] * Ap + r]);
+    const float4 v = Y4[i4];
+    const float y[4] = {v.x * sc, v.y * sc, v.z * sc, v.w * sc};
+    __align__(8) __half h[4], fr[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float hv = rintf(y[j]);
+      h[j] = __float2half_rn(hv);
+      fr[j] = __float2half_rn(y[j] - hv);
+    }
+    *(uint2*)(H + i4 * 4) = *(uint2*)h;
+    *(uint2*)(F + i4 * 4) = *(uint2*)fr;
+  }
 }
 
 // Y (fp32) -> scaled fp16 hi/lo; exponent from max |Y| of the block.
@@ -707,7 +865,8 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   e = cudaMemsetAsync(ws + L.L1max, 0, (size_t)d.Q * sizeof(double), s);
   if (e != cudaSuccess) return e;
   k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB),
-                                          (unsigned long long*)(ws + L.L1max));
+                                          (unsigned long long*)(ws + L.L1max),
+                                          (double*)(ws + L.rn2));
   k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, hdr,
                                           (const int*)(ws + L.eB), (__half*)(ws + L.Bhi),
                                           (__half*)(ws + L.Blo));
@@ -737,11 +896,55 @@ cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cud
   return cudaGetLastError();
 }
 
+cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
+                              cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->sC2, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_gram_rows<<<d.A, 256, 0, s>>>(C, d.N, d.A, hdr);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
   k_reduce_G<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Gpart), d.splits, d.N, d.A, d.Ap,
                                            (const DevHeader*)(ws + L.header), (double*)(ws + L.G));
   count_launch(1);
   return cudaGetLastError();
+}
+
+// lambda[q][p] = sum_mu C[mu][q] G[mu][p] (q < N, p < nact) on the tensor cores with integer +
+// fraction operands (rows of C^T and G^T), written as double into lam (row stride N).
+int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
+                  cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
+  const double* G = (const double*)(ws + L.G);
+  k_colnorm_exp<<<(N + 7) / 8, 256, 0, s>>>(C, N, N, N, N, (int*)(ws + L.eCf));
+  k_split_rows<<<num_sms() * 4, 256, 0, s>>>(C, N, N, N, N, Np, (const int*)(ws + L.eCf),
+                                             (__half*)(ws + L.CfH), (__half*)(ws + L.CfF));
+  k_colnorm_exp<<<(Ap + 7) / 8, 256, 0, s>>>(G, A, N, A, Ap, (int*)(ws + L.eG));
+  k_split_rows<<<num_sms(), 256, 0, s>>>(G, A, N, A, Ap, Np, (const int*)(ws + L.eG),
+                                         (__half*)(ws + L.GtH), (__half*)(ws + L.GtF));
+  count_launch(4);
+  if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
+  CUtensorMap ah, al, bh, bl;
+  const size_t h2 = sizeof(__half);
+  if (!make_map(&ah, ws + L.CfH, N, N, 1, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
+      !make_map(&al, ws + L.CfF, N, N, 1, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
+      !make_map(&bh, ws + L.GtH, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+      !make_map(&bl, ws + L.GtF, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    return DONOF_ERR_CUDA;
+  TcArgs a{};
+  a.mode = 3; a.M = N; a.Nn = Ap;
+  a.m_tiles = (N + BM - 1) / BM; a.z_count = 1; a.splits = 1;
+  a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.eA = (const int*)(ws + L.eCf); a.eB = (const int*)(ws + L.eG);
+  a.glob_exp = &hdr->zero_exp;
+  a.out64 = lam; a.out64_ld = N; a.ncols_valid = A;
+  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+  if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  return DONOF_OK;
 }
 
 // The tensor-core part of one block of np auxiliary slices (slices p0 .. p0+np-1).
@@ -751,11 +954,15 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   CUtensorMap ah, al, bh, bl;
   const size_t h2 = sizeof(__half);
   // (1) X = B C_act  (integer + fraction operands; exact integer products)
-  prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
+  const int splits3 = d.splits < np ? d.splits : np;  // splits of the G contraction
   k_xt_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.L1max) + p0,
                                            (const double*)(ws + L.cnorm), np, Ap,
                                            (int*)(ws + L.eXt));
-  count_launch(1);
+  k_x3_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.rn2) + (size_t)p0 * N,
+                                           (const DevHeader*)hdr, np, splits3, N,
+                                           (int*)(ws + L.spOf), (int*)(ws + L.eX3));
+  count_launch(2);
+  prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * N * Np;
@@ -775,6 +982,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.Nmu = N; a.Ap = Ap; a.Np = Np;
     a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
+    a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
     if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
@@ -801,14 +1009,21 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
   prof_begin(DONOF_PHASE_JK_Y, s);
-  if (cudaMemsetAsync(&hdr->maxY_bits, 0, sizeof(unsigned int), s) != cudaSuccess)
+  if (cudaMemsetAsync(ws + L.ssqY, 0, (size_t)splits3 * Ap * sizeof(float), s) != cudaSuccess)
     return DONOF_ERR_CUDA;
   if (launch_jky_f32(d, (const float*)(ws + L.b32), (float*)(ws + L.Y32), np, ws, L, s) !=
       cudaSuccess)
     return DONOF_ERR_CUDA;
-  if (launch_split_Y(d, np, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  k_y_exponents<<<num_sms(), 256, 0, s>>>((const float*)(ws + L.ssqY), splits3 * Ap,
+                                          (int*)(ws + L.eY));
+  k_quant_Y<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Y32), np, Ap,
+                                          (const int*)(ws + L.spOf), (const int*)(ws + L.eY),
+                                          (__half*)(ws + L.Yhi), (__half*)(ws + L.Ylo), hdr);
+  count_launch(2);
+  if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
   prof_end(DONOF_PHASE_JK_Y, s);
-  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]  (hi/lo split operands)
+  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]  (integer + fraction operands, exponents
+  //     common to the slices of a split)
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
     if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
@@ -819,12 +1034,14 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     TcArgs a{};
     a.mode = 2; a.M = N; a.Nn = Ap;
     a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
-    a.splits = d.splits < np ? d.splits : np;
+    a.splits = splits3;
     a.kt_per_kb = (Ap + 31) / 32; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
+    a.eA = (const int*)(ws + L.eX3); a.eA_sstride = N;
+    a.eB = (const int*)(ws + L.eY); a.eB_sstride = Ap;
     a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
-    a.glob_exp = &hdr->zero_exp;  // partials stay in scaled units
+    a.glob_exp = &hdr->zero_exp;
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<32, kSplit3>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc<32, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
     if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
