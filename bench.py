@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--cpu-slices", type=int, default=480)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--naux", type=int, default=0,
                     help="override naux (profiling captures on a slice of the workload)")
@@ -343,6 +344,11 @@ def run_ours(args):
     ms_e2e = f0.elapsed_time(f1) / args.steps
     assert abs(oE.item() - E_mixed) < 1e-9
 
+    # ---------------- the batched workload: 64 uneven instances in one graph launch
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(dn, dev, args.steps, args.warmup)
+
     # ---------------- the plain FP64 GPU path on the same inputs
     fp64 = None
     if not args.no_fp64 and rank == 0:
@@ -426,6 +432,7 @@ def run_ours(args):
             "tflops_algorithmic": flops_build(N, Q, A) * ws / (ms_max * 1e-3) / 1e12,
             "phases_ms": {k: v["ms_per_launch"] for k, v in phases.items()},
             "fp64_path": fp64,
+            "batch_workload": batch,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -440,6 +447,53 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         tdist.destroy_process_group()
+
+
+def run_batch(dn, dev, steps, warmup, ninst=64):
+    """Dissociation-scan-shaped batch: instance i has seed i, nbf ~ U{40..240}, naux = 4 nbf,
+    5 pairs, Ncwo ~ U{1..4}; PNOF7, mixed precision, forward + adjoint, one CUDA-graph replay
+    per step."""
+    import numpy as np
+    import torch
+
+    import synth
+    probs = synth.batch_problems(ninst)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    cprobs, tens = [], []
+    flops = 0.0
+    for pr in probs:
+        d = synth.generate(pr)
+        cprobs.append(dn.make_problem(pr.nbf, pr.naux, pr.npair, pr.ncwo, dn.PNOF7, dn.B_DENSE,
+                                      dn.MIXED))
+        f64 = torch.float64
+        tens.append(dict(h=t(d["h"]), B=t(d["B"]), C=t(d["C"]), gamma=t(d["gamma"]),
+                         pair_map=t(d["pair_map"].astype(np.int32)),
+                         E=torch.empty(1, dtype=f64, device=dev),
+                         lam=torch.empty(pr.nbf, pr.nbf, dtype=f64, device=dev),
+                         dE_dgamma=torch.empty(pr.ngamma, dtype=f64, device=dev),
+                         dE_dC=torch.empty(pr.nbf, pr.nbf, dtype=f64, device=dev)))
+        flops += flops_build(pr.nbf, pr.naux, pr.nact)
+    b = dn.Batch(cprobs, tens, device=dev)
+    b.prepare()
+    flags = dn.BATCH_BACKWARD | dn.BATCH_GRAPH
+    for _ in range(max(1, warmup)):
+        b.run(flags)
+    torch.cuda.synchronize()
+    l0 = dn.donof_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.run(flags)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nb = [pr.nbf for pr in probs]
+    return {"workload": f"{ninst} instances, nbf {min(nb)}..{max(nb)} (seeds 0..{ninst - 1}), "
+                        "naux = 4 nbf, 5 pairs, Ncwo 1..4, PNOF7, mixed, forward + adjoint",
+            "builds_per_s": ninst * 1e3 / ms, "ms_per_batch": ms,
+            "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
+            "graph_launches_per_step": 1,
+            "kernels_per_step": (dn.donof_launch_count() - l0) // steps}
 
 
 def main():

@@ -123,6 +123,34 @@ int donof_get_jk(const donof_problem* prob, const void* workspace, size_t worksp
  * last call on `workspace` (DONOF_OK or a DONOF_ERR_* code) and clears it. */
 int donof_read_status(const void* workspace, int32_t* status, void* stream);
 
+/* Batched builds: ninst independent instances (e.g. one molecule at many geometries), each
+ * with its own problem description probs[i] and device pointers inst[i].  The workspace
+ * (donof_batched_workspace_size bytes) holds one slice per instance; prepare every B once
+ * with donof_prepare_B_batched.  Instances run concurrently on library-owned streams that
+ * fork from and join back to `stream`.
+ *   DONOF_BATCH_BACKWARD: also write inst[i].dE_dC = dE/dC (upstream gradient 1).
+ *   DONOF_BATCH_GRAPH: capture the whole batch into a CUDA graph on the first call and
+ *     replay it (one graph launch) on every later call with identical arguments (same
+ *     problems, pointers, workspace and flags); tracing is not recorded inside graphs. */
+typedef struct {
+  const double* h;
+  const double* B;
+  const double* C;
+  const double* gamma;
+  const int32_t* pair_map;
+  double* E;          /* [1] */
+  double* lam;        /* [nbf*nbf] or NULL */
+  double* dE_dgamma;  /* [npair*ncwo] or NULL */
+  double* dE_dC;      /* [nbf*nbf] or NULL (DONOF_BATCH_BACKWARD) */
+} donof_instance;
+enum { DONOF_BATCH_BACKWARD = 1, DONOF_BATCH_GRAPH = 2 };
+int donof_batched_workspace_size(int32_t ninst, const donof_problem* probs, size_t* bytes);
+int donof_prepare_B_batched(int32_t ninst, const donof_problem* probs, const donof_instance* inst,
+                            void* workspace, size_t workspace_bytes, void* stream);
+int donof_energy_lagrangian_batched(int32_t ninst, const donof_problem* probs,
+                                    const donof_instance* inst, void* workspace,
+                                    size_t workspace_bytes, int32_t flags, void* stream);
+
 /* A build that allocates no device memory, for callers that cannot allocate at the time
  * they need one (a host framework that owns the device memory pool, a loop where an
  * allocation's synchronisation or failure is not acceptable).  The paper has no

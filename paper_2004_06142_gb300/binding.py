@@ -33,6 +33,14 @@ class DonofError(RuntimeError):
         self.code = code
 
 
+BATCH_BACKWARD, BATCH_GRAPH = 1, 2
+
+
+class donof_instance(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("h", "B", "C", "gamma", "pair_map", "E", "lam",
+                                              "dE_dgamma", "dE_dC")]
+
+
 class donof_problem(ctypes.Structure):
     _fields_ = [("nbf", ctypes.c_int32), ("naux", ctypes.c_int32), ("npair", ctypes.c_int32),
                 ("ncwo", ctypes.c_int32), ("functional", ctypes.c_int32),
@@ -61,6 +69,10 @@ def lib() -> ctypes.CDLL:
         L.donof_status_string.argtypes = [ctypes.c_int]
         L.donof_status_string.restype = ctypes.c_char_p
         L.donof_energy_lagrangian_noalloc.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        PI = ctypes.POINTER(donof_instance)
+        L.donof_batched_workspace_size.argtypes = [ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_prepare_B_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, vp]
+        L.donof_energy_lagrangian_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, ctypes.c_int32, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -68,7 +80,9 @@ def lib() -> ctypes.CDLL:
         L.donof_launch_count.restype = ctypes.c_int64
         for f in ("donof_workspace_size", "donof_prepare_B", "donof_energy_lagrangian",
                   "donof_energy_backward", "donof_get_jk", "donof_read_status",
-                  "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc"):
+                  "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
+                  "donof_batched_workspace_size", "donof_prepare_B_batched",
+                  "donof_energy_lagrangian_batched"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -211,6 +225,44 @@ class Builder:
 
     def status(self) -> int:
         return donof_read_status(self.ws)
+
+
+def donof_batched_workspace_size(probs) -> int:
+    arr = (donof_problem * len(probs))(*probs)
+    n = ctypes.c_size_t(0)
+    _check(lib().donof_batched_workspace_size(len(probs), arr, ctypes.byref(n)),
+           "donof_batched_workspace_size")
+    return n.value
+
+
+class Batch:
+    """Many independent instances in one call (library-owned streams, optional CUDA graph).
+
+    ``instances`` is a list of dicts of device tensors: h, B, C, gamma, pair_map and the
+    outputs E, lam, dE_dgamma, dE_dC (outputs may be missing)."""
+
+    def __init__(self, probs, instances, device="cuda"):
+        self.n = len(probs)
+        self.probs = (donof_problem * self.n)(*probs)
+        self.tensors = instances  # keeps the tensors alive
+        rows = []
+        for x in instances:
+            rows.append(donof_instance(*[(x[k].data_ptr() if x.get(k) is not None else None)
+                                         for k in ("h", "B", "C", "gamma", "pair_map", "E", "lam",
+                                                   "dE_dgamma", "dE_dC")]))
+        self.inst = (donof_instance * self.n)(*rows)
+        self.ws = torch.empty(donof_batched_workspace_size(probs), dtype=torch.uint8,
+                              device=device)
+
+    def prepare(self, stream=None):
+        _check(lib().donof_prepare_B_batched(self.n, self.probs, self.inst, _ptr(self.ws),
+                                             self.ws.numel(), _stream(stream)),
+               "donof_prepare_B_batched")
+
+    def run(self, flags=BATCH_BACKWARD, stream=None):
+        _check(lib().donof_energy_lagrangian_batched(self.n, self.probs, self.inst, _ptr(self.ws),
+                                                     self.ws.numel(), flags, _stream(stream)),
+               "donof_energy_lagrangian_batched")
 
 
 class DonofEnergy(torch.autograd.Function):

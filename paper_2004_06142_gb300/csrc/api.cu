@@ -149,9 +149,14 @@ void prof_clear_locked() {
 
 void count_launch(int n) { g_launches += n; }
 
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
 void prof_begin(int phase, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES) return;
+  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES || capturing(s)) return;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess) return;
   if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
@@ -162,7 +167,7 @@ void prof_begin(int phase, cudaStream_t s) {
 
 void prof_end(int phase, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES) return;
+  if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES || capturing(s)) return;
   PhaseRec& r = g_prof[phase];
   if (!r.open || r.ev.empty()) return;
   cudaEventRecord(r.ev.back().second, s);
