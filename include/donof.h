@@ -123,6 +123,22 @@ int donof_get_jk(const donof_problem* prob, const void* workspace, size_t worksp
  * last call on `workspace` (DONOF_OK or a DONOF_ERR_* code) and clears it. */
 int donof_read_status(const void* workspace, int32_t* status, void* stream);
 
+/* Hand-off to the orbital update (Sec. III.B).  Builds the symmetric matrix of Eq. Fockian,
+ *   F_qp = theta(p - q)[lambda_qp - lambda_pq] + theta(q - p)[lambda_pq - lambda_qp] (q != p),
+ *   F_pp = Fdiag[p]   (the paper takes the diagonal from the previous diagonalisation),
+ * diagonalises it in double, F = V diag(eps) V^T with eps ascending, and writes the rotated
+ * orbitals C_new = C V after one double Newton-Schulz reorthonormalisation step
+ * C_new <- C_new (3 I - C_new^T C_new) / 2.  lam, Fdiag[nbf], C (device, as in
+ * donof_energy_lagrangian) in; C_new[nbf*nbf] (column j = new orbital j) and eps[nbf]
+ * (device) out.  Workspace: donof_orbital_update_workspace_size bytes (device, 256-byte
+ * aligned).  Note: with lambda as defined here (lambda = C^T G, G = dE/dC / 4) the first-order
+ * energy change of this update is 4 sum_{q<p} F_qp^2 / (F_pp - F_qq), so a diagonal that
+ * decreases with the orbital index lowers E (the paper's Eq. ene1 prints the opposite sign). */
+int donof_orbital_update_workspace_size(int32_t nbf, size_t* bytes);
+int donof_orbital_update(int32_t nbf, const double* lam, const double* Fdiag, const double* C,
+                         void* workspace, size_t workspace_bytes, double* C_new, double* eps,
+                         void* stream);
+
 /* Batched builds: ninst independent instances (e.g. one molecule at many geometries), each
  * with its own problem description probs[i] and device pointers inst[i].  The workspace
  * (donof_batched_workspace_size bytes) holds one slice per instance; prepare every B once
@@ -187,7 +203,8 @@ enum {
   DONOF_PHASE_ENERGY_LAMBDA = 5,   /* E, dE/dgamma, lambda = C^T G */
   DONOF_PHASE_BACKWARD = 6,        /* donof_energy_backward */
   DONOF_PHASE_PREPARE_B = 7,       /* donof_prepare_B */
-  DONOF_NUM_PHASES = 8
+  DONOF_PHASE_ORBITAL_UPDATE = 8,  /* donof_orbital_update */
+  DONOF_NUM_PHASES = 9
 };
 int donof_profile_enable(int32_t enable);
 int donof_profile_read(int32_t phase, double* total_ms, int32_t* intervals);

@@ -280,6 +280,31 @@ def occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional):
     return dE_dn @ occ["dn"] + dE_dsq @ occ["dsqrt_n"] + dE_dphi @ occ["dphi"]
 
 
+# ----------------------------------------------------------------------------
+# hand-off to the orbital update (Sec. III.B)
+# ----------------------------------------------------------------------------
+def fockian(lam: np.ndarray, Fdiag: np.ndarray) -> np.ndarray:
+    """The symmetric matrix of Eq. Fockian: off-diagonal
+    F_qp = theta(p - q)[lambda_qp - lambda_pq] + theta(q - p)[lambda_pq - lambda_qp],
+    diagonal given (the paper takes it from the previous diagonalisation)."""
+    N = lam.shape[0]
+    F = np.zeros((N, N))
+    for q in range(N):
+        for p in range(N):
+            if q < p:
+                F[q, p] = lam[q, p] - lam[p, q]
+            elif q > p:
+                F[q, p] = lam[p, q] - lam[q, p]
+    F[np.diag_indices(N)] = Fdiag
+    return F
+
+
+def orbital_update(lam: np.ndarray, Fdiag: np.ndarray, C: np.ndarray):
+    """Diagonalise F (eigenvalues ascending) and rotate the orbitals, C_new = C V."""
+    eps, V = np.linalg.eigh(fockian(lam, Fdiag))
+    return eps, C @ V
+
+
 def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False):
     """One Lagrangian build: E, lambda, dE/dgamma, dE/dC and the intermediates.
 

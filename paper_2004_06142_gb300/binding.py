@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.donof_batched_workspace_size.argtypes = [ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_prepare_B_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, vp]
         L.donof_energy_lagrangian_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, ctypes.c_int32, vp]
+        L.donof_orbital_update_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_orbital_update.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp, vp, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -82,7 +84,8 @@ def lib() -> ctypes.CDLL:
                   "donof_energy_backward", "donof_get_jk", "donof_read_status",
                   "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
-                  "donof_energy_lagrangian_batched"):
+                  "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
+                  "donof_orbital_update"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -149,6 +152,21 @@ def donof_energy_lagrangian_noalloc(prob, h, B, C, gamma, pair_map, E, lam=None,
            "donof_energy_lagrangian_noalloc")
 
 
+def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):
+    """F of Eq. Fockian from lambda and a given diagonal, its eigendecomposition, C_new = C V
+    reorthonormalised (all on the device).  Returns the workspace used."""
+    n = C.shape[0]
+    if ws is None:
+        nb = ctypes.c_size_t(0)
+        _check(lib().donof_orbital_update_workspace_size(n, ctypes.byref(nb)),
+               "donof_orbital_update_workspace_size")
+        ws = torch.empty(nb.value, dtype=torch.uint8, device=C.device)
+    _check(lib().donof_orbital_update(n, _ptr(lam), _ptr(Fdiag), _ptr(C), _ptr(ws), ws.numel(),
+                                      _ptr(C_new), _ptr(eps), _stream(stream)),
+           "donof_orbital_update")
+    return ws
+
+
 def donof_get_jk(prob, ws, J=None, K=None, stream=None):
     _check(lib().donof_get_jk(ctypes.byref(prob), _ptr(ws), ws.numel(), _ptr(J), _ptr(K),
                               _stream(stream)), "donof_get_jk")
@@ -161,7 +179,7 @@ def donof_read_status(ws, stream=None) -> int:
 
 
 PHASES = ["prep", "half_transform", "mo_3index", "jk_y", "g_build", "energy_lambda",
-          "backward", "prepare_B"]
+          "backward", "prepare_B", "orbital_update"]
 
 
 def donof_profile_enable(enable: bool):

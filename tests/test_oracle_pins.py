@@ -270,3 +270,32 @@ def test_jk_entries_streaming_matches_operator_route():
     for pq in pairs:
         assert abs(J[pq] - out["J"][pq]) < 1e-13
         assert abs(K[pq] - out["K"][pq]) < 1e-13
+
+
+def test_fockian_first_order_energy_change():
+    """Diagonalising F of Eq. Fockian with a widely spaced diagonal rotates the orbitals by
+    A_qp = F_qp / (F_pp - F_qq) to first order (Eq. fi1); since dE/dC = 4 G and
+    lambda = C^T G, the energy then changes by 4 sum_{q<p} F_qp^2 / (F_pp - F_qq).
+    (Eq. ene1 prints the opposite sign with a factor 2: under the paper's own definition of
+    lambda in Eq. lag it is a decreasing diagonal that lowers E.)"""
+    prob, d = tiny(nbf=10, naux=16, npair=2, ncwo=2, seed=3)
+    out = run(prob, d, pnof.PNOF7)
+    N = prob.nbf
+    F0 = pnof.fockian(out["lam"], np.zeros(N))
+    assert np.allclose(F0, F0.T, atol=0)
+    for scale in (-200.0, 200.0):
+        diag = scale * np.arange(N)
+        eps, Cn = pnof.orbital_update(out["lam"], diag, d["C"])
+        np.testing.assert_allclose(Cn.T @ Cn, np.eye(N), atol=1e-12)
+        np.testing.assert_allclose(np.sort(eps), np.sort(np.linalg.eigvalsh(pnof.fockian(out["lam"], diag))))
+        # eigenvector j is close to e_j: restore the orbital order and signs
+        V = d["C"].T @ Cn
+        idx = np.argmax(np.abs(V), axis=0)
+        assert sorted(idx) == list(range(N))
+        V2 = np.zeros_like(V)
+        for j in range(N):
+            V2[:, idx[j]] = V[:, j] * np.sign(V[idx[j], j])
+        E1 = run(prob, d, pnof.PNOF7, C=d["C"] @ V2)["E"]
+        pred = sum(4 * F0[q, p] ** 2 / (diag[p] - diag[q]) for p in range(N) for q in range(p))
+        assert abs((E1 - out["E"]) - pred) < 0.02 * abs(pred), (E1 - out["E"], pred)
+        assert np.sign(E1 - out["E"]) == np.sign(scale)
