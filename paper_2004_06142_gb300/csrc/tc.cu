@@ -251,11 +251,13 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
 
   const int units = args.z_count * args.m_tiles * args.splits;
+  // consecutive units share the split (and so the B tiles of one K range, which then come
+  // from L2 for all M tiles of that split)
   auto decode = [&](int u, int& z, int& mt, int& sp) {
     z = u / (args.m_tiles * args.splits);
     const int r = u % (args.m_tiles * args.splits);
-    mt = r / args.splits;
-    sp = r % args.splits;
+    sp = r / args.m_tiles;
+    mt = r % args.m_tiles;
   };
 
   if (warp == 0 && lane == 0) {
@@ -990,19 +992,22 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
   prof_begin(DONOF_PHASE_MO_3INDEX, s);
   {
-    if (!make_map(&ah, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
-        !make_map(&al, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, BM) ||
-        !make_map(&bh, ws + L.Xthi, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
-        !make_map(&bl, ws + L.Xtlo, N, Ap, np, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    // one GEMM over all slices: rows (P, q) of X^T flattened into M, C_act^T rows as N;
+    // b[(P, q)][p] = b^P[q][p] is b^P (symmetric) in the [P][Ap][Ap] layout
+    const uint64_t rows = (uint64_t)np * Ap;
+    if (!make_map(&ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
+        !make_map(&al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
+        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
       return DONOF_ERR_CUDA;
     TcArgs a{};
-    a.mode = 2; a.M = Ap; a.Nn = Ap;
-    a.m_tiles = (Ap + BM - 1) / BM; a.z_count = np; a.splits = 1;
-    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 1;
-    a.eA = (const int*)(ws + L.eC); a.eA_zstride = 0;
-    a.eB = (const int*)(ws + L.eXt); a.eB_zstride = Ap;
+    a.mode = 2; a.M = (int)rows; a.Nn = Ap;
+    a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
+    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.eA = (const int*)(ws + L.eXt); a.eA_zstride = 0;
+    a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->zero_exp;
-    a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = (long long)Ap * Ap;
+    a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
     if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
