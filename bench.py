@@ -266,6 +266,7 @@ def run_ours(args):
 
     mixed = dn.Builder(N, Q, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.MIXED, device=dev)
     mixed.prepare(x["B"])
+    mixed.autotune(x["h"], x["C"], x["gamma"], x["pair_map"])
     Ebar = torch.ones(1, dtype=torch.float64, device=dev)
 
     def step():

@@ -189,6 +189,16 @@ int donof_energy_lagrangian_noalloc(const donof_problem* prob, const double* h, 
                                     const int32_t* pair_map, double* E, double* lam,
                                     double* dE_dgamma, double* dE_dC, void* stream);
 
+/* Tile autotuner (DONOF_MIXED): times each tensor-core contraction of a build with K tiles
+ * of 64 and of 32 elements (a few builds on the given inputs, B already prepared) and keeps
+ * the faster per contraction for this shape.  Later builds of the same shape use the choice.
+ * If the environment variable DONOF_TUNE_CACHE names a file, choices are loaded from it on
+ * first use and written back after tuning.  Uses (and clears) the tracing record; returns
+ * DONOF_OK without work for DONOF_FP64. */
+int donof_autotune(const donof_problem* prob, const double* h, const double* B, const double* C,
+                   const double* gamma, const int32_t* pair_map, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
 /* Tracing.  While enabled, every call records a pair of CUDA events on its stream around
  * each phase of the build; donof_profile_read() waits for them and returns the summed
  * device time (ms) and the number of timed intervals of one phase.  Enabling clears the

@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.donof_energy_lagrangian_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, ctypes.c_int32, vp]
         L.donof_orbital_update_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_orbital_update.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp, vp, vp]
+        L.donof_autotune.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -85,7 +86,7 @@ def lib() -> ctypes.CDLL:
                   "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
-                  "donof_orbital_update"):
+                  "donof_orbital_update", "donof_autotune"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -219,6 +220,12 @@ class Builder:
     def prepare(self, B: torch.Tensor):
         self.B = B
         donof_prepare_B(self.prob, B, self.ws)
+
+    def autotune(self, h, C, gamma, pair_map):
+        """Pick the tensor-core tile widths for this shape by timing builds (mixed only)."""
+        _check(lib().donof_autotune(ctypes.byref(self.prob), _ptr(h), _ptr(self.B), _ptr(C),
+                                    _ptr(gamma), _ptr(pair_map), _ptr(self.ws), self.ws.numel(),
+                                    _stream(None)), "donof_autotune")
 
     def forward(self, h, C, gamma, pair_map, want_lam=True):
         dev, f64 = self.device, torch.float64

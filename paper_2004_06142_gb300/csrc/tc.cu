@@ -17,6 +17,11 @@
 // next.  Persistent grid: one CTA per SM, tiles handed out round-robin.
 #include <cuda.h>
 #include <stdio.h>
+#include <stdlib.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -475,6 +480,53 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+// ------------------------------------------------------------------ host: tile tuning
+// K-tile width (BK, 32 or 64 elements) per contraction kind and shape, chosen by
+// donof_autotune from timed builds; optional persistence in the file named by the
+// DONOF_TUNE_CACHE environment variable (lines "kind N Ap np bk").
+struct TuneKey {
+  int kind, N, Ap, np;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, N, Ap, np) < std::tie(o.kind, o.N, o.Ap, o.np);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("DONOF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  int bk;
+  while (fscanf(f, "%d %d %d %d %d", &k.kind, &k.N, &k.Ap, &k.np, &bk) == 5)
+    if (bk == 32 || bk == 64) g_tune[k] = bk;
+  fclose(f);
+}
+
+void tune_save_locked() {
+  const char* path = getenv("DONOF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune)
+    fprintf(f, "%d %d %d %d %d\n", kv.first.kind, kv.first.N, kv.first.Ap, kv.first.np, kv.second);
+  fclose(f);
+}
+
+// kinds: 1 = half transform, 2 = b, 3 = G
+int tuned_bk(int kind, int N, int Ap, int np) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(TuneKey{kind, N, Ap, np});
+  if (it != g_tune.end()) return it->second;
+  return kind == 3 ? 32 : 64;
+}
+
 // ------------------------------------------------------------------ host: tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -551,6 +603,13 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   k_tc_gemm<BK, NUM><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
   count_launch(1);
   return cudaGetLastError();
+}
+
+template <int NUM>
+cudaError_t launch_tc_bk(int bk, const CUtensorMap& ah, const CUtensorMap& al,
+                         const CUtensorMap& bh, const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
+  return bk == 32 ? launch_tc<32, NUM>(ah, al, bh, bl, a, s)
+                  : launch_tc<64, NUM>(ah, al, bh, bl, a, s);
 }
 
 // ------------------------------------------------------------------ split / scale kernels
@@ -969,15 +1028,16 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * N * Np;
     const uint64_t rows = (uint64_t)np * N;
-    if (!make_map(&ah, Bh, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
-        !make_map(&al, Bl, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
-        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
-        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    const int bk = tuned_bk(1, N, Ap, np);
+    if (!make_map(&ah, Bh, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+        !make_map(&al, Bl, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
+        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
       return DONOF_ERR_CUDA;
     TcArgs a{};
     a.mode = 1; a.M = (int)rows; a.Nn = Ap;
     a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
-    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.kt_per_kb = (N + bk - 1) / bk; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->sX;
@@ -986,7 +1046,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
   // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
@@ -995,21 +1055,22 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     // one GEMM over all slices: rows (P, q) of X^T flattened into M, C_act^T rows as N;
     // b[(P, q)][p] = b^P[q][p] is b^P (symmetric) in the [P][Ap][Ap] layout
     const uint64_t rows = (uint64_t)np * Ap;
-    if (!make_map(&ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
-        !make_map(&al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, 64, BM) ||
-        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
-        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    const int bk = tuned_bk(2, N, Ap, np);
+    if (!make_map(&ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+        !make_map(&al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
+        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
       return DONOF_ERR_CUDA;
     TcArgs a{};
     a.mode = 2; a.M = (int)rows; a.Nn = Ap;
     a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
-    a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.kt_per_kb = (N + bk - 1) / bk; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
     a.eA = (const int*)(ws + L.eXt); a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->zero_exp;
     a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
@@ -1031,22 +1092,23 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   //     common to the slices of a split)
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
-    if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
-        !make_map(&al, ws + L.Xlo, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, 32, BM) ||
-        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, 32, Ap) ||
-        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, 32, Ap))
+    const int bk = tuned_bk(3, N, Ap, np);
+    if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, bk, BM) ||
+        !make_map(&al, ws + L.Xlo, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, bk, BM) ||
+        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap) ||
+        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap))
       return DONOF_ERR_CUDA;
     TcArgs a{};
     a.mode = 2; a.M = N; a.Nn = Ap;
     a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
     a.splits = splits3;
-    a.kt_per_kb = (Ap + 31) / 32; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
+    a.kt_per_kb = (Ap + bk - 1) / bk; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
     a.eA = (const int*)(ws + L.eX3); a.eA_sstride = N;
     a.eB = (const int*)(ws + L.eY); a.eB_sstride = Ap;
     a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
     a.glob_exp = &hdr->zero_exp;
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc<32, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
     if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
@@ -1056,6 +1118,62 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
 }
 
 }  // namespace donof
+
+// ---------------------------------------------------------------------------
+// Autotuner: time each tensor-core contraction of a build with BK = 64 and BK = 32 (CUDA
+// events through the tracing phases) and keep the faster per contraction and shape.
+namespace donof {
+int autotune_build(const donof_problem* prob, const double* h, const double* B, const double* C,
+                   const double* gamma, const int32_t* pair_map, void* ws, size_t bytes,
+                   cudaStream_t s) {
+  const Dims d = make_dims(prob);
+  const int np = d.pb < d.Q ? d.pb : d.Q;
+  const int phases[3] = {DONOF_PHASE_HALF_TRANSFORM, DONOF_PHASE_MO_3INDEX, DONOF_PHASE_G_BUILD};
+  const int cand[2] = {64, 32};
+  double best_ms[3] = {1e300, 1e300, 1e300};
+  int best_bk[3] = {64, 64, 32};
+  double* E = nullptr;
+  if (cudaMallocAsync((void**)&E, sizeof(double), s) != cudaSuccess) return DONOF_ERR_CUDA;
+  int rc = DONOF_OK;
+  for (int c = 0; c < 2 && rc == DONOF_OK; ++c) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_locked();
+      for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = cand[c];
+    }
+    rc = donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, bytes, E, nullptr, nullptr,
+                                 s);  // warm-up
+    if (rc != DONOF_OK) break;
+    donof_profile_enable(1);
+    for (int r = 0; r < 2 && rc == DONOF_OK; ++r)
+      rc = donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, bytes, E, nullptr, nullptr,
+                                   s);
+    for (int k = 0; k < 3 && rc == DONOF_OK; ++k) {
+      double ms = 0.0;
+      int n = 0;
+      if (donof_profile_read(phases[k], &ms, &n) != DONOF_OK || n == 0) continue;
+      if (ms / n < best_ms[k]) {
+        best_ms[k] = ms / n;
+        best_bk[k] = cand[c];
+      }
+    }
+    donof_profile_enable(0);
+  }
+  cudaFreeAsync(E, s);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = best_bk[k];
+  tune_save_locked();
+  return rc;
+}
+}  // namespace donof
+
+extern "C" int donof_autotune(const donof_problem* prob, const double* h, const double* B,
+                              const double* C, const double* gamma, const int32_t* pair_map,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  if (!prob || prob->precision != DONOF_MIXED) return DONOF_OK;  // nothing to tune
+  return donof::autotune_build(prob, h, B, C, gamma, pair_map, workspace, workspace_bytes,
+                               (cudaStream_t)stream);
+}
 
 // ---------------------------------------------------------------------------
 // Test hook (include/donof_testing.h): one plain split-product GEMM.

@@ -88,3 +88,23 @@ def test_packed_and_blocked(precision):
     for packed in (False, True):
         out = gpu_build(prob, d, precision, pnof.PNOF7, packed=packed, budget=budget)
         compare(out, ref, *tol)
+
+
+def test_autotuned_tiles_keep_parity():
+    """After the autotuner has picked tile widths, the mixed path still matches the oracle."""
+    import torch
+    import paper_2004_06142_gb300 as dn
+    from helpers import to_dev
+    prob = synth.Problem(130, 257, 6, 4, seed=6)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, pnof.PNOF7)
+    b = dn.Builder(prob.nbf, prob.naux, prob.npair, prob.ncwo, dn.PNOF7, dn.B_DENSE, dn.MIXED)
+    b.prepare(to_dev(d["B"]))
+    args = (to_dev(d["h"]), to_dev(d["C"]), to_dev(d["gamma"]), to_dev(d["pair_map"].astype(np.int32)))
+    b.autotune(*args)
+    E, lam, dg = b.forward(*args)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    assert abs(E.item() - ref["E"]) <= MIX_E
+    assert np.abs(lam.cpu().numpy() - ref["lam"]).max() <= MIX_G
+    assert np.abs(dg.cpu().numpy() - ref["dE_dgamma"]).max() <= MIX_G
