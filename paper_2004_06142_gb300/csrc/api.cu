@@ -80,6 +80,7 @@ Layout make_layout(const Dims& d) {
   L.K = take(A * A * 8);
   L.G = take(N * A * 8);
   L.dEdg = take(ng * 8);
+  L.Epart = take(4 * A * 8);
   if (d.precision == DONOF_FP64) {
     L.X64 = take(pb * N * A * 8);
     L.b64 = take(pb * A * A * 8);
@@ -87,8 +88,9 @@ Layout make_layout(const Dims& d) {
     L.Bun = d.layout == DONOF_B_PACKED ? take(pb * N * N * 8) : 0;
   } else {
     const size_t Q = d.Q;
-    L.Bhi = take(Q * N * Np * 2);
-    L.Blo = take(Q * N * Np * 2);
+    // pre-tiled split B: [ceil(N / 64)][Q * Np rows][64] per plane
+    L.Bhi = take((N + 63) / 64 * Q * Np * 64 * 2);
+    L.Blo = take((N + 63) / 64 * Q * Np * 64 * 2);
     L.eB = take(Q * N * 4);
     L.L1max = take(Q * 8);
     L.Chi = take(Ap * Np * 2);

@@ -44,7 +44,7 @@ struct Dims {
 struct Layout {
   size_t header;
   // shared by both precisions
-  size_t n, sqn, phi, dn, dsq, dphi, Acoef, Bcoef, Hd, hC, J, K, G, dEdg;
+  size_t n, sqn, phi, dn, dsq, dphi, Acoef, Bcoef, Hd, hC, J, K, G, dEdg, Epart;
   // FP64 path
   size_t X64, b64, Y64, Bun, W64;
   // mixed path

@@ -652,66 +652,75 @@ cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char
 }
 
 // ---------------------------------------------------------------------------
-// Energy and occupation gradient (one CTA, double throughout).
+// Energy and occupation gradient (double throughout).
 //   dE/dn_p     = 2 H_pp + 2 sum_{q not in g(p)} n_q (2 J_pq - K_pq)
 //                 [PNOF7s: - 8 (1 - 2 n_p) sum_{q not in g(p)} Phi_q^2 K_pq]
 //   dE/dsqrt_np = 2 sum_{q in g(p)} s_pq sqrt(n_q) K_pq   (s_pq the sign of Pi_pq)
 //   dE/dPhi_p   = -2 sum_{q not in g(p)} Phi_q K_pq       [PNOF7]
 //   dE/dgamma_k = sum_p (dE/dn_p dn_p/dgamma_k + dE/dsqrt_np dsqrt_np/dgamma_k
 //                        + dE/dPhi_p dPhi_p/dgamma_k)
+// k_energy_rows: one warp per orbital p (its share of E and the three partials);
+// k_energy_final: E as an ordered sum of the shares, then dE/dgamma.
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void __launch_bounds__(256) k_energy(Dims d, const int32_t* __restrict__ pm,
-                                                const double* __restrict__ n,
-                                                const double* __restrict__ sqn,
-                                                const double* __restrict__ phi,
-                                                const double* __restrict__ dn,
-                                                const double* __restrict__ dsq,
-                                                const double* __restrict__ dphi,
-                                                const double* __restrict__ Ac,
-                                                const double* __restrict__ Bc,
-                                                const double* __restrict__ Hd,
-                                                const double* __restrict__ J,
-                                                const double* __restrict__ K, DevHeader* hdr,
-                                                double* dEdg_ws, double* E_out, double* dEdg_out) {
-  extern __shared__ double sh[];  // 3 * A
-  double* gn = sh;
-  double* gs = sh + d.A;
-  double* gp = sh + 2 * d.A;
-  __shared__ double red[32];
+__global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+                              const double* __restrict__ sqn, const double* __restrict__ phi,
+                              const double* __restrict__ Ac, const double* __restrict__ Bc,
+                              const double* __restrict__ Hd, const double* __restrict__ J,
+                              const double* __restrict__ K, double* part) {
   const int A = d.A;
-  double e = 0.0;
-  for (int p = threadIdx.x; p < A; p += blockDim.x) {
-    e += 2.0 * n[p] * Hd[p];
-    double a_n = 2.0 * Hd[p], a_s = 0.0, a_p = 0.0, a_7s = 0.0;
-    const int g = pm[p];
-    for (int q = 0; q < A; ++q) {
-      const double kpq = K[(size_t)p * A + q];
-      e += Ac[(size_t)p * A + q] * J[(size_t)p * A + q] + Bc[(size_t)p * A + q] * kpq;
-      if (pm[q] == g) {
-        const bool sgnp = (p == q || (p >= d.npair && q >= d.npair));
-        a_s += (sgnp ? 2.0 : -2.0) * sqn[q] * kpq;
-      } else {
-        a_n += 2.0 * n[q] * (2.0 * J[(size_t)p * A + q] - kpq);
-        a_p -= 2.0 * phi[q] * kpq;
-        a_7s += phi[q] * phi[q] * kpq;
-      }
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (p >= A) return;
+  const int g = pm[p];
+  double e = 0.0, a_n = 0.0, a_s = 0.0, a_p = 0.0, a_7s = 0.0;
+  for (int q = lane; q < A; q += 32) {
+    const size_t o = (size_t)p * A + q;
+    const double kpq = K[o], jpq = J[o];
+    e += Ac[o] * jpq + Bc[o] * kpq;
+    if (pm[q] == g) {
+      const bool plus = (p == q || (p >= d.npair && q >= d.npair));
+      a_s += (plus ? 2.0 : -2.0) * sqn[q] * kpq;
+    } else {
+      a_n += 2.0 * n[q] * (2.0 * jpq - kpq);
+      a_p -= 2.0 * phi[q] * kpq;
+      a_7s += phi[q] * phi[q] * kpq;
     }
-    if (d.functional == DONOF_PNOF7S) a_n -= 8.0 * (1.0 - 2.0 * n[p]) * a_7s;
-    gn[p] = a_n;
-    gs[p] = a_s;
-    gp[p] = (d.functional == DONOF_PNOF7) ? a_p : 0.0;
   }
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = e;
-  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    a_n += __shfl_xor_sync(0xffffffffu, a_n, o);
+    a_s += __shfl_xor_sync(0xffffffffu, a_s, o);
+    a_p += __shfl_xor_sync(0xffffffffu, a_p, o);
+    a_7s += __shfl_xor_sync(0xffffffffu, a_7s, o);
+  }
+  if (lane == 0) {
+    a_n += 2.0 * Hd[p];
+    if (d.functional == DONOF_PNOF7S) a_n -= 8.0 * (1.0 - 2.0 * n[p]) * a_7s;
+    part[p] = e + 2.0 * n[p] * Hd[p];
+    part[A + p] = a_n;
+    part[2 * A + p] = a_s;
+    part[3 * A + p] = (d.functional == DONOF_PNOF7) ? a_p : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __restrict__ part,
+                                                      const double* __restrict__ dn,
+                                                      const double* __restrict__ dsq,
+                                                      const double* __restrict__ dphi,
+                                                      DevHeader* hdr, double* dEdg_ws,
+                                                      double* E_out, double* dEdg_out) {
+  const int A = d.A;
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int i = 0; i < (int)blockDim.x / 32; ++i) t += red[i];
+    for (int p = 0; p < A; ++p) t += part[p];
     hdr->E = t;
     if (E_out) *E_out = t;
     if (!isfinite(t)) set_status(hdr, DONOF_ERR_NONFINITE);
   }
+  const double* gn = part + A;
+  const double* gs = part + 2 * A;
+  const double* gp = part + 3 * A;
   for (int k = threadIdx.x; k < d.ng; k += blockDim.x) {
     double t = 0.0;
     for (int p = 0; p < A; ++p) {
@@ -726,19 +735,16 @@ __global__ void __launch_bounds__(256) k_energy(Dims d, const int32_t* __restric
 
 cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layout& L,
                           double* E_out, double* dEdg_out, cudaStream_t s) {
-  const size_t shm = 3 * (size_t)d.A * sizeof(double);
-  if (shm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)shm);
-    if (e != cudaSuccess) return e;
-  }
-  k_energy<<<1, 256, shm, s>>>(
+  double* part = (double*)(ws + L.Epart);
+  k_energy_rows<<<(d.A + 7) / 8, 256, 0, s>>>(
       d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
-      (const double*)(ws + L.dn), (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
       (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef), (const double*)(ws + L.Hd),
-      (const double*)(ws + L.J), (const double*)(ws + L.K), (DevHeader*)(ws + L.header),
-      (double*)(ws + L.dEdg), E_out, dEdg_out);
-  count_launch(1);
+      (const double*)(ws + L.J), (const double*)(ws + L.K), part);
+  k_energy_final<<<1, 256, 0, s>>>(d, part, (const double*)(ws + L.dn),
+                                   (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
+                                   (DevHeader*)(ws + L.header), (double*)(ws + L.dEdg), E_out,
+                                   dEdg_out);
+  count_launch(2);
   return cudaGetLastError();
 }
 

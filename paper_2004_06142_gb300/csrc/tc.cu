@@ -86,6 +86,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+// Plain (untiled) bulk copy global -> shared, completion counted on an mbarrier; the
+// source is read once, so it is marked evict-first in L2.
+__device__ __forceinline__ void bulk_load_once(uint32_t dst, const void* src, uint32_t bytes,
+                                               uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], pol;\n\t}" ::"r"(dst),
+      "l"((unsigned long long)src), "r"(bytes), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -186,10 +198,18 @@ struct TcArgs {
   const int* eB; long long eB_zstride, eB_sstride;
   const int* glob_exp;  // extra power of two applied to every output (mode 2), or the
                         // exponent of the hi/lo split written for the G contraction (mode 1)
-  // mode 1 outputs, X[row][c] with row = P * Nmu + mu: integer + fraction X[P][mu][c] for
-  // the G contraction (exponent eX3[spOf[P]][mu], common to the slices of one G split) and
-  // X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X
-  int Nmu, Ap, Np;
+  // A operand from pre-tiled planes (BK = 64 only): the tile of rows [r0, r0 + 128) and
+  // k block kb is the contiguous run of rows x 128 bytes at a_tiled + kb * a_kb_stride +
+  // r0 * 64, already in the 128-byte swizzled order; a partial last row block is copied
+  // as far as it goes (its missing rows only reach accumulator rows that are not stored)
+  const __half* a_tiled_h;
+  const __half* a_tiled_f;
+  long long a_kb_stride;
+  // mode 1 outputs, X[row][c] with row = P * Nmu + mu (mu < Nrow valid): integer +
+  // fraction X[P][mu][c] for the G contraction (exponent eX3[spOf[P]][mu], common to the
+  // slices of one G split) and X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X; the row
+  // exponents eA are indexed by P * Nrow + mu
+  int Nmu, Nrow, Ap, Np;
   __half *xhi, *xlo, *xth, *xtf;
   const int* eXt;
   const int* spOf;
@@ -282,10 +302,20 @@ __global__ void __launch_bounds__(256, 1)
           const uint32_t eb = smem_u32(&bars[S + stage]);
           if (!mbar_wait(eb, phase ^ 1u, status, abort_flag)) { ok = false; break; }
           const uint32_t fb = smem_u32(&bars[stage]);
-          mbar_expect_tx(fb, stage_bytes);
           const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
-          tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
-          tma_load_3d(base + a_bytes, &mAl, fb, kt * BK, mt * BM, az);
+          if (BK == 64 && args.a_tiled_h) {
+            const int r0 = mt * BM;
+            const int rv = args.M - r0 < BM ? args.M - r0 : BM;
+            const uint32_t abytes = (uint32_t)rv * 128u;
+            mbar_expect_tx(fb, 2 * abytes + 2 * b_bytes);
+            const size_t off = (size_t)kt * args.a_kb_stride + (size_t)r0 * 64;
+            bulk_load_once(base, args.a_tiled_h + off, abytes, fb);
+            bulk_load_once(base + a_bytes, args.a_tiled_f + off, abytes, fb);
+          } else {
+            mbar_expect_tx(fb, stage_bytes);
+            tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
+            tma_load_3d(base + a_bytes, &mAl, fb, kt * BK, mt * BM, az);
+          }
           tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, 0, bz);
           tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, 0, bz);
           if (++stage == S) { stage = 0; phase ^= 1u; }
@@ -354,21 +384,26 @@ __global__ void __launch_bounds__(256, 1)
       if (!ok) break;
       tc_fence_after();
       const int row = mt * BM + ew * 32 + lane;
-      const bool valid = row < args.M;
-      const uint32_t t0 =
-          tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
-      const uint32_t t1 = t0 + (uint32_t)args.Nn;
-      const int erow =
-          (NUM == kIntFrac && valid) ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + row] : 0;
       // mode 1: slice and AO index of this row, the exponent of its X row in the G
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
+      bool valid = row < args.M;
+      if (args.mode == 1) {
+        rP = row / args.Nmu;
+        rmu = row % args.Nmu;
+        valid = valid && rmu < args.Nrow;
+      }
+      const int erow_i = args.mode == 1 ? rP * args.Nrow + rmu : row;
+      const uint32_t t0 =
+          tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
+      const uint32_t t1 = t0 + (uint32_t)args.Nn;
+      const int erow = (NUM == kIntFrac && valid)
+                           ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + erow_i]
+                           : 0;
       float sx3 = 1.f;
       const int* exrow = nullptr;
       if (args.mode == 1 && valid) {
-        rP = row / args.Nmu;
-        rmu = row % args.Nmu;
-        sx3 = pow2f(-args.eX3[(size_t)args.spOf[rP] * args.Nmu + rmu]);
+        sx3 = pow2f(-args.eX3[(size_t)args.spOf[rP] * args.Nrow + rmu]);
         exrow = args.eXt + (size_t)rP * args.Ap;
       }
       const int* ecol =
@@ -401,7 +436,7 @@ __global__ void __launch_bounds__(256, 1)
             hi[j] = __float2half_rn(h);
             lo[j] = __float2half_rn(w - h);
           }
-          const size_t o = (size_t)row * args.Ap + c0;
+          const size_t o = ((size_t)rP * args.Nrow + rmu) * args.Ap + c0;
           uint4* dh = (uint4*)(args.xhi + o);
           uint4* dl = (uint4*)(args.xlo + o);
           dh[0] = ((uint4*)hi)[0]; dh[1] = ((uint4*)hi)[1];
@@ -673,26 +708,44 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
   }
 }
 
-// B (double, dense or packed) -> integer + fraction planes [Q][N][Np], columns >= N zero.
+// B (double, dense or packed) -> integer + fraction planes in the pre-tiled layout of the
+// half transform: [KB][Q * Np rows][64] (KB = ceil(N / 64) k blocks of 64 columns, the
+// rows of slice P at P * Np .. P * Np + N - 1, padding rows and columns >= N zero), the
+// 16-byte chunk j of row R stored at chunk j ^ (R % 8): the 128-byte swizzle of a shared
+// memory tile that starts on a row multiple of 8.  One thread per chunk of 8 elements.
 __global__ void k_split_B(const double* __restrict__ B, int layout, long long Q, int N, int Np,
-                          DevHeader* hdr, const int* __restrict__ eB, __half* H, __half* F) {
+                          int KB, DevHeader* hdr, const int* __restrict__ eB, __half* H,
+                          __half* F) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hdr->maxB = __longlong_as_double((long long)hdr->maxB_bits);
     hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
   }
   const long long npk = (long long)N * (N + 1) / 2;
-  const long long tot = Q * N * Np;
+  const long long rows = Q * Np;
+  const long long tot = (long long)KB * rows * 8;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
-    const int nu = (int)(i % Np);
-    const long long r = i / Np;
-    const int mu = (int)(r % N);
-    const long long P = r / N;
-    const double v = nu < N ? load_B_elem(B, layout, P, r, mu, nu, N, npk) : 0.0;
-    const double y = ldexp(v, -eB[r]);
-    const double h = rint(y);
-    H[i] = __double2half(h);
-    F[i] = __double2half(y - h);
+    const int j = (int)(i % 8);
+    const long long t = i / 8;
+    const long long R = t % rows;
+    const int kb = (int)(t / rows);
+    const long long P = R / Np;
+    const int mu = (int)(R % Np);
+    __align__(16) __half hv[8], fv[8];
+    const long long r = P * N + mu;
+    const int e = mu < N ? eB[r] : 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int nu = kb * 64 + j * 8 + k;
+      const double v = (mu < N && nu < N) ? load_B_elem(B, layout, P, r, mu, nu, N, npk) : 0.0;
+      const double y = ldexp(v, -e);
+      const double h = rint(y);
+      hv[k] = __double2half(h);
+      fv[k] = __double2half(y - h);
+    }
+    const size_t o = ((size_t)kb * rows + R) * 64 + (size_t)((j ^ (int)(R & 7)) * 8);
+    *(uint4*)(H + o) = *(const uint4*)hv;
+    *(uint4*)(F + o) = *(const uint4*)fv;
   }
 }
 
@@ -928,7 +981,7 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB),
                                           (unsigned long long*)(ws + L.L1max),
                                           (double*)(ws + L.rn2));
-  k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, hdr,
+  k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, (d.N + 63) / 64, hdr,
                                           (const int*)(ws + L.eB), (__half*)(ws + L.Bhi),
                                           (__half*)(ws + L.Blo));
   count_launch(2);
@@ -1025,23 +1078,27 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   count_launch(2);
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
-    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * N * Np;
-    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * N * Np;
-    const uint64_t rows = (uint64_t)np * N;
-    const int bk = tuned_bk(1, N, Ap, np);
-    if (!make_map(&ah, Bh, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
-        !make_map(&al, Bl, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
-        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
+    // A operand: the pre-tiled split B (bulk copies, BK = 64); rows (P, mu) of the block
+    // flattened with pitch Np per slice
+    const int KB = (N + 63) / 64;
+    const uint64_t rows = (uint64_t)np * Np;
+    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * Np * 64;
+    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * Np * 64;
+    const int bk = 64;
+    if (!make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
         !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
       return DONOF_ERR_CUDA;
+    ah = bh;  // unused: the A tiles come from the bulk copies
+    al = bl;
     TcArgs a{};
     a.mode = 1; a.M = (int)rows; a.Nn = Ap;
     a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
-    a.kt_per_kb = (N + bk - 1) / bk; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.kt_per_kb = KB; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.a_tiled_h = Bh; a.a_tiled_f = Bl; a.a_kb_stride = (long long)d.Q * Np * 64;
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->sX;
-    a.Nmu = N; a.Ap = Ap; a.Np = Np;
+    a.Nmu = Np; a.Nrow = N; a.Ap = Ap; a.Np = Np;
     a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
@@ -1128,6 +1185,7 @@ int autotune_build(const donof_problem* prob, const double* h, const double* B, 
                    cudaStream_t s) {
   const Dims d = make_dims(prob);
   const int np = d.pb < d.Q ? d.pb : d.Q;
+  // the half transform always runs with BK = 64 (its pre-tiled operand is laid out for it)
   const int phases[3] = {DONOF_PHASE_HALF_TRANSFORM, DONOF_PHASE_MO_3INDEX, DONOF_PHASE_G_BUILD};
   const int cand[2] = {64, 32};
   double best_ms[3] = {1e300, 1e300, 1e300};
@@ -1148,7 +1206,7 @@ int autotune_build(const donof_problem* prob, const double* h, const double* B, 
     for (int r = 0; r < 2 && rc == DONOF_OK; ++r)
       rc = donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, bytes, E, nullptr, nullptr,
                                    s);
-    for (int k = 0; k < 3 && rc == DONOF_OK; ++k) {
+    for (int k = 1; k < 3 && rc == DONOF_OK; ++k) {
       double ms = 0.0;
       int n = 0;
       if (donof_profile_read(phases[k], &ms, &n) != DONOF_OK || n == 0) continue;
