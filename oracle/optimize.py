@@ -37,10 +37,20 @@ def optimize_occupations(Hdiag, J, K, gamma0, pair_map, npair, ncwo, functional,
                          gtol=1e-10, maxiter=2000):
     """argmin_gamma E[n(gamma)] at fixed orbitals; returns (gamma, E, iterations)."""
     fun = lambda x: energy_of_gamma(x, Hdiag, J, K, pair_map, npair, ncwo, functional)
-    res = minimize(fun, np.asarray(gamma0, dtype=np.float64), jac=True, method="L-BFGS-B",
-                   options=dict(gtol=gtol, ftol=0.0, maxiter=maxiter, maxcor=8))
-    E, _ = fun(res.x)
-    return res.x, E, res.nit
+    x = np.asarray(gamma0, dtype=np.float64)
+    E, _ = fun(x)
+    nit = 0
+    # restarted until E stops decreasing: an optimum on a kink of sqrt(n) = |sin gamma|
+    # (an emptied orbital) stalls one run of the quasi-Newton method before it is reached
+    for _ in range(50):
+        res = minimize(fun, x, jac=True, method="L-BFGS-B",
+                       options=dict(gtol=gtol, ftol=0.0, maxiter=maxiter, maxcor=8))
+        nit += res.nit
+        E_new, _ = fun(res.x)
+        if not E_new < E:
+            break
+        x, E = res.x, E_new
+    return x, E, nit
 
 
 # ----------------------------------------------------------------------------
