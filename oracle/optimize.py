@@ -33,17 +33,29 @@ def energy_of_gamma(gamma, Hdiag, J, K, pair_map, npair, ncwo, functional):
     return E, g
 
 
+def fold_gamma(gamma):
+    """The representative of gamma in [0, pi/2]: n, sqrt(n) and Phi of Eqs. soo/woo depend on
+    each gamma only through |sin gamma| and |cos gamma|, so E is unchanged by gamma -> -gamma
+    and gamma -> pi - gamma."""
+    t = np.remainder(np.asarray(gamma, dtype=np.float64), np.pi)
+    return np.where(t > np.pi / 2, np.pi - t, t)
+
+
 def optimize_occupations(Hdiag, J, K, gamma0, pair_map, npair, ncwo, functional,
                          gtol=1e-10, maxiter=2000):
-    """argmin_gamma E[n(gamma)] at fixed orbitals; returns (gamma, E, iterations)."""
+    """argmin_gamma E[n(gamma)] at fixed orbitals; returns (gamma, E, iterations).
+
+    Reading: the minimisation runs over the fundamental box [0, pi/2]^ng (fold_gamma), with
+    bounds; a minimum on a kink of sqrt(n) = |sin gamma| (an emptied weak orbital, a pair
+    split evenly) is then a bound-constrained minimum, where a projected quasi-Newton method
+    converges instead of zigzagging across the kink."""
     fun = lambda x: energy_of_gamma(x, Hdiag, J, K, pair_map, npair, ncwo, functional)
-    x = np.asarray(gamma0, dtype=np.float64)
+    x = fold_gamma(gamma0)
     E, _ = fun(x)
     nit = 0
-    # restarted until E stops decreasing: an optimum on a kink of sqrt(n) = |sin gamma|
-    # (an emptied orbital) stalls one run of the quasi-Newton method before it is reached
-    for _ in range(50):
-        res = minimize(fun, x, jac=True, method="L-BFGS-B",
+    bounds = [(0.0, np.pi / 2)] * len(x)
+    for _ in range(20):  # restarted until E stops decreasing
+        res = minimize(fun, x, jac=True, method="L-BFGS-B", bounds=bounds,
                        options=dict(gtol=gtol, ftol=0.0, maxiter=maxiter, maxcor=8))
         nit += res.nit
         E_new, _ = fun(res.x)
