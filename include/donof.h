@@ -123,6 +123,25 @@ int donof_get_jk(const donof_problem* prob, const void* workspace, size_t worksp
  * last call on `workspace` (DONOF_OK or a DONOF_ERR_* code) and clears it. */
 int donof_read_status(const void* workspace, int32_t* status, void* stream);
 
+/* Occupation optimisation at fixed orbitals (Sec. III.D: in every iteration gamma is
+ * optimised for fixed natural orbitals, by CG or L-BFGS).  Minimises E[n(gamma), phi] of
+ * Eqs. EPNOF7 / Eg / Efg (/ Efg_s) over the unconstrained gamma (occupations by Eqs. soo,
+ * woo) with L-BFGS (memory 8) and an Armijo backtracking line search, in one CTA, using the
+ * H_pp, J_pq and K_pq of the last donof_energy_lagrangian call on `workspace` (same problem;
+ * the orbitals of that call are the fixed ones).  Since the occupations depend on each gamma
+ * only through |sin gamma| and |cos gamma|, the search runs over the box [0, pi/2]^ng of
+ * representatives (projected L-BFGS; the start point is folded into it first), so that a
+ * minimum on a kink of sqrt(n) = |sin gamma| is a minimum on a bound.  gamma[npair*ncwo]
+ * (device) holds the start point on entry and the optimum (in the box) on return; E (device
+ * scalar, may be NULL) receives the optimal energy and iters (device int32, may be NULL) the
+ * L-BFGS iterations taken.  Stops when the projected gradient is below gtol in every
+ * component, when no step lowers E any further, or after max_iter iterations.  DONOF_ERR_UNSUPPORTED when nact is too large for one CTA's shared memory
+ * (about 2400 active orbitals). */
+int donof_optimize_occupations(const donof_problem* prob, const int32_t* pair_map,
+                               double* gamma, void* workspace, size_t workspace_bytes,
+                               int32_t max_iter, double gtol, double* E, int32_t* iters,
+                               void* stream);
+
 /* Hand-off to the orbital update (Sec. III.B).  Builds the symmetric matrix of Eq. Fockian,
  *   F_qp = theta(p - q)[lambda_qp - lambda_pq] + theta(q - p)[lambda_pq - lambda_qp] (q != p),
  *   F_pp = Fdiag[p]   (the paper takes the diagonal from the previous diagonalisation),
@@ -166,6 +185,55 @@ int donof_prepare_B_batched(int32_t ninst, const donof_problem* probs, const don
 int donof_energy_lagrangian_batched(int32_t ninst, const donof_problem* probs,
                                     const donof_instance* inst, void* workspace,
                                     size_t workspace_bytes, int32_t flags, void* stream);
+
+/* The optimisation procedure around the build (Sec. III.D, with Sec. III.B's scaling and
+ * Sec. III.C's DIIS).  Each outer iteration optimises the occupations at fixed orbitals
+ * (donof_optimize_occupations) and then the orbitals at fixed occupations by up to
+ * max_inner diagonalisations of F (Eq. Fockian):
+ *   - the off-diagonal of F comes from the build's lambda; every element above zeta in
+ *     magnitude is divided by ten until it is not (zeta <= 0: no scaling);
+ *   - the diagonal is the previous diagonalisation's eigenvalues (Fdiag, in/out);
+ *   - F and its error vector e = offdiag F are taken to the AO basis (C F C^T, C e C^T) and,
+ *     with diis_depth >= 2, the last diis_depth of them are combined with the coefficients
+ *     of the bordered least-squares system of Sec. III.C;
+ *   - the eigenvectors of the result, in decreasing eigenvalue order (the energy-lowering
+ *     order for lambda = C^T G as defined here), are the new orbitals, reorthonormalised by
+ *     one Newton-Schulz step, and those eigenvalues the next diagonal.
+ * The orbital iterations of an outer iteration stop when max |lambda_qp - lambda_pq| < delta
+ * or E changed by less than eps_energy; the procedure has converged when, after an outer
+ * iteration, the asymmetry is below delta and E changed by less than eps_energy over it.
+ * With init_diagonal != 0 the start follows Sec. III.D's initial step: after the first
+ * occupation optimisation the symmetrised lambda is diagonalised, its eigenvectors (ascending)
+ * rotate C and minus its eigenvalues are the first diagonal; otherwise Fdiag is used as given.
+ * h, B, pair_map as for donof_energy_lagrangian (B already prepared in build_ws); C[nbf*nbf],
+ * gamma[npair*ncwo] and Fdiag[nbf] are device arrays updated in place.  opt_ws: device,
+ * 256-byte aligned, donof_optimize_workspace_size bytes.  The call is synchronous: the host
+ * reads E and the asymmetry after every build.  *result (host) receives the final E and
+ * asymmetry, the iteration counts and whether it converged; energies (host, optional)
+ * receives the energy of every orbital-iteration build, at most energies_cap of them. */
+typedef struct {
+  int32_t max_outer;    /* outer iterations (>= 1) */
+  int32_t max_inner;    /* diagonalisations per outer iteration (>= 1) */
+  int32_t diis_depth;   /* 0 or 1: no extrapolation; 2..16: matrices combined */
+  int32_t occ_max_iter; /* L-BFGS iterations per occupation optimisation */
+  double zeta;          /* scaling bound of F's off-diagonal (<= 0: none) */
+  double delta;         /* max |lambda_qp - lambda_pq| criterion */
+  double eps_energy;    /* energy criterion */
+  double occ_gtol;      /* occupation optimisation: max |dE/dgamma| criterion (> 0) */
+} donof_opt_params;
+
+typedef struct {
+  double E;             /* energy at the final orbitals and occupations */
+  double max_asym;      /* max |lambda_qp - lambda_pq| there */
+  int32_t outer, inner, builds, converged, energies_recorded, reserved;
+} donof_opt_result;
+
+int donof_optimize_workspace_size(const donof_problem* prob, int32_t diis_depth, size_t* bytes);
+int donof_optimize(const donof_problem* prob, const donof_opt_params* params, const double* h,
+                   const double* B, double* C, double* gamma, const int32_t* pair_map,
+                   double* Fdiag, int32_t init_diagonal, void* build_ws, size_t build_bytes,
+                   void* opt_ws, size_t opt_bytes, donof_opt_result* result, double* energies,
+                   int32_t energies_cap, void* stream);
 
 /* A build that allocates no device memory, for callers that cannot allocate at the time
  * they need one (a host framework that owns the device memory pool, a loop where an

@@ -41,6 +41,20 @@ class donof_instance(ctypes.Structure):
                                               "dE_dgamma", "dE_dC")]
 
 
+class donof_opt_params(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("diis_depth", ctypes.c_int32), ("occ_max_iter", ctypes.c_int32),
+                ("zeta", ctypes.c_double), ("delta", ctypes.c_double),
+                ("eps_energy", ctypes.c_double), ("occ_gtol", ctypes.c_double)]
+
+
+class donof_opt_result(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("max_asym", ctypes.c_double),
+                ("outer", ctypes.c_int32), ("inner", ctypes.c_int32), ("builds", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("energies_recorded", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class donof_problem(ctypes.Structure):
     _fields_ = [("nbf", ctypes.c_int32), ("naux", ctypes.c_int32), ("npair", ctypes.c_int32),
                 ("ncwo", ctypes.c_int32), ("functional", ctypes.c_int32),
@@ -76,6 +90,13 @@ def lib() -> ctypes.CDLL:
         L.donof_orbital_update_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_orbital_update.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp, vp, vp]
         L.donof_autotune.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.donof_optimize_occupations.argtypes = [P, vp, vp, vp, sz, ctypes.c_int32,
+                                                 ctypes.c_double, vp, vp, vp]
+        L.donof_optimize_workspace_size.argtypes = [P, ctypes.c_int32,
+                                                    ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_optimize.argtypes = [P, ctypes.POINTER(donof_opt_params), vp, vp, vp, vp, vp, vp,
+                                     ctypes.c_int32, vp, sz, vp, sz,
+                                     ctypes.POINTER(donof_opt_result), vp, ctypes.c_int32, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -86,7 +107,8 @@ def lib() -> ctypes.CDLL:
                   "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
-                  "donof_orbital_update", "donof_autotune"):
+                  "donof_orbital_update", "donof_autotune", "donof_optimize_occupations",
+                  "donof_optimize_workspace_size", "donof_optimize"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -168,6 +190,15 @@ def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):
     return ws
 
 
+def donof_optimize_occupations(prob, pair_map, gamma, ws, max_iter=500, gtol=1e-9, E=None,
+                               iters=None, stream=None):
+    """L-BFGS over gamma at the orbitals of the last build on ``ws`` (gamma updated in place)."""
+    _check(lib().donof_optimize_occupations(ctypes.byref(prob), _ptr(pair_map), _ptr(gamma),
+                                            _ptr(ws), ws.numel(), int(max_iter), float(gtol),
+                                            _ptr(E), _ptr(iters), _stream(stream)),
+           "donof_optimize_occupations")
+
+
 def donof_get_jk(prob, ws, J=None, K=None, stream=None):
     _check(lib().donof_get_jk(ctypes.byref(prob), _ptr(ws), ws.numel(), _ptr(J), _ptr(K),
                               _stream(stream)), "donof_get_jk")
@@ -241,6 +272,42 @@ class Builder:
         dg = torch.empty(self.ngamma, dtype=f64, device=dev)
         donof_energy_backward(self.prob, Ebar, self.ws, dC, dg)
         return dC, dg
+
+    def optimize_occupations(self, gamma, pair_map, max_iter=500, gtol=1e-9):
+        """Optimal gamma (in place), its energy and the iterations taken, at the orbitals of
+        the last forward()."""
+        E = torch.empty(1, dtype=torch.float64, device=self.device)
+        it = torch.zeros(1, dtype=torch.int32, device=self.device)
+        donof_optimize_occupations(self.prob, pair_map, gamma, self.ws, max_iter, gtol, E, it)
+        return E, it
+
+    def optimize(self, h, C, gamma, pair_map, Fdiag=None, max_outer=50, max_inner=10,
+                 diis_depth=6, zeta=1.0, delta=1e-6, eps_energy=1e-10, occ_max_iter=500,
+                 occ_gtol=1e-10, max_energies=4096):
+        """The optimisation procedure (donof_optimize): C, gamma and the diagonal (returned)
+        are updated in place; with Fdiag None the initial diagonal comes from the
+        symmetrised lambda.  Returns (result dict, energies of the orbital iterations)."""
+        prm = donof_opt_params(max_outer, max_inner, diis_depth, occ_max_iter, zeta, delta,
+                               eps_energy, occ_gtol)
+        nb = ctypes.c_size_t(0)
+        _check(lib().donof_optimize_workspace_size(ctypes.byref(self.prob), diis_depth,
+                                                   ctypes.byref(nb)),
+               "donof_optimize_workspace_size")
+        ows = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        init = Fdiag is None
+        if init:
+            Fdiag = torch.zeros(self.nbf, dtype=torch.float64, device=self.device)
+        res = donof_opt_result()
+        energies = (ctypes.c_double * max(max_energies, 1))()
+        _check(lib().donof_optimize(ctypes.byref(self.prob), ctypes.byref(prm), _ptr(h),
+                                    _ptr(self.B), _ptr(C), _ptr(gamma), _ptr(pair_map),
+                                    _ptr(Fdiag), 1 if init else 0, _ptr(self.ws),
+                                    self.ws.numel(), _ptr(ows), ows.numel(), ctypes.byref(res),
+                                    energies, max_energies, _stream(None)), "donof_optimize")
+        out = dict(E=res.E, max_asym=res.max_asym, outer=res.outer, inner=res.inner,
+                   builds=res.builds, converged=bool(res.converged), Fdiag=Fdiag)
+        n = min(res.energies_recorded, max_energies)
+        return out, [energies[i] for i in range(n)]
 
     def jk(self):
         J = torch.empty(self.nact, self.nact, dtype=torch.float64, device=self.device)

@@ -6,6 +6,7 @@
 //   J / K accumulation over P, the Y^P operands . Eqs. JKpq (density-fitted)
 //   energy and dE/dgamma ........................ Eqs. EPNOF7, Eg, Efg, Efg_s
 #include "common.cuh"
+#include "occ.cuh"
 
 namespace donof {
 
@@ -118,60 +119,25 @@ __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
     set_status(hdr, DONOF_ERR_PAIR_MAP);
     return;
   }
-  const double rs2 = 0.70710678118654752440;  // 1/sqrt(2)
-  const double tg = gamma[g];
-  const double cg = cos(tg), sg = sin(tg);
-  const double sh = fabs(sg) * rs2;                 // sqrt(1 - n_g) = sqrt(h_g)
-  const double dsh = copysign(1.0, sg) * cg * rs2;
+  int rank = 0;
   if (p < npair) {
-    // strong orbital g = p: n_g = (1 + cos^2 gamma_g) / 2
     int cnt = 0;
     for (int q = npair; q < A; ++q) cnt += (pm[q] == p);
     if (cnt != ncwo) set_status(hdr, DONOF_ERR_PAIR_MAP);
-    const double ng_ = 0.5 * (1.0 + cg * cg);
-    const double r = sqrt(ng_);
-    const double dng = -cg * sg;
-    n[p] = ng_; sqn[p] = r; phi[p] = r * sh;
-    dn[(size_t)p * ng + g] = dng;
-    dsq[(size_t)p * ng + g] = dng / (2.0 * r);
-    dphi[(size_t)p * ng + g] = dng / (2.0 * r) * sh + r * dsh;
-    return;
+  } else {
+    // rank among the pair's weak orbitals
+    for (int q = npair; q < p; ++q) rank += (pm[q] == g);
+    if (rank >= ncwo) {
+      set_status(hdr, DONOF_ERR_PAIR_MAP);
+      return;
+    }
   }
-  // weak orbital p_i of pair g: i = its rank among the pair's weak orbitals
-  int i = 0;
-  for (int q = npair; q < p; ++q) i += (pm[q] == g);
-  if (i >= ncwo) {
-    set_status(hdr, DONOF_ERR_PAIR_MAP);
-    return;
-  }
-  const int wbase = npair + g * (ncwo - 1);
-  const bool has_sin = (i < ncwo - 1);
-  // sqrt(n_{p_i}) = sh * prod_{j<i} |cos gamma_j| * (|sin gamma_i| unless last)
-  double prodc = 1.0;
-  for (int j = 0; j < i; ++j) prodc *= fabs(cos(gamma[wbase + j]));
-  const double si = has_sin ? fabs(sin(gamma[wbase + i])) : 1.0;
-  const double val = sh * prodc * si;
-  const double nn = val * val;
-  const double om = sqrt(1.0 - nn);
-  n[p] = nn; sqn[p] = val; phi[p] = val * om;
-  auto put = [&](int k, double ds) {
-    const double dnk = 2.0 * val * ds;
-    dsq[(size_t)p * ng + k] = ds;
-    dn[(size_t)p * ng + k] = dnk;
-    dphi[(size_t)p * ng + k] = ds * om - val * dnk / (2.0 * om);
-  };
-  put(g, dsh * prodc * si);
-  for (int j = 0; j < i; ++j) {
-    const double t = gamma[wbase + j];
-    double rest = sh * si;
-    for (int jj = 0; jj < i; ++jj)
-      if (jj != j) rest *= fabs(cos(gamma[wbase + jj]));
-    put(wbase + j, -copysign(1.0, cos(t)) * sin(t) * rest);
-  }
-  if (has_sin) {
-    const double t = gamma[wbase + i];
-    put(wbase + i, copysign(1.0, sin(t)) * cos(t) * sh * prodc);
-  }
+  occ_orbital(p, g, rank, npair, ncwo, gamma, n[p], sqn[p], phi[p],
+              [&](int k, double dnk, double dsk, double dpk) {
+                dn[(size_t)p * ng + k] = dnk;
+                dsq[(size_t)p * ng + k] = dsk;
+                dphi[(size_t)p * ng + k] = dpk;
+              });
 }
 }  // namespace
 
@@ -206,17 +172,9 @@ __global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const dou
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)A * A) return;
   const int p = (int)(idx / A), q = (int)(idx % A);
-  double a = 0.0, b;
-  if (pm[p] == pm[q]) {
-    const bool p_strong = (p < d.npair), q_strong = (q < d.npair);
-    const double sgn = (p == q || (!p_strong && !q_strong)) ? 1.0 : -1.0;
-    b = sgn * sqn[p] * sqn[q];
-  } else {
-    a = 2.0 * n[p] * n[q];
-    b = -n[p] * n[q];
-    if (d.functional == DONOF_PNOF7) b -= phi[p] * phi[q];
-    else if (d.functional == DONOF_PNOF7S) b -= 4.0 * phi[p] * phi[p] * phi[q] * phi[q];
-  }
+  double a, b;
+  pair_coefficients(d.functional, d.npair, p, q, pm[p] == pm[q], n[p], n[q], sqn[p], sqn[q],
+                    phi[p], phi[q], a, b);
   Ac[idx] = a;
   Bc[idx] = b;
 }
@@ -660,7 +618,7 @@ cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char
 //   dE/dgamma_k = sum_p (dE/dn_p dn_p/dgamma_k + dE/dsqrt_np dsqrt_np/dgamma_k
 //                        + dE/dPhi_p dPhi_p/dgamma_k)
 // k_energy_rows: one warp per orbital p (its share of E and the three partials);
-// k_energy_final: E as an ordered sum of the shares, then dE/dgamma.
+// k_energy_final: E as a fixed-order sum of the shares, then dE/dgamma (a warp per output).
 // ---------------------------------------------------------------------------
 namespace {
 __global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
@@ -704,31 +662,40 @@ __global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const doub
   }
 }
 
-__global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __restrict__ part,
-                                                      const double* __restrict__ dn,
-                                                      const double* __restrict__ dsq,
-                                                      const double* __restrict__ dphi,
-                                                      DevHeader* hdr, double* dEdg_ws,
-                                                      double* E_out, double* dEdg_out) {
+__global__ void __launch_bounds__(1024) k_energy_final(Dims d, const double* __restrict__ part,
+                                                       const double* __restrict__ dn,
+                                                       const double* __restrict__ dsq,
+                                                       const double* __restrict__ dphi,
+                                                       DevHeader* hdr, double* dEdg_ws,
+                                                       double* E_out, double* dEdg_out) {
+  // one warp per output (E first, then each dE/dgamma_k), lanes over orbitals, a fixed
+  // shuffle tree: the sums do not depend on scheduling
   const int A = d.A;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int p = 0; p < A; ++p) t += part[p];
-    hdr->E = t;
-    if (E_out) *E_out = t;
-    if (!isfinite(t)) set_status(hdr, DONOF_ERR_NONFINITE);
-  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const double* gn = part + A;
   const double* gs = part + 2 * A;
   const double* gp = part + 3 * A;
-  for (int k = threadIdx.x; k < d.ng; k += blockDim.x) {
+  for (int k = warp - 1; k < d.ng; k += nw) {
     double t = 0.0;
-    for (int p = 0; p < A; ++p) {
-      const size_t o = (size_t)p * d.ng + k;
-      t += gn[p] * dn[o] + gs[p] * dsq[o] + gp[p] * dphi[o];
+    if (k < 0) {
+      for (int p = lane; p < A; p += 32) t += part[p];
+    } else {
+      for (int p = lane; p < A; p += 32) {
+        const size_t o = (size_t)p * d.ng + k;
+        t += gn[p] * dn[o] + gs[p] * dsq[o] + gp[p] * dphi[o];
+      }
     }
-    dEdg_ws[k] = t;
-    if (dEdg_out) dEdg_out[k] = t;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      if (k < 0) {
+        hdr->E = t;
+        if (E_out) *E_out = t;
+        if (!isfinite(t)) set_status(hdr, DONOF_ERR_NONFINITE);
+      } else {
+        dEdg_ws[k] = t;
+        if (dEdg_out) dEdg_out[k] = t;
+      }
+    }
   }
 }
 }  // namespace
@@ -740,7 +707,7 @@ cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layo
       d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
       (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef), (const double*)(ws + L.Hd),
       (const double*)(ws + L.J), (const double*)(ws + L.K), part);
-  k_energy_final<<<1, 256, 0, s>>>(d, part, (const double*)(ws + L.dn),
+  k_energy_final<<<1, 1024, 0, s>>>(d, part, (const double*)(ws + L.dn),
                                    (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
                                    (DevHeader*)(ws + L.header), (double*)(ws + L.dEdg), E_out,
                                    dEdg_out);

@@ -1,0 +1,89 @@
+"""The optimisation procedure on the GPU (donof_optimize: occupation optimisation, zeta-scaled
+and DIIS-extrapolated diagonalisations of F, Sec. III.B-D) against the oracle's procedure
+with the same readings and parameters: the energy of every orbital-iteration build along the
+trajectory, and a run to convergence."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import optimize, pnof
+
+from helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2004_06142_gb300.build as b
+    b.build()
+
+
+def _gpu(prob, d, precision, functional, **kw):
+    import torch
+    import paper_2004_06142_gb300 as dn
+    b = dn.Builder(prob.nbf, prob.naux, prob.npair, prob.ncwo, functional, dn.B_DENSE, precision)
+    b.prepare(to_dev(d["B"]))
+    C = to_dev(d["C"]).clone()
+    g = to_dev(d["gamma"]).clone()
+    out, energies = b.optimize(to_dev(d["h"]), C, g, to_dev(d["pair_map"].astype(np.int32)), **kw)
+    torch.cuda.synchronize()
+    return out, np.array(energies), C.cpu().numpy(), g.cpu().numpy()
+
+
+PARAMS = dict(zeta=1.0, diis_depth=6, delta=1e-12, eps_energy=0.0, max_outer=3, max_inner=5)
+
+
+@pytest.mark.parametrize("functional", [pnof.PNOF7, pnof.PNOF5, pnof.PNOF7S])
+@pytest.mark.parametrize("depth", [0, 6])
+def test_trajectory_matches_oracle(functional, depth):
+    prob = synth.Problem(24, 96, 5, 1, seed=0)
+    d = synth.generate(prob)
+    p = dict(PARAMS, diis_depth=depth)
+    out, E_gpu, C, g = _gpu(prob, d, 0, functional, **p)
+    ref = optimize.optimize(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], prob.npair,
+                            prob.ncwo, functional, zeta=p["zeta"], depth=depth,
+                            delta=p["delta"], eps_energy=p["eps_energy"],
+                            max_outer=p["max_outer"], max_inner=p["max_inner"])
+    E_ref = np.array(ref["energies"])
+    assert len(E_gpu) == len(E_ref) == 15
+    np.testing.assert_allclose(E_gpu, E_ref, rtol=0, atol=1e-8)
+    assert abs(out["E"] - ref["E"]) < 1e-8
+    # the final orbitals are orthonormal and give the reported energy in the oracle
+    np.testing.assert_allclose(C.T @ C, np.eye(prob.nbf), rtol=0, atol=1e-12)
+    E_at = pnof.build(d["h"], d["B"], C, g, d["pair_map"], prob.npair, prob.ncwo,
+                      functional)["E"]
+    assert abs(E_at - out["E"]) < 1e-9
+
+
+def test_converged_run_matches_oracle():
+    prob = synth.Problem(10, 40, 2, 1, seed=1)
+    d = synth.generate(prob)
+    kw = dict(zeta=1.0, delta=1e-7, eps_energy=1e-11, max_outer=100, max_inner=20)
+    out, _, C, g = _gpu(prob, d, 0, pnof.PNOF7, diis_depth=6, **kw)
+    ref = optimize.optimize(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], prob.npair,
+                            prob.ncwo, pnof.PNOF7, depth=6, **kw)
+    assert ref["converged"] and out["converged"]
+    assert out["max_asym"] < 1e-7
+    assert abs(out["E"] - ref["E"]) < 1e-9
+    lam = pnof.build(d["h"], d["B"], C, g, d["pair_map"], 2, 1, pnof.PNOF7)["lam"]
+    assert optimize.max_asymmetry(lam) < 1e-6
+
+
+def test_mixed_precision_trajectory_follows_oracle():
+    prob = synth.Problem(24, 96, 5, 1, seed=0)
+    d = synth.generate(prob)
+    p = dict(PARAMS, max_outer=2)
+    out, E_gpu, _, _ = _gpu(prob, d, 1, pnof.PNOF7, **p)
+    ref = optimize.optimize(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], prob.npair,
+                            prob.ncwo, pnof.PNOF7, zeta=p["zeta"], depth=p["diis_depth"],
+                            delta=p["delta"], eps_energy=p["eps_energy"],
+                            max_outer=p["max_outer"], max_inner=p["max_inner"])
+    E_ref = np.array(ref["energies"])
+    # the mixed lambda (about 1e-6 from the FP64 one) perturbs every rotation a little: the
+    # trajectories agree closely at first and drift apart slowly
+    np.testing.assert_allclose(E_gpu[:3], E_ref[:3], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(E_gpu, E_ref, rtol=0, atol=1e-4)
