@@ -62,6 +62,33 @@ def optimize_occupations(Hdiag, J, K, gamma0, pair_map, npair, ncwo, functional,
         if not E_new < E:
             break
         x, E = res.x, E_new
+    # Newton polish on the free variables (Hessian by central differences of the analytic
+    # gradient, minimum-norm steps for flat directions): gamma to near rounding, which the
+    # energy alone (flat to second order at the optimum) cannot pin
+    for _ in range(6):
+        E0, g0 = fun(x)
+        free = ~(((x <= 0.0) & (g0 > 0)) | ((x >= np.pi / 2) & (g0 < 0)))
+        pg0 = np.abs(np.clip(x - g0, 0.0, np.pi / 2) - x).max()
+        if not free.any() or pg0 < 1e-13:
+            break
+        idx = np.flatnonzero(free)
+        H = np.zeros((len(idx), len(idx)))
+        hs = 1e-5
+        for a, k in enumerate(idx):
+            xp, xm = x.copy(), x.copy()
+            xp[k] += hs
+            xm[k] -= hs
+            H[:, a] = (fun(xp)[1][idx] - fun(xm)[1][idx]) / (2 * hs)
+        H = 0.5 * (H + H.T)
+        step = -np.linalg.lstsq(H, g0[idx], rcond=1e-10)[0]
+        xn = x.copy()
+        xn[idx] = np.clip(x[idx] + step, 0.0, np.pi / 2)
+        En, gn = fun(xn)
+        pgn = np.abs(np.clip(xn - gn, 0.0, np.pi / 2) - xn).max()
+        if En <= E0 + 1e-14 * abs(E0) and pgn < pg0:
+            x, E = xn, En
+        else:
+            break
     return x, E, nit
 
 
