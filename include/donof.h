@@ -282,7 +282,9 @@ enum {
   DONOF_PHASE_BACKWARD = 6,        /* donof_energy_backward */
   DONOF_PHASE_PREPARE_B = 7,       /* donof_prepare_B */
   DONOF_PHASE_ORBITAL_UPDATE = 8,  /* donof_orbital_update */
-  DONOF_NUM_PHASES = 9
+  DONOF_PHASE_OCC_OPT = 9,         /* donof_optimize_occupations */
+  DONOF_PHASE_ORBITAL_STEP = 10,   /* one diagonalisation step of donof_optimize */
+  DONOF_NUM_PHASES = 11
 };
 int donof_profile_enable(int32_t enable);
 int donof_profile_read(int32_t phase, double* total_ms, int32_t* intervals);

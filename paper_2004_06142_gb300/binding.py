@@ -211,7 +211,7 @@ def donof_read_status(ws, stream=None) -> int:
 
 
 PHASES = ["prep", "half_transform", "mo_3index", "jk_y", "g_build", "energy_lambda",
-          "backward", "prepare_B", "orbital_update"]
+          "backward", "prepare_B", "orbital_update", "occ_opt", "orbital_step"]
 
 
 def donof_profile_enable(enable: bool):

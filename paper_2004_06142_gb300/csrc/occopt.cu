@@ -257,6 +257,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           accepted = true;
           break;
         }
+        // at the rounding level of E the Armijo test is noise: a step that does not raise E
+        // beyond rounding and shrinks the projected gradient is taken
+        if (fn <= f + 4e-16 * fabs(f)) {
+          double pgn = 0.0;
+          for (int k = threadIdx.x; k < ng; k += kThreads)
+            pgn = fmax(pgn, fabs(fmin(fmax(xn[k] - gn[k], kLo), kHi) - xn[k]));
+          pgn = block_max(pgn, c.red);
+          if (pgn < pg) {
+            accepted = true;
+            break;
+          }
+        }
       }
       t *= 0.5;
     }
@@ -324,10 +336,12 @@ extern "C" int donof_optimize_occupations(const donof_problem* prob, const int32
   if (cudaFuncSetAttribute(k_occ_lbfgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return DONOF_ERR_CUDA;
+  prof_begin(DONOF_PHASE_OCC_OPT, s);
   k_occ_lbfgs<<<1, kThreads, smem, s>>>(d, pair_map, (const double*)(ws + L.J),
                                         (const double*)(ws + L.K), (const double*)(ws + L.Hd),
                                         gamma, max_iter, gtol, (DevHeader*)(ws + L.header), E,
                                         iters);
   count_launch(1);
+  prof_end(DONOF_PHASE_OCC_OPT, s);
   return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
 }

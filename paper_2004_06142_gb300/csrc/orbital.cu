@@ -423,6 +423,7 @@ int loop_orbital_step(Loop& lp, double zeta, int depth, std::vector<int>& active
   double* F_ao = hist + 2 * (size_t)slot * nn;
   double* e_ao = F_ao + nn;
   double* c = (double*)(o + lp.L.c);
+  prof_begin(DONOF_PHASE_ORBITAL_STEP, lp.s);
   k_fockian_offdiag<<<152 * 4, 256, 0, lp.s>>>(lam, N, zeta, Emo);
   count_launch(1);
   // e_AO = C Emo C^T; F_AO = e_AO + C diag(Fdiag) C^T
@@ -466,6 +467,7 @@ int loop_orbital_step(Loop& lp, double zeta, int depth, std::vector<int>& active
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
   int rc = loop_reorthonormalise(lp);
   if (rc != DONOF_OK) return rc;
+  prof_end(DONOF_PHASE_ORBITAL_STEP, lp.s);
   // the restart decision is needed before the next step: read it now
   double flag = 0.0;
   if (!ok(cudaMemcpyAsync(&flag, c + kMaxDepth + 1, 8, cudaMemcpyDeviceToHost, lp.s)) ||
