@@ -25,6 +25,14 @@ int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo, const uint
                           const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
                           void* stream);
 
+/* The same product with A given MN-major, A_*[K][M] (M contiguous), loaded as two 64-wide
+ * M boxes per 64-deep K step and read through MN-major shared-memory descriptors (leading
+ * byte offset = the distance between the 64-wide M chunks, stride byte offset = the
+ * distance between groups of 8 K rows, 128-byte swizzle).  M must be a multiple of 64. */
+int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_lo, const uint16_t* B_hi,
+                             const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
+                             void* stream);
+
 /* Synchronises `stream` and returns (then clears) the status word of the test hooks. */
 int donof_testing_status(void* stream);
 

@@ -115,6 +115,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int swz) {
   d |= (uint64_t)(swz == 128 ? 2 : 4) << 61;       // swizzle mode
   return d;
 }
+// Shared-memory descriptor of an MN-major operand with the 128-byte swizzle: K rows of 64
+// MN elements (128 B each), the 64-wide MN chunks `chunk` bytes apart, groups of 8 K rows
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 // Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -205,6 +217,7 @@ struct TcArgs {
   const __half* a_tiled_h;
   const __half* a_tiled_f;
   long long a_kb_stride;
+  int a_mn;  // 1: A operand MN-major (BK = 64): its map is [K][M], two 64-wide M boxes
   // mode 1 outputs, X[row][c] with row = P * Nmu + mu (mu < Nrow valid): integer +
   // fraction X[P][mu][c] for the G contraction (exponent eX3[spOf[P]][mu], common to the
   // slices of one G split) and X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X; the row
@@ -311,6 +324,12 @@ __global__ void __launch_bounds__(256, 1)
             const size_t off = (size_t)kt * args.a_kb_stride + (size_t)r0 * 64;
             bulk_load_once(base, args.a_tiled_h + off, abytes, fb);
             bulk_load_once(base + a_bytes, args.a_tiled_f + off, abytes, fb);
+          } else if (BK == 64 && args.a_mn) {
+            mbar_expect_tx(fb, stage_bytes);
+            tma_load_3d(base, &mAh, fb, mt * BM, kt * BK, az);
+            tma_load_3d(base + a_bytes / 2, &mAh, fb, mt * BM + 64, kt * BK, az);
+            tma_load_3d(base + a_bytes, &mAl, fb, mt * BM, kt * BK, az);
+            tma_load_3d(base + a_bytes + a_bytes / 2, &mAl, fb, mt * BM + 64, kt * BK, az);
           } else {
             mbar_expect_tx(fb, stage_bytes);
             tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
@@ -324,7 +343,10 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    const uint32_t idesc = idesc_f16(BM, args.Nn);
+    const uint32_t idesc = idesc_f16(BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
+    // MN-major A (BK = 64): the two 64-wide M chunks 8 KB apart (leading byte offset),
+    // 8-row K groups 1 KB apart (stride byte offset)
+    const uint32_t mn_lbo = 8192u, mn_sbo = 1024u;
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -347,8 +369,10 @@ __global__ void __launch_bounds__(256, 1)
         const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ah = sdesc(base + k * 32, SWZ);
-          const uint64_t al = sdesc(base + a_bytes + k * 32, SWZ);
+          const uint64_t ah = args.a_mn ? sdesc_mn(base + k * 2048, mn_lbo, mn_sbo)
+                                        : sdesc(base + k * 32, SWZ);
+          const uint64_t al = args.a_mn ? sdesc_mn(base + a_bytes + k * 2048, mn_lbo, mn_sbo)
+                                        : sdesc(base + a_bytes + k * 32, SWZ);
           const uint64_t bh = sdesc(base + 2 * a_bytes + k * 32, SWZ);
           const uint64_t bl = sdesc(base + 2 * a_bytes + b_bytes + k * 32, SWZ);
           const uint32_t first = (it > 0 || k > 0) ? 1u : 0u;
@@ -1264,6 +1288,37 @@ extern "C" int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo,
   a.mode = 2; a.M = M; a.Nn = N;
   a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
   a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.out = D; a.out_ld = N; a.out_zstride = 0;
+  a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
+  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  return DONOF_OK;
+}
+
+extern "C" int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_lo,
+                                        const uint16_t* B_hi, const uint16_t* B_lo, float* D,
+                                        int32_t M, int32_t N, int32_t K, void* stream) {
+  using namespace donof;
+  if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
+  if (M < 1 || M % 64 != 0 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
+    return DONOF_ERR_INVALID_ARG;
+  int* words = nullptr;
+  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
+  CUtensorMap ah, al, bh, bl;
+  const uint64_t h2 = 2;
+  // A as [K][M]: x = M (contiguous), y = K; box 64 x 64
+  if (!make_map(&ah, A_hi, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64) ||
+      !make_map(&al, A_lo, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64) ||
+      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
+      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
+    return DONOF_ERR_CUDA;
+  TcArgs a{};
+  a.mode = 2; a.M = M; a.Nn = N;
+  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
+  a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.a_mn = 1;
   a.out = D; a.out_ld = N; a.out_zstride = 0;
   a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
   if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)

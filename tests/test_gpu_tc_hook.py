@@ -1,0 +1,55 @@
+"""The tensor-core building block alone (include/donof_testing.h): with integer-valued fp16
+operands (and a low part of multiples of 1/64) every product and partial sum is exact in
+fp32, so the result must equal the double-precision product exactly, for A given K-major
+and MN-major, ragged K (zero fill past the end) and one or several M tiles."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2004_06142_gb300.build as b
+    b.build()
+    import paper_2004_06142_gb300.binding as bd
+    L = bd.lib()
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    L.donof_testing_tc_gemm.argtypes = [vp] * 5 + [i32] * 3 + [vp]
+    L.donof_testing_tc_gemm_mn.argtypes = [vp] * 5 + [i32] * 3 + [vp]
+    L.donof_testing_status.argtypes = [vp]
+    return L
+
+
+def _half_dev(a):
+    import torch
+    bits = np.ascontiguousarray(a.astype(np.float16)).view(np.int16)
+    return torch.from_numpy(bits.copy()).cuda()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 160, 128), (256, 160, 200), (64, 32, 64),
+                                   (192, 48, 72)])
+@pytest.mark.parametrize("mn_major", [False, True])
+def test_split_product_exact(lib, M, N, K, mn_major):
+    import torch
+    rng = np.random.default_rng(M + N + K)
+    Ah = rng.integers(-8, 9, (M, K)).astype(np.float64)
+    Al = rng.integers(-8, 9, (M, K)) / 64.0
+    Bh = rng.integers(-8, 9, (N, K)).astype(np.float64)
+    Bl = rng.integers(-8, 9, (N, K)) / 64.0
+    ref = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    a_h, a_l = (Ah.T, Al.T) if mn_major else (Ah, Al)
+    dah, dal, dbh, dbl = _half_dev(a_h), _half_dev(a_l), _half_dev(Bh), _half_dev(Bl)
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    fn = lib.donof_testing_tc_gemm_mn if mn_major else lib.donof_testing_tc_gemm
+    rc = fn(dah.data_ptr(), dal.data_ptr(), dbh.data_ptr(), dbl.data_ptr(), D.data_ptr(), M, N,
+            K, s)
+    assert rc == 0
+    assert lib.donof_testing_status(s) == 0
+    np.testing.assert_array_equal(D.cpu().numpy().astype(np.float64), ref)
