@@ -33,6 +33,13 @@ int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_lo, const u
                              const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
                              void* stream);
 
+/* The same product with A interleaved by 8 along K, A_*[K/8][M][8] (element (m, k) at
+ * ((k / 8) * M + m) * 8 + k % 8), loaded without swizzle as 8-row x 16-byte core matrices.
+ * K and M must be multiples of 8. */
+int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A_lo, const uint16_t* B_hi,
+                              const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
+                              void* stream);
+
 /* Synchronises `stream` and returns (then clears) the status word of the test hooks. */
 int donof_testing_status(void* stream);
 

@@ -34,7 +34,7 @@ Dims make_dims(const donof_problem* p) {
     perP = (size_t)d.N * d.A * 8 + 2 * (size_t)d.A * d.A * 8 +
            (d.layout == DONOF_B_PACKED ? (size_t)d.N * d.N * 8 : 0);
   } else {
-    perP = (size_t)d.N * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
+    perP = (size_t)d.Np * d.Ap * 4 + (size_t)d.Ap * d.Np * 4 + (size_t)d.Ap * d.Ap * (4 + 4 + 4) +
            (size_t)d.Ap * 4 + (size_t)d.A * 8;
   }
   long long pb = d.Q;
@@ -88,17 +88,24 @@ Layout make_layout(const Dims& d) {
     L.Bun = d.layout == DONOF_B_PACKED ? take(pb * N * N * 8) : 0;
   } else {
     const size_t Q = d.Q;
-    // pre-tiled split B: [ceil(N / 64)][Q * Np rows][64] per plane
-    L.Bhi = take((N + 63) / 64 * Q * Np * 64 * 2);
-    L.Blo = take((N + 63) / 64 * Q * Np * 64 * 2);
+    // split B in symmetric lower-triangle tiles, per plane Q x SymTiles::perP halves
+    const size_t perP = (size_t)sym_tiles((int)N).perP;
+    L.Bhi = take(Q * perP * 2);
+    L.Blo = take(Q * perP * 2);
+    L.eS = take(N * 4);
+    L.rnmax = take(N * 8);
+    L.tmax = take(Q * 8);
+    L.ChiS = take(Ap * Np * 2);
+    L.CloS = take(Ap * Np * 2);
+    L.eCs = take(Ap * 4);
     L.eB = take(Q * N * 4);
     L.L1max = take(Q * 8);
     L.Chi = take(Ap * Np * 2);
     L.Clo = take(Ap * Np * 2);
     L.eC = take(Ap * 4);
     L.cnorm = take(Ap * 8);
-    L.Xhi = take(pb * N * Ap * 2);
-    L.Xlo = take(pb * N * Ap * 2);
+    L.Xhi = take(pb * Np * Ap * 2);  // [P][Ap/8][Np][8]
+    L.Xlo = take(pb * Np * Ap * 2);
     L.Xthi = take(pb * Ap * Np * 2);
     L.Xtlo = take(pb * Ap * Np * 2);
     L.eXt = take(pb * Ap * 4);

@@ -52,10 +52,35 @@ struct Layout {
   // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
   size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo,
       Gpart, D, rn2, spOf, eX3, ssqY, eY, CfH, CfF, eCf, GtH, GtF, eG;
+  // symmetric storage of the split B: per-AO scale exponents s, their source (max over P of
+  // the row norms), per-slice maxima of the scaled row norms, and the split of
+  // (diag 2^s C_act)^T that multiplies it
+  size_t eS, rnmax, tmax, ChiS, CloS, eCs;
   size_t total;
 };
 
 Dims make_dims(const donof_problem* p);
+
+// Lower-triangle tile storage of the split B for the half transform: row tiles of 128 AO
+// indices (T of them), the last one stored with its rows rounded up to a multiple of 64;
+// tile (i, j), j <= i, holds rows of tile i and columns of tile j as chunks of 64 columns,
+// each chunk [R_i rows][64] with the 16-byte pieces of row r at piece ^ (r % 8).
+struct SymTiles {
+  int T, Rlast;
+  long long perP;  // elements per slice and plane
+};
+__host__ __device__ inline int sym_R(const SymTiles& t, int i) { return i < t.T - 1 ? 128 : t.Rlast; }
+__host__ __device__ inline long long sym_tile_off(const SymTiles& t, int i, int j) {
+  return 16384LL * i * (i + 1) / 2 + (long long)sym_R(t, i) * 128 * j;
+}
+__host__ __device__ inline SymTiles sym_tiles(int N) {
+  SymTiles t;
+  t.T = (N + 127) / 128;
+  const int last = N - 128 * (t.T - 1);
+  t.Rlast = (last + 63) / 64 * 64;
+  t.perP = sym_tile_off(t, t.T - 1, 0) + (long long)t.Rlast * (128LL * (t.T - 1) + t.Rlast);
+  return t;
+}
 
 // Tracing (api.cu): no-ops unless donof_profile_enable(1) was called.
 void prof_begin(int phase, cudaStream_t s);

@@ -86,6 +86,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
 // Plain (untiled) bulk copy global -> shared, completion counted on an mbarrier; the
 // source is read once, so it is marked evict-first in L2.
 __device__ __forceinline__ void bulk_load_once(uint32_t dst, const void* src, uint32_t bytes,
@@ -126,6 +134,17 @@ __device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo, uint3
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
   return d;
+}
+// Shared-memory descriptor of a K-major operand without swizzle, stored as core matrices of
+// 8 rows x 16 bytes: rows 16 bytes apart, 8-row groups `sbo` bytes apart, K-adjacent core
+// matrices `lbo` bytes apart.
+__device__ __forceinline__ uint64_t sdesc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;  // layout type 0: no swizzle
 }
 // Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
@@ -218,10 +237,21 @@ struct TcArgs {
   const __half* a_tiled_f;
   long long a_kb_stride;
   int a_mn;  // 1: A operand MN-major (BK = 64): its map is [K][M], two 64-wide M boxes
+  // 1: A operand interleaved by 8 along K, [z][K/8][rows][8], loaded without swizzle as
+  // core matrices (4-D map of 8-row groups, coordinates {0, row/8, k/8, z})
+  int a_il8;
+  // symmetric half transform (BK = 64): A from the lower-triangle tile storage of the split
+  // B at a_tiled_h/f + z * st.perP; unit = (slice z, row tile mt); its K steps visit the tile
+  // columns in a round-robin order in which row tiles i and j of a slice read their shared
+  // stored tile (i, j) in the same round (K-major for the larger index, MN-major transposed
+  // for the smaller); output row mt * 128 + r is AO index mu of slice z
+  int sym;
+  SymTiles st;
+  int grid;  // CTAs to launch (0: one per SM, at most one per unit)
   // mode 1 outputs, X[row][c] with row = P * Nmu + mu (mu < Nrow valid): integer +
-  // fraction X[P][mu][c] for the G contraction (exponent eX3[spOf[P]][mu], common to the
-  // slices of one G split) and X^T[P][c][mu] (exponent eXt[P][c]) for b = C^T X; the row
-  // exponents eA are indexed by P * Nrow + mu
+  // fraction X for the G contraction, interleaved by 8 along c as [P][c/8][mu < Np][8]
+  // (exponent eX3[spOf[P]][mu], common to the slices of one G split) and X^T[P][c][mu]
+  // (exponent eXt[P][c]) for b = C^T X; the row exponents eA are indexed by P * Nrow + mu
   int Nmu, Nrow, Ap, Np;
   __half *xhi, *xlo, *xth, *xtf;
   const int* eXt;
@@ -237,6 +267,20 @@ struct TcArgs {
   int* status;
   int* abort_flag;
 };
+
+// Round-robin (circle method) schedule over the T row tiles of a slice: in round r row
+// tile i works on tile column rr_partner(i, r, T), an involution, so both row tiles that
+// share a stored tile read it in the same round; every tile column once in T rounds (the
+// diagonal tile in the round with no partner).
+__device__ __forceinline__ int rr_partner(int i, int r, int T) {
+  if ((T & 1) == 0 && r == T - 1) return i;  // even T: the round of the diagonal tiles
+  const int n = T + (T & 1);                 // participants (a dummy when T is odd)
+  int p;
+  if (i == n - 1) p = r;
+  else if (i == r) p = n - 1;
+  else p = ((2 * r - i) % (n - 1) + (n - 1)) % (n - 1);
+  return p >= T ? i : p;
+}
 
 __device__ __forceinline__ float pow2f(int e) {
   e = e < -126 ? -126 : (e > 127 ? 127 : e);
@@ -306,6 +350,44 @@ __global__ void __launch_bounds__(256, 1)
     for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
       int z, mt, sp;
       decode(u, z, mt, sp);
+      if (BK == 64 && args.sym) {
+        const SymTiles st = args.st;
+        const int i = mt, Ri = sym_R(st, i);
+        const size_t zoff = (size_t)z * st.perP;
+        for (int r = 0; r < st.T && ok; ++r) {
+          const int j = rr_partner(i, r, st.T);
+          const int nch = j < st.T - 1 ? 2 : st.Rlast / 64;
+          for (int c = 0; c < nch; ++c) {
+            if (!mbar_wait(smem_u32(&bars[S + stage]), phase ^ 1u, status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&bars[stage]);
+            const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
+            if (j <= i) {  // stored tile (i, j), chunk c: Ri rows of 128 bytes, K-major
+              const uint32_t ab = (uint32_t)Ri * 128u;
+              mbar_expect_tx(fb, 2 * ab + 2 * b_bytes);
+              const size_t off = zoff + sym_tile_off(st, i, j) + (size_t)c * Ri * 64;
+              bulk_load_once(base, args.a_tiled_h + off, ab, fb);
+              bulk_load_once(base + a_bytes, args.a_tiled_f + off, ab, fb);
+            } else {  // stored tile (j, i), rows 64c..64c+63 of both its chunks: MN-major
+              const int Rj = sym_R(st, j);
+              mbar_expect_tx(fb, 2 * a_bytes + 2 * b_bytes);
+#pragma unroll
+              for (int m = 0; m < 2; ++m) {
+                const size_t off =
+                    zoff + sym_tile_off(st, j, i) + ((size_t)m * Rj + 64 * c) * 64;
+                bulk_load_once(base + m * 8192, args.a_tiled_h + off, 8192, fb);
+                bulk_load_once(base + a_bytes + m * 8192, args.a_tiled_f + off, 8192, fb);
+              }
+            }
+            tma_load_3d(base + 2 * a_bytes, &mBh, fb, 128 * j + 64 * c, 0, 0);
+            tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, 128 * j + 64 * c, 0, 0);
+            if (++stage == S) { stage = 0; phase ^= 1u; }
+          }
+        }
+        continue;
+      }
       const int kb0 = (int)((long long)args.nkb * sp / args.splits);
       const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
       for (int kb = kb0; kb < kb1 && ok; ++kb) {
@@ -324,6 +406,10 @@ __global__ void __launch_bounds__(256, 1)
             const size_t off = (size_t)kt * args.a_kb_stride + (size_t)r0 * 64;
             bulk_load_once(base, args.a_tiled_h + off, abytes, fb);
             bulk_load_once(base + a_bytes, args.a_tiled_f + off, abytes, fb);
+          } else if (args.a_il8) {
+            mbar_expect_tx(fb, stage_bytes);
+            tma_load_4d(base, &mAh, fb, 0, mt * BM / 8, kt * BK / 8, az);
+            tma_load_4d(base + a_bytes, &mAl, fb, 0, mt * BM / 8, kt * BK / 8, az);
           } else if (BK == 64 && args.a_mn) {
             mbar_expect_tx(fb, stage_bytes);
             tma_load_3d(base, &mAh, fb, mt * BM, kt * BK, az);
@@ -362,33 +448,58 @@ __global__ void __launch_bounds__(256, 1)
       const uint32_t d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
       const int kb0 = (int)((long long)args.nkb * sp / args.splits);
       const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
-      const int iters = (kb1 - kb0) * args.kt_per_kb;
+      // symmetric mode: the K steps in the producer's order, K-major or transposed
+      const bool sym = BK == 64 && args.sym;
+      const int T = args.st.T;
+      int iters = (kb1 - kb0) * args.kt_per_kb;
+      int rr = 0, cc = 0, jj = 0, nch = 0;
+      if (sym) {
+        iters = 2 * (T - 1) + args.st.Rlast / 64;
+        jj = rr_partner(mt, 0, T);
+        nch = jj < T - 1 ? 2 : args.st.Rlast / 64;
+      }
       for (int it = 0; it < iters; ++it) {
         if (!mbar_wait(smem_u32(&bars[stage]), phase, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
+        const bool tr = args.a_mn || (sym && jj > mt);
+        const uint32_t id = tr ? (idesc | (1u << 15)) : idesc;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ah = args.a_mn ? sdesc_mn(base + k * 2048, mn_lbo, mn_sbo)
-                                        : sdesc(base + k * 32, SWZ);
-          const uint64_t al = args.a_mn ? sdesc_mn(base + a_bytes + k * 2048, mn_lbo, mn_sbo)
-                                        : sdesc(base + a_bytes + k * 32, SWZ);
+          uint64_t ah, al;
+          if (args.a_il8) {  // two K-adjacent core-matrix columns (BM rows x 16 B) per step
+            ah = sdesc_plain(base + k * 2 * BM * 16, BM * 16, 128);
+            al = sdesc_plain(base + a_bytes + k * 2 * BM * 16, BM * 16, 128);
+          } else if (tr) {
+            ah = sdesc_mn(base + k * 2048, mn_lbo, mn_sbo);
+            al = sdesc_mn(base + a_bytes + k * 2048, mn_lbo, mn_sbo);
+          } else {
+            ah = sdesc(base + k * 32, SWZ);
+            al = sdesc(base + a_bytes + k * 32, SWZ);
+          }
           const uint64_t bh = sdesc(base + 2 * a_bytes + k * 32, SWZ);
           const uint64_t bl = sdesc(base + 2 * a_bytes + b_bytes + k * 32, SWZ);
           const uint32_t first = (it > 0 || k > 0) ? 1u : 0u;
           if (NUM == kSplit3) {
-            mma_f16(d0, ah, bh, idesc, first);
-            mma_f16(d0, ah, bl, idesc, 1u);
-            mma_f16(d0, al, bh, idesc, 1u);
+            mma_f16(d0, ah, bh, id, first);
+            mma_f16(d0, ah, bl, id, 1u);
+            mma_f16(d0, al, bh, id, 1u);
           } else {
-            mma_f16(d0, ah, bh, idesc, first);  // integer x integer: exact
-            mma_f16(d1, ah, bl, idesc, first);
-            mma_f16(d1, al, bh, idesc, 1u);
-            mma_f16(d1, al, bl, idesc, 1u);
+            mma_f16(d0, ah, bh, id, first);  // integer x integer: exact
+            mma_f16(d1, ah, bl, id, first);
+            mma_f16(d1, al, bh, id, 1u);
+            mma_f16(d1, al, bl, id, 1u);
           }
         }
         mma_commit(smem_u32(&bars[S + stage]));
         if (++stage == S) { stage = 0; phase ^= 1u; }
+        if (sym && ++cc == nch) {
+          cc = 0;
+          if (++rr < T) {
+            jj = rr_partner(mt, rr, T);
+            nch = jj < T - 1 ? 2 : args.st.Rlast / 64;
+          }
+        }
       }
       if (!ok) break;
       mma_commit(smem_u32(&bars[2 * S + acc]));
@@ -412,12 +523,16 @@ __global__ void __launch_bounds__(256, 1)
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
       bool valid = row < args.M;
-      if (args.mode == 1) {
+      if (args.sym) {
+        rP = z;
+        rmu = row;
+        valid = row < args.Nrow;
+      } else if (args.mode == 1) {
         rP = row / args.Nmu;
         rmu = row % args.Nmu;
         valid = valid && rmu < args.Nrow;
       }
-      const int erow_i = args.mode == 1 ? rP * args.Nrow + rmu : row;
+      const int erow_i = (args.mode == 1 || args.sym) ? rP * args.Nrow + rmu : row;
       const uint32_t t0 =
           tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
       const uint32_t t1 = t0 + (uint32_t)args.Nn;
@@ -460,11 +575,14 @@ __global__ void __launch_bounds__(256, 1)
             hi[j] = __float2half_rn(h);
             lo[j] = __float2half_rn(w - h);
           }
-          const size_t o = ((size_t)rP * args.Nrow + rmu) * args.Ap + c0;
-          uint4* dh = (uint4*)(args.xhi + o);
-          uint4* dl = (uint4*)(args.xlo + o);
-          dh[0] = ((uint4*)hi)[0]; dh[1] = ((uint4*)hi)[1];
-          dl[0] = ((uint4*)lo)[0]; dl[1] = ((uint4*)lo)[1];
+          // X interleaved by 8 along c, [P][c/8][mu][8]: the lanes (consecutive mu) of one
+          // store write 512 contiguous bytes
+          const size_t o0 = (((size_t)rP * (args.Ap / 8) + c0 / 8) * args.Np + rmu) * 8;
+          const size_t o1 = o0 + (size_t)args.Np * 8;
+          *(uint4*)(args.xhi + o0) = ((uint4*)hi)[0];
+          *(uint4*)(args.xhi + o1) = ((uint4*)hi)[1];
+          *(uint4*)(args.xlo + o0) = ((uint4*)lo)[0];
+          *(uint4*)(args.xlo + o1) = ((uint4*)lo)[1];
         } else if (args.mode == 3) {
           double* o = args.out64 + (long long)row * args.out64_ld + c0;
 #pragma unroll
@@ -624,6 +742,25 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t dx, uint64_t dy, uint64
   return r == CUDA_SUCCESS;
 }
 
+// 4-D fp16 map of an operand interleaved by 8 along K: [nz][K/8][rows][8] (K and rows
+// multiples of 8), viewed with 8-row groups as its innermost 64-element (128-byte) rows so
+// that TMA moves whole 128-byte lines: dims {64, rows/8, K/8, nz}, box {64, box_rows/8,
+// bk/8, 1}, no swizzle; in shared memory the same [K/8][rows][8] order (core matrices of 8
+// rows x 16 bytes).
+bool make_map_il8(CUtensorMap* m, const void* base, uint64_t K, uint64_t rows, uint64_t nz,
+                  uint32_t bk, uint32_t box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc || K % 8 != 0 || rows % 8 != 0) return false;
+  cuuint64_t dims[4] = {64, rows / 8, K / 8, nz};
+  cuuint64_t strides[3] = {128, rows * 16, (K / 8) * rows * 16};
+  cuuint32_t box[4] = {64, box_rows / 8, bk / 8, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -657,7 +794,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int units = a.z_count * a.m_tiles * a.splits;
-  int grid = num_sms();
+  int grid = a.grid > 0 ? a.grid : num_sms();
   if (grid > units) grid = units;
   k_tc_gemm<BK, NUM><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
   count_launch(1);
@@ -695,7 +832,8 @@ __device__ inline double load_B_elem(const double* __restrict__ B, int layout, l
 // Per row (P, mu): norm -> exponent of its integer + fraction split; global max |B| and
 // max row norm (the latter bounds |X| for the hi/lo split of the G contraction).
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
-                          DevHeader* hdr, int* eB, unsigned long long* L1max_bits, double* rn2) {
+                          DevHeader* hdr, unsigned long long* L1max_bits, double* rn2,
+                          unsigned long long* rnmax_bits) {
   const long long rows = Q * N;
   const int lane = threadIdx.x % 32;
   const long long npk = (long long)N * (N + 1) / 2;
@@ -718,9 +856,9 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
     }
     const double nr = sqrt(ss);
     if (lane == 0) {
-      eB[row] = intfrac_exponent(nr);
       rn2[row] = ss;
       atomic_max_nonneg(L1max_bits + P, l1);
+      atomic_max_nonneg(rnmax_bits + mu, nr);
     }
     mx = fmax(mx, m);
     mr = fmax(mr, nr);
@@ -732,42 +870,101 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
   }
 }
 
-// B (double, dense or packed) -> integer + fraction planes in the pre-tiled layout of the
-// half transform: [KB][Q * Np rows][64] (KB = ceil(N / 64) k blocks of 64 columns, the
-// rows of slice P at P * Np .. P * Np + N - 1, padding rows and columns >= N zero), the
-// 16-byte chunk j of row R stored at chunk j ^ (R % 8): the 128-byte swizzle of a shared
-// memory tile that starts on a row multiple of 8.  One thread per chunk of 8 elements.
-__global__ void k_split_B(const double* __restrict__ B, int layout, long long Q, int N, int Np,
-                          int KB, DevHeader* hdr, const int* __restrict__ eB, __half* H,
-                          __half* F) {
+// Symmetric scaling of B: B^P_{mu nu} = 2^(t_P + s_mu + s_nu) Bt^P_{mu nu} keeps Bt^P
+// symmetric, so one stored triangle serves both operand orders of the half transform.
+// s equilibrates the AO indices: with a_mu = max_P ||B^P_{mu .}||_2, a rank-one-like
+// |B_{mu nu}| ~ d_mu d_nu has a_mu = d_mu ||d||, ||d||^4 = sum_mu a_mu^2, so
+// 2^s_mu = d_mu rounded to a power of two.  One CTA.
+__global__ void __launch_bounds__(1024) k_sym_scale(const double* __restrict__ rnmax, int N,
+                                                    int* eS) {
+  __shared__ double red[32];
+  double ss = 0.0;
+  for (int mu = threadIdx.x; mu < N; mu += blockDim.x) ss += rnmax[mu] * rnmax[mu];
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    red[0] = t;
+  }
+  __syncthreads();
+  const double norm_d = sqrt(sqrt(red[0]));
+  for (int mu = threadIdx.x; mu < N; mu += blockDim.x) {
+    const double dmu = rnmax[mu] / norm_d;
+    eS[mu] = (dmu > 0.0 && norm_d > 0.0) ? (int)rint(log2(dmu)) : 0;
+  }
+}
+
+// Per slice: the largest row norm of Bt^P without t_P (one warp per row).
+__global__ void k_p_scale(const double* __restrict__ B, int layout, long long Q, int N,
+                          const int* __restrict__ eS, unsigned long long* tmax_bits) {
+  const long long rows = Q * N;
+  const int lane = threadIdx.x % 32;
+  const long long npk = (long long)N * (N + 1) / 2;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; row < rows;
+       row += (long long)gridDim.x * blockDim.x / 32) {
+    const long long P = row / N;
+    const int mu = (int)(row % N);
+    double ss = 0.0;
+    for (int nu = lane; nu < N; nu += 32) {
+      const double v = ldexp(load_B_elem(B, layout, P, row, mu, nu, N, npk), -eS[mu] - eS[nu]);
+      ss = fma(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) atomic_max_nonneg(tmax_bits + P, sqrt(ss));
+  }
+}
+
+// eA[P][mu] = t_P + s_mu: the exponent of output row (P, mu) of the half transform.
+__global__ void k_sym_exps(const double* __restrict__ tmax, const int* __restrict__ eS,
+                           long long Q, int N, int* eA) {
+  const long long tot = Q * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x)
+    eA[i] = intfrac_exponent(tmax[i / N]) + eS[i % N];
+}
+
+// Bt^P 2^-t_P -> integer + fraction planes in the lower-triangle tile storage (SymTiles).
+// One thread per 8 consecutive stored elements: slice P, stored row mu (rows of the last
+// tile padded to Rlast), 64-wide k block kb of a tile column not right of mu's tile.
+__global__ void k_split_B_sym(const double* __restrict__ B, int layout, long long Q, int N,
+                              SymTiles st, DevHeader* hdr, const int* __restrict__ eS,
+                              const double* __restrict__ tmax, __half* H, __half* F) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hdr->maxB = __longlong_as_double((long long)hdr->maxB_bits);
     hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
   }
   const long long npk = (long long)N * (N + 1) / 2;
-  const long long rows = Q * Np;
-  const long long tot = (long long)KB * rows * 8;
+  const int rows = 128 * (st.T - 1) + st.Rlast;  // stored rows (= columns) per slice
+  const int KB = rows / 64;
+  const long long tot = Q * rows * KB * 8;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(i % 8);
-    const long long t = i / 8;
-    const long long R = t % rows;
-    const int kb = (int)(t / rows);
-    const long long P = R / Np;
-    const int mu = (int)(R % Np);
+    const int j8 = (int)(i % 8);
+    long long t = i / 8;
+    const int kb = (int)(t % KB);
+    t /= KB;
+    const int mu = (int)(t % rows);
+    const long long P = t / rows;
+    const int ti = mu / 128, tj = kb / 2;
+    if (tj > ti) continue;  // upper triangle: not stored
+    const int r = mu - 128 * ti, c = kb - 2 * tj;
+    const int Ri = sym_R(st, ti);
+    const int tP = intfrac_exponent(tmax[P]);
     __align__(16) __half hv[8], fv[8];
-    const long long r = P * N + mu;
-    const int e = mu < N ? eB[r] : 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int nu = kb * 64 + j * 8 + k;
-      const double v = (mu < N && nu < N) ? load_B_elem(B, layout, P, r, mu, nu, N, npk) : 0.0;
-      const double y = ldexp(v, -e);
+      const int nu = kb * 64 + j8 * 8 + k;
+      double y = 0.0;
+      if (mu < N && nu < N)
+        y = ldexp(load_B_elem(B, layout, P, P * N + mu, mu, nu, N, npk), -tP - eS[mu] - eS[nu]);
       const double h = rint(y);
       hv[k] = __double2half(h);
       fv[k] = __double2half(y - h);
     }
-    const size_t o = ((size_t)kb * rows + R) * 64 + (size_t)((j ^ (int)(R & 7)) * 8);
+    const size_t o = (size_t)P * st.perP + sym_tile_off(st, ti, tj) +
+                     ((size_t)c * Ri + r) * 64 + (size_t)((j8 ^ (r & 7)) * 8);
     *(uint4*)(H + o) = *(const uint4*)hv;
     *(uint4*)(F + o) = *(const uint4*)fv;
   }
@@ -775,15 +972,18 @@ __global__ void k_split_B(const double* __restrict__ B, int layout, long long Q,
 
 // Column norms of C_act -> exponents of the integer + fraction split of C_act^T (one warp
 // per column); max column norm for the bound on |X|.
-__global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, int* eC,
-                          double* cnorm, DevHeader* hdr) {
+// With eS given, the columns of diag(2^s) C_act instead (the operand of the symmetric half
+// transform); cnorm and the header maximum are then not written.
+__global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap,
+                          const int* __restrict__ eS, int* eC, double* cnorm, DevHeader* hdr) {
   const int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (q >= Ap) return;
   double ss = 0.0;
   if (q < A)
     for (int mu = lane; mu < N; mu += 32) {
-      const double v = C[(size_t)mu * N + q];
+      double v = C[(size_t)mu * N + q];
+      if (eS) v = ldexp(v, eS[mu]);
       ss = fma(v, v, ss);
     }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -791,8 +991,11 @@ __global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap, in
     const double nr = sqrt(ss);
     if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
     eC[q] = intfrac_exponent(nr);
-    cnorm[q] = nr;
-    atomicMax((unsigned long long*)&hdr->maxCcol_bits, (unsigned long long)__double_as_longlong(nr));
+    if (!eS) {
+      cnorm[q] = nr;
+      atomicMax((unsigned long long*)&hdr->maxCcol_bits,
+                (unsigned long long)__double_as_longlong(nr));
+    }
   }
 }
 
@@ -837,13 +1040,14 @@ __global__ void k_c_finish(DevHeader* hdr) {
 
 // C_act^T -> integer + fraction planes [Ap][Np] (rows q >= A and columns mu >= N zero).
 __global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, int Np,
-                          const int* __restrict__ eC, __half* H, __half* F) {
+                          const int* __restrict__ eS, const int* __restrict__ eC, __half* H,
+                          __half* F) {
   const long long tot = (long long)Ap * Np;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     const int p = (int)(i / Np), mu = (int)(i % Np);
     const double v = (p < A && mu < N) ? C[(size_t)mu * N + p] : 0.0;
-    const double y = ldexp(v, -eC[p]);
+    const double y = ldexp(v, (eS && mu < N ? eS[mu] : 0) - eC[p]);
     const double h = rint(y);
     H[i] = __double2half(h);
     F[i] = __double2half(y - h);
@@ -1002,13 +1206,25 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(ws + L.L1max, 0, (size_t)d.Q * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr, (int*)(ws + L.eB),
+  e = cudaMemsetAsync(ws + L.rnmax, 0, (size_t)d.N * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ws + L.tmax, 0, (size_t)d.Q * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr,
                                           (unsigned long long*)(ws + L.L1max),
-                                          (double*)(ws + L.rn2));
-  k_split_B<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, d.Np, (d.N + 63) / 64, hdr,
-                                          (const int*)(ws + L.eB), (__half*)(ws + L.Bhi),
-                                          (__half*)(ws + L.Blo));
-  count_launch(2);
+                                          (double*)(ws + L.rn2),
+                                          (unsigned long long*)(ws + L.rnmax));
+  k_sym_scale<<<1, 1024, 0, s>>>((const double*)(ws + L.rnmax), d.N, (int*)(ws + L.eS));
+  k_p_scale<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, (const int*)(ws + L.eS),
+                                          (unsigned long long*)(ws + L.tmax));
+  k_sym_exps<<<num_sms() * 4, 256, 0, s>>>((const double*)(ws + L.tmax),
+                                           (const int*)(ws + L.eS), d.Q, d.N,
+                                           (int*)(ws + L.eB));
+  k_split_B_sym<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, sym_tiles(d.N), hdr,
+                                              (const int*)(ws + L.eS),
+                                              (const double*)(ws + L.tmax),
+                                              (__half*)(ws + L.Bhi), (__half*)(ws + L.Blo));
+  count_launch(5);
   return cudaGetLastError();
 }
 
@@ -1017,12 +1233,18 @@ cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layou
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->maxCcol_bits, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, (int*)(ws + L.eC),
+  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
                                            (double*)(ws + L.cnorm), hdr);
   k_c_finish<<<1, 1, 0, s>>>(hdr);
-  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, (const int*)(ws + L.eC),
+  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, nullptr, (const int*)(ws + L.eC),
                                       (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
-  count_launch(3);
+  // diag(2^s) C_act for the symmetric half transform
+  const int* eS = (const int*)(ws + L.eS);
+  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, eS, (int*)(ws + L.eCs), nullptr,
+                                           hdr);
+  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, eS, (const int*)(ws + L.eCs),
+                                      (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS));
+  count_launch(5);
   return cudaGetLastError();
 }
 
@@ -1102,27 +1324,28 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   count_launch(2);
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
-    // A operand: the pre-tiled split B (bulk copies, BK = 64); rows (P, mu) of the block
-    // flattened with pitch Np per slice
-    const int KB = (N + 63) / 64;
-    const uint64_t rows = (uint64_t)np * Np;
-    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * Np * 64;
-    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * Np * 64;
+    // A operand: the symmetric tile storage of the split B (bulk copies, BK = 64); B
+    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices)
+    const SymTiles st = sym_tiles(N);
+    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
+    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
     const int bk = 64;
-    if (!make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
-        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
+    if (!make_map(&bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
+        !make_map(&bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
       return DONOF_ERR_CUDA;
     ah = bh;  // unused: the A tiles come from the bulk copies
     al = bl;
     TcArgs a{};
-    a.mode = 1; a.M = (int)rows; a.Nn = Ap;
-    a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
-    a.kt_per_kb = KB; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-    a.a_tiled_h = Bh; a.a_tiled_f = Bl; a.a_kb_stride = (long long)d.Q * Np * 64;
+    a.mode = 1; a.M = st.T * BM; a.Nn = Ap;
+    a.m_tiles = st.T; a.z_count = np; a.splits = 1;
+    a.kt_per_kb = 1; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+    a.sym = 1; a.st = st;
+    a.grid = num_sms() >= st.T ? num_sms() / st.T * st.T : num_sms();  // whole slices at once
+    a.a_tiled_h = Bh; a.a_tiled_f = Bl;
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
-    a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
+    a.eB = (const int*)(ws + L.eCs); a.eB_zstride = 0;
     a.glob_exp = &hdr->sX;
-    a.Nmu = Np; a.Nrow = N; a.Ap = Ap; a.Np = Np;
+    a.Nmu = N; a.Nrow = N; a.Ap = Ap; a.Np = Np;
     a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
@@ -1174,8 +1397,8 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
     const int bk = tuned_bk(3, N, Ap, np);
-    if (!make_map(&ah, ws + L.Xhi, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, bk, BM) ||
-        !make_map(&al, ws + L.Xlo, Ap, N, np, Ap * h2, (uint64_t)N * Ap * h2, bk, BM) ||
+    if (!make_map_il8(&ah, ws + L.Xhi, Ap, Np, np, bk, BM) ||
+        !make_map_il8(&al, ws + L.Xlo, Ap, Np, np, bk, BM) ||
         !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap) ||
         !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap))
       return DONOF_ERR_CUDA;
@@ -1184,6 +1407,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
     a.splits = splits3;
     a.kt_per_kb = (Ap + bk - 1) / bk; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
+    a.a_il8 = 1;  // X interleaved by 8 along q
     a.eA = (const int*)(ws + L.eX3); a.eA_sstride = N;
     a.eB = (const int*)(ws + L.eY); a.eB_sstride = Ap;
     a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
@@ -1319,6 +1543,35 @@ extern "C" int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_
   a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
   a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
   a.a_mn = 1;
+  a.out = D; a.out_ld = N; a.out_zstride = 0;
+  a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
+  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  return DONOF_OK;
+}
+
+extern "C" int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A_lo,
+                                         const uint16_t* B_hi, const uint16_t* B_lo, float* D,
+                                         int32_t M, int32_t N, int32_t K, void* stream) {
+  using namespace donof;
+  if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
+  if (M < 1 || M % 8 != 0 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
+    return DONOF_ERR_INVALID_ARG;
+  int* words = nullptr;
+  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
+  CUtensorMap ah, al, bh, bl;
+  const uint64_t h2 = 2;
+  if (!make_map_il8(&ah, A_hi, K, M, 1, 64, BM) || !make_map_il8(&al, A_lo, K, M, 1, 64, BM) ||
+      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
+      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
+    return DONOF_ERR_CUDA;
+  TcArgs a{};
+  a.mode = 2; a.M = M; a.Nn = N;
+  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
+  a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.a_il8 = 1;
   a.out = D; a.out_ld = N; a.out_zstride = 0;
   a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
   if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)

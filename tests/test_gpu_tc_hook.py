@@ -1,7 +1,8 @@
 """The tensor-core building block alone (include/donof_testing.h): with integer-valued fp16
 operands (and a low part of multiples of 1/64) every product and partial sum is exact in
 fp32, so the result must equal the double-precision product exactly, for A given K-major
-and MN-major, ragged K (zero fill past the end) and one or several M tiles."""
+(128-byte swizzle), MN-major, and K-major interleaved by 8 (no swizzle, core matrices),
+ragged K (zero fill past the end) and one or several M tiles."""
 import ctypes
 
 import numpy as np
@@ -22,6 +23,7 @@ def lib():
     vp, i32 = ctypes.c_void_p, ctypes.c_int32
     L.donof_testing_tc_gemm.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_tc_gemm_mn.argtypes = [vp] * 5 + [i32] * 3 + [vp]
+    L.donof_testing_tc_gemm_il8.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_status.argtypes = [vp]
     return L
 
@@ -34,8 +36,8 @@ def _half_dev(a):
 
 @pytest.mark.parametrize("M,N,K", [(128, 160, 128), (256, 160, 200), (64, 32, 64),
                                    (192, 48, 72)])
-@pytest.mark.parametrize("mn_major", [False, True])
-def test_split_product_exact(lib, M, N, K, mn_major):
+@pytest.mark.parametrize("layout", ["k_major", "mn_major", "il8"])
+def test_split_product_exact(lib, M, N, K, layout):
     import torch
     rng = np.random.default_rng(M + N + K)
     Ah = rng.integers(-8, 9, (M, K)).astype(np.float64)
@@ -43,11 +45,17 @@ def test_split_product_exact(lib, M, N, K, mn_major):
     Bh = rng.integers(-8, 9, (N, K)).astype(np.float64)
     Bl = rng.integers(-8, 9, (N, K)) / 64.0
     ref = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
-    a_h, a_l = (Ah.T, Al.T) if mn_major else (Ah, Al)
+    if layout == "mn_major":
+        a_h, a_l = Ah.T, Al.T
+    elif layout == "il8":  # [K/8][M][8]
+        a_h, a_l = (x.reshape(M, K // 8, 8).transpose(1, 0, 2) for x in (Ah, Al))
+    else:
+        a_h, a_l = Ah, Al
     dah, dal, dbh, dbl = _half_dev(a_h), _half_dev(a_l), _half_dev(Bh), _half_dev(Bl)
     D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    fn = lib.donof_testing_tc_gemm_mn if mn_major else lib.donof_testing_tc_gemm
+    fn = {"k_major": lib.donof_testing_tc_gemm, "mn_major": lib.donof_testing_tc_gemm_mn,
+          "il8": lib.donof_testing_tc_gemm_il8}[layout]
     rc = fn(dah.data_ptr(), dal.data_ptr(), dbh.data_ptr(), dbl.data_ptr(), D.data_ptr(), M, N,
             K, s)
     assert rc == 0
