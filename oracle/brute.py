@@ -129,10 +129,12 @@ def apsg_wavefunction(members, sqrt_n) -> dict:
 # ----------------------------------------------------------------------------
 # Eq. ENOF with the reconstructed 2RDM of Eqs. intra, interaa, interab
 # ----------------------------------------------------------------------------
-def energy_from_2rdm(h_mo, eri_mo_, n, sqrt_n, phi, members, with_phi=True) -> float:
+def energy_from_2rdm(h_mo, eri_mo_, n, sqrt_n, phi, members, with_phi=True, singles=()) -> float:
     """E = sum_sigma sum_p n_p H_pp + sum over spin blocks of D_{pq,rt} <pq|rt>,
     <pq|rt> = (pr|qt).  D^{ab} enters twice (alpha-beta and beta-alpha), D^{ss}
-    once per spin.  All subspaces belong to Omega_II (no singles)."""
+    once per spin.  ``members`` lists the subspaces of Omega_II; ``singles`` the orbitals
+    of Omega_I, each its own subspace, with no intra-subspace alpha-beta element and the
+    delta_pt delta_qr form of the Phi block between two of them (Eq. interab)."""
     nact = len(n)
     sub = np.empty(nact, dtype=int)
     strong = set()
@@ -140,14 +142,18 @@ def energy_from_2rdm(h_mo, eri_mo_, n, sqrt_n, phi, members, with_phi=True) -> f
         strong.add(Om[0])
         for p in Om:
             sub[p] = g
+    single_sub = set()
+    for k, s in enumerate(singles):
+        sub[s] = len(members) + k
+        single_sub.add(len(members) + k)
     phys = lambda p, q, r, t: eri_mo_[p, r, q, t]
     E = 2.0 * sum(n[p] * h_mo[p, p] for p in range(nact))
     Dab = np.zeros((nact,) * 4)
     Dss = np.zeros((nact,) * 4)
     for p, q, r, t in itertools.product(range(nact), repeat=4):
         v = 0.0
-        # intra-pair alpha-beta block (Eq. intra)
-        if p == q and r == t and sub[p] == sub[r]:
+        # intra-pair alpha-beta block (Eq. intra), Omega_II only
+        if p == q and r == t and sub[p] == sub[r] and sub[p] not in single_sub:
             if p == r or (p not in strong and r not in strong):
                 Pi = sqrt_n[p] * sqrt_n[r]
             else:
@@ -156,8 +162,10 @@ def energy_from_2rdm(h_mo, eri_mo_, n, sqrt_n, phi, members, with_phi=True) -> f
         # inter-pair alpha-beta block (Eq. interab), f = sub[p], g = sub[q] or sub[r]
         if sub[p] != sub[q] and p == r and q == t:
             v += 0.5 * n[p] * n[q]
-        if with_phi and sub[p] != sub[r] and p == q and r == t:
-            v -= 0.5 * phi[p] * phi[r]
+        both_single = sub[p] in single_sub and sub[r] in single_sub
+        if with_phi and sub[p] != sub[r]:
+            if (not both_single and p == q and r == t) or (both_single and p == t and q == r):
+                v -= 0.5 * phi[p] * phi[r]
         Dab[p, q, r, t] = v
         # inter-pair parallel-spin block (Eq. interaa)
         if sub[p] != sub[q]:

@@ -25,11 +25,11 @@ from scipy.optimize import minimize
 from . import pnof
 
 
-def energy_of_gamma(gamma, Hdiag, J, K, pair_map, npair, ncwo, functional):
+def energy_of_gamma(gamma, Hdiag, J, K, pair_map, npair, ncwo, functional, nsingle=0):
     """E and dE/dgamma at fixed orbitals (Hdiag, J, K fixed)."""
-    occ = pnof.occupations(np.asarray(gamma, dtype=np.float64), pair_map, npair, ncwo)
-    E = pnof.energy(Hdiag, J, K, occ, pair_map, npair, functional)
-    g = pnof.occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional)
+    occ = pnof.occupations(np.asarray(gamma, dtype=np.float64), pair_map, npair, ncwo, nsingle)
+    E = pnof.energy(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
+    g = pnof.occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
     return E, g
 
 
@@ -42,14 +42,14 @@ def fold_gamma(gamma):
 
 
 def optimize_occupations(Hdiag, J, K, gamma0, pair_map, npair, ncwo, functional,
-                         gtol=1e-10, maxiter=2000):
+                         gtol=1e-10, maxiter=2000, nsingle=0):
     """argmin_gamma E[n(gamma)] at fixed orbitals; returns (gamma, E, iterations).
 
     Reading: the minimisation runs over the fundamental box [0, pi/2]^ng (fold_gamma), with
     bounds; a minimum on a kink of sqrt(n) = |sin gamma| (an emptied weak orbital, a pair
     split evenly) is then a bound-constrained minimum, where a projected quasi-Newton method
     converges instead of zigzagging across the kink."""
-    fun = lambda x: energy_of_gamma(x, Hdiag, J, K, pair_map, npair, ncwo, functional)
+    fun = lambda x: energy_of_gamma(x, Hdiag, J, K, pair_map, npair, ncwo, functional, nsingle)
     x = fold_gamma(gamma0)
     E, _ = fun(x)
     nit = 0
@@ -170,7 +170,7 @@ def orbital_step(lam, Fdiag, C, zeta, history, depth):
 
 def optimize(h, B, C, gamma, pair_map, npair, ncwo, functional, Fdiag=None, zeta=0.1,
              depth=6, delta=1e-6, eps_energy=1e-10, max_outer=50, max_inner=10,
-             occ_gtol=1e-10, packed=False, log=None):
+             occ_gtol=1e-10, packed=False, log=None, nsingle=0):
     """The procedure of Sec. III.D: in each outer iteration the occupations are optimised at
     fixed orbitals, then the orbitals by up to `max_inner` diagonalisations of F at fixed
     occupations; converged when max |lambda_qp - lambda_pq| < delta (and the energy changed
@@ -181,11 +181,12 @@ def optimize(h, B, C, gamma, pair_map, npair, ncwo, functional, Fdiag=None, zeta
     C = np.array(C, dtype=np.float64)
     gamma = np.array(gamma, dtype=np.float64)
     pair_map = np.asarray(pair_map)
-    run = lambda C_, g_: pnof.build(h, B, C_, g_, pair_map, npair, ncwo, functional, packed)
+    run = lambda C_, g_: pnof.build(h, B, C_, g_, pair_map, npair, ncwo, functional, packed,
+                                    nsingle)
     energies = []
     ref = run(C, gamma)
     gamma, _, _ = optimize_occupations(ref["Hdiag"], ref["J"], ref["K"], gamma, pair_map,
-                                       npair, ncwo, functional, occ_gtol)
+                                       npair, ncwo, functional, occ_gtol, nsingle=nsingle)
     if Fdiag is None:
         ref = run(C, gamma)
         lam = ref["lam"]
@@ -202,7 +203,8 @@ def optimize(h, B, C, gamma, pair_map, npair, ncwo, functional, Fdiag=None, zeta
         if outer > 1:
             ref = run(C, gamma)
             gamma, _, _ = optimize_occupations(ref["Hdiag"], ref["J"], ref["K"], gamma,
-                                               pair_map, npair, ncwo, functional, occ_gtol)
+                                               pair_map, npair, ncwo, functional, occ_gtol,
+                                               nsingle=nsingle)
         E_prev = None
         for _ in range(max_inner):
             ref = run(C, gamma)

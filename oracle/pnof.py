@@ -31,6 +31,9 @@ Readings of the paper taken here (all listed in the design notes):
   of Eq. woo; gamma holds the npair strong gammas, then (Ng - 1) weak gammas
   per pair, pair-major.
 * orbitals p >= nact are empty (n = 0): their lambda columns are zero.
+* multiplets (Sec. II): the N_I singly occupied orbitals of Omega_I sit at indices
+  npair .. npair + N_I - 1 (pair_map[g] = g), n = 1/2 fixed; they have no intra-subspace
+  term (D_pp,pp = 0), contribute H_gg to E, and enter E_fg with every other subspace.
 """
 from __future__ import annotations
 
@@ -55,7 +58,14 @@ def pair_members(pair_map: np.ndarray, npair: int):
     return members
 
 
-def occupations(gamma: np.ndarray, pair_map: np.ndarray, npair: int, ncwo: int):
+def subspaces(pair_map: np.ndarray, npair: int, nsingle: int = 0):
+    """All subspaces of Omega: the pairs of Omega_II (pair_members), then the singly
+    occupied orbitals of Omega_I, orbital g = npair .. npair + nsingle - 1 each alone."""
+    return pair_members(pair_map, npair) + [[g] for g in range(npair, npair + nsingle)]
+
+
+def occupations(gamma: np.ndarray, pair_map: np.ndarray, npair: int, ncwo: int,
+                nsingle: int = 0):
     """n_p, sqrt(n_p), Phi_p = sqrt(n_p (1 - n_p)) and their Jacobians w.r.t. gamma.
 
     Eq. soo: n_g = (1 + cos^2 gamma_g) / 2, hole h_g = sin^2(gamma_g) / 2.
@@ -111,6 +121,11 @@ def occupations(gamma: np.ndarray, pair_map: np.ndarray, npair: int, ncwo: int):
             om = math.sqrt(1.0 - n[p])
             phi[p] = sq[p] * om
             dphi[p] = dsq[p] * om - sq[p] * dn[p] / (2.0 * om)
+    # Omega_I (Sec. II): each singly occupied orbital has n = 1/2, fixed (no gamma)
+    for g in range(npair, npair + nsingle):
+        n[g] = 0.5
+        sq[g] = math.sqrt(0.5)
+        phi[g] = 0.5
     return dict(n=n, sqrt_n=sq, phi=phi, dn=dn, dsqrt_n=dsq, dphi=dphi)
 
 
@@ -194,10 +209,11 @@ def _pi(p: int, q: int, g: int, sq: np.ndarray) -> float:
     return sq[p] * sq[q]
 
 
-def energy(Hdiag, J, K, occ, pair_map, npair, functional):
-    """E = sum_g E_g + sum_{f != g} E_fg (Eqs. EPNOF7, Eg, Efg / Efg_s); no singly occupied subspaces."""
+def energy(Hdiag, J, K, occ, pair_map, npair, functional, nsingle=0):
+    """E = sum_g E_g + sum_{g in Omega_I} H_gg + sum_{f != g} E_fg (Eqs. EPNOF7, Eg, Efg /
+    Efg_s); f, g run over all subspaces, the singly occupied ones included."""
     n, sq, phi = occ["n"], occ["sqrt_n"], occ["phi"]
-    members = pair_members(pair_map, npair)
+    members = subspaces(pair_map, npair, nsingle)
     E = 0.0
     for g in range(npair):
         Om = members[g]
@@ -206,8 +222,10 @@ def energy(Hdiag, J, K, occ, pair_map, npair, functional):
             for p in Om:
                 Eg += _pi(p, q, g, sq) * K[p, q]
         E += Eg
-    for f in range(npair):
-        for g in range(npair):
+    for g in range(npair, npair + nsingle):
+        E += Hdiag[g]
+    for f in range(len(members)):
+        for g in range(len(members)):
             if f == g:
                 continue
             for p in members[f]:
@@ -224,7 +242,7 @@ def energy(Hdiag, J, K, occ, pair_map, npair, functional):
 # ----------------------------------------------------------------------------
 # orbital gradient and Lagrangian (Sec. III.B)
 # ----------------------------------------------------------------------------
-def generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional):
+def generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional, nsingle=0):
     """G[:, p] = (1/4) dE/dphi_p expanded in the AO basis (Eqs. lowdin, Vee-s, Vee-d):
 
     G_p = F_p C_p,  F_p = n_p h
@@ -242,7 +260,8 @@ def generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional):
         for q in range(nact):
             gq = int(pair_map[q])
             if gq == gp:
-                c[p, q] = _pi(p, q, gp, sq)
+                if gp < npair:  # a singly occupied orbital has no intra-subspace term
+                    c[p, q] = _pi(p, q, gp, sq)
             else:
                 a[p, q] = 2.0 * n[q] * n[p]
                 c[p, q] = -n[q] * n[p]
@@ -256,7 +275,7 @@ def generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional):
     return G
 
 
-def occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional):
+def occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional, nsingle=0):
     """dE/dgamma: partial derivatives of E in n, sqrt(n), Phi, then the chain rule
     through Eqs. soo/woo."""
     n, sq, phi = occ["n"], occ["sqrt_n"], occ["phi"]
@@ -270,7 +289,8 @@ def occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional):
         for q in range(nact):
             gq = int(pair_map[q])
             if gq == gp:
-                dE_dsq[p] += 2.0 * _pi(p, q, gp, np.ones(nact)) * sq[q] * K[p, q]
+                if gp < npair:
+                    dE_dsq[p] += 2.0 * _pi(p, q, gp, np.ones(nact)) * sq[q] * K[p, q]
             else:
                 dE_dn[p] += 2.0 * n[q] * (2.0 * J[p, q] - K[p, q])
                 if functional == PNOF7:
@@ -305,8 +325,10 @@ def orbital_update(lam: np.ndarray, Fdiag: np.ndarray, C: np.ndarray):
     return eps, C @ V
 
 
-def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False):
+def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False, nsingle=0):
     """One Lagrangian build: E, lambda, dE/dgamma, dE/dC and the intermediates.
+    nsingle singly occupied orbitals (Omega_I, n = 1/2) sit at npair .. npair + nsingle - 1
+    with pair_map[g] = g.
 
     B: dense [naux][nbf][nbf] or packed [naux][nbf(nbf+1)/2] (packed=True).
     C: [nbf][nbf], column p = orbital p (Eq. lcao).
@@ -320,16 +342,16 @@ def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False)
     pair_map = np.asarray(pair_map)
     nact = len(pair_map)
     C_act = C[:, :nact]
-    occ = occupations(np.asarray(gamma, dtype=np.float64), pair_map, npair, ncwo)
+    occ = occupations(np.asarray(gamma, dtype=np.float64), pair_map, npair, ncwo, nsingle)
     Jq, Kq = ao_operators(B, C_act)
     J, K = mo_jk(C_act, Jq, Kq)
     Hdiag = np.einsum("mp,mn,np->p", C_act, h, C_act)
-    E = energy(Hdiag, J, K, occ, pair_map, npair, functional)
-    G = generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional)
+    E = energy(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
+    G = generalized_fock_action(h, C_act, Jq, Kq, occ, pair_map, npair, functional, nsingle)
     lam = np.zeros((nbf, nbf))
     lam[:, :nact] = C.T @ G
     dE_dC = np.zeros((nbf, nbf))
     dE_dC[:, :nact] = 4.0 * G
-    dE_dgamma = occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional)
+    dE_dgamma = occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
     return dict(E=E, lam=lam, dE_dgamma=dE_dgamma, dE_dC=dE_dC, G=G, J=J, K=K,
                 Hdiag=Hdiag, n=occ["n"], occ=occ)

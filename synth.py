@@ -17,8 +17,9 @@ soo/woo), drawn with numpy's PCG64 ``default_rng``:
 * strong ``gamma_g ~ U(0, 1.45)``; the hole ``1 - n_g`` of pair g is split over
   its weak orbitals by ``Dirichlet(1, ..., 1)``; the weak gammas are the
   inverse of Eq. woo for that split.  Stream ``[seed, 3]``.
-* ``pair_map``: strong orbital g at index g, weak orbital i of pair g at index
-  ``npair + g * ncwo + i`` (block layout).
+* ``pair_map``: strong orbital g at index g, the ``nsingle`` singly occupied orbitals
+  of a multiplet at ``npair .. npair + nsingle - 1`` (their own subspaces, pair_map[g] =
+  g), weak orbital i of pair g at index ``npair + nsingle + g * ncwo + i`` (block layout).
 """
 from __future__ import annotations
 
@@ -45,10 +46,11 @@ class Problem:
     npair: int
     ncwo: int
     seed: int = 0
+    nsingle: int = 0  # singly occupied orbitals (Omega_I), at npair .. npair + nsingle - 1
 
     @property
     def nact(self) -> int:
-        return self.npair * (1 + self.ncwo)
+        return self.npair * (1 + self.ncwo) + self.nsingle
 
     @property
     def ngamma(self) -> int:
@@ -116,11 +118,12 @@ def gen_C(seed: int, nbf: int) -> np.ndarray:
     return np.ascontiguousarray(q)
 
 
-def block_pair_map(npair: int, ncwo: int) -> np.ndarray:
-    pm = np.empty(npair * (1 + ncwo), dtype=np.int32)
-    pm[:npair] = np.arange(npair)
+def block_pair_map(npair: int, ncwo: int, nsingle: int = 0) -> np.ndarray:
+    pm = np.empty(npair * (1 + ncwo) + nsingle, dtype=np.int32)
+    pm[:npair + nsingle] = np.arange(npair + nsingle)
+    w0 = npair + nsingle
     for g in range(npair):
-        pm[npair + g * ncwo: npair + (g + 1) * ncwo] = g
+        pm[w0 + g * ncwo: w0 + (g + 1) * ncwo] = g
     return pm
 
 
@@ -149,7 +152,7 @@ def generate(prob: Problem, packed: bool = False, with_B: bool = True) -> dict:
         h=gen_h(prob.seed, prob.nbf),
         C=gen_C(prob.seed, prob.nbf),
         gamma=gen_gamma(prob.seed, prob.npair, prob.ncwo),
-        pair_map=block_pair_map(prob.npair, prob.ncwo),
+        pair_map=block_pair_map(prob.npair, prob.ncwo, prob.nsingle),
     )
     if with_B:
         d["B"] = gen_B(prob.seed, prob.naux, prob.nbf, packed=packed)
