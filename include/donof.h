@@ -26,11 +26,13 @@
  *   - C[nbf*nbf]   MO coefficients, column p is orbital p (Eq. lcao): C[mu*nbf + p].
  *   - gamma[npair*ncwo]  gamma[0..npair) strong (Eq. soo), then (ncwo-1) weak gammas
  *                  per pair, pair-major (Eq. woo).
- *   - pair_map[nact], nact = npair*(1+ncwo) <= nbf: subspace of each active orbital.
- *                  pair_map[g] == g for g < npair (strong orbital g sits at index g);
- *                  every pair owns exactly ncwo weak orbitals with index >= npair; the
- *                  weak orbitals of a pair, in increasing index, are p_1..p_Ng of Eq. woo.
- *                  Orbitals p >= nact are empty (n_p = 0).
+ *   - pair_map[nact], nact = npair*(1+ncwo) + nsingle <= nbf: subspace of each active
+ *                  orbital.  pair_map[g] == g for g < npair (strong orbital g sits at
+ *                  index g) and for the nsingle singly occupied orbitals of a multiplet
+ *                  (Omega_I, Sec. II) at npair <= g < npair + nsingle, each its own
+ *                  subspace with n = 1/2; every pair owns exactly ncwo weak orbitals with
+ *                  index >= npair + nsingle; the weak orbitals of a pair, in increasing
+ *                  index, are p_1..p_Ng of Eq. woo.  Orbitals p >= nact are empty (n_p = 0).
  *   - lam[nbf*nbf] lam[q*nbf + p] = lambda_qp (column p is the differentiated orbital);
  *                  columns p >= nact are zero.
  *   - Calls are asynchronous on `stream` (a cudaStream_t, 0 = legacy default stream).
@@ -85,7 +87,9 @@ typedef struct {
   int32_t functional;  /* DONOF_PNOF5 | DONOF_PNOF7 | DONOF_PNOF7S */
   int32_t b_layout;    /* DONOF_B_DENSE | DONOF_B_PACKED */
   int32_t precision;   /* DONOF_FP64 | DONOF_MIXED */
-  int32_t reserved;    /* must be 0 */
+  int32_t nsingle;     /* N_I, singly occupied orbitals of a multiplet (S = N_I / 2), >= 0:
+                        * n = 1/2 each, no intra-subspace term, H_gg in E and E_fg with every
+                        * other subspace (Eqs. EPNOF7, Efg / Efg_s) */
   /* Upper bound, in bytes, on the per-pass intermediate X[P][mu][q] (and its
    * companions) held in the workspace; the auxiliary index is streamed in blocks that
    * fit.  0 = hold every P at once. */

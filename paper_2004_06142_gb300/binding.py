@@ -59,7 +59,7 @@ class donof_problem(ctypes.Structure):
     _fields_ = [("nbf", ctypes.c_int32), ("naux", ctypes.c_int32), ("npair", ctypes.c_int32),
                 ("ncwo", ctypes.c_int32), ("functional", ctypes.c_int32),
                 ("b_layout", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("x_budget_bytes", ctypes.c_uint64)]
+                ("nsingle", ctypes.c_int32), ("x_budget_bytes", ctypes.c_uint64)]
 
 
 _lib = None
@@ -115,8 +115,8 @@ def lib() -> ctypes.CDLL:
 
 
 def make_problem(nbf, naux, npair, ncwo, functional=PNOF7, b_layout=B_DENSE, precision=FP64,
-                 x_budget_bytes=0) -> donof_problem:
-    return donof_problem(nbf, naux, npair, ncwo, functional, b_layout, precision, 0,
+                 x_budget_bytes=0, nsingle=0) -> donof_problem:
+    return donof_problem(nbf, naux, npair, ncwo, functional, b_layout, precision, nsingle,
                          x_budget_bytes)
 
 
@@ -238,11 +238,12 @@ class Builder:
     """Owns a workspace for one problem and one prepared B (device tensors)."""
 
     def __init__(self, nbf, naux, npair, ncwo, functional=PNOF7, b_layout=B_DENSE,
-                 precision=FP64, x_budget_bytes=0, device="cuda"):
+                 precision=FP64, x_budget_bytes=0, device="cuda", nsingle=0):
         self.prob = make_problem(nbf, naux, npair, ncwo, functional, b_layout, precision,
-                                 x_budget_bytes)
+                                 x_budget_bytes, nsingle)
         self.nbf, self.naux, self.npair, self.ncwo = nbf, naux, npair, ncwo
-        self.nact = npair * (1 + ncwo)
+        self.nsingle = nsingle
+        self.nact = npair * (1 + ncwo) + nsingle
         self.ngamma = npair * ncwo
         self.device = torch.device(device)
         self.ws = torch.empty(donof_workspace_size(self.prob), dtype=torch.uint8, device=self.device)

@@ -22,7 +22,8 @@ Dims make_dims(const donof_problem* p) {
   d.Q = p->naux;
   d.npair = p->npair;
   d.ncwo = p->ncwo;
-  d.A = p->npair * (1 + p->ncwo);
+  d.nsingle = p->nsingle;
+  d.A = p->npair * (1 + p->ncwo) + p->nsingle;
   d.Ap = round_up_int(d.A, 16);
   d.Np = round_up_int(d.N, 8);
   d.ng = p->npair * p->ncwo;
@@ -194,20 +195,20 @@ std::unordered_map<const void*, Registration> g_reg;
 
 bool same_problem(const donof_problem& a, const donof_problem& b) {
   return a.nbf == b.nbf && a.naux == b.naux && a.npair == b.npair && a.ncwo == b.ncwo &&
-         a.b_layout == b.b_layout && a.precision == b.precision &&
+         a.nsingle == b.nsingle && a.b_layout == b.b_layout && a.precision == b.precision &&
          a.x_budget_bytes == b.x_budget_bytes;
 }
 
 int check_problem(const donof_problem* p) {
   if (!p) return DONOF_ERR_INVALID_ARG;
-  if (p->nbf < 1 || p->naux < 1 || p->npair < 1 || p->ncwo < 1 || p->reserved != 0)
+  if (p->nbf < 1 || p->naux < 1 || p->npair < 1 || p->ncwo < 1 || p->nsingle < 0)
     return DONOF_ERR_INVALID_ARG;
   if (p->functional != DONOF_PNOF5 && p->functional != DONOF_PNOF7 &&
       p->functional != DONOF_PNOF7S)
     return DONOF_ERR_INVALID_ARG;
   if (p->b_layout != DONOF_B_DENSE && p->b_layout != DONOF_B_PACKED) return DONOF_ERR_INVALID_ARG;
   if (p->precision != DONOF_FP64 && p->precision != DONOF_MIXED) return DONOF_ERR_INVALID_ARG;
-  const long long nact = (long long)p->npair * (1 + p->ncwo);
+  const long long nact = (long long)p->npair * (1 + p->ncwo) + p->nsingle;
   if (nact > p->nbf) return DONOF_ERR_INVALID_ARG;
   if (p->nbf > 65536 || p->naux > (1 << 24)) return DONOF_ERR_UNSUPPORTED;
   if (p->precision == DONOF_MIXED && round_up_int((int)nact, 16) > 256)

@@ -71,7 +71,7 @@ size_t instance_offset(int32_t i, const donof_problem* probs) {
 
 // Relative cost of one build, for the stream assignment.
 double est_cost(const donof_problem& p) {
-  const double N = p.nbf, Q = p.naux, A = (double)p.npair * (1 + p.ncwo);
+  const double N = p.nbf, Q = p.naux, A = (double)p.npair * (1 + p.ncwo) + p.nsingle;
   return 2.0 * Q * N * A * (N + 2.0 * A) + 4.0 * N * N * A + 2e7;  // + launch overhead
 }
 

@@ -37,6 +37,7 @@ __host__ __device__ inline int round_up_int(int x, int a) { return (x + a - 1) /
 // Derived sizes of one problem.
 struct Dims {
   int N, Q, A, Ap, Np, npair, ncwo, ng, pb, nblk, functional, layout, precision;
+  int nsingle;  // singly occupied orbitals (Omega_I) at npair .. npair + nsingle - 1
   int splits;  // split-K factor of the G contraction (mixed path)
 };
 

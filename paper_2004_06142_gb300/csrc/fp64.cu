@@ -114,19 +114,26 @@ __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
     if (!isfinite(gamma[k])) set_status(hdr, DONOF_ERR_NONFINITE);
   const int p = threadIdx.x + blockIdx.x * blockDim.x;
   if (p >= A) return;
+  const int nsub = npair + d.nsingle;  // subspaces: pairs, then the singly occupied orbitals
   const int g = pm[p];
-  if (g < 0 || g >= npair || (p < npair && g != p)) {
+  if (g < 0 || g >= nsub || (p < nsub && g != p) || (p >= nsub && g >= npair)) {
     set_status(hdr, DONOF_ERR_PAIR_MAP);
+    return;
+  }
+  if (p >= npair && p < nsub) {  // Omega_I: n = 1/2, no gamma
+    n[p] = 0.5;
+    sqn[p] = 0.70710678118654752440;
+    phi[p] = 0.5;
     return;
   }
   int rank = 0;
   if (p < npair) {
     int cnt = 0;
-    for (int q = npair; q < A; ++q) cnt += (pm[q] == p);
+    for (int q = nsub; q < A; ++q) cnt += (pm[q] == p);
     if (cnt != ncwo) set_status(hdr, DONOF_ERR_PAIR_MAP);
   } else {
     // rank among the pair's weak orbitals
-    for (int q = npair; q < p; ++q) rank += (pm[q] == g);
+    for (int q = nsub; q < p; ++q) rank += (pm[q] == g);
     if (rank >= ncwo) {
       set_status(hdr, DONOF_ERR_PAIR_MAP);
       return;
@@ -173,8 +180,8 @@ __global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const dou
   if (idx >= (long long)A * A) return;
   const int p = (int)(idx / A), q = (int)(idx % A);
   double a, b;
-  pair_coefficients(d.functional, d.npair, p, q, pm[p] == pm[q], n[p], n[q], sqn[p], sqn[q],
-                    phi[p], phi[q], a, b);
+  pair_coefficients(d.functional, d.npair, p, q, pm[p] == pm[q], pm[p] >= d.npair, n[p], n[q],
+                    sqn[p], sqn[q], phi[p], phi[q], a, b);
   Ac[idx] = a;
   Bc[idx] = b;
 }
@@ -637,8 +644,10 @@ __global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const doub
     const double kpq = K[o], jpq = J[o];
     e += Ac[o] * jpq + Bc[o] * kpq;
     if (pm[q] == g) {
-      const bool plus = (p == q || (p >= d.npair && q >= d.npair));
-      a_s += (plus ? 2.0 : -2.0) * sqn[q] * kpq;
+      if (g < d.npair) {  // a singly occupied orbital has no intra-subspace term
+        const bool plus = (p == q || (p >= d.npair && q >= d.npair));
+        a_s += (plus ? 2.0 : -2.0) * sqn[q] * kpq;
+      }
     } else {
       a_n += 2.0 * n[q] * (2.0 * jpq - kpq);
       a_p -= 2.0 * phi[q] * kpq;

@@ -67,12 +67,17 @@ __device__ inline void occ_orbital(int p, int g, int rank, int npair, int ncwo,
 }
 
 // Coefficients of J_pq and K_pq in E (Eqs. Eg, Efg, Efg_s): same subspace A = 0, B = Pi_pq
-// (sign + for p = q or both weak, - when one of them is the strong orbital); different
+// (sign + for p = q or both weak, - when one of them is the strong orbital), none for a
+// singly occupied orbital (`single`: the subspace belongs to Omega_I); different
 // subspaces A = 2 n_p n_q and B = -n_p n_q [- Phi_p Phi_q (PNOF7) | - 4 Phi_p^2 Phi_q^2 (PNOF7s)].
 __device__ inline void pair_coefficients(int functional, int npair, int p, int q, bool same,
-                                         double np_, double nq, double sp, double sq,
-                                         double fp, double fq, double& a, double& b) {
-  if (same) {
+                                         bool single, double np_, double nq, double sp,
+                                         double sq, double fp, double fq, double& a,
+                                         double& b) {
+  if (same && single) {  // Omega_I: D_pp,pp = 0, no intra-subspace term
+    a = 0.0;
+    b = 0.0;
+  } else if (same) {
     const bool plus = (p == q || (p >= npair && q >= npair));
     a = 0.0;
     b = (plus ? 1.0 : -1.0) * sp * sq;

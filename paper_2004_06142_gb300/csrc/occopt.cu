@@ -78,9 +78,16 @@ __device__ double dot(const double* a, const double* b, int m, double* red) {
 // E(gamma) and dE/dgamma -> grad (shared), returned E identical on every thread.
 __device__ double evaluate(const OccCtx& c, const double* x, double* grad) {
   const int A = c.A;
-  for (int p = threadIdx.x; p < A; p += kThreads)
-    occ_orbital(p, c.pm[p], c.rank[p], c.npair, c.ncwo, x, c.n[p], c.sqn[p], c.phi[p],
-                [](int, double, double, double) {});
+  for (int p = threadIdx.x; p < A; p += kThreads) {
+    if (c.pm[p] >= c.npair) {  // Omega_I: n = 1/2, no gamma
+      c.n[p] = 0.5;
+      c.sqn[p] = 0.70710678118654752440;
+      c.phi[p] = 0.5;
+    } else {
+      occ_orbital(p, c.pm[p], c.rank[p], c.npair, c.ncwo, x, c.n[p], c.sqn[p], c.phi[p],
+                  [](int, double, double, double) {});
+    }
+  }
   __syncthreads();
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   for (int p = warp; p < A; p += kWarps) {
@@ -91,13 +98,13 @@ __device__ double evaluate(const OccCtx& c, const double* x, double* grad) {
       const double kpq = c.K[o], jpq = c.J[o];
       const bool same = c.pm[q] == g;
       double a, b;
-      pair_coefficients(c.functional, c.npair, p, q, same, c.n[p], c.n[q], c.sqn[p], c.sqn[q],
-                        c.phi[p], c.phi[q], a, b);
+      pair_coefficients(c.functional, c.npair, p, q, same, g >= c.npair, c.n[p], c.n[q],
+                        c.sqn[p], c.sqn[q], c.phi[p], c.phi[q], a, b);
       e += a * jpq + b * kpq;
-      if (same) {
+      if (same && g < c.npair) {
         const bool plus = (p == q || (p >= c.npair && q >= c.npair));
         a_s += (plus ? 2.0 : -2.0) * c.sqn[q] * kpq;
-      } else {
+      } else if (!same) {
         a_n += 2.0 * c.n[q] * (2.0 * jpq - kpq);
         a_p -= 2.0 * c.phi[q] * kpq;
         a_7s += c.phi[q] * c.phi[q] * kpq;
@@ -172,9 +179,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int p = threadIdx.x; p < A; p += kThreads) {
     int r = 0;
     const int g = pm[p];
-    if (g < 0 || g >= d.npair) set_status(hdr, DONOF_ERR_PAIR_MAP);
-    if (p >= d.npair)
-      for (int q = d.npair; q < p; ++q) r += (pm[q] == g);
+    if (g < 0 || g >= d.npair + d.nsingle) set_status(hdr, DONOF_ERR_PAIR_MAP);
+    if (p >= d.npair + d.nsingle)
+      for (int q = d.npair + d.nsingle; q < p; ++q) r += (pm[q] == g);
     c.rank[p] = r;
   }
   // the representative in [0, pi/2]: n, sqrt n and Phi depend on each gamma only through

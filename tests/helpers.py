@@ -23,7 +23,8 @@ def gpu_build(prob: synth.Problem, d: dict, precision: int, functional: int, pac
         mu, nu = synth.packed_index(prob.nbf)
         Bh = np.ascontiguousarray(Bh[:, mu, nu])
     b = dn.Builder(prob.nbf, prob.naux, prob.npair, prob.ncwo, functional,
-                   dn.B_PACKED if packed else dn.B_DENSE, precision, budget)
+                   dn.B_PACKED if packed else dn.B_DENSE, precision, budget,
+                   nsingle=prob.nsingle)
     Bd = to_dev(Bh)
     b.prepare(Bd)
     h, C = to_dev(d["h"]), to_dev(d["C"])
