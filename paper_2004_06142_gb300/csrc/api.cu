@@ -99,6 +99,7 @@ Layout make_layout(const Dims& d) {
     L.ChiS = take(Ap * Np * 2);
     L.CloS = take(Ap * Np * 2);
     L.eCs = take(Ap * 4);
+    L.gram = take((N + 63) / 64 * A * A * 4);
     L.eB = take(Q * N * 4);
     L.L1max = take(Q * 8);
     L.Chi = take(Ap * Np * 2);
@@ -231,7 +232,7 @@ DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long
   DgemmArgs a{};
   a.M = M; a.N = N; a.K = 64; a.KB = (K + 63) / 64; a.Ktot = K; a.batch = 1;
   const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
-  long long ks = (2 * 152 + tiles - 1) / tiles;
+  long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
   if (ks > a.KB) ks = a.KB;
   if (ks < 1) ks = 1;
   a.ksplit = (int)ks;
@@ -368,7 +369,7 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
       DgemmArgs a{};
       a.M = N; a.N = A; a.K = A; a.KB = np; a.batch = 1;
       const long long tiles = (long long)((N + 63) / 64) * ((A + 63) / 64);
-      long long ks = (2 * 152 + tiles - 1) / tiles;
+      long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
       if (ks > np) ks = np;
       a.ksplit = (int)ks;
       a.A = X; a.sAm = A; a.sAk = 1; a.sAkb = (long long)N * A;

@@ -57,6 +57,7 @@ struct Layout {
   // the row norms), per-slice maxima of the scaled row norms, and the split of
   // (diag 2^s C_act)^T that multiplies it
   size_t eS, rnmax, tmax, ChiS, CloS, eCs;
+  size_t gram;  // per-chunk parts of the Gram matrix of C_act (fp32)
   size_t total;
 };
 

@@ -1065,19 +1065,21 @@ __global__ void k_xt_exponents(const double* __restrict__ L1max, const double* _
 }
 
 // s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
-// matrix, formed in fp32 (one CTA per row i) with a relative safety margin of 1e-4 far above
-// its rounding error.
-__global__ void __launch_bounds__(256) k_gram_rows(const double* __restrict__ C, int N, int A,
-                                                   DevHeader* hdr) {
-  // row i of the Gram matrix: warp w sums mu = w, w + 8, ...; lane l owns columns l + 32k
-  const int i = blockIdx.x;
+// matrix, formed in fp32 with a relative safety margin of 1e-4 far above its rounding
+// error.  k_gram_part: one CTA per (row i, chunk of 64 AO indices mu), the chunk's part of
+// row i in a fixed order; k_gram_final: one CTA per row, the chunks summed in order.
+constexpr int kGramChunk = 64;
+__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ C, int N, int A,
+                                                   float* part) {
+  const int i = blockIdx.x, ch = blockIdx.y;
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   constexpr int kCols = 8;  // A <= 256
-  __shared__ float part[8][256];
+  __shared__ float sp[8][256];
   float g[kCols];
 #pragma unroll
   for (int k = 0; k < kCols; ++k) g[k] = 0.f;
-  for (int mu = w; mu < N; mu += 8) {
+  const int mu1 = min(N, (ch + 1) * kGramChunk);
+  for (int mu = ch * kGramChunk + w; mu < mu1; mu += 8) {
     const double* Cm = C + (size_t)mu * N;
     const float ci = (float)Cm[i];
 #pragma unroll
@@ -1089,13 +1091,24 @@ __global__ void __launch_bounds__(256) k_gram_rows(const double* __restrict__ C,
 #pragma unroll
   for (int k = 0; k < kCols; ++k) {
     const int j = lane + 32 * k;
-    if (j < A) part[w][j] = g[k];
+    if (j < A) sp[w][j] = g[k];
   }
   __syncthreads();
+  for (int j = threadIdx.x; j < A; j += blockDim.x) {
+    float t = 0.f;
+    for (int ww = 0; ww < 8; ++ww) t += sp[ww][j];
+    part[((size_t)ch * A + i) * A + j] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ part, int nch,
+                                                    int A, DevHeader* hdr) {
+  const int i = blockIdx.x;
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   float rs = 0.f;
   for (int j = threadIdx.x; j < A; j += blockDim.x) {
     float t = 0.f;
-    for (int ww = 0; ww < 8; ++ww) t += part[ww][j];
+    for (int ch = 0; ch < nch; ++ch) t += part[((size_t)ch * A + i) * A + j];
     rs += fabsf(t);
   }
   __shared__ float red[8];
@@ -1104,15 +1117,11 @@ __global__ void __launch_bounds__(256) k_gram_rows(const double* __restrict__ C,
   __syncthreads();
   if (threadIdx.x == 0) {
     float t = 0.f;
-    for (int ww = 0; ww < 8; ++ww) t += red[ww];
+    for (int k = 0; k < 8; ++k) t += red[k];
     atomic_max_nonneg((unsigned long long*)&hdr->sC2, (double)t * (1.0 + 1e-4));
   }
 }
 
-// Slices P of a block belong to G split sp when nkb*sp/splits <= P < nkb*(sp+1)/splits (the
-// split of the G contraction).  spOf[P] = sp; eX3[sp][mu] is the exponent of the integer +
-// fraction split of X rows (P in sp, mu) over (P, q):
-//   sum_{P in sp} ||X[P][mu][:]||^2 <= ||C_act||_2^2 sum_{P in sp} ||B^P[mu][:]||^2.
 __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* hdr, int np,
                                int splits, int N, int* spOf, int* eX3) {
   const double sC2 = hdr->sC2;
@@ -1261,8 +1270,11 @@ cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const La
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->sC2, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
-  k_gram_rows<<<d.A, 256, 0, s>>>(C, d.N, d.A, hdr);
-  count_launch(1);
+  const int nch = (d.N + kGramChunk - 1) / kGramChunk;
+  float* part = (float*)(ws + L.gram);
+  k_gram_part<<<dim3(d.A, nch), 256, 0, s>>>(C, d.N, d.A, part);
+  k_gram_final<<<d.A, 256, 0, s>>>(part, nch, d.A, hdr);
+  count_launch(2);
   return cudaGetLastError();
 }
 
