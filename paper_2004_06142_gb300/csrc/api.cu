@@ -112,7 +112,6 @@ Layout make_layout(const Dims& d) {
     L.Xtlo = take(pb * Ap * Np * 2);
     L.eXt = take(pb * Ap * 4);
     L.b32 = take(pb * Ap * Ap * 4);
-    L.Y32 = take(pb * Ap * Ap * 4);
     L.Yhi = take(pb * Ap * Ap * 2);
     L.Ylo = take(pb * Ap * Ap * 2);
     L.Gpart = take((size_t)d.splits * N * Ap * 4);
@@ -120,7 +119,11 @@ Layout make_layout(const Dims& d) {
     L.rn2 = take(Q * N * 8);
     L.spOf = take(pb * 4);
     L.eX3 = take((size_t)d.splits * N * 4);
-    L.ssqY = take((size_t)d.splits * Ap * 4);
+    L.W = take(pb * A * 4);
+    L.Ksp = take((size_t)d.splits * A * A * 8);
+    L.Jsp = take((size_t)d.splits * A * A * 8);
+    L.AcF = take(Ap * Ap * 4);
+    L.BcF = take(Ap * Ap * 4);
     L.eY = take((size_t)d.splits * Ap * 4);
     L.CfH = take(N * Np * 2);
     L.CfF = take(N * Np * 2);
@@ -307,6 +310,7 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(cudaMemsetAsync(&((DevHeader*)(ws + L.header))->abort_flag, 0, sizeof(int32_t), s));
   CK(launch_occupations(d, gamma, pair_map, ws, L, s));
   CK(launch_coefficients(d, pair_map, ws, L, s));
+  if (d.precision == DONOF_MIXED) CK(launch_coef_f32(d, ws, L, s));
   // hC = h C_act, H_pp, G = n o hC
   CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
   CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1), s));

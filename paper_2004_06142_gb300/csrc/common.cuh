@@ -58,6 +58,9 @@ struct Layout {
   // (diag 2^s C_act)^T that multiplies it
   size_t eS, rnmax, tmax, ChiS, CloS, eCs;
   size_t gram;  // per-chunk parts of the Gram matrix of C_act (fp32)
+  // between the b and G contractions: w^P (fp32), per-split K and J partials (double),
+  // fp32 copies of the J and K coefficient matrices ([Ap][Ap])
+  size_t W, Ksp, Jsp, AcF, BcF;
   size_t total;
 };
 
@@ -135,15 +138,15 @@ cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const L
                                cudaStream_t s);
 cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
                                      const Layout& L, cudaStream_t s);
-cudaError_t launch_jk_accumulate_f32(const Dims& d, const float* b, int np, int ld, char* ws,
-                                     const Layout& L, cudaStream_t s);
+
 cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np, char* ws,
                                const Layout& L, cudaStream_t s);
-cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
-                               const Layout& L, cudaStream_t s);
-// J, K accumulation and Y^P in one pass over b (fp32 b, mixed path).
-cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
-                           const Layout& L, cudaStream_t s);
+
+// Mixed path between the b and G contractions (mid.cu): J, K and the Y operand split.
+cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const Layout& L,
+                             cudaStream_t s);
+cudaError_t launch_coef_f32(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
+
 cudaError_t launch_energy(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
                           double* E_out, double* dEdg_out, cudaStream_t s);
 cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s);
@@ -155,7 +158,6 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
                                    cudaStream_t s);
 cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
                            cudaStream_t s);
-cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
                               cudaStream_t s);

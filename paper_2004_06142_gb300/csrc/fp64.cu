@@ -299,11 +299,6 @@ cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int
                                      const Layout& L, cudaStream_t s) {
   return launch_jk_t<double>(d, b, np, ld, ws, L, s);
 }
-cudaError_t launch_jk_accumulate_f32(const Dims& d, const float* b, int np, int ld, char* ws,
-                                     const Layout& L, cudaStream_t s) {
-  return launch_jk_t<float>(d, b, np, ld, ws, L, s);
-}
-
 // ---------------------------------------------------------------------------
 // Y^P[q][p] = Bcoef_qp b^P_qp + delta_qp w^P_p,  w^P_p = sum_r Acoef_pr b^P_rr.
 // G_p = n_p (hC)_p + sum_P X^P Y^P  is then (1/4) dE/dC (Eqs. lowdin, Vee-s, Vee-d).
@@ -366,256 +361,6 @@ cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np
   count_launch(1);
   return cudaGetLastError();
 }
-cudaError_t launch_build_Y_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
-                               const Layout& L, cudaStream_t s) {
-  const int grid = np < 152 * 4 ? np : 152 * 4;
-  k_build_Y<float><<<grid, 256, 2 * d.Ap * sizeof(double), s>>>(
-      d, b, Y, np, d.Ap, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef),
-      (DevHeader*)(ws + L.header));
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-#define CK_RET(x)                    \
-  do {                               \
-    const cudaError_t e_ = (x);      \
-    if (e_ != cudaSuccess) return e_; \
-  } while (0)
-
-namespace {
-__global__ void k_diag(const float* __restrict__ b, int np, int ld, int A, float* D) {
-  const long long tot = (long long)np * A;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long P = i / A;
-    const int r = (int)(i % A);
-    D[i] = b[(size_t)P * ld * ld + (size_t)r * ld + r];
-  }
-}
-}  // namespace
-
-namespace {
-__global__ void k_row_ssq(const float* __restrict__ Y, int np, int ld, const int* __restrict__ spOf,
-                          float* ssqY) {
-  const long long rows = (long long)np * ld;
-  const int lane = threadIdx.x % 32;
-  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; row < rows;
-       row += (long long)gridDim.x * blockDim.x / 32) {
-    float ss = 0.f;
-    for (int c = lane; c < ld; c += 32) {
-      const float v = Y[row * ld + c];
-      ss = fmaf(v, v, ss);
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) atomicAdd(ssqY + (size_t)spOf[row / ld] * ld + row % ld, ss);
-  }
-}
-}  // namespace
-
-static cudaError_t launch_row_ssq(const float* Y, int np, int ld, char* ws, const Layout& L,
-                                  cudaStream_t s) {
-  k_row_ssq<<<152 * 4, 256, 0, s>>>(Y, np, ld, (const int*)(ws + L.spOf), (float*)(ws + L.ssqY));
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-static cudaError_t launch_diag(const Dims& d, const float* b, int np, int ld, float* D,
-                               cudaStream_t s) {
-  k_diag<<<152, 256, 0, s>>>(b, np, ld, d.A, D);
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Mixed path: J, K accumulation and Y^P from fp32 b.
-//   k_y_smem:    one CTA per slice at a time; Acoef and Bcoef cached in shared memory as
-//                fp32; also writes the diagonals D[P][p] = b^P_pp;
-//   k_jk_stream: K from the squares of b and J from D (streaming, no gathers).
-// ---------------------------------------------------------------------------
-namespace {
-// K_pq += sum_P b[P][q][p]^2 and J_pq += sum_P d_q^P d_p^P (d^P the diagonal of b^P, given
-// as Dg[P][p]): four consecutive entries of one row per thread, a chunk of slices per CTA.
-// Products and sums over 16 slices in fp32 (round-to-nearest, unbiased), partial sums of
-// those groups in double: the FP64 pipe of GB300 would otherwise bound this pass.
-__global__ void __launch_bounds__(256) k_jk_stream(Dims d, const float* __restrict__ b,
-                                                   const float* __restrict__ Dg, int np, int ld,
-                                                   double* J, double* K) {
-  const int A = d.A;
-  const int n4 = ld * ld / 4;
-  const int i4 = blockIdx.x * 256 + threadIdx.x;
-  const int chunk = (np + gridDim.y - 1) / gridDim.y;
-  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
-  if (i4 >= n4 || P0 >= P1) return;
-  const int q = (i4 * 4) / ld, p0 = (i4 * 4) % ld;
-  if (q >= A || p0 >= A) return;
-  const int np4 = min(4, A - p0);
-  double sk[4] = {0.0, 0.0, 0.0, 0.0}, sj[4] = {0.0, 0.0, 0.0, 0.0};
-  const float4* b4 = (const float4*)b;
-  for (int G0 = P0; G0 < P1; G0 += 16) {
-    const int G1 = min(P1, G0 + 16);
-    float fk[4] = {0.f, 0.f, 0.f, 0.f}, fj[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int P = G0; P < G1; ++P) {
-      const float4 v = b4[(size_t)P * n4 + i4];
-      const float* dP = Dg + (size_t)P * A;
-      const float dq = dP[q];
-      fk[0] = fmaf(v.x, v.x, fk[0]);
-      fk[1] = fmaf(v.y, v.y, fk[1]);
-      fk[2] = fmaf(v.z, v.z, fk[2]);
-      fk[3] = fmaf(v.w, v.w, fk[3]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < np4) fj[j] = fmaf(dq, dP[p0 + j], fj[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      sk[j] += fk[j];
-      sj[j] += fj[j];
-    }
-  }
-  for (int j = 0; j < np4; ++j) {
-    atomicAdd(K + (size_t)q * A + p0 + j, sk[j]);
-    atomicAdd(J + (size_t)q * A + p0 + j, sj[j]);
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_y_smem(Dims d, const float* __restrict__ b, float* Y,
-                                                 int np, int ld, const double* __restrict__ Ac,
-                                                 const double* __restrict__ Bc, float* D,
-                                                 const int* __restrict__ spOf, float* ssqY) {
-  extern __shared__ float shf[];
-  const int A = d.A;
-  float* sA = shf;                 // A * A
-  float* sB = sA + A * A;          // A * A
-  float* dv = sB + A * A;          // ld
-  float* wv = dv + ld;             // ld
-  float* srow = wv + ld;           // ld: per-row sums of squares of Y^P
-  for (int i = threadIdx.x; i < A * A; i += blockDim.x) {
-    sA[i] = (float)Ac[i];
-    sB[i] = (float)Bc[i];
-  }
-  for (int r = threadIdx.x; r < ld; r += blockDim.x) srow[r] = 0.f;
-  __syncthreads();
-  const int ents = ld * ld;
-  for (int P = blockIdx.x; P < np; P += gridDim.x) {
-    const float* bp = b + (size_t)P * ents;
-    float* yp = Y + (size_t)P * ents;
-    for (int r = threadIdx.x; r < A; r += blockDim.x) {
-      const float v = bp[r * ld + r];
-      dv[r] = v;
-      D[(size_t)P * A + r] = v;  // diagonal d^P for J
-    }
-    __syncthreads();
-    // w_p = sum_r Acoef_pr d_r: eight threads per p, each over a strided eighth of r
-    for (int t0 = 0; t0 < 8 * A; t0 += blockDim.x) {  // uniform trip count: full warps
-      const int t = t0 + threadIdx.x;
-      const bool act = t < 8 * A;
-      const int pp = act ? t / 8 : 0, part = t % 8;
-      float w = 0.f;
-      if (act)
-        for (int r = part; r < A; r += 8) w = fmaf(sA[pp * A + r], dv[r], w);
-      w += __shfl_xor_sync(0xffffffffu, w, 1);
-      w += __shfl_xor_sync(0xffffffffu, w, 2);
-      w += __shfl_xor_sync(0xffffffffu, w, 4);
-      if (act && part == 0) wv[pp] = w;
-    }
-    __syncthreads();
-    // four consecutive entries of one row per thread, all of a thread's loads issued first;
-    // the squares of each row are summed in shared memory for the exponent of its integer +
-    // fraction split (Y is symmetric, so row r is also the r-th operand row of the G
-    // contraction)
-    const float4* b4 = (const float4*)bp;
-    float4* y4 = (float4*)yp;
-    const int n4 = ents / 4;
-    constexpr int kPer = 8;  // float4 per thread per slice (ents/4 <= 8 * 1024)
-    float4 in4[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int i4 = threadIdx.x + k * blockDim.x;
-      in4[k] = i4 < n4 ? b4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int i4 = threadIdx.x + k * blockDim.x;
-      const bool act = i4 < n4;
-      if (!__any_sync(0xffffffffu, act)) break;  // warp-uniform
-      const int i = i4 * 4;
-      const int qq = act ? i / ld : 0, p0 = act ? i % ld : 0;
-      const float in[4] = {in4[k].x, in4[k].y, in4[k].z, in4[k].w};
-      float o[4];
-      float ss = 0.f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int pp = p0 + j;
-        float t = 0.f;
-        if (act && qq < A && pp < A) {
-          t = sB[qq * A + pp] * in[j];
-          if (qq == pp) t += wv[pp];
-        }
-        o[j] = t;
-        ss = fmaf(t, t, ss);
-      }
-      if (act) y4[i4] = make_float4(o[0], o[1], o[2], o[3]);
-      if (ld / 4 >= 32) {
-        // the warp's 32 consecutive float4 span at most two rows: one atomic per row part
-        const int lane = threadIdx.x % 32;
-        const int q0 = __shfl_sync(0xffffffffu, qq, 0);
-        const int qa = act ? qq : q0;
-        float s0 = (qa == q0) ? ss : 0.f, s1 = (qa == q0) ? 0.f : ss;
-        int qmax = qa;
-        for (int o2 = 16; o2 > 0; o2 >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o2);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, o2);
-          qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o2));
-        }
-        if (lane == 0) {
-          if (s0 != 0.f) atomicAdd(&srow[q0], s0);
-          if (qmax != q0 && s1 != 0.f) atomicAdd(&srow[qmax], s1);
-        }
-      } else if (act && ss != 0.f) {
-        atomicAdd(&srow[qq], ss);
-      }
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < A; r += blockDim.x) {
-      atomicAdd(ssqY + (size_t)spOf[P] * ld + r, srow[r]);
-      srow[r] = 0.f;
-    }
-    __syncthreads();
-  }
-}
-}  // namespace
-
-cudaError_t launch_jky_f32(const Dims& d, const float* b, float* Y, int np, char* ws,
-                           const Layout& L, cudaStream_t s) {
-  const int ld = d.Ap;
-  float* D = (float*)(ws + L.D);
-  // Y, its row norms and the diagonals D
-  const size_t shm = (2 * (size_t)d.A * d.A + 3 * (size_t)ld) * sizeof(float);
-  if (shm > 200 * 1024 || ld * ld / 4 > 8 * 1024) {  // too large for the shared-memory kernel
-    CK_RET(launch_build_Y_f32(d, b, Y, np, ws, L, s));
-    CK_RET(launch_diag(d, b, np, ld, D, s));
-    CK_RET(launch_row_ssq(Y, np, ld, ws, L, s));
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_y_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)shm);
-    if (e != cudaSuccess) return e;
-    const int grid = np < 152 ? np : 152;
-    k_y_smem<<<grid, 1024, shm, s>>>(d, b, Y, np, ld, (const double*)(ws + L.Acoef),
-                                     (const double*)(ws + L.Bcoef), D,
-                                     (const int*)(ws + L.spOf), (float*)(ws + L.ssqY));
-    count_launch(1);
-  }
-  // J and K
-  const unsigned gx = (unsigned)((ld * ld / 4 + 255) / 256);
-  unsigned gy = (unsigned)((6 * 152 + gx - 1) / gx);
-  if (gy > (unsigned)np) gy = (unsigned)np;
-  k_jk_stream<<<dim3(gx, gy), 256, 0, s>>>(d, b, D, np, ld, (double*)(ws + L.J),
-                                           (double*)(ws + L.K));
-  count_launch(1);
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // Energy and occupation gradient (double throughout).
 //   dE/dn_p     = 2 H_pp + 2 sum_{q not in g(p)} n_q (2 J_pq - K_pq)

@@ -1,0 +1,238 @@
+// Mixed path, between the b contraction and the G contraction: from the MO three-index
+// slices b^P (fp32, [P][q][p], pitch Ap) to J, K (Eq. JKpq in density-fitted form) and to
+// the integer + fraction operand of the G contraction,
+//   Y^P_qp = Bcoef_qp b^P_qp + delta_qp w^P_p,   w^P_p = sum_r Acoef_pr d^P_r,  d^P_r = b^P_rr,
+// (the J and K coefficient matrices of E applied slice by slice, Eqs. Vee-s, Vee-d), without
+// materialising Y in fp32:
+//   k_diag_w   d^P and w^P per slice (fp32, a warp per output);
+//   k_kpart    per G split sp: Ksp_qp = sum_{P in sp} (b^P_qp)^2 and Jsp_qp = sum d^P_q d^P_p
+//              (fp32 groups of 16 slices, double across groups), b read once;
+//   k_jk_eY    K += sum_sp Ksp, J += sum_sp Jsp (double, fixed order), and the exponent of
+//              row p of Y over split sp from its exact squared norm
+//                sum_q Bcoef_qp^2 Ksp_qp + 2 Bcoef_pp sum_P d^P_p w^P_p + sum_P (w^P_p)^2;
+//   k_y_quant  Y computed on the fly and written as integer + fraction planes, b read again.
+#include "common.cuh"
+
+namespace donof {
+namespace {
+
+__device__ __forceinline__ float pow2f_m(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((e + 127) << 23);
+}
+
+__host__ __device__ inline int intfrac_exp(double nrm) {
+  if (!(nrm > 0.0)) return 0;
+  int e;
+  frexp(nrm, &e);
+  return e - 11;
+}
+
+// fp32 copies of the coefficient matrices, [Ap][Ap] with zero padding
+__global__ void k_coef_f32(const double* __restrict__ Ac, const double* __restrict__ Bc, int A,
+                           int Ap, float* AcF, float* BcF) {
+  const int tot = Ap * Ap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+    const int p = i / Ap, q = i % Ap;
+    const bool in = p < A && q < A;
+    AcF[i] = in ? (float)Ac[(size_t)p * A + q] : 0.f;
+    BcF[i] = in ? (float)Bc[(size_t)p * A + q] : 0.f;
+  }
+}
+
+// d^P (the diagonal of b^P) and w^P = Acoef d^P: one CTA per slice at a time, a warp per w_p
+__global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ b, int np, int A,
+                                                int Ap, const float* __restrict__ AcF,
+                                                float* D, float* W) {
+  __shared__ float dv[256];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    const float* bp = b + (size_t)P * Ap * Ap;
+    for (int r = threadIdx.x; r < A; r += blockDim.x) {
+      const float v = bp[(size_t)r * Ap + r];
+      dv[r] = v;
+      D[(size_t)P * A + r] = v;
+    }
+    __syncthreads();
+    for (int p = warp; p < A; p += blockDim.x / 32) {
+      float w = 0.f;
+      for (int r = lane; r < A; r += 32) w = fmaf(AcF[(size_t)p * Ap + r], dv[r], w);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0) W[(size_t)P * A + p] = w;
+    }
+    __syncthreads();
+  }
+}
+
+// Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread.
+__global__ void __launch_bounds__(256) k_kpart(const float* __restrict__ b,
+                                               const float* __restrict__ D, int np, int A,
+                                               int Ap, int splits, double* Ksp, double* Jsp) {
+  const int n4 = A * (Ap / 4);
+  const int i4 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sp = blockIdx.y;
+  if (i4 >= n4) return;
+  const int q = i4 / (Ap / 4), p0 = (i4 % (Ap / 4)) * 4;
+  const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
+  double sk[4] = {0.0, 0.0, 0.0, 0.0}, sj[4] = {0.0, 0.0, 0.0, 0.0};
+  const float4* b4 = (const float4*)b;
+  const size_t slice4 = (size_t)Ap * Ap / 4;
+  const size_t e4 = (size_t)q * (Ap / 4) + p0 / 4;
+  for (int G0 = P0; G0 < P1; G0 += 16) {
+    const int G1 = min(P1, G0 + 16);
+    float fk[4] = {0.f, 0.f, 0.f, 0.f}, fj[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int P = G0; P < G1; ++P) {
+      const float4 v = b4[(size_t)P * slice4 + e4];
+      const float* dP = D + (size_t)P * A;
+      const float dq = dP[q];
+      fk[0] = fmaf(v.x, v.x, fk[0]);
+      fk[1] = fmaf(v.y, v.y, fk[1]);
+      fk[2] = fmaf(v.z, v.z, fk[2]);
+      fk[3] = fmaf(v.w, v.w, fk[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (p0 + j < A) fj[j] = fmaf(dq, dP[p0 + j], fj[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      sk[j] += fk[j];
+      sj[j] += fj[j];
+    }
+  }
+  const size_t o = ((size_t)sp * A + q) * A + p0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (p0 + j < A) {
+      Ksp[o + j] = sk[j];
+      Jsp[o + j] = sj[j];
+    }
+}
+
+// K += sum_sp Ksp, J += sum_sp Jsp (entries of blocks x), then the Y row exponents (blocks y).
+__global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
+                                               const double* __restrict__ Jsp,
+                                               const float* __restrict__ D,
+                                               const float* __restrict__ W,
+                                               const float* __restrict__ BcF, int np, int A,
+                                               int Ap, int splits, double* K, double* J,
+                                               int* eY) {
+  const int AA = A * A;
+  if (blockIdx.y == 0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < AA; i += gridDim.x * blockDim.x) {
+      double k = 0.0, j = 0.0;
+      for (int sp = 0; sp < splits; ++sp) {
+        k += Ksp[(size_t)sp * AA + i];
+        j += Jsp[(size_t)sp * AA + i];
+      }
+      K[i] += k;
+      J[i] += j;
+    }
+    return;
+  }
+  // blockIdx.y = 1: one warp per (split, row p), rows p >= A get exponent 0
+  const int lane = threadIdx.x % 32;
+  const int nrow = splits * Ap;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) / 32; t < nrow;
+       t += gridDim.x * blockDim.x / 32) {
+    const int sp = t / Ap, p = t % Ap;
+    double ss = 0.0;
+    if (p < A) {
+      const double* Ks = Ksp + (size_t)sp * AA;
+      for (int q = lane; q < A; q += 32) {
+        const double bc = BcF[(size_t)q * Ap + p];
+        ss += bc * bc * Ks[(size_t)q * A + p];
+      }
+      const int P0 = (int)((long long)np * sp / splits);
+      const int P1 = (int)((long long)np * (sp + 1) / splits);
+      const double bpp = BcF[(size_t)p * Ap + p];
+      for (int P = P0 + lane; P < P1; P += 32) {
+        const double d = D[(size_t)P * A + p], w = W[(size_t)P * A + p];
+        ss += 2.0 * bpp * d * w + w * w;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) eY[t] = intfrac_exp(sqrt(fmax(ss, 0.0)) * (1.0 + 1e-6));
+  }
+}
+
+// Y^P_rc = Bcoef_rc b^P_rc + delta_rc w^P_r -> integer + fraction planes with row exponent
+// eY[spOf[P]][r]; four consecutive entries of one row per thread.
+__global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__ W,
+                          const float* __restrict__ BcF, int np, int A, int Ap,
+                          const int* __restrict__ spOf, const int* __restrict__ eY, __half* H,
+                          __half* F, DevHeader* hdr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->e3 = 0;  // G partials are in true units
+  const int r4 = Ap / 4;
+  const long long tot4 = (long long)np * Ap * r4;
+  const float4* b4 = (const float4*)b;
+  const float4* Bc4 = (const float4*)BcF;
+  for (long long i4 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i4 < tot4;
+       i4 += (long long)gridDim.x * blockDim.x) {
+    const long long row = i4 / r4;  // P * Ap + r
+    const int P = (int)(row / Ap), r = (int)(row % Ap);
+    const int c0 = (int)(i4 % r4) * 4;
+    const float sc = pow2f_m(-eY[(size_t)spOf[P] * Ap + r]);
+    const float4 v = b4[i4];
+    const float4 bc = Bc4[(size_t)r * r4 + c0 / 4];
+    float y[4] = {bc.x * v.x, bc.y * v.y, bc.z * v.z, bc.w * v.w};
+    if (r < A && r >= c0 && r < c0 + 4) y[r - c0] += W[(size_t)P * A + r];
+    __align__(8) __half h[4], fr[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float x = y[j] * sc;
+      const float hv = rintf(x);
+      h[j] = __float2half_rn(hv);
+      fr[j] = __float2half_rn(x - hv);
+    }
+    *(uint2*)(H + i4 * 4) = *(uint2*)h;
+    *(uint2*)(F + i4 * 4) = *(uint2*)fr;
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const Layout& L,
+                             cudaStream_t s) {
+  const int A = d.A, Ap = d.Ap;
+  const float* b = (const float*)(ws + L.b32);
+  float* D = (float*)(ws + L.D);
+  float* W = (float*)(ws + L.W);
+  const float* AcF = (const float*)(ws + L.AcF);
+  const float* BcF = (const float*)(ws + L.BcF);
+  k_diag_w<<<sm_count() * 2, 256, 0, s>>>(b, np, A, Ap, AcF, D, W);
+  const int n4 = A * (Ap / 4);
+  k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
+                                                         (double*)(ws + L.Ksp),
+                                                         (double*)(ws + L.Jsp));
+  k_jk_eY<<<dim3(sm_count(), 2), 256, 0, s>>>((const double*)(ws + L.Ksp),
+                                             (const double*)(ws + L.Jsp), D, W, BcF, np, A, Ap,
+                                             splits, (double*)(ws + L.K), (double*)(ws + L.J),
+                                             (int*)(ws + L.eY));
+  k_y_quant<<<sm_count() * 8, 256, 0, s>>>(b, W, BcF, np, A, Ap, (const int*)(ws + L.spOf),
+                                          (const int*)(ws + L.eY), (__half*)(ws + L.Yhi),
+                                          (__half*)(ws + L.Ylo), (DevHeader*)(ws + L.header));
+  count_launch(4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_f32(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
+  k_coef_f32<<<sm_count(), 256, 0, s>>>((const double*)(ws + L.Acoef),
+                                       (const double*)(ws + L.Bcoef), d.A, d.Ap,
+                                       (float*)(ws + L.AcF), (float*)(ws + L.BcF));
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace donof

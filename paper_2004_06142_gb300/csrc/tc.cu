@@ -1139,56 +1139,8 @@ __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* 
   }
 }
 
-// eY[sp][r] from the accumulated squares of the Y rows of split sp.
-__global__ void k_y_exponents(const float* __restrict__ ssqY, int n, int* eY) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    eY[i] = intfrac_exponent(sqrt((double)ssqY[i]) * (1.0 + 1e-6));
-}
 
-// Y (fp32, [P][r][c], symmetric) -> integer + fraction planes with row exponent
-// eY[spOf[P]][r]; four consecutive entries of one row per thread.
-__global__ void k_quant_Y(const float* __restrict__ Y, int np, int Ap, const int* __restrict__ spOf,
-                          const int* __restrict__ eY, __half* H, __half* F, DevHeader* hdr) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->e3 = 0;  // G partials are in true units
-  const int r4 = Ap / 4;                                  // float4 per row
-  const long long tot4 = (long long)np * Ap * r4;
-  const float4* Y4 = (const float4*)Y;
-  for (long long i4 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i4 < tot4;
-       i4 += (long long)gridDim.x * blockDim.x) {
-    const long long row = i4 / r4;  // P * Ap + r
-    const int P = (int)(row / Ap), r = (int)(row % Ap);
-    const float sc = pow2f(-eY[(size_t)spOf[P] * Ap + r]);
-    const float4 v = Y4[i4];
-    const float y[4] = {v.x * sc, v.y * sc, v.z * sc, v.w * sc};
-    __align__(8) __half h[4], fr[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float hv = rintf(y[j]);
-      h[j] = __float2half_rn(hv);
-      fr[j] = __float2half_rn(y[j] - hv);
-    }
-    *(uint2*)(H + i4 * 4) = *(uint2*)h;
-    *(uint2*)(F + i4 * 4) = *(uint2*)fr;
-  }
-}
 
-// Y (fp32) -> scaled fp16 hi/lo; exponent from max |Y| of the block.
-__global__ void k_split_Y(const float* __restrict__ Y, long long tot, DevHeader* hdr, __half* hi,
-                          __half* lo) {
-  const float maxY = __uint_as_float(hdr->maxY_bits);
-  const int sY = split_exponent((double)maxY);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    hdr->sY = sY;
-    hdr->e3 = -hdr->sX - sY;
-  }
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float x = ldexpf(Y[i], sY);
-    const __half h = __float2half_rn(x);
-    hi[i] = h;
-    lo[i] = __float2half_rn(x - __half2float(h));
-  }
-}
 
 // G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]   (double sums)
 __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
@@ -1257,13 +1209,6 @@ cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layou
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_Y(const Dims& d, int np, char* ws, const Layout& L, cudaStream_t s) {
-  DevHeader* hdr = (DevHeader*)(ws + L.header);
-  k_split_Y<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Y32), (long long)np * d.Ap * d.Ap,
-                                          hdr, (__half*)(ws + L.Yhi), (__half*)(ws + L.Ylo));
-  count_launch(1);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
                               cudaStream_t s) {
@@ -1391,18 +1336,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
   prof_begin(DONOF_PHASE_JK_Y, s);
-  if (cudaMemsetAsync(ws + L.ssqY, 0, (size_t)splits3 * Ap * sizeof(float), s) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  if (launch_jky_f32(d, (const float*)(ws + L.b32), (float*)(ws + L.Y32), np, ws, L, s) !=
-      cudaSuccess)
-    return DONOF_ERR_CUDA;
-  k_y_exponents<<<num_sms(), 256, 0, s>>>((const float*)(ws + L.ssqY), splits3 * Ap,
-                                          (int*)(ws + L.eY));
-  k_quant_Y<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Y32), np, Ap,
-                                          (const int*)(ws + L.spOf), (const int*)(ws + L.eY),
-                                          (__half*)(ws + L.Yhi), (__half*)(ws + L.Ylo), hdr);
-  count_launch(2);
-  if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
+  if (launch_mid_mixed(d, np, splits3, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
   prof_end(DONOF_PHASE_JK_Y, s);
   // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]  (integer + fraction operands, exponents
   //     common to the slices of a split)
