@@ -100,6 +100,31 @@ __device__ inline void set_status(DevHeader* h, int code) {
   atomicCAS(&h->status, 0, code);
 }
 
+// Integer + fraction split of the tensor-core operands.  A vector x of K elements is
+// 2^e (h + f) with y = x / 2^e, h = rint(y) rounded to fp16 (exact up to 2048, even
+// integers up to 4096) and f = fp16(y - h).  e is the smallest exponent with
+// ||y||_2 < T = 2^12 - sqrt(K)/2 - 2: then at most three elements exceed 2048, so
+// |h - y| <= 1/2 elementwise except there (<= 3/2), ||h - y||_2 <= sqrt(K)/2 + 2 and
+// ||h||_2 < 2^12.  For two such vectors every partial sum of h_a h_b is an integer below
+// 2^24 in magnitude (Cauchy-Schwarz), so the integer products accumulate exactly in fp32.
+// `nrm` must bound ||x||_2.
+__host__ __device__ inline int intfrac_exponent(double nrm, double K) {
+  if (!(nrm > 0.0)) return 0;
+  double T = 4096.0 - 0.5 * sqrt(K) - 2.0;
+  if (T < 1024.0) T = 1024.0;  // K above 3.7e7: exactness no longer guaranteed, values still
+  int e;                       // represented to within the fp16 fraction
+  frexp(nrm / T, &e);  // nrm / T < 2^e, and >= 2^(e-1)
+  return e;
+}
+__device__ inline void intfrac_split(double y, __half& h, __half& f) {
+  h = __double2half(rint(y));
+  f = __double2half(y - (double)__half2float(h));
+}
+__device__ inline void intfrac_split(float y, __half& h, __half& f) {
+  h = __float2half_rn(rintf(y));
+  f = __float2half_rn(y - __half2float(h));  // exact difference: |y| < 4096
+}
+
 // Exponent s such that |x| * 2^s < 2^14 for |x| <= bound (bound > 0); 0 for bound == 0.
 __host__ __device__ inline int split_exponent(double bound) {
   if (!(bound > 0.0)) return 0;

@@ -21,13 +21,6 @@ __device__ __forceinline__ float pow2f_m(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-__host__ __device__ inline int intfrac_exp(double nrm) {
-  if (!(nrm > 0.0)) return 0;
-  int e;
-  frexp(nrm, &e);
-  return e - 11;
-}
-
 // fp32 copies of the coefficient matrices, [Ap][Ap] with zero padding
 __global__ void k_coef_f32(const double* __restrict__ Ac, const double* __restrict__ Bc, int A,
                            int Ap, float* AcF, float* BcF) {
@@ -152,7 +145,9 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
       }
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) eY[t] = intfrac_exp(sqrt(fmax(ss, 0.0)) * (1.0 + 1e-6));
+    // row length of the G contraction over this split: (slices in it) x Ap
+    const double Kc = (double)(np * (sp + 1LL) / splits - np * (long long)sp / splits) * Ap;
+    if (lane == 0) eY[t] = intfrac_exponent(sqrt(fmax(ss, 0.0)) * (1.0 + 1e-6), Kc);
   }
 }
 
@@ -180,10 +175,7 @@ __global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__
     __align__(8) __half h[4], fr[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float x = y[j] * sc;
-      const float hv = rintf(x);
-      h[j] = __float2half_rn(hv);
-      fr[j] = __float2half_rn(x - hv);
+      intfrac_split(y[j] * sc, h[j], fr[j]);
     }
     *(uint2*)(H + i4 * 4) = *(uint2*)h;
     *(uint2*)(F + i4 * 4) = *(uint2*)fr;

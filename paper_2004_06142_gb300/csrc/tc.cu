@@ -201,12 +201,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // Operand numerics.
 //   kSplit3: every operand x is s * (hi + lo), hi = fp16(x / s), lo = fp16(x / s - hi), with one
 //            power-of-two s per matrix; D = hi*hi + hi*lo + lo*hi in one fp32 accumulator.
-//   kIntFrac: every operand row r is u_r * (h + f) with u_r = 2^e_r chosen from the row's
-//            L2 norm so that ||h||_2 < 2^12, h integer (|h| <= 2048, exact in fp16) and
-//            f = fp16(x / u_r - h) in [-1/2, 1/2].  For any two rows |sum_k h_a h_b| < 2^24
-//            (Cauchy-Schwarz, every partial sum included), so the integer products
+//   kIntFrac: every operand row r is u_r * (h + f) with u_r = 2^e_r chosen from (a bound on)
+//            the row's L2 norm so that ||h||_2 < 2^12 (intfrac_exponent), h an integer
+//            exact in fp16 and f = fp16(x / u_r - h).  For any two rows |sum_k h_a h_b| <
+//            2^24 (Cauchy-Schwarz, every partial sum included), so the integer products
 //            accumulate exactly in fp32 -- the tensor core's truncating accumulation
 //            cannot bias them.  h*h goes to accumulator 0, h*f + f*h + f*f to accumulator 1.
+//            The representation error is about 2^-13 u_r per element, so the norm target
+//            is kept as close to 2^12 as the rounding of h allows.
 constexpr int kSplit3 = 0;
 constexpr int kIntFrac = 1;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
@@ -562,18 +564,13 @@ __global__ void __launch_bounds__(256, 1)
           const int* ex = exrow + c0;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float y = v[j] * pow2f(-ex[j]);
-            const float h = rintf(y);
-            args.xth[to + (size_t)j * args.Np] = __float2half_rn(h);
-            args.xtf[to + (size_t)j * args.Np] = __float2half_rn(y - h);
+            intfrac_split(v[j] * pow2f(-ex[j]), args.xth[to + (size_t)j * args.Np],
+                          args.xtf[to + (size_t)j * args.Np]);
           }
           __align__(16) __half hi[16], lo[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float w = v[j] * sx3;
-            const float h = rintf(w);
-            hi[j] = __float2half_rn(h);
-            lo[j] = __float2half_rn(w - h);
+            intfrac_split(v[j] * sx3, hi[j], lo[j]);
           }
           // X interleaved by 8 along c, [P][c/8][mu][8]: the lanes (consecutive mu) of one
           // store write 512 contiguous bytes
@@ -813,14 +810,6 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
-// Exponent e of the integer + fraction split of a row with L2 norm `nrm`: the row is
-// 2^e (h + f) with ||x / 2^e||_2 <= 2^11, so |h| <= 2048 and ||h||_2 < 2^12.
-__host__ __device__ inline int intfrac_exponent(double nrm) {
-  if (!(nrm > 0.0)) return 0;
-  int e;
-  frexp(nrm, &e);  // nrm <= 2^e
-  return e - 11;
-}
 
 __device__ inline double load_B_elem(const double* __restrict__ B, int layout, long long P,
                                      long long r, int mu, int nu, int N, long long npk) {
@@ -922,7 +911,7 @@ __global__ void k_sym_exps(const double* __restrict__ tmax, const int* __restric
   const long long tot = Q * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x)
-    eA[i] = intfrac_exponent(tmax[i / N]) + eS[i % N];
+    eA[i] = intfrac_exponent(tmax[i / N], N) + eS[i % N];
 }
 
 // Bt^P 2^-t_P -> integer + fraction planes in the lower-triangle tile storage (SymTiles).
@@ -951,7 +940,7 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
     if (tj > ti) continue;  // upper triangle: not stored
     const int r = mu - 128 * ti, c = kb - 2 * tj;
     const int Ri = sym_R(st, ti);
-    const int tP = intfrac_exponent(tmax[P]);
+    const int tP = intfrac_exponent(tmax[P], N);
     __align__(16) __half hv[8], fv[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -959,9 +948,7 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
       double y = 0.0;
       if (mu < N && nu < N)
         y = ldexp(load_B_elem(B, layout, P, P * N + mu, mu, nu, N, npk), -tP - eS[mu] - eS[nu]);
-      const double h = rint(y);
-      hv[k] = __double2half(h);
-      fv[k] = __double2half(y - h);
+      intfrac_split(y, hv[k], fv[k]);
     }
     const size_t o = (size_t)P * st.perP + sym_tile_off(st, ti, tj) +
                      ((size_t)c * Ri + r) * 64 + (size_t)((j8 ^ (r & 7)) * 8);
@@ -990,7 +977,7 @@ __global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap,
   if (lane == 0) {
     const double nr = sqrt(ss);
     if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
-    eC[q] = intfrac_exponent(nr);
+    eC[q] = intfrac_exponent(nr, N);
     if (!eS) {
       cnorm[q] = nr;
       atomicMax((unsigned long long*)&hdr->maxCcol_bits,
@@ -1014,7 +1001,7 @@ __global__ void k_colnorm_exp(const double* __restrict__ S, long long ld, int N,
       ss = fma(v, v, ss);
     }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if (lane == 0) e[c] = intfrac_exponent(sqrt(ss));
+  if (lane == 0) e[c] = intfrac_exponent(sqrt(ss), N);
 }
 
 __global__ void k_split_rows(const double* __restrict__ S, long long ld, int N, int ncols,
@@ -1025,10 +1012,7 @@ __global__ void k_split_rows(const double* __restrict__ S, long long ld, int N, 
        i += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(i / Np), mu = (int)(i % Np);
     const double v = (c < ncols && mu < N) ? S[(size_t)mu * ld + c] : 0.0;
-    const double y = ldexp(v, -e[c]);
-    const double h = rint(y);
-    H[i] = __double2half(h);
-    F[i] = __double2half(y - h);
+    intfrac_split(ldexp(v, -e[c]), H[i], F[i]);
   }
 }
 
@@ -1047,21 +1031,18 @@ __global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, in
        i += (long long)gridDim.x * blockDim.x) {
     const int p = (int)(i / Np), mu = (int)(i % Np);
     const double v = (p < A && mu < N) ? C[(size_t)mu * N + p] : 0.0;
-    const double y = ldexp(v, (eS && mu < N ? eS[mu] : 0) - eC[p]);
-    const double h = rint(y);
-    H[i] = __double2half(h);
-    F[i] = __double2half(y - h);
+    intfrac_split(ldexp(v, (eS && mu < N ? eS[mu] : 0) - eC[p]), H[i], F[i]);
   }
 }
 
 // Exponents of the integer + fraction split of X^T rows (P, q): ||X[P][:][q]||_2 =
 // ||B^P C_q||_2 <= ||B^P||_inf ||C_q||_2 (B^P symmetric, so ||B^P||_2 <= ||B^P||_inf).
 __global__ void k_xt_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
-                               int np, int Ap, int* eXt) {
+                               int np, int Ap, int N, int* eXt) {
   const long long tot = (long long)np * Ap;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x)
-    eXt[i] = intfrac_exponent(L1max[i / Ap] * cnorm[i % Ap]);
+    eXt[i] = intfrac_exponent(L1max[i / Ap] * cnorm[i % Ap], N);
 }
 
 // s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
@@ -1123,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
 }
 
 __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* hdr, int np,
-                               int splits, int N, int* spOf, int* eX3) {
+                               int splits, int N, int Ap, int* spOf, int* eX3) {
   const double sC2 = hdr->sC2;
   const long long tot = (long long)splits * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
@@ -1135,7 +1116,7 @@ __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* 
       r2 += rn2[(size_t)P * N + mu];
       if (mu == 0) spOf[P] = sp;
     }
-    eX3[i] = intfrac_exponent(sqrt(sC2 * r2) * (1.0 + 1e-12));
+    eX3[i] = intfrac_exponent(sqrt(sC2 * r2) * (1.0 + 1e-12), (double)(P1 - P0) * Ap);
   }
 }
 
@@ -1273,10 +1254,10 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   // (1) X = B C_act  (integer + fraction operands; exact integer products)
   const int splits3 = d.splits < np ? d.splits : np;  // splits of the G contraction
   k_xt_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.L1max) + p0,
-                                           (const double*)(ws + L.cnorm), np, Ap,
+                                           (const double*)(ws + L.cnorm), np, Ap, N,
                                            (int*)(ws + L.eXt));
   k_x3_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.rn2) + (size_t)p0 * N,
-                                           (const DevHeader*)hdr, np, splits3, N,
+                                           (const DevHeader*)hdr, np, splits3, N, Ap,
                                            (int*)(ws + L.spOf), (int*)(ws + L.eX3));
   count_launch(2);
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
