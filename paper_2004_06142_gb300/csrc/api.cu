@@ -99,7 +99,7 @@ Layout make_layout(const Dims& d) {
     L.ChiS = take(Ap * Np * 2);
     L.CloS = take(Ap * Np * 2);
     L.eCs = take(Ap * 4);
-    L.gram = take((N + 63) / 64 * A * A * 4);
+    L.gram = take((N + 31) / 32 * A * A * 4);  // chunks of 32 AO indices (k_gram_part)
     L.eB = take(Q * N * 4);
     L.L1max = take(Q * 8);
     L.Chi = take(Ap * Np * 2);

@@ -4,7 +4,7 @@
 //   Y^P_qp = Bcoef_qp b^P_qp + delta_qp w^P_p,   w^P_p = sum_r Acoef_pr d^P_r,  d^P_r = b^P_rr,
 // (the J and K coefficient matrices of E applied slice by slice, Eqs. Vee-s, Vee-d), without
 // materialising Y in fp32:
-//   k_diag_w   d^P and w^P per slice (fp32, a warp per output);
+//   k_diag_w   d^P and w^P per slice (fp32, 16 slices per CTA);
 //   k_kpart    per G split sp: Ksp_qp = sum_{P in sp} (b^P_qp)^2 and Jsp_qp = sum d^P_q d^P_p
 //              (fp32 groups of 16 slices, double across groups), b read once;
 //   k_jk_eY    K += sum_sp Ksp, J += sum_sp Jsp (double, fixed order), and the exponent of
@@ -33,27 +33,38 @@ __global__ void k_coef_f32(const double* __restrict__ Ac, const double* __restri
   }
 }
 
-// d^P (the diagonal of b^P) and w^P = Acoef d^P: one CTA per slice at a time, a warp per w_p
+// d^P (the diagonal of b^P) and w^P = Acoef d^P for a group of kDwSlices slices per CTA:
+// the group's d in shared memory, thread p forms w_p of every slice of the group (Acoef is
+// symmetric, so its column p is read, coalesced across threads).
+constexpr int kDwSlices = 16;
 __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ b, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
                                                 float* D, float* W) {
-  __shared__ float dv[256];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  for (int P = blockIdx.x; P < np; P += gridDim.x) {
-    const float* bp = b + (size_t)P * Ap * Ap;
-    for (int r = threadIdx.x; r < A; r += blockDim.x) {
-      const float v = bp[(size_t)r * Ap + r];
-      dv[r] = v;
-      D[(size_t)P * A + r] = v;
+  __shared__ float dv[kDwSlices][256];  // A <= 256
+  const int P0 = blockIdx.x * kDwSlices;
+  const int nP = min(kDwSlices, np - P0);
+  for (int t = threadIdx.x; t < kDwSlices * A; t += blockDim.x) {
+    const int sl = t / A, r = t % A;
+    float v = 0.f;
+    if (sl < nP) {
+      v = b[((size_t)(P0 + sl) * Ap + r) * Ap + r];
+      D[(size_t)(P0 + sl) * A + r] = v;
     }
-    __syncthreads();
-    for (int p = warp; p < A; p += blockDim.x / 32) {
-      float w = 0.f;
-      for (int r = lane; r < A; r += 32) w = fmaf(AcF[(size_t)p * Ap + r], dv[r], w);
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (lane == 0) W[(size_t)P * A + p] = w;
+    dv[sl][r] = v;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < A; p += blockDim.x) {
+    float w[kDwSlices];
+#pragma unroll
+    for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = 0.f;
+    for (int r = 0; r < A; ++r) {
+      const float a = AcF[(size_t)r * Ap + p];
+#pragma unroll
+      for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = fmaf(a, dv[sl][r], w[sl]);
     }
-    __syncthreads();
+#pragma unroll
+    for (int sl = 0; sl < kDwSlices; ++sl)
+      if (sl < nP) W[(size_t)(P0 + sl) * A + p] = w[sl];
   }
 }
 
@@ -114,7 +125,21 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
   if (blockIdx.y == 0) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < AA; i += gridDim.x * blockDim.x) {
       double k = 0.0, j = 0.0;
-      for (int sp = 0; sp < splits; ++sp) {
+      int sp = 0;
+      for (; sp + 8 <= splits; sp += 8) {  // eight splits in flight, summed in order
+        double kv[8], jv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          kv[u] = Ksp[(size_t)(sp + u) * AA + i];
+          jv[u] = Jsp[(size_t)(sp + u) * AA + i];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          k += kv[u];
+          j += jv[u];
+        }
+      }
+      for (; sp < splits; ++sp) {
         k += Ksp[(size_t)sp * AA + i];
         j += Jsp[(size_t)sp * AA + i];
       }
@@ -203,7 +228,7 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   float* W = (float*)(ws + L.W);
   const float* AcF = (const float*)(ws + L.AcF);
   const float* BcF = (const float*)(ws + L.BcF);
-  k_diag_w<<<sm_count() * 2, 256, 0, s>>>(b, np, A, Ap, AcF, D, W);
+  k_diag_w<<<(np + kDwSlices - 1) / kDwSlices, 256, 0, s>>>(b, np, A, Ap, AcF, D, W);
   const int n4 = A * (Ap / 4);
   k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),

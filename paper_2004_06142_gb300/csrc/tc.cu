@@ -1047,38 +1047,38 @@ __global__ void k_xt_exponents(const double* __restrict__ L1max, const double* _
 
 // s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
 // matrix, formed in fp32 with a relative safety margin of 1e-4 far above its rounding
-// error.  k_gram_part: one CTA per (row i, chunk of 64 AO indices mu), the chunk's part of
-// row i in a fixed order; k_gram_final: one CTA per row, the chunks summed in order.
-constexpr int kGramChunk = 64;
+// error.  k_gram_part: one CTA per (chunk of 32 AO indices mu, block of 16 rows i): the
+// chunk of C_act in shared memory (fp32), thread (i, j0) forms entries (i, j0 + 16 k) with
+// the chunk's mu in order; k_gram_final: one CTA per row, the chunks summed in order.
+constexpr int kGramChunk = 32;
 __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ C, int N, int A,
                                                    float* part) {
-  const int i = blockIdx.x, ch = blockIdx.y;
-  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  constexpr int kCols = 8;  // A <= 256
-  __shared__ float sp[8][256];
-  float g[kCols];
-#pragma unroll
-  for (int k = 0; k < kCols; ++k) g[k] = 0.f;
-  const int mu1 = min(N, (ch + 1) * kGramChunk);
-  for (int mu = ch * kGramChunk + w; mu < mu1; mu += 8) {
-    const double* Cm = C + (size_t)mu * N;
-    const float ci = (float)Cm[i];
-#pragma unroll
-    for (int k = 0; k < kCols; ++k) {
-      const int j = lane + 32 * k;
-      if (j < A) g[k] = fmaf(ci, (float)Cm[j], g[k]);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kCols; ++k) {
-    const int j = lane + 32 * k;
-    if (j < A) sp[w][j] = g[k];
+  __shared__ float cs[kGramChunk][256];  // A <= 256
+  const int ch = blockIdx.x, i0 = blockIdx.y * 16;
+  const int mu0 = ch * kGramChunk, nmu = min(kGramChunk, N - mu0);
+  for (int t = threadIdx.x; t < kGramChunk * A; t += blockDim.x) {
+    const int m = t / A, j = t % A;
+    cs[m][j] = m < nmu ? (float)C[(size_t)(mu0 + m) * N + j] : 0.f;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < A; j += blockDim.x) {
-    float t = 0.f;
-    for (int ww = 0; ww < 8; ++ww) t += sp[ww][j];
-    part[((size_t)ch * A + i) * A + j] = t;
+  const int i = i0 + threadIdx.x / 16, jl = threadIdx.x % 16;
+  if (i >= A) return;
+  float g[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) g[k] = 0.f;
+  for (int m = 0; m < kGramChunk; ++m) {
+    const float ci = cs[m][i];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int j = jl + 16 * k;
+      if (j < A) g[k] = fmaf(ci, cs[m][j], g[k]);
+    }
+  }
+  float* out = part + ((size_t)ch * A + i) * A;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = jl + 16 * k;
+    if (j < A) out[j] = g[k];
   }
 }
 
@@ -1112,10 +1112,17 @@ __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* 
     const int sp = (int)(i / N), mu = (int)(i % N);
     const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
     double r2 = 0.0;
-    for (int P = P0; P < P1; ++P) {
-      r2 += rn2[(size_t)P * N + mu];
-      if (mu == 0) spOf[P] = sp;
+    int P = P0;
+    for (; P + 8 <= P1; P += 8) {  // eight loads in flight, summed in order of P
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = rn2[(size_t)(P + u) * N + mu];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r2 += v[u];
     }
+    for (; P < P1; ++P) r2 += rn2[(size_t)P * N + mu];
+    if (mu == 0)
+      for (int Q = P0; Q < P1; ++Q) spOf[Q] = sp;
     eX3[i] = intfrac_exponent(sqrt(sC2 * r2) * (1.0 + 1e-12), (double)(P1 - P0) * Ap);
   }
 }
@@ -1123,18 +1130,44 @@ __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* 
 
 
 
-// G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]   (double sums)
+// G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]   (double sums in order of s; four consecutive p
+// per thread, eight partials in flight)
 __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
                            const DevHeader* hdr, double* G) {
   const double sc = ldexp(1.0, hdr->e3);
-  const long long tot = (long long)N * A;
+  const int r4 = Ap / 4;
+  const long long tot = (long long)N * r4;
+  const float4* G4 = (const float4*)Gp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long mu = i / A;
-    const int p = (int)(i % A);
-    double s = 0.0;
-    for (int k = 0; k < S; ++k) s += (double)Gp[((long long)k * N + mu) * Ap + p];
-    G[i] += sc * s;
+    const long long mu = i / r4;
+    const int p0 = (int)(i % r4) * 4;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 8 <= S; k += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = G4[(size_t)(k + u) * tot + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        s0 += v[u].x;
+        s1 += v[u].y;
+        s2 += v[u].z;
+        s3 += v[u].w;
+      }
+    }
+    for (; k < S; ++k) {
+      const float4 v = G4[(size_t)k * tot + i];
+      s0 += v.x;
+      s1 += v.y;
+      s2 += v.z;
+      s3 += v.w;
+    }
+    double* g = G + mu * A + p0;
+    const double sv[4] = {s0, s1, s2, s3};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (p0 + j < A) g[j] += sc * sv[j];
   }
 }
 
@@ -1198,14 +1231,15 @@ cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const La
   if (e != cudaSuccess) return e;
   const int nch = (d.N + kGramChunk - 1) / kGramChunk;
   float* part = (float*)(ws + L.gram);
-  k_gram_part<<<dim3(d.A, nch), 256, 0, s>>>(C, d.N, d.A, part);
+  k_gram_part<<<dim3(nch, (d.A + 15) / 16), 256, 0, s>>>(C, d.N, d.A, part);
   k_gram_final<<<d.A, 256, 0, s>>>(part, nch, d.A, hdr);
   count_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
-  k_reduce_G<<<num_sms() * 4, 256, 0, s>>>((const float*)(ws + L.Gpart), d.splits, d.N, d.A, d.Ap,
+  const int nb = (int)(((long long)d.N * (d.Ap / 4) + 255) / 256);
+  k_reduce_G<<<nb, 256, 0, s>>>((const float*)(ws + L.Gpart), d.splits, d.N, d.A, d.Ap,
                                            (const DevHeader*)(ws + L.header), (double*)(ws + L.G));
   count_launch(1);
   return cudaGetLastError();
