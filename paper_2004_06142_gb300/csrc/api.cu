@@ -47,11 +47,18 @@ Dims make_dims(const donof_problem* p) {
   if (pb > 65535) pb = 65535;  // batch index of the double GEMMs lives in gridDim.z
   d.pb = (int)pb;
   d.nblk = (d.Q + d.pb - 1) / d.pb;
-  // split-K of the G contraction: at most 32 slices per split, enough units for 2 waves
+  // split-K of the G contraction: at most 64 slices per split, enough units (row tiles x
+  // splits) for 2 waves over the 152 SMs, and where a few more splits make the units a
+  // whole number of waves, those
   const int mt = (d.N + 127) / 128;
-  int sp = (d.pb + 31) / 32;
+  int sp = (d.pb + 63) / 64;
   const int want = (2 * 152 + mt - 1) / mt;
   if (sp < want) sp = want;
+  for (int s2 = sp; s2 <= sp + sp / 4; ++s2)
+    if ((mt * s2) % 152 == 0) {
+      sp = s2;
+      break;
+    }
   if (sp > d.pb) sp = d.pb;
   d.splits = sp;
   return d;
