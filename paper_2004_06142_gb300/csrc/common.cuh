@@ -108,17 +108,46 @@ __device__ inline void set_status(DevHeader* h, int code) {
 // ||h||_2 < 2^12.  For two such vectors every partial sum of h_a h_b is an integer below
 // 2^24 in magnitude (Cauchy-Schwarz), so the integer products accumulate exactly in fp32.
 // `nrm` must bound ||x||_2.
-__host__ __device__ inline int intfrac_exponent(double nrm, double K) {
-  if (!(nrm > 0.0)) return 0;
+// 1/T rounded up (relative 2^-50), so that nrm * intfrac_inv_target(K) >= nrm / T after
+// rounding: the exponent below never comes out too small.  Computed once per launch (the
+// FP64 square root and division are slow on this GPU).
+__host__ __device__ inline double intfrac_inv_target(double K) {
   double T = 4096.0 - 0.5 * sqrt(K) - 2.0;
   if (T < 1024.0) T = 1024.0;  // K above 3.7e7: exactness no longer guaranteed, values still
-  int e;                       // represented to within the fp16 fraction
-  frexp(nrm / T, &e);  // nrm / T < 2^e, and >= 2^(e-1)
+                               // represented to within the fp16 fraction
+  return (1.0 / T) * (1.0 + 0x1p-50);
+}
+__host__ __device__ inline int intfrac_exponent_inv(double nrm, double invT) {
+  if (!(nrm > 0.0)) return 0;
+  int e;
+  frexp(nrm * invT, &e);  // nrm / T <= nrm * invT < 2^e
   return e;
 }
+__host__ __device__ inline int intfrac_exponent(double nrm, double K) {
+  return intfrac_exponent_inv(nrm, intfrac_inv_target(K));
+}
+// Exponent of a row from its squared norm, without the FP64 square root: the smallest e
+// with sqrt(nrm2) / T < 2^e, from x = nrm2 * invT2 (invT2 >= 1/T^2 after rounding):
+// x < 2^e2 gives sqrt(nrm2) / T <= sqrt(x) < 2^(e2/2) <= 2^ceil(e2/2).
+__host__ __device__ inline double intfrac_inv_target_sq(double K) {
+  const double i = intfrac_inv_target(K);
+  return (i * i) * (1.0 + 0x1p-50);
+}
+__host__ __device__ inline int intfrac_exponent_sq(double nrm2, double invT2) {
+  if (!(nrm2 > 0.0)) return 0;
+  int e2;
+  frexp(nrm2 * invT2, &e2);
+  return e2 >= 0 ? (e2 + 1) / 2 : -((-e2) / 2);  // ceil(e2 / 2)
+}
+// 2^e as a double, exact for -1022 <= e <= 1023 (the exponents here are far inside)
+__device__ inline double pow2d(int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
 __device__ inline void intfrac_split(double y, __half& h, __half& f) {
-  h = __double2half(rint(y));
-  f = __double2half(y - (double)__half2float(h));
+  const float hf = (float)rint(y);  // exact: |y| < 4096
+  h = __float2half_rn(hf);
+  f = __float2half_rn((float)(y - (double)__half2float(h)));
 }
 __device__ inline void intfrac_split(float y, __half& h, __half& f) {
   h = __float2half_rn(rintf(y));

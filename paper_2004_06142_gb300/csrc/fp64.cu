@@ -416,7 +416,7 @@ __global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const doub
   }
 }
 
-__global__ void __launch_bounds__(1024) k_energy_final(Dims d, const double* __restrict__ part,
+__global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __restrict__ part,
                                                        const double* __restrict__ dn,
                                                        const double* __restrict__ dsq,
                                                        const double* __restrict__ dphi,
@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(1024) k_energy_final(Dims d, const double* __r
   // one warp per output (E first, then each dE/dgamma_k), lanes over orbitals, a fixed
   // shuffle tree: the sums do not depend on scheduling
   const int A = d.A;
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int lane = threadIdx.x % 32, nw = gridDim.x * (blockDim.x / 32);
+  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const double* gn = part + A;
   const double* gs = part + 2 * A;
   const double* gp = part + 3 * A;
@@ -461,7 +462,7 @@ cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layo
       d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
       (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef), (const double*)(ws + L.Hd),
       (const double*)(ws + L.J), (const double*)(ws + L.K), part);
-  k_energy_final<<<1, 1024, 0, s>>>(d, part, (const double*)(ws + L.dn),
+  k_energy_final<<<(d.ng + 1 + 7) / 8, 256, 0, s>>>(d, part, (const double*)(ws + L.dn),
                                    (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
                                    (DevHeader*)(ws + L.header), (double*)(ws + L.dEdg), E_out,
                                    dEdg_out);

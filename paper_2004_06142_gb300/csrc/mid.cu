@@ -43,14 +43,25 @@ __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ b, int
   __shared__ float dv[kDwSlices][256];  // A <= 256
   const int P0 = blockIdx.x * kDwSlices;
   const int nP = min(kDwSlices, np - P0);
-  for (int t = threadIdx.x; t < kDwSlices * A; t += blockDim.x) {
-    const int sl = t / A, r = t % A;
-    float v = 0.f;
-    if (sl < nP) {
-      v = b[((size_t)(P0 + sl) * Ap + r) * Ap + r];
-      D[(size_t)(P0 + sl) * A + r] = v;
+  // the group's diagonal: slice sl = threadIdx.x / 16 (16 threads per slice), entries
+  // r = threadIdx.x % 16 + 16 k, all loads of a thread in flight together
+  {
+    const int sl = threadIdx.x / 16, r0 = threadIdx.x % 16;
+    constexpr int kMaxK = 16;  // A <= 256
+    float v[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+      const int r = r0 + 16 * k;
+      v[k] = (sl < nP && r < A) ? b[((size_t)(P0 + sl) * Ap + r) * Ap + r] : 0.f;
     }
-    dv[sl][r] = v;
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+      const int r = r0 + 16 * k;
+      if (r < A) {
+        dv[sl][r] = v[k];
+        if (sl < nP) D[(size_t)(P0 + sl) * A + r] = v[k];
+      }
+    }
   }
   __syncthreads();
   for (int p = threadIdx.x; p < A; p += blockDim.x) {
@@ -177,33 +188,32 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
 }
 
 // Y^P_rc = Bcoef_rc b^P_rc + delta_rc w^P_r -> integer + fraction planes with row exponent
-// eY[spOf[P]][r]; four consecutive entries of one row per thread.
+// eY[spOf[P]][r]: a CTA per slice at a time, thread (c4, y) handles four consecutive entries
+// of rows r = y, y + 8, ... (blockDim = (Ap / 4, 8)).
 __global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__ W,
                           const float* __restrict__ BcF, int np, int A, int Ap,
                           const int* __restrict__ spOf, const int* __restrict__ eY, __half* H,
                           __half* F, DevHeader* hdr) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->e3 = 0;  // G partials are in true units
-  const int r4 = Ap / 4;
-  const long long tot4 = (long long)np * Ap * r4;
-  const float4* b4 = (const float4*)b;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    hdr->e3 = 0;  // G partials are in true units
+  const int r4 = Ap / 4, c4 = threadIdx.x, c0 = 4 * c4;
   const float4* Bc4 = (const float4*)BcF;
-  for (long long i4 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i4 < tot4;
-       i4 += (long long)gridDim.x * blockDim.x) {
-    const long long row = i4 / r4;  // P * Ap + r
-    const int P = (int)(row / Ap), r = (int)(row % Ap);
-    const int c0 = (int)(i4 % r4) * 4;
-    const float sc = pow2f_m(-eY[(size_t)spOf[P] * Ap + r]);
-    const float4 v = b4[i4];
-    const float4 bc = Bc4[(size_t)r * r4 + c0 / 4];
-    float y[4] = {bc.x * v.x, bc.y * v.y, bc.z * v.z, bc.w * v.w};
-    if (r < A && r >= c0 && r < c0 + 4) y[r - c0] += W[(size_t)P * A + r];
-    __align__(8) __half h[4], fr[4];
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    const float4* b4 = (const float4*)b + (size_t)P * Ap * r4;
+    const int* eYs = eY + (size_t)spOf[P] * Ap;
+    for (int r = threadIdx.y; r < Ap; r += blockDim.y) {
+      const float sc = pow2f_m(-eYs[r]);
+      const float4 v = b4[(size_t)r * r4 + c4];
+      const float4 bc = Bc4[(size_t)r * r4 + c4];
+      float y[4] = {bc.x * v.x, bc.y * v.y, bc.z * v.z, bc.w * v.w};
+      if (r < A && r >= c0 && r < c0 + 4) y[r - c0] += W[(size_t)P * A + r];
+      __align__(8) __half h[4], fr[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      intfrac_split(y[j] * sc, h[j], fr[j]);
+      for (int j = 0; j < 4; ++j) intfrac_split(y[j] * sc, h[j], fr[j]);
+      const size_t o = ((size_t)P * Ap + r) * Ap + c0;
+      *(uint2*)(H + o) = *(uint2*)h;
+      *(uint2*)(F + o) = *(uint2*)fr;
     }
-    *(uint2*)(H + i4 * 4) = *(uint2*)h;
-    *(uint2*)(F + i4 * 4) = *(uint2*)fr;
   }
 }
 
@@ -233,13 +243,14 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),
                                                          (double*)(ws + L.Jsp));
-  k_jk_eY<<<dim3(sm_count(), 2), 256, 0, s>>>((const double*)(ws + L.Ksp),
+  const int ncta_e = (splits * Ap + 7) / 8;  // a warp per (split, row) of the exponents
+  k_jk_eY<<<dim3(ncta_e > sm_count() ? ncta_e : sm_count(), 2), 256, 0, s>>>((const double*)(ws + L.Ksp),
                                              (const double*)(ws + L.Jsp), D, W, BcF, np, A, Ap,
                                              splits, (double*)(ws + L.K), (double*)(ws + L.J),
                                              (int*)(ws + L.eY));
-  k_y_quant<<<sm_count() * 8, 256, 0, s>>>(b, W, BcF, np, A, Ap, (const int*)(ws + L.spOf),
-                                          (const int*)(ws + L.eY), (__half*)(ws + L.Yhi),
-                                          (__half*)(ws + L.Ylo), (DevHeader*)(ws + L.header));
+  k_y_quant<<<np < sm_count() * 8 ? np : sm_count() * 8, dim3(Ap / 4, 8), 0, s>>>(
+      b, W, BcF, np, A, Ap, (const int*)(ws + L.spOf), (const int*)(ws + L.eY),
+      (__half*)(ws + L.Yhi), (__half*)(ws + L.Ylo), (DevHeader*)(ws + L.header));
   count_launch(4);
   return cudaGetLastError();
 }

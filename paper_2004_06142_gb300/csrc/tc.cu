@@ -907,11 +907,11 @@ __global__ void k_p_scale(const double* __restrict__ B, int layout, long long Q,
 
 // eA[P][mu] = t_P + s_mu: the exponent of output row (P, mu) of the half transform.
 __global__ void k_sym_exps(const double* __restrict__ tmax, const int* __restrict__ eS,
-                           long long Q, int N, int* eA) {
+                           long long Q, int N, double invT, int* eA) {
   const long long tot = Q * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x)
-    eA[i] = intfrac_exponent(tmax[i / N], N) + eS[i % N];
+    eA[i] = intfrac_exponent_inv(tmax[i / N], invT) + eS[i % N];
 }
 
 // Bt^P 2^-t_P -> integer + fraction planes in the lower-triangle tile storage (SymTiles).
@@ -919,7 +919,8 @@ __global__ void k_sym_exps(const double* __restrict__ tmax, const int* __restric
 // tile padded to Rlast), 64-wide k block kb of a tile column not right of mu's tile.
 __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long long Q, int N,
                               SymTiles st, DevHeader* hdr, const int* __restrict__ eS,
-                              const double* __restrict__ tmax, __half* H, __half* F) {
+                              const double* __restrict__ tmax, double invT, __half* H,
+                              __half* F) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hdr->maxB = __longlong_as_double((long long)hdr->maxB_bits);
     hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
@@ -940,7 +941,7 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
     if (tj > ti) continue;  // upper triangle: not stored
     const int r = mu - 128 * ti, c = kb - 2 * tj;
     const int Ri = sym_R(st, ti);
-    const int tP = intfrac_exponent(tmax[P], N);
+    const int tP = intfrac_exponent_inv(tmax[P], invT);
     __align__(16) __half hv[8], fv[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -957,92 +958,91 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
   }
 }
 
-// Column norms of C_act -> exponents of the integer + fraction split of C_act^T (one warp
-// per column); max column norm for the bound on |X|.
-// With eS given, the columns of diag(2^s) C_act instead (the operand of the symmetric half
-// transform); cnorm and the header maximum are then not written.
-__global__ void k_c_norms(const double* __restrict__ C, int N, int A, int Ap,
-                          const int* __restrict__ eS, int* eC, double* cnorm, DevHeader* hdr) {
-  const int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x % 32;
-  if (q >= Ap) return;
+// Column norms of a double matrix S (N rows, leading dimension ld) -> exponents of the
+// integer + fraction split of S^T: e[c] for c < nrows_out (columns c >= ncols are zero).
+// With eS given, the columns of diag(2^s) S.  norm (optional) receives the norms.  A CTA
+// of 32 x 32 threads per 32 columns: thread (c, g) sums rows g, g + 32, ... (coalesced
+// across c), the 32 partial sums of a column are then added in order.
+__global__ void __launch_bounds__(1024) k_colnorms(const double* __restrict__ S, long long ld,
+                                                   int N, int ncols, int nrows_out,
+                                                   const int* __restrict__ eS, double invT,
+                                                   int* e, double* norm, DevHeader* hdr) {
+  __shared__ double red[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int c = blockIdx.x * 32 + tx;
   double ss = 0.0;
-  if (q < A)
-    for (int mu = lane; mu < N; mu += 32) {
-      double v = C[(size_t)mu * N + q];
-      if (eS) v = ldexp(v, eS[mu]);
+  if (c < ncols) {
+    int mu = ty;
+    for (; mu + 96 < N; mu += 128) {  // four loads in flight, summed in order of mu
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = S[(size_t)(mu + 32 * u) * ld + c];
+        if (eS) v[u] *= pow2d(eS[mu + 32 * u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ss = fma(v[u], v[u], ss);
+    }
+    for (; mu < N; mu += 32) {
+      double v = S[(size_t)mu * ld + c];
+      if (eS) v *= pow2d(eS[mu]);
       ss = fma(v, v, ss);
     }
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if (lane == 0) {
-    const double nr = sqrt(ss);
+  }
+  red[ty][tx] = ss;
+  __syncthreads();
+  if (ty == 0 && c < nrows_out) {
+    double t = 0.0;
+    for (int g = 0; g < 32; ++g) t += red[g][tx];
+    const double nr = sqrt(t);
     if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
-    eC[q] = intfrac_exponent(nr, N);
-    if (!eS) {
-      cnorm[q] = nr;
-      atomicMax((unsigned long long*)&hdr->maxCcol_bits,
-                (unsigned long long)__double_as_longlong(nr));
-    }
+    e[c] = intfrac_exponent_inv(nr, invT);
+    if (norm) norm[c] = nr;
   }
 }
 
-// Integer + fraction split of the transpose of a double matrix S (N rows, leading dimension
-// ld): output row c < nrows_out holds column c of S (zero for c >= ncols), exponent from
-// the column's L2 norm.  One warp per column for the norms.
-__global__ void k_colnorm_exp(const double* __restrict__ S, long long ld, int N, int ncols,
-                              int nrows_out, int* e) {
-  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x % 32;
-  if (c >= nrows_out) return;
-  double ss = 0.0;
-  if (c < ncols)
-    for (int mu = lane; mu < N; mu += 32) {
-      const double v = S[(size_t)mu * ld + c];
-      ss = fma(v, v, ss);
+// Integer + fraction split of S^T (S: N rows, leading dimension ld), written as rows
+// c < nrows_out of Np halves (zero for c >= ncols or mu >= N): element (c, mu) is
+// 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given).  32 x 32 tiles through
+// shared memory, so that both the reads and the writes are coalesced.
+__global__ void __launch_bounds__(256) k_split_T(const double* __restrict__ S, long long ld,
+                                                 int N, int ncols, int nrows_out, int Np,
+                                                 const int* __restrict__ eS,
+                                                 const int* __restrict__ e, __half* H,
+                                                 __half* F) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int mu0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int mu = mu0 + ty + 8 * j, c = c0 + tx;
+    double v = 0.0;
+    if (mu < N && c < ncols) {
+      v = S[(size_t)mu * ld + c];
+      if (eS) v *= pow2d(eS[mu]);
     }
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if (lane == 0) e[c] = intfrac_exponent(sqrt(ss), N);
-}
-
-__global__ void k_split_rows(const double* __restrict__ S, long long ld, int N, int ncols,
-                             int nrows_out, int Np, const int* __restrict__ e, __half* H,
-                             __half* F) {
-  const long long tot = (long long)nrows_out * Np;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / Np), mu = (int)(i % Np);
-    const double v = (c < ncols && mu < N) ? S[(size_t)mu * ld + c] : 0.0;
-    intfrac_split(ldexp(v, -e[c]), H[i], F[i]);
+    tile[ty + 8 * j][tx] = v;
   }
-}
-
-// Exponent of the hi/lo split of X used by the G contraction: |X| <= maxBrow * max ||C_q||.
-__global__ void k_c_finish(DevHeader* hdr) {
-  const double nc = __longlong_as_double((long long)hdr->maxCcol_bits);
-  hdr->sX = split_exponent(hdr->maxBrow * nc);
-}
-
-// C_act^T -> integer + fraction planes [Ap][Np] (rows q >= A and columns mu >= N zero).
-__global__ void k_split_C(const double* __restrict__ C, int N, int A, int Ap, int Np,
-                          const int* __restrict__ eS, const int* __restrict__ eC, __half* H,
-                          __half* F) {
-  const long long tot = (long long)Ap * Np;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(i / Np), mu = (int)(i % Np);
-    const double v = (p < A && mu < N) ? C[(size_t)mu * N + p] : 0.0;
-    intfrac_split(ldexp(v, (eS && mu < N ? eS[mu] : 0) - eC[p]), H[i], F[i]);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + ty + 8 * j, mu = mu0 + tx;
+    if (c < nrows_out && mu < Np) {
+      const size_t o = (size_t)c * Np + mu;
+      intfrac_split(tile[tx][ty + 8 * j] * pow2d(-e[c]), H[o], F[o]);
+    }
   }
 }
 
 // Exponents of the integer + fraction split of X^T rows (P, q): ||X[P][:][q]||_2 =
 // ||B^P C_q||_2 <= ||B^P||_inf ||C_q||_2 (B^P symmetric, so ||B^P||_2 <= ||B^P||_inf).
 __global__ void k_xt_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
-                               int np, int Ap, int N, int* eXt) {
-  const long long tot = (long long)np * Ap;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x)
-    eXt[i] = intfrac_exponent(L1max[i / Ap] * cnorm[i % Ap], N);
+                               int np, int Ap, double invT, int* eXt) {
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    const double l = L1max[P];
+    for (int q = threadIdx.x; q < Ap; q += blockDim.x)
+      eXt[(size_t)P * Ap + q] = intfrac_exponent_inv(l * cnorm[q], invT);
+  }
 }
 
 // s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
 }
 
 __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* hdr, int np,
-                               int splits, int N, int Ap, int* spOf, int* eX3) {
+                               int splits, int N, double invT2, int* spOf, int* eX3) {
   const double sC2 = hdr->sC2;
   const long long tot = (long long)splits * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
@@ -1123,15 +1123,16 @@ __global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* 
     for (; P < P1; ++P) r2 += rn2[(size_t)P * N + mu];
     if (mu == 0)
       for (int Q = P0; Q < P1; ++Q) spOf[Q] = sp;
-    eX3[i] = intfrac_exponent(sqrt(sC2 * r2) * (1.0 + 1e-12), (double)(P1 - P0) * Ap);
+    eX3[i] = intfrac_exponent_sq(sC2 * r2 * (1.0 + 1e-12), invT2);
   }
 }
 
 
 
 
-// G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]   (double sums in order of s; four consecutive p
-// per thread, eight partials in flight)
+// G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]: groups of eight partials summed in fp32 (the
+// FP64 pipe of this GPU is narrow), the groups in double, in order of s; four consecutive p
+// per thread.
 __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
                            const DevHeader* hdr, double* G) {
   const double sc = ldexp(1.0, hdr->e3);
@@ -1144,17 +1145,22 @@ __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, in
     const int p0 = (int)(i % r4) * 4;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int k = 0;
-    for (; k + 8 <= S; k += 8) {
+    for (; k + 8 <= S; k += 8) {  // groups of eight partials in fp32, double across groups
       float4 v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = G4[(size_t)(k + u) * tot + i];
+      float4 g = v[0];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        s0 += v[u].x;
-        s1 += v[u].y;
-        s2 += v[u].z;
-        s3 += v[u].w;
+      for (int u = 1; u < 8; ++u) {
+        g.x += v[u].x;
+        g.y += v[u].y;
+        g.z += v[u].z;
+        g.w += v[u].w;
       }
+      s0 += g.x;
+      s1 += g.y;
+      s2 += g.z;
+      s3 += g.w;
     }
     for (; k < S; ++k) {
       const float4 v = G4[(size_t)k * tot + i];
@@ -1194,11 +1200,12 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
                                           (unsigned long long*)(ws + L.tmax));
   k_sym_exps<<<num_sms() * 4, 256, 0, s>>>((const double*)(ws + L.tmax),
                                            (const int*)(ws + L.eS), d.Q, d.N,
-                                           (int*)(ws + L.eB));
+                                           intfrac_inv_target(d.N), (int*)(ws + L.eB));
   k_split_B_sym<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, sym_tiles(d.N), hdr,
                                               (const int*)(ws + L.eS),
                                               (const double*)(ws + L.tmax),
-                                              (__half*)(ws + L.Bhi), (__half*)(ws + L.Blo));
+                                              intfrac_inv_target(d.N), (__half*)(ws + L.Bhi),
+                                              (__half*)(ws + L.Blo));
   count_launch(5);
   return cudaGetLastError();
 }
@@ -1206,20 +1213,19 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
 cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
                            cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  cudaError_t e = cudaMemsetAsync(&hdr->maxCcol_bits, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
-                                           (double*)(ws + L.cnorm), hdr);
-  k_c_finish<<<1, 1, 0, s>>>(hdr);
-  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, nullptr, (const int*)(ws + L.eC),
-                                      (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
+  const double invT = intfrac_inv_target(d.N);
+  const dim3 gT((d.Np + 31) / 32, (d.Ap + 31) / 32);
+  k_colnorms<<<(d.Ap + 31) / 32, 1024, 0, s>>>(C, d.N, d.N, d.A, d.Ap, nullptr, invT,
+                                              (int*)(ws + L.eC), (double*)(ws + L.cnorm), hdr);
+  k_split_T<<<gT, 256, 0, s>>>(C, d.N, d.N, d.A, d.Ap, d.Np, nullptr, (const int*)(ws + L.eC),
+                               (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
   // diag(2^s) C_act for the symmetric half transform
   const int* eS = (const int*)(ws + L.eS);
-  k_c_norms<<<(d.Ap + 7) / 8, 256, 0, s>>>(C, d.N, d.A, d.Ap, eS, (int*)(ws + L.eCs), nullptr,
-                                           hdr);
-  k_split_C<<<num_sms(), 256, 0, s>>>(C, d.N, d.A, d.Ap, d.Np, eS, (const int*)(ws + L.eCs),
-                                      (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS));
-  count_launch(5);
+  k_colnorms<<<(d.Ap + 31) / 32, 1024, 0, s>>>(C, d.N, d.N, d.A, d.Ap, eS, invT,
+                                              (int*)(ws + L.eCs), nullptr, hdr);
+  k_split_T<<<gT, 256, 0, s>>>(C, d.N, d.N, d.A, d.Ap, d.Np, eS, (const int*)(ws + L.eCs),
+                               (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS));
+  count_launch(4);
   return cudaGetLastError();
 }
 
@@ -1252,12 +1258,17 @@ int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, dou
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
   const double* G = (const double*)(ws + L.G);
-  k_colnorm_exp<<<(N + 7) / 8, 256, 0, s>>>(C, N, N, N, N, (int*)(ws + L.eCf));
-  k_split_rows<<<num_sms() * 4, 256, 0, s>>>(C, N, N, N, N, Np, (const int*)(ws + L.eCf),
-                                             (__half*)(ws + L.CfH), (__half*)(ws + L.CfF));
-  k_colnorm_exp<<<(Ap + 7) / 8, 256, 0, s>>>(G, A, N, A, Ap, (int*)(ws + L.eG));
-  k_split_rows<<<num_sms(), 256, 0, s>>>(G, A, N, A, Ap, Np, (const int*)(ws + L.eG),
-                                         (__half*)(ws + L.GtH), (__half*)(ws + L.GtF));
+  const double invT = intfrac_inv_target(N);
+  k_colnorms<<<(N + 31) / 32, 1024, 0, s>>>(C, N, N, N, N, nullptr, invT, (int*)(ws + L.eCf),
+                                           nullptr, hdr);
+  k_split_T<<<dim3((Np + 31) / 32, (N + 31) / 32), 256, 0, s>>>(
+      C, N, N, N, N, Np, nullptr, (const int*)(ws + L.eCf), (__half*)(ws + L.CfH),
+      (__half*)(ws + L.CfF));
+  k_colnorms<<<(Ap + 31) / 32, 1024, 0, s>>>(G, A, N, A, Ap, nullptr, invT, (int*)(ws + L.eG),
+                                            nullptr, hdr);
+  k_split_T<<<dim3((Np + 31) / 32, (Ap + 31) / 32), 256, 0, s>>>(
+      G, A, N, A, Ap, Np, nullptr, (const int*)(ws + L.eG), (__half*)(ws + L.GtH),
+      (__half*)(ws + L.GtF));
   count_launch(4);
   if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
   CUtensorMap ah, al, bh, bl;
@@ -1287,12 +1298,14 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   const size_t h2 = sizeof(__half);
   // (1) X = B C_act  (integer + fraction operands; exact integer products)
   const int splits3 = d.splits < np ? d.splits : np;  // splits of the G contraction
-  k_xt_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.L1max) + p0,
-                                           (const double*)(ws + L.cnorm), np, Ap, N,
-                                           (int*)(ws + L.eXt));
-  k_x3_exponents<<<num_sms(), 256, 0, s>>>((const double*)(ws + L.rn2) + (size_t)p0 * N,
-                                           (const DevHeader*)hdr, np, splits3, N, Ap,
-                                           (int*)(ws + L.spOf), (int*)(ws + L.eX3));
+  k_xt_exponents<<<num_sms() * 8, 160, 0, s>>>((const double*)(ws + L.L1max) + p0,
+                                               (const double*)(ws + L.cnorm), np, Ap,
+                                               intfrac_inv_target(N), (int*)(ws + L.eXt));
+  // the G contraction's rows run over (slices of a split) x Ap: the largest split's length
+  const double invT2 = intfrac_inv_target_sq((double)((np + splits3 - 1) / splits3) * Ap);
+  k_x3_exponents<<<(splits3 * N + 255) / 256, 256, 0, s>>>(
+      (const double*)(ws + L.rn2) + (size_t)p0 * N, (const DevHeader*)hdr, np, splits3, N, invT2,
+      (int*)(ws + L.spOf), (int*)(ws + L.eX3));
   count_launch(2);
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
@@ -1316,7 +1329,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.a_tiled_h = Bh; a.a_tiled_f = Bl;
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eCs); a.eB_zstride = 0;
-    a.glob_exp = &hdr->sX;
+    a.glob_exp = &hdr->zero_exp;  // not applied in mode 1
     a.Nmu = N; a.Nrow = N; a.Ap = Ap; a.Np = Np;
     a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
