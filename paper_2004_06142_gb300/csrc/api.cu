@@ -241,7 +241,8 @@ DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long
                        long long sCn) {
   DgemmArgs a{};
   a.M = M; a.N = N; a.K = 64; a.KB = (K + 63) / 64; a.Ktot = K; a.batch = 1;
-  const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+  const int bn = dgemm_tile_n(N);
+  const long long tiles = (long long)((M + 63) / 64) * ((N + bn - 1) / bn);
   long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
   if (ks > a.KB) ks = a.KB;
   if (ks < 1) ks = 1;
@@ -379,7 +380,8 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
     {  // G[mu][p] += sum_P sum_q X[P][mu][q] Y[P][q][p]
       DgemmArgs a{};
       a.M = N; a.N = A; a.K = A; a.KB = np; a.batch = 1;
-      const long long tiles = (long long)((N + 63) / 64) * ((A + 63) / 64);
+      const int bn = dgemm_tile_n(A);
+      const long long tiles = (long long)((N + 63) / 64) * ((A + bn - 1) / bn);
       long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
       if (ks > np) ks = np;
       a.ksplit = (int)ks;

@@ -173,6 +173,8 @@ __host__ __device__ inline int split_exponent(double bound) {
 // ksplit > 1 splits the kb range over CTAs and accumulates with atomicAdd (beta must be 1).
 // Ktot > 0 limits the flattened contraction index kb*K + k to [0, Ktot) (used to split one
 // long contraction into KB chunks of K that ksplit CTAs share).
+// Output tile width of k_dgemm: 32 where it pads the width less than 64 does.
+inline int dgemm_tile_n(int N) { return (N + 31) / 32 * 32 < (N + 63) / 64 * 64 ? 32 : 64; }
 struct DgemmArgs {
   int M, N, K, KB, batch, ksplit, Ktot;
   const double* A; long long sAb, sAm, sAk, sAkb;

@@ -11,17 +11,20 @@
 namespace donof {
 
 // ---------------------------------------------------------------------------
-// Strided batched DGEMM, 64x64 output tile per CTA, 4x4 per thread, DFMA.
+// Strided batched DGEMM, 64 x BN output tile per CTA (BN = 64, or 32 for narrow outputs
+// whose width a 64 tile would pad by more), 4 x BN/16 per thread, DFMA.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int DBM = 64, DBN = 64, DBK = 16;
+constexpr int DBM = 64, DBK = 16;
 
+template <int BN>
 __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
+  constexpr int NJ = BN / 16;
   __shared__ double As[DBK][DBM + 1];
-  __shared__ double Bs[DBK][DBN + 1];
+  __shared__ double Bs[DBK][BN + 1];
   const int bz = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
   const long long m0 = (long long)blockIdx.x * DBM;
-  const int n0 = blockIdx.y * DBN;
+  const int n0 = blockIdx.y * BN;
   const double* A = a.A + (long long)bz * a.sAb;
   const double* B = a.B + (long long)bz * a.sBb;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -29,11 +32,11 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
   const bool b_n_fast = (a.sBn == 1);
   const int kb0 = (int)((long long)a.KB * ks / a.ksplit);
   const int kb1 = (int)((long long)a.KB * (ks + 1) / a.ksplit);
-  double acc[4][4];
+  double acc[4][NJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
 
   for (int kb = kb0; kb < kb1; ++kb) {
     const double* Akb = A + (long long)kb * a.sAkb;
@@ -48,25 +51,29 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
         const int gk = k0 + kk;
         const bool kin = gk < a.K && (a.Ktot <= 0 || kb * a.K + gk < a.Ktot);
         As[kk][mm] = (gm < a.M && kin) ? Akb[gm * a.sAm + (long long)gk * a.sAk] : 0.0;
-        int nn;
-        if (b_n_fast) { nn = idx % DBN; kk = idx / DBN; } else { kk = idx % DBK; nn = idx / DBK; }
+      }
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) {
+        const int idx = threadIdx.x + i * 256;
+        int nn, kk;
+        if (b_n_fast) { nn = idx % BN; kk = idx / BN; } else { kk = idx % DBK; nn = idx / DBK; }
         const int gn = n0 + nn;
-        const int gk2 = k0 + kk;
-        const bool kin2 = gk2 < a.K && (a.Ktot <= 0 || kb * a.K + gk2 < a.Ktot);
-        Bs[kk][nn] = (gn < a.N && kin2) ? Bkb[(long long)gk2 * a.sBk + (long long)gn * a.sBn] : 0.0;
+        const int gk = k0 + kk;
+        const bool kin = gk < a.K && (a.Ktot <= 0 || kb * a.K + gk < a.Ktot);
+        Bs[kk][nn] = (gn < a.N && kin) ? Bkb[(long long)gk * a.sBk + (long long)gn * a.sBn] : 0.0;
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < DBK; ++kk) {
-        double ra[4], rb[4];
+        double ra[4], rb[NJ];
 #pragma unroll
         for (int i = 0; i < 4; ++i) ra[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rb[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < NJ; ++j) rb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
+          for (int j = 0; j < NJ; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
     const long long gm = m0 + ty + 16 * i;
     if (gm >= a.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NJ; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= a.N) continue;
       double* c = C + gm * a.sCm + (long long)gn * a.sCn;
@@ -94,8 +101,14 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
 cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
   const long long mt = (a.M + DBM - 1) / DBM;
-  dim3 grid((unsigned)mt, (unsigned)((a.N + DBN - 1) / DBN), (unsigned)(a.batch * a.ksplit));
-  k_dgemm<<<grid, 256, 0, s>>>(a);
+  // the narrow tile where it pads the output width less (e.g. 150 -> 160 instead of 192)
+  const int bn = dgemm_tile_n(a.N);
+  const bool narrow = bn == 32;
+  dim3 grid((unsigned)mt, (unsigned)((a.N + bn - 1) / bn), (unsigned)(a.batch * a.ksplit));
+  if (narrow)
+    k_dgemm<32><<<grid, 256, 0, s>>>(a);
+  else
+    k_dgemm<64><<<grid, 256, 0, s>>>(a);
   count_launch(1);
   return cudaGetLastError();
 }
