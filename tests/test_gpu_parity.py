@@ -88,6 +88,36 @@ def test_mixed_path_few_aux():
     compare(out, ref, MIX_E, MIX_G, MIX_G, tol_jk=MIX_G)
 
 
+@pytest.mark.parametrize("shape", [(200, 400, 44, 3), (260, 520, 50, 4), (300, 600, 64, 3)],
+                         ids=["nact176", "nact250", "nact256"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wide_active_space(shape, precision):
+    """nact above 160 up to the mixed path's limit of 256 (padded width 176, 256 with padding
+    rows, 256 exactly): every tensor-core contraction then drains its accumulators 16 columns
+    at a time, and at 256 the two accumulators fill the tensor memory."""
+    nbf, naux, npair, ncwo = shape
+    prob = synth.Problem(nbf, naux, npair, ncwo, seed=7)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, pnof.PNOF7)
+    out = gpu_build(prob, d, precision, pnof.PNOF7)
+    tol = (F64_TOL, F64_TOL, F64_TOL) if precision == 0 else (MIX_E, MIX_G, MIX_G)
+    compare(out, ref, *tol)
+
+
+@pytest.mark.parametrize("shape", [(8, 1, 1, 1), (12, 3, 4, 2), (16, 2, 8, 1)],
+                         ids=["one_slice", "nact_eq_nbf", "no_inactive_two_slices"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_shapes(shape, precision):
+    """One auxiliary function; every orbital active (nact = nbf, no inactive orbitals)."""
+    nbf, naux, npair, ncwo = shape
+    prob = synth.Problem(nbf, naux, npair, ncwo, seed=8)
+    d = synth.generate(prob)
+    ref = oracle(prob, d, pnof.PNOF7)
+    out = gpu_build(prob, d, precision, pnof.PNOF7)
+    tol = (F64_TOL, F64_TOL, F64_TOL) if precision == 0 else (MIX_E, MIX_G, MIX_G)
+    compare(out, ref, *tol)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_packed_and_blocked(precision):
     """Packed B and a budget that streams P in several blocks (with a ragged last one)."""
