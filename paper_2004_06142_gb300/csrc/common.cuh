@@ -15,19 +15,12 @@ namespace donof {
 // Device-resident header at the start of every workspace.
 // ---------------------------------------------------------------------------
 struct DevHeader {
-  int32_t status;        // DONOF_OK or the first DONOF_ERR_* raised on the device
-  int32_t sB, sC, sX, sY;  // power-of-two exponents of the fp16 split operands
-  int32_t e1, e2, e3;    // output exponents of the three tensor-core contractions
-  double maxB;           // max |B|                      (set by prepare)
-  double maxBrow;        // max_P,mu ||B[P][mu][:]||_2   (set by prepare)
-  unsigned long long maxB_bits, maxBrow_bits;  // atomicMax scratch (double bits, >= 0)
-  unsigned long long maxCcol_bits;  // max column norm of C_act (double bits)
-  unsigned int maxY_bits;  // max |Y| of the current block (float bits)
-  int32_t zero_exp;       // always 0 (epilogue exponent of raw partial sums)
-  int32_t abort_flag;     // set when a bounded device wait gives up; cleared per build
-  int32_t pad1;
-  double E;              // energy of the last build
-  double sC2;            // bound on ||C_act||_2^2 (Gershgorin on C_act^T C_act)
+  int32_t status;      // DONOF_OK or the first DONOF_ERR_* raised on the device
+  int32_t e3;          // output exponent of the G split partials (0: true units)
+  int32_t zero_exp;    // always 0 (epilogue exponent of raw partial sums)
+  int32_t abort_flag;  // set when a bounded device wait gives up; cleared per build
+  double E;            // energy of the last build
+  double sC2;          // bound on ||C_act||_2^2 (Gershgorin on C_act^T C_act)
 };
 
 constexpr size_t kAlign = 256;
@@ -47,12 +40,14 @@ struct Layout {
   // shared by both precisions
   size_t n, sqn, phi, dn, dsq, dphi, Acoef, Bcoef, Hd, hC, J, K, G, dEdg, Epart;
   // FP64 path
-  size_t X64, b64, Y64, Bun, W64;
+  size_t X64, b64, Y64, Bun;
   // mixed path
-  // Bhi/Blo, Chi/Clo, Xthi/Xtlo hold integer + fraction planes, Xhi/Xlo and Yhi/Ylo
-  // hi/lo split planes; eB, eC, eXt are the per-row exponents of the former.
-  size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Y32, Yhi, Ylo,
-      Gpart, D, rn2, spOf, eX3, ssqY, eY, CfH, CfF, eCf, GtH, GtF, eG;
+  // integer + fraction planes (h, f) of the tensor-core operands and their per-row
+  // exponents: B (Bhi/Blo, eB), C_act^T (Chi/Clo, eC), X^T for b (Xthi/Xtlo, eXt), X for G
+  // (Xhi/Xlo, eX3 per split), Y (Yhi/Ylo, eY per split), C^T and G^T for lambda (CfH/CfF,
+  // eCf; GtH/GtF, eG)
+  size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Yhi, Ylo,
+      Gpart, D, rn2, spOf, eX3, eY, CfH, CfF, eCf, GtH, GtF, eG;
   // symmetric storage of the split B: per-AO scale exponents s, their source (max over P of
   // the row norms), per-slice maxima of the scaled row norms, and the split of
   // (diag 2^s C_act)^T that multiplies it

@@ -273,8 +273,8 @@ cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const L
 // Grid: x over (p, q), y over chunks of P.
 // ---------------------------------------------------------------------------
 namespace {
-template <typename T>
-__global__ void k_jk(Dims d, const T* __restrict__ b, int np, int ld, double* J, double* K) {
+__global__ void k_jk(Dims d, const double* __restrict__ b, int np, int ld, double* J,
+                     double* K) {
   const int A = d.A;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)A * A) return;
@@ -283,9 +283,9 @@ __global__ void k_jk(Dims d, const T* __restrict__ b, int np, int ld, double* J,
   const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
   double sj = 0.0, sk = 0.0;
   for (int P = P0; P < P1; ++P) {
-    const T* bp = b + (size_t)P * ld * ld;
-    const double dp = (double)bp[(size_t)p * ld + p], dq = (double)bp[(size_t)q * ld + q];
-    const double v = (double)bp[(size_t)p * ld + q];
+    const double* bp = b + (size_t)P * ld * ld;
+    const double dp = bp[(size_t)p * ld + p], dq = bp[(size_t)q * ld + q];
+    const double v = bp[(size_t)p * ld + q];
     sj = fma(dp, dq, sj);
     sk = fma(v, v, sk);
   }
@@ -296,43 +296,34 @@ __global__ void k_jk(Dims d, const T* __restrict__ b, int np, int ld, double* J,
 }
 }  // namespace
 
-template <typename T>
-static cudaError_t launch_jk_t(const Dims& d, const T* b, int np, int ld, char* ws,
-                               const Layout& L, cudaStream_t s) {
+cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
+                                     const Layout& L, cudaStream_t s) {
   const long long tot = (long long)d.A * d.A;
   const unsigned gx = (unsigned)((tot + 255) / 256);
   unsigned gy = (unsigned)((np + 31) / 32);
   const unsigned want = 152u * 8u;
   if (gx * gy > want) gy = want / gx > 0 ? want / gx : 1;
-  k_jk<T><<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
+  k_jk<<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
   count_launch(1);
   return cudaGetLastError();
-}
-cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
-                                     const Layout& L, cudaStream_t s) {
-  return launch_jk_t<double>(d, b, np, ld, ws, L, s);
 }
 // ---------------------------------------------------------------------------
 // Y^P[q][p] = Bcoef_qp b^P_qp + delta_qp w^P_p,  w^P_p = sum_r Acoef_pr b^P_rr.
 // G_p = n_p (hC)_p + sum_P X^P Y^P  is then (1/4) dE/dC (Eqs. lowdin, Vee-s, Vee-d).
 // One CTA per auxiliary slice; ld = leading dimension of b and Y (A or Ap), padding
-// entries (q or p >= A) are written as zero.  The float variant also records max |Y|.
+// entries (q or p >= A) are written as zero.
 // ---------------------------------------------------------------------------
 namespace {
-template <typename T>
-__global__ void k_build_Y(Dims d, const T* __restrict__ b, T* Y, int np, int ld,
-                          const double* __restrict__ Ac, const double* __restrict__ Bc,
-                          DevHeader* hdr) {
+__global__ void k_build_Y(Dims d, const double* __restrict__ b, double* Y, int np, int ld,
+                          const double* __restrict__ Ac, const double* __restrict__ Bc) {
   extern __shared__ double sh[];  // d[ld], w[ld]
   double* dv = sh;
   double* wv = sh + ld;
-  __shared__ float red[32];
   const int A = d.A;
-  float ymax = 0.f;
   for (int P = blockIdx.x; P < np; P += gridDim.x) {
-    const T* bp = b + (size_t)P * ld * ld;
-    T* yp = Y + (size_t)P * ld * ld;
-    for (int r = threadIdx.x; r < A; r += blockDim.x) dv[r] = (double)bp[(size_t)r * ld + r];
+    const double* bp = b + (size_t)P * ld * ld;
+    double* yp = Y + (size_t)P * ld * ld;
+    for (int r = threadIdx.x; r < A; r += blockDim.x) dv[r] = bp[(size_t)r * ld + r];
     __syncthreads();
     for (int p = threadIdx.x; p < A; p += blockDim.x) {
       double w = 0.0;
@@ -344,23 +335,12 @@ __global__ void k_build_Y(Dims d, const T* __restrict__ b, T* Y, int np, int ld,
       const int q = i / ld, p = i % ld;
       double v = 0.0;
       if (q < A && p < A) {
-        v = Bc[(size_t)q * A + p] * (double)bp[i];
+        v = Bc[(size_t)q * A + p] * bp[i];
         if (q == p) v += wv[p];
       }
-      yp[i] = (T)v;
-      ymax = fmaxf(ymax, fabsf((float)v));
+      yp[i] = v;
     }
     __syncthreads();
-  }
-  if (sizeof(T) == 4) {
-    for (int o = 16; o > 0; o >>= 1) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
-    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = ymax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float m = 0.f;
-      for (int i = 0; i < (int)blockDim.x / 32; ++i) m = fmaxf(m, red[i]);
-      atomicMax(&hdr->maxY_bits, __float_as_uint(m));
-    }
   }
 }
 }  // namespace
@@ -368,9 +348,8 @@ __global__ void k_build_Y(Dims d, const T* __restrict__ b, T* Y, int np, int ld,
 cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np, char* ws,
                                const Layout& L, cudaStream_t s) {
   const int grid = np < 152 * 4 ? np : 152 * 4;
-  k_build_Y<double><<<grid, 256, 2 * d.A * sizeof(double), s>>>(
-      d, b, Y, np, d.A, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef),
-      (DevHeader*)(ws + L.header));
+  k_build_Y<<<grid, 256, 2 * d.A * sizeof(double), s>>>(
+      d, b, Y, np, d.A, (const double*)(ws + L.Acoef), (const double*)(ws + L.Bcoef));
   count_launch(1);
   return cudaGetLastError();
 }

@@ -1,20 +1,23 @@
 // Tensor-core (tcgen05 + TMEM + TMA) contractions of the mixed-precision build.
 //
-// The three large contractions of one build (DF form of Eqs. JKpq / Gpmn and of the
-// orbital gradient of Eqs. lowdin, Vee-s, Vee-d):
-//   (1) X[P][mu][q] = sum_nu B[P][mu][nu] C[nu][q]         M = np*N, N = Ap, K = N
-//   (2) b[P][p][q]  = sum_mu C[mu][p] X[P][mu][q]          per P: M = Ap, N = Ap, K = N
+// The large contractions of one build (DF form of Eqs. JKpq / Gpmn and of the orbital
+// gradient of Eqs. lowdin, Vee-s, Vee-d), all on one warp-specialised kernel:
+//   (1) X[P][mu][q] = sum_nu B[P][mu][nu] C[nu][q]    unit = (slice, 128-row tile); A from
+//       the lower-triangle tile storage of the split B (B symmetric), N = Ap, K = N
+//   (2) b[P][p][q]  = sum_mu C[mu][p] X[P][mu][q]     M = np*Ap (rows (P, q)), N = Ap, K = N
 //   (3) G[mu][p]   += sum_P sum_q X[P][mu][q] Y[P][q][p]   M = N, N = Ap, K = np*Ap (split)
-// run on one kernel: D = A_hi B_hi + A_hi B_lo + A_lo B_hi, where every operand is an
-// fp16 hi/lo pair of a power-of-two-scaled double or float (error-free splitting in
-// the spirit of the published "3xTF32" / Ozaki splitting; fp16 keeps 11+11 bits), with
-// fp32 accumulation in tensor memory.  Both operands are K-major and staged by TMA with
-// 128-byte (BK = 64) or 64-byte (BK = 32) swizzling.
+//   (4) lambda[q][p] = sum_mu C[mu][q] G[mu][p]       M = N, N = Ap, K = N
+// Operands are integer + fraction pairs (kIntFrac below): four products per K step, the
+// integer products exact in one TMEM accumulator, the others in a second, fp32.  A and B
+// are staged by TMA (or bulk copies for the tile storage of B) with 128-byte (BK = 64) or
+// 64-byte (BK = 32) swizzling; A may also be MN-major (transposed tiles of B) or K-major
+// interleaved by 8 (X in the G contraction).
 //
 // CTA roles (256 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma,
 // warp 2 owns the TMEM allocation, warps 4..7 drain the accumulator (one TMEM lane per
-// thread).  Two accumulators in TMEM let the epilogue of one tile overlap the MMAs of the
-// next.  Persistent grid: one CTA per SM, tiles handed out round-robin.
+// thread).  When two accumulator sets fit in TMEM the epilogue of one tile overlaps the
+// MMAs of the next; otherwise the epilogue releases TMEM as soon as the accumulators are
+// in registers.  Persistent grid: one CTA per SM, units handed out round-robin.
 #include <cuda.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -200,7 +203,8 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // ------------------------------------------------------------------ kernel
 // Operand numerics.
 //   kSplit3: every operand x is s * (hi + lo), hi = fp16(x / s), lo = fp16(x / s - hi), with one
-//            power-of-two s per matrix; D = hi*hi + hi*lo + lo*hi in one fp32 accumulator.
+//            power-of-two s per matrix; D = hi*hi + hi*lo + lo*hi in one fp32 accumulator
+//            (the building block exposed by the test hook; the build itself uses kIntFrac).
 //   kIntFrac: every operand row r is u_r * (h + f) with u_r = 2^e_r chosen from (a bound on)
 //            the row's L2 norm so that ||h||_2 < 2^12 (intfrac_exponent), h an integer
 //            exact in fp16 and f = fp16(x / u_r - h).  For any two rows |sum_k h_a h_b| <
@@ -214,7 +218,7 @@ constexpr int kIntFrac = 1;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
 
 struct TcArgs {
-  int mode;        // 1: X store (fp32 + hi/lo split for the G contraction); 2: fp32 store
+  int mode;        // 1: X stores (integer + fraction X^T for b, X for G); 2: fp32; 3: double
   int M;           // valid output rows per z
   int Nn;          // output columns = B box rows (multiple of 16, <= 256)
   int m_tiles, z_count, splits;
@@ -229,8 +233,7 @@ struct TcArgs {
   // eA indexed by z * eA_zstride + split * eA_sstride + row (eB likewise by column)
   const int* eA; long long eA_zstride, eA_sstride;
   const int* eB; long long eB_zstride, eB_sstride;
-  const int* glob_exp;  // extra power of two applied to every output (mode 2), or the
-                        // exponent of the hi/lo split written for the G contraction (mode 1)
+  const int* glob_exp;  // extra power of two applied to every output (modes 2 and 3)
   // A operand from pre-tiled planes (BK = 64 only): the tile of rows [r0, r0 + 128) and
   // k block kb is the contiguous run of rows x 128 bytes at a_tiled + kb * a_kb_stride +
   // r0 * 64, already in the 128-byte swizzled order; a partial last row block is copied
@@ -818,8 +821,10 @@ __device__ inline double load_B_elem(const double* __restrict__ B, int layout, l
   return B[P * npk + (long long)a * (a + 1) / 2 + b];
 }
 
-// Per row (P, mu): norm -> exponent of its integer + fraction split; global max |B| and
-// max row norm (the latter bounds |X| for the hi/lo split of the G contraction).
+// Per row (P, mu) of B: its squared L2 norm (rn2, for the exponents of X in the G
+// contraction), the slice's largest row L1 norm (L1max, the bound on X^T rows) and the AO
+// index's largest row norm over the slices (rnmax, for the symmetric scaling); any
+// non-finite element raises DONOF_ERR_NONFINITE.
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
                           DevHeader* hdr, unsigned long long* L1max_bits, double* rn2,
                           unsigned long long* rnmax_bits) {
@@ -854,8 +859,6 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
   }
   if (lane == 0) {
     if (!isfinite(mx) || !isfinite(mr)) set_status(hdr, DONOF_ERR_NONFINITE);
-    atomic_max_nonneg(&hdr->maxB_bits, mx);
-    atomic_max_nonneg(&hdr->maxBrow_bits, mr);
   }
 }
 
@@ -921,10 +924,6 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
                               SymTiles st, DevHeader* hdr, const int* __restrict__ eS,
                               const double* __restrict__ tmax, double invT, __half* H,
                               __half* F) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    hdr->maxB = __longlong_as_double((long long)hdr->maxB_bits);
-    hdr->maxBrow = __longlong_as_double((long long)hdr->maxBrow_bits);
-  }
   const long long npk = (long long)N * (N + 1) / 2;
   const int rows = 128 * (st.T - 1) + st.Rlast;  // stored rows (= columns) per slice
   const int KB = rows / 64;
@@ -1183,9 +1182,7 @@ __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, in
 cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, const Layout& L,
                                    cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  cudaError_t e = cudaMemsetAsync(&hdr->maxB_bits, 0, 2 * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(ws + L.L1max, 0, (size_t)d.Q * sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(ws + L.L1max, 0, (size_t)d.Q * sizeof(double), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(ws + L.rnmax, 0, (size_t)d.N * sizeof(double), s);
   if (e != cudaSuccess) return e;
