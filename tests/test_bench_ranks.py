@@ -1,0 +1,43 @@
+"""The multi-process side of bench.py on CPU (world size 2, gloo): the job's time is the
+slowest rank's, the rate counts every rank's builds, and a single process needs no group."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as tdist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        ms = [12.5, 20.0][rank]
+        m = bench.max_over_ranks(ms, ws, torch.device("cpu"))
+        out[rank] = (m, bench.job_rate(m, ws))
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_clock():
+    ws, port = 2, _free_port()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
+    for r in range(ws):
+        m, rate = out[r]
+        assert m == 20.0
+        assert rate == pytest.approx(2 * 1e3 / 20.0)
+
+
+def test_single_process_needs_no_group():
+    assert bench.max_over_ranks(7.0, 1, torch.device("cpu")) == 7.0
+    assert bench.job_rate(8.0, 1) == pytest.approx(125.0)
