@@ -10,10 +10,12 @@
 // One CTA runs the whole optimisation: projected L-BFGS (memory kMem, two-loop recursion
 // on the free variables, initial inverse-Hessian scale s.y / y.y) with a backtracking
 // line search on the Armijo condition along the projected path; converged when the
-// projected gradient is below gtol.  Each evaluation of E and dE/dgamma is a block-wide pass: occupations per
-// orbital (Eqs. soo, woo), the energy rows and the partials dE/dn, dE/dsqrt n, dE/dPhi per
-// orbital (one warp each), then the chain rule per pair (one thread each, over the pair's
-// members in index order, so the result does not depend on thread scheduling).
+// projected gradient is below gtol.  Each evaluation of E and dE/dgamma is a block-wide
+// pass: occupations per orbital (Eqs. soo, woo), the energy rows and the partials dE/dn,
+// dE/dsqrt n, dE/dPhi per orbital (one warp each, from three matrix-vector products with J
+// and K and a correction over the orbital's own subspace), then the chain rule per pair
+// (one thread each, over the pair's members in index order, so the result does not depend
+// on thread scheduling).
 #include "common.cuh"
 #include "occ.cuh"
 
@@ -34,6 +36,9 @@ struct OccCtx {
   const double* Hd;
   // shared memory
   int* rank;
+  int* mem;     // members of subspace g at mem[g * msz + k], k < cnt[g], in index order
+  int* cnt;
+  int msz;      // 1 + ncwo
   double *n, *sqn, *phi, *en, *es, *ep, *epart;
   double* red;  // kWarps + 1 words
 };
@@ -89,51 +94,64 @@ __device__ double evaluate(const OccCtx& c, const double* x, double* grad) {
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  for (int p = warp; p < A; p += kWarps) {
+  // Row p of E and the partials dE/dn_p, dE/dsqrt n_p, dE/dPhi_p (one thread per row): the
+  // different-subspace form summed over every q by three matrix-vector products,
+  //   u = J n, v = K n, w = K Phi (PNOF7) or K Phi^2 (PNOF7s),
+  // then the few q of p's own subspace moved from that form to the intra-subspace one
+  // (coefficients as in pair_coefficients).  J and K are symmetric, so row p is read as
+  // column p: consecutive threads read consecutive words.
+  const bool f7 = c.functional == DONOF_PNOF7, f7s = c.functional == DONOF_PNOF7S;
+  for (int p = threadIdx.x; p < A; p += kThreads) {
+    double u = 0.0, v = 0.0, w = 0.0;
+#pragma unroll 4
+    for (int q = 0; q < A; ++q) {
+      const double jqp = c.J[(size_t)q * A + p], kqp = c.K[(size_t)q * A + p], nq = c.n[q];
+      u = fma(jqp, nq, u);
+      v = fma(kqp, nq, v);
+      if (f7) w = fma(kqp, c.phi[q], w);
+      else if (f7s) w = fma(kqp, c.phi[q] * c.phi[q], w);
+    }
+    const double* Jp = c.J + (size_t)p * A;
+    const double* Kp = c.K + (size_t)p * A;
     const int g = c.pm[p];
-    double e = 0.0, a_n = 0.0, a_s = 0.0, a_p = 0.0, a_7s = 0.0;
-    for (int q = lane; q < A; q += 32) {
-      const size_t o = (size_t)p * A + q;
-      const double kpq = c.K[o], jpq = c.J[o];
-      const bool same = c.pm[q] == g;
-      double a, b;
-      pair_coefficients(c.functional, c.npair, p, q, same, g >= c.npair, c.n[p], c.n[q],
-                        c.sqn[p], c.sqn[q], c.phi[p], c.phi[q], a, b);
-      e += a * jpq + b * kpq;
-      if (same && g < c.npair) {
+    const bool single = g >= c.npair;
+    const double np_ = c.n[p], sp = c.sqn[p], fp = c.phi[p];
+    double e = 2.0 * np_ * u - np_ * v;
+    double a_n = 2.0 * (2.0 * u - v), a_s = 0.0, a_p = -2.0 * w, a_7s = w;
+    if (f7) e -= fp * w;
+    else if (f7s) e -= 4.0 * fp * fp * w;
+    for (int k = 0; k < c.cnt[g]; ++k) {
+      const int q = c.mem[g * c.msz + k];
+      const double jpq = Jp[q], kpq = Kp[q];
+      const double nq = c.n[q], sq = c.sqn[q], fq = c.phi[q];
+      e -= 2.0 * np_ * nq * jpq - np_ * nq * kpq;
+      if (f7) e += fp * fq * kpq;
+      else if (f7s) e += 4.0 * fp * fp * fq * fq * kpq;
+      a_n -= 2.0 * nq * (2.0 * jpq - kpq);
+      a_p += 2.0 * fq * kpq;
+      a_7s -= fq * fq * kpq;
+      if (!single) {
         const bool plus = (p == q || (p >= c.npair && q >= c.npair));
-        a_s += (plus ? 2.0 : -2.0) * c.sqn[q] * kpq;
-      } else if (!same) {
-        a_n += 2.0 * c.n[q] * (2.0 * jpq - kpq);
-        a_p -= 2.0 * c.phi[q] * kpq;
-        a_7s += c.phi[q] * c.phi[q] * kpq;
+        e += (plus ? 1.0 : -1.0) * sp * sq * kpq;
+        a_s += (plus ? 2.0 : -2.0) * sq * kpq;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      e += __shfl_xor_sync(0xffffffffu, e, o);
-      a_n += __shfl_xor_sync(0xffffffffu, a_n, o);
-      a_s += __shfl_xor_sync(0xffffffffu, a_s, o);
-      a_p += __shfl_xor_sync(0xffffffffu, a_p, o);
-      a_7s += __shfl_xor_sync(0xffffffffu, a_7s, o);
-    }
-    if (lane == 0) {
-      a_n += 2.0 * c.Hd[p];
-      if (c.functional == DONOF_PNOF7S) a_n -= 8.0 * (1.0 - 2.0 * c.n[p]) * a_7s;
-      c.epart[p] = e + 2.0 * c.n[p] * c.Hd[p];
-      c.en[p] = a_n;
-      c.es[p] = a_s;
-      c.ep[p] = (c.functional == DONOF_PNOF7) ? a_p : 0.0;
-    }
+    a_n += 2.0 * c.Hd[p];
+    if (f7s) a_n -= 8.0 * (1.0 - 2.0 * np_) * a_7s;
+    c.epart[p] = e + 2.0 * np_ * c.Hd[p];
+    c.en[p] = a_n;
+    c.es[p] = a_s;
+    c.ep[p] = f7 ? a_p : 0.0;
   }
   __syncthreads();
-  // chain rule, one thread per pair: its gamma's are g and the pair's weak block
+  // chain rule, one thread per pair: its gamma's are g and the pair's weak block; the
+  // members in index order (the threads of a warp handle their k-th members together)
   for (int g = threadIdx.x; g < c.npair; g += kThreads) {
     const int wbase = c.npair + g * (c.ncwo - 1);
     grad[g] = 0.0;
     for (int j = 0; j < c.ncwo - 1; ++j) grad[wbase + j] = 0.0;
-    for (int p = 0; p < A; ++p) {
-      if (c.pm[p] != g) continue;
+    for (int m = 0; m < c.cnt[g]; ++m) {
+      const int p = c.mem[g * c.msz + m];
       double nn, sq, ph;
       occ_orbital(p, g, c.rank[p], c.npair, c.ncwo, x, nn, sq, ph,
                   [&](int k, double dnk, double dsk, double dpk) {
@@ -175,6 +193,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.epart = c.ep + A;
   c.red = c.epart + A;             // kWarps + 1
   c.rank = (int*)(c.red + kWarps + 1);
+  const int nsub = d.npair + d.nsingle;
+  c.msz = 1 + d.ncwo;
+  c.cnt = c.rank + A;              // [nsub]
+  c.mem = c.cnt + nsub;            // [nsub][1 + ncwo]
+  if (threadIdx.x == 0) {          // member lists in index order
+    for (int g = 0; g < nsub; ++g) c.cnt[g] = 0;
+    for (int p = 0; p < A; ++p) {
+      const int g = pm[p];
+      if (g >= 0 && g < nsub && c.cnt[g] < c.msz) c.mem[g * c.msz + c.cnt[g]++] = p;
+    }
+  }
 
   for (int p = threadIdx.x; p < A; p += kThreads) {
     int r = 0;
@@ -314,8 +343,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t occ_smem_bytes(const Dims& d) {
   const size_t ng = d.ng > 0 ? d.ng : 1;
+  const size_t nsub = (size_t)d.npair + d.nsingle;
   return (6 * ng + 2 * kMem * ng + 2 * kMem + 7 * (size_t)d.A + kWarps + 1) * sizeof(double) +
-         (size_t)d.A * sizeof(int);
+         ((size_t)d.A + nsub + nsub * (1 + d.ncwo)) * sizeof(int);
 }
 
 }  // namespace
