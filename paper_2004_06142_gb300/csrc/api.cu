@@ -233,6 +233,14 @@ int check_ws(const donof_problem* p, const void* ws, size_t bytes) {
   return bytes >= L.total ? DONOF_OK : DONOF_ERR_WORKSPACE;
 }
 
+
+#define CK(x)                                  \
+  do {                                         \
+    if ((x) != cudaSuccess) return DONOF_ERR_CUDA; \
+  } while (0)
+
+}  // namespace
+
 // C(m, n) += sum_k A(m, k) B(k, n) for an M x N output with a long contraction K: the
 // contraction is cut into 64-wide chunks shared by enough CTAs to fill the GPU (atomic
 // double accumulation, so C must be initialised).
@@ -253,13 +261,6 @@ DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long
   a.alpha = 1.0; a.beta = 1.0;
   return a;
 }
-
-#define CK(x)                                  \
-  do {                                         \
-    if ((x) != cudaSuccess) return DONOF_ERR_CUDA; \
-  } while (0)
-
-}  // namespace
 }  // namespace donof
 
 using namespace donof;

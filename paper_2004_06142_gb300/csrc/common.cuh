@@ -172,12 +172,18 @@ __host__ __device__ inline int split_exponent(double bound) {
 inline int dgemm_tile_n(int N) { return (N + 31) / 32 * 32 < (N + 63) / 64 * 64 ? 32 : 64; }
 struct DgemmArgs {
   int M, N, K, KB, batch, ksplit, Ktot;
+  int lower;  // 1: only output tiles that reach the lower triangle (m >= n); ksplit == 1
   const double* A; long long sAb, sAm, sAk, sAkb;
   const double* B; long long sBb, sBk, sBn, sBkb;
   double* C; long long sCb, sCm, sCn;
   double alpha, beta;
 };
 cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s);
+// C(m, n) += sum_k A(m, k) B(k, n) with the contraction cut into 64-wide chunks shared by
+// enough CTAs to fill the GPU (atomic double accumulation: C must be initialised).
+DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long long sAk,
+                       const double* B, long long sBk, long long sBn, double* C, long long sCm,
+                       long long sCn);
 
 cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pair_map,
                                char* ws, const Layout& L, cudaStream_t s);

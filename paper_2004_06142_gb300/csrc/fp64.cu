@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
   const int bz = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
   const long long m0 = (long long)blockIdx.x * DBM;
   const int n0 = blockIdx.y * BN;
+  if (a.lower && n0 > m0 + DBM - 1) return;  // tile strictly above the diagonal
   const double* A = a.A + (long long)bz * a.sAb;
   const double* B = a.B + (long long)bz * a.sBb;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;

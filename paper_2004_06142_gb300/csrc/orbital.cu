@@ -67,6 +67,26 @@ DgemmArgs plain(int M, int N, int K, const double* A, long long sAm, long long s
   return a;
 }
 
+// M[i][j] = M[j][i] for i < j: the upper triangle from the lower one (a symmetric product
+// formed on its lower-triangle tiles only)
+__global__ void k_mirror_lower(double* M, int N) {
+  const long long tot = (long long)N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / N), c = (int)(i % N);
+    if (r < c) M[i] = M[(size_t)c * N + r];
+  }
+}
+
+// A symmetric product C_out (+)= A B formed on the lower-triangle tiles, then mirrored.
+int sym_product(DgemmArgs a, cudaStream_t s) {
+  a.lower = 1;
+  if (launch_dgemm(a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  k_mirror_lower<<<152 * 4, 256, 0, s>>>(a.C, a.N);
+  count_launch(1);
+  return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace donof
 
@@ -125,7 +145,7 @@ extern "C" int donof_orbital_update(int32_t nbf, const double* lam, const double
   // T[mu][j] = sum_i C[mu][i] V[i][j], V[i][j] = F[j * N + i]
   if (launch_dgemm(plain(N, N, N, C, N, 1, F, 1, N, T), s) != cudaSuccess) return DONOF_ERR_CUDA;
   // S = T^T T;  M = (3I - S) / 2;  C_new = T M
-  if (launch_dgemm(plain(N, N, N, T, 1, N, T, N, 1, S), s) != cudaSuccess) return DONOF_ERR_CUDA;
+  if (sym_product(plain(N, N, N, T, 1, N, T, N, 1, S), s) != DONOF_OK) return DONOF_ERR_CUDA;
   k_newton_schulz<<<152 * 4, 256, 0, s>>>(S, N, S);
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
@@ -219,6 +239,24 @@ __global__ void k_fockian_offdiag(const double* __restrict__ lam, int N, double 
     if (zeta > 0.0)
       while (fabs(v) > zeta) v /= 10.0;
     E[i] = v;
+  }
+}
+
+// M[q][p] /= 2 for q, p < A (the active block of the first A rows)
+__global__ void k_halve_block(double* M, int N, int A) {
+  const long long tot = (long long)A * A;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x)
+    M[(size_t)(i / A) * N + (i % A)] *= 0.5;
+}
+
+// S = Z + Z^T
+__global__ void k_sym_sum(const double* __restrict__ Z, int N, double* S) {
+  const long long tot = (long long)N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / N), c = (int)(i % N);
+    S[i] = Z[i] + Z[(size_t)c * N + r];
   }
 }
 
@@ -396,7 +434,8 @@ int loop_reorthonormalise(Loop& lp) {
   const int N = lp.N;
   double* T1 = (double*)(lp.ows + lp.L.T1);
   double* T2 = (double*)(lp.ows + lp.L.T2);
-  if (!ok(launch_dgemm(plain(N, N, N, lp.C, 1, N, lp.C, N, 1, T1), lp.s))) return DONOF_ERR_CUDA;
+  if (sym_product(plain(N, N, N, lp.C, 1, N, lp.C, N, 1, T1), lp.s) != DONOF_OK)
+    return DONOF_ERR_CUDA;
   k_newton_schulz<<<152 * 4, 256, 0, lp.s>>>(T1, N, T1);
   count_launch(1);
   if (!ok(launch_dgemm(plain(N, N, N, lp.C, N, 1, T1, N, 1, T2), lp.s))) return DONOF_ERR_CUDA;
@@ -426,14 +465,24 @@ int loop_orbital_step(Loop& lp, double zeta, int depth, std::vector<int>& active
   prof_begin(DONOF_PHASE_ORBITAL_STEP, lp.s);
   k_fockian_offdiag<<<152 * 4, 256, 0, lp.s>>>(lam, N, zeta, Emo);
   count_launch(1);
-  // e_AO = C Emo C^T; F_AO = e_AO + C diag(Fdiag) C^T
-  if (!ok(launch_dgemm(plain(N, N, N, lp.C, N, 1, Emo, N, 1, T1), lp.s)) ||
-      !ok(launch_dgemm(plain(N, N, N, T1, N, 1, lp.C, 1, N, e_ao), lp.s)))
+  // e_AO = C Emo C^T.  Emo vanishes between inactive orbitals (lambda_qp = 0 for p >= nact),
+  // so Emo = R + R^T with R = [Emo_aa / 2, Emo_ai; 0, 0] (nonzero in the nact active rows
+  // only) and e_AO = Z + Z^T with Z = C_a (R_a C^T): two products of rank nact.
+  const int A = lp.prob->npair * (1 + lp.prob->ncwo) + lp.prob->nsingle;
+  double* W = (double*)(o + lp.L.T2);  // R_a C^T, nact x N
+  k_halve_block<<<152, 256, 0, lp.s>>>(Emo, N, A);
+  count_launch(1);
+  if (!ok(cudaMemsetAsync(W, 0, (size_t)A * N * 8, lp.s)) ||
+      !ok(launch_dgemm(split_k_args(A, N, N, Emo, N, 1, lp.C, 1, N, W, N, 1), lp.s)) ||
+      !ok(launch_dgemm(plain(N, N, A, lp.C, N, 1, W, N, 1, T1), lp.s)))
     return DONOF_ERR_CUDA;
+  k_sym_sum<<<152 * 4, 256, 0, lp.s>>>(T1, N, e_ao);
+  count_launch(1);
+  // F_AO = e_AO + (C diag(Fdiag)) C^T, symmetric
   k_scale_cols<<<152 * 4, 256, 0, lp.s>>>(lp.C, lp.Fdiag, N, T1);
   count_launch(1);
   if (!ok(cudaMemcpyAsync(F_ao, e_ao, nn * 8, cudaMemcpyDeviceToDevice, lp.s)) ||
-      !ok(launch_dgemm(plain(N, N, N, T1, N, 1, lp.C, 1, N, F_ao, 1.0), lp.s)) ||
+      sym_product(plain(N, N, N, T1, N, 1, lp.C, 1, N, F_ao, 1.0), lp.s) != DONOF_OK ||
       !ok(cudaMemsetAsync(c + kMaxDepth + 1, 0, 8, lp.s)))
     return DONOF_ERR_CUDA;
   Slots sl{};
