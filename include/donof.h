@@ -190,6 +190,23 @@ int donof_energy_lagrangian_batched(int32_t ninst, const donof_problem* probs,
                                     const donof_instance* inst, void* workspace,
                                     size_t workspace_bytes, int32_t flags, void* stream);
 
+/* The parts of the NOF-MP2 energy (Sec. "Dynamic Correlation", Eq. Etotal:
+ * E = E_hf~ + E^sta + E^dyn) that need only the integrals of a build, from the H_pp, J_pq,
+ * K_pq and occupations of the last donof_energy_lagrangian call on `workspace` (same
+ * problem and pair_map):
+ *   E_hf  (device scalar) = Eq. HFL: 2 sum_g H_gg + sum_{f,g} (2 J_fg - K_fg)
+ *                            - sum_{g singly occupied} J_gg / 4, f and g over the
+ *                            npair + nsingle strong orbitals (indices 0 .. npair+nsingle-1);
+ *   E_sta (device scalar) = Eq. Esta: sum over the pair subspaces and ordered q != p in each
+ *                            of sqrt(Lambda_q Lambda_p) Pi_qp K_pq, Lambda_p = 1 - |1 - 2 n_p|,
+ *                            minus 4 sum over ordered pairs in different subspaces of
+ *                            Phi_q^2 Phi_p^2 K_pq.
+ * E^dyn (Eq. E2) is not computed: its amplitudes come from modified MP2 residual equations
+ * that the paper cites but does not state.  One CTA; fixed summation order. */
+int donof_nofmp2_static(const donof_problem* prob, const int32_t* pair_map,
+                        const void* workspace, size_t workspace_bytes, double* E_hf,
+                        double* E_sta, void* stream);
+
 /* The optimisation procedure around the build (Sec. III.D, with Sec. III.B's scaling and
  * Sec. III.C's DIIS).  Each outer iteration optimises the occupations at fixed orbitals
  * (donof_optimize_occupations) and then the orbitals at fixed occupations by up to

@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.donof_optimize.argtypes = [P, ctypes.POINTER(donof_opt_params), vp, vp, vp, vp, vp, vp,
                                      ctypes.c_int32, vp, sz, vp, sz,
                                      ctypes.POINTER(donof_opt_result), vp, ctypes.c_int32, vp]
+        L.donof_nofmp2_static.argtypes = [P, vp, vp, sz, vp, vp, vp]
         L.donof_profile_enable.argtypes = [ctypes.c_int32]
         L.donof_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]
@@ -108,7 +109,7 @@ def lib() -> ctypes.CDLL:
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
                   "donof_orbital_update", "donof_autotune", "donof_optimize_occupations",
-                  "donof_optimize_workspace_size", "donof_optimize"):
+                  "donof_optimize_workspace_size", "donof_optimize", "donof_nofmp2_static"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -199,6 +200,12 @@ def donof_optimize_occupations(prob, pair_map, gamma, ws, max_iter=500, gtol=1e-
            "donof_optimize_occupations")
 
 
+def donof_nofmp2_static(prob, pair_map, ws, E_hf, E_sta, stream=None):
+    _check(lib().donof_nofmp2_static(ctypes.byref(prob), _ptr(pair_map), _ptr(ws), ws.numel(),
+                                     _ptr(E_hf), _ptr(E_sta), _stream(stream)),
+           "donof_nofmp2_static")
+
+
 def donof_get_jk(prob, ws, J=None, K=None, stream=None):
     _check(lib().donof_get_jk(ctypes.byref(prob), _ptr(ws), ws.numel(), _ptr(J), _ptr(K),
                               _stream(stream)), "donof_get_jk")
@@ -281,6 +288,14 @@ class Builder:
         it = torch.zeros(1, dtype=torch.int32, device=self.device)
         donof_optimize_occupations(self.prob, pair_map, gamma, self.ws, max_iter, gtol, E, it)
         return E, it
+
+    def nofmp2_static(self, pair_map):
+        """The HF-like energy and the static correlation energy of NOF-MP2 (Eqs. HFL, Esta)
+        at the orbitals and occupations of the last forward(); device scalars."""
+        E_hf = torch.empty(1, dtype=torch.float64, device=self.device)
+        E_sta = torch.empty(1, dtype=torch.float64, device=self.device)
+        donof_nofmp2_static(self.prob, pair_map, self.ws, E_hf, E_sta)
+        return E_hf, E_sta
 
     def optimize(self, h, C, gamma, pair_map, Fdiag=None, max_outer=50, max_inner=10,
                  diis_depth=6, zeta=1.0, delta=1e-6, eps_energy=1e-10, occ_max_iter=500,

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdonof.so")
-SOURCES = ["api.cu", "fp64.cu", "tc.cu", "noalloc.cu", "batch.cu", "orbital.cu", "occopt.cu", "mid.cu"]
+SOURCES = ["api.cu", "fp64.cu", "tc.cu", "noalloc.cu", "batch.cu", "orbital.cu", "occopt.cu", "mid.cu",
+           "nofmp2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
