@@ -10,7 +10,9 @@ Readings (listed in the design notes):
 
 * the strong orbitals of Eq. HFL are the first N_Omega orbitals: g < npair the strong
   orbital of pair g, npair <= g < npair + nsingle the singly occupied ones; Eq. HFL is
-  taken as printed, its last sum running over the singly occupied g;
+  taken as printed, its last sum running over the singly occupied g.  For closed shells
+  it is pinned (the RHF energy of the strong orbitals); its singly occupied terms are
+  parity unpinned (transcription only);
 * Pi_qp in Eq. Esta is that of Eq. intra (pnof._pi); the first sum of Eq. Esta runs over
   the pair subspaces and over ordered q != p inside each; the second over ordered pairs of
   orbitals in different subspaces (singly occupied ones included, Phi = 1/2 there).
