@@ -2,8 +2,9 @@
  * donof_testing.h -- test hooks of libdonof (not needed to use the library).
  *
  * They expose the tensor-core building block of the mixed-precision build so that its
- * arithmetic can be checked in isolation against exact products on the host.  The paper
- * has no counterpart; these hooks exist for verification only.
+ * arithmetic can be checked in isolation against exact products on the host, and the
+ * bounded device wait so that its time-out path can be exercised.  The paper has no
+ * counterpart; these hooks exist for verification only.
  */
 #ifndef DONOF_TESTING_H
 #define DONOF_TESTING_H
@@ -39,6 +40,14 @@ int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_lo, const u
 int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A_lo, const uint16_t* B_hi,
                               const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
                               void* stream);
+
+/* The bounded device wait of the tensor-core kernel, run out on purpose: one CTA whose two
+ * roles wait on mbarriers that nothing completes, the first with a limit of limit_a_ns
+ * (at most 2 s), the second with limit_b_ns (at most 20 s).  The first wait's time-out
+ * sets the status word to DONOF_ERR_TIMEOUT and raises the abort flag, which must end the
+ * second wait well before its own limit; the kernel then returns normally and the context
+ * stays usable.  Read the outcome with donof_testing_status. */
+int donof_testing_wait_timeout(int64_t limit_a_ns, int64_t limit_b_ns, void* stream);
 
 /* Synchronises `stream` and returns (then clears) the status word of the test hooks. */
 int donof_testing_status(void* stream);

@@ -66,14 +66,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: after kWaitLimitNs it raises the abort flag and DONOF_ERR_TIMEOUT and
 // returns false; it also returns false soon after another role raised the abort flag.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int* abort_flag) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int* abort_flag,
+                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (*(volatile int*)abort_flag != 0) return false;
-      if (globaltimer() - t0 > kWaitLimitNs) {
+      if (globaltimer() - t0 > limit_ns) {
         atomicExch(abort_flag, 1);
         atomicCAS(status, 0, (int)DONOF_ERR_TIMEOUT);
         return false;
@@ -1550,6 +1551,41 @@ extern "C" int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A
   if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
     return DONOF_ERR_CUDA;
   return DONOF_OK;
+}
+
+namespace donof {
+namespace {
+// Two roles wait on mbarriers that nothing completes: warp 0 with a short limit, warp 1
+// with a long one; warp 0's time-out must raise the abort flag and end warp 1's wait too.
+__global__ void k_test_wait(unsigned long long limit_a, unsigned long long limit_b, int* words) {
+  __shared__ __align__(8) uint64_t bars[2];
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0 && warp < 2)
+    mbar_wait(smem_u32(&bars[warp]), 0, words + 1, words + 2, warp == 0 ? limit_a : limit_b);
+  __syncthreads();
+}
+}  // namespace
+}  // namespace donof
+
+extern "C" int donof_testing_wait_timeout(int64_t limit_a_ns, int64_t limit_b_ns, void* stream) {
+  using namespace donof;
+  if (limit_a_ns <= 0 || limit_b_ns <= 0 || limit_a_ns > 2000000000LL ||
+      limit_b_ns > 20000000000LL)
+    return DONOF_ERR_INVALID_ARG;
+  int* words = nullptr;
+  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
+  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  k_test_wait<<<1, 64, 0, (cudaStream_t)stream>>>((unsigned long long)limit_a_ns,
+                                                  (unsigned long long)limit_b_ns, words);
+  count_launch(1);
+  return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
 }
 
 extern "C" int donof_testing_status(void* stream) {

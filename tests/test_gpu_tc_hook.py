@@ -2,8 +2,11 @@
 operands (and a low part of multiples of 1/64) every product and partial sum is exact in
 fp32, so the result must equal the double-precision product exactly, for A given K-major
 (128-byte swizzle), MN-major, and K-major interleaved by 8 (no swizzle, core matrices),
-ragged K (zero fill past the end) and one or several M tiles."""
+ragged K (zero fill past the end) and one or several M tiles.  Also the bounded device
+wait: run out on purpose, it reports DONOF_ERR_TIMEOUT, ends the other role's wait through
+the abort flag, and leaves the context usable."""
 import ctypes
+import time
 
 import numpy as np
 import pytest
@@ -25,6 +28,7 @@ def lib():
     L.donof_testing_tc_gemm_mn.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_tc_gemm_il8.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_status.argtypes = [vp]
+    L.donof_testing_wait_timeout.argtypes = [ctypes.c_int64, ctypes.c_int64, vp]
     return L
 
 
@@ -61,3 +65,18 @@ def test_split_product_exact(lib, M, N, K, layout):
     assert rc == 0
     assert lib.donof_testing_status(s) == 0
     np.testing.assert_array_equal(D.cpu().numpy().astype(np.float64), ref)
+
+
+def test_bounded_wait_runs_out_and_context_survives(lib):
+    import torch
+    import paper_2004_06142_gb300.binding as bd
+    s = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    t0 = time.time()
+    assert lib.donof_testing_wait_timeout(20_000_000, 5_000_000_000, s) == 0  # 20 ms, 5 s
+    st = lib.donof_testing_status(s)
+    dt = time.time() - t0
+    assert st == -6, bd.donof_status_string(st)  # DONOF_ERR_TIMEOUT
+    assert dt < 1.0, dt  # the 5 s wait ended on the abort flag
+    assert lib.donof_testing_status(s) == 0  # the status word was cleared
+    test_split_product_exact(lib, 128, 160, 128, "k_major")  # the context still works
