@@ -48,11 +48,13 @@ Dims make_dims(const donof_problem* p) {
   d.pb = (int)pb;
   d.nblk = (d.Q + d.pb - 1) / d.pb;
   // split-K of the G contraction: at most 64 slices per split, enough units (row tiles x
-  // splits) for 2 waves over the 152 SMs, and where a few more splits make the units a
-  // whole number of waves, those
+  // splits) for 2 waves over the 152 SMs but at least 32 slices per split (short splits
+  // only add partials to reduce), and where a few more splits make the units a whole
+  // number of waves, those
   const int mt = (d.N + 127) / 128;
   int sp = (d.pb + 63) / 64;
-  const int want = (2 * 152 + mt - 1) / mt;
+  int want = (2 * 152 + mt - 1) / mt;
+  if (want > (d.pb + 31) / 32) want = (d.pb + 31) / 32;
   if (sp < want) sp = want;
   for (int s2 = sp; s2 <= sp + sp / 4; ++s2)
     if ((mt * s2) % 152 == 0) {
@@ -248,15 +250,18 @@ DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long
                        const double* B, long long sBk, long long sBn, double* C, long long sCm,
                        long long sCn) {
   DgemmArgs a{};
-  a.M = M; a.N = N; a.K = 64; a.KB = (K + 63) / 64; a.Ktot = K; a.batch = 1;
   const int bn = dgemm_tile_n(N);
   const long long tiles = (long long)((M + 63) / 64) * ((N + bn - 1) / bn);
+  // 64-wide chunks of the contraction, or 16-wide ones when even all 64-wide chunks would
+  // leave most SMs idle (small problems: the narrow FP64 pipe makes every CTA's share count)
+  const int chunk = tiles * ((K + 63) / 64) < 2 * 152 ? 16 : 64;
+  a.M = M; a.N = N; a.K = chunk; a.KB = (K + chunk - 1) / chunk; a.Ktot = K; a.batch = 1;
   long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
   if (ks > a.KB) ks = a.KB;
   if (ks < 1) ks = 1;
   a.ksplit = (int)ks;
-  a.A = A; a.sAm = sAm; a.sAk = sAk; a.sAkb = 64 * sAk;
-  a.B = B; a.sBk = sBk; a.sBn = sBn; a.sBkb = 64 * sBk;
+  a.A = A; a.sAm = sAm; a.sAk = sAk; a.sAkb = (long long)chunk * sAk;
+  a.B = B; a.sBk = sBk; a.sBn = sBn; a.sBkb = (long long)chunk * sBk;
   a.C = C; a.sCm = sCm; a.sCn = sCn;
   a.alpha = 1.0; a.beta = 1.0;
   return a;
