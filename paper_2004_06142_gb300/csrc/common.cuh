@@ -206,7 +206,6 @@ cudaError_t launch_coef_f32(const Dims& d, char* ws, const Layout& L, cudaStream
 
 cudaError_t launch_energy(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
                           double* E_out, double* dEdg_out, cudaStream_t s);
-cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s);
 cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, const Layout& L,
                             double* dE_dC, double* dE_dgamma, cudaStream_t s);
 

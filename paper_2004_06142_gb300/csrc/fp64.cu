@@ -465,13 +465,6 @@ cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layo
 
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_zero_cols(double* M, int rows, int ld, int c0, int c1) {
-  const int w = c1 - c0;
-  const long long tot = (long long)rows * w;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x)
-    M[(i / w) * ld + c0 + (i % w)] = 0.0;
-}
 __global__ void k_backward(Dims d, const double* __restrict__ Ebar, const double* __restrict__ G,
                            const double* __restrict__ dEdg, double* dE_dC, double* dE_dgamma) {
   const double eb = *Ebar;
@@ -485,13 +478,6 @@ __global__ void k_backward(Dims d, const double* __restrict__ Ebar, const double
   }
 }
 }  // namespace
-
-cudaError_t launch_zero_cols(double* M, int rows, int ld, int c0, int c1, cudaStream_t s) {
-  if (c1 <= c0 || rows <= 0) return cudaSuccess;
-  k_zero_cols<<<152 * 4, 256, 0, s>>>(M, rows, ld, c0, c1);
-  count_launch(1);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, const Layout& L,
                             double* dE_dC, double* dE_dgamma, cudaStream_t s) {
