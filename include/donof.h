@@ -63,8 +63,9 @@ enum { DONOF_B_DENSE = 0, DONOF_B_PACKED = 1 };
  * tensor cores.  Every operand row is stored as 2^e (h + f): h an fp16 integer with the
  * row's L2 norm bounding ||h||_2 below 2^12, f the fp16 remainder.  The integer products
  * h*h then accumulate exactly in fp32 (no partial sum reaches 2^24), and h*f + f*h + f*f
- * go to a second accumulator.  h C_act, the energy, dE/dgamma, J, K and every cross-tile
- * or cross-slice sum are in double. */
+ * go to a second accumulator.  h C_act, the energy and dE/dgamma are in double; J, K and
+ * G are summed over slices in short fp32 groups (16 slices for J and K, 8 split partials
+ * for G) and in double across groups. */
 enum { DONOF_FP64 = 0, DONOF_MIXED = 1 };
 
 enum {
