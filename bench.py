@@ -374,6 +374,7 @@ def run_ours(args):
     batch = None
     if not args.no_batch:
         batch = run_batch(dn, dev, args.steps, args.warmup)
+        batch["small_workloads"] = run_small_workloads(dn, dev, args.steps, args.warmup)
 
     # ---------------- the optimisation procedure around the build (occupation optimisation +
     # orbital iterations), mixed builds, on copies of C and gamma
@@ -550,6 +551,58 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         tdist.destroy_process_group()
+
+
+def run_small_workloads(dn, dev, steps, warmup):
+    """The plain, differentiation and precision workloads (nbf/naux/npair/Ncwo 24/96/5/1,
+    120/480/8/4, 500/2000/20/3): one mixed build + adjoint per step, captured once into a
+    CUDA graph and replayed (small builds are launch-bound), CUDA events over the replays."""
+    import numpy as np
+    import torch
+
+    import synth
+    out = {}
+    for name in ("plain", "differentiation", "precision"):
+        c = synth.CONFIGS[name]
+        prob = synth.Problem(c["nbf"], c["naux"], c["npair"], c["ncwo"], 0)
+        d = synth.generate(prob)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        h, B, C, g = t(d["h"]), t(d["B"]), t(d["C"]), t(d["gamma"])
+        pm = t(d["pair_map"].astype(np.int32))
+        b = dn.Builder(prob.nbf, prob.naux, prob.npair, prob.ncwo, dn.PNOF7, dn.B_DENSE,
+                       dn.MIXED, device=dev)
+        b.prepare(B)
+        Ebar = torch.ones(1, dtype=torch.float64, device=dev)
+        st = torch.cuda.Stream(device=dev)
+        st.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(st):
+            for _ in range(max(3, warmup)):
+                b.forward(h, C, g, pm)
+                b.backward(Ebar)
+        torch.cuda.current_stream(dev).wait_stream(st)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            b.forward(h, C, g, pm)
+            b.backward(Ebar)
+        graph.replay()
+        torch.cuda.synchronize()
+        reps = max(20, 10 * steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"shape": f"{prob.nbf}/{prob.naux}/{prob.npair}/{prob.ncwo}",
+                     "builds_per_s": 1e3 / ms, "ms_per_build": ms,
+                     "tflops_algorithmic": flops_build(prob.nbf, prob.naux, prob.nact)
+                     / (ms * 1e-3) / 1e12, "graph_replay": True}
+        del b, graph
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(dn, dev, steps, warmup, ninst=64):
