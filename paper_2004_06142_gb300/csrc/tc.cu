@@ -958,20 +958,37 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
   }
 }
 
-// Column norms of a double matrix S (N rows, leading dimension ld) -> exponents of the
-// integer + fraction split of S^T: e[c] for c < nrows_out (columns c >= ncols are zero).
-// With eS given, the columns of diag(2^s) S.  norm (optional) receives the norms.  A CTA
-// of 32 x 32 threads per 32 columns: thread (c, g) sums rows g, g + 32, ... (coalesced
-// across c), the 32 partial sums of a column are then added in order.
-__global__ void __launch_bounds__(1024) k_colnorms(const double* __restrict__ S, long long ld,
-                                                   int N, int ncols, int nrows_out,
-                                                   const int* __restrict__ eS, double invT,
-                                                   int* e, double* norm, DevHeader* hdr) {
+// One transposed integer + fraction split: S (N rows, leading dimension ld), output rows
+// c < nrows_out of the split of S^T (zero for c >= ncols), optionally of diag(2^eS) S.
+struct SplitJob {
+  const double* S;
+  long long ld;
+  int N, ncols, nrows_out;
+  const int* eS;  // may be null
+  int* e;         // per-row exponents of the output
+  double* norm;   // may be null: receives the column norms
+  __half* H;
+  __half* F;
+};
+struct SplitJobs {
+  SplitJob j[2];  // blockIdx.y (norms) or blockIdx.z (splits) selects the job
+};
+
+// Column norms of job.S -> exponents of the integer + fraction split of S^T: e[c] for
+// c < nrows_out.  A CTA of 32 x 32 threads per 32 columns: thread (c, g) sums rows g,
+// g + 32, ... (coalesced across c), the 32 partial sums of a column are then added in order.
+__global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, DevHeader* hdr) {
+  const SplitJob& jb = jobs.j[blockIdx.y];
+  if ((int)blockIdx.x * 32 >= jb.nrows_out) return;  // uniform over the CTA
   __shared__ double red[32][33];
+  const double* __restrict__ S = jb.S;
+  const int* __restrict__ eS = jb.eS;
+  const long long ld = jb.ld;
+  const int N = jb.N;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   const int c = blockIdx.x * 32 + tx;
   double ss = 0.0;
-  if (c < ncols) {
+  if (c < jb.ncols) {
     int mu = ty;
     for (; mu + 96 < N; mu += 128) {  // four loads in flight, summed in order of mu
       double v[4];
@@ -991,35 +1008,32 @@ __global__ void __launch_bounds__(1024) k_colnorms(const double* __restrict__ S,
   }
   red[ty][tx] = ss;
   __syncthreads();
-  if (ty == 0 && c < nrows_out) {
+  if (ty == 0 && c < jb.nrows_out) {
     double t = 0.0;
     for (int g = 0; g < 32; ++g) t += red[g][tx];
     const double nr = sqrt(t);
     if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
-    e[c] = intfrac_exponent_inv(nr, invT);
-    if (norm) norm[c] = nr;
+    jb.e[c] = intfrac_exponent_inv(nr, invT);
+    if (jb.norm) jb.norm[c] = nr;
   }
 }
 
-// Integer + fraction split of S^T (S: N rows, leading dimension ld), written as rows
-// c < nrows_out of Np halves (zero for c >= ncols or mu >= N): element (c, mu) is
-// 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given).  32 x 32 tiles through
-// shared memory, so that both the reads and the writes are coalesced.
-__global__ void __launch_bounds__(256) k_split_T(const double* __restrict__ S, long long ld,
-                                                 int N, int ncols, int nrows_out, int Np,
-                                                 const int* __restrict__ eS,
-                                                 const int* __restrict__ e, __half* H,
-                                                 __half* F) {
+// The split itself, as rows c < nrows_out of Np halves (zero for c >= ncols or mu >= N):
+// element (c, mu) is 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given).  32 x 32
+// tiles through shared memory, so that both the reads and the writes are coalesced.
+__global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
+  const SplitJob& jb = jobs.j[blockIdx.z];
+  const int mu0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  if (c0 >= jb.nrows_out) return;  // uniform over the CTA
   __shared__ double tile[32][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int mu0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int mu = mu0 + ty + 8 * j, c = c0 + tx;
     double v = 0.0;
-    if (mu < N && c < ncols) {
-      v = S[(size_t)mu * ld + c];
-      if (eS) v *= pow2d(eS[mu]);
+    if (mu < jb.N && c < jb.ncols) {
+      v = jb.S[(size_t)mu * jb.ld + c];
+      if (jb.eS) v *= pow2d(jb.eS[mu]);
     }
     tile[ty + 8 * j][tx] = v;
   }
@@ -1027,22 +1041,22 @@ __global__ void __launch_bounds__(256) k_split_T(const double* __restrict__ S, l
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = c0 + ty + 8 * j, mu = mu0 + tx;
-    if (c < nrows_out && mu < Np) {
+    if (c < jb.nrows_out && mu < Np) {
       const size_t o = (size_t)c * Np + mu;
-      intfrac_split(tile[tx][ty + 8 * j] * pow2d(-e[c]), H[o], F[o]);
+      intfrac_split(tile[tx][ty + 8 * j] * pow2d(-jb.e[c]), jb.H[o], jb.F[o]);
     }
   }
 }
 
-// Exponents of the integer + fraction split of X^T rows (P, q): ||X[P][:][q]||_2 =
-// ||B^P C_q||_2 <= ||B^P||_inf ||C_q||_2 (B^P symmetric, so ||B^P||_2 <= ||B^P||_inf).
-__global__ void k_xt_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
-                               int np, int Ap, double invT, int* eXt) {
-  for (int P = blockIdx.x; P < np; P += gridDim.x) {
-    const double l = L1max[P];
-    for (int q = threadIdx.x; q < Ap; q += blockDim.x)
-      eXt[(size_t)P * Ap + q] = intfrac_exponent_inv(l * cnorm[q], invT);
-  }
+// Both jobs' norms, then both splits: two launches.
+cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHeader* hdr,
+                              cudaStream_t s) {
+  const int r0 = jobs.j[0].nrows_out, r1 = jobs.j[1].nrows_out;
+  const int rmax = r0 > r1 ? r0 : r1;
+  k_colnorms<<<dim3((rmax + 31) / 32, 2), 1024, 0, s>>>(jobs, invT, hdr);
+  k_split_T<<<dim3((Np + 31) / 32, (rmax + 31) / 32, 2), 256, 0, s>>>(jobs, Np);
+  count_launch(2);
+  return cudaGetLastError();
 }
 
 // s_C^2 >= ||C_act||_2^2: Gershgorin bound max_i sum_j |(C_act^T C_act)_ij| of the Gram
@@ -1103,8 +1117,24 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
   }
 }
 
-__global__ void k_x3_exponents(const double* __restrict__ rn2, const DevHeader* hdr, int np,
-                               int splits, int N, double invT2, int* spOf, int* eX3) {
+// The per-block exponents of the two X splits written by the half transform (blocks with
+// blockIdx.y = 0 and 1 respectively):
+//  * X^T rows (P, q) for b: ||X[P][:][q]||_2 = ||B^P C_q||_2 <= ||B^P||_inf ||C_q||_2 (B^P
+//    symmetric, so ||B^P||_2 <= ||B^P||_inf);
+//  * X rows (split, mu) for G: the row runs over the split's slices and q, and its squared
+//    norm sum_P ||B^P_mu C_act||^2 <= s_C^2 sum_P ||B^P_mu||^2 (s_C^2 the Gram bound).
+__global__ void k_x_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
+                              int Ap, double invT, int* eXt, const double* __restrict__ rn2,
+                              const DevHeader* hdr, int np, int splits, int N, double invT2,
+                              int* spOf, int* eX3) {
+  if (blockIdx.y == 0) {
+    for (int P = blockIdx.x; P < np; P += gridDim.x) {
+      const double l = L1max[P];
+      for (int q = threadIdx.x; q < Ap; q += blockDim.x)
+        eXt[(size_t)P * Ap + q] = intfrac_exponent_inv(l * cnorm[q], invT);
+    }
+    return;
+  }
   const double sC2 = hdr->sC2;
   const long long tot = (long long)splits * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
@@ -1210,21 +1240,13 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
 
 cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
                            cudaStream_t s) {
-  DevHeader* hdr = (DevHeader*)(ws + L.header);
-  const double invT = intfrac_inv_target(d.N);
-  const dim3 gT((d.Np + 31) / 32, (d.Ap + 31) / 32);
-  k_colnorms<<<(d.Ap + 31) / 32, 1024, 0, s>>>(C, d.N, d.N, d.A, d.Ap, nullptr, invT,
-                                              (int*)(ws + L.eC), (double*)(ws + L.cnorm), hdr);
-  k_split_T<<<gT, 256, 0, s>>>(C, d.N, d.N, d.A, d.Ap, d.Np, nullptr, (const int*)(ws + L.eC),
-                               (__half*)(ws + L.Chi), (__half*)(ws + L.Clo));
-  // diag(2^s) C_act for the symmetric half transform
-  const int* eS = (const int*)(ws + L.eS);
-  k_colnorms<<<(d.Ap + 31) / 32, 1024, 0, s>>>(C, d.N, d.N, d.A, d.Ap, eS, invT,
-                                              (int*)(ws + L.eCs), nullptr, hdr);
-  k_split_T<<<gT, 256, 0, s>>>(C, d.N, d.N, d.A, d.Ap, d.Np, eS, (const int*)(ws + L.eCs),
-                               (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS));
-  count_launch(4);
-  return cudaGetLastError();
+  // C_act^T for b, and diag(2^s) C_act for the symmetric half transform
+  SplitJobs jobs{};
+  jobs.j[0] = SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
+                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo)};
+  jobs.j[1] = SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
+                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS)};
+  return launch_split_jobs(jobs, d.Np, intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
 }
 
 
@@ -1256,18 +1278,14 @@ int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, dou
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
   const double* G = (const double*)(ws + L.G);
-  const double invT = intfrac_inv_target(N);
-  k_colnorms<<<(N + 31) / 32, 1024, 0, s>>>(C, N, N, N, N, nullptr, invT, (int*)(ws + L.eCf),
-                                           nullptr, hdr);
-  k_split_T<<<dim3((Np + 31) / 32, (N + 31) / 32), 256, 0, s>>>(
-      C, N, N, N, N, Np, nullptr, (const int*)(ws + L.eCf), (__half*)(ws + L.CfH),
-      (__half*)(ws + L.CfF));
-  k_colnorms<<<(Ap + 31) / 32, 1024, 0, s>>>(G, A, N, A, Ap, nullptr, invT, (int*)(ws + L.eG),
-                                            nullptr, hdr);
-  k_split_T<<<dim3((Np + 31) / 32, (Ap + 31) / 32), 256, 0, s>>>(
-      G, A, N, A, Ap, Np, nullptr, (const int*)(ws + L.eG), (__half*)(ws + L.GtH),
-      (__half*)(ws + L.GtF));
-  count_launch(4);
+  // C^T (all N columns) and G^T rows
+  SplitJobs jobs{};
+  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr,
+                       (__half*)(ws + L.CfH), (__half*)(ws + L.CfF)};
+  jobs.j[1] = SplitJob{G, A, N, A, Ap, nullptr, (int*)(ws + L.eG), nullptr,
+                       (__half*)(ws + L.GtH), (__half*)(ws + L.GtF)};
+  if (launch_split_jobs(jobs, Np, intfrac_inv_target(N), hdr, s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
   CUtensorMap ah, al, bh, bl;
   const size_t h2 = sizeof(__half);
@@ -1296,15 +1314,14 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   const size_t h2 = sizeof(__half);
   // (1) X = B C_act  (integer + fraction operands; exact integer products)
   const int splits3 = d.splits < np ? d.splits : np;  // splits of the G contraction
-  k_xt_exponents<<<num_sms() * 8, 160, 0, s>>>((const double*)(ws + L.L1max) + p0,
-                                               (const double*)(ws + L.cnorm), np, Ap,
-                                               intfrac_inv_target(N), (int*)(ws + L.eXt));
   // the G contraction's rows run over (slices of a split) x Ap: the largest split's length
   const double invT2 = intfrac_inv_target_sq((double)((np + splits3 - 1) / splits3) * Ap);
-  k_x3_exponents<<<(splits3 * N + 255) / 256, 256, 0, s>>>(
-      (const double*)(ws + L.rn2) + (size_t)p0 * N, (const DevHeader*)hdr, np, splits3, N, invT2,
-      (int*)(ws + L.spOf), (int*)(ws + L.eX3));
-  count_launch(2);
+  const int gx3 = (splits3 * N + 255) / 256;
+  k_x_exponents<<<dim3(gx3 > num_sms() * 4 ? gx3 : num_sms() * 4, 2), 256, 0, s>>>(
+      (const double*)(ws + L.L1max) + p0, (const double*)(ws + L.cnorm), Ap,
+      intfrac_inv_target(N), (int*)(ws + L.eXt), (const double*)(ws + L.rn2) + (size_t)p0 * N,
+      (const DevHeader*)hdr, np, splits3, N, invT2, (int*)(ws + L.spOf), (int*)(ws + L.eX3));
+  count_launch(1);
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
     // A operand: the symmetric tile storage of the split B (bulk copies, BK = 64); B
