@@ -66,6 +66,17 @@ Dims make_dims(const donof_problem* p) {
   return d;
 }
 
+// Split count of the FP64 path's G contraction (contraction over the np slices): about
+// four CTAs per SM, at most one split per slice.
+int g_splits_fp64(int N, int A, int np) {
+  const int bn = dgemm_tile_n(A);
+  const long long tiles = (long long)((N + 63) / 64) * ((A + bn - 1) / bn);
+  long long ks = (4 * 152 + tiles - 1) / tiles;
+  if (ks > np) ks = np;
+  if (ks < 1) ks = 1;
+  return (int)ks;
+}
+
 Layout make_layout(const Dims& d) {
   Layout L{};
   size_t off = 0;
@@ -91,6 +102,14 @@ Layout make_layout(const Dims& d) {
   L.G = take(N * A * 8);
   L.dEdg = take(ng * 8);
   L.Epart = take(4 * A * 8);
+  {  // split-K partials of the FP64 products with N x A outputs (h C_act; FP64: lambda, G)
+    size_t ks = (size_t)splitk_count((int)N, (int)A, (int)N);
+    if (d.precision == DONOF_FP64) {
+      const size_t kg = (size_t)g_splits_fp64((int)N, (int)A, (int)pb);
+      if (kg > ks) ks = kg;
+    }
+    L.skp = take(ks > 1 ? ks * N * A * 8 : 0);
+  }
   if (d.precision == DONOF_FP64) {
     L.X64 = take(pb * N * A * 8);
     L.b64 = take(pb * A * A * 8);
@@ -246,24 +265,39 @@ int check_ws(const donof_problem* p, const void* ws, size_t bytes) {
 // C(m, n) += sum_k A(m, k) B(k, n) for an M x N output with a long contraction K: the
 // contraction is cut into 64-wide chunks shared by enough CTAs to fill the GPU (atomic
 // double accumulation, so C must be initialised).
-DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long long sAk,
-                       const double* B, long long sBk, long long sBn, double* C, long long sCm,
-                       long long sCn) {
-  DgemmArgs a{};
+namespace {
+// 64-wide chunks of the contraction, or 16-wide ones when even all 64-wide chunks would
+// leave most SMs idle (small problems: the narrow FP64 pipe makes every CTA's share count)
+int splitk_chunk(int M, int N, int K) {
   const int bn = dgemm_tile_n(N);
   const long long tiles = (long long)((M + 63) / 64) * ((N + bn - 1) / bn);
-  // 64-wide chunks of the contraction, or 16-wide ones when even all 64-wide chunks would
-  // leave most SMs idle (small problems: the narrow FP64 pipe makes every CTA's share count)
-  const int chunk = tiles * ((K + 63) / 64) < 2 * 152 ? 16 : 64;
-  a.M = M; a.N = N; a.K = chunk; a.KB = (K + chunk - 1) / chunk; a.Ktot = K; a.batch = 1;
+  return tiles * ((K + 63) / 64) < 2 * 152 ? 16 : 64;
+}
+}  // namespace
+
+int splitk_count(int M, int N, int K) {
+  const int bn = dgemm_tile_n(N);
+  const long long tiles = (long long)((M + 63) / 64) * ((N + bn - 1) / bn);
+  const int chunk = splitk_chunk(M, N, K);
   long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
-  if (ks > a.KB) ks = a.KB;
+  const long long kb = (K + chunk - 1) / chunk;
+  if (ks > kb) ks = kb;
   if (ks < 1) ks = 1;
-  a.ksplit = (int)ks;
+  return (int)ks;
+}
+
+DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long long sAk,
+                       const double* B, long long sBk, long long sBn, double* C, long long sCm,
+                       long long sCn, double* part) {
+  DgemmArgs a{};
+  const int chunk = splitk_chunk(M, N, K);
+  a.M = M; a.N = N; a.K = chunk; a.KB = (K + chunk - 1) / chunk; a.Ktot = K; a.batch = 1;
+  a.ksplit = splitk_count(M, N, K);
   a.A = A; a.sAm = sAm; a.sAk = sAk; a.sAkb = (long long)chunk * sAk;
   a.B = B; a.sBk = sBk; a.sBn = sBn; a.sBkb = (long long)chunk * sBk;
   a.C = C; a.sCm = sCm; a.sCn = sCn;
   a.alpha = 1.0; a.beta = 1.0;
+  a.part = part;
   return a;
 }
 }  // namespace donof
@@ -324,10 +358,10 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(cudaMemsetAsync(&((DevHeader*)(ws + L.header))->abort_flag, 0, sizeof(int32_t), s));
   CK(launch_occupations(d, gamma, pair_map, ws, L, s));
   CK(launch_coefficients(d, pair_map, ws, L, s));
-  if (d.precision == DONOF_MIXED) CK(launch_coef_f32(d, ws, L, s));
   // hC = h C_act, H_pp, G = n o hC
   CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
-  CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1), s));
+  CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1,
+                               (double*)(ws + L.skp)), s));
   CK(launch_hdiag_ginit(d, C, ws, L, s));
   CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
   CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
@@ -386,11 +420,8 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
     {  // G[mu][p] += sum_P sum_q X[P][mu][q] Y[P][q][p]
       DgemmArgs a{};
       a.M = N; a.N = A; a.K = A; a.KB = np; a.batch = 1;
-      const int bn = dgemm_tile_n(A);
-      const long long tiles = (long long)((N + 63) / 64) * ((A + bn - 1) / bn);
-      long long ks = (4 * 152 + tiles - 1) / tiles;  // about four CTAs per SM: latency hiding
-      if (ks > np) ks = np;
-      a.ksplit = (int)ks;
+      a.ksplit = g_splits_fp64(N, A, np);
+      a.part = (double*)(ws + L.skp);
       a.A = X; a.sAm = A; a.sAk = 1; a.sAkb = (long long)N * A;
       a.B = Y; a.sBk = A; a.sBn = 1; a.sBkb = (long long)A * A;
       a.C = (double*)(ws + L.G); a.sCm = A; a.sCn = 1;
@@ -408,7 +439,8 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
       rc = run_lambda_tc(d, C, ws, L, lam, s);
       if (rc != DONOF_OK) return rc;
     } else {
-      CK(launch_dgemm(split_k_args(N, A, N, C, 1, N, (const double*)(ws + L.G), A, 1, lam, N, 1),
+      CK(launch_dgemm(split_k_args(N, A, N, C, 1, N, (const double*)(ws + L.G), A, 1, lam, N, 1,
+                                   (double*)(ws + L.skp)),
                       s));
     }
   }

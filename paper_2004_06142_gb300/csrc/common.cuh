@@ -39,6 +39,7 @@ struct Layout {
   size_t header;
   // shared by both precisions
   size_t n, sqn, phi, dn, dsq, dphi, Acoef, Bcoef, Hd, hC, J, K, G, dEdg, Epart;
+  size_t skp;  // deterministic split-K partials of the FP64 N x A products
   // FP64 path
   size_t X64, b64, Y64, Bun;
   // mixed path
@@ -149,14 +150,6 @@ __device__ inline void intfrac_split(float y, __half& h, __half& f) {
   f = __float2half_rn(y - __half2float(h));  // exact difference: |y| < 4096
 }
 
-// Exponent s such that |x| * 2^s < 2^14 for |x| <= bound (bound > 0); 0 for bound == 0.
-__host__ __device__ inline int split_exponent(double bound) {
-  if (!(bound > 0.0)) return 0;
-  int e;
-  frexp(bound, &e);  // bound < 2^e
-  return 14 - e;
-}
-
 // ---------------------------------------------------------------------------
 // Kernel launchers (host side), implemented in fp64.cu and tc.cu.
 // All return a cudaError_t of the launch.
@@ -170,6 +163,9 @@ __host__ __device__ inline int split_exponent(double bound) {
 // long contraction into KB chunks of K that ksplit CTAs share).
 // Output tile width of k_dgemm: 32 where it pads the width less than 64 does.
 inline int dgemm_tile_n(int N) { return (N + 31) / 32 * 32 < (N + 63) / 64 * 64 ? 32 : 64; }
+// ksplit > 1 (batch 1 only): each CTA stores its partial product alpha * A B over its share
+// of the kb range in part[ks][M][N], and a second kernel adds the ksplit partials to C in
+// order of ks (C += sum, so beta must be 1): the result does not depend on scheduling.
 struct DgemmArgs {
   int M, N, K, KB, batch, ksplit, Ktot;
   int lower;  // 1: only output tiles that reach the lower triangle (m >= n); ksplit == 1
@@ -177,13 +173,18 @@ struct DgemmArgs {
   const double* B; long long sBb, sBk, sBn, sBkb;
   double* C; long long sCb, sCm, sCn;
   double alpha, beta;
+  double* part;  // ksplit x M x N scratch when ksplit > 1
 };
 cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s);
-// C(m, n) += sum_k A(m, k) B(k, n) with the contraction cut into 64-wide chunks shared by
-// enough CTAs to fill the GPU (atomic double accumulation: C must be initialised).
+// The split count split_k_args uses for an M x N output with contraction length K.
+int splitk_count(int M, int N, int K);
+int g_splits_fp64(int N, int A, int np);
+// C(m, n) += sum_k A(m, k) B(k, n) with the contraction cut into 64-wide (or 16-wide) chunks
+// shared by enough CTAs to fill the GPU; `part` holds splitk_count(M, N, K) x M x N doubles
+// (C must be initialised).
 DgemmArgs split_k_args(int M, int N, int K, const double* A, long long sAm, long long sAk,
                        const double* B, long long sBk, long long sBn, double* C, long long sCm,
-                       long long sCn);
+                       long long sCn, double* part);
 
 cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pair_map,
                                char* ws, const Layout& L, cudaStream_t s);
@@ -202,7 +203,6 @@ cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np
 // Mixed path between the b and G contractions (mid.cu): J, K and the Y operand split.
 cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const Layout& L,
                              cudaStream_t s);
-cudaError_t launch_coef_f32(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
 
 cudaError_t launch_energy(const Dims& d, const int32_t* pair_map, char* ws, const Layout& L,
                           double* E_out, double* dEdg_out, cudaStream_t s);

@@ -88,19 +88,32 @@ __global__ void __launch_bounds__(256) k_dgemm(DgemmArgs a) {
     for (int j = 0; j < NJ; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= a.N) continue;
-      double* c = C + gm * a.sCm + (long long)gn * a.sCn;
       if (a.ksplit > 1) {
-        atomicAdd(c, a.alpha * acc[i][j]);
+        a.part[((size_t)ks * a.M + gm) * a.N + gn] = a.alpha * acc[i][j];
       } else {
+        double* c = C + gm * a.sCm + (long long)gn * a.sCn;
         *c = a.alpha * acc[i][j] + (a.beta != 0.0 ? a.beta * *c : 0.0);
       }
     }
+  }
+}
+
+// C[m][n] += sum_ks part[ks][m][n], in order of ks
+__global__ void k_splitk_reduce(const double* __restrict__ part, int ksplit, int M, int N,
+                                double* C, long long sCm, long long sCn) {
+  const long long tot = (long long)M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int k = 0; k < ksplit; ++k) t += part[(size_t)k * tot + i];
+    C[(i / N) * sCm + (i % N) * sCn] += t;
   }
 }
 }  // namespace
 
 cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  if (a.ksplit > 1 && (!a.part || a.batch != 1 || a.beta != 1.0)) return cudaErrorInvalidValue;
   const long long mt = (a.M + DBM - 1) / DBM;
   // the narrow tile where it pads the output width less (e.g. 150 -> 160 instead of 192)
   const int bn = dgemm_tile_n(a.N);
@@ -111,6 +124,12 @@ cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
   else
     k_dgemm<64><<<grid, 256, 0, s>>>(a);
   count_launch(1);
+  if (a.ksplit > 1) {
+    const long long tot = (long long)a.M * a.N;
+    const int nb = (int)((tot + 255) / 256 < 152 * 8 ? (tot + 255) / 256 : 152 * 8);
+    k_splitk_reduce<<<nb, 256, 0, s>>>(a.part, a.ksplit, a.M, a.N, a.C, a.sCm, a.sCn);
+    count_launch(1);
+  }
   return cudaGetLastError();
 }
 
@@ -188,25 +207,34 @@ cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t
 namespace {
 __global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
                                const double* __restrict__ sqn, const double* __restrict__ phi,
-                               double* Ac, double* Bc) {
-  const int A = d.A;
+                               double* Ac, double* Bc, float* AcF, float* BcF) {
+  // with AcF/BcF (mixed path) also their fp32 copies, [Ap][Ap] with zero padding
+  const int A = d.A, W = AcF ? d.Ap : d.A;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)A * A) return;
-  const int p = (int)(idx / A), q = (int)(idx % A);
-  double a, b;
-  pair_coefficients(d.functional, d.npair, p, q, pm[p] == pm[q], pm[p] >= d.npair, n[p], n[q],
-                    sqn[p], sqn[q], phi[p], phi[q], a, b);
-  Ac[idx] = a;
-  Bc[idx] = b;
+  if (idx >= (long long)W * W) return;
+  const int p = (int)(idx / W), q = (int)(idx % W);
+  double a = 0.0, b = 0.0;
+  if (p < A && q < A) {
+    pair_coefficients(d.functional, d.npair, p, q, pm[p] == pm[q], pm[p] >= d.npair, n[p], n[q],
+                      sqn[p], sqn[q], phi[p], phi[q], a, b);
+    Ac[(size_t)p * A + q] = a;
+    Bc[(size_t)p * A + q] = b;
+  }
+  if (AcF) {
+    AcF[idx] = (float)a;
+    BcF[idx] = (float)b;
+  }
 }
 }  // namespace
 
 cudaError_t launch_coefficients(const Dims& d, const int32_t* pm, char* ws, const Layout& L,
                                 cudaStream_t s) {
-  const long long tot = (long long)d.A * d.A;
-  k_coefficients<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+  const bool mixed = d.precision == DONOF_MIXED;
+  const long long W = mixed ? d.Ap : d.A;
+  k_coefficients<<<(unsigned)((W * W + 255) / 256), 256, 0, s>>>(
       d, pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn), (const double*)(ws + L.phi),
-      (double*)(ws + L.Acoef), (double*)(ws + L.Bcoef));
+      (double*)(ws + L.Acoef), (double*)(ws + L.Bcoef), mixed ? (float*)(ws + L.AcF) : nullptr,
+      mixed ? (float*)(ws + L.BcF) : nullptr);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -240,38 +268,36 @@ cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, dou
 // H_pp = C_p^T (h C)_p and G_p = n_p (h C)_p.
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_hdiag(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
-                        double* Hd) {
-  // one warp per orbital p
+// one warp per orbital p: H_pp over the lanes' rows mu, and G[mu][p] = n_p (h C)[mu][p]
+__global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
+                              const double* __restrict__ n, double* Hd, double* G) {
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (p >= d.A) return;
+  const double np_ = n[p];
   double s = 0.0;
-  for (int mu = lane; mu < d.N; mu += 32) s += C[(size_t)mu * d.N + p] * hC[(size_t)mu * d.A + p];
+  for (int mu = lane; mu < d.N; mu += 32) {
+    const double v = hC[(size_t)mu * d.A + p];
+    s += C[(size_t)mu * d.N + p] * v;
+    G[(size_t)mu * d.A + p] = np_ * v;
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) Hd[p] = s;
-}
-__global__ void k_ginit(Dims d, const double* __restrict__ n, const double* __restrict__ hC,
-                        double* G) {
-  const long long tot = (long long)d.N * d.A;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x)
-    G[i] = n[i % d.A] * hC[i];
 }
 }  // namespace
 
 cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const Layout& L,
                                cudaStream_t s) {
-  k_hdiag<<<(d.A + 7) / 8, 256, 0, s>>>(d, C, (const double*)(ws + L.hC), (double*)(ws + L.Hd));
-  k_ginit<<<152 * 4, 256, 0, s>>>(d, (const double*)(ws + L.n), (const double*)(ws + L.hC),
-                                  (double*)(ws + L.G));
-  count_launch(2);
+  k_hdiag_ginit<<<(d.A + 7) / 8, 256, 0, s>>>(d, C, (const double*)(ws + L.hC),
+                                              (const double*)(ws + L.n), (double*)(ws + L.Hd),
+                                              (double*)(ws + L.G));
+  count_launch(1);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// J_pq += sum_P b[P][p][p] b[P][q][q],  K_pq += sum_P b[P][p][q]^2  (double sums).
-// Grid: x over (p, q), y over chunks of P.
+// J_pq += sum_P b[P][p][p] b[P][q][q],  K_pq += sum_P b[P][p][q]^2  (double sums, a thread
+// per (p, q) over the block's slices in order, so the sums do not depend on scheduling).
 // ---------------------------------------------------------------------------
 namespace {
 __global__ void k_jk(Dims d, const double* __restrict__ b, int np, int ld, double* J,
@@ -280,31 +306,25 @@ __global__ void k_jk(Dims d, const double* __restrict__ b, int np, int ld, doubl
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)A * A) return;
   const int p = (int)(idx / A), q = (int)(idx % A);
-  const int chunk = (np + gridDim.y - 1) / gridDim.y;
-  const int P0 = blockIdx.y * chunk, P1 = min(np, P0 + chunk);
   double sj = 0.0, sk = 0.0;
-  for (int P = P0; P < P1; ++P) {
+#pragma unroll 4
+  for (int P = 0; P < np; ++P) {
     const double* bp = b + (size_t)P * ld * ld;
     const double dp = bp[(size_t)p * ld + p], dq = bp[(size_t)q * ld + q];
     const double v = bp[(size_t)p * ld + q];
     sj = fma(dp, dq, sj);
     sk = fma(v, v, sk);
   }
-  if (P0 < P1) {
-    atomicAdd(J + idx, sj);
-    atomicAdd(K + idx, sk);
-  }
+  J[idx] += sj;
+  K[idx] += sk;
 }
 }  // namespace
 
 cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
                                      const Layout& L, cudaStream_t s) {
   const long long tot = (long long)d.A * d.A;
-  const unsigned gx = (unsigned)((tot + 255) / 256);
-  unsigned gy = (unsigned)((np + 31) / 32);
-  const unsigned want = 152u * 8u;
-  if (gx * gy > want) gy = want / gx > 0 ? want / gx : 1;
-  k_jk<<<dim3(gx, gy), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J), (double*)(ws + L.K));
+  k_jk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, b, np, ld, (double*)(ws + L.J),
+                                                     (double*)(ws + L.K));
   count_launch(1);
   return cudaGetLastError();
 }

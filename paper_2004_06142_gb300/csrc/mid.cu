@@ -21,17 +21,6 @@ __device__ __forceinline__ float pow2f_m(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// fp32 copies of the coefficient matrices, [Ap][Ap] with zero padding
-__global__ void k_coef_f32(const double* __restrict__ Ac, const double* __restrict__ Bc, int A,
-                           int Ap, float* AcF, float* BcF) {
-  const int tot = Ap * Ap;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
-    const int p = i / Ap, q = i % Ap;
-    const bool in = p < A && q < A;
-    AcF[i] = in ? (float)Ac[(size_t)p * A + q] : 0.f;
-    BcF[i] = in ? (float)Bc[(size_t)p * A + q] : 0.f;
-  }
-}
 
 // d^P (the diagonal of b^P) and w^P = Acoef d^P for a group of kDwSlices slices per CTA:
 // the group's d in shared memory, thread p forms w_p of every slice of the group (Acoef is
@@ -255,12 +244,5 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_coef_f32(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
-  k_coef_f32<<<sm_count(), 256, 0, s>>>((const double*)(ws + L.Acoef),
-                                       (const double*)(ws + L.Bcoef), d.A, d.Ap,
-                                       (float*)(ws + L.AcF), (float*)(ws + L.BcF));
-  count_launch(1);
-  return cudaGetLastError();
-}
 
 }  // namespace donof

@@ -186,10 +186,11 @@ struct Slots {
 
 struct OptLayout {
   size_t lam, Emo, T1, T2, Fbar, hist, eps, scal, B, c, info, work;
+  size_t skp;  // split-K partials of R_a C^T (nact x N)
   size_t total;
 };
 
-int opt_layout(int N, int depth, int lwork, OptLayout* o) {
+int opt_layout(int N, int A, int depth, int lwork, OptLayout* o) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t r = off;
@@ -210,6 +211,8 @@ int opt_layout(int N, int depth, int lwork, OptLayout* o) {
   o->c = take((size_t)(kMaxDepth + 2) * 8);  // c[0..n]; the restart flag kept at [kMaxDepth + 1]
   o->info = take(16);
   o->work = take((size_t)lwork * 8);
+  const int ks = splitk_count(A, N, N);
+  o->skp = take(ks > 1 ? (size_t)ks * A * N * 8 : 0);
   o->total = off;
   return DONOF_OK;
 }
@@ -473,7 +476,9 @@ int loop_orbital_step(Loop& lp, double zeta, int depth, std::vector<int>& active
   k_halve_block<<<152, 256, 0, lp.s>>>(Emo, N, A);
   count_launch(1);
   if (!ok(cudaMemsetAsync(W, 0, (size_t)A * N * 8, lp.s)) ||
-      !ok(launch_dgemm(split_k_args(A, N, N, Emo, N, 1, lp.C, 1, N, W, N, 1), lp.s)) ||
+      !ok(launch_dgemm(split_k_args(A, N, N, Emo, N, 1, lp.C, 1, N, W, N, 1,
+                                    (double*)(o + lp.L.skp)),
+                       lp.s)) ||
       !ok(launch_dgemm(plain(N, N, A, lp.C, N, 1, W, N, 1, T1), lp.s)))
     return DONOF_ERR_CUDA;
   k_sym_sum<<<152 * 4, 256, 0, lp.s>>>(T1, N, e_ao);
@@ -565,7 +570,7 @@ extern "C" int donof_optimize_workspace_size(const donof_problem* prob, int32_t 
                                   nullptr, prob->nbf, nullptr, &lwork) != CUSOLVER_STATUS_SUCCESS)
     return DONOF_ERR_CUDA;
   OptLayout L;
-  opt_layout(prob->nbf, diis_depth, lwork, &L);
+  opt_layout(prob->nbf, prob->npair * (1 + prob->ncwo) + prob->nsingle, diis_depth, lwork, &L);
   *bytes = L.total;
   return DONOF_OK;
 }
@@ -599,7 +604,8 @@ extern "C" int donof_optimize(const donof_problem* prob, const donof_opt_params*
   if (cusolverDnDsyevd_bufferSize(lp.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, lp.N,
                                   nullptr, lp.N, nullptr, &lp.lwork) != CUSOLVER_STATUS_SUCCESS)
     return DONOF_ERR_CUDA;
-  opt_layout(lp.N, prm->diis_depth, lp.lwork, &lp.L);
+  opt_layout(lp.N, prob->npair * (1 + prob->ncwo) + prob->nsingle, prm->diis_depth, lp.lwork,
+             &lp.L);
 
   int nE = 0;
   auto record = [&](double E) {
