@@ -119,6 +119,19 @@ def test_degenerate_shapes(shape, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_builds_are_bitwise_reproducible(precision):
+    """Every sum runs in a fixed order (no atomic accumulation), so two builds of the same
+    inputs agree bit for bit, in both precisions."""
+    prob = synth.Problem(300, 700, 12, 3, seed=9)
+    d = synth.generate(prob)
+    a = gpu_build(prob, d, precision, pnof.PNOF7)
+    b = gpu_build(prob, d, precision, pnof.PNOF7)
+    assert a["E"] == b["E"]
+    for k in ("lam", "dE_dgamma", "dE_dC", "J", "K"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_packed_and_blocked(precision):
     """Packed B and a budget that streams P in several blocks (with a ragged last one)."""
     prob = synth.Problem(57, 203, 4, 2, seed=3)
