@@ -139,12 +139,22 @@ cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s) {
 // nonzero entries are written.  Also validates pair_map and gamma.
 // ---------------------------------------------------------------------------
 namespace {
+// kTable (one CTA): sin and cos of every gamma are formed once into shared memory, so the
+// FP64 trigonometry is not repeated per orbital (the narrow FP64 pipe makes it the cost).
+template <bool kTable>
 __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
                               const int32_t* __restrict__ pm, DevHeader* hdr, double* n,
                               double* sqn, double* phi, double* dn, double* dsq, double* dphi) {
+  extern __shared__ double trig[];  // kTable: sin[ng], cos[ng]
   const int A = d.A, ng = d.ng, npair = d.npair, ncwo = d.ncwo;
-  for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < ng; k += blockDim.x * gridDim.x)
+  for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < ng; k += blockDim.x * gridDim.x) {
     if (!isfinite(gamma[k])) set_status(hdr, DONOF_ERR_NONFINITE);
+    if (kTable) {
+      trig[k] = sin(gamma[k]);
+      trig[ng + k] = cos(gamma[k]);
+    }
+  }
+  if (kTable) __syncthreads();
   const int p = threadIdx.x + blockIdx.x * blockDim.x;
   if (p >= A) return;
   const int nsub = npair + d.nsingle;  // subspaces: pairs, then the singly occupied orbitals
@@ -172,12 +182,15 @@ __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
       return;
     }
   }
-  occ_orbital(p, g, rank, npair, ncwo, gamma, n[p], sqn[p], phi[p],
-              [&](int k, double dnk, double dsk, double dpk) {
-                dn[(size_t)p * ng + k] = dnk;
-                dsq[(size_t)p * ng + k] = dsk;
-                dphi[(size_t)p * ng + k] = dpk;
-              });
+  auto put = [&](int k, double dnk, double dsk, double dpk) {
+    dn[(size_t)p * ng + k] = dnk;
+    dsq[(size_t)p * ng + k] = dsk;
+    dphi[(size_t)p * ng + k] = dpk;
+  };
+  if (kTable)
+    occ_orbital(p, g, rank, npair, ncwo, TrigTable{trig, trig + ng}, n[p], sqn[p], phi[p], put);
+  else
+    occ_orbital(p, g, rank, npair, ncwo, TrigDirect{gamma}, n[p], sqn[p], phi[p], put);
 }
 }  // namespace
 
@@ -188,11 +201,18 @@ cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t
     const cudaError_t e = cudaMemsetAsync(ws + off, 0, jac, s);
     if (e != cudaSuccess) return e;
   }
-  const int threads = 128;
-  const int blocks = (d.A + threads - 1) / threads;
-  k_occupations<<<blocks, threads, 0, s>>>(
-      d, gamma, pm, (DevHeader*)(ws + L.header), (double*)(ws + L.n), (double*)(ws + L.sqn),
-      (double*)(ws + L.phi), (double*)(ws + L.dn), (double*)(ws + L.dsq), (double*)(ws + L.dphi));
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  double *n = (double*)(ws + L.n), *sqn = (double*)(ws + L.sqn), *phi = (double*)(ws + L.phi);
+  double *dn = (double*)(ws + L.dn), *dsq = (double*)(ws + L.dsq), *dphi = (double*)(ws + L.dphi);
+  if (d.A <= 1024) {  // one CTA with the sin/cos table (at most 16 KB: ng < nact)
+    const int threads = (d.A + 31) / 32 * 32;
+    const size_t smem = (size_t)(d.ng > 0 ? d.ng : 1) * 2 * sizeof(double);
+    k_occupations<true><<<1, threads, smem, s>>>(d, gamma, pm, hdr, n, sqn, phi, dn, dsq, dphi);
+  } else {
+    const int threads = 128;
+    k_occupations<false><<<(d.A + threads - 1) / threads, threads, 0, s>>>(
+        d, gamma, pm, hdr, n, sqn, phi, dn, dsq, dphi);
+  }
   count_launch(1);
   return cudaGetLastError();
 }

@@ -7,8 +7,8 @@
 //   Phi = sqrt(n (1 - n))
 //
 // `rank` is the orbital's rank among the weak orbitals of its pair (ignored for strong
-// orbitals); `put(k, dn/dgamma_k, dsqrt_n/dgamma_k, dPhi/dgamma_k)` receives the nonzero
-// derivatives (pass a no-op to skip them).
+// orbitals); `tr` gives sin and cos of each gamma; `put(k, dn/dgamma_k, dsqrt_n/dgamma_k,
+// dPhi/dgamma_k)` receives the nonzero derivatives (pass a no-op to skip them).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,13 +17,25 @@
 
 namespace donof {
 
-template <typename Put>
-__device__ inline void occ_orbital(int p, int g, int rank, int npair, int ncwo,
-                                   const double* __restrict__ gamma, double& n_out,
-                                   double& sqn_out, double& phi_out, Put put) {
+// Sines and cosines of the gamma variables, evaluated on demand or read from a table that
+// holds exactly those values (the results are the same bits either way).
+struct TrigDirect {
+  const double* gamma;
+  __device__ double s(int k) const { return sin(gamma[k]); }
+  __device__ double c(int k) const { return cos(gamma[k]); }
+};
+struct TrigTable {
+  const double* sn;  // sin(gamma[k])
+  const double* cs;  // cos(gamma[k])
+  __device__ double s(int k) const { return sn[k]; }
+  __device__ double c(int k) const { return cs[k]; }
+};
+
+template <typename Trig, typename Put>
+__device__ inline void occ_orbital(int p, int g, int rank, int npair, int ncwo, const Trig& tr,
+                                   double& n_out, double& sqn_out, double& phi_out, Put put) {
   const double rs2 = 0.70710678118654752440;  // 1/sqrt(2)
-  const double tg = gamma[g];
-  const double cg = cos(tg), sg = sin(tg);
+  const double cg = tr.c(g), sg = tr.s(g);
   const double sh = fabs(sg) * rs2;  // sqrt(1 - n_g) = sqrt(h_g)
   const double dsh = copysign(1.0, sg) * cg * rs2;
   if (p < npair) {
@@ -40,8 +52,8 @@ __device__ inline void occ_orbital(int p, int g, int rank, int npair, int ncwo,
   const int wbase = npair + g * (ncwo - 1);
   const bool has_sin = (i < ncwo - 1);
   double prodc = 1.0;
-  for (int j = 0; j < i; ++j) prodc *= fabs(cos(gamma[wbase + j]));
-  const double si = has_sin ? fabs(sin(gamma[wbase + i])) : 1.0;
+  for (int j = 0; j < i; ++j) prodc *= fabs(tr.c(wbase + j));
+  const double si = has_sin ? fabs(tr.s(wbase + i)) : 1.0;
   const double val = sh * prodc * si;
   const double nn = val * val;
   const double om = sqrt(1.0 - nn);
@@ -54,16 +66,13 @@ __device__ inline void occ_orbital(int p, int g, int rank, int npair, int ncwo,
   };
   emit(g, dsh * prodc * si);
   for (int j = 0; j < i; ++j) {
-    const double t = gamma[wbase + j];
     double rest = sh * si;
     for (int jj = 0; jj < i; ++jj)
-      if (jj != j) rest *= fabs(cos(gamma[wbase + jj]));
-    emit(wbase + j, -copysign(1.0, cos(t)) * sin(t) * rest);
+      if (jj != j) rest *= fabs(tr.c(wbase + jj));
+    emit(wbase + j, -copysign(1.0, tr.c(wbase + j)) * tr.s(wbase + j) * rest);
   }
-  if (has_sin) {
-    const double t = gamma[wbase + i];
-    emit(wbase + i, copysign(1.0, sin(t)) * cos(t) * sh * prodc);
-  }
+  if (has_sin)
+    emit(wbase + i, copysign(1.0, tr.s(wbase + i)) * tr.c(wbase + i) * sh * prodc);
 }
 
 // Coefficients of J_pq and K_pq in E (Eqs. Eg, Efg, Efg_s): same subspace A = 0, B = Pi_pq

@@ -40,7 +40,8 @@ struct OccCtx {
   int* cnt;
   int msz;      // 1 + ncwo
   double *n, *sqn, *phi, *en, *es, *ep, *epart;
-  double* red;  // kWarps + 1 words
+  double *sn, *cs;  // sin and cos of the current gamma's, formed once per evaluation
+  double* red;      // kWarps + 1 words
 };
 
 // Sum of v over the block, the same value returned to every thread (fixed order).
@@ -83,13 +84,19 @@ __device__ double dot(const double* a, const double* b, int m, double* red) {
 // E(gamma) and dE/dgamma -> grad (shared), returned E identical on every thread.
 __device__ double evaluate(const OccCtx& c, const double* x, double* grad) {
   const int A = c.A;
+  for (int k = threadIdx.x; k < c.ng; k += kThreads) {
+    c.sn[k] = sin(x[k]);
+    c.cs[k] = cos(x[k]);
+  }
+  __syncthreads();
+  const TrigTable tr{c.sn, c.cs};
   for (int p = threadIdx.x; p < A; p += kThreads) {
     if (c.pm[p] >= c.npair) {  // Omega_I: n = 1/2, no gamma
       c.n[p] = 0.5;
       c.sqn[p] = 0.70710678118654752440;
       c.phi[p] = 0.5;
     } else {
-      occ_orbital(p, c.pm[p], c.rank[p], c.npair, c.ncwo, x, c.n[p], c.sqn[p], c.phi[p],
+      occ_orbital(p, c.pm[p], c.rank[p], c.npair, c.ncwo, tr, c.n[p], c.sqn[p], c.phi[p],
                   [](int, double, double, double) {});
     }
   }
@@ -153,7 +160,7 @@ __device__ double evaluate(const OccCtx& c, const double* x, double* grad) {
     for (int m = 0; m < c.cnt[g]; ++m) {
       const int p = c.mem[g * c.msz + m];
       double nn, sq, ph;
-      occ_orbital(p, g, c.rank[p], c.npair, c.ncwo, x, nn, sq, ph,
+      occ_orbital(p, g, c.rank[p], c.npair, c.ncwo, tr, nn, sq, ph,
                   [&](int k, double dnk, double dsk, double dpk) {
                     grad[k] += c.en[p] * dnk + c.es[p] * dsk + c.ep[p] * dpk;
                   });
@@ -191,7 +198,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.es = c.en + A;
   c.ep = c.es + A;
   c.epart = c.ep + A;
-  c.red = c.epart + A;             // kWarps + 1
+  c.sn = c.epart + A;              // [ng]
+  c.cs = c.sn + ng;                // [ng]
+  c.red = c.cs + ng;               // kWarps + 1
   c.rank = (int*)(c.red + kWarps + 1);
   const int nsub = d.npair + d.nsingle;
   c.msz = 1 + d.ncwo;
@@ -344,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 size_t occ_smem_bytes(const Dims& d) {
   const size_t ng = d.ng > 0 ? d.ng : 1;
   const size_t nsub = (size_t)d.npair + d.nsingle;
-  return (6 * ng + 2 * kMem * ng + 2 * kMem + 7 * (size_t)d.A + kWarps + 1) * sizeof(double) +
+  return (8 * ng + 2 * kMem * ng + 2 * kMem + 7 * (size_t)d.A + kWarps + 1) * sizeof(double) +
          ((size_t)d.A + nsub + nsub * (1 + d.ncwo)) * sizeof(int);
 }
 
