@@ -102,9 +102,10 @@ Layout make_layout(const Dims& d) {
   L.G = take(N * A * 8);
   L.dEdg = take(ng * 8);
   L.Epart = take(4 * A * 8);
-  {  // split-K partials of the FP64 products with N x A outputs (h C_act; FP64: lambda, G)
-    size_t ks = (size_t)splitk_count((int)N, (int)A, (int)N);
+  {  // split-K partials of the FP64 products with N x A outputs (h C_act, lambda, G)
+    size_t ks = 0;
     if (d.precision == DONOF_FP64) {
+      ks = (size_t)splitk_count((int)N, (int)A, (int)N);
       const size_t kg = (size_t)g_splits_fp64((int)N, (int)A, (int)pb);
       if (kg > ks) ks = kg;
     }
@@ -159,6 +160,12 @@ Layout make_layout(const Dims& d) {
     L.GtH = take(Ap * Np * 2);
     L.GtF = take(Ap * Np * 2);
     L.eG = take(Ap * 4);
+    L.hAH = take(4 * N * Np * 2);
+    L.hAF = take(4 * N * Np * 2);
+    L.cPH = take(4 * Ap * Np * 2);
+    L.cPF = take(4 * Ap * Np * 2);
+    L.eh = take(N * 4);
+    L.hpart = take(4 * N * Ap * 4);
   }
   L.total = off;
   return L;
@@ -358,18 +365,22 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   CK(cudaMemsetAsync(&((DevHeader*)(ws + L.header))->abort_flag, 0, sizeof(int32_t), s));
   CK(launch_occupations(d, gamma, pair_map, ws, L, s));
   CK(launch_coefficients(d, pair_map, ws, L, s));
-  // hC = h C_act, H_pp, G = n o hC
-  CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
-  CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1,
-                               (double*)(ws + L.skp)), s));
+  // hC = h C_act (FP64 DGEMM, or on the tensor cores with residual-extended operands), then
+  // H_pp and G = n o hC
+  if (d.precision == DONOF_MIXED) {
+    CK(launch_split_C(d, C, h, ws, L, s));
+    rc = run_hc_tc(d, ws, L, s);
+    if (rc != DONOF_OK) return rc;
+    // bound on ||C_act||_2 for the exponents of X in the G contraction
+    CK(launch_gram_bound(d, C, ws, L, s));
+  } else {
+    CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
+    CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1,
+                                 (double*)(ws + L.skp)), s));
+  }
   CK(launch_hdiag_ginit(d, C, ws, L, s));
   CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
   CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
-  if (d.precision == DONOF_MIXED) {
-    CK(launch_split_C(d, C, ws, L, s));
-    // bound on ||C_act||_2 for the exponents of X in the G contraction
-    CK(launch_gram_bound(d, C, ws, L, s));
-  }
   prof_end(DONOF_PHASE_PREP, s);
 
   for (int p0 = 0; p0 < d.Q; p0 += d.pb) {

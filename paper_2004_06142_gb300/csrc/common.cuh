@@ -57,6 +57,10 @@ struct Layout {
   // between the b and G contractions: w^P (fp32), per-split K and J partials (double),
   // fp32 copies of the J and K coefficient matrices ([Ap][Ap])
   size_t W, Ksp, Jsp, AcF, BcF;
+  // h C_act on the tensor cores: the split of h extended by its residual (four K-block
+  // planes per slot, hAH/hAF, exponents eh), the same planes of C_act^T (cPH/cPF, exponents
+  // eC), and the four fp32 products per block (hpart)
+  size_t hAH, hAF, cPH, cPF, eh, hpart;
   size_t total;
 };
 
@@ -212,8 +216,12 @@ cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, c
 // mixed path
 cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, const Layout& L,
                                    cudaStream_t s);
-cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
-                           cudaStream_t s);
+// The splits of C_act^T (for b and for h C_act), of diag(2^s) C_act (half transform) and of
+// h (for h C_act), in two launches.
+cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char* ws,
+                           const Layout& L, cudaStream_t s);
+// hC = h C_act on the tensor cores from the planes written by launch_split_C (mixed path).
+int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
                               cudaStream_t s);

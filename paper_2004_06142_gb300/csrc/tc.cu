@@ -960,6 +960,19 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
 
 // One transposed integer + fraction split: S (N rows, leading dimension ld), output rows
 // c < nrows_out of the split of S^T (zero for c >= ncols), optionally of diag(2^eS) S.
+//
+// Residual planes (planes != 0) serve a product U V^T that must come out to near double
+// precision from the integer + fraction kernel.  With y = h + f + r per element (r, the
+// residual of the split, rounded to fp16) the product is taken as four K blocks, block k
+// with operands (PH[k], PF[k]) on each side; the kernel forms PH_U PH_V exactly in one
+// accumulator and PH_U PF_V + PF_U PH_V + PF_U PF_V in the other, and each block is kept
+// as its own output, so that no block sums an exact part with a rounded one:
+//   block 0: U (h, 0), V (h, 0)  ->  h_U h_V                 (exact)
+//   block 1: U (0, h), V (r, f)  ->  h_U (r_V + f_V)
+//   block 2: U (0, f), V (h, f)  ->  f_U (h_V + f_V)
+//   block 3: U (0, r), V (h, f)  ->  r_U (h_V + f_V)
+// together (h_U + f_U + r_U)(h_V + f_V + r_V) less f_U r_V and r_U r_V, the two smallest
+// terms.  planes = 1 writes the U side, planes = 2 the V side ([4][nrows_out][Np] each).
 struct SplitJob {
   const double* S;
   long long ld;
@@ -967,11 +980,15 @@ struct SplitJob {
   const int* eS;  // may be null
   int* e;         // per-row exponents of the output
   double* norm;   // may be null: receives the column norms
-  __half* H;
+  __half* H;      // may be null (planes only)
   __half* F;
+  int planes;     // 0, 1 (U side) or 2 (V side)
+  __half* PH;
+  __half* PF;
 };
 struct SplitJobs {
-  SplitJob j[2];  // blockIdx.y (norms) or blockIdx.z (splits) selects the job
+  SplitJob j[3];  // blockIdx.y (norms) or blockIdx.z (splits) selects the job
+  int count;
 };
 
 // Column norms of job.S -> exponents of the integer + fraction split of S^T: e[c] for
@@ -1019,8 +1036,9 @@ __global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, 
 }
 
 // The split itself, as rows c < nrows_out of Np halves (zero for c >= ncols or mu >= N):
-// element (c, mu) is 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given).  32 x 32
-// tiles through shared memory, so that both the reads and the writes are coalesced.
+// element (c, mu) is 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given), and the
+// residual planes when asked for.  32 x 32 tiles through shared memory, so that both the
+// reads and the writes are coalesced.
 __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
   const SplitJob& jb = jobs.j[blockIdx.z];
   const int mu0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
@@ -1043,18 +1061,38 @@ __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
     const int c = c0 + ty + 8 * j, mu = mu0 + tx;
     if (c < jb.nrows_out && mu < Np) {
       const size_t o = (size_t)c * Np + mu;
-      intfrac_split(tile[tx][ty + 8 * j] * pow2d(-jb.e[c]), jb.H[o], jb.F[o]);
+      const double y = tile[tx][ty + 8 * j] * pow2d(-jb.e[c]);
+      __half h, f;
+      intfrac_split(y, h, f);
+      if (jb.H) {
+        jb.H[o] = h;
+        jb.F[o] = f;
+      }
+      if (jb.planes) {
+        // y - h and (y - h) - f are exact in double (the operands agree in their leading bits)
+        const __half r = __double2half((y - (double)__half2float(h)) - (double)__half2float(f));
+        const __half z = __float2half_rn(0.f);
+        const size_t ps = (size_t)jb.nrows_out * Np;
+        if (jb.planes == 1) {
+          jb.PH[o] = h; jb.PH[ps + o] = z; jb.PH[2 * ps + o] = z; jb.PH[3 * ps + o] = z;
+          jb.PF[o] = z; jb.PF[ps + o] = h; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = r;
+        } else {
+          jb.PH[o] = h; jb.PH[ps + o] = r; jb.PH[2 * ps + o] = h; jb.PH[3 * ps + o] = h;
+          jb.PF[o] = z; jb.PF[ps + o] = f; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = f;
+        }
+      }
     }
   }
 }
 
-// Both jobs' norms, then both splits: two launches.
+// All jobs' norms, then all splits: two launches.
 cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHeader* hdr,
                               cudaStream_t s) {
-  const int r0 = jobs.j[0].nrows_out, r1 = jobs.j[1].nrows_out;
-  const int rmax = r0 > r1 ? r0 : r1;
-  k_colnorms<<<dim3((rmax + 31) / 32, 2), 1024, 0, s>>>(jobs, invT, hdr);
-  k_split_T<<<dim3((Np + 31) / 32, (rmax + 31) / 32, 2), 256, 0, s>>>(jobs, Np);
+  int rmax = 0;
+  for (int k = 0; k < jobs.count; ++k)
+    if (jobs.j[k].nrows_out > rmax) rmax = jobs.j[k].nrows_out;
+  k_colnorms<<<dim3((rmax + 31) / 32, jobs.count), 1024, 0, s>>>(jobs, invT, hdr);
+  k_split_T<<<dim3((Np + 31) / 32, (rmax + 31) / 32, jobs.count), 256, 0, s>>>(jobs, Np);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -1238,15 +1276,35 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_C(const Dims& d, const double* C, char* ws, const Layout& L,
-                           cudaStream_t s) {
-  // C_act^T for b, and diag(2^s) C_act for the symmetric half transform
+cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char* ws,
+                           const Layout& L, cudaStream_t s) {
+  // C_act^T for b (and its residual planes, the V side of h C_act), diag(2^s) C_act for the
+  // symmetric half transform, and h^T = h (the U side of h C_act)
   SplitJobs jobs{};
   jobs.j[0] = SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
-                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo)};
+                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo),
+                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
   jobs.j[1] = SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
-                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS)};
+                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS),
+                       0, nullptr, nullptr};
+  jobs.j[2] = SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
+                       nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+  jobs.count = 3;
   return launch_split_jobs(jobs, d.Np, intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
+}
+
+// hC[mu][q] = sum_s hpart[s][mu][q] (q < nact), the four K blocks of the residual-extended
+// product added in double in block order.
+__global__ void k_sum_hc(const float* __restrict__ part, int N, int A, int Ap, double* hC) {
+  const long long tot = (long long)N * A;
+  const size_t ps = (size_t)N * Ap;
+  for (long long i = threadIdx.x + (long long)blockIdx.x * blockDim.x; i < tot;
+       i += (long long)blockDim.x * gridDim.x) {
+    const int mu = (int)(i / A), q = (int)(i - (long long)mu * A);
+    const size_t o = (size_t)mu * Ap + q;
+    hC[i] = (((double)part[o] + (double)part[ps + o]) + (double)part[2 * ps + o]) +
+            (double)part[3 * ps + o];
+  }
 }
 
 
@@ -1284,6 +1342,7 @@ int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, dou
                        (__half*)(ws + L.CfH), (__half*)(ws + L.CfF)};
   jobs.j[1] = SplitJob{G, A, N, A, Ap, nullptr, (int*)(ws + L.eG), nullptr,
                        (__half*)(ws + L.GtH), (__half*)(ws + L.GtF)};
+  jobs.count = 2;
   if (launch_split_jobs(jobs, Np, intfrac_inv_target(N), hdr, s) != cudaSuccess)
     return DONOF_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
@@ -1304,6 +1363,40 @@ int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, dou
   a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
   if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   return DONOF_OK;
+}
+
+// hC[mu][q] = sum_nu h[mu][nu] C[nu][q] (q < nact) on the tensor cores from the residual
+// planes of h (rows mu; h symmetric) and of C_act^T written by launch_split_C: the four K
+// blocks as four splits of one launch, each with its own fp32 output (exact block 0, the
+// others to fp32 rounding of terms 2^-12 and smaller relative to the row norms), added in
+// double by k_sum_hc.
+int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
+  CUtensorMap ah, al, bh, bl;
+  const size_t h2 = sizeof(__half);
+  if (!make_map(&ah, ws + L.hAH, N, N, 4, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
+      !make_map(&al, ws + L.hAF, N, N, 4, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
+      !make_map(&bh, ws + L.cPH, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+      !make_map(&bl, ws + L.cPF, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    return DONOF_ERR_CUDA;
+  TcArgs a{};
+  a.mode = 2; a.M = N; a.Nn = Ap;
+  a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
+  a.splits = 4;  // one K block per split
+  a.kt_per_kb = (N + 63) / 64; a.nkb = 4; a.a_z_kb = 1; a.b_z_mode = 2;
+  a.eA = (const int*)(ws + L.eh); a.eA_sstride = 0;
+  a.eB = (const int*)(ws + L.eC); a.eB_sstride = 0;
+  a.out = (float*)(ws + L.hpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
+  a.glob_exp = &hdr->zero_exp;
+  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+  if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  const long long tot = (long long)N * A;
+  const long long nb = (tot + 255) / 256;
+  k_sum_hc<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
+      (const float*)(ws + L.hpart), N, A, Ap, (double*)(ws + L.hC));
+  count_launch(1);
+  return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
 }
 
 // The tensor-core part of one block of np auxiliary slices (slices p0 .. p0+np-1).
