@@ -154,11 +154,7 @@ Layout make_layout(const Dims& d) {
     L.AcF = take(Ap * Ap * 4);
     L.BcF = take(Ap * Ap * 4);
     L.eY = take((size_t)d.splits * Ap * 4);
-    L.CfH = take(N * Np * 2);
-    L.CfF = take(N * Np * 2);
     L.eCf = take(N * 4);
-    L.GtH = take(Ap * Np * 2);
-    L.GtF = take(Ap * Np * 2);
     L.eG = take(Ap * 4);
     L.hAH = take(4 * N * Np * 2);
     L.hAF = take(4 * N * Np * 2);

@@ -45,10 +45,10 @@ struct Layout {
   // mixed path
   // integer + fraction planes (h, f) of the tensor-core operands and their per-row
   // exponents: B (Bhi/Blo, eB), C_act^T (Chi/Clo, eC), X^T for b (Xthi/Xtlo, eXt), X for G
-  // (Xhi/Xlo, eX3 per split), Y (Yhi/Ylo, eY per split), C^T and G^T for lambda (CfH/CfF,
-  // eCf; GtH/GtF, eG)
+  // (Xhi/Xlo, eX3 per split), Y (Yhi/Ylo, eY per split); the exponents of C^T and G^T for
+  // lambda (eCf, eG; their planes share the buffers of h C_act below)
   size_t Bhi, Blo, eB, L1max, Chi, Clo, eC, cnorm, Xhi, Xlo, Xthi, Xtlo, eXt, b32, Yhi, Ylo,
-      Gpart, D, rn2, spOf, eX3, eY, CfH, CfF, eCf, GtH, GtF, eG;
+      Gpart, D, rn2, spOf, eX3, eY, eCf, eG;
   // symmetric storage of the split B: per-AO scale exponents s, their source (max over P of
   // the row norms), per-slice maxima of the scaled row norms, and the split of
   // (diag 2^s C_act)^T that multiplies it
@@ -57,9 +57,9 @@ struct Layout {
   // between the b and G contractions: w^P (fp32), per-split K and J partials (double),
   // fp32 copies of the J and K coefficient matrices ([Ap][Ap])
   size_t W, Ksp, Jsp, AcF, BcF;
-  // h C_act on the tensor cores: the split of h extended by its residual (four K-block
-  // planes per slot, hAH/hAF, exponents eh), the same planes of C_act^T (cPH/cPF, exponents
-  // eC), and the four fp32 products per block (hpart)
+  // h C_act and lambda = C^T G on the tensor cores: the split of h (then of C^T) extended
+  // by its residual (four K-block planes per slot, hAH/hAF, exponents eh), the same planes
+  // of C_act^T (then of G^T) (cPH/cPF), and the fp32 products of the four blocks (hpart)
   size_t hAH, hAF, cPH, cPF, eh, hpart;
   size_t total;
 };
@@ -227,7 +227,7 @@ cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const La
                               cudaStream_t s);
 // The three tensor-core contractions of one block of np auxiliary slices starting at p0.
 int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaStream_t s);
-// lambda = C^T G on the tensor cores (mixed path).
+// lambda = C^T G on the tensor cores with residual-extended operands (mixed path).
 int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
                   cudaStream_t s);
 

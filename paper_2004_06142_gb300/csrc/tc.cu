@@ -6,7 +6,8 @@
 //       the lower-triangle tile storage of the split B (B symmetric), N = Ap, K = N
 //   (2) b[P][p][q]  = sum_mu C[mu][p] X[P][mu][q]     M = np*Ap (rows (P, q)), N = Ap, K = N
 //   (3) G[mu][p]   += sum_P sum_q X[P][mu][q] Y[P][q][p]   M = N, N = Ap, K = np*Ap (split)
-//   (4) lambda[q][p] = sum_mu C[mu][q] G[mu][p]       M = N, N = Ap, K = N
+//   (4) h C_act and lambda = C^T G                    M = N, N = Ap, K = 4 blocks of N:
+//       residual-extended operands (see SplitJob), near double precision
 // Operands are integer + fraction pairs (kIntFrac below): four products per K step, the
 // integer products exact in one TMEM accumulator, the others in a second, fp32.  A and B
 // are staged by TMA (or bulk copies for the tile storage of B) with 128-byte (BK = 64) or
@@ -219,7 +220,7 @@ constexpr int kIntFrac = 1;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
 
 struct TcArgs {
-  int mode;        // 1: X stores (integer + fraction X^T for b, X for G); 2: fp32; 3: double
+  int mode;        // 1: X stores (integer + fraction X^T for b, X for G); 2: fp32
   int M;           // valid output rows per z
   int Nn;          // output columns = B box rows (multiple of 16, <= 256)
   int m_tiles, z_count, splits;
@@ -234,7 +235,7 @@ struct TcArgs {
   // eA indexed by z * eA_zstride + split * eA_sstride + row (eB likewise by column)
   const int* eA; long long eA_zstride, eA_sstride;
   const int* eB; long long eB_zstride, eB_sstride;
-  const int* glob_exp;  // extra power of two applied to every output (modes 2 and 3)
+  const int* glob_exp;  // extra power of two applied to every output (mode 2)
   // A operand from pre-tiled planes (BK = 64 only): the tile of rows [r0, r0 + 128) and
   // k block kb is the contiguous run of rows x 128 bytes at a_tiled + kb * a_kb_stride +
   // r0 * 64, already in the 128-byte swizzled order; a partial last row block is copied
@@ -266,10 +267,6 @@ struct TcArgs {
   // mode 2 output
   float* out;
   long long out_ld, out_zstride;
-  // mode 3 output: double, columns c < ncols_valid only
-  double* out64;
-  long long out64_ld;
-  int ncols_valid;
   int* status;
   int* abort_flag;
 };
@@ -584,11 +581,6 @@ __global__ void __launch_bounds__(256, 1)
           *(uint4*)(args.xhi + o1) = ((uint4*)hi)[1];
           *(uint4*)(args.xlo + o0) = ((uint4*)lo)[0];
           *(uint4*)(args.xlo + o1) = ((uint4*)lo)[1];
-        } else if (args.mode == 3) {
-          double* o = args.out64 + (long long)row * args.out64_ld + c0;
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < args.ncols_valid) o[j] = (double)v[j];
         } else {
           float* o = args.out + (long long)(z * args.splits + sp) * args.out_zstride +
                      (long long)row * args.out_ld + c0;
@@ -1293,21 +1285,6 @@ cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char
   return launch_split_jobs(jobs, d.Np, intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
 }
 
-// hC[mu][q] = sum_s hpart[s][mu][q] (q < nact), the four K blocks of the residual-extended
-// product added in double in block order.
-__global__ void k_sum_hc(const float* __restrict__ part, int N, int A, int Ap, double* hC) {
-  const long long tot = (long long)N * A;
-  const size_t ps = (size_t)N * Ap;
-  for (long long i = threadIdx.x + (long long)blockIdx.x * blockDim.x; i < tot;
-       i += (long long)blockDim.x * gridDim.x) {
-    const int mu = (int)(i / A), q = (int)(i - (long long)mu * A);
-    const size_t o = (size_t)mu * Ap + q;
-    hC[i] = (((double)part[o] + (double)part[ps + o]) + (double)part[2 * ps + o]) +
-            (double)part[3 * ps + o];
-  }
-}
-
-
 cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
                               cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
@@ -1329,74 +1306,80 @@ cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream
   return cudaGetLastError();
 }
 
-// lambda[q][p] = sum_mu C[mu][q] G[mu][p] (q < N, p < nact) on the tensor cores with integer +
-// fraction operands (rows of C^T and G^T), written as double into lam (row stride N).
-int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
-                  cudaStream_t s) {
-  DevHeader* hdr = (DevHeader*)(ws + L.header);
-  const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
-  const double* G = (const double*)(ws + L.G);
-  // C^T (all N columns) and G^T rows
-  SplitJobs jobs{};
-  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr,
-                       (__half*)(ws + L.CfH), (__half*)(ws + L.CfF)};
-  jobs.j[1] = SplitJob{G, A, N, A, Ap, nullptr, (int*)(ws + L.eG), nullptr,
-                       (__half*)(ws + L.GtH), (__half*)(ws + L.GtF)};
-  jobs.count = 2;
-  if (launch_split_jobs(jobs, Np, intfrac_inv_target(N), hdr, s) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
-  CUtensorMap ah, al, bh, bl;
-  const size_t h2 = sizeof(__half);
-  if (!make_map(&ah, ws + L.CfH, N, N, 1, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
-      !make_map(&al, ws + L.CfF, N, N, 1, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
-      !make_map(&bh, ws + L.GtH, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
-      !make_map(&bl, ws + L.GtF, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
-    return DONOF_ERR_CUDA;
-  TcArgs a{};
-  a.mode = 3; a.M = N; a.Nn = Ap;
-  a.m_tiles = (N + BM - 1) / BM; a.z_count = 1; a.splits = 1;
-  a.kt_per_kb = (N + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-  a.eA = (const int*)(ws + L.eCf); a.eB = (const int*)(ws + L.eG);
-  a.glob_exp = &hdr->zero_exp;
-  a.out64 = lam; a.out64_ld = N; a.ncols_valid = A;
-  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-  if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
-  return DONOF_OK;
+// out[r * ld + c] = sum_s part[s][r][c] (r < M, c < ncols): the four K blocks of a
+// residual-extended product added in double in block order.
+__global__ void k_sum_blocks(const float* __restrict__ part, int M, int ncols, int Ap,
+                             double* out, long long ld) {
+  const long long tot = (long long)M * ncols;
+  const size_t ps = (size_t)M * Ap;
+  for (long long i = threadIdx.x + (long long)blockIdx.x * blockDim.x; i < tot;
+       i += (long long)blockDim.x * gridDim.x) {
+    const int r = (int)(i / ncols), c = (int)(i - (long long)r * ncols);
+    const size_t o = (size_t)r * Ap + c;
+    out[(size_t)r * ld + c] = (((double)part[o] + (double)part[ps + o]) +
+                               (double)part[2 * ps + o]) + (double)part[3 * ps + o];
+  }
 }
 
-// hC[mu][q] = sum_nu h[mu][nu] C[nu][q] (q < nact) on the tensor cores from the residual
-// planes of h (rows mu; h symmetric) and of C_act^T written by launch_split_C: the four K
-// blocks as four splits of one launch, each with its own fp32 output (exact block 0, the
-// others to fp32 rounding of terms 2^-12 and smaller relative to the row norms), added in
-// double by k_sum_hc.
-int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
+// out = U V^T (M x ncols, row stride ld) from the residual planes of U (M rows, in
+// hAH/hAF, exponents eU) and V (Ap rows, in cPH/cPF, exponents eV) over K = N: the four K
+// blocks as four splits of one launch, each with its own fp32 output (block 0 exact, the
+// others to the fp32 rounding of terms 2^-12 and smaller relative to the row norms), added
+// in double by k_sum_blocks.
+int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int ncols,
+                         double* out, long long ld, char* ws, const Layout& L, cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  const int N = d.N, A = d.A, Ap = d.Ap, Np = d.Np;
+  const int N = d.N, Ap = d.Ap, Np = d.Np;
   CUtensorMap ah, al, bh, bl;
   const size_t h2 = sizeof(__half);
-  if (!make_map(&ah, ws + L.hAH, N, N, 4, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
-      !make_map(&al, ws + L.hAF, N, N, 4, Np * h2, (uint64_t)N * Np * h2, 64, BM) ||
+  if (!make_map(&ah, ws + L.hAH, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
+      !make_map(&al, ws + L.hAF, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
       !make_map(&bh, ws + L.cPH, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
       !make_map(&bl, ws + L.cPF, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
     return DONOF_ERR_CUDA;
   TcArgs a{};
-  a.mode = 2; a.M = N; a.Nn = Ap;
-  a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
+  a.mode = 2; a.M = M; a.Nn = Ap;
+  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1;
   a.splits = 4;  // one K block per split
   a.kt_per_kb = (N + 63) / 64; a.nkb = 4; a.a_z_kb = 1; a.b_z_mode = 2;
-  a.eA = (const int*)(ws + L.eh); a.eA_sstride = 0;
-  a.eB = (const int*)(ws + L.eC); a.eB_sstride = 0;
-  a.out = (float*)(ws + L.hpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
+  a.eA = eU; a.eA_sstride = 0;
+  a.eB = eV; a.eB_sstride = 0;
+  a.out = (float*)(ws + L.hpart); a.out_ld = Ap; a.out_zstride = (long long)M * Ap;
   a.glob_exp = &hdr->zero_exp;
   a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
   if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
-  const long long tot = (long long)N * A;
-  const long long nb = (tot + 255) / 256;
-  k_sum_hc<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
-      (const float*)(ws + L.hpart), N, A, Ap, (double*)(ws + L.hC));
+  const long long nb = ((long long)M * ncols + 255) / 256;
+  k_sum_blocks<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
+      (const float*)(ws + L.hpart), M, ncols, Ap, out, ld);
   count_launch(1);
   return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
+}
+
+// hC = h C_act (h symmetric: its rows are the rows of h^T) from the planes written by
+// launch_split_C.
+int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
+  return run_extended_product(d, d.N, (const int*)(ws + L.eh), (const int*)(ws + L.eC), d.A,
+                              (double*)(ws + L.hC), d.A, ws, L, s);
+}
+
+// lambda[q][p] = sum_mu C[mu][q] G[mu][p] (q < N, p < nact), row stride N, from the planes
+// of C^T (all N columns of C) and G^T; the planes and block outputs of h C_act are free by
+// now and are reused.
+int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
+                  cudaStream_t s) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, A = d.A, Ap = d.Ap;
+  const double* G = (const double*)(ws + L.G);
+  SplitJobs jobs{};
+  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr, nullptr, nullptr,
+                       1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+  jobs.j[1] = SplitJob{G, A, N, A, Ap, nullptr, (int*)(ws + L.eG), nullptr, nullptr, nullptr,
+                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+  jobs.count = 2;
+  if (launch_split_jobs(jobs, d.Np, intfrac_inv_target(N), hdr, s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  return run_extended_product(d, N, (const int*)(ws + L.eCf), (const int*)(ws + L.eG), A, lam,
+                              N, ws, L, s);
 }
 
 // The tensor-core part of one block of np auxiliary slices (slices p0 .. p0+np-1).

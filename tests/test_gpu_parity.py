@@ -88,6 +88,18 @@ def test_mixed_path_few_aux():
     compare(out, ref, MIX_E, MIX_G, MIX_G, tol_jk=MIX_G)
 
 
+def test_mixed_one_electron_part_is_near_double():
+    """h scaled by 100 (|h| up to 1e3) so that the one-electron energy 2 sum n_p H_pp
+    dominates: h C_act with one integer + fraction split per operand would miss E by about
+    3e-5 Eh here (CPU emulation of the split); the residual-extended product by about 7e-8."""
+    prob = synth.Problem(300, 200, 10, 2, seed=4)
+    d = synth.generate(prob)
+    d["h"] = d["h"] * 100.0
+    ref = oracle(prob, d, pnof.PNOF7)
+    out = gpu_build(prob, d, 1, pnof.PNOF7)
+    compare(out, ref, MIX_E, MIX_G, MIX_G, tol_jk=MIX_G)
+
+
 @pytest.mark.parametrize("shape", [(200, 400, 44, 3), (260, 520, 50, 4), (300, 600, 64, 3)],
                          ids=["nact176", "nact250", "nact256"])
 @pytest.mark.parametrize("precision", [0, 1])
