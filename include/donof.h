@@ -63,9 +63,9 @@ enum { DONOF_B_DENSE = 0, DONOF_B_PACKED = 1 };
  * tensor cores.  Every operand row is stored as 2^e (h + f): h an fp16 integer with the
  * row's L2 norm bounding ||h||_2 below 2^12, f the fp16 remainder.  The integer products
  * h*h then accumulate exactly in fp32 (no partial sum reaches 2^24), and h*f + f*h + f*f
- * go to a second accumulator.  h C_act is taken on the tensor cores too, with the split of
- * each operand extended by its residual r = y - h - f (fp16) and the product cut into four
- * K blocks kept apart until a double sum, to about 1e-10 relative to the row norms.  The
+ * go to a second accumulator.  h C_act and lambda = C^T G take each operand's split
+ * extended by its residual r = y - h - f (fp16), the product cut into four K blocks kept
+ * apart until a double sum: about 1e-10 relative to the row norms.  The
  * energy and dE/dgamma are in double; J, K and G are summed over slices in short fp32
  * groups (16 slices for J and K, 8 split partials for G) and in double across groups.
  * The tensor-core outputs pass through fp32, so the mixed path needs each product of two
