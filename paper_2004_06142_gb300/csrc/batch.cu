@@ -18,7 +18,7 @@
 namespace donof {
 namespace {
 
-constexpr int kStreams = 8;
+constexpr int kStreams = 16;
 constexpr size_t kTableBytes = 256;  // head of the batched workspace: the constant 1.0
 
 struct StreamPool {
