@@ -297,7 +297,10 @@ int donof_autotune(const donof_problem* prob, const double* h, const double* B, 
  * each phase of the build; donof_profile_read() waits for them and returns the summed
  * device time (ms) and the number of timed intervals of one phase.  Enabling clears the
  * previous record.  The launch counter counts every kernel the library has launched in
- * this process (tracing on or off). */
+ * this process (tracing on or off).  Independently of tracing, each phase is also an NVTX
+ * range named "donof/<phase>" (prep, half_transform, mo_3index, jk_y, g_build,
+ * energy_lambda, backward, prepare_B, orbital_update, occ_opt, orbital_step) on the calling
+ * host thread, for profilers that filter by range. */
 enum {
   DONOF_PHASE_PREP = 0,            /* occupations, coefficients, h C, operand splits */
   DONOF_PHASE_HALF_TRANSFORM = 1,  /* X = B C_act (the dominant contraction) */

@@ -12,6 +12,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace donof {
@@ -199,7 +201,15 @@ static bool capturing(cudaStream_t s) {
   return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
 }
 
+// NVTX range names of the phases (host-side enqueue ranges, for filtering kernels by phase
+// in profilers: ncu --nvtx --nvtx-include "donof/half_transform/")
+const char* const kPhaseRange[DONOF_NUM_PHASES] = {
+    "donof/prep", "donof/half_transform", "donof/mo_3index", "donof/jk_y",
+    "donof/g_build", "donof/energy_lambda", "donof/backward", "donof/prepare_B",
+    "donof/orbital_update", "donof/occ_opt", "donof/orbital_step"};
+
 void prof_begin(int phase, cudaStream_t s) {
+  if (phase >= 0 && phase < DONOF_NUM_PHASES) nvtxRangePushA(kPhaseRange[phase]);
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES || capturing(s)) return;
   cudaEvent_t a, b;
@@ -211,6 +221,7 @@ void prof_begin(int phase, cudaStream_t s) {
 }
 
 void prof_end(int phase, cudaStream_t s) {
+  if (phase >= 0 && phase < DONOF_NUM_PHASES) nvtxRangePop();
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on || phase < 0 || phase >= DONOF_NUM_PHASES || capturing(s)) return;
   PhaseRec& r = g_prof[phase];
