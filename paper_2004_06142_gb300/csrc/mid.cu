@@ -57,10 +57,18 @@ __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ b, int
     float w[kDwSlices];
 #pragma unroll
     for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = 0.f;
-    for (int r = 0; r < A; ++r) {
-      const float a = AcF[(size_t)r * Ap + p];
+    // eight loads of Acoef in flight, the products still added in order of r
+    for (int r0 = 0; r0 < A; r0 += 8) {
+      float a[8];
 #pragma unroll
-      for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = fmaf(a, dv[sl][r], w[sl]);
+      for (int u = 0; u < 8; ++u) a[u] = r0 + u < A ? AcF[(size_t)(r0 + u) * Ap + p] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (r0 + u < A) {
+#pragma unroll
+          for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = fmaf(a[u], dv[sl][r0 + u], w[sl]);
+        }
+      }
     }
 #pragma unroll
     for (int sl = 0; sl < kDwSlices; ++sl)
@@ -181,8 +189,8 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
 // of rows r = y, y + 8, ... (blockDim = (Ap / 4, 8)).
 __global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__ W,
                           const float* __restrict__ BcF, int np, int A, int Ap,
-                          const int* __restrict__ spOf, const int* __restrict__ eY, __half* H,
-                          __half* F, DevHeader* hdr) {
+                          const int* __restrict__ spOf, const int* __restrict__ eY,
+                          __half* __restrict__ H, __half* __restrict__ F, DevHeader* hdr) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
     hdr->e3 = 0;  // G partials are in true units
   const int r4 = Ap / 4, c4 = threadIdx.x, c0 = 4 * c4;
@@ -190,18 +198,32 @@ __global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__
   for (int P = blockIdx.x; P < np; P += gridDim.x) {
     const float4* b4 = (const float4*)b + (size_t)P * Ap * r4;
     const int* eYs = eY + (size_t)spOf[P] * Ap;
-    for (int r = threadIdx.y; r < Ap; r += blockDim.y) {
-      const float sc = pow2f_m(-eYs[r]);
-      const float4 v = b4[(size_t)r * r4 + c4];
-      const float4 bc = Bc4[(size_t)r * r4 + c4];
-      float y[4] = {bc.x * v.x, bc.y * v.y, bc.z * v.z, bc.w * v.w};
-      if (r < A && r >= c0 && r < c0 + 4) y[r - c0] += W[(size_t)P * A + r];
-      __align__(8) __half h[4], fr[4];
+    constexpr int kRows = 4;  // rows of a thread whose loads are in flight together
+    for (int r0 = threadIdx.y; r0 < Ap; r0 += kRows * blockDim.y) {
+      float4 v[kRows], bc[kRows];
+      int ey[kRows];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) intfrac_split(y[j] * sc, h[j], fr[j]);
-      const size_t o = ((size_t)P * Ap + r) * Ap + c0;
-      *(uint2*)(H + o) = *(uint2*)h;
-      *(uint2*)(F + o) = *(uint2*)fr;
+      for (int k = 0; k < kRows; ++k) {
+        const int r = r0 + k * blockDim.y;
+        const bool in = r < Ap;
+        v[k] = in ? b4[(size_t)r * r4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        bc[k] = in ? Bc4[(size_t)r * r4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ey[k] = in ? eYs[r] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        const int r = r0 + k * blockDim.y;
+        if (r >= Ap) break;
+        const float sc = pow2f_m(-ey[k]);
+        float y[4] = {bc[k].x * v[k].x, bc[k].y * v[k].y, bc[k].z * v[k].z, bc[k].w * v[k].w};
+        if (r < A && r >= c0 && r < c0 + 4) y[r - c0] += W[(size_t)P * A + r];
+        __align__(8) __half h[4], fr[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) intfrac_split(y[j] * sc, h[j], fr[j]);
+        const size_t o = ((size_t)P * Ap + r) * Ap + c0;
+        *(uint2*)(H + o) = *(uint2*)h;
+        *(uint2*)(F + o) = *(uint2*)fr;
+      }
     }
   }
 }
