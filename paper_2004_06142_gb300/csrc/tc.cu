@@ -34,6 +34,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long kDrainLimitNs = 200000000ull;  // clean-up after an abort
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -64,6 +65,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
+}
+// Wait for phase `parity` of a barrier for at most limit_ns without raising anything (the
+// clean-up after an abort); returns whether the phase completed.
+__device__ bool mbar_wait_quiet(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > limit_ns) return false;
+  return true;
 }
 // Bounded wait: after kWaitLimitNs it raises the abort flag and DONOF_ERR_TIMEOUT and
 // returns false; it also returns false soon after another role raised the abort flag.
@@ -304,8 +313,8 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t b_bytes = (uint32_t)args.Nn * BK * 2;
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   uint64_t* bars = (uint64_t*)(smem + (size_t)S * stage_bytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2]; then the TMEM address slot
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4);
+  // bars: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 5);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int* status = args.status;
   int* abort_flag = args.abort_flag;
@@ -320,6 +329,7 @@ __global__ void __launch_bounds__(256, 1)
     mbar_init(smem_u32(&bars[2 * S + 1]), 1);
     mbar_init(smem_u32(&bars[2 * S + 2]), 128);
     mbar_init(smem_u32(&bars[2 * S + 3]), 128);
+    mbar_init(smem_u32(&bars[2 * S + 4]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -350,6 +360,7 @@ __global__ void __launch_bounds__(256, 1)
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
+    long long issued = 0;  // stages filled so far
     for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
       int z, mt, sp;
       decode(u, z, mt, sp);
@@ -386,6 +397,7 @@ __global__ void __launch_bounds__(256, 1)
             }
             tma_load_3d(base + 2 * a_bytes, &mBh, fb, 128 * j + 64 * c, 0, 0);
             tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, 128 * j + 64 * c, 0, 0);
+            ++issued;
             if (++stage == S) { stage = 0; phase ^= 1u; }
           }
         }
@@ -426,8 +438,17 @@ __global__ void __launch_bounds__(256, 1)
           }
           tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, 0, bz);
           tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, 0, bz);
+          ++issued;
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
+      }
+    }
+    // after an abort, every load already issued lands before the CTA leaves: stages below
+    // `stage` were filled in this lap of the ring, the others in the previous one (if any)
+    if (*(volatile int*)abort_flag != 0) {
+      for (int s = 0; s < S; ++s) {
+        if (s < stage) mbar_wait_quiet(smem_u32(&bars[s]), phase, kDrainLimitNs);
+        else if (issued >= S) mbar_wait_quiet(smem_u32(&bars[s]), phase ^ 1u, kDrainLimitNs);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -506,6 +527,11 @@ __global__ void __launch_bounds__(256, 1)
       }
       if (!ok) break;
       mma_commit(smem_u32(&bars[2 * S + acc]));
+    }
+    // after an abort, the MMAs already issued complete before the TMEM is freed
+    if (*(volatile int*)abort_flag != 0) {
+      mma_commit(smem_u32(&bars[2 * S + 4]));
+      mbar_wait_quiet(smem_u32(&bars[2 * S + 4]), 0u, kDrainLimitNs);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue: TMEM -> registers -> global
@@ -781,7 +807,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   a.nbuf = (2 * per_set <= 512) ? 2 : 1;
   a.buf_stride = (a.nbuf == 2) ? 256 : 0;
   if (a.nbuf == 2 && per_set > 256) return cudaErrorInvalidValue;
-  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 4) * 8 + 16;
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 5) * 8 + 16;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
