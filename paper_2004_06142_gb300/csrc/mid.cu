@@ -4,7 +4,7 @@
 //   Y^P_qp = Bcoef_qp b^P_qp + delta_qp w^P_p,   w^P_p = sum_r Acoef_pr d^P_r,  d^P_r = b^P_rr,
 // (the J and K coefficient matrices of E applied slice by slice, Eqs. Vee-s, Vee-d), without
 // materialising Y in fp32:
-//   k_diag_w   d^P and w^P per slice (fp32, 16 slices per CTA);
+//   k_diag_w   w^P per slice from d^P (written by the b contraction; fp32, 16 slices per CTA);
 //   k_kpart    per G split sp: Ksp_qp = sum_{P in sp} (b^P_qp)^2 and Jsp_qp = sum d^P_q d^P_p
 //              (fp32 groups of 16 slices, double across groups), b read once;
 //   k_jk_eY    K += sum_sp Ksp, J += sum_sp Jsp (double, fixed order), and the exponent of
@@ -22,35 +22,20 @@ __device__ __forceinline__ float pow2f_m(int e) {
 }
 
 
-// d^P (the diagonal of b^P) and w^P = Acoef d^P for a group of kDwSlices slices per CTA:
-// the group's d in shared memory, thread p forms w_p of every slice of the group (Acoef is
-// symmetric, so its column p is read, coalesced across threads).
+// w^P = Acoef d^P for a group of kDwSlices slices per CTA, from the diagonals d^P of b^P that
+// the b contraction wrote into D: the group's d in shared memory, thread p forms w_p of
+// every slice of the group (Acoef is symmetric, so its column p is read, coalesced across
+// threads).
 constexpr int kDwSlices = 16;
-__global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ b, int np, int A,
+__global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
-                                                float* D, float* W) {
+                                                float* W) {
   __shared__ float dv[kDwSlices][256];  // A <= 256
   const int P0 = blockIdx.x * kDwSlices;
   const int nP = min(kDwSlices, np - P0);
-  // the group's diagonal: slice sl = threadIdx.x / 16 (16 threads per slice), entries
-  // r = threadIdx.x % 16 + 16 k, all loads of a thread in flight together
-  {
-    const int sl = threadIdx.x / 16, r0 = threadIdx.x % 16;
-    constexpr int kMaxK = 16;  // A <= 256
-    float v[kMaxK];
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-      const int r = r0 + 16 * k;
-      v[k] = (sl < nP && r < A) ? b[((size_t)(P0 + sl) * Ap + r) * Ap + r] : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-      const int r = r0 + 16 * k;
-      if (r < A) {
-        dv[sl][r] = v[k];
-        if (sl < nP) D[(size_t)(P0 + sl) * A + r] = v[k];
-      }
-    }
+  for (int i = threadIdx.x; i < kDwSlices * A; i += blockDim.x) {
+    const int sl = i / A, r = i - sl * A;
+    dv[sl][r] = sl < nP ? D[(size_t)(P0 + sl) * A + r] : 0.f;
   }
   __syncthreads();
   for (int p = threadIdx.x; p < A; p += blockDim.x) {
@@ -249,7 +234,7 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   float* W = (float*)(ws + L.W);
   const float* AcF = (const float*)(ws + L.AcF);
   const float* BcF = (const float*)(ws + L.BcF);
-  k_diag_w<<<(np + kDwSlices - 1) / kDwSlices, 256, 0, s>>>(b, np, A, Ap, AcF, D, W);
+  k_diag_w<<<(np + kDwSlices - 1) / kDwSlices, 256, 0, s>>>(D, np, A, Ap, AcF, W);
   const int n4 = A * (Ap / 4);
   k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),

@@ -276,6 +276,10 @@ struct TcArgs {
   // mode 2 output
   float* out;
   long long out_ld, out_zstride;
+  // mode 2, rows (P, q) of slices of Ap rows: when set, the diagonal b^P_qq (q < diag_A) is
+  // also written to diag[P * diag_A + q]
+  float* diag;
+  int diag_A;
   int* status;
   int* abort_flag;
 };
@@ -576,6 +580,16 @@ __global__ void __launch_bounds__(256, 1)
       }
       const int* ecol =
           (NUM == kIntFrac) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
+      // the diagonal entry of this row (mode 2 with diag): its column, -1 for none
+      int dq = -1;
+      long long drow = 0;
+      if (args.mode == 2 && args.diag && valid) {
+        const int q = row % args.Nn;
+        if (q < args.diag_A) {
+          dq = q;
+          drow = (long long)(row / args.Nn) * args.diag_A + q;
+        }
+      }
 
       // one 16-column chunk: raw accumulator values -> outputs
       auto emit = [&](int c0, const float (&a)[16]) {
@@ -612,6 +626,11 @@ __global__ void __launch_bounds__(256, 1)
                      (long long)row * args.out_ld + c0;
 #pragma unroll
           for (int j = 0; j < 16; j += 4) *(float4*)(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          if (dq >= c0 && dq < c0 + 16) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j == dq) args.diag[drow] = v[j];
+          }
         }
       };
       auto load = [&](int c0, float (&a)[16]) {
@@ -1475,6 +1494,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
     a.glob_exp = &hdr->zero_exp;
     a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
+    a.diag = (float*)(ws + L.D); a.diag_A = d.A;  // d^P for the mid section
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
     if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
