@@ -217,6 +217,18 @@ def split_b_bytes(Q, N):
     return Q * per_slice * 4
 
 
+def tensor_peak(pk, region_s, clk):
+    """(kind, dense fp16 TFLOP/s) for the roofline: the burst peak for a timed region
+    shorter than 2 s whose SM clock median stays within 5 % of its maximum (the kernel then
+    runs at full clocks, as the burst GEMM did), the sustained peak (seconds of back-to-back
+    GEMMs under the power cap) otherwise."""
+    mhz, mhz_max = (clk or {}).get("sm_mhz"), (clk or {}).get("sm_max_mhz")
+    capped = bool(mhz and mhz_max and mhz < 0.95 * mhz_max)
+    kind = "sustained" if (region_s >= 2.0 or capped) else "burst"
+    key = "bf16_tflops_sustained" if kind == "sustained" else "bf16_tflops"
+    return kind, pk.get(key, FALLBACK_PEAKS[key])
+
+
 # ----------------------------------------------------------------------------- traffic record
 def recorded_traffic(kernel_src):
     """Per-launch DRAM bytes of the half-transform kernel from the committed ncu summary,
@@ -492,14 +504,9 @@ def run_ours(args):
 
     # ---------------- roofline of the dominant kernel (half transform X = B C)
     pk, src = peaks()
-    # the burst peak for a short timed region at full clocks, the sustained one (seconds of
-    # back-to-back work under the power cap) once the region is that long or the clocks drop
     region_s = args.steps * ms * 1e-3
     mhz, mhz_max = (clk or {}).get("sm_mhz"), (clk or {}).get("sm_max_mhz")
-    capped = bool(mhz and mhz_max and mhz < 0.95 * mhz_max)
-    kind = "sustained" if (region_s >= 2.0 or capped) else "burst"
-    peak_key = "bf16_tflops_sustained" if kind == "sustained" else "bf16_tflops"
-    peak_f16 = pk.get(peak_key, FALLBACK_PEAKS[peak_key])
+    kind, peak_f16 = tensor_peak(pk, region_s, clk)
     half = phases.get("half_transform", {}).get("ms_per_launch")
     roof = None
     if half:

@@ -41,3 +41,17 @@ def test_two_ranks_take_the_slowest_clock():
 def test_single_process_needs_no_group():
     assert bench.max_over_ranks(7.0, 1, torch.device("cpu")) == 7.0
     assert bench.job_rate(8.0, 1) == pytest.approx(125.0)
+
+
+def test_roofline_peak_follows_the_timed_region():
+    """Burst peak for a short region at full clocks; sustained for a long region, for
+    clocks well below their maximum, and as the fallback when the file lacks a figure."""
+    pk = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    full = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0}
+    assert bench.tensor_peak(pk, 0.1, full) == ("burst", 1900.0)
+    assert bench.tensor_peak(pk, 3.0, full) == ("sustained", 1700.0)
+    assert bench.tensor_peak(pk, 0.1, {"sm_mhz": 1500.0, "sm_max_mhz": 2070.0}) == \
+        ("sustained", 1700.0)
+    assert bench.tensor_peak(pk, 0.1, None) == ("burst", 1900.0)
+    kind, peak = bench.tensor_peak({}, 0.1, full)
+    assert kind == "burst" and peak == bench.FALLBACK_PEAKS["bf16_tflops"]
