@@ -34,6 +34,19 @@ class DonofError(RuntimeError):
 
 
 BATCH_BACKWARD, BATCH_GRAPH = 1, 2
+ERR_WORKSPACE = -4
+
+
+def alloc_workspace(nbytes: int, device) -> torch.Tensor:
+    """Device workspace of nbytes.  An allocation failure is reported as DonofError with
+    the workspace status; DONOF_INJECT_ALLOC_FAILURE=1 in the environment makes every such
+    allocation fail that way (host-side fault injection, no device involved)."""
+    if os.environ.get("DONOF_INJECT_ALLOC_FAILURE") == "1":
+        raise DonofError(ERR_WORKSPACE, f"workspace allocation of {nbytes} bytes (injected failure)")
+    try:
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+    except (RuntimeError, MemoryError) as e:  # torch.OutOfMemoryError derives from RuntimeError
+        raise DonofError(ERR_WORKSPACE, f"workspace allocation of {nbytes} bytes: {e}") from e
 
 
 class donof_instance(ctypes.Structure):
@@ -184,7 +197,7 @@ def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):
         nb = ctypes.c_size_t(0)
         _check(lib().donof_orbital_update_workspace_size(n, ctypes.byref(nb)),
                "donof_orbital_update_workspace_size")
-        ws = torch.empty(nb.value, dtype=torch.uint8, device=C.device)
+        ws = alloc_workspace(nb.value, C.device)
     _check(lib().donof_orbital_update(n, _ptr(lam), _ptr(Fdiag), _ptr(C), _ptr(ws), ws.numel(),
                                       _ptr(C_new), _ptr(eps), _stream(stream)),
            "donof_orbital_update")
@@ -253,7 +266,7 @@ class Builder:
         self.nact = npair * (1 + ncwo) + nsingle
         self.ngamma = npair * ncwo
         self.device = torch.device(device)
-        self.ws = torch.empty(donof_workspace_size(self.prob), dtype=torch.uint8, device=self.device)
+        self.ws = alloc_workspace(donof_workspace_size(self.prob), self.device)
         self.B = None
 
     def prepare(self, B: torch.Tensor):
@@ -309,7 +322,7 @@ class Builder:
         _check(lib().donof_optimize_workspace_size(ctypes.byref(self.prob), diis_depth,
                                                    ctypes.byref(nb)),
                "donof_optimize_workspace_size")
-        ows = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        ows = alloc_workspace(nb.value, self.device)
         init = Fdiag is None
         if init:
             Fdiag = torch.zeros(self.nbf, dtype=torch.float64, device=self.device)
@@ -359,8 +372,7 @@ class Batch:
                                          for k in ("h", "B", "C", "gamma", "pair_map", "E", "lam",
                                                    "dE_dgamma", "dE_dC")]))
         self.inst = (donof_instance * self.n)(*rows)
-        self.ws = torch.empty(donof_batched_workspace_size(probs), dtype=torch.uint8,
-                              device=device)
+        self.ws = alloc_workspace(donof_batched_workspace_size(probs), device)
 
     def prepare(self, stream=None):
         _check(lib().donof_prepare_B_batched(self.n, self.probs, self.inst, _ptr(self.ws),

@@ -84,3 +84,20 @@ def test_entry_points_reject_null_workspace(lib):
     assert rc == -4
     rc = lib.donof_energy_lagrangian(ctypes.byref(p), None, E, E, E, E, E, 0, E, None, None, None)
     assert rc == -1
+
+
+def test_injected_workspace_allocation_failure(lib, monkeypatch):
+    """Host-side fault injection: with DONOF_INJECT_ALLOC_FAILURE=1 every workspace the
+    binding would allocate fails as an allocation failure does, before any device is
+    touched, and surfaces as DonofError with the workspace status."""
+    from paper_2004_06142_gb300 import binding as b
+    monkeypatch.setenv("DONOF_INJECT_ALLOC_FAILURE", "1")
+    with pytest.raises(b.DonofError) as e:
+        b.Builder(24, 96, 5, 1)
+    assert e.value.code == b.ERR_WORKSPACE
+    assert "injected" in str(e.value)
+    with pytest.raises(b.DonofError) as e:
+        b.alloc_workspace(1 << 20, "cpu")
+    assert e.value.code == b.ERR_WORKSPACE
+    monkeypatch.delenv("DONOF_INJECT_ALLOC_FAILURE")
+    assert b.alloc_workspace(1 << 10, "cpu").numel() == 1 << 10
