@@ -325,25 +325,17 @@ def orbital_update(lam: np.ndarray, Fdiag: np.ndarray, C: np.ndarray):
     return eps, C @ V
 
 
-def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False, nsingle=0):
-    """One Lagrangian build: E, lambda, dE/dgamma, dE/dC and the intermediates.
-    nsingle singly occupied orbitals (Omega_I, n = 1/2) sit at npair .. npair + nsingle - 1
-    with pair_map[g] = g.
-
-    B: dense [naux][nbf][nbf] or packed [naux][nbf(nbf+1)/2] (packed=True).
-    C: [nbf][nbf], column p = orbital p (Eq. lcao).
-    """
+def from_operators(h, C, gamma, pair_map, Jq, Kq, npair, ncwo, functional=PNOF7, nsingle=0):
+    """Everything of one build after the AO operators J^q, K^q of Eq. Gpmn: J_pq, K_pq
+    (Eq. JKpq), E (Eqs. EPNOF7, Eg, Efg / Efg_s), G and lambda = C^T G (Eqs. lowdin, Vee-s,
+    Vee-d, lag), dE/dC = 4 G and dE/dgamma (chain rule through Eqs. soo/woo)."""
     h = np.asarray(h, dtype=np.float64)
     C = np.asarray(C, dtype=np.float64)
     nbf = h.shape[0]
-    if packed:
-        B = unpack_B(np.asarray(B, dtype=np.float64), nbf)
-    B = np.asarray(B, dtype=np.float64)
     pair_map = np.asarray(pair_map)
     nact = len(pair_map)
     C_act = C[:, :nact]
     occ = occupations(np.asarray(gamma, dtype=np.float64), pair_map, npair, ncwo, nsingle)
-    Jq, Kq = ao_operators(B, C_act)
     J, K = mo_jk(C_act, Jq, Kq)
     Hdiag = np.einsum("mp,mn,np->p", C_act, h, C_act)
     E = energy(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
@@ -355,3 +347,47 @@ def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False,
     dE_dgamma = occupation_gradient(Hdiag, J, K, occ, pair_map, npair, functional, nsingle)
     return dict(E=E, lam=lam, dE_dgamma=dE_dgamma, dE_dC=dE_dC, G=G, J=J, K=K,
                 Hdiag=Hdiag, n=occ["n"], occ=occ)
+
+
+def build(h, B, C, gamma, pair_map, npair, ncwo, functional=PNOF7, packed=False, nsingle=0):
+    """One Lagrangian build: E, lambda, dE/dgamma, dE/dC and the intermediates.
+    nsingle singly occupied orbitals (Omega_I, n = 1/2) sit at npair .. npair + nsingle - 1
+    with pair_map[g] = g.
+
+    B: dense [naux][nbf][nbf] or packed [naux][nbf(nbf+1)/2] (packed=True).
+    C: [nbf][nbf], column p = orbital p (Eq. lcao).
+    """
+    nbf = np.asarray(h).shape[0]
+    if packed:
+        B = unpack_B(np.asarray(B, dtype=np.float64), nbf)
+    B = np.asarray(B, dtype=np.float64)
+    C_act = np.asarray(C, dtype=np.float64)[:, :len(pair_map)]
+    Jq, Kq = ao_operators(B, C_act)
+    return from_operators(h, C, gamma, pair_map, Jq, Kq, npair, ncwo, functional, nsingle)
+
+
+def build_streamed(h, blocks, C, gamma, pair_map, npair, ncwo, functional=PNOF7, nsingle=0,
+                   on_block=None):
+    """build() for workloads too large to hold B: `blocks` yields consecutive blocks of
+    auxiliary slices, dense [np][nbf][nbf] (or packed [np][nbf(nbf+1)/2], unpacked here).
+    J^q and K^q of Eq. Gpmn are sums over the auxiliary index, so ao_operators of each block
+    is added to the running J^q, K^q; the rest is build()'s route unchanged.  on_block, when
+    given, is called after each block with the number of slices done (progress, timing)."""
+    nbf = np.asarray(h).shape[0]
+    C_act = np.asarray(C, dtype=np.float64)[:, :len(pair_map)]
+    Jq = Kq = None
+    done = 0
+    for blk in blocks:
+        blk = np.asarray(blk, dtype=np.float64)
+        if blk.ndim == 2:
+            blk = unpack_B(blk, nbf)
+        Jb, Kb = ao_operators(blk, C_act)
+        if Jq is None:
+            Jq, Kq = Jb, Kb
+        else:
+            Jq += Jb
+            Kq += Kb
+        done += blk.shape[0]
+        if on_block is not None:
+            on_block(done)
+    return from_operators(h, C, gamma, pair_map, Jq, Kq, npair, ncwo, functional, nsingle)

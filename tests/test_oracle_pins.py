@@ -299,3 +299,23 @@ def test_fockian_first_order_energy_change():
         pred = sum(4 * F0[q, p] ** 2 / (diag[p] - diag[q]) for p in range(N) for q in range(p))
         assert abs((E1 - out["E"]) - pred) < 0.02 * abs(pred), (E1 - out["E"], pred)
         assert np.sign(E1 - out["E"]) == np.sign(scale)
+
+
+# --------------------------------------------------------------------------- streaming
+def test_streamed_build_equals_plain_build():
+    # the AO operators of Eq. Gpmn are sums over the auxiliary index: accumulating them over
+    # blocks of slices (dense or packed, ragged last block) must give the one-pass build
+    prob, d = tiny(nbf=11, naux=23, npair=2, ncwo=2, seed=4)
+    ref = run(prob, d)
+    mu, nu = synth.packed_index(prob.nbf)
+    for bs, packed in ((5, False), (7, True), (23, False)):
+        blocks = [d["B"][p0:p0 + bs] for p0 in range(0, prob.naux, bs)]
+        if packed:
+            blocks = [b[:, mu, nu] for b in blocks]
+        seen = []
+        out = pnof.build_streamed(d["h"], iter(blocks), d["C"], d["gamma"], d["pair_map"],
+                                  prob.npair, prob.ncwo, pnof.PNOF7, on_block=seen.append)
+        assert seen[-1] == prob.naux and len(seen) == len(blocks)
+        assert abs(out["E"] - ref["E"]) <= 1e-12
+        for k in ("lam", "dE_dgamma", "dE_dC", "J", "K"):
+            np.testing.assert_allclose(out[k], ref[k], rtol=0, atol=1e-12)
