@@ -199,9 +199,13 @@ int donof_energy_lagrangian_batched(int32_t ninst, const donof_problem* probs,
  * E = E_hf~ + E^sta + E^dyn) that need only the integrals of a build, from the H_pp, J_pq,
  * K_pq and occupations of the last donof_energy_lagrangian call on `workspace` (same
  * problem and pair_map):
- *   E_hf  (device scalar) = Eq. HFL: 2 sum_g H_gg + sum_{f,g} (2 J_fg - K_fg)
- *                            - sum_{g singly occupied} J_gg / 4, f and g over the
- *                            npair + nsingle strong orbitals (indices 0 .. npair+nsingle-1);
+ *   E_hf  (device scalar) = Eq. HFL, the energy of its closed-shell-like HF density matrix
+ *                            with 2n_g = 2 (pairs) and 2n_g = 1 (singly occupied orbitals):
+ *                            2 sum_g w_g H_gg + sum_{f,g} w_f w_g (2 J_fg - K_fg)
+ *                            - sum_{g singly occupied} J_gg / 4, w_g = 1 for the strong
+ *                            orbital of a pair and 1/2 for a singly occupied one, f and g
+ *                            over the npair + nsingle strong orbitals (indices
+ *                            0 .. npair+nsingle-1); without singles, the printed formula;
  *   E_sta (device scalar) = Eq. Esta: sum over the pair subspaces and ordered q != p in each
  *                            of sqrt(Lambda_q Lambda_p) Pi_qp K_pq, Lambda_p = 1 - |1 - 2 n_p|,
  *                            minus 4 sum over ordered pairs in different subspaces of

@@ -9,10 +9,17 @@ leg of ``bench.py`` may import this module.  It shares no code with the CUDA lib
 Readings (listed in the design notes):
 
 * the strong orbitals of Eq. HFL are the first N_Omega orbitals: g < npair the strong
-  orbital of pair g, npair <= g < npair + nsingle the singly occupied ones; Eq. HFL is
-  taken as printed, its last sum running over the singly occupied g.  For closed shells
-  it is pinned (the RHF energy of the strong orbitals); its singly occupied terms are
-  parity unpinned (transcription only);
+  orbital of pair g, npair <= g < npair + nsingle the singly occupied ones.  The paper
+  defines E_hf as the energy of a closed-shell-like HF density matrix with doubly
+  (2n_g = 2) and singly (2n_g = 1) occupied orbitals; its printed formula carries no
+  occupation factors, which with singles would count each singly occupied orbital as
+  doubly occupied.  Reading: each H_gg and (2 J_fg - K_fg) carries the HF occupations
+  w_g = 1 (pairs), 1/2 (singles) of that density matrix, i.e.
+  2 sum_g w_g H_gg + sum_{f,g} w_f w_g (2 J_fg - K_fg) - sum_{g singly occupied} J_gg / 4;
+  the last sum (as printed) removes the self-interaction w_g^2 J_gg of a singly occupied
+  orbital.  Without singles this is the printed formula.  Pinned by the RHF energy (no
+  singles), the doublet determinant energy (one single: Slater-Condon rules) and the
+  fractional-occupation Roothaan energy of that density matrix (several singles);
 * Pi_qp in Eq. Esta is that of Eq. intra (pnof._pi); the first sum of Eq. Esta runs over
   the pair subspaces and over ordered q != p inside each; the second over ordered pairs of
   orbitals in different subspaces (singly occupied ones included, Phi = 1/2 there).
@@ -27,15 +34,18 @@ from oracle import pnof
 
 
 def hf_like_energy(Hdiag, J, K, npair, nsingle=0):
-    """Eq. HFL: 2 sum_g H_gg + sum_{f,g} (2 J_fg - K_fg) - sum_{g singly occupied} J_gg / 4,
+    """Eq. HFL with the occupations of its HF density matrix (w_g = 1 for the strong orbitals
+    of the pairs, 1/2 for the singly occupied ones):
+    2 sum_g w_g H_gg + sum_{f,g} w_f w_g (2 J_fg - K_fg) - sum_{g singly occupied} J_gg / 4,
     f and g over the N_Omega = npair + nsingle strong orbitals."""
     n_omega = npair + nsingle
+    w = [1.0 if g < npair else 0.5 for g in range(n_omega)]
     E = 0.0
     for g in range(n_omega):
-        E += 2.0 * Hdiag[g]
+        E += 2.0 * w[g] * Hdiag[g]
     for f in range(n_omega):
         for g in range(n_omega):
-            E += 2.0 * J[f, g] - K[f, g]
+            E += w[f] * w[g] * (2.0 * J[f, g] - K[f, g])
     for g in range(npair, n_omega):
         E -= J[g, g] / 4.0
     return E

@@ -23,9 +23,12 @@ __device__ double block_sum_fixed(double v, double* red) {
   return t;  // valid on thread 0
 }
 
-// One CTA.  E_hf: pairs (f, g) of the N_Omega strong orbitals; E_sta: pairs (p, q) of the
-// active orbitals, the intra-pair term for p != q in one pair subspace (Pi_qp negative when
-// exactly one of them is the strong orbital), the inter term for different subspaces.
+// One CTA.  E_hf: pairs (f, g) of the N_Omega strong orbitals, each H_gg and
+// (2 J_fg - K_fg) weighted by the occupations of the HF density matrix of Eq. HFL (w = 1 for
+// the strong orbital of a pair, 1/2 for a singly occupied one: 2n_g = 2 and 2n_g = 1), and
+// the self-interaction J_gg / 4 of every singly occupied g removed; E_sta: pairs (p, q) of
+// the active orbitals, the intra-pair term for p != q in one pair subspace (Pi_qp negative
+// when exactly one of them is the strong orbital), the inter term for different subspaces.
 __global__ void __launch_bounds__(kThreads) k_nofmp2_static(
     Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
     const double* __restrict__ sqn, const double* __restrict__ phi, const double* __restrict__ Hd,
@@ -35,9 +38,10 @@ __global__ void __launch_bounds__(kThreads) k_nofmp2_static(
   double hf = 0.0;
   for (int i = threadIdx.x; i < n_omega * n_omega; i += kThreads) {
     const int f = i / n_omega, g = i % n_omega;
-    hf += 2.0 * J[(size_t)f * A + g] - K[(size_t)f * A + g];
+    const double wf = f < npair ? 1.0 : 0.5, wg = g < npair ? 1.0 : 0.5;
+    hf += wf * wg * (2.0 * J[(size_t)f * A + g] - K[(size_t)f * A + g]);
     if (f == g) {
-      hf += 2.0 * Hd[g];
+      hf += 2.0 * wg * Hd[g];
       if (g >= npair) hf -= J[(size_t)g * A + g] / 4.0;
     }
   }
