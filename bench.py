@@ -40,7 +40,6 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-slices", type=int, default=480)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -165,10 +164,11 @@ def make_inputs(w, seed, dev):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(w, seed, slices):
-    """The FP64 oracle on the large workload with `slices` of its naux auxiliary slices:
-    the naux-dependent part (AO operators) is scaled linearly to the full naux, the rest
-    (MO integrals, energy, G, lambda, dE/dgamma) is timed once.  Returns seconds per build."""
+def oracle_streamed_build(w, seed, nsteps=1, on_step=None):
+    """One full FP64 oracle build of the workload (E, lambda, dE/dgamma, dE/dC), its operator
+    route streamed over nsteps blocks of auxiliary slices (oracle.pnof.build_streamed).  The
+    inputs are regenerated block by block outside the timed parts.  Returns (result, list
+    of per-block oracle seconds; the last one includes the work after the final block)."""
     import numpy as np
 
     import synth
@@ -176,22 +176,62 @@ def cpu_oracle_sample(w, seed, slices):
     N, Q = w["nbf"], w["naux"]
     prob = synth.Problem(N, Q, w["npair"], w["ncwo"], seed)
     d = synth.generate(prob, with_B=False)
-    B = synth.gen_B(seed, Q, N, packed=False, p0=0, p1=slices)
-    pm = d["pair_map"]
-    C_act = d["C"][:, : prob.nact]
-    t0 = time.perf_counter()
-    occ = pnof.occupations(d["gamma"], pm, prob.npair, prob.ncwo)
-    Jq, Kq = pnof.ao_operators(B, C_act)
-    t1 = time.perf_counter()
-    J, K = pnof.mo_jk(C_act, Jq, Kq)
-    Hd = np.einsum("mp,mn,np->p", C_act, d["h"], C_act)
-    pnof.energy(Hd, J, K, occ, pm, prob.npair, pnof.PNOF7)
-    G = pnof.generalized_fock_action(d["h"], C_act, Jq, Kq, occ, pm, prob.npair, pnof.PNOF7)
-    _ = d["C"].T @ G
-    pnof.occupation_gradient(Hd, J, K, occ, pm, prob.npair, pnof.PNOF7)
-    t2 = time.perf_counter()
-    per_build = (t1 - t0) * (Q / slices) + (t2 - t1)
-    return per_build, (t2 - t0)
+    bounds = [Q * k // nsteps for k in range(nsteps + 1)]
+    ready, done = [], []
+
+    def blocks():
+        for k in range(nsteps):
+            blk = synth.gen_B(seed, Q, N, packed=False, p0=bounds[k], p1=bounds[k + 1])
+            ready.append(time.perf_counter())
+            yield blk
+
+    def mark(_n):
+        done.append(time.perf_counter())
+        if on_step is not None:
+            on_step(len(done), done[-1] - ready[-1])
+
+    res = pnof.build_streamed(d["h"], blocks(), d["C"], d["gamma"], d["pair_map"], prob.npair,
+                              prob.ncwo, pnof.PNOF7, on_block=mark)
+    t_end = time.perf_counter()
+    steps = [b - a for a, b in zip(ready, done)]
+    steps[-1] += t_end - done[-1]
+    return res, np.array(steps)
+
+
+def oracle_block_sample(w, seed, k, nblk):
+    """Untimed warm-up work for the reference arm: the oracle's AO operators on block k of
+    nblk blocks of auxiliary slices."""
+    import synth
+    from oracle import pnof
+    N, Q = w["nbf"], w["naux"]
+    prob = synth.Problem(N, Q, w["npair"], w["ncwo"], seed)
+    d = synth.generate(prob, with_B=False)
+    p0, p1 = Q * k // nblk, Q * (k + 1) // nblk
+    blk = synth.gen_B(seed, Q, N, packed=False, p0=p0, p1=p1)
+    pnof.ao_operators(blk, d["C"][:, :prob.nact])
+
+
+def oracle_small_medians(reps=5):
+    """Builds/s of the FP64 oracle on the plain, differentiation and precision workloads:
+    the median of `reps` timed builds each (inputs generated beforehand)."""
+    import numpy as np
+
+    import synth
+    from oracle import pnof
+    out = {}
+    for name in ("plain", "differentiation", "precision"):
+        prob, packed = synth.config_problem(name)
+        d = synth.generate(prob, packed=packed)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            pnof.build(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], prob.npair, prob.ncwo,
+                       pnof.PNOF7, packed=packed)
+            ts.append(time.perf_counter() - t0)
+        med = float(np.median(ts))
+        out[name] = {"shape": f"{prob.nbf}/{prob.naux}/{prob.npair}/{prob.ncwo}",
+                     "builds_per_s": 1.0 / med, "median_s": med, "runs": reps}
+    return out
 
 
 def blas_threads():
@@ -247,29 +287,34 @@ def recorded_traffic(kernel_src):
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The FP64 CPU oracle on the host cores, the same workload as our arm.  The K timed steps
+    together are exactly one full build: step k runs the oracle's operator route on block k of
+    K blocks of auxiliary slices (the last step also the work after the final block), so
+    value = 1 build / (sum of the step times), with nothing extrapolated.  Warm-up: W blocks,
+    untimed.  Rank 0 only under torchrun."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    slices = max(8, min(args.cpu_slices, 96))
-    for _ in range(args.warmup):
-        cpu_oracle_sample(w, args.seed, slices)
-    times = []
-    for _ in range(args.steps):
-        per_build, _wall = cpu_oracle_sample(w, args.seed, slices)
-        times.append(per_build)
-    value = len(times) / sum(times)
+    for k in range(args.warmup):
+        oracle_block_sample(w, args.seed, k % args.steps, args.steps)
+    _, steps = oracle_streamed_build(w, args.seed, nsteps=args.steps)
+    total = float(steps.sum())
+    value = 1.0 / total
     cores = blas_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: nbf={w['nbf']}, naux={w['naux']}, npair={w['npair']}, "
-                               f"ncwo={w['ncwo']}, PNOF7, FP64 CPU oracle"},
+        "config": {"workload": f"{args.workload}: nbf={w['nbf']}, naux={w['naux']}, "
+                               f"npair={w['npair']}, ncwo={w['ncwo']}, PNOF7, FP64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{slices} of {w['naux']} auxiliary slices per step; the "
-                                   "naux-dependent part scaled linearly to the full naux"},
+                         "sample": f"one full build of the workload, its {w['naux']} auxiliary "
+                                   f"slices streamed in {args.steps} blocks, one block per "
+                                   "step (the last step also forms J, K, E, G, lambda and "
+                                   "dE/dgamma); input generation untimed",
+                         "step_s": [round(float(x), 3) for x in steps]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -326,16 +371,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     dn.donof_profile_enable(True)
     launches0 = dn.donof_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
+    # one event per step boundary on the launching stream (the library launches on torch's
+    # current stream): the total over K steps gives `value`, the per-step times the median
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record()
+    for k in range(args.steps):
         out = step()
-    e1.record()
+        evs[k + 1].record()
     torch.cuda.synchronize()
     barrier()
     launches = dn.donof_launch_count() - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = evs[0].elapsed_time(evs[-1]) / args.steps
+    step_ms = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    ms_median = step_ms[len(step_ms) // 2] if args.steps % 2 else \
+        0.5 * (step_ms[args.steps // 2 - 1] + step_ms[args.steps // 2])
     phases = {}
     for i, nm in enumerate(dn.PHASES):
         t, n = dn.donof_profile_read(i)
@@ -494,13 +544,31 @@ def run_ours(args):
             "orbital_update_ms": upd_ms,
         }
 
+    # ---------------- errors against the FP64 oracle's stored values (large workload)
+    oracle_err = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"large_seed{args.seed}.npz")
+    if args.workload == "large" and not args.naux and os.path.exists(gpath):
+        z = np.load(gpath)
+        oracle_err = {"source": f"tests/golden/large_seed{args.seed}.npz (FP64 oracle, streamed)"}
+        paths = [("mixed", res_mixed)] + ([("fp64", r64)] if fp64 else [])
+        for nm, r in paths:
+            oracle_err[nm] = {
+                "E_abs": float(abs(r[0][0] - z["E"][0])),
+                "lambda_maxabs": float(np.abs(r[1][:, :A] - z["lam_act"]).max()),
+                "dE_dgamma_maxabs": float(np.abs(r[2] - z["dE_dgamma"]).max()),
+                "dE_dC_maxabs": float(np.abs(r[3][:, :A] - z["dE_dC_act"]).max()),
+            }
+
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
-        per_build, wall = cpu_oracle_sample(w, args.seed, args.cpu_slices)
-        cpu = {"value": 1.0 / per_build, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"{args.cpu_slices} of {Q} auxiliary slices ({wall:.1f} s wall); "
-                         "naux-dependent part scaled linearly to the full naux"}
+        _, steps = oracle_streamed_build(w, args.seed, nsteps=20)
+        cpu = {"value": 1.0 / float(steps.sum()), "unit": UNIT, "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": f"one full build of the workload ({float(steps.sum()):.1f} s), the "
+                         f"{Q} auxiliary slices streamed in 20 blocks; input generation "
+                         "untimed",
+               "small_workloads_median_of_5": oracle_small_medians(5)}
 
     # ---------------- roofline of the dominant kernel (half transform X = B C)
     pk, src = peaks()
@@ -534,7 +602,10 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_max, "ms_per_step_median": ms_median,
+            "timing_note": "value = K steps / their total CUDA-event time (mean step); "
+                           "ms_per_step_median = the median of the per-step event times",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f16 integer+fraction split operands (4 products, exact integer "
                      "accumulation) for X, b and G; fp32 J/K/Y; f64 reductions and outputs",
@@ -550,6 +621,7 @@ def run_ours(args):
             "tflops_algorithmic": flops_build(N, Q, A) * ws / (ms_max * 1e-3) / 1e12,
             "phases_ms": {k: v["ms_per_launch"] for k, v in phases.items()},
             "fp64_path": fp64,
+            "oracle_errors": oracle_err,
             "optimisation_loop": loop,
             "batch_workload": batch,
             "roofline": roof,
