@@ -276,16 +276,25 @@ int donof_optimize(const donof_problem* prob, const donof_opt_params* params, co
  * Scratch: a fixed 64 MiB array in device global memory, held by every GPU that loads the
  * library until the process exits.  Problems whose donof_workspace_size exceeds it are
  * rejected with DONOF_ERR_WORKSPACE before any device work.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call on a device shares the
- * array and leaves its contents behind: the call clears what must start at zero itself,
- * and calls whose device work overlaps (other streams, other threads) race on it.
- * Device-side status (pair_map / non-finite checks) is not reported by this entry point.
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current (and
+ * looks it up again after a reset of the device's context); make that first call before
+ * any stream capture.  Every call on a device shares the array and leaves its contents
+ * behind: the call clears what must start at zero itself.  Calls from several host threads
+ * on one device are serialised on the host; calls whose device work overlaps (other
+ * streams) race on the array.
+ * Device-side checks (pair_map contents, non-finite gamma, B, C or results, kernel wait
+ * limits) write the status word at the head of the array; donof_noalloc_read_status reads
+ * it.  The next call clears it, so read it before the next call.
  * No cudaMalloc, cudaFree or allocating library routine is called. */
 int donof_energy_lagrangian_noalloc(const donof_problem* prob, const double* h, const double* B,
                                     const double* C, const double* gamma,
                                     const int32_t* pair_map, double* E, double* lam,
                                     double* dE_dgamma, double* dE_dC, void* stream);
+
+/* Synchronises `stream`, then returns in *status (host) the device status word of the last
+ * donof_energy_lagrangian_noalloc call on the current device (DONOF_OK or a DONOF_ERR_*
+ * code) and clears it.  Allocates nothing. */
+int donof_noalloc_read_status(int32_t* status, void* stream);
 
 /* Tile autotuner (DONOF_MIXED): times each tensor-core contraction of a build with K tiles
  * of 64 and of 32 elements (a few builds on the given inputs, B already prepared) and keeps

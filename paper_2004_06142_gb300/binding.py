@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
         L.donof_status_string.argtypes = [ctypes.c_int]
         L.donof_status_string.restype = ctypes.c_char_p
         L.donof_energy_lagrangian_noalloc.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.donof_noalloc_read_status.argtypes = [ctypes.POINTER(ctypes.c_int32), vp]
         PI = ctypes.POINTER(donof_instance)
         L.donof_batched_workspace_size.argtypes = [ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_prepare_B_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, vp]
@@ -119,6 +120,7 @@ def lib() -> ctypes.CDLL:
         for f in ("donof_workspace_size", "donof_prepare_B", "donof_energy_lagrangian",
                   "donof_energy_backward", "donof_get_jk", "donof_read_status",
                   "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
+                  "donof_noalloc_read_status",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
                   "donof_orbital_update", "donof_autotune", "donof_optimize_occupations",
@@ -187,6 +189,14 @@ def donof_energy_lagrangian_noalloc(prob, h, B, C, gamma, pair_map, E, lam=None,
                                                  _ptr(gamma), _ptr(pair_map), _ptr(E), _ptr(lam),
                                                  _ptr(dE_dgamma), _ptr(dE_dC), _stream(stream)),
            "donof_energy_lagrangian_noalloc")
+
+
+def donof_noalloc_read_status(stream=None) -> int:
+    """Device status of the last allocation-free build on the current device (then cleared)."""
+    st = ctypes.c_int32(0)
+    _check(lib().donof_noalloc_read_status(ctypes.byref(st), _stream(stream)),
+           "donof_noalloc_read_status")
+    return st.value
 
 
 def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):

@@ -6,6 +6,8 @@
 // device and fail under fragmentation) is not acceptable.  For small problems they can use
 // this entry point: its scratch is a fixed array in device global memory that exists for
 // as long as the library is loaded, so nothing is allocated or freed per call.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -23,25 +25,62 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 // Upstream gradient 1.0 for the optional dE/dC (a constant, not scratch).
 __device__ double g_noalloc_one = 1.0;
 
-std::mutex g_noalloc_mu;
+// One lock per device, held for a whole call: the host-side registration of the scratch
+// (donof_prepare_B) and the enqueue of the build and adjoint of one call are never
+// interleaved with another thread's call on the same device.
+std::mutex g_noalloc_mu[kMaxDevices];
 void* g_scratch_ptr[kMaxDevices] = {};
 double* g_one_ptr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // context the addresses belong to
 
-// Once per device, with that device current: resolve the device addresses of the arrays.
+// Unique id of the current context (cuCtxGetId; 0 when it cannot be read).  A device reset
+// destroys the primary context, and the module holding the scratch is loaded again, possibly
+// elsewhere, in the next one: the cached addresses are then resolved again.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrentFn)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (GetIdFn)p;
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+      get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Set-up, once per device (and again after a reset of its context), with that device
+// current: resolve the device addresses of the arrays.  Called with g_noalloc_mu[dev] held.
 int noalloc_setup(int dev, void** scratch, double** one) {
-  if (dev < 0 || dev >= kMaxDevices) return DONOF_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx != g_ctx_id[dev]) {
     void* p = nullptr;
     void* q = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return DONOF_ERR_CUDA;
     if (cudaGetSymbolAddress(&q, g_noalloc_one) != cudaSuccess) return DONOF_ERR_CUDA;
     g_scratch_ptr[dev] = p;
     g_one_ptr[dev] = (double*)q;
+    g_ctx_id[dev] = ctx;
   }
   *scratch = g_scratch_ptr[dev];
   *one = g_one_ptr[dev];
   return DONOF_OK;
+}
+
+int current_device(int* dev) {
+  if (cudaGetDevice(dev) != cudaSuccess) return DONOF_ERR_CUDA;
+  return (*dev < 0 || *dev >= kMaxDevices) ? DONOF_ERR_UNSUPPORTED : DONOF_OK;
 }
 
 }  // namespace
@@ -58,7 +97,9 @@ extern "C" int donof_energy_lagrangian_noalloc(const donof_problem* prob, const 
   if (rc != DONOF_OK) return rc;
   if (need > kNoAllocScratchBytes) return DONOF_ERR_WORKSPACE;  // problem too large
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DONOF_ERR_CUDA;
+  rc = current_device(&dev);
+  if (rc != DONOF_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu[dev]);
   void* scratch = nullptr;
   double* one = nullptr;
   rc = noalloc_setup(dev, &scratch, &one);
@@ -73,4 +114,19 @@ extern "C" int donof_energy_lagrangian_noalloc(const donof_problem* prob, const 
   if (dE_dC) rc = donof_energy_backward(prob, one, scratch, kNoAllocScratchBytes, dE_dC, nullptr,
                                         stream);
   return rc;
+}
+
+extern "C" int donof_noalloc_read_status(int32_t* status, void* stream) {
+  using namespace donof;
+  if (!status) return DONOF_ERR_INVALID_ARG;
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc != DONOF_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu[dev]);
+  void* scratch = nullptr;
+  double* one = nullptr;
+  rc = noalloc_setup(dev, &scratch, &one);
+  if (rc != DONOF_OK) return rc;
+  // the status word heads the scratch (it is the workspace header of every call)
+  return donof_read_status(scratch, status, stream);
 }
