@@ -277,8 +277,9 @@ int check_ws(const donof_problem* p, const void* ws, size_t bytes) {
 }  // namespace
 
 // C(m, n) += sum_k A(m, k) B(k, n) for an M x N output with a long contraction K: the
-// contraction is cut into 64-wide chunks shared by enough CTAs to fill the GPU (atomic
-// double accumulation, so C must be initialised).
+// contraction is cut into 64-wide chunks shared by enough CTAs to fill the GPU; each CTA
+// writes its partial product to scratch and a second kernel adds the partials to C in a
+// fixed order (so C must be initialised, and the result does not depend on scheduling).
 namespace {
 // 64-wide chunks of the contraction, or 16-wide ones when even all 64-wide chunks would
 // leave most SMs idle (small problems: the narrow FP64 pipe makes every CTA's share count)

@@ -162,7 +162,6 @@ __device__ inline void intfrac_split(float y, __half& h, __half& f) {
 // C[b](m, n) = alpha * sum_{kb, k} A(m, kb, k) B(kb, k, n) + beta * C[b](m, n)
 // with A(m, kb, k) = A[b*sAb + m*sAm + kb*sAkb + k*sAk] and
 //      B(kb, k, n) = B[b*sBb + kb*sBkb + k*sBk + n*sBn];
-// ksplit > 1 splits the kb range over CTAs and accumulates with atomicAdd (beta must be 1).
 // Ktot > 0 limits the flattened contraction index kb*K + k to [0, Ktot) (used to split one
 // long contraction into KB chunks of K that ksplit CTAs share).
 // Output tile width of k_dgemm: 32 where it pads the width less than 64 does.

@@ -1,9 +1,9 @@
 """Batched builds (donof_energy_lagrangian_batched) on instances of the dissociation-scan
 workload: uneven nbf in 40..240, naux = 4 nbf, 5 pairs, Ncwo in 1..4, one seed per instance.
 
-Every instance of a batched call must reproduce the single-instance entry point (same
-kernels; only the order of floating-point atomics may differ) and the oracle within the
-parity tolerances, with and without CUDA-graph capture/replay.
+Every instance of a batched call must reproduce the single-instance entry point (the same
+kernels, every sum in a fixed order) and the oracle within the parity tolerances, with and
+without CUDA-graph capture/replay.
 """
 import numpy as np
 import pytest
