@@ -4,7 +4,9 @@
 One step = one build (E, lambda, dE/dgamma) plus its adjoint (dE/dC) of the large
 workload: nbf 1200, naux 4800, 50 pairs, Ncwo 2 (150 active orbitals), packed B,
 mixed precision, inputs resident in HBM (the 27.6 GB split copy of B that each build
-streams is far larger than L2).  Prints one JSON line.
+streams is far larger than L2).  Prints one JSON line.  Under torchrun (--gpus N) the
+ranks share each build: the auxiliary index is sharded over them and one NCCL all-reduce
+of the partial sums J, K and the two-electron G finishes it (strong scaling).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -84,9 +86,10 @@ def max_over_ranks(ms, ws, device):
     return t.item()
 
 
-def job_rate(ms_max, ws):
-    """Whole-job builds/s: every rank builds one instance per step (weak scaling)."""
-    return ws * 1e3 / ms_max
+def job_rate(ms_max, builds_per_step=1):
+    """Whole-job builds/s over the slowest rank's step time.  Under torchrun the ranks share
+    one build per step (its auxiliary index sharded over them), so builds_per_step is 1."""
+    return builds_per_step * 1e3 / ms_max
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -143,21 +146,25 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- inputs
-def make_inputs(w, seed, dev):
+def make_inputs(w, seed, dev, P0=0, P1=None):
+    """The workload's inputs on the device; of B only the auxiliary slices [P0, P1)."""
     import numpy as np
     import torch
 
     import synth
     N, Q = w["nbf"], w["naux"]
+    P1 = Q if P1 is None else P1
     prob = synth.Problem(N, Q, w["npair"], w["ncwo"], seed)
     d = synth.generate(prob, with_B=False)
     npk = N * (N + 1) // 2
-    B = torch.empty((Q, npk) if w["packed"] else (Q, N, N), dtype=torch.float64, device=dev)
+    nloc = P1 - P0
+    B = torch.empty((nloc, npk) if w["packed"] else (nloc, N, N), dtype=torch.float64,
+                    device=dev)
     chunk = 160
-    for p0 in range(0, Q, chunk):
-        p1 = min(Q, p0 + chunk)
+    for p0 in range(P0, P1, chunk):
+        p1 = min(P1, p0 + chunk)
         host = synth.gen_B(seed, Q, N, packed=w["packed"], p0=p0, p1=p1)
-        B[p0:p1].copy_(torch.from_numpy(host))
+        B[p0 - P0:p1 - P0].copy_(torch.from_numpy(host))
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     return prob, d, dict(B=B, h=t(d["h"]), C=t(d["C"]), gamma=t(d["gamma"]),
                          pair_map=t(d["pair_map"].astype(np.int32)))
@@ -340,7 +347,12 @@ def run_ours(args):
     if args.naux:
         w["naux"] = args.naux
     N, Q = w["nbf"], w["naux"]
-    prob, host, x = make_inputs(w, args.seed, dev)
+    # with several ranks the auxiliary index is sharded: rank r holds slices [P0, P1) of B,
+    # builds its partial sums, and one all-reduce (NCCL) of J, K and the two-electron G
+    # precedes the finish on every rank (Sec. III.D: these are sums over P)
+    P0, P1 = dn.shard_range(Q, rank, ws)
+    Qloc = P1 - P0
+    prob, host, x = make_inputs(w, args.seed, dev, P0, P1)
     A = prob.nact
     layout = dn.B_PACKED if w["packed"] else dn.B_DENSE
 
@@ -348,13 +360,18 @@ def run_ours(args):
         if ws > 1:
             tdist.barrier()
 
-    mixed = dn.Builder(N, Q, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.MIXED, device=dev)
+    mixed = dn.Builder(N, Qloc, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.MIXED, device=dev)
     mixed.prepare(x["B"])
     mixed.autotune(x["h"], x["C"], x["gamma"], x["pair_map"])
     Ebar = torch.ones(1, dtype=torch.float64, device=dev)
 
+    def forward(C, g):
+        if ws > 1:
+            return mixed.forward_sharded(x["h"], C, g, x["pair_map"])
+        return mixed.forward(x["h"], C, g, x["pair_map"])
+
     def step():
-        E, lam, dEdg = mixed.forward(x["h"], x["C"], x["gamma"], x["pair_map"])
+        E, lam, dEdg = forward(x["C"], x["gamma"])
         dC, dg = mixed.backward(Ebar)
         return E, lam, dEdg, dC
 
@@ -393,7 +410,7 @@ def run_ours(args):
             phases[nm] = {"ms_per_launch": t / n, "intervals": n}
     dn.donof_profile_enable(False)
     ms_max = max_over_ranks(ms, ws, dev)
-    value = job_rate(ms_max, ws)
+    value = job_rate(ms_max)
     E_mixed = out[0].item()
     res_mixed = [t.detach().cpu().numpy() for t in out]
 
@@ -411,7 +428,7 @@ def run_ours(args):
     def e2e_step():
         Cd.copy_(hC, non_blocking=True)
         gd.copy_(hg, non_blocking=True)
-        E, lam, dEdg = mixed.forward(x["h"], Cd, gd, x["pair_map"])
+        E, lam, dEdg = forward(Cd, gd)
         dC, _ = mixed.backward(Ebar)
         oE.copy_(E, non_blocking=True)
         olam.copy_(lam, non_blocking=True)
@@ -434,14 +451,14 @@ def run_ours(args):
 
     # ---------------- the batched workload: 64 uneven instances in one graph launch
     batch = None
-    if not args.no_batch:
+    if not args.no_batch and ws == 1:
         batch = run_batch(dn, dev, args.steps, args.warmup)
         batch["small_workloads"] = run_small_workloads(dn, dev, args.steps, args.warmup)
 
     # ---------------- the optimisation procedure around the build (occupation optimisation +
     # orbital iterations), mixed builds, on copies of C and gamma
     loop = None
-    if not args.no_loop and rank == 0:
+    if not args.no_loop and ws == 1:
         kw = dict(diis_depth=6, zeta=1.0, delta=1e-12, eps_energy=0.0, occ_max_iter=200,
                   occ_gtol=1e-10)
         Cl, gl = x["C"].clone(), x["gamma"].clone()
@@ -471,7 +488,7 @@ def run_ours(args):
 
     # ---------------- the plain FP64 GPU path on the same inputs
     fp64 = None
-    if not args.no_fp64 and rank == 0:
+    if not args.no_fp64 and ws == 1:
         del mixed
         torch.cuda.empty_cache()
         b64 = dn.Builder(N, Q, prob.npair, prob.ncwo, dn.PNOF7, layout, dn.FP64,
@@ -578,8 +595,8 @@ def run_ours(args):
     half = phases.get("half_transform", {}).get("ms_per_launch")
     roof = None
     if half:
-        flops_half = 2.0 * Q * N * N * A
-        hbm_bytes = split_b_bytes(Q, N) + Q * N * ((A + 15) // 16 * 16) * 8
+        flops_half = 2.0 * Qloc * N * N * A
+        hbm_bytes = split_b_bytes(Qloc, N) + Qloc * N * ((A + 15) // 16 * 16) * 8
         achieved = flops_half / (half * 1e-3) / 1e12
         peak_eff = peak_f16 / 4.0
         traffic = recorded_traffic(os.path.join(ROOT, "paper_2004_06142_gb300", "csrc", "tc.cu"))
@@ -590,7 +607,7 @@ def run_ours(args):
                              f"{region_s:.2f} s, SM clock median {mhz} of {mhz_max} MHz) / 4 "
                              "tensor products per algorithmic product (h*h + h*f + f*h + f*f "
                              "of the integer + fraction split)",
-                "issued_tflops": 4 * 2.0 * Q * N * N * ((A + 15) // 16 * 16) / (half * 1e-3) / 1e12,
+                "issued_tflops": 4 * 2.0 * Qloc * N * N * ((A + 15) // 16 * 16) / (half * 1e-3) / 1e12,
                 "hbm_gbs": hbm_bytes / (half * 1e-3) / 1e9,
                 "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]),
                 "hbm_frac": hbm_bytes / (half * 1e-3) / 1e9 / pk.get("hbm_gbs",
@@ -606,7 +623,7 @@ def run_ours(args):
             "timing_note": "value = K steps / their total CUDA-event time (mean step); "
                            "ms_per_step_median = the median of the per-step event times",
             "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None,
             "dtype": "f16 integer+fraction split operands (4 products, exact integer "
                      "accumulation) for X, b and G; fp32 J/K/Y; f64 reductions and outputs",
             "data": "synthetic",
@@ -617,8 +634,10 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (the split B's stored triangle, "
                              f"{split_b_bytes(Q, N) / 1e9:.1f} GB, "
                              "streamed per build)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "tflops_algorithmic": flops_build(N, Q, A) * ws / (ms_max * 1e-3) / 1e12,
+                       "parallelism": (f"auxiliary index sharded over {ws} GPUs ({Qloc} slices "
+                                       "on rank 0), one NCCL all-reduce of J, K and the "
+                                       "two-electron G per build") if ws > 1 else "single GPU"},
+            "tflops_algorithmic": flops_build(N, Q, A) / (ms_max * 1e-3) / 1e12,
             "phases_ms": {k: v["ms_per_launch"] for k, v in phases.items()},
             "fp64_path": fp64,
             "oracle_errors": oracle_err,
@@ -626,7 +645,7 @@ def run_ours(args):
             "batch_workload": batch,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": job_rate(ms_e2e, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "note": "per step: C and gamma host->device, E, lambda, dE/dgamma, dE/dC "
                             "device->host; B and h stay resident (fixed across orbital "

@@ -124,6 +124,36 @@ int donof_energy_lagrangian(const donof_problem* prob, const double* h, const do
 int donof_energy_backward(const donof_problem* prob, const double* Ebar, const void* workspace,
                           size_t workspace_bytes, double* dE_dC, double* dE_dgamma, void* stream);
 
+/* A build sharded over the auxiliary index, one shard per GPU (Sec. III.D: J_pq, K_pq of
+ * Eq. JKpq and the exchange and Coulomb operators of Eq. Gpmn are sums over the auxiliary
+ * functions P of the density-fitted integrals, and so is the two-electron part of the
+ * generalised-Fock action G of Eqs. Vee-s, Vee-d).  Each shard holds its own slices of B
+ * and describes them as a problem of its own: `prob` with naux = the slices it holds, its
+ * workspace prepared with donof_prepare_B on those slices.
+ *   donof_partial_size: *count (host) = 2 nact^2 + nbf nact, the doubles of one partial.
+ *   donof_energy_lagrangian_partial: this shard's partial sums (device, caller-owned,
+ *     partial[count]): J[nact][nact], then K[nact][nact], then the two-electron part of
+ *     G[nbf][nact], each a sum over the shard's slices (FP64 path: in double; mixed path:
+ *     as in donof_energy_lagrangian).
+ *   (the caller sums the partials of all shards elementwise, e.g. an all-reduce)
+ *   donof_energy_lagrangian_finish: from the summed partial (device) and the shard's own
+ *     h, C, gamma, pair_map, forms what a full build forms after its sums over P: E,
+ *     lambda, dE/dgamma (outputs as in donof_energy_lagrangian), and leaves G, J, K in the
+ *     workspace, so that donof_energy_backward and donof_get_jk work after it.  It reads no
+ *     B.  Every shard may finish (the results agree), or only one.
+ * The summed partials reproduce a full build on all the slices up to the order of the sums
+ * over P. */
+int donof_partial_size(const donof_problem* prob, size_t* count);
+int donof_energy_lagrangian_partial(const donof_problem* prob, const double* h, const double* B,
+                                    const double* C, const double* gamma,
+                                    const int32_t* pair_map, void* workspace,
+                                    size_t workspace_bytes, double* partial, void* stream);
+int donof_energy_lagrangian_finish(const donof_problem* prob, const double* h, const double* C,
+                                   const double* gamma, const int32_t* pair_map,
+                                   const double* partial, void* workspace,
+                                   size_t workspace_bytes, double* E, double* lam,
+                                   double* dE_dgamma, void* stream);
+
 /* Copies J[nact*nact] and K[nact*nact] (device) of the last build in `workspace`. */
 int donof_get_jk(const donof_problem* prob, const void* workspace, size_t workspace_bytes,
                  double* J, double* K, void* stream);

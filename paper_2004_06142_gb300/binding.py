@@ -92,6 +92,9 @@ def lib() -> ctypes.CDLL:
         L.donof_energy_lagrangian.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp]
         L.donof_energy_backward.argtypes = [P, vp, vp, sz, vp, vp, vp]
         L.donof_get_jk.argtypes = [P, vp, sz, vp, vp, vp]
+        L.donof_partial_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_energy_lagrangian_partial.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp, vp]
+        L.donof_energy_lagrangian_finish.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp]
         L.donof_read_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
         L.donof_status_string.argtypes = [ctypes.c_int]
         L.donof_status_string.restype = ctypes.c_char_p
@@ -120,7 +123,8 @@ def lib() -> ctypes.CDLL:
         for f in ("donof_workspace_size", "donof_prepare_B", "donof_energy_lagrangian",
                   "donof_energy_backward", "donof_get_jk", "donof_read_status",
                   "donof_profile_enable", "donof_profile_read", "donof_energy_lagrangian_noalloc",
-                  "donof_noalloc_read_status",
+                  "donof_noalloc_read_status", "donof_partial_size",
+                  "donof_energy_lagrangian_partial", "donof_energy_lagrangian_finish",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
                   "donof_orbital_update", "donof_autotune", "donof_optimize_occupations",
@@ -173,6 +177,44 @@ def donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, E, lam=None, dE_
                                          _ptr(pair_map), _ptr(ws), ws.numel(), _ptr(E), _ptr(lam),
                                          _ptr(dE_dgamma), _stream(stream)),
            "donof_energy_lagrangian")
+
+
+def donof_partial_size(prob: donof_problem) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().donof_partial_size(ctypes.byref(prob), ctypes.byref(n)), "donof_partial_size")
+    return n.value
+
+
+def donof_energy_lagrangian_partial(prob, h, B, C, gamma, pair_map, ws, partial, stream=None):
+    _check(lib().donof_energy_lagrangian_partial(ctypes.byref(prob), _ptr(h), _ptr(B), _ptr(C),
+                                                 _ptr(gamma), _ptr(pair_map), _ptr(ws),
+                                                 ws.numel(), _ptr(partial), _stream(stream)),
+           "donof_energy_lagrangian_partial")
+
+
+def donof_energy_lagrangian_finish(prob, h, C, gamma, pair_map, partial, ws, E, lam=None,
+                                   dE_dgamma=None, stream=None):
+    _check(lib().donof_energy_lagrangian_finish(ctypes.byref(prob), _ptr(h), _ptr(C), _ptr(gamma),
+                                                _ptr(pair_map), _ptr(partial), _ptr(ws),
+                                                ws.numel(), _ptr(E), _ptr(lam), _ptr(dE_dgamma),
+                                                _stream(stream)),
+           "donof_energy_lagrangian_finish")
+
+
+def shard_range(naux: int, rank: int, world: int):
+    """The auxiliary slices [P0, P1) of shard `rank` out of `world`: contiguous, sizes
+    differing by at most one."""
+    return naux * rank // world, naux * (rank + 1) // world
+
+
+def exchange_partial(partial: torch.Tensor, group=None) -> torch.Tensor:
+    """The one exchange of a sharded build: every rank's partial sums (J, K, two-electron G)
+    replaced in place by their sum over the ranks of the process group (an all-reduce; NCCL
+    for device tensors, gloo for host tensors).  Returns `partial`."""
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size(group) > 1:
+        tdist.all_reduce(partial, op=tdist.ReduceOp.SUM, group=group)
+    return partial
 
 
 def donof_energy_backward(prob, Ebar, ws, dE_dC=None, dE_dgamma=None, stream=None):
@@ -296,6 +338,33 @@ class Builder:
         dEdg = torch.empty(self.ngamma, dtype=f64, device=dev)
         donof_energy_lagrangian(self.prob, h, self.B, C, gamma, pair_map, self.ws, E, lam, dEdg)
         return E, lam, dEdg
+
+    def forward_partial(self, h, C, gamma, pair_map, partial=None):
+        """This shard's partial sums (J, K, two-electron G) over the slices of the prepared B,
+        as one flat double tensor of donof_partial_size elements."""
+        if partial is None:
+            partial = torch.empty(donof_partial_size(self.prob), dtype=torch.float64,
+                                  device=self.device)
+        donof_energy_lagrangian_partial(self.prob, h, self.B, C, gamma, pair_map, self.ws, partial)
+        return partial
+
+    def finish(self, h, C, gamma, pair_map, partial, want_lam=True):
+        """E, lambda, dE/dgamma from the partial sums of every shard, summed."""
+        dev, f64 = self.device, torch.float64
+        E = torch.empty(1, dtype=f64, device=dev)
+        lam = torch.empty(self.nbf, self.nbf, dtype=f64, device=dev) if want_lam else None
+        dEdg = torch.empty(self.ngamma, dtype=f64, device=dev)
+        donof_energy_lagrangian_finish(self.prob, h, C, gamma, pair_map, partial, self.ws, E, lam,
+                                       dEdg)
+        return E, lam, dEdg
+
+    def forward_sharded(self, h, C, gamma, pair_map, group=None, want_lam=True):
+        """One build of a problem whose auxiliary index is sharded over the ranks of a
+        torch.distributed process group (this Builder holds this rank's slices): the shard's
+        partial sums, their all-reduce (sum) over the group, then E, lambda, dE/dgamma on every
+        rank."""
+        partial = exchange_partial(self.forward_partial(h, C, gamma, pair_map), group)
+        return self.finish(h, C, gamma, pair_map, partial, want_lam)
 
     def backward(self, Ebar):
         dev, f64 = self.device, torch.float64

@@ -347,27 +347,36 @@ extern "C" int donof_prepare_B(const donof_problem* prob, const double* B, void*
   return DONOF_OK;
 }
 
-extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* h, const double* B,
-                                       const double* C, const double* gamma,
-                                       const int32_t* pair_map, void* workspace,
-                                       size_t workspace_bytes, double* E, double* lam,
-                                       double* dE_dgamma, void* stream) {
+namespace donof {
+namespace {
+// What one call of the build runs: the whole build; one shard of a build sharded over the
+// auxiliary index (its two-electron partial sums J, K and G, nothing after them); or the
+// part after the exchange (E, dE/dgamma, lambda from the summed partial sums).
+enum BuildMode { kFull = 0, kPartial = 1, kFinish = 2 };
+
+int run_build(const donof_problem* prob, const double* h, const double* B, const double* C,
+              const double* gamma, const int32_t* pair_map, void* workspace,
+              size_t workspace_bytes, BuildMode mode, double* partial, double* E, double* lam,
+              double* dE_dgamma, cudaStream_t s) {
   int rc = check_problem(prob);
   if (rc != DONOF_OK) return rc;
-  if (!h || !B || !C || !gamma || !pair_map || !E) return DONOF_ERR_INVALID_ARG;
+  if (!h || !C || !gamma || !pair_map) return DONOF_ERR_INVALID_ARG;
+  if (mode != kPartial && !E) return DONOF_ERR_INVALID_ARG;
+  if (mode != kFull && !partial) return DONOF_ERR_INVALID_ARG;
+  if (mode != kFinish && !B) return DONOF_ERR_INVALID_ARG;
   rc = check_ws(prob, workspace, workspace_bytes);
   if (rc != DONOF_OK) return rc;
-  {
+  if (mode != kFinish) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_reg.find(workspace);
     if (it == g_reg.end() || it->second.B != B || !same_problem(it->second.prob, *prob))
       return DONOF_ERR_NOT_PREPARED;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   const Dims d = make_dims(prob);
   const Layout L = make_layout(d);
   char* ws = (char*)workspace;
   const int N = d.N, A = d.A;
+  const size_t AA = (size_t)A * A * 8;
 
   prof_begin(DONOF_PHASE_PREP, s);
   CK(cudaMemsetAsync(&((DevHeader*)(ws + L.header))->abort_flag, 0, sizeof(int32_t), s));
@@ -376,22 +385,28 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   // hC = h C_act (FP64 DGEMM, or on the tensor cores with residual-extended operands), then
   // H_pp and G = n o hC
   if (d.precision == DONOF_MIXED) {
-    CK(launch_split_C(d, C, h, ws, L, s));
+    CK(launch_split_C(d, C, h, ws, L, mode != kFinish, s));
     rc = run_hc_tc(d, ws, L, s);
     if (rc != DONOF_OK) return rc;
     // bound on ||C_act||_2 for the exponents of X in the G contraction
-    CK(launch_gram_bound(d, C, ws, L, s));
+    if (mode != kFinish) CK(launch_gram_bound(d, C, ws, L, s));
   } else {
     CK(cudaMemsetAsync(ws + L.hC, 0, (size_t)N * A * 8, s));
     CK(launch_dgemm(split_k_args(N, A, N, h, N, 1, C, N, 1, (double*)(ws + L.hC), A, 1,
                                  (double*)(ws + L.skp)), s));
   }
-  CK(launch_hdiag_ginit(d, C, ws, L, s));
-  CK(cudaMemsetAsync(ws + L.J, 0, (size_t)A * A * 8, s));
-  CK(cudaMemsetAsync(ws + L.K, 0, (size_t)A * A * 8, s));
+  CK(launch_hdiag_ginit(d, C, ws, L, mode != kPartial, s));
+  if (mode == kFinish) {  // the summed two-electron parts of every shard
+    CK(cudaMemcpyAsync(ws + L.J, partial, AA, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ws + L.K, partial + (size_t)A * A, AA, cudaMemcpyDeviceToDevice, s));
+    CK(launch_add((double*)(ws + L.G), partial + 2 * (size_t)A * A, (long long)N * A, s));
+  } else {
+    CK(cudaMemsetAsync(ws + L.J, 0, AA, s));
+    CK(cudaMemsetAsync(ws + L.K, 0, AA, s));
+  }
   prof_end(DONOF_PHASE_PREP, s);
 
-  for (int p0 = 0; p0 < d.Q; p0 += d.pb) {
+  for (int p0 = 0; p0 < d.Q && mode != kFinish; p0 += d.pb) {
     const int np = (d.Q - p0) < d.pb ? (d.Q - p0) : d.pb;
     if (d.precision == DONOF_MIXED) {
       rc = run_tc_block(d, p0, np, ws, L, s);
@@ -450,6 +465,14 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
     prof_end(DONOF_PHASE_G_BUILD, s);
   }
 
+  if (mode == kPartial) {  // this shard's J, K and two-electron G, for the exchange
+    CK(cudaMemcpyAsync(partial, ws + L.J, AA, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(partial + (size_t)A * A, ws + L.K, AA, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(partial + 2 * (size_t)A * A, ws + L.G, (size_t)N * A * 8,
+                       cudaMemcpyDeviceToDevice, s));
+    return DONOF_OK;
+  }
+
   prof_begin(DONOF_PHASE_ENERGY_LAMBDA, s);
   CK(launch_energy(d, pair_map, ws, L, E, dE_dgamma, s));
   if (lam) {  // lambda_qp = C_q^T G_p (q < N, p < nact), zero for p >= nact
@@ -465,6 +488,44 @@ extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* 
   }
   prof_end(DONOF_PHASE_ENERGY_LAMBDA, s);
   return DONOF_OK;
+}
+}  // namespace
+}  // namespace donof
+
+extern "C" int donof_energy_lagrangian(const donof_problem* prob, const double* h, const double* B,
+                                       const double* C, const double* gamma,
+                                       const int32_t* pair_map, void* workspace,
+                                       size_t workspace_bytes, double* E, double* lam,
+                                       double* dE_dgamma, void* stream) {
+  return run_build(prob, h, B, C, gamma, pair_map, workspace, workspace_bytes, kFull, nullptr, E,
+                   lam, dE_dgamma, (cudaStream_t)stream);
+}
+
+extern "C" int donof_partial_size(const donof_problem* prob, size_t* count) {
+  const int rc = check_problem(prob);
+  if (rc != DONOF_OK) return rc;
+  if (!count) return DONOF_ERR_INVALID_ARG;
+  const size_t A = (size_t)prob->npair * (1 + prob->ncwo) + prob->nsingle;
+  *count = 2 * A * A + (size_t)prob->nbf * A;
+  return DONOF_OK;
+}
+
+extern "C" int donof_energy_lagrangian_partial(const donof_problem* prob, const double* h,
+                                               const double* B, const double* C,
+                                               const double* gamma, const int32_t* pair_map,
+                                               void* workspace, size_t workspace_bytes,
+                                               double* partial, void* stream) {
+  return run_build(prob, h, B, C, gamma, pair_map, workspace, workspace_bytes, kPartial, partial,
+                   nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int donof_energy_lagrangian_finish(const donof_problem* prob, const double* h,
+                                              const double* C, const double* gamma,
+                                              const int32_t* pair_map, const double* partial,
+                                              void* workspace, size_t workspace_bytes, double* E,
+                                              double* lam, double* dE_dgamma, void* stream) {
+  return run_build(prob, h, nullptr, C, gamma, pair_map, workspace, workspace_bytes, kFinish,
+                   const_cast<double*>(partial), E, lam, dE_dgamma, (cudaStream_t)stream);
 }
 
 extern "C" int donof_energy_backward(const donof_problem* prob, const double* Ebar,

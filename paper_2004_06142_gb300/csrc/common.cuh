@@ -195,8 +195,12 @@ cudaError_t launch_coefficients(const Dims& d, const int32_t* pair_map, char* ws
                                 cudaStream_t s);
 cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, double* out,
                             cudaStream_t s);
+// H_pp = C_p^T h C_p and G = n o (h C_act) (one_electron_G), or G = 0 (the partial sums of
+// one shard of a sharded build carry only the two-electron part).
 cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const Layout& L,
-                               cudaStream_t s);
+                               bool one_electron_G, cudaStream_t s);
+// y += x over n doubles.
+cudaError_t launch_add(double* y, const double* x, long long n, cudaStream_t s);
 cudaError_t launch_jk_accumulate_f64(const Dims& d, const double* b, int np, int ld, char* ws,
                                      const Layout& L, cudaStream_t s);
 
@@ -217,8 +221,10 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
                                    cudaStream_t s);
 // The splits of C_act^T (for b and for h C_act), of diag(2^s) C_act (half transform) and of
 // h (for h C_act), in two launches.
+// with_half_transform = false leaves out the operand of the half transform (its exponents
+// come from the prepared B), for a build that runs no contraction over B.
 cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char* ws,
-                           const Layout& L, cudaStream_t s);
+                           const Layout& L, bool with_half_transform, cudaStream_t s);
 // hC = h C_act on the tensor cores from the planes written by launch_split_C (mixed path).
 int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream_t s);

@@ -290,7 +290,7 @@ cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, dou
 namespace {
 // one warp per orbital p: H_pp over the lanes' rows mu, and G[mu][p] = n_p (h C)[mu][p]
 __global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
-                              const double* __restrict__ n, double* Hd, double* G) {
+                              const double* __restrict__ n, double* Hd, double* G, double gscale) {
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (p >= d.A) return;
@@ -299,7 +299,7 @@ __global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double
   for (int mu = lane; mu < d.N; mu += 32) {
     const double v = hC[(size_t)mu * d.A + p];
     s += C[(size_t)mu * d.N + p] * v;
-    G[(size_t)mu * d.A + p] = np_ * v;
+    G[(size_t)mu * d.A + p] = gscale * np_ * v;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) Hd[p] = s;
@@ -307,10 +307,27 @@ __global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double
 }  // namespace
 
 cudaError_t launch_hdiag_ginit(const Dims& d, const double* C, char* ws, const Layout& L,
-                               cudaStream_t s) {
+                               bool one_electron_G, cudaStream_t s) {
   k_hdiag_ginit<<<(d.A + 7) / 8, 256, 0, s>>>(d, C, (const double*)(ws + L.hC),
                                               (const double*)(ws + L.n), (double*)(ws + L.Hd),
-                                              (double*)(ws + L.G));
+                                              (double*)(ws + L.G), one_electron_G ? 1.0 : 0.0);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// y[i] += x[i] (double), i < n: the summed partial sums of a sharded build into the
+// workspace's J, K and G.
+namespace {
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+}  // namespace
+
+cudaError_t launch_add(double* y, const double* x, long long n, cudaStream_t s) {
+  const long long nb = (n + 255) / 256;
+  k_add<<<(int)(nb < 152 * 8 ? (nb > 0 ? nb : 1) : 152 * 8), 256, 0, s>>>(y, x, n);
   count_launch(1);
   return cudaGetLastError();
 }

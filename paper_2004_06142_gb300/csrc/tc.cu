@@ -1314,7 +1314,7 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
 }
 
 cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char* ws,
-                           const Layout& L, cudaStream_t s) {
+                           const Layout& L, bool with_half_transform, cudaStream_t s) {
   // C_act^T for b (and its residual planes, the V side of h C_act), diag(2^s) C_act for the
   // symmetric half transform, and h^T = h (the U side of h C_act)
   SplitJobs jobs{};
@@ -1327,6 +1327,10 @@ cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char
   jobs.j[2] = SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
                        nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
   jobs.count = 3;
+  if (!with_half_transform) {
+    jobs.j[1] = jobs.j[2];
+    jobs.count = 2;
+  }
   return launch_split_jobs(jobs, d.Np, intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
 }
 

@@ -1,5 +1,6 @@
 """The multi-process side of bench.py on CPU (world size 2, gloo): the job's time is the
-slowest rank's, the rate counts every rank's builds, and a single process needs no group."""
+slowest rank's, the ranks share one build per step (the auxiliary index sharded over them),
+and a single process needs no group."""
 import os
 import socket
 
@@ -23,7 +24,7 @@ def _rank(rank, ws, port, out):
     try:
         ms = [12.5, 20.0][rank]
         m = bench.max_over_ranks(ms, ws, torch.device("cpu"))
-        out[rank] = (m, bench.job_rate(m, ws))
+        out[rank] = (m, bench.job_rate(m))
     finally:
         tdist.destroy_process_group()
 
@@ -35,12 +36,13 @@ def test_two_ranks_take_the_slowest_clock():
     for r in range(ws):
         m, rate = out[r]
         assert m == 20.0
-        assert rate == pytest.approx(2 * 1e3 / 20.0)
+        assert rate == pytest.approx(1e3 / 20.0)
 
 
 def test_single_process_needs_no_group():
     assert bench.max_over_ranks(7.0, 1, torch.device("cpu")) == 7.0
-    assert bench.job_rate(8.0, 1) == pytest.approx(125.0)
+    assert bench.job_rate(8.0) == pytest.approx(125.0)
+    assert bench.job_rate(8.0, 64) == pytest.approx(8000.0)
 
 
 def test_roofline_peak_follows_the_timed_region():
