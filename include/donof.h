@@ -326,12 +326,15 @@ int donof_energy_lagrangian_noalloc(const donof_problem* prob, const double* h, 
  * code) and clears it.  Allocates nothing. */
 int donof_noalloc_read_status(int32_t* status, void* stream);
 
-/* Tile autotuner (DONOF_MIXED): times each tensor-core contraction of a build with K tiles
- * of 64 and of 32 elements (a few builds on the given inputs, B already prepared) and keeps
- * the faster per contraction for this shape.  Later builds of the same shape use the choice.
- * If the environment variable DONOF_TUNE_CACHE names a file, choices are loaded from it on
- * first use and written back after tuning.  Uses (and clears) the tracing record; returns
- * DONOF_OK without work for DONOF_FP64. */
+/* Launch autotuner (DONOF_MIXED): times each tensor-core contraction of a build (a few builds
+ * on the given inputs, B already prepared) in each of its launch variants and keeps the
+ * fastest per contraction for this shape: for b = C^T X and the G contraction the K tile (64
+ * or 32 elements) on single CTAs, or 256-row tiles on CTA pairs (cta_group::2); for the half
+ * transform single CTAs or CTA pairs, with a grid of a whole number of slices' row tiles or of
+ * every SM pair.  Later builds of the same shape use the choice.  If the environment variable
+ * DONOF_TUNE_CACHE names a file, choices are loaded from it on first use and written back
+ * after tuning.  Uses (and clears) the tracing record; returns DONOF_OK without work for
+ * DONOF_FP64. */
 int donof_autotune(const donof_problem* prob, const double* h, const double* B, const double* C,
                    const double* gamma, const int32_t* pair_map, void* workspace,
                    size_t workspace_bytes, void* stream);

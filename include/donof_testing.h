@@ -41,6 +41,14 @@ int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A_lo, const 
                               const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
                               void* stream);
 
+/* Any of the three A layouts above (layout 0: K-major, 1: MN-major, 2: interleaved by 8;
+ * the same constraints), on one SM per 128-row tile (pair = 0) or with the 256-row tiles of
+ * a CTA pair (pair = 1: a cluster of two CTAs, cta_group::2 MMAs issued by the even CTA, each
+ * CTA staging its 128 rows of A and half of the N rows of B). */
+int donof_testing_tc_gemm_ex(const uint16_t* A_hi, const uint16_t* A_lo, const uint16_t* B_hi,
+                             const uint16_t* B_lo, float* D, int32_t M, int32_t N, int32_t K,
+                             int32_t layout, int32_t pair, void* stream);
+
 /* The bounded device wait of the tensor-core kernel, run out on purpose: one CTA whose two
  * roles wait on mbarriers that nothing completes, the first with a limit of limit_a_ns
  * (at most 2 s), the second with limit_b_ns (at most 20 s).  The first wait's time-out

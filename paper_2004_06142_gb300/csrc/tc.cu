@@ -164,18 +164,106 @@ __device__ __forceinline__ uint64_t sdesc_plain(uint32_t saddr, uint32_t lbo, ui
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// One MMA, D (TMEM) (+)= A B: cta_group::1 on this SM, or cta_group::2 over the CTA pair of a
+// cluster (M = 256: A rows and accumulator rows split between the two SMs, B columns too),
+// issued by the even CTA.
+template <int PAIR>
 __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if (PAIR)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
+// Arrive on `bar` once the MMAs issued so far are complete: in this CTA, or (PAIR) on the
+// barrier at the same offset in both CTAs of the pair.
+template <int PAIR>
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
+  if (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
+        : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+// The same, on the issuing CTA's own barrier only.
+template <int PAIR>
+__device__ __forceinline__ void mma_commit_local(uint32_t bar) {
+  if (PAIR)
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+// TMEM allocation by one warp (PAIR: one warp in each CTA of the pair, the same columns in
+// both SMs), and its release.
+template <int PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, int cols) {
+  if (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+}
+template <int PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, int cols) {
+  if (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols)
+                 : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols)
+                 : "memory");
+}
+// Cluster of a CTA pair: rank, cluster index and count, a barrier over all its threads, the
+// address of a shared variable in another CTA of the cluster, and an arrival there.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t ncluster_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
                : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -237,7 +325,7 @@ struct TcArgs {
   int a_z_kb;      // A tile z coordinate = kb (else 0)
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
-  int nbuf;        // TMEM accumulator sets (1 or 2)
+  int nbuf;        // TMEM accumulator sets: 1, 2, or 3 (three regions in rotation, below)
   int buf_stride;  // TMEM columns per accumulator set
   int tmem_cols;
   // per-row / per-column exponents (kIntFrac): value = 2^(eA[row] + eB[col]) * acc, with
@@ -245,13 +333,9 @@ struct TcArgs {
   const int* eA; long long eA_zstride, eA_sstride;
   const int* eB; long long eB_zstride, eB_sstride;
   const int* glob_exp;  // extra power of two applied to every output (mode 2)
-  // A operand from pre-tiled planes (BK = 64 only): the tile of rows [r0, r0 + 128) and
-  // k block kb is the contiguous run of rows x 128 bytes at a_tiled + kb * a_kb_stride +
-  // r0 * 64, already in the 128-byte swizzled order; a partial last row block is copied
-  // as far as it goes (its missing rows only reach accumulator rows that are not stored)
+  // symmetric half transform: the lower-triangle tile storage of the split B (see sym below)
   const __half* a_tiled_h;
   const __half* a_tiled_f;
-  long long a_kb_stride;
   int a_mn;  // 1: A operand MN-major (BK = 64): its map is [K][M], two 64-wide M boxes
   // 1: A operand interleaved by 8 along K, [z][K/8][rows][8], loaded without swizzle as
   // core matrices (4-D map of 8-row groups, coordinates {0, row/8, k/8, z})
@@ -263,7 +347,7 @@ struct TcArgs {
   // for the smaller); output row mt * 128 + r is AO index mu of slice z
   int sym;
   SymTiles st;
-  int grid;  // CTAs to launch (0: one per SM, at most one per unit)
+  int grid;  // CTAs (CTA pairs) to launch (0: one per SM (pair of SMs), at most one per unit)
   // mode 1 outputs, X[row][c] with row = P * Nmu + mu (mu < Nrow valid): integer +
   // fraction X for the G contraction, interleaved by 8 along c as [P][c/8][mu < Np][8]
   // (exponent eX3[spOf[P]][mu], common to the slices of one G split) and X^T[P][c][mu]
@@ -303,7 +387,7 @@ __device__ __forceinline__ float pow2f(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-template <int BK, int NUM>
+template <int BK, int NUM, int PAIR>
 __global__ void __launch_bounds__(256, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -313,76 +397,103 @@ __global__ void __launch_bounds__(256, 1)
   uint8_t* smem =
       (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = args.stages;
+  // PAIR: the two CTAs of a cluster compute one M = 256 tile with cta_group::2 MMAs issued by
+  // the even CTA: each CTA stages its own 128 rows of A and half of the B rows (the output
+  // columns), and holds its 128 rows of the accumulator in its own TMEM
+  const int nb_rows = PAIR ? args.Nn / 2 : args.Nn;  // B rows staged by this CTA
   const uint32_t a_bytes = BM * BK * 2;
-  const uint32_t b_bytes = (uint32_t)args.Nn * BK * 2;
+  const uint32_t b_bytes = (uint32_t)nb_rows * BK * 2;
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   uint64_t* bars = (uint64_t*)(smem + (size_t)S * stage_bytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address slot
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 5);
+  // barriers: full[S], empty[S], tfull[2], tempty[2], drain, trel[2]; then the TMEM address
+  const int kFull = 0, kEmpty = S, kTfull = 2 * S, kTempty = 2 * S + 2, kDrain = 2 * S + 4,
+            kTrel = 2 * S + 5;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 7);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int* status = args.status;
   int* abort_flag = args.abort_flag;
   const int nbuf = args.nbuf;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int cl = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;   // this CTA's work stream
+  const int ncl = PAIR ? (int)ncluster_x() : (int)gridDim.x;
+  const uint32_t rel_count = PAIR ? 256u : 128u;  // epilogue threads that release TMEM
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
-      mbar_init(smem_u32(&bars[i]), 1);
-      mbar_init(smem_u32(&bars[S + i]), 1);
+      // PAIR: the even CTA's full barrier also waits for the odd CTA's relayed arrival
+      mbar_init(bar(kFull + i), (PAIR && rank == 0) ? 2 : 1);
+      mbar_init(bar(kEmpty + i), 1);
     }
-    mbar_init(smem_u32(&bars[2 * S + 0]), 1);
-    mbar_init(smem_u32(&bars[2 * S + 1]), 1);
-    mbar_init(smem_u32(&bars[2 * S + 2]), 128);
-    mbar_init(smem_u32(&bars[2 * S + 3]), 128);
-    mbar_init(smem_u32(&bars[2 * S + 4]), 1);
+    mbar_init(bar(kTfull + 0), 1);
+    mbar_init(bar(kTfull + 1), 1);
+    mbar_init(bar(kTempty + 0), rel_count);
+    mbar_init(bar(kTempty + 1), rel_count);
+    mbar_init(bar(kDrain), 1);
+    mbar_init(bar(kTrel + 0), rel_count);
+    mbar_init(bar(kTrel + 1), rel_count);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(args.tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 2) tmem_alloc<PAIR>(smem_u32(tmem_slot), args.tmem_cols);
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync_all();  // the peer's barriers are initialised before any remote use
   tc_fence_after();
   const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
 
-  const int units = args.z_count * args.m_tiles * args.splits;
+  // work units: (z, row tile, split); PAIR: a unit is the M = 256 tile of the cluster, rows
+  // of slice pair (2 zp, 2 zp + 1) in the symmetric mode, row tiles (2 mu, 2 mu + 1) otherwise
+  const bool sym = BK == 64 && args.sym;
+  const int z_units = (PAIR && sym) ? (args.z_count + 1) / 2 : args.z_count;
+  const int m_units = (PAIR && !sym) ? (args.m_tiles + 1) / 2 : args.m_tiles;
+  const int units = z_units * m_units * args.splits;
   // consecutive units share the split (and so the B tiles of one K range, which then come
   // from L2 for all M tiles of that split)
   auto decode = [&](int u, int& z, int& mt, int& sp) {
-    z = u / (args.m_tiles * args.splits);
-    const int r = u % (args.m_tiles * args.splits);
-    sp = r / args.m_tiles;
-    mt = r % args.m_tiles;
+    const int zu = u / (m_units * args.splits);
+    const int r = u % (m_units * args.splits);
+    sp = r / m_units;
+    const int mu = r % m_units;
+    z = (PAIR && sym) ? 2 * zu + (int)rank : zu;
+    mt = (PAIR && !sym) ? 2 * mu + (int)rank : mu;
+  };
+  const int T = args.st.T;
+  auto unit_iters = [&](int sp) {
+    if (sym) return 2 * (T - 1) + args.st.Rlast / 64;
+    const int kb0 = (int)((long long)args.nkb * sp / args.splits);
+    const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
+    return (kb1 - kb0) * args.kt_per_kb;
   };
 
   if (warp == 0 && lane == 0) {
-    // ------------------------------------------------ TMA producer
+    // ------------------------------------------------ TMA producer (both CTAs of a pair)
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
     long long issued = 0;  // stages filled so far
-    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+    const int b_row0 = (int)rank * nb_rows;
+    for (int u = cl; u < units && ok; u += ncl) {
       int z, mt, sp;
       decode(u, z, mt, sp);
-      if (BK == 64 && args.sym) {
+      if (sym) {
         const SymTiles st = args.st;
+        const bool a_valid = z < args.z_count;  // PAIR: the odd slice of an odd count is absent
         const int i = mt, Ri = sym_R(st, i);
         const size_t zoff = (size_t)z * st.perP;
         for (int r = 0; r < st.T && ok; ++r) {
           const int j = rr_partner(i, r, st.T);
           const int nch = j < st.T - 1 ? 2 : st.Rlast / 64;
           for (int c = 0; c < nch; ++c) {
-            if (!mbar_wait(smem_u32(&bars[S + stage]), phase ^ 1u, status, abort_flag)) {
+            if (!mbar_wait(bar(kEmpty + stage), phase ^ 1u, status, abort_flag)) {
               ok = false;
               break;
             }
-            const uint32_t fb = smem_u32(&bars[stage]);
+            const uint32_t fb = bar(kFull + stage);
             const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
-            if (j <= i) {  // stored tile (i, j), chunk c: Ri rows of 128 bytes, K-major
+            if (!a_valid) {
+              mbar_expect_tx(fb, 2 * b_bytes);
+            } else if (j <= i) {  // stored tile (i, j), chunk c: Ri rows of 128 bytes, K-major
               const uint32_t ab = (uint32_t)Ri * 128u;
               mbar_expect_tx(fb, 2 * ab + 2 * b_bytes);
               const size_t off = zoff + sym_tile_off(st, i, j) + (size_t)c * Ri * 64;
@@ -399,8 +510,8 @@ __global__ void __launch_bounds__(256, 1)
                 bulk_load_once(base + a_bytes + m * 8192, args.a_tiled_f + off, 8192, fb);
               }
             }
-            tma_load_3d(base + 2 * a_bytes, &mBh, fb, 128 * j + 64 * c, 0, 0);
-            tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, 128 * j + 64 * c, 0, 0);
+            tma_load_3d(base + 2 * a_bytes, &mBh, fb, 128 * j + 64 * c, b_row0, 0);
+            tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, 128 * j + 64 * c, b_row0, 0);
             ++issued;
             if (++stage == S) { stage = 0; phase ^= 1u; }
           }
@@ -413,35 +524,24 @@ __global__ void __launch_bounds__(256, 1)
         const int az = args.a_z_kb ? kb : 0;
         const int bz = args.b_z_mode == 1 ? z : (args.b_z_mode == 2 ? kb : 0);
         for (int kt = 0; kt < args.kt_per_kb; ++kt) {
-          const uint32_t eb = smem_u32(&bars[S + stage]);
-          if (!mbar_wait(eb, phase ^ 1u, status, abort_flag)) { ok = false; break; }
-          const uint32_t fb = smem_u32(&bars[stage]);
+          if (!mbar_wait(bar(kEmpty + stage), phase ^ 1u, status, abort_flag)) { ok = false; break; }
+          const uint32_t fb = bar(kFull + stage);
           const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
-          if (BK == 64 && args.a_tiled_h) {
-            const int r0 = mt * BM;
-            const int rv = args.M - r0 < BM ? args.M - r0 : BM;
-            const uint32_t abytes = (uint32_t)rv * 128u;
-            mbar_expect_tx(fb, 2 * abytes + 2 * b_bytes);
-            const size_t off = (size_t)kt * args.a_kb_stride + (size_t)r0 * 64;
-            bulk_load_once(base, args.a_tiled_h + off, abytes, fb);
-            bulk_load_once(base + a_bytes, args.a_tiled_f + off, abytes, fb);
-          } else if (args.a_il8) {
-            mbar_expect_tx(fb, stage_bytes);
+          mbar_expect_tx(fb, stage_bytes);
+          if (args.a_il8) {
             tma_load_4d(base, &mAh, fb, 0, mt * BM / 8, kt * BK / 8, az);
             tma_load_4d(base + a_bytes, &mAl, fb, 0, mt * BM / 8, kt * BK / 8, az);
           } else if (BK == 64 && args.a_mn) {
-            mbar_expect_tx(fb, stage_bytes);
             tma_load_3d(base, &mAh, fb, mt * BM, kt * BK, az);
             tma_load_3d(base + a_bytes / 2, &mAh, fb, mt * BM + 64, kt * BK, az);
             tma_load_3d(base + a_bytes, &mAl, fb, mt * BM, kt * BK, az);
             tma_load_3d(base + a_bytes + a_bytes / 2, &mAl, fb, mt * BM + 64, kt * BK, az);
           } else {
-            mbar_expect_tx(fb, stage_bytes);
             tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
             tma_load_3d(base + a_bytes, &mAl, fb, kt * BK, mt * BM, az);
           }
-          tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, 0, bz);
-          tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, 0, bz);
+          tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, b_row0, bz);
+          tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, b_row0, bz);
           ++issued;
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
@@ -451,13 +551,29 @@ __global__ void __launch_bounds__(256, 1)
     // `stage` were filled in this lap of the ring, the others in the previous one (if any)
     if (*(volatile int*)abort_flag != 0) {
       for (int s = 0; s < S; ++s) {
-        if (s < stage) mbar_wait_quiet(smem_u32(&bars[s]), phase, kDrainLimitNs);
-        else if (issued >= S) mbar_wait_quiet(smem_u32(&bars[s]), phase ^ 1u, kDrainLimitNs);
+        if (s < stage) mbar_wait_quiet(bar(kFull + s), phase, kDrainLimitNs);
+        else if (issued >= S) mbar_wait_quiet(bar(kFull + s), phase ^ 1u, kDrainLimitNs);
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------ MMA issuer
-    const uint32_t idesc = idesc_f16(BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
+  } else if (PAIR && rank == 1 && warp == 3 && lane == 0) {
+    // ------------------------------------------------ relay (odd CTA of a pair): each stage
+    // of this CTA that has landed is announced on the even CTA's full barrier
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int u = cl; u < units && ok; u += ncl) {
+      int z, mt, sp;
+      decode(u, z, mt, sp);
+      const int iters = unit_iters(sp);
+      for (int it = 0; it < iters; ++it) {
+        if (!mbar_wait(bar(kFull + stage), phase, status, abort_flag)) { ok = false; break; }
+        mbar_arrive_remote(mapa_shared(bar(kFull + stage), 0));
+        if (++stage == S) { stage = 0; phase ^= 1u; }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------ MMA issuer (even CTA of a pair)
+    const uint32_t idesc = idesc_f16(PAIR ? 2 * BM : BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
     // MN-major A (BK = 64): the two 64-wide M chunks 8 KB apart (leading byte offset),
     // 8-row K groups 1 KB apart (stride byte offset)
     const uint32_t mn_lbo = 8192u, mn_sbo = 1024u;
@@ -465,29 +581,41 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t phase = 0;
     bool ok = true;
     int local = 0;
-    for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++local) {
+    for (int u = cl; u < units && ok; u += ncl, ++local) {
       int z, mt, sp;
       decode(u, z, mt, sp);
-      const int acc = local % nbuf;
-      const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
-      if (!mbar_wait(smem_u32(&bars[2 * S + 2 + acc]), acc_phase ^ 1u, status, abort_flag)) break;
+      // the accumulator pair (d0: h*h, d1: the cross products) of this unit
+      uint32_t d0, d1;
+      int tf;
+      if (nbuf == 3) {
+        // three regions of Nn columns, X = [0, Nn), Y = [Nn, 2 Nn), Z = [2 Nn, 3 Nn): d1 is
+        // always Y, d0 alternates X, Z; the epilogue releases Y first, so the next unit
+        // waits for half of the drain only
+        tf = 0;
+        if (!mbar_wait(bar(kTempty + 0), (uint32_t)(local & 1) ^ 1u, status, abort_flag)) break;
+        if (!mbar_wait(bar(kTrel + (local & 1)), (uint32_t)((local / 2) & 1) ^ 1u, status,
+                       abort_flag))
+          break;
+        d1 = tmem_base + (uint32_t)args.Nn;
+        d0 = tmem_base + (uint32_t)((local & 1) ? 2 * args.Nn : 0);
+      } else {
+        const int acc = local % nbuf;
+        const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
+        if (!mbar_wait(bar(kTempty + acc), acc_phase ^ 1u, status, abort_flag)) break;
+        tf = acc;
+        d0 = tmem_base + (uint32_t)(acc * args.buf_stride);
+        d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
+      }
       tc_fence_after();
-      const uint32_t d0 = tmem_base + (uint32_t)(acc * args.buf_stride);
-      const uint32_t d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
-      const int kb0 = (int)((long long)args.nkb * sp / args.splits);
-      const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
       // symmetric mode: the K steps in the producer's order, K-major or transposed
-      const bool sym = BK == 64 && args.sym;
-      const int T = args.st.T;
-      int iters = (kb1 - kb0) * args.kt_per_kb;
+      const int iters = unit_iters(sp);
       int rr = 0, cc = 0, jj = 0, nch = 0;
       if (sym) {
-        iters = 2 * (T - 1) + args.st.Rlast / 64;
         jj = rr_partner(mt, 0, T);
         nch = jj < T - 1 ? 2 : args.st.Rlast / 64;
       }
       for (int it = 0; it < iters; ++it) {
-        if (!mbar_wait(smem_u32(&bars[stage]), phase, status, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(bar(kFull + stage), phase, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
         const bool tr = args.a_mn || (sym && jj > mt);
@@ -509,17 +637,17 @@ __global__ void __launch_bounds__(256, 1)
           const uint64_t bl = sdesc(base + 2 * a_bytes + b_bytes + k * 32, SWZ);
           const uint32_t first = (it > 0 || k > 0) ? 1u : 0u;
           if (NUM == kSplit3) {
-            mma_f16(d0, ah, bh, id, first);
-            mma_f16(d0, ah, bl, id, 1u);
-            mma_f16(d0, al, bh, id, 1u);
+            mma_f16<PAIR>(d0, ah, bh, id, first);
+            mma_f16<PAIR>(d0, ah, bl, id, 1u);
+            mma_f16<PAIR>(d0, al, bh, id, 1u);
           } else {
-            mma_f16(d0, ah, bh, id, first);  // integer x integer: exact
-            mma_f16(d1, ah, bl, id, first);
-            mma_f16(d1, al, bh, id, 1u);
-            mma_f16(d1, al, bl, id, 1u);
+            mma_f16<PAIR>(d0, ah, bh, id, first);  // integer x integer: exact
+            mma_f16<PAIR>(d1, ah, bl, id, first);
+            mma_f16<PAIR>(d1, al, bh, id, 1u);
+            mma_f16<PAIR>(d1, al, bl, id, 1u);
           }
         }
-        mma_commit(smem_u32(&bars[S + stage]));
+        mma_commit<PAIR>(bar(kEmpty + stage));  // frees the stage in both CTAs of a pair
         if (++stage == S) { stage = 0; phase ^= 1u; }
         if (sym && ++cc == nch) {
           cc = 0;
@@ -530,24 +658,41 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       if (!ok) break;
-      mma_commit(smem_u32(&bars[2 * S + acc]));
+      mma_commit<PAIR>(bar(kTfull + tf));
     }
     // after an abort, the MMAs already issued complete before the TMEM is freed
     if (*(volatile int*)abort_flag != 0) {
-      mma_commit(smem_u32(&bars[2 * S + 4]));
-      mbar_wait_quiet(smem_u32(&bars[2 * S + 4]), 0u, kDrainLimitNs);
+      mma_commit_local<PAIR>(bar(kDrain));
+      mbar_wait_quiet(bar(kDrain), 0u, kDrainLimitNs);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue: TMEM -> registers -> global
     const int ew = warp - 4;
     const int glob = args.glob_exp ? *args.glob_exp : 0;
+    // a release of TMEM: on the even CTA's barrier (remotely from the odd CTA of a pair)
+    auto release = [&](int i) {
+      tc_fence_before();
+      if (PAIR && rank == 1) mbar_arrive_remote(mapa_shared(bar(i), 0));
+      else mbar_arrive(bar(i));
+    };
     int local = 0;
-    for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
+    for (int u = cl; u < units; u += ncl, ++local) {
       int z, mt, sp;
       decode(u, z, mt, sp);
-      const int acc = local % nbuf;
-      const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
-      bool ok = mbar_wait(smem_u32(&bars[2 * S + acc]), acc_phase, status, abort_flag);
+      int tf;
+      uint32_t tf_phase, c0off, c1off;
+      if (nbuf == 3) {
+        tf = 0;
+        tf_phase = (uint32_t)(local & 1);
+        c0off = (uint32_t)((local & 1) ? 2 * args.Nn : 0);
+        c1off = (uint32_t)args.Nn;
+      } else {
+        tf = local % nbuf;
+        tf_phase = (uint32_t)((local / nbuf) & 1);
+        c0off = (uint32_t)(tf * args.buf_stride);
+        c1off = c0off + (uint32_t)args.Nn;
+      }
+      bool ok = mbar_wait(bar(kTfull + tf), tf_phase, status, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
@@ -555,20 +700,20 @@ __global__ void __launch_bounds__(256, 1)
       // mode 1: slice and AO index of this row, the exponent of its X row in the G
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
-      bool valid = row < args.M;
+      bool valid = row < args.M && z < args.z_count;
       if (args.sym) {
         rP = z;
         rmu = row;
-        valid = row < args.Nrow;
+        valid = row < args.Nrow && z < args.z_count;
       } else if (args.mode == 1) {
         rP = row / args.Nmu;
         rmu = row % args.Nmu;
         valid = valid && rmu < args.Nrow;
       }
       const int erow_i = (args.mode == 1 || args.sym) ? rP * args.Nrow + rmu : row;
-      const uint32_t t0 =
-          tmem_base + (uint32_t)(acc * args.buf_stride) + ((uint32_t)(ew * 32) << 16);
-      const uint32_t t1 = t0 + (uint32_t)args.Nn;
+      const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+      const uint32_t t0 = tmem_base + c0off + lane_off;
+      const uint32_t t1 = tmem_base + c1off + lane_off;
       const int erow = (NUM == kIntFrac && valid)
                            ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + erow_i]
                            : 0;
@@ -646,25 +791,41 @@ __global__ void __launch_bounds__(256, 1)
       };
 
       if (args.Nn <= kMaxRegCols) {
-        // drain the accumulators into registers (32 columns per load, one wait per pair of
-        // loads), hand TMEM back, then write
+        // drain the accumulators into registers (32 columns per load), hand TMEM back, then
+        // write.  nbuf 3: the cross products (region Y) first, all in flight together, then Y
+        // is released and the integer products (X or Z) are added in chunks; otherwise both
+        // accumulators chunk by chunk, one wait per pair of loads
         float keep[kMaxRegCols];
+        if (nbuf == 3) {
+#pragma unroll
+          for (int cc = 0; cc < kMaxRegCols / 32; ++cc)
+            if (cc * 32 < args.Nn) tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), keep + cc * 32);
+          tmem_wait_ld();
+          release(kTempty + 0);
+        }
 #pragma unroll
         for (int cc = 0; cc < kMaxRegCols / 32; ++cc) {
           if (cc * 32 < args.Nn) {
-            tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), keep + cc * 32);
-            if (NUM == kIntFrac) {
+            if (nbuf == 3) {
               float tmp[32];
-              tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), tmp);
+              tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), tmp);
               tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < 32; ++j) keep[cc * 32 + j] += tmp[j];
+              for (int j = 0; j < 32; ++j) keep[cc * 32 + j] = tmp[j] + keep[cc * 32 + j];
+            } else {
+              tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), keep + cc * 32);
+              if (NUM == kIntFrac) {
+                float tmp[32];
+                tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), tmp);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) keep[cc * 32 + j] += tmp[j];
+              }
             }
           }
         }
         tmem_wait_ld();
-        tc_fence_before();
-        mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
+        release(nbuf == 3 ? kTrel + (local & 1) : kTempty + tf);
 #pragma unroll
         for (int cc = 0; cc < kMaxRegCols / 16; ++cc) {
           if (cc * 16 < args.Nn) {
@@ -680,31 +841,41 @@ __global__ void __launch_bounds__(256, 1)
           load(c0, a);
           emit(c0, a);
         }
-        tc_fence_before();
-        mbar_arrive(smem_u32(&bars[2 * S + 2 + acc]));
+        release(kTempty + tf);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync_all();  // no CTA frees its TMEM while the pair's MMAs may write it
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(args.tmem_cols)
-                 : "memory");
+    tmem_dealloc<PAIR>(tmem_base, args.tmem_cols);
   }
 }
 
 // ------------------------------------------------------------------ host: tile tuning
-// K-tile width (BK, 32 or 64 elements) per contraction kind and shape, chosen by
-// donof_autotune from timed builds; optional persistence in the file named by the
-// DONOF_TUNE_CACHE environment variable (lines "kind N Ap np bk").
+// Launch variant per contraction kind and shape, chosen by donof_autotune from timed builds;
+// optional persistence in the file named by the DONOF_TUNE_CACHE environment variable (lines
+// "kind N Ap np code").  A code is bk + 1000 pair + 2000 full: the K-tile width (BK, 32 or
+// 64 elements), whether a CTA pair computes each 256-row tile with cta_group::2 MMAs, and
+// (half transform) whether the grid takes every SM pair rather than a whole number of
+// slices' row tiles at once.
 struct TuneKey {
   int kind, N, Ap, np;
   bool operator<(const TuneKey& o) const {
     return std::tie(kind, N, Ap, np) < std::tie(o.kind, o.N, o.Ap, o.np);
   }
 };
+struct TuneCode {
+  int bk, pair, full;
+};
+TuneCode decode_tune(int code) { return TuneCode{code % 1000, (code / 1000) & 1, code >= 2000}; }
+bool valid_tune(int code) {
+  const TuneCode t = decode_tune(code);
+  return (t.bk == 32 || t.bk == 64) && code >= 0 && code < 4000 && !(t.pair && t.bk != 64) &&
+         !(t.full && !t.pair);
+}
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
@@ -719,7 +890,7 @@ void tune_load_locked() {
   TuneKey k;
   int bk;
   while (fscanf(f, "%d %d %d %d %d", &k.kind, &k.N, &k.Ap, &k.np, &bk) == 5)
-    if (bk == 32 || bk == 64) g_tune[k] = bk;
+    if (valid_tune(bk)) g_tune[k] = bk;
   fclose(f);
 }
 
@@ -733,13 +904,15 @@ void tune_save_locked() {
   fclose(f);
 }
 
-// kinds: 1 = half transform, 2 = b, 3 = G
-int tuned_bk(int kind, int N, int Ap, int np) {
+// kinds: 1 = half transform, 2 = b, 3 = G.  Defaults: the half transform on CTA pairs (two
+// slices' row tiles per cluster, a whole number of slices at once), b with BK 64 and G with
+// BK 32 on single CTAs.
+TuneCode tuned_variant(int kind, int N, int Ap, int np) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_load_locked();
   auto it = g_tune.find(TuneKey{kind, N, Ap, np});
-  if (it != g_tune.end()) return it->second;
-  return kind == 3 ? 32 : 64;
+  if (it != g_tune.end()) return decode_tune(it->second);
+  return decode_tune(kind == 1 ? 1064 : (kind == 3 ? 32 : 64));
 }
 
 // ------------------------------------------------------------------ host: tensor maps
@@ -810,31 +983,62 @@ int num_sms() {
   return n;
 }
 
-template <int BK, int NUM>
+template <int BK, int NUM, int PAIR>
 cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
-  const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)a.Nn * BK * 2;
+  const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)(PAIR ? a.Nn / 2 : a.Nn) * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   const size_t budget = 232448 - 1024 - 512;  // the 227 KB opt-in limit, less alignment and barriers
   int stages = (int)(budget / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
   a.stages = stages;
-  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart), two sets if they fit
+  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart); two sets if they fit,
+  // else (kIntFrac, up to kMaxRegCols columns) three regions in rotation, else one set
   const int per_set = (NUM == kIntFrac ? 2 : 1) * a.Nn;
   a.tmem_cols = 512;
-  a.nbuf = (2 * per_set <= 512) ? 2 : 1;
-  a.buf_stride = (a.nbuf == 2) ? 256 : 0;
-  if (a.nbuf == 2 && per_set > 256) return cudaErrorInvalidValue;
-  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 5) * 8 + 16;
+  if (2 * per_set <= 512) {
+    a.nbuf = 2;
+    a.buf_stride = 256;
+    if (per_set > 256) return cudaErrorInvalidValue;
+  } else if (NUM == kIntFrac && 3 * a.Nn <= 512 && a.Nn <= kMaxRegCols) {
+    a.nbuf = 3;
+    a.buf_stride = 0;
+  } else {
+    a.nbuf = 1;
+    a.buf_stride = 0;
+  }
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 7) * 8 + 16;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM>,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int units = a.z_count * a.m_tiles * a.splits;
-  int grid = a.grid > 0 ? a.grid : num_sms();
-  if (grid > units) grid = units;
-  k_tc_gemm<BK, NUM><<<grid, 256, smem, s>>>(ah, al, bh, bl, a);
+  const bool sym = BK == 64 && a.sym;
+  const int z_units = (PAIR && sym) ? (a.z_count + 1) / 2 : a.z_count;
+  const int m_units = (PAIR && !sym) ? (a.m_tiles + 1) / 2 : a.m_tiles;
+  const int units = z_units * m_units * a.splits;
+  int work = a.grid > 0 ? a.grid : (PAIR ? num_sms() / 2 : num_sms());  // CTAs or CTA pairs
+  if (work > units) work = units;
+  if (work < 1) work = 1;
+  if (PAIR) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * work);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BK, NUM, PAIR>, ah, al, bh, bl, a);
+    count_launch(1);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  k_tc_gemm<BK, NUM, PAIR><<<work, 256, smem, s>>>(ah, al, bh, bl, a);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -842,8 +1046,17 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
 template <int NUM>
 cudaError_t launch_tc_bk(int bk, const CUtensorMap& ah, const CUtensorMap& al,
                          const CUtensorMap& bh, const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
-  return bk == 32 ? launch_tc<32, NUM>(ah, al, bh, bl, a, s)
-                  : launch_tc<64, NUM>(ah, al, bh, bl, a, s);
+  return bk == 32 ? launch_tc<32, NUM, 0>(ah, al, bh, bl, a, s)
+                  : launch_tc<64, NUM, 0>(ah, al, bh, bl, a, s);
+}
+
+// The launch of a tuned variant (the B maps must have boxes of Nn / 2 rows for a pair).
+template <int NUM>
+cudaError_t launch_tc_variant(const TuneCode& t, const CUtensorMap& ah, const CUtensorMap& al,
+                              const CUtensorMap& bh, const CUtensorMap& bl, TcArgs a,
+                              cudaStream_t s) {
+  if (t.pair) return launch_tc<64, NUM, 1>(ah, al, bh, bl, a, s);
+  return launch_tc_bk<NUM>(t.bk, ah, al, bh, bl, a, s);
 }
 
 // ------------------------------------------------------------------ split / scale kernels
@@ -1396,7 +1609,7 @@ int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int
   a.out = (float*)(ws + L.hpart); a.out_ld = Ap; a.out_zstride = (long long)M * Ap;
   a.glob_exp = &hdr->zero_exp;
   a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-  if (launch_tc<64, kIntFrac>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  if (launch_tc<64, kIntFrac, 0>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   const long long nb = ((long long)M * ncols + 255) / 256;
   k_sum_blocks<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
       (const float*)(ws + L.hpart), M, ncols, Ap, out, ld);
@@ -1454,9 +1667,11 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     const SymTiles st = sym_tiles(N);
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
-    const int bk = 64;
-    if (!make_map(&bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
-        !make_map(&bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
+    const int bk = 64;  // the stored tiles are laid out for it
+    const TuneCode tv = tuned_variant(1, N, Ap, np);
+    const uint32_t brows = tv.pair ? Ap / 2 : Ap;  // B rows staged per CTA
+    if (!make_map(&bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
+        !make_map(&bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
       return DONOF_ERR_CUDA;
     ah = bh;  // unused: the A tiles come from the bulk copies
     al = bl;
@@ -1465,7 +1680,10 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.m_tiles = st.T; a.z_count = np; a.splits = 1;
     a.kt_per_kb = 1; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
     a.sym = 1; a.st = st;
-    a.grid = num_sms() >= st.T ? num_sms() / st.T * st.T : num_sms();  // whole slices at once
+    // whole slices at once (the partner row tiles of a slice read their shared stored tile
+    // in the same round, so the second read can hit L2); a pair takes two slices' row tiles
+    const int work = tv.pair ? num_sms() / 2 : num_sms();
+    a.grid = (tv.full || work < st.T) ? work : work / st.T * st.T;
     a.a_tiled_h = Bh; a.a_tiled_f = Bl;
     a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
     a.eB = (const int*)(ws + L.eCs); a.eB_zstride = 0;
@@ -1475,7 +1693,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
   // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
@@ -1484,11 +1702,13 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     // one GEMM over all slices: rows (P, q) of X^T flattened into M, C_act^T rows as N;
     // b[(P, q)][p] = b^P[q][p] is b^P (symmetric) in the [P][Ap][Ap] layout
     const uint64_t rows = (uint64_t)np * Ap;
-    const int bk = tuned_bk(2, N, Ap, np);
+    const TuneCode tv = tuned_variant(2, N, Ap, np);
+    const int bk = tv.bk;
+    const uint32_t brows = tv.pair ? Ap / 2 : Ap;
     if (!make_map(&ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
         !make_map(&al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
-        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap) ||
-        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, Ap))
+        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
+        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
       return DONOF_ERR_CUDA;
     TcArgs a{};
     a.mode = 2; a.M = (int)rows; a.Nn = Ap;
@@ -1500,7 +1720,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
     a.diag = (float*)(ws + L.D); a.diag_A = d.A;  // d^P for the mid section
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
@@ -1511,11 +1731,13 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   //     common to the slices of a split)
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
-    const int bk = tuned_bk(3, N, Ap, np);
+    const TuneCode tv = tuned_variant(3, N, Ap, np);
+    const int bk = tv.bk;
+    const uint32_t brows = tv.pair ? Ap / 2 : Ap;
     if (!make_map_il8(&ah, ws + L.Xhi, Ap, Np, np, bk, BM) ||
         !make_map_il8(&al, ws + L.Xlo, Ap, Np, np, bk, BM) ||
-        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap) ||
-        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, Ap))
+        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows) ||
+        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows))
       return DONOF_ERR_CUDA;
     TcArgs a{};
     a.mode = 2; a.M = N; a.Nn = Ap;
@@ -1528,7 +1750,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
     a.glob_exp = &hdr->zero_exp;
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_bk<kIntFrac>(bk, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
     if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
@@ -1540,27 +1762,31 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
 }  // namespace donof
 
 // ---------------------------------------------------------------------------
-// Autotuner: time each tensor-core contraction of a build with BK = 64 and BK = 32 (CUDA
-// events through the tracing phases) and keep the faster per contraction and shape.
+// Autotuner: time each tensor-core contraction of a build in each of its launch variants (K
+// tile, single CTAs or CTA pairs, grid; CUDA events through the tracing phases) and keep the
+// fastest per contraction and shape.
 namespace donof {
 int autotune_build(const donof_problem* prob, const double* h, const double* B, const double* C,
                    const double* gamma, const int32_t* pair_map, void* ws, size_t bytes,
                    cudaStream_t s) {
   const Dims d = make_dims(prob);
   const int np = d.pb < d.Q ? d.pb : d.Q;
-  // the half transform always runs with BK = 64 (its pre-tiled operand is laid out for it)
+  // candidates per contraction (codes of decode_tune); the half transform always runs with
+  // BK = 64 (its pre-tiled operand is laid out for it): single CTAs or CTA pairs, the grid a
+  // whole number of slices' row tiles or every SM pair
   const int phases[3] = {DONOF_PHASE_HALF_TRANSFORM, DONOF_PHASE_MO_3INDEX, DONOF_PHASE_G_BUILD};
-  const int cand[2] = {64, 32};
+  constexpr int kCand = 3;
+  const int cand[3][kCand] = {{1064, 3064, 64}, {64, 32, 1064}, {32, 64, 1064}};
   double best_ms[3] = {1e300, 1e300, 1e300};
-  int best_bk[3] = {64, 64, 32};
+  int best_code[3] = {1064, 64, 32};
   double* E = nullptr;
   if (cudaMallocAsync((void**)&E, sizeof(double), s) != cudaSuccess) return DONOF_ERR_CUDA;
   int rc = DONOF_OK;
-  for (int c = 0; c < 2 && rc == DONOF_OK; ++c) {
+  for (int c = 0; c < kCand && rc == DONOF_OK; ++c) {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       tune_load_locked();
-      for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = cand[c];
+      for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = cand[k][c];
     }
     rc = donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, bytes, E, nullptr, nullptr,
                                  s);  // warm-up
@@ -1569,20 +1795,20 @@ int autotune_build(const donof_problem* prob, const double* h, const double* B, 
     for (int r = 0; r < 2 && rc == DONOF_OK; ++r)
       rc = donof_energy_lagrangian(prob, h, B, C, gamma, pair_map, ws, bytes, E, nullptr, nullptr,
                                    s);
-    for (int k = 1; k < 3 && rc == DONOF_OK; ++k) {
+    for (int k = 0; k < 3 && rc == DONOF_OK; ++k) {
       double ms = 0.0;
       int n = 0;
       if (donof_profile_read(phases[k], &ms, &n) != DONOF_OK || n == 0) continue;
       if (ms / n < best_ms[k]) {
         best_ms[k] = ms / n;
-        best_bk[k] = cand[c];
+        best_code[k] = cand[k][c];
       }
     }
     donof_profile_enable(0);
   }
   cudaFreeAsync(E, s);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = best_bk[k];
+  for (int k = 0; k < 3; ++k) g_tune[TuneKey{k + 1, d.N, d.Ap, np}] = best_code[k];
   tune_save_locked();
   return rc;
 }
@@ -1607,93 +1833,65 @@ __device__ int g_test_words[4];  // [0] zero exponent, [1] status, [2] abort fla
 }  // namespace
 }  // namespace donof
 
-extern "C" int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo,
-                                     const uint16_t* B_hi, const uint16_t* B_lo, float* D,
-                                     int32_t M, int32_t N, int32_t K, void* stream) {
+extern "C" int donof_testing_tc_gemm_ex(const uint16_t* A_hi, const uint16_t* A_lo,
+                                        const uint16_t* B_hi, const uint16_t* B_lo, float* D,
+                                        int32_t M, int32_t N, int32_t K, int32_t layout,
+                                        int32_t pair, void* stream) {
   using namespace donof;
   if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
   if (M < 1 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
+    return DONOF_ERR_INVALID_ARG;
+  if (layout < 0 || layout > 2 || pair < 0 || pair > 1) return DONOF_ERR_INVALID_ARG;
+  if ((layout == 1 && M % 64 != 0) || (layout == 2 && M % 8 != 0))
     return DONOF_ERR_INVALID_ARG;
   int* words = nullptr;
   if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
   CUtensorMap ah, al, bh, bl;
   const uint64_t h2 = 2;
-  if (!make_map(&ah, A_hi, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM) ||
-      !make_map(&al, A_lo, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM) ||
-      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
-      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
-    return DONOF_ERR_CUDA;
+  bool ok;
+  if (layout == 1)  // A as [K][M]: x = M (contiguous), y = K; box 64 x 64
+    ok = make_map(&ah, A_hi, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64) &&
+         make_map(&al, A_lo, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64);
+  else if (layout == 2)
+    ok = make_map_il8(&ah, A_hi, K, M, 1, 64, BM) && make_map_il8(&al, A_lo, K, M, 1, 64, BM);
+  else
+    ok = make_map(&ah, A_hi, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM) &&
+         make_map(&al, A_lo, K, M, 1, K * h2, (uint64_t)M * K * h2, 64, BM);
+  const uint32_t brows = pair ? N / 2 : N;  // B rows staged per CTA
+  ok = ok && make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, brows) &&
+       make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, brows);
+  if (!ok) return DONOF_ERR_CUDA;
   TcArgs a{};
   a.mode = 2; a.M = M; a.Nn = N;
   a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
   a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.a_mn = layout == 1;
+  a.a_il8 = layout == 2;
   a.out = D; a.out_ld = N; a.out_zstride = 0;
   a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
   if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
     return DONOF_ERR_CUDA;
-  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  return DONOF_OK;
+  const cudaError_t e = pair ? launch_tc<64, kSplit3, 1>(ah, al, bh, bl, a, (cudaStream_t)stream)
+                             : launch_tc<64, kSplit3, 0>(ah, al, bh, bl, a, (cudaStream_t)stream);
+  return e == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
+}
+
+extern "C" int donof_testing_tc_gemm(const uint16_t* A_hi, const uint16_t* A_lo,
+                                     const uint16_t* B_hi, const uint16_t* B_lo, float* D,
+                                     int32_t M, int32_t N, int32_t K, void* stream) {
+  return donof_testing_tc_gemm_ex(A_hi, A_lo, B_hi, B_lo, D, M, N, K, 0, 0, stream);
 }
 
 extern "C" int donof_testing_tc_gemm_mn(const uint16_t* A_hi, const uint16_t* A_lo,
                                         const uint16_t* B_hi, const uint16_t* B_lo, float* D,
                                         int32_t M, int32_t N, int32_t K, void* stream) {
-  using namespace donof;
-  if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
-  if (M < 1 || M % 64 != 0 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
-    return DONOF_ERR_INVALID_ARG;
-  int* words = nullptr;
-  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
-  CUtensorMap ah, al, bh, bl;
-  const uint64_t h2 = 2;
-  // A as [K][M]: x = M (contiguous), y = K; box 64 x 64
-  if (!make_map(&ah, A_hi, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64) ||
-      !make_map(&al, A_lo, M, K, 1, M * h2, (uint64_t)M * K * h2, 64, 64) ||
-      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
-      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
-    return DONOF_ERR_CUDA;
-  TcArgs a{};
-  a.mode = 2; a.M = M; a.Nn = N;
-  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
-  a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-  a.a_mn = 1;
-  a.out = D; a.out_ld = N; a.out_zstride = 0;
-  a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
-  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  return DONOF_OK;
+  return donof_testing_tc_gemm_ex(A_hi, A_lo, B_hi, B_lo, D, M, N, K, 1, 0, stream);
 }
 
 extern "C" int donof_testing_tc_gemm_il8(const uint16_t* A_hi, const uint16_t* A_lo,
                                          const uint16_t* B_hi, const uint16_t* B_lo, float* D,
                                          int32_t M, int32_t N, int32_t K, void* stream) {
-  using namespace donof;
-  if (!A_hi || !A_lo || !B_hi || !B_lo || !D) return DONOF_ERR_INVALID_ARG;
-  if (M < 1 || M % 8 != 0 || K < 8 || K % 8 != 0 || N < 16 || N > 256 || N % 16 != 0)
-    return DONOF_ERR_INVALID_ARG;
-  int* words = nullptr;
-  if (cudaGetSymbolAddress((void**)&words, g_test_words) != cudaSuccess) return DONOF_ERR_CUDA;
-  CUtensorMap ah, al, bh, bl;
-  const uint64_t h2 = 2;
-  if (!make_map_il8(&ah, A_hi, K, M, 1, 64, BM) || !make_map_il8(&al, A_lo, K, M, 1, 64, BM) ||
-      !make_map(&bh, B_hi, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N) ||
-      !make_map(&bl, B_lo, K, N, 1, K * h2, (uint64_t)N * K * h2, 64, N))
-    return DONOF_ERR_CUDA;
-  TcArgs a{};
-  a.mode = 2; a.M = M; a.Nn = N;
-  a.m_tiles = (M + BM - 1) / BM; a.z_count = 1; a.splits = 1;
-  a.kt_per_kb = (K + 63) / 64; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-  a.a_il8 = 1;
-  a.out = D; a.out_ld = N; a.out_zstride = 0;
-  a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
-  if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  if (launch_tc<64, kSplit3>(ah, al, bh, bl, a, (cudaStream_t)stream) != cudaSuccess)
-    return DONOF_ERR_CUDA;
-  return DONOF_OK;
+  return donof_testing_tc_gemm_ex(A_hi, A_lo, B_hi, B_lo, D, M, N, K, 2, 0, stream);
 }
 
 namespace donof {

@@ -2,7 +2,8 @@
 operands (and a low part of multiples of 1/64) every product and partial sum is exact in
 fp32, so the result must equal the double-precision product exactly, for A given K-major
 (128-byte swizzle), MN-major, and K-major interleaved by 8 (no swizzle, core matrices),
-ragged K (zero fill past the end) and one or several M tiles.  Also the bounded device
+ragged K (zero fill past the end) and one or several M tiles, on single CTAs and on CTA pairs
+(cta_group::2, 256-row tiles).  Also the bounded device
 wait: run out on purpose, it reports DONOF_ERR_TIMEOUT, ends the other role's wait through
 the abort flag, and leaves the context usable."""
 import ctypes
@@ -27,6 +28,7 @@ def lib():
     L.donof_testing_tc_gemm.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_tc_gemm_mn.argtypes = [vp] * 5 + [i32] * 3 + [vp]
     L.donof_testing_tc_gemm_il8.argtypes = [vp] * 5 + [i32] * 3 + [vp]
+    L.donof_testing_tc_gemm_ex.argtypes = [vp] * 5 + [i32] * 5 + [vp]
     L.donof_testing_status.argtypes = [vp]
     L.donof_testing_wait_timeout.argtypes = [ctypes.c_int64, ctypes.c_int64, vp]
     return L
@@ -65,6 +67,37 @@ def test_split_product_exact(lib, M, N, K, layout):
     assert rc == 0
     assert lib.donof_testing_status(s) == 0
     np.testing.assert_array_equal(D.cpu().numpy().astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 160, 200), (384, 160, 128), (128, 48, 72),
+                                   (512, 144, 1216)])
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_pair_product_exact(lib, M, N, K, layout):
+    # the cta_group::2 path (a CTA pair per 256-row tile, each CTA staging half of B): the same
+    # exact products, with an odd number of 128-row tiles (the second CTA of the last pair
+    # has no rows) and a long K
+    import torch
+    rng = np.random.default_rng(7 * M + N + K)
+    Ah = rng.integers(-8, 9, (M, K)).astype(np.float64)
+    Al = rng.integers(-8, 9, (M, K)) / 64.0
+    Bh = rng.integers(-8, 9, (N, K)).astype(np.float64)
+    Bl = rng.integers(-8, 9, (N, K)) / 64.0
+    ref = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    if layout == 1:
+        a_h, a_l = Ah.T, Al.T
+    elif layout == 2:
+        a_h, a_l = (x.reshape(M, K // 8, 8).transpose(1, 0, 2) for x in (Ah, Al))
+    else:
+        a_h, a_l = Ah, Al
+    dah, dal, dbh, dbl = _half_dev(a_h), _half_dev(a_l), _half_dev(Bh), _half_dev(Bl)
+    s = torch.cuda.current_stream().cuda_stream
+    for pair in (1, 0):
+        D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        rc = lib.donof_testing_tc_gemm_ex(dah.data_ptr(), dal.data_ptr(), dbh.data_ptr(),
+                                          dbl.data_ptr(), D.data_ptr(), M, N, K, layout, pair, s)
+        assert rc == 0
+        assert lib.donof_testing_status(s) == 0
+        np.testing.assert_array_equal(D.cpu().numpy().astype(np.float64), ref)
 
 
 def test_bounded_wait_runs_out_and_context_survives(lib):
