@@ -14,11 +14,16 @@
 // 64-byte (BK = 32) swizzling; A may also be MN-major (transposed tiles of B) or K-major
 // interleaved by 8 (X in the G contraction).
 //
-// CTA roles (256 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma,
-// warp 2 owns the TMEM allocation, warps 4..7 drain the accumulator (one TMEM lane per
-// thread).  When two accumulator sets fit in TMEM the epilogue of one tile overlaps the
-// MMAs of the next; otherwise the epilogue releases TMEM as soon as the accumulators are
-// in registers.  Persistent grid: one CTA per SM, units handed out round-robin.
+// CTA roles (384 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma,
+// warp 2 owns the TMEM allocation, warps 4..11 drain the accumulator (one TMEM lane per
+// thread, two warps per lane quadrant, each with half of the columns).  When two accumulator
+// sets fit in TMEM the epilogue of one tile overlaps the MMAs of the next; with three
+// regions in rotation (144 or 160 columns) the next tile waits for half of the drain;
+// otherwise the epilogue releases TMEM as soon as the accumulators are in registers.
+// Persistent grid: one CTA per SM, units handed out round-robin.  With CTA pairs (clusters
+// of two, cta_group::2) each 256-row tile is split between two SMs: the even CTA issues the
+// MMAs, each CTA stages its 128 rows of A and half of the B rows, the odd CTA's warp 3
+// relays its landed stages to the even CTA.
 #include <cuda.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -278,22 +283,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -315,6 +316,12 @@ __device__ __forceinline__ void tmem_wait_ld() {
 constexpr int kSplit3 = 0;
 constexpr int kIntFrac = 1;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
+constexpr int kEpiGroups = 2;     // epilogue warps per TMEM lane quadrant (each half the columns)
+constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay warps + epilogue
+// per epilogue warp, the column factors of its chunks (up to 256 columns split between the
+// groups), one float2 per column, in shared memory after the barriers
+constexpr int kTabCols = 256 / kEpiGroups;
+constexpr int kTabBytes = 4 * kEpiGroups * kTabCols * 8;
 
 struct TcArgs {
   int mode;        // 1: X stores (integer + fraction X^T for b, X for G); 2: fp32
@@ -382,13 +389,20 @@ __device__ __forceinline__ int rr_partner(int i, int r, int T) {
   return p >= T ? i : p;
 }
 
+// intfrac_split of two values at once (paired conversions; the same results)
+__device__ __forceinline__ void intfrac_split2(float y0, float y1, __half2& h, __half2& f) {
+  h = __floats2half2_rn(rintf(y0), rintf(y1));
+  const float2 hb = __half22float2(h);
+  f = __floats2half2_rn(y0 - hb.x, y1 - hb.y);
+}
+
 __device__ __forceinline__ float pow2f(int e) {
   e = e < -126 ? -126 : (e > 127 ? 127 : e);
   return __int_as_float((e + 127) << 23);
 }
 
 template <int BK, int NUM, int PAIR>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               const TcArgs args) {
@@ -416,7 +430,8 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
   const int cl = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;   // this CTA's work stream
   const int ncl = PAIR ? (int)ncluster_x() : (int)gridDim.x;
-  const uint32_t rel_count = PAIR ? 256u : 128u;  // epilogue threads that release TMEM
+  // epilogue threads that release TMEM (of both CTAs of a pair)
+  const uint32_t rel_count = (PAIR ? 2u : 1u) * 128u * kEpiGroups;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (threadIdx.x == 0) {
@@ -667,7 +682,14 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue: TMEM -> registers -> global
+    // warp 4 + ew reads TMEM lane quadrant q = ew % 4 (the quadrant a warp may access is its
+    // index mod 4) and the column chunks of group ew / 4
     const int ew = warp - 4;
+    const int q = ew & 3, eg = ew >> 2;
+    // this group's 16-column chunks [ch0, ch1), and this warp's table of column factors
+    const int nch = args.Nn / 16, hch = (nch + kEpiGroups - 1) / kEpiGroups;
+    const int ch0 = eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
+    float2* ctab = (float2*)(bars + 2 * S + 8) + ew * kTabCols;
     const int glob = args.glob_exp ? *args.glob_exp : 0;
     // a release of TMEM: on the even CTA's barrier (remotely from the odd CTA of a pair)
     auto release = [&](int i) {
@@ -692,11 +714,9 @@ __global__ void __launch_bounds__(256, 1)
         c0off = (uint32_t)(tf * args.buf_stride);
         c1off = c0off + (uint32_t)args.Nn;
       }
-      bool ok = mbar_wait(bar(kTfull + tf), tf_phase, status, abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      tc_fence_after();
-      const int row = mt * BM + ew * 32 + lane;
+      // everything that needs no accumulator (exponents, the factor table) is looked up
+      // before waiting for it, while the tile's MMAs run
+      const int row = mt * BM + q * 32 + lane;
       // mode 1: slice and AO index of this row, the exponent of its X row in the G
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
@@ -711,52 +731,69 @@ __global__ void __launch_bounds__(256, 1)
         valid = valid && rmu < args.Nrow;
       }
       const int erow_i = (args.mode == 1 || args.sym) ? rP * args.Nrow + rmu : row;
-      const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
       const uint32_t t0 = tmem_base + c0off + lane_off;
       const uint32_t t1 = tmem_base + c1off + lane_off;
       const int erow = (NUM == kIntFrac && valid)
                            ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + erow_i]
                            : 0;
-      float sx3 = 1.f;
-      const int* exrow = nullptr;
-      if (args.mode == 1 && valid) {
-        sx3 = pow2f(-args.eX3[(size_t)args.spOf[rP] * args.Nrow + rmu]);
-        exrow = args.eXt + (size_t)rP * args.Ap;
-      }
+      // every output is the accumulator times powers of two: a row factor 2^erow (and for X
+      // 2^-eX3 of its G split) and a column factor, 2^(ecol - eXt) for X^T and 2^ecol for X
+      // (mode 1), 2^(ecol + glob) (mode 2); the column factors of this warp's chunks are
+      // tabulated once per tile
+      const bool zvalid = z < args.z_count;
       const int* ecol =
           (NUM == kIntFrac) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
+      __syncwarp();  // every lane is done with the previous tile's table
+      if (zvalid) {
+        const int* exz = args.mode == 1 ? args.eXt + (size_t)z * args.Ap : nullptr;
+        for (int k = lane; k < (ch1 - ch0) * 16; k += 32) {
+          const int c = ch0 * 16 + k;
+          const int ec = NUM == kIntFrac ? ecol[c] : 0;
+          ctab[k] = args.mode == 1 ? make_float2(pow2f(ec - exz[c]), pow2f(ec))
+                                   : make_float2(pow2f(ec + glob), 0.f);
+        }
+      }
+      __syncwarp();
+      const float rT = pow2f(erow);
+      float rX = 0.f;
+      if (args.mode == 1 && valid)
+        rX = rT * pow2f(-args.eX3[(size_t)args.spOf[rP] * args.Nrow + rmu]);
       // the diagonal entry of this row (mode 2 with diag): its column, -1 for none
       int dq = -1;
       long long drow = 0;
       if (args.mode == 2 && args.diag && valid) {
-        const int q = row % args.Nn;
-        if (q < args.diag_A) {
-          dq = q;
-          drow = (long long)(row / args.Nn) * args.diag_A + q;
+        const int qd = row % args.Nn;
+        if (qd < args.diag_A) {
+          dq = qd;
+          drow = (long long)(row / args.Nn) * args.diag_A + qd;
         }
       }
+
+      bool ok = mbar_wait(bar(kTfull + tf), tf_phase, status, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
 
       // one 16-column chunk: raw accumulator values -> outputs
       auto emit = [&](int c0, const float (&a)[16]) {
         if (!valid) return;
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int e = (NUM == kIntFrac ? erow + ecol[c0 + j] : 0) + (args.mode >= 2 ? glob : 0);
-          v[j] = a[j] * pow2f(e);
-        }
+        const float2* tb = ctab + (c0 - ch0 * 16);
         if (args.mode == 1) {
           const size_t to = ((size_t)rP * args.Ap + c0) * args.Np + rmu;
-          const int* ex = exrow + c0;
+          __align__(16) __half2 hi[8], lo[8];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            intfrac_split(v[j] * pow2f(-ex[j]), args.xth[to + (size_t)j * args.Np],
-                          args.xtf[to + (size_t)j * args.Np]);
-          }
-          __align__(16) __half hi[16], lo[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            intfrac_split(v[j] * sx3, hi[j], lo[j]);
+          for (int j = 0; j < 16; j += 2) {
+            const float2 t0 = tb[j], t1 = tb[j + 1];
+            __half2 h, f;
+            // X^T for b = C^T X (exponent of its row (P, q))
+            intfrac_split2(a[j] * rT * t0.x, a[j + 1] * rT * t1.x, h, f);
+            args.xth[to + (size_t)j * args.Np] = __low2half(h);
+            args.xth[to + (size_t)(j + 1) * args.Np] = __high2half(h);
+            args.xtf[to + (size_t)j * args.Np] = __low2half(f);
+            args.xtf[to + (size_t)(j + 1) * args.Np] = __high2half(f);
+            // X for the G contraction (exponent of its row (split, mu))
+            intfrac_split2(a[j] * rX * t0.y, a[j + 1] * rX * t1.y, hi[j / 2], lo[j / 2]);
           }
           // X interleaved by 8 along c, [P][c/8][mu][8]: the lanes (consecutive mu) of one
           // store write 512 contiguous bytes
@@ -767,6 +804,9 @@ __global__ void __launch_bounds__(256, 1)
           *(uint4*)(args.xlo + o0) = ((uint4*)lo)[0];
           *(uint4*)(args.xlo + o1) = ((uint4*)lo)[1];
         } else {
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = a[j] * rT * tb[j].x;
           float* o = args.out + (long long)(z * args.splits + sp) * args.out_zstride +
                      (long long)row * args.out_ld + c0;
 #pragma unroll
@@ -790,36 +830,38 @@ __global__ void __launch_bounds__(256, 1)
         }
       };
 
+      constexpr int kKeep = (kMaxRegCols / 16 + kEpiGroups - 1) / kEpiGroups;  // chunks held
       if (args.Nn <= kMaxRegCols) {
-        // drain the accumulators into registers (32 columns per load), hand TMEM back, then
-        // write.  nbuf 3: the cross products (region Y) first, all in flight together, then Y
-        // is released and the integer products (X or Z) are added in chunks; otherwise both
-        // accumulators chunk by chunk, one wait per pair of loads
-        float keep[kMaxRegCols];
+        // drain the accumulators into registers, hand TMEM back, then write.  nbuf 3: the
+        // cross products (region Y) first, all in flight together, then Y is released and the
+        // integer products (X or Z) are added chunk by chunk; otherwise both accumulators
+        // chunk by chunk
+        float keep[kKeep * 16];
         if (nbuf == 3) {
 #pragma unroll
-          for (int cc = 0; cc < kMaxRegCols / 32; ++cc)
-            if (cc * 32 < args.Nn) tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), keep + cc * 32);
+          for (int k = 0; k < kKeep; ++k)
+            if (ch0 + k < ch1) tmem_ld16_nowait(t1 + (uint32_t)((ch0 + k) * 16), keep + k * 16);
           tmem_wait_ld();
           release(kTempty + 0);
         }
 #pragma unroll
-        for (int cc = 0; cc < kMaxRegCols / 32; ++cc) {
-          if (cc * 32 < args.Nn) {
+        for (int k = 0; k < kKeep; ++k) {
+          if (ch0 + k < ch1) {
+            const uint32_t c = (uint32_t)((ch0 + k) * 16);
             if (nbuf == 3) {
-              float tmp[32];
-              tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), tmp);
+              float tmp[16];
+              tmem_ld16_nowait(t0 + c, tmp);
               tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < 32; ++j) keep[cc * 32 + j] = tmp[j] + keep[cc * 32 + j];
+              for (int j = 0; j < 16; ++j) keep[k * 16 + j] = tmp[j] + keep[k * 16 + j];
             } else {
-              tmem_ld32_nowait(t0 + (uint32_t)(cc * 32), keep + cc * 32);
+              tmem_ld16_nowait(t0 + c, keep + k * 16);
               if (NUM == kIntFrac) {
-                float tmp[32];
-                tmem_ld32_nowait(t1 + (uint32_t)(cc * 32), tmp);
+                float tmp[16];
+                tmem_ld16_nowait(t1 + c, tmp);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) keep[cc * 32 + j] += tmp[j];
+                for (int j = 0; j < 16; ++j) keep[k * 16 + j] += tmp[j];
               }
             }
           }
@@ -827,19 +869,19 @@ __global__ void __launch_bounds__(256, 1)
         tmem_wait_ld();
         release(nbuf == 3 ? kTrel + (local & 1) : kTempty + tf);
 #pragma unroll
-        for (int cc = 0; cc < kMaxRegCols / 16; ++cc) {
-          if (cc * 16 < args.Nn) {
+        for (int k = 0; k < kKeep; ++k) {
+          if (ch0 + k < ch1) {
             float a[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) a[j] = keep[cc * 16 + j];
-            emit(cc * 16, a);
+            for (int j = 0; j < 16; ++j) a[j] = keep[k * 16 + j];
+            emit((ch0 + k) * 16, a);
           }
         }
       } else {
-        for (int c0 = 0; c0 < args.Nn; c0 += 16) {
+        for (int c = ch0; c < ch1; ++c) {
           float a[16];
-          load(c0, a);
-          emit(c0, a);
+          load(c * 16, a);
+          emit(c * 16, a);
         }
         release(kTempty + tf);
       }
@@ -988,7 +1030,8 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)(PAIR ? a.Nn / 2 : a.Nn) * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  const size_t budget = 232448 - 1024 - 512;  // the 227 KB opt-in limit, less alignment and barriers
+  // the 227 KB opt-in limit, less alignment, barriers and the epilogue's factor tables
+  const size_t budget = 232448 - 1024 - 512 - kTabBytes;
   int stages = (int)(budget / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
@@ -1008,7 +1051,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
     a.nbuf = 1;
     a.buf_stride = 0;
   }
-  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 7) * 8 + 16;
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 8) * 8 + kTabBytes;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1023,7 +1066,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   if (PAIR) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * work);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -1038,7 +1081,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  k_tc_gemm<BK, NUM, PAIR><<<work, 256, smem, s>>>(ah, al, bh, bl, a);
+  k_tc_gemm<BK, NUM, PAIR><<<work, kThreads, smem, s>>>(ah, al, bh, bl, a);
   count_launch(1);
   return cudaGetLastError();
 }
