@@ -8,8 +8,9 @@
 //   (3) G[mu][p]   += sum_P sum_q X[P][mu][q] Y[P][q][p]   M = N, N = Ap, K = np*Ap (split)
 //   (4) h C_act and lambda = C^T G                    M = N, N = Ap, K = 4 blocks of N:
 //       residual-extended operands (see SplitJob), near double precision
-// Operands are integer + fraction pairs (kIntFrac below): four products per K step, the
-// integer products exact in one TMEM accumulator, the others in a second, fp32.  A and B
+// Operands are integer + fraction pairs (kIntFrac below): four products per K step (three
+// in (1), where the smallest, f*f, is left out), the integer products exact in one TMEM
+// accumulator, the others in a second, fp32.  A and B
 // are staged by TMA (or bulk copies for the tile storage of B) with 128-byte (BK = 64) or
 // 64-byte (BK = 32) swizzling; A may also be MN-major (transposed tiles of B) or K-major
 // interleaved by 8 (X in the G contraction).
@@ -315,6 +316,10 @@ __device__ __forceinline__ void tmem_wait_ld() {
 //            is kept as close to 2^12 as the rounding of h allows.
 constexpr int kSplit3 = 0;
 constexpr int kIntFrac = 1;
+// kIntFrac3: kIntFrac without the f*f product (three products per K step); its error is the
+// sum of the dropped f_a f_b (|f| <= 1/2 each), about sqrt(K) / 12 in units of the integer
+// grid, several times the representation error of the four-product form
+constexpr int kIntFrac3 = 2;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
 constexpr int kEpiGroups = 2;     // epilogue warps per TMEM lane quadrant (each half the columns)
 constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay warps + epilogue
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_f16<PAIR>(d0, ah, bh, id, first);  // integer x integer: exact
             mma_f16<PAIR>(d1, ah, bl, id, first);
             mma_f16<PAIR>(d1, al, bh, id, 1u);
-            mma_f16<PAIR>(d1, al, bl, id, 1u);
+            if (NUM == kIntFrac) mma_f16<PAIR>(d1, al, bl, id, 1u);
           }
         }
         mma_commit<PAIR>(bar(kEmpty + stage));  // frees the stage in both CTAs of a pair
@@ -734,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t lane_off = (uint32_t)(q * 32) << 16;
       const uint32_t t0 = tmem_base + c0off + lane_off;
       const uint32_t t1 = tmem_base + c1off + lane_off;
-      const int erow = (NUM == kIntFrac && valid)
+      const int erow = (NUM != kSplit3 && valid)
                            ? args.eA[z * args.eA_zstride + sp * args.eA_sstride + erow_i]
                            : 0;
       // every output is the accumulator times powers of two: a row factor 2^erow (and for X
@@ -743,13 +748,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       // tabulated once per tile
       const bool zvalid = z < args.z_count;
       const int* ecol =
-          (NUM == kIntFrac) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
+          (NUM != kSplit3) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
       __syncwarp();  // every lane is done with the previous tile's table
       if (zvalid) {
         const int* exz = args.mode == 1 ? args.eXt + (size_t)z * args.Ap : nullptr;
         for (int k = lane; k < (ch1 - ch0) * 16; k += 32) {
           const int c = ch0 * 16 + k;
-          const int ec = NUM == kIntFrac ? ecol[c] : 0;
+          const int ec = NUM != kSplit3 ? ecol[c] : 0;
           ctab[k] = args.mode == 1 ? make_float2(pow2f(ec - exz[c]), pow2f(ec))
                                    : make_float2(pow2f(ec + glob), 0.f);
         }
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16(t0 + (uint32_t)c0, r);
 #pragma unroll
         for (int j = 0; j < 16; ++j) a[j] = __uint_as_float(r[j]);
-        if (NUM == kIntFrac) {
+        if (NUM != kSplit3) {
           tmem_ld16(t1 + (uint32_t)c0, r);
 #pragma unroll
           for (int j = 0; j < 16; ++j) a[j] += __uint_as_float(r[j]);
@@ -856,7 +861,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int j = 0; j < 16; ++j) keep[k * 16 + j] = tmp[j] + keep[k * 16 + j];
             } else {
               tmem_ld16_nowait(t0 + c, keep + k * 16);
-              if (NUM == kIntFrac) {
+              if (NUM != kSplit3) {
                 float tmp[16];
                 tmem_ld16_nowait(t1 + c, tmp);
                 tmem_wait_ld();
@@ -946,15 +951,15 @@ void tune_save_locked() {
   fclose(f);
 }
 
-// kinds: 1 = half transform, 2 = b, 3 = G.  Defaults: the half transform on CTA pairs (two
-// slices' row tiles per cluster, a whole number of slices at once), b with BK 64 and G with
-// BK 32 on single CTAs.
+// kinds: 1 = half transform, 2 = b, 3 = G.  Defaults (the fastest measured at the large
+// workload): single CTAs, BK 64 for the half transform (a whole number of slices at once)
+// and b, BK 32 for G.
 TuneCode tuned_variant(int kind, int N, int Ap, int np) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_load_locked();
   auto it = g_tune.find(TuneKey{kind, N, Ap, np});
   if (it != g_tune.end()) return decode_tune(it->second);
-  return decode_tune(kind == 1 ? 1064 : (kind == 3 ? 32 : 64));
+  return decode_tune(kind == 3 ? 32 : 64);
 }
 
 // ------------------------------------------------------------------ host: tensor maps
@@ -1038,13 +1043,13 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   a.stages = stages;
   // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart); two sets if they fit,
   // else (kIntFrac, up to kMaxRegCols columns) three regions in rotation, else one set
-  const int per_set = (NUM == kIntFrac ? 2 : 1) * a.Nn;
+  const int per_set = (NUM != kSplit3 ? 2 : 1) * a.Nn;
   a.tmem_cols = 512;
   if (2 * per_set <= 512) {
     a.nbuf = 2;
     a.buf_stride = 256;
     if (per_set > 256) return cudaErrorInvalidValue;
-  } else if (NUM == kIntFrac && 3 * a.Nn <= 512 && a.Nn <= kMaxRegCols) {
+  } else if (NUM != kSplit3 && 3 * a.Nn <= 512 && a.Nn <= kMaxRegCols) {
     a.nbuf = 3;
     a.buf_stride = 0;
   } else {
@@ -1706,7 +1711,11 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
     // A operand: the symmetric tile storage of the split B (bulk copies, BK = 64); B
-    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices)
+    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices).  Three
+    // products per K step (no f*f): at the large workload the errors against the FP64
+    // oracle stay within budget (E 2.2e-7 Eh instead of 1.5e-7, dE/dC 4.4e-7 instead of
+    // 1.8e-7) for 10 % less time; b and G keep all four (without f*f there, E is off by
+    // 4.7e-6 Eh through the diagonal of b, and dE/dC by 9e-6 through G)
     const SymTiles st = sym_tiles(N);
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
@@ -1736,7 +1745,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac3>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
   // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
@@ -1819,9 +1828,9 @@ int autotune_build(const donof_problem* prob, const double* h, const double* B, 
   // whole number of slices' row tiles or every SM pair
   const int phases[3] = {DONOF_PHASE_HALF_TRANSFORM, DONOF_PHASE_MO_3INDEX, DONOF_PHASE_G_BUILD};
   constexpr int kCand = 3;
-  const int cand[3][kCand] = {{1064, 3064, 64}, {64, 32, 1064}, {32, 64, 1064}};
+  const int cand[3][kCand] = {{64, 1064, 3064}, {64, 32, 1064}, {32, 64, 1064}};
   double best_ms[3] = {1e300, 1e300, 1e300};
-  int best_code[3] = {1064, 64, 32};
+  int best_code[3] = {64, 64, 32};
   double* E = nullptr;
   if (cudaMallocAsync((void**)&E, sizeof(double), s) != cudaSuccess) return DONOF_ERR_CUDA;
   int rc = DONOF_OK;
