@@ -8,9 +8,8 @@
 //   (3) G[mu][p]   += sum_P sum_q X[P][mu][q] Y[P][q][p]   M = N, N = Ap, K = np*Ap (split)
 //   (4) h C_act and lambda = C^T G                    M = N, N = Ap, K = 4 blocks of N:
 //       residual-extended operands (see SplitJob), near double precision
-// Operands are integer + fraction pairs (kIntFrac below): four products per K step (three
-// in (1), where the smallest, f*f, is left out), the integer products exact in one TMEM
-// accumulator, the others in a second, fp32.  A and B
+// Operands are integer + fraction pairs (kIntFrac below): four products per K step, the
+// integer products exact in one TMEM accumulator, the others in a second, fp32.  A and B
 // are staged by TMA (or bulk copies for the tile storage of B) with 128-byte (BK = 64) or
 // 64-byte (BK = 32) swizzling; A may also be MN-major (transposed tiles of B) or K-major
 // interleaved by 8 (X in the G contraction).
@@ -316,10 +315,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
 //            is kept as close to 2^12 as the rounding of h allows.
 constexpr int kSplit3 = 0;
 constexpr int kIntFrac = 1;
-// kIntFrac3: kIntFrac without the f*f product (three products per K step); its error is the
-// sum of the dropped f_a f_b (|f| <= 1/2 each), about sqrt(K) / 12 in units of the integer
-// grid, several times the representation error of the four-product form
-constexpr int kIntFrac3 = 2;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
 constexpr int kEpiGroups = 2;     // epilogue warps per TMEM lane quadrant (each half the columns)
 constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay warps + epilogue
@@ -664,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_f16<PAIR>(d0, ah, bh, id, first);  // integer x integer: exact
             mma_f16<PAIR>(d1, ah, bl, id, first);
             mma_f16<PAIR>(d1, al, bh, id, 1u);
-            if (NUM == kIntFrac) mma_f16<PAIR>(d1, al, bl, id, 1u);
+            mma_f16<PAIR>(d1, al, bl, id, 1u);
           }
         }
         mma_commit<PAIR>(bar(kEmpty + stage));  // frees the stage in both CTAs of a pair
@@ -1711,11 +1706,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
     // A operand: the symmetric tile storage of the split B (bulk copies, BK = 64); B
-    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices).  Three
-    // products per K step (no f*f): at the large workload the errors against the FP64
-    // oracle stay within budget (E 2.2e-7 Eh instead of 1.5e-7, dE/dC 4.4e-7 instead of
-    // 1.8e-7) for 10 % less time; b and G keep all four (without f*f there, E is off by
-    // 4.7e-6 Eh through the diagonal of b, and dE/dC by 9e-6 through G)
+    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices)
     const SymTiles st = sym_tiles(N);
     const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
     const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
@@ -1745,7 +1736,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
     a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
     a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
     a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_variant<kIntFrac3>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
   // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
