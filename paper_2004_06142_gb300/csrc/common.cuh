@@ -87,6 +87,55 @@ __host__ __device__ inline SymTiles sym_tiles(int N) {
   return t;
 }
 
+// ---------------------------------------------------------------------------
+// Grouped launches (batch.cu): one launch runs a kernel for every instance of a batch.  A
+// kernel body takes its block coordinates as a Blk (the native ones for a single instance);
+// in a grouped launch instance i owns the blocks [start[i], start[i+1]) of the flat grid,
+// laid out as its own grid of dims[3i .. 3i+2].
+// ---------------------------------------------------------------------------
+struct Blk {
+  int x, y, z, gx, gy, gz;
+};
+__device__ __forceinline__ Blk native_blk() {
+  return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+             (int)gridDim.x,  (int)gridDim.y,  (int)gridDim.z};
+}
+// One instance of a batch: its sizes, workspace carving and pointers.
+struct InstRec {
+  Dims d;
+  Layout L;
+  char* ws;
+  const double *h, *B, *C, *gamma;
+  const int32_t* pm;
+  double *E, *lam, *dEdg, *dEdC;
+  const double* Ebar;  // upstream gradient of the adjoint (1.0)
+};
+struct GroupLaunch {
+  const InstRec* inst;
+  const int* start;  // [ninst + 1]
+  const int* dims;   // [3 ninst]
+  int ninst;
+};
+// The instance of this block and its coordinates in that instance's grid.
+__device__ __forceinline__ int group_locate(const GroupLaunch& g, Blk& b) {
+  const int bid = (int)blockIdx.x;
+  int lo = 0, hi = g.ninst - 1;
+  while (lo < hi) {  // the last instance whose first block is at or before bid
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.start[mid] <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  const int l = bid - g.start[lo];
+  const int gx = g.dims[3 * lo], gy = g.dims[3 * lo + 1], gz = g.dims[3 * lo + 2];
+  b.x = l % gx;
+  b.y = (l / gx) % gy;
+  b.z = l / (gx * gy);
+  b.gx = gx;
+  b.gy = gy;
+  b.gz = gz;
+  return lo;
+}
+
 // Tracing (api.cu): no-ops unless donof_profile_enable(1) was called.
 void prof_begin(int phase, cudaStream_t s);
 void prof_end(int phase, cudaStream_t s);

@@ -142,12 +142,12 @@ namespace {
 // kTable (one CTA): sin and cos of every gamma are formed once into shared memory, so the
 // FP64 trigonometry is not repeated per orbital (the narrow FP64 pipe makes it the cost).
 template <bool kTable>
-__global__ void k_occupations(Dims d, const double* __restrict__ gamma,
+__device__ __forceinline__ void k_occupations_body(const Blk& B_, Dims d, const double* __restrict__ gamma,
                               const int32_t* __restrict__ pm, DevHeader* hdr, double* n,
                               double* sqn, double* phi, double* dn, double* dsq, double* dphi) {
   extern __shared__ double trig[];  // kTable: sin[ng], cos[ng]
   const int A = d.A, ng = d.ng, npair = d.npair, ncwo = d.ncwo;
-  for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < ng; k += blockDim.x * gridDim.x) {
+  for (int k = threadIdx.x + B_.x * blockDim.x; k < ng; k += blockDim.x * B_.gx) {
     if (!isfinite(gamma[k])) set_status(hdr, DONOF_ERR_NONFINITE);
     if (kTable) {
       trig[k] = sin(gamma[k]);
@@ -155,7 +155,7 @@ __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
     }
   }
   if (kTable) __syncthreads();
-  const int p = threadIdx.x + blockIdx.x * blockDim.x;
+  const int p = threadIdx.x + B_.x * blockDim.x;
   if (p >= A) return;
   const int nsub = npair + d.nsingle;  // subspaces: pairs, then the singly occupied orbitals
   const int g = pm[p];
@@ -192,6 +192,12 @@ __global__ void k_occupations(Dims d, const double* __restrict__ gamma,
   else
     occ_orbital(p, g, rank, npair, ncwo, TrigDirect{gamma}, n[p], sqn[p], phi[p], put);
 }
+template <bool kTable>
+__global__ void k_occupations(Dims d, const double* __restrict__ gamma,
+                              const int32_t* __restrict__ pm, DevHeader* hdr, double* n,
+                              double* sqn, double* phi, double* dn, double* dsq, double* dphi) {
+  k_occupations_body<kTable>(native_blk(), d, gamma, pm, hdr, n, sqn, phi, dn, dsq, dphi);
+}
 }  // namespace
 
 cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t* pm, char* ws,
@@ -225,12 +231,12 @@ cudaError_t launch_occupations(const Dims& d, const double* gamma, const int32_t
 //                                          -n_p n_q - 4 Phi_p^2 Phi_q^2 (Eq. Efg_s)
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+__device__ __forceinline__ void k_coefficients_body(const Blk& B_, Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
                                const double* __restrict__ sqn, const double* __restrict__ phi,
                                double* Ac, double* Bc, float* AcF, float* BcF) {
   // with AcF/BcF (mixed path) also their fp32 copies, [Ap][Ap] with zero padding
   const int A = d.A, W = AcF ? d.Ap : d.A;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = (long long)B_.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)W * W) return;
   const int p = (int)(idx / W), q = (int)(idx % W);
   double a = 0.0, b = 0.0;
@@ -244,6 +250,11 @@ __global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const dou
     AcF[idx] = (float)a;
     BcF[idx] = (float)b;
   }
+}
+__global__ void k_coefficients(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+                               const double* __restrict__ sqn, const double* __restrict__ phi,
+                               double* Ac, double* Bc, float* AcF, float* BcF) {
+  k_coefficients_body(native_blk(), d, pm, n, sqn, phi, Ac, Bc, AcF, BcF);
 }
 }  // namespace
 
@@ -289,9 +300,9 @@ cudaError_t launch_unpack_B(const Dims& d, const double* Bp, int p0, int np, dou
 // ---------------------------------------------------------------------------
 namespace {
 // one warp per orbital p: H_pp over the lanes' rows mu, and G[mu][p] = n_p (h C)[mu][p]
-__global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
+__device__ __forceinline__ void k_hdiag_ginit_body(const Blk& B_, Dims d, const double* __restrict__ C, const double* __restrict__ hC,
                               const double* __restrict__ n, double* Hd, double* G, double gscale) {
-  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int p = B_.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (p >= d.A) return;
   const double np_ = n[p];
@@ -303,6 +314,10 @@ __global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) Hd[p] = s;
+}
+__global__ void k_hdiag_ginit(Dims d, const double* __restrict__ C, const double* __restrict__ hC,
+                              const double* __restrict__ n, double* Hd, double* G, double gscale) {
+  k_hdiag_ginit_body(native_blk(), d, C, hC, n, Hd, G, gscale);
 }
 }  // namespace
 
@@ -423,13 +438,13 @@ cudaError_t launch_build_Y_f64(const Dims& d, const double* b, double* Y, int np
 // k_energy_final: E as a fixed-order sum of the shares, then dE/dgamma (a warp per output).
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+__device__ __forceinline__ void k_energy_rows_body(const Blk& B_, Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
                               const double* __restrict__ sqn, const double* __restrict__ phi,
                               const double* __restrict__ Ac, const double* __restrict__ Bc,
                               const double* __restrict__ Hd, const double* __restrict__ J,
                               const double* __restrict__ K, double* part) {
   const int A = d.A;
-  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int p = B_.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (p >= A) return;
   const int g = pm[p];
@@ -465,8 +480,15 @@ __global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const doub
     part[3 * A + p] = (d.functional == DONOF_PNOF7) ? a_p : 0.0;
   }
 }
+__global__ void k_energy_rows(Dims d, const int32_t* __restrict__ pm, const double* __restrict__ n,
+                              const double* __restrict__ sqn, const double* __restrict__ phi,
+                              const double* __restrict__ Ac, const double* __restrict__ Bc,
+                              const double* __restrict__ Hd, const double* __restrict__ J,
+                              const double* __restrict__ K, double* part) {
+  k_energy_rows_body(native_blk(), d, pm, n, sqn, phi, Ac, Bc, Hd, J, K, part);
+}
 
-__global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __restrict__ part,
+__device__ __forceinline__ void k_energy_final_body(const Blk& B_, Dims d, const double* __restrict__ part,
                                                        const double* __restrict__ dn,
                                                        const double* __restrict__ dsq,
                                                        const double* __restrict__ dphi,
@@ -475,8 +497,8 @@ __global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __re
   // one warp per output (E first, then each dE/dgamma_k), lanes over orbitals, a fixed
   // shuffle tree: the sums do not depend on scheduling
   const int A = d.A;
-  const int lane = threadIdx.x % 32, nw = gridDim.x * (blockDim.x / 32);
-  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32, nw = B_.gx * (blockDim.x / 32);
+  const int warp = B_.x * (blockDim.x / 32) + threadIdx.x / 32;
   const double* gn = part + A;
   const double* gs = part + 2 * A;
   const double* gp = part + 3 * A;
@@ -503,6 +525,14 @@ __global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __re
     }
   }
 }
+__global__ void __launch_bounds__(256) k_energy_final(Dims d, const double* __restrict__ part,
+                                                       const double* __restrict__ dn,
+                                                       const double* __restrict__ dsq,
+                                                       const double* __restrict__ dphi,
+                                                       DevHeader* hdr, double* dEdg_ws,
+                                                       double* E_out, double* dEdg_out) {
+  k_energy_final_body(native_blk(), d, part, dn, dsq, dphi, hdr, dEdg_ws, E_out, dEdg_out);
+}
 }  // namespace
 
 cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layout& L,
@@ -522,17 +552,21 @@ cudaError_t launch_energy(const Dims& d, const int32_t* pm, char* ws, const Layo
 
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_backward(Dims d, const double* __restrict__ Ebar, const double* __restrict__ G,
+__device__ __forceinline__ void k_backward_body(const Blk& B_, Dims d, const double* __restrict__ Ebar, const double* __restrict__ G,
                            const double* __restrict__ dEdg, double* dE_dC, double* dE_dgamma) {
   const double eb = *Ebar;
   const long long tot = (long long)d.N * d.N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = B_.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)B_.gx * blockDim.x) {
     const int p = (int)(i % d.N);
     const long long mu = i / d.N;
     if (dE_dC) dE_dC[i] = (p < d.A) ? 4.0 * eb * G[mu * d.A + p] : 0.0;
     if (dE_dgamma && i < d.ng) dE_dgamma[i] = eb * dEdg[i];
   }
+}
+__global__ void k_backward(Dims d, const double* __restrict__ Ebar, const double* __restrict__ G,
+                           const double* __restrict__ dEdg, double* dE_dC, double* dE_dgamma) {
+  k_backward_body(native_blk(), d, Ebar, G, dEdg, dE_dC, dE_dgamma);
 }
 }  // namespace
 

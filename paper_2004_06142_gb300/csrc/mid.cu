@@ -27,11 +27,11 @@ __device__ __forceinline__ float pow2f_m(int e) {
 // every slice of the group (Acoef is symmetric, so its column p is read, coalesced across
 // threads).
 constexpr int kDwSlices = 16;
-__global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int np, int A,
+__device__ __forceinline__ void k_diag_w_body(const Blk& B_, const float* __restrict__ D, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
                                                 float* W) {
   __shared__ float dv[kDwSlices][256];  // A <= 256
-  const int P0 = blockIdx.x * kDwSlices;
+  const int P0 = B_.x * kDwSlices;
   const int nP = min(kDwSlices, np - P0);
   for (int i = threadIdx.x; i < kDwSlices * A; i += blockDim.x) {
     const int sl = i / A, r = i - sl * A;
@@ -60,14 +60,19 @@ __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int
       if (sl < nP) W[(size_t)(P0 + sl) * A + p] = w[sl];
   }
 }
+__global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int np, int A,
+                                                int Ap, const float* __restrict__ AcF,
+                                                float* W) {
+  k_diag_w_body(native_blk(), D, np, A, Ap, AcF, W);
+}
 
 // Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread.
-__global__ void __launch_bounds__(256) k_kpart(const float* __restrict__ b,
+__device__ __forceinline__ void k_kpart_body(const Blk& B_, const float* __restrict__ b,
                                                const float* __restrict__ D, int np, int A,
                                                int Ap, int splits, double* Ksp, double* Jsp) {
   const int n4 = A * (Ap / 4);
-  const int i4 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int sp = blockIdx.y;
+  const int i4 = B_.x * blockDim.x + threadIdx.x;
+  const int sp = B_.y;
   if (i4 >= n4) return;
   const int q = i4 / (Ap / 4), p0 = (i4 % (Ap / 4)) * 4;
   const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
@@ -105,9 +110,14 @@ __global__ void __launch_bounds__(256) k_kpart(const float* __restrict__ b,
       Jsp[o + j] = sj[j];
     }
 }
+__global__ void __launch_bounds__(256) k_kpart(const float* __restrict__ b,
+                                               const float* __restrict__ D, int np, int A,
+                                               int Ap, int splits, double* Ksp, double* Jsp) {
+  k_kpart_body(native_blk(), b, D, np, A, Ap, splits, Ksp, Jsp);
+}
 
 // K += sum_sp Ksp, J += sum_sp Jsp (entries of blocks x), then the Y row exponents (blocks y).
-__global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
+__device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __restrict__ Ksp,
                                                const double* __restrict__ Jsp,
                                                const float* __restrict__ D,
                                                const float* __restrict__ W,
@@ -115,8 +125,8 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
                                                int Ap, int splits, double* K, double* J,
                                                int* eY) {
   const int AA = A * A;
-  if (blockIdx.y == 0) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < AA; i += gridDim.x * blockDim.x) {
+  if (B_.y == 0) {
+    for (int i = B_.x * blockDim.x + threadIdx.x; i < AA; i += B_.gx * blockDim.x) {
       double k = 0.0, j = 0.0;
       int sp = 0;
       for (; sp + 8 <= splits; sp += 8) {  // eight splits in flight, summed in order
@@ -141,11 +151,11 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
     }
     return;
   }
-  // blockIdx.y = 1: one warp per (split, row p), rows p >= A get exponent 0
+  // B_.y = 1: one warp per (split, row p), rows p >= A get exponent 0
   const int lane = threadIdx.x % 32;
   const int nrow = splits * Ap;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) / 32; t < nrow;
-       t += gridDim.x * blockDim.x / 32) {
+  for (int t = (B_.x * blockDim.x + threadIdx.x) / 32; t < nrow;
+       t += B_.gx * blockDim.x / 32) {
     const int sp = t / Ap, p = t % Ap;
     double ss = 0.0;
     if (p < A) {
@@ -168,19 +178,28 @@ __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
     if (lane == 0) eY[t] = intfrac_exponent(sqrt(fmax(ss, 0.0)) * (1.0 + 1e-6), Kc);
   }
 }
+__global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,
+                                               const double* __restrict__ Jsp,
+                                               const float* __restrict__ D,
+                                               const float* __restrict__ W,
+                                               const float* __restrict__ BcF, int np, int A,
+                                               int Ap, int splits, double* K, double* J,
+                                               int* eY) {
+  k_jk_eY_body(native_blk(), Ksp, Jsp, D, W, BcF, np, A, Ap, splits, K, J, eY);
+}
 
 // Y^P_rc = Bcoef_rc b^P_rc + delta_rc w^P_r -> integer + fraction planes with row exponent
 // eY[spOf[P]][r]: a CTA per slice at a time, thread (c4, y) handles four consecutive entries
 // of rows r = y, y + 8, ... (blockDim = (Ap / 4, 8)).
-__global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__ W,
+__device__ __forceinline__ void k_y_quant_body(const Blk& B_, const float* __restrict__ b, const float* __restrict__ W,
                           const float* __restrict__ BcF, int np, int A, int Ap,
                           const int* __restrict__ spOf, const int* __restrict__ eY,
                           __half* __restrict__ H, __half* __restrict__ F, DevHeader* hdr) {
-  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+  if (B_.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
     hdr->e3 = 0;  // G partials are in true units
   const int r4 = Ap / 4, c4 = threadIdx.x, c0 = 4 * c4;
   const float4* Bc4 = (const float4*)BcF;
-  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+  for (int P = B_.x; P < np; P += B_.gx) {
     const float4* b4 = (const float4*)b + (size_t)P * Ap * r4;
     const int* eYs = eY + (size_t)spOf[P] * Ap;
     constexpr int kRows = 4;  // rows of a thread whose loads are in flight together
@@ -211,6 +230,12 @@ __global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__
       }
     }
   }
+}
+__global__ void k_y_quant(const float* __restrict__ b, const float* __restrict__ W,
+                          const float* __restrict__ BcF, int np, int A, int Ap,
+                          const int* __restrict__ spOf, const int* __restrict__ eY,
+                          __half* __restrict__ H, __half* __restrict__ F, DevHeader* hdr) {
+  k_y_quant_body(native_blk(), b, W, BcF, np, A, Ap, spOf, eY, H, F, hdr);
 }
 
 int sm_count() {

@@ -333,6 +333,8 @@ struct TcArgs {
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
   int nbuf;        // TMEM accumulator sets: 1, 2, or 3 (three regions in rotation, below)
+  int region;      // nbuf 3: columns of each region (at least Nn)
+  int nb_stage;    // B rows a shared-memory stage holds (at least this CTA's share of Nn)
   int buf_stride;  // TMEM columns per accumulator set
   int tmem_cols;
   // per-row / per-column exponents (kIntFrac): value = 2^(eA[row] + eB[col]) * acc, with
@@ -375,6 +377,11 @@ struct TcArgs {
   int* abort_flag;
 };
 
+// The four operand maps of one contraction (integer and fraction planes of A and B).
+struct TcMaps {
+  CUtensorMap ah, al, bh, bl;
+};
+
 // Round-robin (circle method) schedule over the T row tiles of a slice: in round r row
 // tile i works on tile column rr_partner(i, r, T), an involution, so both row tiles that
 // share a stored tile read it in the same round; every tile column once in T rounds (the
@@ -401,20 +408,24 @@ __device__ __forceinline__ float pow2f(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
+// The kernel body over a table of problems: problem i has the arguments targs[i] and the
+// tensor maps tmaps[i] and owns the work units [ustart[i], ustart[i + 1]) of the grid's
+// unit sequence (ustart null: one problem).  The kernel-wide settings (stages, TMEM layout,
+// the rows of B a stage holds, the status and abort words) are those of targs[0].
 template <int BK, int NUM, int PAIR>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-              const TcArgs args) {
+__device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
+                                        const TcMaps* __restrict__ tmaps,
+                                        const int* __restrict__ ustart, int ninst) {
+  const TcArgs& a0 = targs[0];
   constexpr int SWZ = BK * 2;  // bytes per tile row
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = args.stages;
+  const int S = a0.stages;
   // PAIR: the two CTAs of a cluster compute one M = 256 tile with cta_group::2 MMAs issued by
   // the even CTA: each CTA stages its own 128 rows of A and half of the B rows (the output
   // columns), and holds its 128 rows of the accumulator in its own TMEM
-  const int nb_rows = PAIR ? args.Nn / 2 : args.Nn;  // B rows staged by this CTA
+  const int nb_rows = a0.nb_stage;  // B rows a stage holds (this CTA's share, widest problem)
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)nb_rows * BK * 2;
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
@@ -424,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             kTrel = 2 * S + 5;
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 7);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int* status = args.status;
-  int* abort_flag = args.abort_flag;
-  const int nbuf = args.nbuf;
+  int* status = a0.status;
+  int* abort_flag = a0.abort_flag;
+  const int nbuf = a0.nbuf;
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
   const int cl = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;   // this CTA's work stream
   const int ncl = PAIR ? (int)ncluster_x() : (int)gridDim.x;
@@ -450,36 +461,54 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 2) tmem_alloc<PAIR>(smem_u32(tmem_slot), args.tmem_cols);
+  if (warp == 2) tmem_alloc<PAIR>(smem_u32(tmem_slot), a0.tmem_cols);
   tc_fence_before();
   __syncthreads();
   if (PAIR) cluster_sync_all();  // the peer's barriers are initialised before any remote use
   tc_fence_after();
   const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
 
-  // work units: (z, row tile, split); PAIR: a unit is the M = 256 tile of the cluster, rows
-  // of slice pair (2 zp, 2 zp + 1) in the symmetric mode, row tiles (2 mu, 2 mu + 1) otherwise
-  const bool sym = BK == 64 && args.sym;
-  const int z_units = (PAIR && sym) ? (args.z_count + 1) / 2 : args.z_count;
-  const int m_units = (PAIR && !sym) ? (args.m_tiles + 1) / 2 : args.m_tiles;
-  const int units = z_units * m_units * args.splits;
+  // work units: (z, row tile, split) of each problem; PAIR: a unit is the M = 256 tile of the
+  // cluster, rows of slice pair (2 zp, 2 zp + 1) in the symmetric mode, row tiles
+  // (2 mu, 2 mu + 1) otherwise
+  const bool sym = BK == 64 && a0.sym;
+  auto z_units = [&](const TcArgs& A) { return (PAIR && sym) ? (A.z_count + 1) / 2 : A.z_count; };
+  auto m_units = [&](const TcArgs& A) { return (PAIR && !sym) ? (A.m_tiles + 1) / 2 : A.m_tiles; };
+  const int units = ustart ? ustart[ninst] : z_units(a0) * m_units(a0) * a0.splits;
+  // the problem of unit u and the unit's index lu among that problem's units
+  auto locate = [&](int u, int& lu) {
+    if (!ustart) {
+      lu = u;
+      return 0;
+    }
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ustart[mid] <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    lu = u - ustart[lo];
+    return lo;
+  };
   // consecutive units share the split (and so the B tiles of one K range, which then come
   // from L2 for all M tiles of that split)
-  auto decode = [&](int u, int& z, int& mt, int& sp) {
-    const int zu = u / (m_units * args.splits);
-    const int r = u % (m_units * args.splits);
-    sp = r / m_units;
-    const int mu = r % m_units;
+  auto decode = [&](const TcArgs& A, int u, int& z, int& mt, int& sp) {
+    const int mu_n = m_units(A);
+    const int zu = u / (mu_n * A.splits);
+    const int r = u % (mu_n * A.splits);
+    sp = r / mu_n;
+    const int mu = r % mu_n;
     z = (PAIR && sym) ? 2 * zu + (int)rank : zu;
     mt = (PAIR && !sym) ? 2 * mu + (int)rank : mu;
   };
-  const int T = args.st.T;
-  auto unit_iters = [&](int sp) {
-    if (sym) return 2 * (T - 1) + args.st.Rlast / 64;
-    const int kb0 = (int)((long long)args.nkb * sp / args.splits);
-    const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
-    return (kb1 - kb0) * args.kt_per_kb;
+  auto unit_iters = [&](const TcArgs& A, int sp) {
+    if (sym) return 2 * (A.st.T - 1) + A.st.Rlast / 64;
+    const int kb0 = (int)((long long)A.nkb * sp / A.splits);
+    const int kb1 = (int)((long long)A.nkb * (sp + 1) / A.splits);
+    return (kb1 - kb0) * A.kt_per_kb;
   };
+  // bytes of B a stage receives for a problem (its own rows)
+  auto b_bytes_of = [&](const TcArgs& A) { return (uint32_t)(PAIR ? A.Nn / 2 : A.Nn) * BK * 2; };
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ TMA producer (both CTAs of a pair)
@@ -489,8 +518,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long issued = 0;  // stages filled so far
     const int b_row0 = (int)rank * nb_rows;
     for (int u = cl; u < units && ok; u += ncl) {
+      int lu;
+      const int inst = locate(u, lu);
+      const TcArgs& args = targs[inst];
+      const TcMaps& maps = tmaps[inst];
+      const uint32_t bu = b_bytes_of(args);
       int z, mt, sp;
-      decode(u, z, mt, sp);
+      decode(args, lu, z, mt, sp);
       if (sym) {
         const SymTiles st = args.st;
         const bool a_valid = z < args.z_count;  // PAIR: the odd slice of an odd count is absent
@@ -507,16 +541,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t fb = bar(kFull + stage);
             const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
             if (!a_valid) {
-              mbar_expect_tx(fb, 2 * b_bytes);
+              mbar_expect_tx(fb, 2 * bu);
             } else if (j <= i) {  // stored tile (i, j), chunk c: Ri rows of 128 bytes, K-major
               const uint32_t ab = (uint32_t)Ri * 128u;
-              mbar_expect_tx(fb, 2 * ab + 2 * b_bytes);
+              mbar_expect_tx(fb, 2 * ab + 2 * bu);
               const size_t off = zoff + sym_tile_off(st, i, j) + (size_t)c * Ri * 64;
               bulk_load_once(base, args.a_tiled_h + off, ab, fb);
               bulk_load_once(base + a_bytes, args.a_tiled_f + off, ab, fb);
             } else {  // stored tile (j, i), rows 64c..64c+63 of both its chunks: MN-major
               const int Rj = sym_R(st, j);
-              mbar_expect_tx(fb, 2 * a_bytes + 2 * b_bytes);
+              mbar_expect_tx(fb, 2 * a_bytes + 2 * bu);
 #pragma unroll
               for (int m = 0; m < 2; ++m) {
                 const size_t off =
@@ -525,8 +559,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bulk_load_once(base + a_bytes + m * 8192, args.a_tiled_f + off, 8192, fb);
               }
             }
-            tma_load_3d(base + 2 * a_bytes, &mBh, fb, 128 * j + 64 * c, b_row0, 0);
-            tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, 128 * j + 64 * c, b_row0, 0);
+            tma_load_3d(base + 2 * a_bytes, &maps.bh, fb, 128 * j + 64 * c, b_row0, 0);
+            tma_load_3d(base + 2 * a_bytes + b_bytes, &maps.bl, fb, 128 * j + 64 * c, b_row0, 0);
             ++issued;
             if (++stage == S) { stage = 0; phase ^= 1u; }
           }
@@ -542,21 +576,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(bar(kEmpty + stage), phase ^ 1u, status, abort_flag)) { ok = false; break; }
           const uint32_t fb = bar(kFull + stage);
           const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
-          mbar_expect_tx(fb, stage_bytes);
+          mbar_expect_tx(fb, 2 * a_bytes + 2 * bu);
           if (args.a_il8) {
-            tma_load_4d(base, &mAh, fb, 0, mt * BM / 8, kt * BK / 8, az);
-            tma_load_4d(base + a_bytes, &mAl, fb, 0, mt * BM / 8, kt * BK / 8, az);
+            tma_load_4d(base, &maps.ah, fb, 0, mt * BM / 8, kt * BK / 8, az);
+            tma_load_4d(base + a_bytes, &maps.al, fb, 0, mt * BM / 8, kt * BK / 8, az);
           } else if (BK == 64 && args.a_mn) {
-            tma_load_3d(base, &mAh, fb, mt * BM, kt * BK, az);
-            tma_load_3d(base + a_bytes / 2, &mAh, fb, mt * BM + 64, kt * BK, az);
-            tma_load_3d(base + a_bytes, &mAl, fb, mt * BM, kt * BK, az);
-            tma_load_3d(base + a_bytes + a_bytes / 2, &mAl, fb, mt * BM + 64, kt * BK, az);
+            tma_load_3d(base, &maps.ah, fb, mt * BM, kt * BK, az);
+            tma_load_3d(base + a_bytes / 2, &maps.ah, fb, mt * BM + 64, kt * BK, az);
+            tma_load_3d(base + a_bytes, &maps.al, fb, mt * BM, kt * BK, az);
+            tma_load_3d(base + a_bytes + a_bytes / 2, &maps.al, fb, mt * BM + 64, kt * BK, az);
           } else {
-            tma_load_3d(base, &mAh, fb, kt * BK, mt * BM, az);
-            tma_load_3d(base + a_bytes, &mAl, fb, kt * BK, mt * BM, az);
+            tma_load_3d(base, &maps.ah, fb, kt * BK, mt * BM, az);
+            tma_load_3d(base + a_bytes, &maps.al, fb, kt * BK, mt * BM, az);
           }
-          tma_load_3d(base + 2 * a_bytes, &mBh, fb, kt * BK, b_row0, bz);
-          tma_load_3d(base + 2 * a_bytes + b_bytes, &mBl, fb, kt * BK, b_row0, bz);
+          tma_load_3d(base + 2 * a_bytes, &maps.bh, fb, kt * BK, b_row0, bz);
+          tma_load_3d(base + 2 * a_bytes + b_bytes, &maps.bl, fb, kt * BK, b_row0, bz);
           ++issued;
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
@@ -577,9 +611,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     bool ok = true;
     for (int u = cl; u < units && ok; u += ncl) {
+      int lu;
+      const TcArgs& args = targs[locate(u, lu)];
       int z, mt, sp;
-      decode(u, z, mt, sp);
-      const int iters = unit_iters(sp);
+      decode(args, lu, z, mt, sp);
+      const int iters = unit_iters(args, sp);
       for (int it = 0; it < iters; ++it) {
         if (!mbar_wait(bar(kFull + stage), phase, status, abort_flag)) { ok = false; break; }
         mbar_arrive_remote(mapa_shared(bar(kFull + stage), 0));
@@ -588,7 +624,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ------------------------------------------------ MMA issuer (even CTA of a pair)
-    const uint32_t idesc = idesc_f16(PAIR ? 2 * BM : BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
     // MN-major A (BK = 64): the two 64-wide M chunks 8 KB apart (leading byte offset),
     // 8-row K groups 1 KB apart (stride byte offset)
     const uint32_t mn_lbo = 8192u, mn_sbo = 1024u;
@@ -597,8 +632,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     int local = 0;
     for (int u = cl; u < units && ok; u += ncl, ++local) {
+      int lu;
+      const TcArgs& args = targs[locate(u, lu)];
+      const uint32_t idesc =
+          idesc_f16(PAIR ? 2 * BM : BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
+      const int T = args.st.T;
       int z, mt, sp;
-      decode(u, z, mt, sp);
+      decode(args, lu, z, mt, sp);
       // the accumulator pair (d0: h*h, d1: the cross products) of this unit
       uint32_t d0, d1;
       int tf;
@@ -611,19 +651,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(bar(kTrel + (local & 1)), (uint32_t)((local / 2) & 1) ^ 1u, status,
                        abort_flag))
           break;
-        d1 = tmem_base + (uint32_t)args.Nn;
-        d0 = tmem_base + (uint32_t)((local & 1) ? 2 * args.Nn : 0);
+        d1 = tmem_base + (uint32_t)a0.region;
+        d0 = tmem_base + (uint32_t)((local & 1) ? 2 * a0.region : 0);
       } else {
         const int acc = local % nbuf;
         const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
         if (!mbar_wait(bar(kTempty + acc), acc_phase ^ 1u, status, abort_flag)) break;
         tf = acc;
-        d0 = tmem_base + (uint32_t)(acc * args.buf_stride);
+        d0 = tmem_base + (uint32_t)(acc * a0.buf_stride);
         d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
       }
       tc_fence_after();
       // symmetric mode: the K steps in the producer's order, K-major or transposed
-      const int iters = unit_iters(sp);
+      const int iters = unit_iters(args, sp);
       int rr = 0, cc = 0, jj = 0, nch = 0;
       if (sym) {
         jj = rr_partner(mt, 0, T);
@@ -686,11 +726,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // index mod 4) and the column chunks of group ew / 4
     const int ew = warp - 4;
     const int q = ew & 3, eg = ew >> 2;
-    // this group's 16-column chunks [ch0, ch1), and this warp's table of column factors
-    const int nch = args.Nn / 16, hch = (nch + kEpiGroups - 1) / kEpiGroups;
-    const int ch0 = eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
+    // this warp's table of column factors
     float2* ctab = (float2*)(bars + 2 * S + 8) + ew * kTabCols;
-    const int glob = args.glob_exp ? *args.glob_exp : 0;
     // a release of TMEM: on the even CTA's barrier (remotely from the odd CTA of a pair)
     auto release = [&](int i) {
       tc_fence_before();
@@ -699,19 +736,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     int local = 0;
     for (int u = cl; u < units; u += ncl, ++local) {
+      int lu;
+      const TcArgs& args = targs[locate(u, lu)];
+      const int glob = args.glob_exp ? *args.glob_exp : 0;
+      // this group's 16-column chunks [ch0, ch1)
+      const int nch = args.Nn / 16, hch = (nch + kEpiGroups - 1) / kEpiGroups;
+      const int ch0 = eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
       int z, mt, sp;
-      decode(u, z, mt, sp);
+      decode(args, lu, z, mt, sp);
       int tf;
       uint32_t tf_phase, c0off, c1off;
       if (nbuf == 3) {
         tf = 0;
         tf_phase = (uint32_t)(local & 1);
-        c0off = (uint32_t)((local & 1) ? 2 * args.Nn : 0);
-        c1off = (uint32_t)args.Nn;
+        c0off = (uint32_t)((local & 1) ? 2 * a0.region : 0);
+        c1off = (uint32_t)a0.region;
       } else {
         tf = local % nbuf;
         tf_phase = (uint32_t)((local / nbuf) & 1);
-        c0off = (uint32_t)(tf * args.buf_stride);
+        c0off = (uint32_t)(tf * a0.buf_stride);
         c1off = c0off + (uint32_t)args.Nn;
       }
       // everything that needs no accumulator (exponents, the factor table) is looked up
@@ -892,8 +935,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (PAIR) cluster_sync_all();  // no CTA frees its TMEM while the pair's MMAs may write it
   if (warp == 2) {
     tc_fence_after();
-    tmem_dealloc<PAIR>(tmem_base, args.tmem_cols);
+    tmem_dealloc<PAIR>(tmem_base, a0.tmem_cols);
   }
+}
+
+template <int BK, int NUM, int PAIR>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
+  tc_body<BK, NUM, PAIR>(&args, &maps, nullptr, 1);
+}
+
+// Grouped launch: the work units of every problem of a batch in one grid.
+template <int BK, int NUM>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm_group(const TcArgs* targs, const TcMaps* tmaps, const int* ustart, int ninst) {
+  tc_body<BK, NUM, 0>(targs, tmaps, ustart, ninst);
 }
 
 // ------------------------------------------------------------------ host: tile tuning
@@ -1051,6 +1107,8 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
     a.nbuf = 1;
     a.buf_stride = 0;
   }
+  a.region = a.Nn;
+  a.nb_stage = PAIR ? a.Nn / 2 : a.Nn;
   size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 8) * 8 + kTabBytes;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM, PAIR>,
@@ -1076,12 +1134,12 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BK, NUM, PAIR>, ah, al, bh, bl, a);
+    e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BK, NUM, PAIR>, TcMaps{ah, al, bh, bl}, a);
     count_launch(1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  k_tc_gemm<BK, NUM, PAIR><<<work, kThreads, smem, s>>>(ah, al, bh, bl, a);
+  k_tc_gemm<BK, NUM, PAIR><<<work, kThreads, smem, s>>>(TcMaps{ah, al, bh, bl}, a);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -1287,16 +1345,16 @@ struct SplitJobs {
 // Column norms of job.S -> exponents of the integer + fraction split of S^T: e[c] for
 // c < nrows_out.  A CTA of 32 x 32 threads per 32 columns: thread (c, g) sums rows g,
 // g + 32, ... (coalesced across c), the 32 partial sums of a column are then added in order.
-__global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, DevHeader* hdr) {
-  const SplitJob& jb = jobs.j[blockIdx.y];
-  if ((int)blockIdx.x * 32 >= jb.nrows_out) return;  // uniform over the CTA
+__device__ __forceinline__ void k_colnorms_body(const Blk& B_, SplitJobs jobs, double invT, DevHeader* hdr) {
+  const SplitJob& jb = jobs.j[B_.y];
+  if ((int)B_.x * 32 >= jb.nrows_out) return;  // uniform over the CTA
   __shared__ double red[32][33];
   const double* __restrict__ S = jb.S;
   const int* __restrict__ eS = jb.eS;
   const long long ld = jb.ld;
   const int N = jb.N;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int c = blockIdx.x * 32 + tx;
+  const int c = B_.x * 32 + tx;
   double ss = 0.0;
   if (c < jb.ncols) {
     int mu = ty;
@@ -1327,14 +1385,17 @@ __global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, 
     if (jb.norm) jb.norm[c] = nr;
   }
 }
+__global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, DevHeader* hdr) {
+  k_colnorms_body(native_blk(), jobs, invT, hdr);
+}
 
 // The split itself, as rows c < nrows_out of Np halves (zero for c >= ncols or mu >= N):
 // element (c, mu) is 2^e[c] (h + f) of S[mu][c] (times 2^eS[mu] when eS is given), and the
 // residual planes when asked for.  32 x 32 tiles through shared memory, so that both the
 // reads and the writes are coalesced.
-__global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
-  const SplitJob& jb = jobs.j[blockIdx.z];
-  const int mu0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+__device__ __forceinline__ void k_split_T_body(const Blk& B_, SplitJobs jobs, int Np) {
+  const SplitJob& jb = jobs.j[B_.z];
+  const int mu0 = B_.x * 32, c0 = B_.y * 32;
   if (c0 >= jb.nrows_out) return;  // uniform over the CTA
   __shared__ double tile[32][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -1377,6 +1438,9 @@ __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
     }
   }
 }
+__global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
+  k_split_T_body(native_blk(), jobs, Np);
+}
 
 // All jobs' norms, then all splits: two launches.
 cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHeader* hdr,
@@ -1396,10 +1460,10 @@ cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHea
 // chunk of C_act in shared memory (fp32), thread (i, j0) forms entries (i, j0 + 16 k) with
 // the chunk's mu in order; k_gram_final: one CTA per row, the chunks summed in order.
 constexpr int kGramChunk = 32;
-__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ C, int N, int A,
+__device__ __forceinline__ void k_gram_part_body(const Blk& B_, const double* __restrict__ C, int N, int A,
                                                    float* part) {
   __shared__ float cs[kGramChunk][256];  // A <= 256
-  const int ch = blockIdx.x, i0 = blockIdx.y * 16;
+  const int ch = B_.x, i0 = B_.y * 16;
   const int mu0 = ch * kGramChunk, nmu = min(kGramChunk, N - mu0);
   for (int t = threadIdx.x; t < kGramChunk * A; t += blockDim.x) {
     const int m = t / A, j = t % A;
@@ -1426,10 +1490,14 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ C,
     if (j < A) out[j] = g[k];
   }
 }
+__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ C, int N, int A,
+                                                   float* part) {
+  k_gram_part_body(native_blk(), C, N, A, part);
+}
 
-__global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ part, int nch,
+__device__ __forceinline__ void k_gram_final_body(const Blk& B_, const float* __restrict__ part, int nch,
                                                     int A, DevHeader* hdr) {
-  const int i = blockIdx.x;
+  const int i = B_.x;
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   float rs = 0.f;
   for (int j = threadIdx.x; j < A; j += blockDim.x) {
@@ -1447,6 +1515,10 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
     atomic_max_nonneg((unsigned long long*)&hdr->sC2, (double)t * (1.0 + 1e-4));
   }
 }
+__global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ part, int nch,
+                                                    int A, DevHeader* hdr) {
+  k_gram_final_body(native_blk(), part, nch, A, hdr);
+}
 
 // The per-block exponents of the two X splits written by the half transform (blocks with
 // blockIdx.y = 0 and 1 respectively):
@@ -1454,12 +1526,12 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
 //    symmetric, so ||B^P||_2 <= ||B^P||_inf);
 //  * X rows (split, mu) for G: the row runs over the split's slices and q, and its squared
 //    norm sum_P ||B^P_mu C_act||^2 <= s_C^2 sum_P ||B^P_mu||^2 (s_C^2 the Gram bound).
-__global__ void k_x_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
+__device__ __forceinline__ void k_x_exponents_body(const Blk& B_, const double* __restrict__ L1max, const double* __restrict__ cnorm,
                               int Ap, double invT, int* eXt, const double* __restrict__ rn2,
                               const DevHeader* hdr, int np, int splits, int N, double invT2,
                               int* spOf, int* eX3) {
-  if (blockIdx.y == 0) {
-    for (int P = blockIdx.x; P < np; P += gridDim.x) {
+  if (B_.y == 0) {
+    for (int P = B_.x; P < np; P += B_.gx) {
       const double l = L1max[P];
       for (int q = threadIdx.x; q < Ap; q += blockDim.x)
         eXt[(size_t)P * Ap + q] = intfrac_exponent_inv(l * cnorm[q], invT);
@@ -1468,8 +1540,8 @@ __global__ void k_x_exponents(const double* __restrict__ L1max, const double* __
   }
   const double sC2 = hdr->sC2;
   const long long tot = (long long)splits * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = B_.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)B_.gx * blockDim.x) {
     const int sp = (int)(i / N), mu = (int)(i % N);
     const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
     double r2 = 0.0;
@@ -1487,6 +1559,12 @@ __global__ void k_x_exponents(const double* __restrict__ L1max, const double* __
     eX3[i] = intfrac_exponent_sq(sC2 * r2 * (1.0 + 1e-12), invT2);
   }
 }
+__global__ void k_x_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
+                              int Ap, double invT, int* eXt, const double* __restrict__ rn2,
+                              const DevHeader* hdr, int np, int splits, int N, double invT2,
+                              int* spOf, int* eX3) {
+  k_x_exponents_body(native_blk(), L1max, cnorm, Ap, invT, eXt, rn2, hdr, np, splits, N, invT2, spOf, eX3);
+}
 
 
 
@@ -1494,14 +1572,14 @@ __global__ void k_x_exponents(const double* __restrict__ L1max, const double* __
 // G[mu][p] += 2^e3 * sum_s Gpart[s][mu][p]: groups of eight partials summed in fp32 (the
 // FP64 pipe of this GPU is narrow), the groups in double, in order of s; four consecutive p
 // per thread.
-__global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
+__device__ __forceinline__ void k_reduce_G_body(const Blk& B_, const float* __restrict__ Gp, int S, int N, int A, int Ap,
                            const DevHeader* hdr, double* G) {
   const double sc = ldexp(1.0, hdr->e3);
   const int r4 = Ap / 4;
   const long long tot = (long long)N * r4;
   const float4* G4 = (const float4*)Gp;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = B_.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)B_.gx * blockDim.x) {
     const long long mu = i / r4;
     const int p0 = (int)(i % r4) * 4;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -1536,6 +1614,10 @@ __global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, in
     for (int j = 0; j < 4; ++j)
       if (p0 + j < A) g[j] += sc * sv[j];
   }
+}
+__global__ void k_reduce_G(const float* __restrict__ Gp, int S, int N, int A, int Ap,
+                           const DevHeader* hdr, double* G) {
+  k_reduce_G_body(native_blk(), Gp, S, N, A, Ap, hdr, G);
 }
 
 }  // namespace
@@ -1613,17 +1695,21 @@ cudaError_t launch_reduce_G(const Dims& d, char* ws, const Layout& L, cudaStream
 
 // out[r * ld + c] = sum_s part[s][r][c] (r < M, c < ncols): the four K blocks of a
 // residual-extended product added in double in block order.
-__global__ void k_sum_blocks(const float* __restrict__ part, int M, int ncols, int Ap,
+__device__ __forceinline__ void k_sum_blocks_body(const Blk& B_, const float* __restrict__ part, int M, int ncols, int Ap,
                              double* out, long long ld) {
   const long long tot = (long long)M * ncols;
   const size_t ps = (size_t)M * Ap;
-  for (long long i = threadIdx.x + (long long)blockIdx.x * blockDim.x; i < tot;
-       i += (long long)blockDim.x * gridDim.x) {
+  for (long long i = threadIdx.x + (long long)B_.x * blockDim.x; i < tot;
+       i += (long long)blockDim.x * B_.gx) {
     const int r = (int)(i / ncols), c = (int)(i - (long long)r * ncols);
     const size_t o = (size_t)r * Ap + c;
     out[(size_t)r * ld + c] = (((double)part[o] + (double)part[ps + o]) +
                                (double)part[2 * ps + o]) + (double)part[3 * ps + o];
   }
+}
+__global__ void k_sum_blocks(const float* __restrict__ part, int M, int ncols, int Ap,
+                             double* out, long long ld) {
+  k_sum_blocks_body(native_blk(), part, M, ncols, Ap, out, ld);
 }
 
 // out = U V^T (M x ncols, row stride ld) from the residual planes of U (M rows, in
