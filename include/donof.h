@@ -199,13 +199,24 @@ int donof_orbital_update(int32_t nbf, const double* lam, const double* Fdiag, co
 
 /* Batched builds: ninst independent instances (e.g. one molecule at many geometries), each
  * with its own problem description probs[i] and device pointers inst[i].  The workspace
- * (donof_batched_workspace_size bytes) holds one slice per instance; prepare every B once
- * with donof_prepare_B_batched.  Instances run concurrently on library-owned streams that
- * fork from and join back to `stream`.
+ * (donof_batched_workspace_size bytes) holds a head (the batch's status word at its start,
+ * then the tables below) and one slice per instance; prepare every B once with
+ * donof_prepare_B_batched.
+ * When every instance is DONOF_MIXED with all its auxiliary slices in one block (no
+ * x_budget_bytes split), each step of the build runs as one launch for all instances (26
+ * launches per batched build and adjoint, whatever ninst): the tables that map a launch's
+ * blocks and tensor-core work units to instances are built on the host and copied into the
+ * workspace head when the arguments change (a synchronisation of `stream`).  Otherwise
+ * instances run their single-instance sequences concurrently on library-owned streams that
+ * fork from and join back to `stream`.  Both give the same results bit for bit.
  *   DONOF_BATCH_BACKWARD: also write inst[i].dE_dC = dE/dC (upstream gradient 1).
  *   DONOF_BATCH_GRAPH: capture the whole batch into a CUDA graph on the first call and
  *     replay it (one graph launch) on every later call with identical arguments (same
- *     problems, pointers, workspace and flags); tracing is not recorded inside graphs. */
+ *     problems, pointers, workspace and flags); tracing is not recorded inside graphs.
+ *   DONOF_BATCH_STREAMS: use the per-instance streams even where the grouped launches apply.
+ * Device-side checks of an instance go to its own status word (donof_read_status on its
+ * slice); wait limits of the grouped tensor-core launches to the batch's (donof_read_status
+ * on the workspace). */
 typedef struct {
   const double* h;
   const double* B;
@@ -217,7 +228,7 @@ typedef struct {
   double* dE_dgamma;  /* [npair*ncwo] or NULL */
   double* dE_dC;      /* [nbf*nbf] or NULL (DONOF_BATCH_BACKWARD) */
 } donof_instance;
-enum { DONOF_BATCH_BACKWARD = 1, DONOF_BATCH_GRAPH = 2 };
+enum { DONOF_BATCH_BACKWARD = 1, DONOF_BATCH_GRAPH = 2, DONOF_BATCH_STREAMS = 4 };
 int donof_batched_workspace_size(int32_t ninst, const donof_problem* probs, size_t* bytes);
 int donof_prepare_B_batched(int32_t ninst, const donof_problem* probs, const donof_instance* inst,
                             void* workspace, size_t workspace_bytes, void* stream);

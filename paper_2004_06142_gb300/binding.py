@@ -33,7 +33,7 @@ class DonofError(RuntimeError):
         self.code = code
 
 
-BATCH_BACKWARD, BATCH_GRAPH = 1, 2
+BATCH_BACKWARD, BATCH_GRAPH, BATCH_STREAMS = 1, 2, 4
 ERR_WORKSPACE = -4
 
 
@@ -462,6 +462,10 @@ class Batch:
         _check(lib().donof_energy_lagrangian_batched(self.n, self.probs, self.inst, _ptr(self.ws),
                                                      self.ws.numel(), flags, _stream(stream)),
                "donof_energy_lagrangian_batched")
+
+    def status(self) -> int:
+        """The batch's status word (wait limits of the grouped launches), then cleared."""
+        return donof_read_status(self.ws)
 
 
 class DonofEnergy(torch.autograd.Function):

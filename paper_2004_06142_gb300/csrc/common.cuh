@@ -136,6 +136,34 @@ __device__ __forceinline__ int group_locate(const GroupLaunch& g, Blk& b) {
   return lo;
 }
 
+// The grouped launches of one batched build, in order (batch.cu builds their grids).
+enum GroupKind {
+  GK_ZERO, GK_OCC, GK_COEF, GK_CNORM_C, GK_SPLIT_C, GK_TC_HC, GK_SUM_HC, GK_GRAM_PART,
+  GK_GRAM_FINAL, GK_HDIAG, GK_XEXP, GK_TC_HALF, GK_TC_B, GK_DIAGW, GK_KPART, GK_JKEY,
+  GK_YQUANT, GK_TC_G, GK_REDUCEG, GK_EROWS, GK_EFINAL, GK_CNORM_L, GK_SPLIT_L, GK_TC_LAM,
+  GK_SUM_L, GK_BWD, GK_COUNT
+};
+// Host launchers of the grouped kernels (blocks: the flat grid; threads, smem per block).
+cudaError_t launch_fp64_group(int kind, const GroupLaunch& g, int blocks, int threads,
+                              size_t smem, cudaStream_t s);
+cudaError_t launch_mid_group(int kind, const GroupLaunch& g, int blocks, dim3 threads,
+                             cudaStream_t s);
+cudaError_t launch_tc_small_group(int kind, const GroupLaunch& g, int blocks, int threads,
+                                  cudaStream_t s);
+// Grouped tensor-core contractions (kind GK_TC_*; tc.cu): their argument and tensor-map
+// records are opaque here, byte records of tc_args_bytes() and tc_maps_bytes() each (maps
+// 64-byte aligned).  Setup fills instance records on the host and counts its work units;
+// finish writes the kernel-wide settings into all records and returns the launch's shared
+// memory; the launch reads the records from device memory.
+bool tc_group_setup(int kind, const Dims& d, char* ws, const Layout& L, void* a_rec,
+                    void* m_rec, int& units);
+size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag);
+cudaError_t launch_tc_group(int kind, const void* args_dev, const void* maps_dev,
+                            const int* ustart, int ninst, int units, size_t smem,
+                            cudaStream_t s);
+size_t tc_args_bytes();
+size_t tc_maps_bytes();
+
 // Tracing (api.cu): no-ops unless donof_profile_enable(1) was called.
 void prof_begin(int phase, cudaStream_t s);
 void prof_end(int phase, cudaStream_t s);

@@ -579,3 +579,106 @@ cudaError_t launch_backward(const Dims& d, const double* Ebar, const char* ws, c
 }
 
 }  // namespace donof
+
+// ---------------------------------------------------------------------------
+// Grouped launches of the kernels above (one launch for every instance of a batch; the
+// per-instance grids are those of the launchers above, laid out by the GroupLaunch).
+// ---------------------------------------------------------------------------
+namespace donof {
+namespace {
+__global__ void k_occupations_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  char* ws = I.ws;
+  const Layout& L = I.L;
+  k_occupations_body<true>(b, I.d, I.gamma, I.pm, (DevHeader*)(ws + L.header),
+                           (double*)(ws + L.n), (double*)(ws + L.sqn), (double*)(ws + L.phi),
+                           (double*)(ws + L.dn), (double*)(ws + L.dsq), (double*)(ws + L.dphi));
+}
+__global__ void k_coefficients_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  char* ws = I.ws;
+  const Layout& L = I.L;
+  k_coefficients_body(b, I.d, I.pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn),
+                      (const double*)(ws + L.phi), (double*)(ws + L.Acoef),
+                      (double*)(ws + L.Bcoef), (float*)(ws + L.AcF), (float*)(ws + L.BcF));
+}
+__global__ void k_hdiag_ginit_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  char* ws = I.ws;
+  const Layout& L = I.L;
+  k_hdiag_ginit_body(b, I.d, I.C, (const double*)(ws + L.hC), (const double*)(ws + L.n),
+                     (double*)(ws + L.Hd), (double*)(ws + L.G), 1.0);
+}
+__global__ void k_energy_rows_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  char* ws = I.ws;
+  const Layout& L = I.L;
+  k_energy_rows_body(b, I.d, I.pm, (const double*)(ws + L.n), (const double*)(ws + L.sqn),
+                     (const double*)(ws + L.phi), (const double*)(ws + L.Acoef),
+                     (const double*)(ws + L.Bcoef), (const double*)(ws + L.Hd),
+                     (const double*)(ws + L.J), (const double*)(ws + L.K),
+                     (double*)(ws + L.Epart));
+}
+__global__ void __launch_bounds__(256) k_energy_final_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  char* ws = I.ws;
+  const Layout& L = I.L;
+  k_energy_final_body(b, I.d, (const double*)(ws + L.Epart), (const double*)(ws + L.dn),
+                      (const double*)(ws + L.dsq), (const double*)(ws + L.dphi),
+                      (DevHeader*)(ws + L.header), (double*)(ws + L.dEdg), I.E, I.dEdg);
+}
+__global__ void k_backward_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  k_backward_body(b, I.d, I.Ebar, (const double*)(I.ws + I.L.G),
+                  (const double*)(I.ws + I.L.dEdg), I.dEdC, nullptr);
+}
+// Zero what a build accumulates into or writes only in part: the abort flag, the occupation
+// Jacobians, the Gram bound, J, K and lambda.  blockIdx.y of the instance's grid: the range.
+__global__ void k_zero_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  const Layout& L = I.L;
+  DevHeader* hdr = (DevHeader*)(I.ws + L.header);
+  const size_t jac = (size_t)d.A * (d.ng > 0 ? d.ng : 0) * 8, aa = (size_t)d.A * d.A * 8;
+  void* p = nullptr;
+  size_t bytes = 0;
+  switch (b.y) {
+    case 0: p = &hdr->abort_flag; bytes = 4; break;
+    case 1: p = I.ws + L.dn; bytes = jac; break;
+    case 2: p = I.ws + L.dsq; bytes = jac; break;
+    case 3: p = I.ws + L.dphi; bytes = jac; break;
+    case 4: p = &hdr->sC2; bytes = 8; break;
+    case 5: p = I.ws + L.J; bytes = aa; break;
+    case 6: p = I.ws + L.K; bytes = aa; break;
+    case 7: p = I.lam; bytes = I.lam ? (size_t)d.N * d.N * 8 : 0; break;
+  }
+  uint32_t* w = (uint32_t*)p;
+  for (size_t i = (size_t)b.x * blockDim.x + threadIdx.x; i < bytes / 4;
+       i += (size_t)b.gx * blockDim.x)
+    w[i] = 0u;
+}
+}  // namespace
+
+cudaError_t launch_fp64_group(int kind, const GroupLaunch& g, int blocks, int threads,
+                              size_t smem, cudaStream_t s) {
+  switch (kind) {
+    case GK_ZERO: k_zero_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_OCC: k_occupations_group<<<blocks, threads, smem, s>>>(g); break;
+    case GK_COEF: k_coefficients_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_HDIAG: k_hdiag_ginit_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_EROWS: k_energy_rows_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_EFINAL: k_energy_final_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_BWD: k_backward_group<<<blocks, threads, 0, s>>>(g); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
+}  // namespace donof

@@ -249,7 +249,63 @@ int sm_count() {
   return n;
 }
 
+// Grouped launches (every instance of a batch, one block of np = naux slices each, the G
+// contraction's split count min(splits, np)).
+__device__ __forceinline__ int group_splits(const Dims& d) { return d.splits < d.Q ? d.splits : d.Q; }
+__global__ void __launch_bounds__(256) k_diag_w_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  char* ws = I.ws;
+  k_diag_w_body(b, (const float*)(ws + I.L.D), d.Q, d.A, d.Ap, (const float*)(ws + I.L.AcF),
+                (float*)(ws + I.L.W));
+}
+__global__ void __launch_bounds__(256) k_kpart_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  char* ws = I.ws;
+  k_kpart_body(b, (const float*)(ws + I.L.b32), (const float*)(ws + I.L.D), d.Q, d.A, d.Ap,
+               group_splits(d), (double*)(ws + I.L.Ksp), (double*)(ws + I.L.Jsp));
+}
+__global__ void __launch_bounds__(256) k_jk_eY_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  char* ws = I.ws;
+  k_jk_eY_body(b, (const double*)(ws + I.L.Ksp), (const double*)(ws + I.L.Jsp),
+               (const float*)(ws + I.L.D), (const float*)(ws + I.L.W),
+               (const float*)(ws + I.L.BcF), d.Q, d.A, d.Ap, group_splits(d),
+               (double*)(ws + I.L.K), (double*)(ws + I.L.J), (int*)(ws + I.L.eY));
+}
+// blockDim.x is that of the widest instance (Ap / 4); the threads past this instance's
+// Ap / 4 columns have nothing to do (the body has no block-wide barrier)
+__global__ void k_y_quant_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  if ((int)threadIdx.x >= d.Ap / 4) return;
+  char* ws = I.ws;
+  k_y_quant_body(b, (const float*)(ws + I.L.b32), (const float*)(ws + I.L.W),
+                 (const float*)(ws + I.L.BcF), d.Q, d.A, d.Ap, (const int*)(ws + I.L.spOf),
+                 (const int*)(ws + I.L.eY), (__half*)(ws + I.L.Yhi), (__half*)(ws + I.L.Ylo),
+                 (DevHeader*)(ws + I.L.header));
+}
+
 }  // namespace
+
+cudaError_t launch_mid_group(int kind, const GroupLaunch& g, int blocks, dim3 threads,
+                             cudaStream_t s) {
+  switch (kind) {
+    case GK_DIAGW: k_diag_w_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_KPART: k_kpart_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_JKEY: k_jk_eY_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_YQUANT: k_y_quant_group<<<blocks, threads, 0, s>>>(g); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const Layout& L,
                              cudaStream_t s) {

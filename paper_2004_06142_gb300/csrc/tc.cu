@@ -1442,6 +1442,43 @@ __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
   k_split_T_body(native_blk(), jobs, Np);
 }
 
+// The splits of a build's prep phase: C_act^T for b (and its residual planes, the V side of
+// h C_act), diag(2^s) C_act for the symmetric half transform (with_half_transform), and
+// h^T = h (the U side of h C_act).
+__host__ __device__ inline SplitJobs split_c_jobs(const Dims& d, const Layout& L, char* ws,
+                                                  const double* C, const double* h,
+                                                  bool with_half_transform) {
+  SplitJobs jobs{};
+  jobs.j[0] = SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
+                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo),
+                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+  jobs.j[1] = SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
+                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS),
+                       0, nullptr, nullptr};
+  jobs.j[2] = SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
+                       nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+  jobs.count = 3;
+  if (!with_half_transform) {
+    jobs.j[1] = jobs.j[2];
+    jobs.count = 2;
+  }
+  return jobs;
+}
+// The splits of lambda = C^T G: the residual planes of C^T (all N columns of C, U side) and of
+// G^T (V side), in the buffers of h C_act (free by then).
+__host__ __device__ inline SplitJobs lambda_jobs(const Dims& d, const Layout& L, char* ws,
+                                                 const double* C) {
+  const int N = d.N, A = d.A;
+  const double* G = (const double*)(ws + L.G);
+  SplitJobs jobs{};
+  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr, nullptr, nullptr,
+                       1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+  jobs.j[1] = SplitJob{G, A, N, A, d.Ap, nullptr, (int*)(ws + L.eG), nullptr, nullptr, nullptr,
+                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+  jobs.count = 2;
+  return jobs;
+}
+
 // All jobs' norms, then all splits: two launches.
 cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHeader* hdr,
                               cudaStream_t s) {
@@ -1653,23 +1690,8 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
 
 cudaError_t launch_split_C(const Dims& d, const double* C, const double* h, char* ws,
                            const Layout& L, bool with_half_transform, cudaStream_t s) {
-  // C_act^T for b (and its residual planes, the V side of h C_act), diag(2^s) C_act for the
-  // symmetric half transform, and h^T = h (the U side of h C_act)
-  SplitJobs jobs{};
-  jobs.j[0] = SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
-                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo),
-                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
-  jobs.j[1] = SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
-                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS),
-                       0, nullptr, nullptr};
-  jobs.j[2] = SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
-                       nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
-  jobs.count = 3;
-  if (!with_half_transform) {
-    jobs.j[1] = jobs.j[2];
-    jobs.count = 2;
-  }
-  return launch_split_jobs(jobs, d.Np, intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
+  return launch_split_jobs(split_c_jobs(d, L, ws, C, h, with_half_transform), d.Np,
+                           intfrac_inv_target(d.N), (DevHeader*)(ws + L.header), s);
 }
 
 cudaError_t launch_gram_bound(const Dims& d, const double* C, char* ws, const Layout& L,
@@ -1712,23 +1734,20 @@ __global__ void k_sum_blocks(const float* __restrict__ part, int M, int ncols, i
   k_sum_blocks_body(native_blk(), part, M, ncols, Ap, out, ld);
 }
 
-// out = U V^T (M x ncols, row stride ld) from the residual planes of U (M rows, in
-// hAH/hAF, exponents eU) and V (Ap rows, in cPH/cPF, exponents eV) over K = N: the four K
-// blocks as four splits of one launch, each with its own fp32 output (block 0 exact, the
-// others to the fp32 rounding of terms 2^-12 and smaller relative to the row norms), added
-// in double by k_sum_blocks.
-int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int ncols,
-                         double* out, long long ld, char* ws, const Layout& L, cudaStream_t s) {
+// Arguments and maps of U V^T (M x Ap, fp32 block outputs in hpart) from the residual planes
+// of U (M rows, in hAH/hAF, exponents eU) and V (Ap rows, in cPH/cPF, exponents eV) over
+// K = N: the four K blocks as four splits.
+bool ext_setup(const Dims& d, int M, const int* eU, const int* eV, char* ws, const Layout& L,
+               TcArgs& a, TcMaps& m) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
   const int N = d.N, Ap = d.Ap, Np = d.Np;
-  CUtensorMap ah, al, bh, bl;
   const size_t h2 = sizeof(__half);
-  if (!make_map(&ah, ws + L.hAH, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
-      !make_map(&al, ws + L.hAF, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
-      !make_map(&bh, ws + L.cPH, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
-      !make_map(&bl, ws + L.cPF, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
-    return DONOF_ERR_CUDA;
-  TcArgs a{};
+  if (!make_map(&m.ah, ws + L.hAH, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
+      !make_map(&m.al, ws + L.hAF, N, M, 4, Np * h2, (uint64_t)M * Np * h2, 64, BM) ||
+      !make_map(&m.bh, ws + L.cPH, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap) ||
+      !make_map(&m.bl, ws + L.cPF, N, Ap, 4, Np * h2, (uint64_t)Ap * Np * h2, 64, Ap))
+    return false;
+  a = TcArgs{};
   a.mode = 2; a.M = M; a.Nn = Ap;
   a.m_tiles = (M + BM - 1) / BM; a.z_count = 1;
   a.splits = 4;  // one K block per split
@@ -1738,10 +1757,22 @@ int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int
   a.out = (float*)(ws + L.hpart); a.out_ld = Ap; a.out_zstride = (long long)M * Ap;
   a.glob_exp = &hdr->zero_exp;
   a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-  if (launch_tc<64, kIntFrac, 0>(ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
+  return true;
+}
+
+// out = U V^T (M x ncols, row stride ld): the four K blocks as four splits of one launch,
+// each with its own fp32 output (block 0 exact, the others to the fp32 rounding of terms
+// 2^-12 and smaller relative to the row norms), added in double by k_sum_blocks.
+int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int ncols,
+                         double* out, long long ld, char* ws, const Layout& L, cudaStream_t s) {
+  TcArgs a;
+  TcMaps m;
+  if (!ext_setup(d, M, eU, eV, ws, L, a, m)) return DONOF_ERR_CUDA;
+  if (launch_tc<64, kIntFrac, 0>(m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
   const long long nb = ((long long)M * ncols + 255) / 256;
   k_sum_blocks<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
-      (const float*)(ws + L.hpart), M, ncols, Ap, out, ld);
+      (const float*)(ws + L.hpart), M, ncols, d.Ap, out, ld);
   count_launch(1);
   return cudaGetLastError() == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
 }
@@ -1759,27 +1790,116 @@ int run_hc_tc(const Dims& d, char* ws, const Layout& L, cudaStream_t s) {
 int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, double* lam,
                   cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  const int N = d.N, A = d.A, Ap = d.Ap;
-  const double* G = (const double*)(ws + L.G);
-  SplitJobs jobs{};
-  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr, nullptr, nullptr,
-                       1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
-  jobs.j[1] = SplitJob{G, A, N, A, Ap, nullptr, (int*)(ws + L.eG), nullptr, nullptr, nullptr,
-                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
-  jobs.count = 2;
-  if (launch_split_jobs(jobs, d.Np, intfrac_inv_target(N), hdr, s) != cudaSuccess)
+  const int N = d.N, A = d.A;
+  if (launch_split_jobs(lambda_jobs(d, L, ws, C), d.Np, intfrac_inv_target(N), hdr, s) !=
+      cudaSuccess)
     return DONOF_ERR_CUDA;
   return run_extended_product(d, N, (const int*)(ws + L.eCf), (const int*)(ws + L.eG), A, lam,
                               N, ws, L, s);
 }
 
+// Arguments and maps of (1) X = B C_act for slices p0 .. p0+np-1: A operand the symmetric
+// tile storage of the split B (bulk copies, BK = 64), B operand (diag(2^s) C_act)^T; unit =
+// (slice, row tile of 128 AO indices); outputs the X and X^T splits (mode 1).
+bool half_setup(const Dims& d, int p0, int np, const TuneCode& tv, char* ws, const Layout& L,
+                TcArgs& a, TcMaps& m) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, Ap = d.Ap, Np = d.Np;
+  const size_t h2 = sizeof(__half);
+  const SymTiles st = sym_tiles(N);
+  const int bk = 64;  // the stored tiles are laid out for it
+  const uint32_t brows = tv.pair ? Ap / 2 : Ap;  // B rows staged per CTA
+  if (!make_map(&m.bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
+      !make_map(&m.bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
+    return false;
+  m.ah = m.bh;  // unused: the A tiles come from the bulk copies
+  m.al = m.bl;
+  a = TcArgs{};
+  a.mode = 1; a.M = st.T * BM; a.Nn = Ap;
+  a.m_tiles = st.T; a.z_count = np; a.splits = 1;
+  a.kt_per_kb = 1; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.sym = 1; a.st = st;
+  // whole slices at once (the partner row tiles of a slice read their shared stored tile
+  // in the same round, so the second read can hit L2); a pair takes two slices' row tiles
+  const int work = tv.pair ? num_sms() / 2 : num_sms();
+  a.grid = (tv.full || work < st.T) ? work : work / st.T * st.T;
+  a.a_tiled_h = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
+  a.a_tiled_f = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
+  a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
+  a.eB = (const int*)(ws + L.eCs); a.eB_zstride = 0;
+  a.glob_exp = &hdr->zero_exp;  // not applied in mode 1
+  a.Nmu = N; a.Nrow = N; a.Ap = Ap; a.Np = Np;
+  a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
+  a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
+  a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
+  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+  return true;
+}
+
+// (2) b[P] = C_act^T X[P] for the np slices of the block: one GEMM over all of them, rows
+// (P, q) of X^T flattened into M, C_act^T rows as N; b[(P, q)][p] = b^P[q][p] is b^P
+// (symmetric) in the [P][Ap][Ap] layout; the epilogue also writes the diagonal d^P.
+bool b_setup(const Dims& d, int np, const TuneCode& tv, char* ws, const Layout& L, TcArgs& a,
+             TcMaps& m) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, Ap = d.Ap, Np = d.Np;
+  const size_t h2 = sizeof(__half);
+  const uint64_t rows = (uint64_t)np * Ap;
+  const int bk = tv.bk;
+  const uint32_t brows = tv.pair ? Ap / 2 : Ap;
+  if (!make_map(&m.ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+      !make_map(&m.al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
+      !make_map(&m.bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
+      !make_map(&m.bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
+    return false;
+  a = TcArgs{};
+  a.mode = 2; a.M = (int)rows; a.Nn = Ap;
+  a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
+  a.kt_per_kb = (N + bk - 1) / bk; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.eA = (const int*)(ws + L.eXt); a.eA_zstride = 0;
+  a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
+  a.glob_exp = &hdr->zero_exp;
+  a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
+  a.diag = (float*)(ws + L.D); a.diag_A = d.A;  // d^P for the mid section
+  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+  return true;
+}
+
+// (3) Gpart[s] = sum_{P in split s} X[P] Y[P] (integer + fraction operands, exponents
+//     common to the slices of a split); X interleaved by 8 along q.
+bool g_setup(const Dims& d, int np, int splits3, const TuneCode& tv, char* ws, const Layout& L,
+             TcArgs& a, TcMaps& m) {
+  DevHeader* hdr = (DevHeader*)(ws + L.header);
+  const int N = d.N, Ap = d.Ap, Np = d.Np;
+  const size_t h2 = sizeof(__half);
+  const int bk = tv.bk;
+  const uint32_t brows = tv.pair ? Ap / 2 : Ap;
+  if (!make_map_il8(&m.ah, ws + L.Xhi, Ap, Np, np, bk, BM) ||
+      !make_map_il8(&m.al, ws + L.Xlo, Ap, Np, np, bk, BM) ||
+      !make_map(&m.bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows) ||
+      !make_map(&m.bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows))
+    return false;
+  a = TcArgs{};
+  a.mode = 2; a.M = N; a.Nn = Ap;
+  a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
+  a.splits = splits3;
+  a.kt_per_kb = (Ap + bk - 1) / bk; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
+  a.a_il8 = 1;
+  a.eA = (const int*)(ws + L.eX3); a.eA_sstride = N;
+  a.eB = (const int*)(ws + L.eY); a.eB_sstride = Ap;
+  a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
+  a.glob_exp = &hdr->zero_exp;
+  a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
+  return true;
+}
+
 // The tensor-core part of one block of np auxiliary slices (slices p0 .. p0+np-1).
 int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaStream_t s) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
-  const int N = d.N, Ap = d.Ap, Np = d.Np;
-  CUtensorMap ah, al, bh, bl;
-  const size_t h2 = sizeof(__half);
-  // (1) X = B C_act  (integer + fraction operands; exact integer products)
+  const int N = d.N, Ap = d.Ap;
+  TcArgs a;
+  TcMaps m;
+  // exponents of the X splits (for b and for the G contraction)
   const int splits3 = d.splits < np ? d.splits : np;  // splits of the G contraction
   // the G contraction's rows run over (slices of a split) x Ap: the largest split's length
   const double invT2 = intfrac_inv_target_sq((double)((np + splits3 - 1) / splits3) * Ap);
@@ -1789,97 +1909,35 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
       intfrac_inv_target(N), (int*)(ws + L.eXt), (const double*)(ws + L.rn2) + (size_t)p0 * N,
       (const DevHeader*)hdr, np, splits3, N, invT2, (int*)(ws + L.spOf), (int*)(ws + L.eX3));
   count_launch(1);
+  // (1) X = B C_act
   prof_begin(DONOF_PHASE_HALF_TRANSFORM, s);
   {
-    // A operand: the symmetric tile storage of the split B (bulk copies, BK = 64); B
-    // operand: (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices)
-    const SymTiles st = sym_tiles(N);
-    const __half* Bh = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
-    const __half* Bl = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
-    const int bk = 64;  // the stored tiles are laid out for it
     const TuneCode tv = tuned_variant(1, N, Ap, np);
-    const uint32_t brows = tv.pair ? Ap / 2 : Ap;  // B rows staged per CTA
-    if (!make_map(&bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
-        !make_map(&bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
+    if (!half_setup(d, p0, np, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
-    ah = bh;  // unused: the A tiles come from the bulk copies
-    al = bl;
-    TcArgs a{};
-    a.mode = 1; a.M = st.T * BM; a.Nn = Ap;
-    a.m_tiles = st.T; a.z_count = np; a.splits = 1;
-    a.kt_per_kb = 1; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-    a.sym = 1; a.st = st;
-    // whole slices at once (the partner row tiles of a slice read their shared stored tile
-    // in the same round, so the second read can hit L2); a pair takes two slices' row tiles
-    const int work = tv.pair ? num_sms() / 2 : num_sms();
-    a.grid = (tv.full || work < st.T) ? work : work / st.T * st.T;
-    a.a_tiled_h = Bh; a.a_tiled_f = Bl;
-    a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
-    a.eB = (const int*)(ws + L.eCs); a.eB_zstride = 0;
-    a.glob_exp = &hdr->zero_exp;  // not applied in mode 1
-    a.Nmu = N; a.Nrow = N; a.Ap = Ap; a.Np = Np;
-    a.xhi = (__half*)(ws + L.Xhi); a.xlo = (__half*)(ws + L.Xlo);
-    a.xth = (__half*)(ws + L.Xthi); a.xtf = (__half*)(ws + L.Xtlo); a.eXt = (const int*)(ws + L.eXt);
-    a.spOf = (const int*)(ws + L.spOf); a.eX3 = (const int*)(ws + L.eX3);
-    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
-  // (2) b[P] = C_act^T X[P]  (integer + fraction operands)
+  // (2) b = C_act^T X
   prof_begin(DONOF_PHASE_MO_3INDEX, s);
   {
-    // one GEMM over all slices: rows (P, q) of X^T flattened into M, C_act^T rows as N;
-    // b[(P, q)][p] = b^P[q][p] is b^P (symmetric) in the [P][Ap][Ap] layout
-    const uint64_t rows = (uint64_t)np * Ap;
     const TuneCode tv = tuned_variant(2, N, Ap, np);
-    const int bk = tv.bk;
-    const uint32_t brows = tv.pair ? Ap / 2 : Ap;
-    if (!make_map(&ah, ws + L.Xthi, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
-        !make_map(&al, ws + L.Xtlo, N, rows, 1, Np * h2, rows * Np * h2, bk, BM) ||
-        !make_map(&bh, ws + L.Chi, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
-        !make_map(&bl, ws + L.Clo, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
+    if (!b_setup(d, np, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
-    TcArgs a{};
-    a.mode = 2; a.M = (int)rows; a.Nn = Ap;
-    a.m_tiles = (int)((rows + BM - 1) / BM); a.z_count = 1; a.splits = 1;
-    a.kt_per_kb = (N + bk - 1) / bk; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-    a.eA = (const int*)(ws + L.eXt); a.eA_zstride = 0;
-    a.eB = (const int*)(ws + L.eC); a.eB_zstride = 0;
-    a.glob_exp = &hdr->zero_exp;
-    a.out = (float*)(ws + L.b32); a.out_ld = Ap; a.out_zstride = 0;
-    a.diag = (float*)(ws + L.D); a.diag_A = d.A;  // d^P for the mid section
-    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_MO_3INDEX, s);
   // J, K and Y from b
   prof_begin(DONOF_PHASE_JK_Y, s);
   if (launch_mid_mixed(d, np, splits3, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
   prof_end(DONOF_PHASE_JK_Y, s);
-  // (3) Gpart[s] = sum_{P in split s} X[P] Y[P]  (integer + fraction operands, exponents
-  //     common to the slices of a split)
+  // (3) the G contraction and the sum of its split partials
   prof_begin(DONOF_PHASE_G_BUILD, s);
   {
     const TuneCode tv = tuned_variant(3, N, Ap, np);
-    const int bk = tv.bk;
-    const uint32_t brows = tv.pair ? Ap / 2 : Ap;
-    if (!make_map_il8(&ah, ws + L.Xhi, Ap, Np, np, bk, BM) ||
-        !make_map_il8(&al, ws + L.Xlo, Ap, Np, np, bk, BM) ||
-        !make_map(&bh, ws + L.Yhi, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows) ||
-        !make_map(&bl, ws + L.Ylo, Ap, Ap, np, Ap * h2, (uint64_t)Ap * Ap * h2, bk, brows))
+    if (!g_setup(d, np, splits3, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
+    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
-    TcArgs a{};
-    a.mode = 2; a.M = N; a.Nn = Ap;
-    a.m_tiles = (N + BM - 1) / BM; a.z_count = 1;
-    a.splits = splits3;
-    a.kt_per_kb = (Ap + bk - 1) / bk; a.nkb = np; a.a_z_kb = 1; a.b_z_mode = 2;
-    a.a_il8 = 1;  // X interleaved by 8 along q
-    a.eA = (const int*)(ws + L.eX3); a.eA_sstride = N;
-    a.eB = (const int*)(ws + L.eY); a.eB_sstride = Ap;
-    a.out = (float*)(ws + L.Gpart); a.out_ld = Ap; a.out_zstride = (long long)N * Ap;
-    a.glob_exp = &hdr->zero_exp;
-    a.status = &hdr->status; a.abort_flag = &hdr->abort_flag;
-    if (launch_tc_variant<kIntFrac>(tv, ah, al, bh, bl, a, s) != cudaSuccess) return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
     if (launch_reduce_G(d2, ws, L, s) != cudaSuccess) return DONOF_ERR_CUDA;
@@ -1888,6 +1946,179 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   return DONOF_OK;
 }
 
+}  // namespace donof
+
+// ---------------------------------------------------------------------------
+// Grouped launches over a batch (one block of np = naux slices per instance).
+// ---------------------------------------------------------------------------
+namespace donof {
+namespace {
+__device__ __forceinline__ int grp_splits(const Dims& d) { return d.splits < d.Q ? d.splits : d.Q; }
+__global__ void __launch_bounds__(1024) k_colnorms_group(const GroupLaunch g, int which) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const SplitJobs jobs = which == 0 ? split_c_jobs(I.d, I.L, I.ws, I.C, I.h, true)
+                                    : lambda_jobs(I.d, I.L, I.ws, I.C);
+  k_colnorms_body(b, jobs, intfrac_inv_target(I.d.N), (DevHeader*)(I.ws + I.L.header));
+}
+__global__ void __launch_bounds__(256) k_split_T_group(const GroupLaunch g, int which) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const SplitJobs jobs = which == 0 ? split_c_jobs(I.d, I.L, I.ws, I.C, I.h, true)
+                                    : lambda_jobs(I.d, I.L, I.ws, I.C);
+  k_split_T_body(b, jobs, I.d.Np);
+}
+__global__ void __launch_bounds__(256) k_gram_part_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  k_gram_part_body(b, I.C, I.d.N, I.d.A, (float*)(I.ws + I.L.gram));
+}
+__global__ void __launch_bounds__(256) k_gram_final_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  k_gram_final_body(b, (const float*)(I.ws + I.L.gram), (I.d.N + kGramChunk - 1) / kGramChunk,
+                    I.d.A, (DevHeader*)(I.ws + I.L.header));
+}
+__global__ void k_x_exponents_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  const Layout& L = I.L;
+  char* ws = I.ws;
+  const int np = d.Q, sp3 = grp_splits(d);
+  const double invT2 = intfrac_inv_target_sq((double)((np + sp3 - 1) / sp3) * d.Ap);
+  k_x_exponents_body(b, (const double*)(ws + L.L1max), (const double*)(ws + L.cnorm), d.Ap,
+                     intfrac_inv_target(d.N), (int*)(ws + L.eXt), (const double*)(ws + L.rn2),
+                     (const DevHeader*)(ws + L.header), np, sp3, d.N, invT2, (int*)(ws + L.spOf),
+                     (int*)(ws + L.eX3));
+}
+__global__ void k_reduce_G_group(const GroupLaunch g) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  char* ws = I.ws;
+  k_reduce_G_body(b, (const float*)(ws + I.L.Gpart), grp_splits(d), d.N, d.A, d.Ap,
+                  (const DevHeader*)(ws + I.L.header), (double*)(ws + I.L.G));
+}
+__global__ void k_sum_blocks_group(const GroupLaunch g, int which) {
+  Blk b;
+  const InstRec& I = g.inst[group_locate(g, b)];
+  const Dims& d = I.d;
+  if (which == 0)
+    k_sum_blocks_body(b, (const float*)(I.ws + I.L.hpart), d.N, d.A, d.Ap,
+                      (double*)(I.ws + I.L.hC), d.A);
+  else
+    k_sum_blocks_body(b, (const float*)(I.ws + I.L.hpart), d.N, d.A, d.Ap, I.lam, d.N);
+}
+}  // namespace
+
+// Arguments and maps of instance (d, ws, L) for a grouped tensor-core contraction (one block
+// of all naux slices), and its number of work units.  The launch settings are those of the
+// single launches' defaults: BK 64 (32 for the G contraction), single CTAs.
+bool tc_group_setup(int kind, const Dims& d, char* ws, const Layout& L, void* a_rec,
+                    void* m_rec, int& units) {
+  TcArgs& a = *(TcArgs*)a_rec;
+  TcMaps& m = *(TcMaps*)m_rec;
+  const int np = d.Q, sp3 = d.splits < np ? d.splits : np;
+  bool ok = false;
+  switch (kind) {
+    case GK_TC_HC:
+      ok = ext_setup(d, d.N, (const int*)(ws + L.eh), (const int*)(ws + L.eC), ws, L, a, m);
+      break;
+    case GK_TC_LAM:
+      ok = ext_setup(d, d.N, (const int*)(ws + L.eCf), (const int*)(ws + L.eG), ws, L, a, m);
+      break;
+    case GK_TC_HALF: ok = half_setup(d, 0, np, TuneCode{64, 0, 0}, ws, L, a, m); break;
+    case GK_TC_B: ok = b_setup(d, np, TuneCode{64, 0, 0}, ws, L, a, m); break;
+    case GK_TC_G: ok = g_setup(d, np, sp3, TuneCode{32, 0, 0}, ws, L, a, m); break;
+    default: return false;
+  }
+  units = a.z_count * a.m_tiles * a.splits;
+  return ok;
+}
+
+// Kernel-wide settings of a grouped contraction from its widest instance (as launch_tc sets
+// them for one), written into every instance's arguments together with the batch's status
+// and abort words; returns the dynamic shared memory of the launch.
+size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag) {
+  TcArgs* a = (TcArgs*)a_recs;
+  const int BK = kind == GK_TC_G ? 32 : 64;
+  int nn = 16;
+  for (int i = 0; i < ninst; ++i) nn = a[i].Nn > nn ? a[i].Nn : nn;
+  const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)nn * BK * 2;
+  const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  int stages = (int)((232448 - 1024 - 512 - kTabBytes) / stage_bytes);
+  stages = stages > 8 ? 8 : (stages < 2 ? 2 : stages);
+  int nbuf, stride;
+  if (4 * nn <= 512) {
+    nbuf = 2;
+    stride = 256;
+  } else if (3 * nn <= 512 && nn <= kMaxRegCols) {
+    nbuf = 3;
+    stride = 0;
+  } else {
+    nbuf = 1;
+    stride = 0;
+  }
+  for (int i = 0; i < ninst; ++i) {
+    a[i].stages = stages;
+    a[i].tmem_cols = 512;
+    a[i].nbuf = nbuf;
+    a[i].buf_stride = stride;
+    a[i].region = nn;
+    a[i].nb_stage = nn;
+    a[i].status = status;
+    a[i].abort_flag = abort_flag;
+  }
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 8) * 8 + kTabBytes;
+  return smem < 120 * 1024 ? 120 * 1024 : smem;
+}
+
+cudaError_t launch_tc_group(int kind, const void* args_dev, const void* maps_dev,
+                            const int* ustart, int ninst, int units, size_t smem,
+                            cudaStream_t s) {
+  const TcArgs* targs = (const TcArgs*)args_dev;
+  const TcMaps* tmaps = (const TcMaps*)maps_dev;
+  int grid = num_sms();
+  if (grid > units) grid = units;
+  if (grid < 1) grid = 1;
+  cudaError_t e;
+  if (kind == GK_TC_G) {
+    e = cudaFuncSetAttribute(k_tc_gemm_group<32, kIntFrac>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm_group<32, kIntFrac><<<grid, kThreads, smem, s>>>(targs, tmaps, ustart, ninst);
+  } else {
+    e = cudaFuncSetAttribute(k_tc_gemm_group<64, kIntFrac>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm_group<64, kIntFrac><<<grid, kThreads, smem, s>>>(targs, tmaps, ustart, ninst);
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+size_t tc_args_bytes() { return sizeof(TcArgs); }
+size_t tc_maps_bytes() { return sizeof(TcMaps); }
+
+cudaError_t launch_tc_small_group(int kind, const GroupLaunch& g, int blocks, int threads,
+                                  cudaStream_t s) {
+  switch (kind) {
+    case GK_CNORM_C: k_colnorms_group<<<blocks, threads, 0, s>>>(g, 0); break;
+    case GK_SPLIT_C: k_split_T_group<<<blocks, threads, 0, s>>>(g, 0); break;
+    case GK_CNORM_L: k_colnorms_group<<<blocks, threads, 0, s>>>(g, 1); break;
+    case GK_SPLIT_L: k_split_T_group<<<blocks, threads, 0, s>>>(g, 1); break;
+    case GK_GRAM_PART: k_gram_part_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_GRAM_FINAL: k_gram_final_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_XEXP: k_x_exponents_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_REDUCEG: k_reduce_G_group<<<blocks, threads, 0, s>>>(g); break;
+    case GK_SUM_HC: k_sum_blocks_group<<<blocks, threads, 0, s>>>(g, 0); break;
+    case GK_SUM_L: k_sum_blocks_group<<<blocks, threads, 0, s>>>(g, 1); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
 }  // namespace donof
 
 // ---------------------------------------------------------------------------

@@ -1,9 +1,10 @@
 """Batched builds (donof_energy_lagrangian_batched) on instances of the dissociation-scan
 workload: uneven nbf in 40..240, naux = 4 nbf, 5 pairs, Ncwo in 1..4, one seed per instance.
 
-Every instance of a batched call must reproduce the single-instance entry point (the same
-kernels, every sum in a fixed order) and the oracle within the parity tolerances, with and
-without CUDA-graph capture/replay.
+The grouped path (one launch per step of the build for all instances) and the per-instance
+stream path run the same kernel bodies, so they must agree bit for bit, with and without
+CUDA-graph capture/replay; every instance must reproduce the single-instance entry point
+(the same kernels, every sum in a fixed order) and the oracle within the parity tolerances.
 """
 import numpy as np
 import pytest
@@ -12,6 +13,8 @@ import synth
 from oracle import pnof
 
 pytestmark = pytest.mark.gpu
+
+KEYS = ("E", "lam", "dE_dgamma", "dE_dC")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,11 +46,21 @@ def _instances(probs, precision):
     return cprobs, tens, host
 
 
+def _run(batch, tens, flags):
+    import torch
+    for x in tens:
+        for k in KEYS:
+            x[k].fill_(np.nan)
+    batch.run(flags)
+    torch.cuda.synchronize()
+    return [{k: x[k].cpu().numpy().copy() for k in KEYS} for x in tens]
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_batched_matches_single_and_oracle(precision):
     import torch
     import paper_2004_06142_gb300 as dn
-    probs = synth.batch_problems(10 if precision else 5)
+    probs = synth.batch_problems(64 if precision else 8)
     cprobs, tens, host = _instances(probs, precision)
     batch = dn.Batch(cprobs, tens)
     batch.prepare()
@@ -59,26 +72,39 @@ def test_batched_matches_single_and_oracle(precision):
         b.prepare(x["B"])
         E, lam, dg = b.forward(x["h"], x["C"], x["gamma"], x["pair_map"])
         dC, _ = b.backward(one)
-        single.append(dict(E=E.item(), lam=lam.cpu().numpy(), dE_dgamma=dg.cpu().numpy(),
+        single.append(dict(E=E.cpu().numpy(), lam=lam.cpu().numpy(), dE_dgamma=dg.cpu().numpy(),
                            dE_dC=dC.cpu().numpy()))
+        del b
+    BW, GR, ST = dn.BATCH_BACKWARD, dn.BATCH_GRAPH, dn.BATCH_STREAMS
+    runs = [_run(batch, tens, f) for f in (BW, BW | GR, BW | GR, BW | ST, BW | ST | GR)]
+    assert batch.status() == 0
+    for out in runs:
+        for s, o in zip(single, out):
+            for k in KEYS:
+                np.testing.assert_array_equal(o[k], s[k], err_msg=k)
+    # every instance against the oracle
     tol_e, tol_a = (1e-6, 1e-5) if precision else (1e-10, 1e-10)
-    for flags in (dn.BATCH_BACKWARD, dn.BATCH_BACKWARD | dn.BATCH_GRAPH,
-                  dn.BATCH_BACKWARD | dn.BATCH_GRAPH):
-        for x in tens:
-            for k in ("E", "lam", "dE_dgamma", "dE_dC"):
-                x[k].fill_(np.nan)
-        batch.run(flags)
-        torch.cuda.synchronize()
-        for s, x in zip(single, tens):
-            assert abs(x["E"].item() - s["E"]) <= 1e-9
-            for k in ("lam", "dE_dgamma", "dE_dC"):
-                assert np.abs(x[k].cpu().numpy() - s[k]).max() <= 1e-8, k
-    # the oracle, on a few instances of the batch
-    for i in (0, len(probs) // 2, len(probs) - 1):
-        pr, d, x = probs[i], host[i], tens[i]
+    for pr, d, o in zip(probs, host, runs[0]):
         ref = pnof.build(d["h"], d["B"], d["C"], d["gamma"], d["pair_map"], pr.npair, pr.ncwo,
                          pnof.PNOF7)
-        assert abs(x["E"].item() - ref["E"]) <= tol_e
-        assert np.abs(x["lam"].cpu().numpy() - ref["lam"]).max() <= tol_a
-        assert np.abs(x["dE_dgamma"].cpu().numpy() - ref["dE_dgamma"]).max() <= tol_a
-        assert np.abs(x["dE_dC"].cpu().numpy() - ref["dE_dC"]).max() <= tol_a
+        assert abs(o["E"][0] - ref["E"]) <= tol_e, (pr, o["E"][0] - ref["E"])
+        for k in ("lam", "dE_dgamma", "dE_dC"):
+            assert np.abs(o[k] - ref[k]).max() <= tol_a, (pr, k)
+
+
+def test_grouped_launch_count():
+    # the grouped path: one launch per step of the build for all instances
+    import paper_2004_06142_gb300 as dn
+    probs = synth.batch_problems(12)
+    cprobs, tens, _ = _instances(probs, 1)
+    batch = dn.Batch(cprobs, tens)
+    batch.prepare()
+    batch.run(dn.BATCH_BACKWARD)
+    n0 = dn.donof_launch_count()
+    batch.run(dn.BATCH_BACKWARD)
+    grouped = dn.donof_launch_count() - n0
+    n0 = dn.donof_launch_count()
+    batch.run(dn.BATCH_BACKWARD | dn.BATCH_STREAMS)
+    streams = dn.donof_launch_count() - n0
+    assert grouped == 26
+    assert streams == 12 * 25
