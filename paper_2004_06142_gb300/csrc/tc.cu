@@ -321,6 +321,8 @@ constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay 
 // per epilogue warp, the column factors of its chunks (up to 256 columns split between the
 // groups), one float2 per column, in shared memory after the barriers
 constexpr int kTabCols = 256 / kEpiGroups;
+constexpr int kMaxSets = 8;  // TMEM accumulator sets at most (narrow tiles)
+constexpr int kBarTail = 2 * kMaxSets + 4;  // barriers after full/empty, then the TMEM slot
 constexpr int kTabBytes = 4 * kEpiGroups * kTabCols * 8;
 
 struct TcArgs {
@@ -332,7 +334,8 @@ struct TcArgs {
   int a_z_kb;      // A tile z coordinate = kb (else 0)
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
-  int nbuf;        // TMEM accumulator sets: 1, 2, or 3 (three regions in rotation, below)
+  int nbuf;        // TMEM accumulator sets: 1, 2, 4, 8, or 3 (three regions in rotation, below)
+  int epi_alt;     // 1: the two epilogue warp groups take alternate tiles (nbuf even)
   int region;      // nbuf 3: columns of each region (at least Nn)
   int nb_stage;    // B rows a shared-memory stage holds (at least this CTA's share of Nn)
   int buf_stride;  // TMEM columns per accumulator set
@@ -430,10 +433,11 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   const uint32_t b_bytes = (uint32_t)nb_rows * BK * 2;
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   uint64_t* bars = (uint64_t*)(smem + (size_t)S * stage_bytes);
-  // barriers: full[S], empty[S], tfull[2], tempty[2], drain, trel[2]; then the TMEM address
-  const int kFull = 0, kEmpty = S, kTfull = 2 * S, kTempty = 2 * S + 2, kDrain = 2 * S + 4,
-            kTrel = 2 * S + 5;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 7);
+  // barriers: full[S], empty[S], tfull[kMaxSets], tempty[kMaxSets], drain, trel[2]; then the
+  // TMEM address and the epilogue's factor tables
+  const int kFull = 0, kEmpty = S, kTfull = 2 * S, kTempty = 2 * S + kMaxSets,
+            kDrain = 2 * S + 2 * kMaxSets, kTrel = 2 * S + 2 * kMaxSets + 1;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + kBarTail - 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int* status = a0.status;
   int* abort_flag = a0.abort_flag;
@@ -442,7 +446,9 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   const int cl = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;   // this CTA's work stream
   const int ncl = PAIR ? (int)ncluster_x() : (int)gridDim.x;
   // epilogue threads that release TMEM (of both CTAs of a pair)
-  const uint32_t rel_count = (PAIR ? 2u : 1u) * 128u * kEpiGroups;
+  // epi_alt: the epilogue groups take alternate tiles (all columns), otherwise they split the
+  // columns of every tile
+  const uint32_t rel_count = (PAIR ? 2u : 1u) * 128u * (a0.epi_alt ? 1u : (uint32_t)kEpiGroups);
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (threadIdx.x == 0) {
@@ -451,10 +457,10 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       mbar_init(bar(kFull + i), (PAIR && rank == 0) ? 2 : 1);
       mbar_init(bar(kEmpty + i), 1);
     }
-    mbar_init(bar(kTfull + 0), 1);
-    mbar_init(bar(kTfull + 1), 1);
-    mbar_init(bar(kTempty + 0), rel_count);
-    mbar_init(bar(kTempty + 1), rel_count);
+    for (int i = 0; i < kMaxSets; ++i) {
+      mbar_init(bar(kTfull + i), 1);
+      mbar_init(bar(kTempty + i), rel_count);
+    }
     mbar_init(bar(kDrain), 1);
     mbar_init(bar(kTrel + 0), rel_count);
     mbar_init(bar(kTrel + 1), rel_count);
@@ -727,7 +733,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     const int ew = warp - 4;
     const int q = ew & 3, eg = ew >> 2;
     // this warp's table of column factors
-    float2* ctab = (float2*)(bars + 2 * S + 8) + ew * kTabCols;
+    float2* ctab = (float2*)(bars + 2 * S + kBarTail) + ew * kTabCols;
     // a release of TMEM: on the even CTA's barrier (remotely from the odd CTA of a pair)
     auto release = [&](int i) {
       tc_fence_before();
@@ -736,12 +742,14 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     };
     int local = 0;
     for (int u = cl; u < units; u += ncl, ++local) {
+      if (a0.epi_alt && (local % kEpiGroups) != eg) continue;  // another group's tile
       int lu;
       const TcArgs& args = targs[locate(u, lu)];
       const int glob = args.glob_exp ? *args.glob_exp : 0;
       // this group's 16-column chunks [ch0, ch1)
-      const int nch = args.Nn / 16, hch = (nch + kEpiGroups - 1) / kEpiGroups;
-      const int ch0 = eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
+      const int nch = args.Nn / 16;
+      const int hch = a0.epi_alt ? nch : (nch + kEpiGroups - 1) / kEpiGroups;
+      const int ch0 = a0.epi_alt ? 0 : eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
       int z, mt, sp;
       decode(args, lu, z, mt, sp);
       int tf;
@@ -1081,6 +1089,34 @@ int num_sms() {
   return n;
 }
 
+// TMEM use of a launch whose widest tile has nn columns (per_set: the columns of one set of
+// accumulators).  Narrow tiles (nn <= 80, all of a tile's columns fit one epilogue warp's
+// registers): as many sets as fit, up to kMaxSets (a power of two), the two epilogue groups on
+// alternate tiles, so that the epilogue's per-tile latency overlaps and the MMAs run several
+// tiles ahead.  Wider: two sets if they fit, else (kIntFrac, up to kMaxRegCols columns) three
+// regions in rotation, else one set; the groups split every tile's columns.  Returns false
+// when a set does not fit.
+bool tmem_plan(int nn, int per_set, bool intfrac, int& nbuf, int& stride, int& epi_alt) {
+  epi_alt = 0;
+  if (nn <= 80 && 2 * per_set <= 512) {
+    nbuf = 2;
+    while (2 * nbuf <= kMaxSets && 2 * nbuf * per_set <= 512) nbuf *= 2;
+    stride = 512 / nbuf;
+    epi_alt = 1;
+  } else if (2 * per_set <= 512) {
+    nbuf = 2;
+    stride = 256;
+    if (per_set > 256) return false;
+  } else if (intfrac && 3 * nn <= 512 && nn <= kMaxRegCols) {
+    nbuf = 3;
+    stride = 0;
+  } else {
+    nbuf = 1;
+    stride = 0;
+  }
+  return per_set <= 512;
+}
+
 template <int BK, int NUM, int PAIR>
 cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
@@ -1092,24 +1128,14 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
   a.stages = stages;
-  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart); two sets if they fit,
-  // else (kIntFrac, up to kMaxRegCols columns) three regions in rotation, else one set
+  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart), sets as tmem_plan says
   const int per_set = (NUM != kSplit3 ? 2 : 1) * a.Nn;
   a.tmem_cols = 512;
-  if (2 * per_set <= 512) {
-    a.nbuf = 2;
-    a.buf_stride = 256;
-    if (per_set > 256) return cudaErrorInvalidValue;
-  } else if (NUM != kSplit3 && 3 * a.Nn <= 512 && a.Nn <= kMaxRegCols) {
-    a.nbuf = 3;
-    a.buf_stride = 0;
-  } else {
-    a.nbuf = 1;
-    a.buf_stride = 0;
-  }
+  if (!tmem_plan(a.Nn, per_set, NUM != kSplit3, a.nbuf, a.buf_stride, a.epi_alt))
+    return cudaErrorInvalidValue;
   a.region = a.Nn;
   a.nb_stage = PAIR ? a.Nn / 2 : a.Nn;
-  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 8) * 8 + kTabBytes;
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + kBarTail) * 8 + kTabBytes;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: the TMEM allocation never waits
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2049,28 +2075,20 @@ size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abor
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   int stages = (int)((232448 - 1024 - 512 - kTabBytes) / stage_bytes);
   stages = stages > 8 ? 8 : (stages < 2 ? 2 : stages);
-  int nbuf, stride;
-  if (4 * nn <= 512) {
-    nbuf = 2;
-    stride = 256;
-  } else if (3 * nn <= 512 && nn <= kMaxRegCols) {
-    nbuf = 3;
-    stride = 0;
-  } else {
-    nbuf = 1;
-    stride = 0;
-  }
+  int nbuf, stride, epi_alt;
+  tmem_plan(nn, 2 * nn, true, nbuf, stride, epi_alt);
   for (int i = 0; i < ninst; ++i) {
     a[i].stages = stages;
     a[i].tmem_cols = 512;
     a[i].nbuf = nbuf;
     a[i].buf_stride = stride;
+    a[i].epi_alt = epi_alt;
     a[i].region = nn;
     a[i].nb_stage = nn;
     a[i].status = status;
     a[i].abort_flag = abort_flag;
   }
-  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 8) * 8 + kTabBytes;
+  size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + kBarTail) * 8 + kTabBytes;
   return smem < 120 * 1024 ? 120 * 1024 : smem;
 }
 
