@@ -157,6 +157,7 @@ struct Plan {
   size_t smem[GK_COUNT] = {};
   int tc_units[kTcKinds] = {};
   size_t tc_smem[kTcKinds] = {};
+  int tc_cat[kTcKinds] = {};
 };
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -269,7 +270,8 @@ int build_plan(int32_t ninst, const donof_problem* probs, const donof_instance* 
     }
     ust[ninst] = tot;
     pl.tc_units[t] = tot;
-    pl.tc_smem[t] = tc_group_finish(kind, h + P.targs[t], ninst, &bhdr->status, &bhdr->abort_flag);
+    pl.tc_smem[t] = tc_group_finish(kind, h + P.targs[t], ninst, &bhdr->status, &bhdr->abort_flag,
+                                    pl.tc_cat[t]);
   }
   return DONOF_OK;
 }
@@ -289,7 +291,7 @@ int enqueue_grouped(int32_t ninst, char* ws, int32_t flags, const Plan& pl, cuda
     if (t >= 0) {
       if (pl.tc_units[t] == 0) continue;
       e = launch_tc_group(k, ws + P.targs[t], ws + P.tmaps[t], (const int*)(ws + P.ustart[t]),
-                          ninst, pl.tc_units[t], pl.tc_smem[t], s);
+                          ninst, pl.tc_units[t], pl.tc_smem[t], pl.tc_cat[t], s);
     } else {
       if (pl.blocks[k] == 0) continue;
       const int* start = grids + (size_t)k * (4 * ninst + 1);

@@ -66,13 +66,19 @@ struct Layout {
 
 Dims make_dims(const donof_problem* p);
 
-// Lower-triangle tile storage of the split B for the half transform: row tiles of 128 AO
-// indices (T of them), the last one stored with its rows rounded up to a multiple of 64;
-// tile (i, j), j <= i, holds rows of tile i and columns of tile j as chunks of 64 columns,
-// each chunk [R_i rows][64] with the 16-byte pieces of row r at piece ^ (r % 8).
+// Storage of the split B for the half transform.  N > kDenseMaxN: lower-triangle tile
+// storage, row tiles of 128 AO indices (T of them), the last one stored with its rows rounded
+// up to a multiple of 64; tile (i, j), j <= i, holds rows of tile i and columns of tile j as
+// chunks of 64 columns, each chunk [R_i rows][64] with the 16-byte pieces of row r at
+// piece ^ (r % 8).  N <= kDenseMaxN (dense): every slice whole, [N][ld] with ld = N rounded up
+// to 8 (a tensor-map row pitch of 16-byte multiples), read through a 3-D tensor map whose
+// zero fill pads the 128-row tiles and 64-wide K steps; at these sizes the tiles' padding
+// would cost more bytes than the dense copy of the upper triangle.
+constexpr int kDenseMaxN = 256;
 struct SymTiles {
   int T, Rlast;
   long long perP;  // elements per slice and plane
+  int dense, ld;   // dense storage and its row pitch (elements)
 };
 __host__ __device__ inline int sym_R(const SymTiles& t, int i) { return i < t.T - 1 ? 128 : t.Rlast; }
 __host__ __device__ inline long long sym_tile_off(const SymTiles& t, int i, int j) {
@@ -83,7 +89,10 @@ __host__ __device__ inline SymTiles sym_tiles(int N) {
   t.T = (N + 127) / 128;
   const int last = N - 128 * (t.T - 1);
   t.Rlast = (last + 63) / 64 * 64;
-  t.perP = sym_tile_off(t, t.T - 1, 0) + (long long)t.Rlast * (128LL * (t.T - 1) + t.Rlast);
+  t.dense = N <= kDenseMaxN ? 1 : 0;
+  t.ld = (N + 7) / 8 * 8;
+  t.perP = t.dense ? (long long)N * t.ld
+                   : sym_tile_off(t, t.T - 1, 0) + (long long)t.Rlast * (128LL * (t.T - 1) + t.Rlast);
   return t;
 }
 
@@ -154,12 +163,14 @@ cudaError_t launch_tc_small_group(int kind, const GroupLaunch& g, int blocks, in
 // records are opaque here, byte records of tc_args_bytes() and tc_maps_bytes() each (maps
 // 64-byte aligned).  Setup fills instance records on the host and counts its work units;
 // finish writes the kernel-wide settings into all records and returns the launch's shared
-// memory; the launch reads the records from device memory.
+// memory and its numeric mode (cat: the planes of B concatenated, for narrow tiles); the
+// launch reads the records from device memory.
 bool tc_group_setup(int kind, const Dims& d, char* ws, const Layout& L, void* a_rec,
                     void* m_rec, int& units);
-size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag);
+size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag,
+                       int& cat);
 cudaError_t launch_tc_group(int kind, const void* args_dev, const void* maps_dev,
-                            const int* ustart, int ninst, int units, size_t smem,
+                            const int* ustart, int ninst, int units, size_t smem, int cat,
                             cudaStream_t s);
 size_t tc_args_bytes();
 size_t tc_maps_bytes();

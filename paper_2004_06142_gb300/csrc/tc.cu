@@ -315,6 +315,12 @@ __device__ __forceinline__ void tmem_wait_ld() {
 //            is kept as close to 2^12 as the rounding of h allows.
 constexpr int kSplit3 = 0;
 constexpr int kIntFrac = 1;
+// kIntFracCat: kIntFrac for narrow tiles (2 Nn <= 128, no CTA pair): the two planes of B,
+// staged back to back, form one operand of 2 Nn rows, so that a K step is two MMAs,
+// h_A [h_B | f_B] and f_A [h_B | f_B], each reading its A plane from shared memory once
+// (half the operand traffic of four N = Nn MMAs, which bounds narrow tiles): accumulators of
+// 2 Nn columns, the first with the exact h_A h_B in its left half
+constexpr int kIntFracCat = 2;
 constexpr int kMaxRegCols = 160;  // epilogue keeps up to this many columns per row in registers
 constexpr int kEpiGroups = 2;     // epilogue warps per TMEM lane quadrant (each half the columns)
 constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay warps + epilogue
@@ -331,7 +337,8 @@ struct TcArgs {
   int Nn;          // output columns = B box rows (multiple of 16, <= 256)
   int m_tiles, z_count, splits;
   int kt_per_kb, nkb;
-  int a_z_kb;      // A tile z coordinate = kb (else 0)
+  int a_z_kb;      // A tile z coordinate = kb (else a_z_unit ? the unit's z : 0)
+  int a_z_unit;
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
   int nbuf;        // TMEM accumulator sets: 1, 2, 4, 8, or 3 (three regions in rotation, below)
@@ -441,14 +448,20 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int* status = a0.status;
   int* abort_flag = a0.abort_flag;
+  // kernel-wide settings in registers (the asm statements' memory clobbers would otherwise
+  // reload them from the argument table after every MMA and TMEM access)
   const int nbuf = a0.nbuf;
+  constexpr bool bcat = NUM == kIntFracCat && !PAIR;
+  const bool nbuf3 = !bcat && nbuf == 3;  // three TMEM regions (never with bcat: Nn <= 64)
+  const bool epi_alt = a0.epi_alt != 0;
+  const uint32_t region = (uint32_t)a0.region, buf_stride = (uint32_t)a0.buf_stride;
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
   const int cl = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;   // this CTA's work stream
   const int ncl = PAIR ? (int)ncluster_x() : (int)gridDim.x;
   // epilogue threads that release TMEM (of both CTAs of a pair)
   // epi_alt: the epilogue groups take alternate tiles (all columns), otherwise they split the
   // columns of every tile
-  const uint32_t rel_count = (PAIR ? 2u : 1u) * 128u * (a0.epi_alt ? 1u : (uint32_t)kEpiGroups);
+  const uint32_t rel_count = (PAIR ? 2u : 1u) * 128u * (epi_alt ? 1u : (uint32_t)kEpiGroups);
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (threadIdx.x == 0) {
@@ -477,24 +490,29 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   // work units: (z, row tile, split) of each problem; PAIR: a unit is the M = 256 tile of the
   // cluster, rows of slice pair (2 zp, 2 zp + 1) in the symmetric mode, row tiles
   // (2 mu, 2 mu + 1) otherwise
-  const bool sym = BK == 64 && a0.sym;
-  auto z_units = [&](const TcArgs& A) { return (PAIR && sym) ? (A.z_count + 1) / 2 : A.z_count; };
-  auto m_units = [&](const TcArgs& A) { return (PAIR && !sym) ? (A.m_tiles + 1) / 2 : A.m_tiles; };
+  // the symmetric mode is per problem (a table may mix it with dense half transforms)
+  auto sym_of = [&](const TcArgs& A) { return BK == 64 && A.sym; };
+  auto z_units = [&](const TcArgs& A) {
+    return (PAIR && sym_of(A)) ? (A.z_count + 1) / 2 : A.z_count;
+  };
+  auto m_units = [&](const TcArgs& A) {
+    return (PAIR && !sym_of(A)) ? (A.m_tiles + 1) / 2 : A.m_tiles;
+  };
   const int units = ustart ? ustart[ninst] : z_units(a0) * m_units(a0) * a0.splits;
-  // the problem of unit u and the unit's index lu among that problem's units
-  auto locate = [&](int u, int& lu) {
-    if (!ustart) {
-      lu = u;
-      return 0;
+  // the problem of unit u and the unit's index lu among that problem's units: every role
+  // walks its units in increasing order, so the problem index only moves forward
+  struct Walk {
+    int inst, lo, hi;
+  };
+  auto walk0 = [&]() { return Walk{0, 0, ustart ? ustart[1] : 0x7fffffff}; };
+  auto locate = [&](Walk& w, int u, int& lu) {
+    while (u >= w.hi && w.inst < ninst - 1) {
+      ++w.inst;
+      w.lo = w.hi;
+      w.hi = ustart[w.inst + 1];
     }
-    int lo = 0, hi = ninst - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (ustart[mid] <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    lu = u - ustart[lo];
-    return lo;
+    lu = u - w.lo;
+    return w.inst;
   };
   // consecutive units share the split (and so the B tiles of one K range, which then come
   // from L2 for all M tiles of that split)
@@ -504,11 +522,11 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     const int r = u % (mu_n * A.splits);
     sp = r / mu_n;
     const int mu = r % mu_n;
-    z = (PAIR && sym) ? 2 * zu + (int)rank : zu;
-    mt = (PAIR && !sym) ? 2 * mu + (int)rank : mu;
+    z = (PAIR && sym_of(A)) ? 2 * zu + (int)rank : zu;
+    mt = (PAIR && !sym_of(A)) ? 2 * mu + (int)rank : mu;
   };
   auto unit_iters = [&](const TcArgs& A, int sp) {
-    if (sym) return 2 * (A.st.T - 1) + A.st.Rlast / 64;
+    if (sym_of(A)) return 2 * (A.st.T - 1) + A.st.Rlast / 64;
     const int kb0 = (int)((long long)A.nkb * sp / A.splits);
     const int kb1 = (int)((long long)A.nkb * (sp + 1) / A.splits);
     return (kb1 - kb0) * A.kt_per_kb;
@@ -523,15 +541,17 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     bool ok = true;
     long long issued = 0;  // stages filled so far
     const int b_row0 = (int)rank * nb_rows;
+    Walk wk = walk0();
     for (int u = cl; u < units && ok; u += ncl) {
       int lu;
-      const int inst = locate(u, lu);
+      const int inst = locate(wk, u, lu);
       const TcArgs& args = targs[inst];
       const TcMaps& maps = tmaps[inst];
       const uint32_t bu = b_bytes_of(args);
+      const uint32_t bl_off = bcat ? bu : b_bytes;  // the fraction plane of B
       int z, mt, sp;
       decode(args, lu, z, mt, sp);
-      if (sym) {
+      if (sym_of(args)) {
         const SymTiles st = args.st;
         const bool a_valid = z < args.z_count;  // PAIR: the odd slice of an odd count is absent
         const int i = mt, Ri = sym_R(st, i);
@@ -566,7 +586,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
               }
             }
             tma_load_3d(base + 2 * a_bytes, &maps.bh, fb, 128 * j + 64 * c, b_row0, 0);
-            tma_load_3d(base + 2 * a_bytes + b_bytes, &maps.bl, fb, 128 * j + 64 * c, b_row0, 0);
+            tma_load_3d(base + 2 * a_bytes + bl_off, &maps.bl, fb, 128 * j + 64 * c, b_row0, 0);
             ++issued;
             if (++stage == S) { stage = 0; phase ^= 1u; }
           }
@@ -575,18 +595,21 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       }
       const int kb0 = (int)((long long)args.nkb * sp / args.splits);
       const int kb1 = (int)((long long)args.nkb * (sp + 1) / args.splits);
+      const bool il8 = args.a_il8 != 0, amn = BK == 64 && args.a_mn != 0;
+      const bool az_kb = args.a_z_kb != 0, az_unit = args.a_z_unit != 0;
+      const int bzm = args.b_z_mode, ktn = args.kt_per_kb;
       for (int kb = kb0; kb < kb1 && ok; ++kb) {
-        const int az = args.a_z_kb ? kb : 0;
-        const int bz = args.b_z_mode == 1 ? z : (args.b_z_mode == 2 ? kb : 0);
-        for (int kt = 0; kt < args.kt_per_kb; ++kt) {
+        const int az = az_kb ? kb : (az_unit ? z : 0);
+        const int bz = bzm == 1 ? z : (bzm == 2 ? kb : 0);
+        for (int kt = 0; kt < ktn; ++kt) {
           if (!mbar_wait(bar(kEmpty + stage), phase ^ 1u, status, abort_flag)) { ok = false; break; }
           const uint32_t fb = bar(kFull + stage);
           const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
           mbar_expect_tx(fb, 2 * a_bytes + 2 * bu);
-          if (args.a_il8) {
+          if (il8) {
             tma_load_4d(base, &maps.ah, fb, 0, mt * BM / 8, kt * BK / 8, az);
             tma_load_4d(base + a_bytes, &maps.al, fb, 0, mt * BM / 8, kt * BK / 8, az);
-          } else if (BK == 64 && args.a_mn) {
+          } else if (amn) {
             tma_load_3d(base, &maps.ah, fb, mt * BM, kt * BK, az);
             tma_load_3d(base + a_bytes / 2, &maps.ah, fb, mt * BM + 64, kt * BK, az);
             tma_load_3d(base + a_bytes, &maps.al, fb, mt * BM, kt * BK, az);
@@ -596,7 +619,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
             tma_load_3d(base + a_bytes, &maps.al, fb, kt * BK, mt * BM, az);
           }
           tma_load_3d(base + 2 * a_bytes, &maps.bh, fb, kt * BK, b_row0, bz);
-          tma_load_3d(base + 2 * a_bytes + b_bytes, &maps.bl, fb, kt * BK, b_row0, bz);
+          tma_load_3d(base + 2 * a_bytes + bl_off, &maps.bl, fb, kt * BK, b_row0, bz);
           ++issued;
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
@@ -616,9 +639,10 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
+    Walk wk = walk0();
     for (int u = cl; u < units && ok; u += ncl) {
       int lu;
-      const TcArgs& args = targs[locate(u, lu)];
+      const TcArgs& args = targs[locate(wk, u, lu)];
       int z, mt, sp;
       decode(args, lu, z, mt, sp);
       const int iters = unit_iters(args, sp);
@@ -637,18 +661,21 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     uint32_t phase = 0;
     bool ok = true;
     int local = 0;
+    Walk wk = walk0();
     for (int u = cl; u < units && ok; u += ncl, ++local) {
       int lu;
-      const TcArgs& args = targs[locate(u, lu)];
+      const TcArgs& args = targs[locate(wk, u, lu)];
+      const int nn = args.Nn;
+      const bool il8 = args.a_il8 != 0, amn = args.a_mn != 0;
       const uint32_t idesc =
-          idesc_f16(PAIR ? 2 * BM : BM, args.Nn) | (args.a_mn ? (1u << 15) : 0u);
-      const int T = args.st.T;
+          idesc_f16(PAIR ? 2 * BM : BM, bcat ? 2 * nn : nn) | (amn ? (1u << 15) : 0u);
+      const int T = args.st.T, rl64 = args.st.Rlast / 64;
       int z, mt, sp;
       decode(args, lu, z, mt, sp);
       // the accumulator pair (d0: h*h, d1: the cross products) of this unit
       uint32_t d0, d1;
       int tf;
-      if (nbuf == 3) {
+      if (nbuf3) {
         // three regions of Nn columns, X = [0, Nn), Y = [Nn, 2 Nn), Z = [2 Nn, 3 Nn): d1 is
         // always Y, d0 alternates X, Z; the epilogue releases Y first, so the next unit
         // waits for half of the drain only
@@ -657,34 +684,35 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
         if (!mbar_wait(bar(kTrel + (local & 1)), (uint32_t)((local / 2) & 1) ^ 1u, status,
                        abort_flag))
           break;
-        d1 = tmem_base + (uint32_t)a0.region;
-        d0 = tmem_base + (uint32_t)((local & 1) ? 2 * a0.region : 0);
+        d1 = tmem_base + region;
+        d0 = tmem_base + ((local & 1) ? 2 * region : 0u);
       } else {
         const int acc = local % nbuf;
         const uint32_t acc_phase = (uint32_t)((local / nbuf) & 1);
         if (!mbar_wait(bar(kTempty + acc), acc_phase ^ 1u, status, abort_flag)) break;
         tf = acc;
-        d0 = tmem_base + (uint32_t)(acc * a0.buf_stride);
-        d1 = d0 + (uint32_t)args.Nn;  // second accumulator (kIntFrac)
+        d0 = tmem_base + (uint32_t)acc * buf_stride;
+        d1 = d0 + (uint32_t)((bcat ? 2 : 1) * nn);  // second accumulator (kIntFrac)
       }
       tc_fence_after();
       // symmetric mode: the K steps in the producer's order, K-major or transposed
       const int iters = unit_iters(args, sp);
+      const bool sym = sym_of(args);
       int rr = 0, cc = 0, jj = 0, nch = 0;
       if (sym) {
         jj = rr_partner(mt, 0, T);
-        nch = jj < T - 1 ? 2 : args.st.Rlast / 64;
+        nch = jj < T - 1 ? 2 : rl64;
       }
       for (int it = 0; it < iters; ++it) {
         if (!mbar_wait(bar(kFull + stage), phase, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t base = smem_u32(smem + (size_t)stage * stage_bytes);
-        const bool tr = args.a_mn || (sym && jj > mt);
+        const bool tr = amn || (sym && jj > mt);
         const uint32_t id = tr ? (idesc | (1u << 15)) : idesc;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           uint64_t ah, al;
-          if (args.a_il8) {  // two K-adjacent core-matrix columns (BM rows x 16 B) per step
+          if (il8) {  // two K-adjacent core-matrix columns (BM rows x 16 B) per step
             ah = sdesc_plain(base + k * 2 * BM * 16, BM * 16, 128);
             al = sdesc_plain(base + a_bytes + k * 2 * BM * 16, BM * 16, 128);
           } else if (tr) {
@@ -701,6 +729,9 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
             mma_f16<PAIR>(d0, ah, bh, id, first);
             mma_f16<PAIR>(d0, ah, bl, id, 1u);
             mma_f16<PAIR>(d0, al, bh, id, 1u);
+          } else if (bcat) {  // bh: the 2 Nn rows of both planes
+            mma_f16<PAIR>(d0, ah, bh, id, first);  // [h h | h f]
+            mma_f16<PAIR>(d1, al, bh, id, first);  // [f h | f f]
           } else {
             mma_f16<PAIR>(d0, ah, bh, id, first);  // integer x integer: exact
             mma_f16<PAIR>(d1, ah, bl, id, first);
@@ -714,7 +745,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
           cc = 0;
           if (++rr < T) {
             jj = rr_partner(mt, rr, T);
-            nch = jj < T - 1 ? 2 : args.st.Rlast / 64;
+            nch = jj < T - 1 ? 2 : rl64;
           }
         }
       }
@@ -741,29 +772,30 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       else mbar_arrive(bar(i));
     };
     int local = 0;
+    Walk wk = walk0();
     for (int u = cl; u < units; u += ncl, ++local) {
-      if (a0.epi_alt && (local % kEpiGroups) != eg) continue;  // another group's tile
+      if (epi_alt && (local % kEpiGroups) != eg) continue;  // another group's tile
       int lu;
-      const TcArgs& args = targs[locate(u, lu)];
+      const TcArgs& args = targs[locate(wk, u, lu)];
       const int glob = args.glob_exp ? *args.glob_exp : 0;
       // this group's 16-column chunks [ch0, ch1)
       const int nch = args.Nn / 16;
-      const int hch = a0.epi_alt ? nch : (nch + kEpiGroups - 1) / kEpiGroups;
-      const int ch0 = a0.epi_alt ? 0 : eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
+      const int hch = epi_alt ? nch : (nch + kEpiGroups - 1) / kEpiGroups;
+      const int ch0 = epi_alt ? 0 : eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
       int z, mt, sp;
       decode(args, lu, z, mt, sp);
       int tf;
       uint32_t tf_phase, c0off, c1off;
-      if (nbuf == 3) {
+      if (nbuf3) {
         tf = 0;
         tf_phase = (uint32_t)(local & 1);
-        c0off = (uint32_t)((local & 1) ? 2 * a0.region : 0);
-        c1off = (uint32_t)a0.region;
+        c0off = (local & 1) ? 2 * region : 0u;
+        c1off = region;
       } else {
         tf = local % nbuf;
         tf_phase = (uint32_t)((local / nbuf) & 1);
-        c0off = (uint32_t)(tf * a0.buf_stride);
-        c1off = c0off + (uint32_t)args.Nn;
+        c0off = (uint32_t)tf * buf_stride;
+        c1off = c0off + (uint32_t)((bcat ? 2 : 1) * args.Nn);
       }
       // everything that needs no accumulator (exponents, the factor table) is looked up
       // before waiting for it, while the tile's MMAs run
@@ -772,7 +804,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
       bool valid = row < args.M && z < args.z_count;
-      if (args.sym) {
+      if (args.sym || args.a_z_unit) {  // the unit is one slice z
         rP = z;
         rmu = row;
         valid = row < args.Nrow && z < args.z_count;
@@ -869,6 +901,10 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
           }
         }
       };
+      // bcat (Nn <= 64, so always drained through registers below): the value is
+      // h h + ((h f + f h) + f f), columns c of the left halves and Nn + c of the right halves
+      // of the two accumulators
+      const uint32_t nnc = (uint32_t)args.Nn;
       auto load = [&](int c0, float (&a)[16]) {
         uint32_t r[16];
         tmem_ld16(t0 + (uint32_t)c0, r);
@@ -881,14 +917,15 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
         }
       };
 
-      constexpr int kKeep = (kMaxRegCols / 16 + kEpiGroups - 1) / kEpiGroups;  // chunks held
-      if (args.Nn <= kMaxRegCols) {
+      // chunks held (bcat: Nn <= 64, four chunks at most)
+      constexpr int kKeep = bcat ? 4 : (kMaxRegCols / 16 + kEpiGroups - 1) / kEpiGroups;
+      if (bcat || args.Nn <= kMaxRegCols) {
         // drain the accumulators into registers, hand TMEM back, then write.  nbuf 3: the
         // cross products (region Y) first, all in flight together, then Y is released and the
         // integer products (X or Z) are added chunk by chunk; otherwise both accumulators
         // chunk by chunk
         float keep[kKeep * 16];
-        if (nbuf == 3) {
+        if (nbuf3) {
 #pragma unroll
           for (int k = 0; k < kKeep; ++k)
             if (ch0 + k < ch1) tmem_ld16_nowait(t1 + (uint32_t)((ch0 + k) * 16), keep + k * 16);
@@ -899,26 +936,39 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
         for (int k = 0; k < kKeep; ++k) {
           if (ch0 + k < ch1) {
             const uint32_t c = (uint32_t)((ch0 + k) * 16);
-            if (nbuf == 3) {
+            if (nbuf3) {
               float tmp[16];
               tmem_ld16_nowait(t0 + c, tmp);
               tmem_wait_ld();
 #pragma unroll
               for (int j = 0; j < 16; ++j) keep[k * 16 + j] = tmp[j] + keep[k * 16 + j];
-            } else {
+            } else if (NUM == kSplit3) {
               tmem_ld16_nowait(t0 + c, keep + k * 16);
-              if (NUM != kSplit3) {
-                float tmp[16];
+            } else {
+              // the cross products, then the exact h h added last: t0 + t1, or with the
+              // planes of B concatenated h h + ((h f + f h) + f f)
+              float tmp[16];
+              const bool cat = bcat;
+              tmem_ld16_nowait((cat ? t0 + nnc : t1) + c, keep + k * 16);
+              if (cat) {
                 tmem_ld16_nowait(t1 + c, tmp);
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) keep[k * 16 + j] += tmp[j];
+                tmem_ld16_nowait(t1 + nnc + c, tmp);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) keep[k * 16 + j] += tmp[j];
               }
+              tmem_ld16_nowait(t0 + c, tmp);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 16; ++j) keep[k * 16 + j] = tmp[j] + keep[k * 16 + j];
             }
           }
         }
         tmem_wait_ld();
-        release(nbuf == 3 ? kTrel + (local & 1) : kTempty + tf);
+        release(nbuf3 ? kTrel + (local & 1) : kTempty + tf);
 #pragma unroll
         for (int k = 0; k < kKeep; ++k) {
           if (ch0 + k < ch1) {
@@ -1120,6 +1170,9 @@ bool tmem_plan(int nn, int per_set, bool intfrac, int& nbuf, int& stride, int& e
 template <int BK, int NUM, int PAIR>
 cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
                       const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
+  if constexpr (NUM == kIntFrac && !PAIR) {
+    if (2 * a.Nn <= 128) return launch_tc<BK, kIntFracCat, 0>(ah, al, bh, bl, a, s);
+  }
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)(PAIR ? a.Nn / 2 : a.Nn) * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   // the 227 KB opt-in limit, less alignment, barriers and the epilogue's factor tables
@@ -1128,8 +1181,9 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   if (stages > 8) stages = 8;
   if (stages < 2) stages = 2;
   a.stages = stages;
-  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart), sets as tmem_plan says
-  const int per_set = (NUM != kSplit3 ? 2 : 1) * a.Nn;
+  // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart; of 2 Nn columns each
+  // with the planes of B concatenated), sets as tmem_plan says
+  const int per_set = (NUM != kSplit3 ? 2 : 1) * (NUM == kIntFracCat ? 2 : 1) * a.Nn;
   a.tmem_cols = 512;
   if (!tmem_plan(a.Nn, per_set, NUM != kSplit3, a.nbuf, a.buf_stride, a.epi_alt))
     return cudaErrorInvalidValue;
@@ -1330,6 +1384,36 @@ __global__ void k_split_B_sym(const double* __restrict__ B, int layout, long lon
     }
     const size_t o = (size_t)P * st.perP + sym_tile_off(st, ti, tj) +
                      ((size_t)c * Ri + r) * 64 + (size_t)((j8 ^ (r & 7)) * 8);
+    *(uint4*)(H + o) = *(const uint4*)hv;
+    *(uint4*)(F + o) = *(const uint4*)fv;
+  }
+}
+
+// Bt^P 2^-t_P -> integer + fraction planes in the dense storage, [P][mu][ld] (columns
+// nu >= N zero).  One thread per 8 consecutive stored elements of a row.
+__global__ void k_split_B_dense(const double* __restrict__ B, int layout, long long Q, int N,
+                                int ld, const int* __restrict__ eS,
+                                const double* __restrict__ tmax, double invT, __half* H,
+                                __half* F) {
+  const long long npk = (long long)N * (N + 1) / 2;
+  const int n8 = ld / 8;
+  const long long tot = Q * N * n8;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j8 = (int)(i % n8);
+    const long long row = i / n8;  // P * N + mu
+    const long long P = row / N;
+    const int mu = (int)(row % N);
+    const int tP = intfrac_exponent_inv(tmax[P], invT);
+    __align__(16) __half hv[8], fv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int nu = j8 * 8 + k;
+      double y = 0.0;
+      if (nu < N) y = ldexp(load_B_elem(B, layout, P, row, mu, nu, N, npk), -tP - eS[mu] - eS[nu]);
+      intfrac_split(y, hv[k], fv[k]);
+    }
+    const size_t o = (size_t)row * ld + (size_t)j8 * 8;
     *(uint4*)(H + o) = *(const uint4*)hv;
     *(uint4*)(F + o) = *(const uint4*)fv;
   }
@@ -1705,11 +1789,19 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   k_sym_exps<<<num_sms() * 4, 256, 0, s>>>((const double*)(ws + L.tmax),
                                            (const int*)(ws + L.eS), d.Q, d.N,
                                            intfrac_inv_target(d.N), (int*)(ws + L.eB));
-  k_split_B_sym<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, sym_tiles(d.N), hdr,
-                                              (const int*)(ws + L.eS),
-                                              (const double*)(ws + L.tmax),
-                                              intfrac_inv_target(d.N), (__half*)(ws + L.Bhi),
-                                              (__half*)(ws + L.Blo));
+  const SymTiles st = sym_tiles(d.N);
+  if (st.dense)
+    k_split_B_dense<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, st.ld,
+                                                  (const int*)(ws + L.eS),
+                                                  (const double*)(ws + L.tmax),
+                                                  intfrac_inv_target(d.N), (__half*)(ws + L.Bhi),
+                                                  (__half*)(ws + L.Blo));
+  else
+    k_split_B_sym<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, st, hdr,
+                                                (const int*)(ws + L.eS),
+                                                (const double*)(ws + L.tmax),
+                                                intfrac_inv_target(d.N), (__half*)(ws + L.Bhi),
+                                                (__half*)(ws + L.Blo));
   count_launch(5);
   return cudaGetLastError();
 }
@@ -1824,9 +1916,10 @@ int run_lambda_tc(const Dims& d, const double* C, char* ws, const Layout& L, dou
                               N, ws, L, s);
 }
 
-// Arguments and maps of (1) X = B C_act for slices p0 .. p0+np-1: A operand the symmetric
-// tile storage of the split B (bulk copies, BK = 64), B operand (diag(2^s) C_act)^T; unit =
-// (slice, row tile of 128 AO indices); outputs the X and X^T splits (mode 1).
+// Arguments and maps of (1) X = B C_act for slices p0 .. p0+np-1: A operand the split B in
+// its symmetric tile storage (bulk copies) or dense (TMA), BK = 64, B operand
+// (diag(2^s) C_act)^T; unit = (slice, row tile of 128 AO indices); outputs the X and X^T
+// splits (mode 1).
 bool half_setup(const Dims& d, int p0, int np, const TuneCode& tv, char* ws, const Layout& L,
                 TcArgs& a, TcMaps& m) {
   DevHeader* hdr = (DevHeader*)(ws + L.header);
@@ -1838,17 +1931,34 @@ bool half_setup(const Dims& d, int p0, int np, const TuneCode& tv, char* ws, con
   if (!make_map(&m.bh, ws + L.ChiS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows) ||
       !make_map(&m.bl, ws + L.CloS, N, Ap, 1, Np * h2, (uint64_t)Ap * Np * h2, bk, brows))
     return false;
-  m.ah = m.bh;  // unused: the A tiles come from the bulk copies
-  m.al = m.bl;
   a = TcArgs{};
-  a.mode = 1; a.M = st.T * BM; a.Nn = Ap;
+  a.mode = 1; a.Nn = Ap;
   a.m_tiles = st.T; a.z_count = np; a.splits = 1;
-  a.kt_per_kb = 1; a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
-  a.sym = 1; a.st = st;
-  // whole slices at once (the partner row tiles of a slice read their shared stored tile
-  // in the same round, so the second read can hit L2); a pair takes two slices' row tiles
+  a.nkb = 1; a.a_z_kb = 0; a.b_z_mode = 0;
+  a.st = st;
   const int work = tv.pair ? num_sms() / 2 : num_sms();
-  a.grid = (tv.full || work < st.T) ? work : work / st.T * st.T;
+  if (st.dense) {
+    // dense slices: A through a 3-D map [np][N][ld] with boxes of 64 x 128 (zero fill past N
+    // in both directions); unit = (slice, row tile), K steps of 64 in order
+    const char* bh = ws + L.Bhi + (size_t)p0 * st.perP * h2;
+    const char* bl = ws + L.Blo + (size_t)p0 * st.perP * h2;
+    if (!make_map(&m.ah, bh, N, N, np, (uint64_t)st.ld * h2, (uint64_t)st.perP * h2, bk, BM) ||
+        !make_map(&m.al, bl, N, N, np, (uint64_t)st.ld * h2, (uint64_t)st.perP * h2, bk, BM))
+      return false;
+    a.M = N;
+    a.kt_per_kb = (N + bk - 1) / bk;
+    a.sym = 0; a.a_z_unit = 1;
+    a.grid = work;
+  } else {
+    m.ah = m.bh;  // unused: the A tiles come from the bulk copies
+    m.al = m.bl;
+    a.M = st.T * BM;
+    a.kt_per_kb = 1;
+    a.sym = 1;
+    // whole slices at once (the partner row tiles of a slice read their shared stored tile
+    // in the same round, so the second read can hit L2); a pair takes two slices' row tiles
+    a.grid = (tv.full || work < st.T) ? work : work / st.T * st.T;
+  }
   a.a_tiled_h = (const __half*)(ws + L.Bhi) + (size_t)p0 * st.perP;
   a.a_tiled_f = (const __half*)(ws + L.Blo) + (size_t)p0 * st.perP;
   a.eA = (const int*)(ws + L.eB) + (size_t)p0 * N; a.eA_zstride = 0;
@@ -2066,7 +2176,8 @@ bool tc_group_setup(int kind, const Dims& d, char* ws, const Layout& L, void* a_
 // Kernel-wide settings of a grouped contraction from its widest instance (as launch_tc sets
 // them for one), written into every instance's arguments together with the batch's status
 // and abort words; returns the dynamic shared memory of the launch.
-size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag) {
+size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abort_flag,
+                       int& cat) {
   TcArgs* a = (TcArgs*)a_recs;
   const int BK = kind == GK_TC_G ? 32 : 64;
   int nn = 16;
@@ -2076,7 +2187,8 @@ size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abor
   int stages = (int)((232448 - 1024 - 512 - kTabBytes) / stage_bytes);
   stages = stages > 8 ? 8 : (stages < 2 ? 2 : stages);
   int nbuf, stride, epi_alt;
-  tmem_plan(nn, 2 * nn, true, nbuf, stride, epi_alt);
+  cat = 2 * nn <= 128 ? 1 : 0;  // kIntFracCat for every instance of the launch
+  tmem_plan(nn, (cat ? 4 : 2) * nn, true, nbuf, stride, epi_alt);
   for (int i = 0; i < ninst; ++i) {
     a[i].stages = stages;
     a[i].tmem_cols = 512;
@@ -2092,28 +2204,30 @@ size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abor
   return smem < 120 * 1024 ? 120 * 1024 : smem;
 }
 
+template <int BK, int NUM>
+cudaError_t launch_group_bk(const TcArgs* targs, const TcMaps* tmaps, const int* ustart,
+                            int ninst, int grid, size_t smem, cudaStream_t s) {
+  const cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_group<BK, NUM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_gemm_group<BK, NUM><<<grid, kThreads, smem, s>>>(targs, tmaps, ustart, ninst);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_group(int kind, const void* args_dev, const void* maps_dev,
-                            const int* ustart, int ninst, int units, size_t smem,
+                            const int* ustart, int ninst, int units, size_t smem, int cat,
                             cudaStream_t s) {
   const TcArgs* targs = (const TcArgs*)args_dev;
   const TcMaps* tmaps = (const TcMaps*)maps_dev;
   int grid = num_sms();
   if (grid > units) grid = units;
   if (grid < 1) grid = 1;
-  cudaError_t e;
-  if (kind == GK_TC_G) {
-    e = cudaFuncSetAttribute(k_tc_gemm_group<32, kIntFrac>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm_group<32, kIntFrac><<<grid, kThreads, smem, s>>>(targs, tmaps, ustart, ninst);
-  } else {
-    e = cudaFuncSetAttribute(k_tc_gemm_group<64, kIntFrac>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm_group<64, kIntFrac><<<grid, kThreads, smem, s>>>(targs, tmaps, ustart, ninst);
-  }
-  count_launch(1);
-  return cudaGetLastError();
+  if (kind == GK_TC_G)
+    return cat ? launch_group_bk<32, kIntFracCat>(targs, tmaps, ustart, ninst, grid, smem, s)
+               : launch_group_bk<32, kIntFrac>(targs, tmaps, ustart, ninst, grid, smem, s);
+  return cat ? launch_group_bk<64, kIntFracCat>(targs, tmaps, ustart, ninst, grid, smem, s)
+             : launch_group_bk<64, kIntFrac>(targs, tmaps, ustart, ninst, grid, smem, s);
 }
 
 size_t tc_args_bytes() { return sizeof(TcArgs); }
