@@ -5,7 +5,7 @@
 // step of the build is one launch for all instances together -- a grouped kernel finds its
 // instance and its block within that instance's grid from a table, and the tensor-core
 // contractions walk one sequence of work units that spans every instance -- so a batched
-// build with its adjoint is 26 launches whatever the number of instances.  The tables (the
+// build with its adjoint is 24 launches whatever the number of instances.  The tables (the
 // instances' records, the grids of every step, the tensor-core arguments and tensor maps)
 // are built on the host and copied into the head of the batched workspace when the call's
 // arguments change.
@@ -167,15 +167,14 @@ dim3 kind_grid(int kind, const Dims& d, const donof_instance& x, bool backward) 
   const int np = d.Q, sp3 = d.splits < np ? d.splits : np, N = d.N, A = d.A, Ap = d.Ap;
   const bool lam = x.lam != nullptr;
   switch (kind) {
-    case GK_ZERO: {
-      const long long big = std::max<long long>(std::max<long long>((long long)N * N, (long long)A * A),
-                                                (long long)A * (d.ng > 0 ? d.ng : 1));
-      return dim3(std::min(64, std::max(1, ceil_div(big * 8 / 4, 256))), 8, 1);
+    case GK_ZERO: {  // every range of the instance strided over one grid, 16 words a thread
+      const long long words = 1 + 2 + 3LL * A * (d.ng > 0 ? d.ng : 0) * 2 + 4LL * A * A +
+                              (lam ? 2LL * N * N : 0);
+      return dim3(std::max(1, ceil_div(words, 256 * 16)), 1, 1);
     }
     case GK_OCC: return dim3(1, 1, 1);
     case GK_COEF: return dim3(ceil_div((long long)Ap * Ap, 256), 1, 1);
-    case GK_CNORM_C: return dim3(ceil_div(N > Ap ? N : Ap, 32), 3, 1);
-    case GK_SPLIT_C: return dim3(ceil_div(d.Np, 32), ceil_div(N > Ap ? N : Ap, 32), 3);
+    case GK_SPLIT_C: return dim3(ceil_div(N > Ap ? N : Ap, 32), 3, 1);  // norms + split
     case GK_SUM_HC: return dim3(std::min(1216, ceil_div((long long)N * A, 256)), 1, 1);
     case GK_GRAM_PART: return dim3(ceil_div(N, 32), ceil_div(A, 16), 1);
     case GK_GRAM_FINAL: return dim3(A, 1, 1);
@@ -183,14 +182,12 @@ dim3 kind_grid(int kind, const Dims& d, const donof_instance& x, bool backward) 
     case GK_XEXP: return dim3(std::max(1, ceil_div((long long)sp3 * N, 256)), 2, 1);
     case GK_DIAGW: return dim3(ceil_div(np, 16), 1, 1);
     case GK_KPART: return dim3(ceil_div((long long)A * (Ap / 4), 256), sp3, 1);
-    case GK_JKEY: return dim3(std::max(1, ceil_div((long long)sp3 * Ap, 8)), 2, 1);
+    case GK_JKEY: return dim3(ceil_div((long long)A * A, 256) + ceil_div((long long)sp3 * Ap, 8), 1, 1);
     case GK_YQUANT: return dim3(std::min(np, 1216), 1, 1);
     case GK_REDUCEG: return dim3(ceil_div((long long)N * (Ap / 4), 256), 1, 1);
     case GK_EROWS: return dim3(ceil_div(A, 8), 1, 1);
     case GK_EFINAL: return dim3(ceil_div(d.ng + 1, 8), 1, 1);
-    case GK_CNORM_L: return lam ? dim3(ceil_div(N > Ap ? N : Ap, 32), 2, 1) : dim3(0, 1, 1);
-    case GK_SPLIT_L:
-      return lam ? dim3(ceil_div(d.Np, 32), ceil_div(N > Ap ? N : Ap, 32), 2) : dim3(0, 1, 1);
+    case GK_SPLIT_L: return lam ? dim3(ceil_div(N > Ap ? N : Ap, 32), 2, 1) : dim3(0, 1, 1);
     case GK_SUM_L: return lam ? dim3(std::min(1216, ceil_div((long long)N * A, 256)), 1, 1)
                               : dim3(0, 1, 1);
     case GK_BWD: return (backward && x.dE_dC) ? dim3(std::min(608, ceil_div((long long)N * N, 256)), 1, 1)
@@ -251,7 +248,7 @@ int build_plan(int32_t ninst, const donof_problem* probs, const donof_instance* 
   }
   pl.threads[GK_OCC] = dim3((max_A + 31) / 32 * 32);
   pl.smem[GK_OCC] = (size_t)max_ng * 2 * sizeof(double);
-  pl.threads[GK_CNORM_C] = pl.threads[GK_CNORM_L] = dim3(1024);
+  pl.threads[GK_SPLIT_C] = pl.threads[GK_SPLIT_L] = dim3(1024);
   pl.threads[GK_YQUANT] = dim3(max_Ap / 4, 8);
   // tensor-core records
   for (int t = 0; t < kTcKinds; ++t) {
@@ -296,16 +293,17 @@ int enqueue_grouped(int32_t ninst, char* ws, int32_t flags, const Plan& pl, cuda
       if (pl.blocks[k] == 0) continue;
       const int* start = grids + (size_t)k * (4 * ninst + 1);
       const GroupLaunch g{inst_dev, start, start + ninst + 1, ninst};
+      const int blocks = pl.blocks[k];
       switch (k) {
         case GK_ZERO: case GK_OCC: case GK_COEF: case GK_HDIAG: case GK_EROWS: case GK_EFINAL:
         case GK_BWD:
-          e = launch_fp64_group(k, g, pl.blocks[k], pl.threads[k].x, pl.smem[k], s);
+          e = launch_fp64_group(k, g, blocks, pl.threads[k].x, pl.smem[k], s);
           break;
         case GK_DIAGW: case GK_KPART: case GK_JKEY: case GK_YQUANT:
-          e = launch_mid_group(k, g, pl.blocks[k], pl.threads[k], s);
+          e = launch_mid_group(k, g, blocks, pl.threads[k], s);
           break;
         default:
-          e = launch_tc_small_group(k, g, pl.blocks[k], pl.threads[k].x, s);
+          e = launch_tc_small_group(k, g, blocks, pl.threads[k].x, s);
       }
     }
     if (e != cudaSuccess) return DONOF_ERR_CUDA;

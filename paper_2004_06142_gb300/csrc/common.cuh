@@ -147,10 +147,9 @@ __device__ __forceinline__ int group_locate(const GroupLaunch& g, Blk& b) {
 
 // The grouped launches of one batched build, in order (batch.cu builds their grids).
 enum GroupKind {
-  GK_ZERO, GK_OCC, GK_COEF, GK_CNORM_C, GK_SPLIT_C, GK_TC_HC, GK_SUM_HC, GK_GRAM_PART,
-  GK_GRAM_FINAL, GK_HDIAG, GK_XEXP, GK_TC_HALF, GK_TC_B, GK_DIAGW, GK_KPART, GK_JKEY,
-  GK_YQUANT, GK_TC_G, GK_REDUCEG, GK_EROWS, GK_EFINAL, GK_CNORM_L, GK_SPLIT_L, GK_TC_LAM,
-  GK_SUM_L, GK_BWD, GK_COUNT
+  GK_ZERO, GK_OCC, GK_COEF, GK_SPLIT_C, GK_TC_HC, GK_SUM_HC, GK_GRAM_PART, GK_GRAM_FINAL,
+  GK_HDIAG, GK_XEXP, GK_TC_HALF, GK_TC_B, GK_DIAGW, GK_KPART, GK_JKEY, GK_YQUANT, GK_TC_G,
+  GK_REDUCEG, GK_EROWS, GK_EFINAL, GK_SPLIT_L, GK_TC_LAM, GK_SUM_L, GK_BWD, GK_COUNT
 };
 // Host launchers of the grouped kernels (blocks: the flat grid; threads, smem per block).
 cudaError_t launch_fp64_group(int kind, const GroupLaunch& g, int blocks, int threads,

@@ -647,22 +647,16 @@ __global__ void k_zero_group(const GroupLaunch g) {
   const Layout& L = I.L;
   DevHeader* hdr = (DevHeader*)(I.ws + L.header);
   const size_t jac = (size_t)d.A * (d.ng > 0 ? d.ng : 0) * 8, aa = (size_t)d.A * d.A * 8;
-  void* p = nullptr;
-  size_t bytes = 0;
-  switch (b.y) {
-    case 0: p = &hdr->abort_flag; bytes = 4; break;
-    case 1: p = I.ws + L.dn; bytes = jac; break;
-    case 2: p = I.ws + L.dsq; bytes = jac; break;
-    case 3: p = I.ws + L.dphi; bytes = jac; break;
-    case 4: p = &hdr->sC2; bytes = 8; break;
-    case 5: p = I.ws + L.J; bytes = aa; break;
-    case 6: p = I.ws + L.K; bytes = aa; break;
-    case 7: p = I.lam; bytes = I.lam ? (size_t)d.N * d.N * 8 : 0; break;
+  // the instance's ranges, each strided over all of its threads
+  void* const p[8] = {&hdr->abort_flag, I.ws + L.dn, I.ws + L.dsq, I.ws + L.dphi, &hdr->sC2,
+                      I.ws + L.J, I.ws + L.K, I.lam};
+  const size_t bytes[8] = {4, jac, jac, jac, 8, aa, aa, I.lam ? (size_t)d.N * d.N * 8 : 0};
+  const size_t t0 = (size_t)b.x * blockDim.x + threadIdx.x, nt = (size_t)b.gx * blockDim.x;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    uint32_t* w = (uint32_t*)p[r];
+    for (size_t i = t0; i < bytes[r] / 4; i += nt) w[i] = 0u;
   }
-  uint32_t* w = (uint32_t*)p;
-  for (size_t i = (size_t)b.x * blockDim.x + threadIdx.x; i < bytes / 4;
-       i += (size_t)b.gx * blockDim.x)
-    w[i] = 0u;
 }
 }  // namespace
 

@@ -125,8 +125,12 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
                                                int Ap, int splits, double* K, double* J,
                                                int* eY) {
   const int AA = A * A;
-  if (B_.y == 0) {
-    for (int i = B_.x * blockDim.x + threadIdx.x; i < AA; i += B_.gx * blockDim.x) {
+  // blocks x < n0: the K, J sums (a thread per entry); the others: the exponents
+  const int n0 = (AA + blockDim.x - 1) / blockDim.x;
+  if (B_.x < n0) {
+    {
+      const int i = B_.x * blockDim.x + threadIdx.x;
+      if (i >= AA) return;
       double k = 0.0, j = 0.0;
       int sp = 0;
       for (; sp + 8 <= splits; sp += 8) {  // eight splits in flight, summed in order
@@ -151,11 +155,11 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
     }
     return;
   }
-  // B_.y = 1: one warp per (split, row p), rows p >= A get exponent 0
+  // one warp per (split, row p), rows p >= A get exponent 0
   const int lane = threadIdx.x % 32;
   const int nrow = splits * Ap;
-  for (int t = (B_.x * blockDim.x + threadIdx.x) / 32; t < nrow;
-       t += B_.gx * blockDim.x / 32) {
+  for (int t = ((B_.x - n0) * blockDim.x + threadIdx.x) / 32; t < nrow;
+       t += (B_.gx - n0) * blockDim.x / 32) {
     const int sp = t / Ap, p = t % Ap;
     double ss = 0.0;
     if (p < A) {
@@ -321,7 +325,7 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
                                                          (double*)(ws + L.Ksp),
                                                          (double*)(ws + L.Jsp));
   const int ncta_e = (splits * Ap + 7) / 8;  // a warp per (split, row) of the exponents
-  k_jk_eY<<<dim3(ncta_e > sm_count() ? ncta_e : sm_count(), 2), 256, 0, s>>>((const double*)(ws + L.Ksp),
+  k_jk_eY<<<(A * A + 255) / 256 + ncta_e, 256, 0, s>>>((const double*)(ws + L.Ksp),
                                              (const double*)(ws + L.Jsp), D, W, BcF, np, A, Ap,
                                              splits, (double*)(ws + L.K), (double*)(ws + L.J),
                                              (int*)(ws + L.eY));

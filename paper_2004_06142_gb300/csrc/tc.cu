@@ -1552,6 +1552,91 @@ __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
   k_split_T_body(native_blk(), jobs, Np);
 }
 
+// Column norms and split of one job at once (grouped launches): a CTA of 32 x 32 threads per
+// job and 32 columns c: the norms as k_colnorms forms them (same order), the exponents kept
+// in shared memory, then the split of those columns as k_split_T forms it, warp w writing the
+// 32-wide chunks of mu = 32 w, 32 (w + 32), ... (the columns come from L1 after the norms).
+__device__ __forceinline__ void k_colsplit_body(const Blk& B_, SplitJobs jobs, double invT,
+                                                DevHeader* hdr, int Np) {
+  const SplitJob& jb = jobs.j[B_.y];
+  const int c0 = B_.x * 32;
+  if (c0 >= jb.nrows_out) return;  // uniform over the CTA
+  __shared__ double red[32][33];
+  __shared__ int ecol[32];
+  const double* __restrict__ S = jb.S;
+  const int* __restrict__ eS = jb.eS;
+  const long long ld = jb.ld;
+  const int N = jb.N;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  {
+    const int c = c0 + tx;
+    double ss = 0.0;
+    if (c < jb.ncols) {
+      int mu = ty;
+      for (; mu + 96 < N; mu += 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = S[(size_t)(mu + 32 * u) * ld + c];
+          if (eS) v[u] *= pow2d(eS[mu + 32 * u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ss = fma(v[u], v[u], ss);
+      }
+      for (; mu < N; mu += 32) {
+        double v = S[(size_t)mu * ld + c];
+        if (eS) v *= pow2d(eS[mu]);
+        ss = fma(v, v, ss);
+      }
+    }
+    red[ty][tx] = ss;
+    __syncthreads();
+    if (ty == 0) {
+      int e = 0;
+      if (c < jb.nrows_out) {
+        double t = 0.0;
+        for (int g = 0; g < 32; ++g) t += red[g][tx];
+        const double nr = sqrt(t);
+        if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
+        e = intfrac_exponent_inv(nr, invT);
+        jb.e[c] = e;
+        if (jb.norm) jb.norm[c] = nr;
+      }
+      ecol[tx] = e;
+    }
+    __syncthreads();
+  }
+  const int ncl = min(32, jb.nrows_out - c0);
+  for (int mu = ty * 32 + tx; mu - tx < Np; mu += 32 * 32) {
+    if (mu >= Np) continue;
+    const double smu = (eS && mu < N) ? pow2d(eS[mu]) : 1.0;
+    for (int cc = 0; cc < ncl; ++cc) {
+      const int c = c0 + cc;
+      const double v = (mu < N && c < jb.ncols) ? S[(size_t)mu * ld + c] * smu : 0.0;
+      const size_t o = (size_t)c * Np + mu;
+      const double y = v * pow2d(-ecol[cc]);
+      __half h, f;
+      intfrac_split(y, h, f);
+      if (jb.H) {
+        jb.H[o] = h;
+        jb.F[o] = f;
+      }
+      if (jb.planes) {
+        const __half r = __double2half((y - (double)__half2float(h)) - (double)__half2float(f));
+        const __half z = __float2half_rn(0.f);
+        const size_t ps = (size_t)jb.nrows_out * Np;
+        if (jb.planes == 1) {
+          jb.PH[o] = h; jb.PH[ps + o] = z; jb.PH[2 * ps + o] = z; jb.PH[3 * ps + o] = z;
+          jb.PF[o] = z; jb.PF[ps + o] = h; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = r;
+        } else {
+          jb.PH[o] = h; jb.PH[ps + o] = r; jb.PH[2 * ps + o] = h; jb.PH[3 * ps + o] = h;
+          jb.PF[o] = z; jb.PF[ps + o] = f; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = f;
+        }
+      }
+    }
+  }
+}
+
 // The splits of a build's prep phase: C_act^T for b (and its residual planes, the V side of
 // h C_act), diag(2^s) C_act for the symmetric half transform (with_half_transform), and
 // h^T = h (the U side of h C_act).
@@ -1677,12 +1762,10 @@ __device__ __forceinline__ void k_x_exponents_body(const Blk& B_, const double* 
                               int Ap, double invT, int* eXt, const double* __restrict__ rn2,
                               const DevHeader* hdr, int np, int splits, int N, double invT2,
                               int* spOf, int* eX3) {
-  if (B_.y == 0) {
-    for (int P = B_.x; P < np; P += B_.gx) {
-      const double l = L1max[P];
-      for (int q = threadIdx.x; q < Ap; q += blockDim.x)
-        eXt[(size_t)P * Ap + q] = intfrac_exponent_inv(l * cnorm[q], invT);
-    }
+  if (B_.y == 0) {  // a thread per (P, q)
+    for (long long i = B_.x * (long long)blockDim.x + threadIdx.x; i < (long long)np * Ap;
+         i += (long long)B_.gx * blockDim.x)
+      eXt[i] = intfrac_exponent_inv(L1max[i / Ap] * cnorm[i % Ap], invT);
     return;
   }
   const double sC2 = hdr->sC2;
@@ -2090,19 +2173,12 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
 namespace donof {
 namespace {
 __device__ __forceinline__ int grp_splits(const Dims& d) { return d.splits < d.Q ? d.splits : d.Q; }
-__global__ void __launch_bounds__(1024) k_colnorms_group(const GroupLaunch g, int which) {
+__global__ void __launch_bounds__(1024) k_colsplit_group(const GroupLaunch g, int which) {
   Blk b;
   const InstRec& I = g.inst[group_locate(g, b)];
   const SplitJobs jobs = which == 0 ? split_c_jobs(I.d, I.L, I.ws, I.C, I.h, true)
                                     : lambda_jobs(I.d, I.L, I.ws, I.C);
-  k_colnorms_body(b, jobs, intfrac_inv_target(I.d.N), (DevHeader*)(I.ws + I.L.header));
-}
-__global__ void __launch_bounds__(256) k_split_T_group(const GroupLaunch g, int which) {
-  Blk b;
-  const InstRec& I = g.inst[group_locate(g, b)];
-  const SplitJobs jobs = which == 0 ? split_c_jobs(I.d, I.L, I.ws, I.C, I.h, true)
-                                    : lambda_jobs(I.d, I.L, I.ws, I.C);
-  k_split_T_body(b, jobs, I.d.Np);
+  k_colsplit_body(b, jobs, intfrac_inv_target(I.d.N), (DevHeader*)(I.ws + I.L.header), I.d.Np);
 }
 __global__ void __launch_bounds__(256) k_gram_part_group(const GroupLaunch g) {
   Blk b;
@@ -2236,10 +2312,8 @@ size_t tc_maps_bytes() { return sizeof(TcMaps); }
 cudaError_t launch_tc_small_group(int kind, const GroupLaunch& g, int blocks, int threads,
                                   cudaStream_t s) {
   switch (kind) {
-    case GK_CNORM_C: k_colnorms_group<<<blocks, threads, 0, s>>>(g, 0); break;
-    case GK_SPLIT_C: k_split_T_group<<<blocks, threads, 0, s>>>(g, 0); break;
-    case GK_CNORM_L: k_colnorms_group<<<blocks, threads, 0, s>>>(g, 1); break;
-    case GK_SPLIT_L: k_split_T_group<<<blocks, threads, 0, s>>>(g, 1); break;
+    case GK_SPLIT_C: k_colsplit_group<<<blocks, threads, 0, s>>>(g, 0); break;
+    case GK_SPLIT_L: k_colsplit_group<<<blocks, threads, 0, s>>>(g, 1); break;
     case GK_GRAM_PART: k_gram_part_group<<<blocks, threads, 0, s>>>(g); break;
     case GK_GRAM_FINAL: k_gram_final_group<<<blocks, threads, 0, s>>>(g); break;
     case GK_XEXP: k_x_exponents_group<<<blocks, threads, 0, s>>>(g); break;

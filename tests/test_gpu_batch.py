@@ -106,5 +106,5 @@ def test_grouped_launch_count():
     n0 = dn.donof_launch_count()
     batch.run(dn.BATCH_BACKWARD | dn.BATCH_STREAMS)
     streams = dn.donof_launch_count() - n0
-    assert grouped == 26
+    assert grouped == 24
     assert streams == 12 * 25
