@@ -145,6 +145,11 @@ __device__ __forceinline__ int group_locate(const GroupLaunch& g, Blk& b) {
   return lo;
 }
 
+// Slices per CTA of k_diag_w (mid.cu): few in a single build, so that the latency-bound kernel
+// has CTAs enough; more in a grouped launch, which has many instances to spread over the SMs.
+constexpr int kDiagWSlices = 4;
+constexpr int kDiagWGroupSlices = 16;
+
 // The grouped launches of one batched build, in order (batch.cu builds their grids).
 enum GroupKind {
   GK_ZERO, GK_OCC, GK_COEF, GK_SPLIT_C, GK_TC_HC, GK_SUM_HC, GK_GRAM_PART, GK_GRAM_FINAL,

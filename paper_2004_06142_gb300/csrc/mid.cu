@@ -26,7 +26,7 @@ __device__ __forceinline__ float pow2f_m(int e) {
 // the b contraction wrote into D: the group's d in shared memory, thread p forms w_p of
 // every slice of the group (Acoef is symmetric, so its column p is read, coalesced across
 // threads).
-constexpr int kDwSlices = 16;
+template <int kDwSlices>
 __device__ __forceinline__ void k_diag_w_body(const Blk& B_, const float* __restrict__ D, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
                                                 float* W) {
@@ -63,10 +63,12 @@ __device__ __forceinline__ void k_diag_w_body(const Blk& B_, const float* __rest
 __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
                                                 float* W) {
-  k_diag_w_body(native_blk(), D, np, A, Ap, AcF, W);
+  k_diag_w_body<kDiagWSlices>(native_blk(), D, np, A, Ap, AcF, W);
 }
 
-// Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread.
+// Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread, for the
+// quads with p0 <= q only (K and J are symmetric: every entry with p <= q is formed, read by
+// k_jk_eY for its mirror too, so that b is read on and below the diagonal only).
 __device__ __forceinline__ void k_kpart_body(const Blk& B_, const float* __restrict__ b,
                                                const float* __restrict__ D, int np, int A,
                                                int Ap, int splits, double* Ksp, double* Jsp) {
@@ -75,6 +77,7 @@ __device__ __forceinline__ void k_kpart_body(const Blk& B_, const float* __restr
   const int sp = B_.y;
   if (i4 >= n4) return;
   const int q = i4 / (Ap / 4), p0 = (i4 % (Ap / 4)) * 4;
+  if (p0 > q) return;  // above the diagonal: the mirror's
   const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
   double sk[4] = {0.0, 0.0, 0.0, 0.0}, sj[4] = {0.0, 0.0, 0.0, 0.0};
   const float4* b4 = (const float4*)b;
@@ -131,14 +134,16 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
     {
       const int i = B_.x * blockDim.x + threadIdx.x;
       if (i >= AA) return;
+      const int qi = i / A, pi = i % A;
+      const int src = pi <= qi ? i : pi * A + qi;  // the partials hold p <= q
       double k = 0.0, j = 0.0;
       int sp = 0;
       for (; sp + 8 <= splits; sp += 8) {  // eight splits in flight, summed in order
         double kv[8], jv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          kv[u] = Ksp[(size_t)(sp + u) * AA + i];
-          jv[u] = Jsp[(size_t)(sp + u) * AA + i];
+          kv[u] = Ksp[(size_t)(sp + u) * AA + src];
+          jv[u] = Jsp[(size_t)(sp + u) * AA + src];
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -147,8 +152,8 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
         }
       }
       for (; sp < splits; ++sp) {
-        k += Ksp[(size_t)sp * AA + i];
-        j += Jsp[(size_t)sp * AA + i];
+        k += Ksp[(size_t)sp * AA + src];
+        j += Jsp[(size_t)sp * AA + src];
       }
       K[i] += k;
       J[i] += j;
@@ -166,7 +171,7 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
       const double* Ks = Ksp + (size_t)sp * AA;
       for (int q = lane; q < A; q += 32) {
         const double bc = BcF[(size_t)q * Ap + p];
-        ss += bc * bc * Ks[(size_t)q * A + p];
+        ss += bc * bc * Ks[q >= p ? (size_t)q * A + p : (size_t)p * A + q];
       }
       const int P0 = (int)((long long)np * sp / splits);
       const int P1 = (int)((long long)np * (sp + 1) / splits);
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(256) k_diag_w_group(const GroupLaunch g) {
   const InstRec& I = g.inst[group_locate(g, b)];
   const Dims& d = I.d;
   char* ws = I.ws;
-  k_diag_w_body(b, (const float*)(ws + I.L.D), d.Q, d.A, d.Ap, (const float*)(ws + I.L.AcF),
+  k_diag_w_body<kDiagWGroupSlices>(b, (const float*)(ws + I.L.D), d.Q, d.A, d.Ap, (const float*)(ws + I.L.AcF),
                 (float*)(ws + I.L.W));
 }
 __global__ void __launch_bounds__(256) k_kpart_group(const GroupLaunch g) {
@@ -319,7 +324,7 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   float* W = (float*)(ws + L.W);
   const float* AcF = (const float*)(ws + L.AcF);
   const float* BcF = (const float*)(ws + L.BcF);
-  k_diag_w<<<(np + kDwSlices - 1) / kDwSlices, 256, 0, s>>>(D, np, A, Ap, AcF, W);
+  k_diag_w<<<(np + kDiagWSlices - 1) / kDiagWSlices, 256, 0, s>>>(D, np, A, Ap, AcF, W);
   const int n4 = A * (Ap / 4);
   k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),
