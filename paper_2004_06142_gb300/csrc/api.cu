@@ -147,7 +147,7 @@ Layout make_layout(const Dims& d) {
     L.Ylo = take(pb * Ap * Ap * 2);
     L.Gpart = take((size_t)d.splits * N * Ap * 4);
     L.D = take(pb * A * 4);
-    L.rn2 = take(Q * N * 8);
+    L.rn2 = take(Q * N * 4);  // fp32
     L.spOf = take(pb * 4);
     L.eX3 = take((size_t)d.splits * N * 4);
     L.W = take(pb * A * 4);
@@ -340,7 +340,15 @@ extern "C" int donof_prepare_B(const donof_problem* prob, const double* B, void*
   char* ws = (char*)workspace;
   prof_begin(DONOF_PHASE_PREPARE_B, s);
   CK(cudaMemsetAsync(ws + L.header, 0, sizeof(DevHeader), s));
-  if (d.precision == DONOF_MIXED) CK(launch_prepare_split_B(d, B, ws, L, s));
+  if (d.precision == DONOF_MIXED) {
+    CK(launch_prepare_split_B(d, B, ws, L, s));
+    // the residual-extended planes' zero blocks, which the splits of every build leave alone
+    const size_t u = 4 * (size_t)d.N * d.Np * 2, v = 4 * (size_t)d.Ap * d.Np * 2;
+    CK(cudaMemsetAsync(ws + L.hAH, 0, u, s));
+    CK(cudaMemsetAsync(ws + L.hAF, 0, u, s));
+    CK(cudaMemsetAsync(ws + L.cPH, 0, v, s));
+    CK(cudaMemsetAsync(ws + L.cPF, 0, v, s));
+  }
   prof_end(DONOF_PHASE_PREPARE_B, s);
   std::lock_guard<std::mutex> lk(g_mu);
   g_reg[workspace] = Registration{B, *prob};

@@ -236,6 +236,31 @@ __device__ inline double pow2d(int e) {
   e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
+// The integer + fraction split (and its residual) of y = v 2^k for a double v, formed in
+// fp32 (this GPU's FP64 pipe is narrow): v as the two-float vh + vl (vh = fl32(v), vl =
+// fl32(v - vh), within 2^-48 |v|); both scaled by 2^k exactly; h = fp16(rint(yh)) (even
+// above 2048), dh = yh - h (exact: |yh| < 2^12), f = fp16(dh + yl), r = fp16((dh - f) + yl).  The same h and f as the
+// double split up to rounding ties (h may then be the other neighbour of y, |y - h| a few
+// units of 2^-24 above 1/2), r to about 2^-36 of the unit of h.  Outside the normal range of
+// a float scale (|k| > 120) the double arithmetic is used.
+__device__ inline void intfrac_split_v(double v, int k, __half& h, __half& f, __half& r) {
+  if (k < -120 || k > 120) {
+    const double y = v * __longlong_as_double((long long)(k + 1023) << 52);
+    const float hf = (float)rint(y);
+    h = __float2half_rn(hf);
+    f = __float2half_rn((float)(y - (double)__half2float(h)));
+    r = __double2half((y - (double)__half2float(h)) - (double)__half2float(f));
+    return;
+  }
+  const float vh = __double2float_rn(v);
+  const float vl = __double2float_rn(v - (double)vh);
+  const float sc = __int_as_float((k + 127) << 23);
+  const float yh = vh * sc, yl = vl * sc;
+  h = __float2half_rn(rintf(yh));
+  const float dh = yh - __half2float(h);  // h as stored (even above 2048): exact
+  f = __float2half_rn(dh + yl);
+  r = __float2half_rn((dh - __half2float(f)) + yl);
+}
 __device__ inline void intfrac_split(double y, __half& h, __half& f) {
   const float hf = (float)rint(y);  // exact: |y| < 4096
   h = __float2half_rn(hf);

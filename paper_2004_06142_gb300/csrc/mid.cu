@@ -166,25 +166,36 @@ __device__ __forceinline__ void k_jk_eY_body(const Blk& B_, const double* __rest
   for (int t = ((B_.x - n0) * blockDim.x + threadIdx.x) / 32; t < nrow;
        t += (B_.gx - n0) * blockDim.x / 32) {
     const int sp = t / Ap, p = t % Ap;
-    double ss = 0.0;
+    // the squared norm in fp32 (this GPU's FP64 pipe is narrow): ss, and sa the sum of the
+    // terms' magnitudes; fewer than 64 roundings of 2^-24 each (conversions included) keep
+    // ss within 2^-17 sa of the exact sum, so ss + 2^-16 sa bounds it from above
+    float ss = 0.f, sa = 0.f;
     if (p < A) {
       const double* Ks = Ksp + (size_t)sp * AA;
       for (int q = lane; q < A; q += 32) {
-        const double bc = BcF[(size_t)q * Ap + p];
-        ss += bc * bc * Ks[q >= p ? (size_t)q * A + p : (size_t)p * A + q];
+        const float bc = BcF[(size_t)q * Ap + p];
+        const float t2 = bc * bc * (float)Ks[q >= p ? (size_t)q * A + p : (size_t)p * A + q];
+        ss += t2;
+        sa += t2;
       }
       const int P0 = (int)((long long)np * sp / splits);
       const int P1 = (int)((long long)np * (sp + 1) / splits);
-      const double bpp = BcF[(size_t)p * Ap + p];
+      const float bpp = BcF[(size_t)p * Ap + p];
       for (int P = P0 + lane; P < P1; P += 32) {
-        const double d = D[(size_t)P * A + p], w = W[(size_t)P * A + p];
-        ss += 2.0 * bpp * d * w + w * w;
+        const float d = D[(size_t)P * A + p], w = W[(size_t)P * A + p];
+        const float c = 2.f * bpp * d * w, w2 = w * w;
+        ss += c + w2;
+        sa += fabsf(c) + w2;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    const double bound = (double)ss + 0x1p-16 * (double)sa;
     // row length of the G contraction over this split: (slices in it) x Ap
     const double Kc = (double)(np * (sp + 1LL) / splits - np * (long long)sp / splits) * Ap;
-    if (lane == 0) eY[t] = intfrac_exponent(sqrt(fmax(ss, 0.0)) * (1.0 + 1e-6), Kc);
+    if (lane == 0) eY[t] = intfrac_exponent(sqrt(fmax(bound, 0.0)) * (1.0 + 1e-6), Kc);
   }
 }
 __global__ void __launch_bounds__(256) k_jk_eY(const double* __restrict__ Ksp,

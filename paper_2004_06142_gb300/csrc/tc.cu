@@ -1253,12 +1253,12 @@ __device__ inline double load_B_elem(const double* __restrict__ B, int layout, l
   return B[P * npk + (long long)a * (a + 1) / 2 + b];
 }
 
-// Per row (P, mu) of B: its squared L2 norm (rn2, for the exponents of X in the G
-// contraction), the slice's largest row L1 norm (L1max, the bound on X^T rows) and the AO
+// Per row (P, mu) of B: its squared L2 norm (rn2, fp32 rounded up, for the exponents of X
+// in the G contraction), the slice's largest row L1 norm (L1max, the bound on X^T rows) and the AO
 // index's largest row norm over the slices (rnmax, for the symmetric scaling); any
 // non-finite element raises DONOF_ERR_NONFINITE.
 __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q, int N,
-                          DevHeader* hdr, unsigned long long* L1max_bits, double* rn2,
+                          DevHeader* hdr, unsigned long long* L1max_bits, float* rn2,
                           unsigned long long* rnmax_bits) {
   const long long rows = Q * N;
   const int lane = threadIdx.x % 32;
@@ -1282,7 +1282,7 @@ __global__ void k_b_stats(const double* __restrict__ B, int layout, long long Q,
     }
     const double nr = sqrt(ss);
     if (lane == 0) {
-      rn2[row] = ss;
+      rn2[row] = __double2float_ru(ss);
       atomic_max_nonneg(L1max_bits + P, l1);
       atomic_max_nonneg(rnmax_bits + mu, nr);
     }
@@ -1512,12 +1512,7 @@ __device__ __forceinline__ void k_split_T_body(const Blk& B_, SplitJobs jobs, in
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int mu = mu0 + ty + 8 * j, c = c0 + tx;
-    double v = 0.0;
-    if (mu < jb.N && c < jb.ncols) {
-      v = jb.S[(size_t)mu * jb.ld + c];
-      if (jb.eS) v *= pow2d(jb.eS[mu]);
-    }
-    tile[ty + 8 * j][tx] = v;
+    tile[ty + 8 * j][tx] = (mu < jb.N && c < jb.ncols) ? jb.S[(size_t)mu * jb.ld + c] : 0.0;
   }
   __syncthreads();
 #pragma unroll
@@ -1525,24 +1520,23 @@ __device__ __forceinline__ void k_split_T_body(const Blk& B_, SplitJobs jobs, in
     const int c = c0 + ty + 8 * j, mu = mu0 + tx;
     if (c < jb.nrows_out && mu < Np) {
       const size_t o = (size_t)c * Np + mu;
-      const double y = tile[tx][ty + 8 * j] * pow2d(-jb.e[c]);
-      __half h, f;
-      intfrac_split(y, h, f);
+      const int k = ((jb.eS && mu < jb.N) ? jb.eS[mu] : 0) - jb.e[c];
+      __half h, f, r;
+      intfrac_split_v(tile[tx][ty + 8 * j], k, h, f, r);
       if (jb.H) {
         jb.H[o] = h;
         jb.F[o] = f;
       }
       if (jb.planes) {
-        // y - h and (y - h) - f are exact in double (the operands agree in their leading bits)
-        const __half r = __double2half((y - (double)__half2float(h)) - (double)__half2float(f));
-        const __half z = __float2half_rn(0.f);
         const size_t ps = (size_t)jb.nrows_out * Np;
+        // the planes' zero blocks (U side: h's blocks 1-3, f's block 0; V side: f's block 0)
+        // are cleared once when B is prepared and never written
         if (jb.planes == 1) {
-          jb.PH[o] = h; jb.PH[ps + o] = z; jb.PH[2 * ps + o] = z; jb.PH[3 * ps + o] = z;
-          jb.PF[o] = z; jb.PF[ps + o] = h; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = r;
+          jb.PH[o] = h;
+          jb.PF[ps + o] = h; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = r;
         } else {
           jb.PH[o] = h; jb.PH[ps + o] = r; jb.PH[2 * ps + o] = h; jb.PH[3 * ps + o] = h;
-          jb.PF[o] = z; jb.PF[ps + o] = f; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = f;
+          jb.PF[ps + o] = f; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = f;
         }
       }
     }
@@ -1606,31 +1600,41 @@ __device__ __forceinline__ void k_colsplit_body(const Blk& B_, SplitJobs jobs, d
     }
     __syncthreads();
   }
+  // two consecutive mu per thread (Np is even), 4-byte stores of both
   const int ncl = min(32, jb.nrows_out - c0);
-  for (int mu = ty * 32 + tx; mu - tx < Np; mu += 32 * 32) {
-    if (mu >= Np) continue;
-    const double smu = (eS && mu < N) ? pow2d(eS[mu]) : 1.0;
+  const int np2 = Np / 2;
+  for (int m2 = ty * 32 + tx; m2 - tx < np2; m2 += 32 * 32) {
+    if (m2 >= np2) continue;
+    const int mu0 = 2 * m2, mu1 = mu0 + 1;
+    const int s0 = (eS && mu0 < N) ? eS[mu0] : 0;
+    const int s1 = (eS && mu1 < N) ? eS[mu1] : 0;
     for (int cc = 0; cc < ncl; ++cc) {
       const int c = c0 + cc;
-      const double v = (mu < N && c < jb.ncols) ? S[(size_t)mu * ld + c] * smu : 0.0;
-      const size_t o = (size_t)c * Np + mu;
-      const double y = v * pow2d(-ecol[cc]);
-      __half h, f;
-      intfrac_split(y, h, f);
+      const bool cin = c < jb.ncols;
+      const double v0 = (mu0 < N && cin) ? S[(size_t)mu0 * ld + c] : 0.0;
+      const double v1 = (mu1 < N && cin) ? S[(size_t)mu1 * ld + c] : 0.0;
+      __half h0, f0, r0, h1, f1, r1;
+      intfrac_split_v(v0, s0 - ecol[cc], h0, f0, r0);
+      intfrac_split_v(v1, s1 - ecol[cc], h1, f1, r1);
+      const size_t o = (size_t)c * Np + mu0;
+      const __half2 h2 = __halves2half2(h0, h1), f2 = __halves2half2(f0, f1);
       if (jb.H) {
-        jb.H[o] = h;
-        jb.F[o] = f;
+        *(__half2*)(jb.H + o) = h2;
+        *(__half2*)(jb.F + o) = f2;
       }
       if (jb.planes) {
-        const __half r = __double2half((y - (double)__half2float(h)) - (double)__half2float(f));
-        const __half z = __float2half_rn(0.f);
+        const __half2 r2 = __halves2half2(r0, r1);
         const size_t ps = (size_t)jb.nrows_out * Np;
+        __half2* PH = (__half2*)(jb.PH + o);
+        __half2* PF = (__half2*)(jb.PF + o);
+        const size_t p2 = ps / 2;  // a plane in half2 units (ps is even)
+        // zero blocks as in k_split_T: cleared when B is prepared
         if (jb.planes == 1) {
-          jb.PH[o] = h; jb.PH[ps + o] = z; jb.PH[2 * ps + o] = z; jb.PH[3 * ps + o] = z;
-          jb.PF[o] = z; jb.PF[ps + o] = h; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = r;
+          PH[0] = h2;
+          PF[p2] = h2; PF[2 * p2] = f2; PF[3 * p2] = r2;
         } else {
-          jb.PH[o] = h; jb.PH[ps + o] = r; jb.PH[2 * ps + o] = h; jb.PH[3 * ps + o] = h;
-          jb.PF[o] = z; jb.PF[ps + o] = f; jb.PF[2 * ps + o] = f; jb.PF[3 * ps + o] = f;
+          PH[0] = h2; PH[p2] = r2; PH[2 * p2] = h2; PH[3 * p2] = h2;
+          PF[p2] = f2; PF[2 * p2] = f2; PF[3 * p2] = f2;
         }
       }
     }
@@ -1759,7 +1763,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const float* __restrict__ pa
 //  * X rows (split, mu) for G: the row runs over the split's slices and q, and its squared
 //    norm sum_P ||B^P_mu C_act||^2 <= s_C^2 sum_P ||B^P_mu||^2 (s_C^2 the Gram bound).
 __device__ __forceinline__ void k_x_exponents_body(const Blk& B_, const double* __restrict__ L1max, const double* __restrict__ cnorm,
-                              int Ap, double invT, int* eXt, const double* __restrict__ rn2,
+                              int Ap, double invT, int* eXt, const float* __restrict__ rn2,
                               const DevHeader* hdr, int np, int splits, int N, double invT2,
                               int* spOf, int* eX3) {
   if (B_.y == 0) {  // a thread per (P, q)
@@ -1774,10 +1778,12 @@ __device__ __forceinline__ void k_x_exponents_body(const Blk& B_, const double* 
        i += (long long)B_.gx * blockDim.x) {
     const int sp = (int)(i / N), mu = (int)(i % N);
     const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
-    double r2 = 0.0;
+    // fp32 sum of the rounded-up row norms, in order of P; the 2^-16 margin covers its
+    // rounding (at most 64 slices a split, 2^-24 an addition)
+    float r2 = 0.f;
     int P = P0;
     for (; P + 8 <= P1; P += 8) {  // eight loads in flight, summed in order of P
-      double v[8];
+      float v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = rn2[(size_t)(P + u) * N + mu];
 #pragma unroll
@@ -1786,11 +1792,11 @@ __device__ __forceinline__ void k_x_exponents_body(const Blk& B_, const double* 
     for (; P < P1; ++P) r2 += rn2[(size_t)P * N + mu];
     if (mu == 0)
       for (int Q = P0; Q < P1; ++Q) spOf[Q] = sp;
-    eX3[i] = intfrac_exponent_sq(sC2 * r2 * (1.0 + 1e-12), invT2);
+    eX3[i] = intfrac_exponent_sq(sC2 * (double)r2 * (1.0 + 0x1p-16), invT2);
   }
 }
 __global__ void k_x_exponents(const double* __restrict__ L1max, const double* __restrict__ cnorm,
-                              int Ap, double invT, int* eXt, const double* __restrict__ rn2,
+                              int Ap, double invT, int* eXt, const float* __restrict__ rn2,
                               const DevHeader* hdr, int np, int splits, int N, double invT2,
                               int* spOf, int* eX3) {
   k_x_exponents_body(native_blk(), L1max, cnorm, Ap, invT, eXt, rn2, hdr, np, splits, N, invT2, spOf, eX3);
@@ -1864,7 +1870,7 @@ cudaError_t launch_prepare_split_B(const Dims& d, const double* B, char* ws, con
   if (e != cudaSuccess) return e;
   k_b_stats<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, hdr,
                                           (unsigned long long*)(ws + L.L1max),
-                                          (double*)(ws + L.rn2),
+                                          (float*)(ws + L.rn2),
                                           (unsigned long long*)(ws + L.rnmax));
   k_sym_scale<<<1, 1024, 0, s>>>((const double*)(ws + L.rnmax), d.N, (int*)(ws + L.eS));
   k_p_scale<<<num_sms() * 8, 256, 0, s>>>(B, d.layout, d.Q, d.N, (const int*)(ws + L.eS),
@@ -2125,7 +2131,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   const int gx3 = (splits3 * N + 255) / 256;
   k_x_exponents<<<dim3(gx3 > num_sms() * 4 ? gx3 : num_sms() * 4, 2), 256, 0, s>>>(
       (const double*)(ws + L.L1max) + p0, (const double*)(ws + L.cnorm), Ap,
-      intfrac_inv_target(N), (int*)(ws + L.eXt), (const double*)(ws + L.rn2) + (size_t)p0 * N,
+      intfrac_inv_target(N), (int*)(ws + L.eXt), (const float*)(ws + L.rn2) + (size_t)p0 * N,
       (const DevHeader*)hdr, np, splits3, N, invT2, (int*)(ws + L.spOf), (int*)(ws + L.eX3));
   count_launch(1);
   // (1) X = B C_act
@@ -2200,7 +2206,7 @@ __global__ void k_x_exponents_group(const GroupLaunch g) {
   const int np = d.Q, sp3 = grp_splits(d);
   const double invT2 = intfrac_inv_target_sq((double)((np + sp3 - 1) / sp3) * d.Ap);
   k_x_exponents_body(b, (const double*)(ws + L.L1max), (const double*)(ws + L.cnorm), d.Ap,
-                     intfrac_inv_target(d.N), (int*)(ws + L.eXt), (const double*)(ws + L.rn2),
+                     intfrac_inv_target(d.N), (int*)(ws + L.eXt), (const float*)(ws + L.rn2),
                      (const DevHeader*)(ws + L.header), np, sp3, d.N, invT2, (int*)(ws + L.spOf),
                      (int*)(ws + L.eX3));
 }
