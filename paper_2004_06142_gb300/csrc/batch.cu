@@ -174,7 +174,8 @@ dim3 kind_grid(int kind, const Dims& d, const donof_instance& x, bool backward) 
     }
     case GK_OCC: return dim3(1, 1, 1);
     case GK_COEF: return dim3(ceil_div((long long)Ap * Ap, 256), 1, 1);
-    case GK_SPLIT_C: return dim3(ceil_div(N > Ap ? N : Ap, 32), 3, 1);  // norms + split
+    case GK_SPLIT_C:  // norms + split, a block per 32 columns of each job (C_act twice, h)
+      return dim3(2 * ceil_div(Ap, 32) + ceil_div(N, 32), 1, 1);
     case GK_SUM_HC: return dim3(std::min(1216, ceil_div((long long)N * A, 256)), 1, 1);
     case GK_GRAM_PART: return dim3(ceil_div(N, 32), ceil_div(A, 16), 1);
     case GK_GRAM_FINAL: return dim3(A, 1, 1);
@@ -187,7 +188,8 @@ dim3 kind_grid(int kind, const Dims& d, const donof_instance& x, bool backward) 
     case GK_REDUCEG: return dim3(ceil_div((long long)N * (Ap / 4), 256), 1, 1);
     case GK_EROWS: return dim3(ceil_div(A, 8), 1, 1);
     case GK_EFINAL: return dim3(ceil_div(d.ng + 1, 8), 1, 1);
-    case GK_SPLIT_L: return lam ? dim3(ceil_div(N > Ap ? N : Ap, 32), 2, 1) : dim3(0, 1, 1);
+    case GK_SPLIT_L:  // C (all N columns), G
+      return lam ? dim3(ceil_div(N, 32) + ceil_div(Ap, 32), 1, 1) : dim3(0, 1, 1);
     case GK_SUM_L: return lam ? dim3(std::min(1216, ceil_div((long long)N * A, 256)), 1, 1)
                               : dim3(0, 1, 1);
     case GK_BWD: return (backward && x.dE_dC) ? dim3(std::min(608, ceil_div((long long)N * N, 256)), 1, 1)
@@ -210,13 +212,14 @@ int build_plan(int32_t ninst, const donof_problem* probs, const donof_instance* 
   DevHeader* bhdr = (DevHeader*)ws;  // the batch's status header (device)
   const bool backward = (flags & DONOF_BATCH_BACKWARD) != 0;
   std::vector<Dims> dims(ninst);
-  int max_A = 1, max_ng = 1, max_Ap = 16;
+  int max_A = 1, max_ng = 1, max_Ap = 16, max_N = 1;
   for (int32_t i = 0; i < ninst; ++i) {
     const Dims d = make_dims(&probs[i]);
     dims[i] = d;
     max_A = std::max(max_A, d.A);
     max_ng = std::max(max_ng, d.ng);
     max_Ap = std::max(max_Ap, d.Ap);
+    max_N = std::max(max_N, d.N);
     InstRec r{};
     r.d = d;
     r.L = make_layout(d);
@@ -248,7 +251,8 @@ int build_plan(int32_t ninst, const donof_problem* probs, const donof_instance* 
   }
   pl.threads[GK_OCC] = dim3((max_A + 31) / 32 * 32);
   pl.smem[GK_OCC] = (size_t)max_ng * 2 * sizeof(double);
-  pl.threads[GK_SPLIT_C] = pl.threads[GK_SPLIT_L] = dim3(1024);
+  // 32 x the row groups of the widest instance's column norms (norm_groups in tc.cu)
+  pl.threads[GK_SPLIT_C] = pl.threads[GK_SPLIT_L] = dim3(max_N > 256 ? 1024 : 256);
   pl.threads[GK_YQUANT] = dim3(max_Ap / 4, 8);
   // tensor-core records
   for (int t = 0; t < kTcKinds; ++t) {

@@ -1453,47 +1453,58 @@ struct SplitJobs {
 };
 
 // Column norms of job.S -> exponents of the integer + fraction split of S^T: e[c] for
-// c < nrows_out.  A CTA of 32 x 32 threads per 32 columns: thread (c, g) sums rows g,
-// g + 32, ... (coalesced across c), the 32 partial sums of a column are then added in order.
-__device__ __forceinline__ void k_colnorms_body(const Blk& B_, SplitJobs jobs, double invT, DevHeader* hdr) {
-  const SplitJob& jb = jobs.j[B_.y];
-  if ((int)B_.x * 32 >= jb.nrows_out) return;  // uniform over the CTA
-  __shared__ double red[32][33];
+// c < nrows_out.  A CTA of at least 32 x G threads per 32 columns, G = norm_groups(N) (row
+// groups enough for the columns' length): thread (c, g < G) sums rows g, g + G, ...
+// (coalesced across c, four loads in flight, in order of mu), the G partial sums of a column
+// are then added in order.
+__host__ __device__ inline int norm_groups(int N) { return N > 256 ? 32 : 8; }
+__device__ __forceinline__ double colnorm_partial(const SplitJob& jb, int c, int g, int G) {
+  double ss = 0.0;
+  if (c >= jb.ncols) return ss;
   const double* __restrict__ S = jb.S;
   const int* __restrict__ eS = jb.eS;
   const long long ld = jb.ld;
   const int N = jb.N;
+  int mu = g;
+  for (; mu + 3 * G < N; mu += 4 * G) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = S[(size_t)(mu + G * u) * ld + c];
+      if (eS) v[u] *= pow2d(eS[mu + G * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ss = fma(v[u], v[u], ss);
+  }
+  for (; mu < N; mu += G) {
+    double v = S[(size_t)mu * ld + c];
+    if (eS) v *= pow2d(eS[mu]);
+    ss = fma(v, v, ss);
+  }
+  return ss;
+}
+// the column's exponent (and norm) from the partial sums red[0..G)[tx]
+__device__ __forceinline__ int colnorm_finish(const SplitJob& jb, int c, const double (*red)[33],
+                                              int tx, int G, double invT, DevHeader* hdr) {
+  double t = 0.0;
+  for (int g = 0; g < G; ++g) t += red[g][tx];
+  const double nr = sqrt(t);
+  if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
+  const int e = intfrac_exponent_inv(nr, invT);
+  jb.e[c] = e;
+  if (jb.norm) jb.norm[c] = nr;
+  return e;
+}
+__device__ __forceinline__ void k_colnorms_body(const Blk& B_, SplitJobs jobs, double invT, DevHeader* hdr) {
+  const SplitJob& jb = jobs.j[B_.y];
+  if ((int)B_.x * 32 >= jb.nrows_out) return;  // uniform over the CTA
+  __shared__ double red[32][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int G = norm_groups(jb.N);
   const int c = B_.x * 32 + tx;
-  double ss = 0.0;
-  if (c < jb.ncols) {
-    int mu = ty;
-    for (; mu + 96 < N; mu += 128) {  // four loads in flight, summed in order of mu
-      double v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = S[(size_t)(mu + 32 * u) * ld + c];
-        if (eS) v[u] *= pow2d(eS[mu + 32 * u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) ss = fma(v[u], v[u], ss);
-    }
-    for (; mu < N; mu += 32) {
-      double v = S[(size_t)mu * ld + c];
-      if (eS) v *= pow2d(eS[mu]);
-      ss = fma(v, v, ss);
-    }
-  }
-  red[ty][tx] = ss;
+  if (ty < G) red[ty][tx] = colnorm_partial(jb, c, ty, G);
   __syncthreads();
-  if (ty == 0 && c < jb.nrows_out) {
-    double t = 0.0;
-    for (int g = 0; g < 32; ++g) t += red[g][tx];
-    const double nr = sqrt(t);
-    if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
-    jb.e[c] = intfrac_exponent_inv(nr, invT);
-    if (jb.norm) jb.norm[c] = nr;
-  }
+  if (ty == 0 && c < jb.nrows_out) colnorm_finish(jb, c, red, tx, G, invT, hdr);
 }
 __global__ void __launch_bounds__(1024) k_colnorms(SplitJobs jobs, double invT, DevHeader* hdr) {
   k_colnorms_body(native_blk(), jobs, invT, hdr);
@@ -1546,14 +1557,15 @@ __global__ void __launch_bounds__(256) k_split_T(SplitJobs jobs, int Np) {
   k_split_T_body(native_blk(), jobs, Np);
 }
 
-// Column norms and split of one job at once (grouped launches): a CTA of 32 x 32 threads per
-// job and 32 columns c: the norms as k_colnorms forms them (same order), the exponents kept
-// in shared memory, then the split of those columns as k_split_T forms it, warp w writing the
-// 32-wide chunks of mu = 32 w, 32 (w + 32), ... (the columns come from L1 after the norms).
-__device__ __forceinline__ void k_colsplit_body(const Blk& B_, SplitJobs jobs, double invT,
+// Column norms and split at once (grouped launches): a CTA of 32 x (at least the row groups)
+// threads per 32 columns cb of one job (the grouped grid runs over the jobs' column blocks in
+// turn, so that no block is idle): the norms as k_colnorms forms them (same order), the
+// exponents kept in shared memory, then the split of those columns as k_split_T forms it,
+// warp w writing pairs of mu 64 w, 64 (w + warps), ... (the columns come from L1 after the
+// norms).
+__device__ __forceinline__ void k_colsplit_body(const SplitJob& jb, int cb, double invT,
                                                 DevHeader* hdr, int Np) {
-  const SplitJob& jb = jobs.j[B_.y];
-  const int c0 = B_.x * 32;
+  const int c0 = cb * 32;
   if (c0 >= jb.nrows_out) return;  // uniform over the CTA
   __shared__ double red[32][33];
   __shared__ int ecol[32];
@@ -1564,46 +1576,16 @@ __device__ __forceinline__ void k_colsplit_body(const Blk& B_, SplitJobs jobs, d
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   {
     const int c = c0 + tx;
-    double ss = 0.0;
-    if (c < jb.ncols) {
-      int mu = ty;
-      for (; mu + 96 < N; mu += 128) {
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          v[u] = S[(size_t)(mu + 32 * u) * ld + c];
-          if (eS) v[u] *= pow2d(eS[mu + 32 * u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ss = fma(v[u], v[u], ss);
-      }
-      for (; mu < N; mu += 32) {
-        double v = S[(size_t)mu * ld + c];
-        if (eS) v *= pow2d(eS[mu]);
-        ss = fma(v, v, ss);
-      }
-    }
-    red[ty][tx] = ss;
+    const int G = norm_groups(N);
+    if (ty < G) red[ty][tx] = colnorm_partial(jb, c, ty, G);
     __syncthreads();
-    if (ty == 0) {
-      int e = 0;
-      if (c < jb.nrows_out) {
-        double t = 0.0;
-        for (int g = 0; g < 32; ++g) t += red[g][tx];
-        const double nr = sqrt(t);
-        if (!isfinite(nr)) set_status(hdr, DONOF_ERR_NONFINITE);
-        e = intfrac_exponent_inv(nr, invT);
-        jb.e[c] = e;
-        if (jb.norm) jb.norm[c] = nr;
-      }
-      ecol[tx] = e;
-    }
+    if (ty == 0) ecol[tx] = c < jb.nrows_out ? colnorm_finish(jb, c, red, tx, G, invT, hdr) : 0;
     __syncthreads();
   }
   // two consecutive mu per thread (Np is even), 4-byte stores of both
   const int ncl = min(32, jb.nrows_out - c0);
   const int np2 = Np / 2;
-  for (int m2 = ty * 32 + tx; m2 - tx < np2; m2 += 32 * 32) {
+  for (int m2 = ty * 32 + tx; m2 - tx < np2; m2 += (int)blockDim.x) {
     if (m2 >= np2) continue;
     const int mu0 = 2 * m2, mu1 = mu0 + 1;
     const int s0 = (eS && mu0 < N) ? eS[mu0] : 0;
@@ -1644,36 +1626,45 @@ __device__ __forceinline__ void k_colsplit_body(const Blk& B_, SplitJobs jobs, d
 // The splits of a build's prep phase: C_act^T for b (and its residual planes, the V side of
 // h C_act), diag(2^s) C_act for the symmetric half transform (with_half_transform), and
 // h^T = h (the U side of h C_act).
+__host__ __device__ inline SplitJob split_c_job(const Dims& d, const Layout& L, char* ws,
+                                               const double* C, const double* h, int k) {
+  if (k == 0)
+    return SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
+                    (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo),
+                    2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+  if (k == 1)
+    return SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
+                    nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS),
+                    0, nullptr, nullptr};
+  return SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
+                  nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+}
 __host__ __device__ inline SplitJobs split_c_jobs(const Dims& d, const Layout& L, char* ws,
                                                   const double* C, const double* h,
                                                   bool with_half_transform) {
   SplitJobs jobs{};
-  jobs.j[0] = SplitJob{C, d.N, d.N, d.A, d.Ap, nullptr, (int*)(ws + L.eC),
-                       (double*)(ws + L.cnorm), (__half*)(ws + L.Chi), (__half*)(ws + L.Clo),
-                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
-  jobs.j[1] = SplitJob{C, d.N, d.N, d.A, d.Ap, (const int*)(ws + L.eS), (int*)(ws + L.eCs),
-                       nullptr, (__half*)(ws + L.ChiS), (__half*)(ws + L.CloS),
-                       0, nullptr, nullptr};
-  jobs.j[2] = SplitJob{h, d.N, d.N, d.N, d.N, nullptr, (int*)(ws + L.eh), nullptr, nullptr,
-                       nullptr, 1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
-  jobs.count = 3;
-  if (!with_half_transform) {
-    jobs.j[1] = jobs.j[2];
-    jobs.count = 2;
-  }
+  jobs.j[0] = split_c_job(d, L, ws, C, h, 0);
+  jobs.j[1] = split_c_job(d, L, ws, C, h, with_half_transform ? 1 : 2);
+  jobs.j[2] = split_c_job(d, L, ws, C, h, 2);
+  jobs.count = with_half_transform ? 3 : 2;
   return jobs;
 }
 // The splits of lambda = C^T G: the residual planes of C^T (all N columns of C, U side) and of
 // G^T (V side), in the buffers of h C_act (free by then).
+__host__ __device__ inline SplitJob lambda_job(const Dims& d, const Layout& L, char* ws,
+                                               const double* C, int k) {
+  const int N = d.N, A = d.A;
+  if (k == 0)
+    return SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr, nullptr, nullptr,
+                    1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
+  return SplitJob{(const double*)(ws + L.G), A, N, A, d.Ap, nullptr, (int*)(ws + L.eG),
+                  nullptr, nullptr, nullptr, 2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+}
 __host__ __device__ inline SplitJobs lambda_jobs(const Dims& d, const Layout& L, char* ws,
                                                  const double* C) {
-  const int N = d.N, A = d.A;
-  const double* G = (const double*)(ws + L.G);
   SplitJobs jobs{};
-  jobs.j[0] = SplitJob{C, N, N, N, N, nullptr, (int*)(ws + L.eCf), nullptr, nullptr, nullptr,
-                       1, (__half*)(ws + L.hAH), (__half*)(ws + L.hAF)};
-  jobs.j[1] = SplitJob{G, A, N, A, d.Ap, nullptr, (int*)(ws + L.eG), nullptr, nullptr, nullptr,
-                       2, (__half*)(ws + L.cPH), (__half*)(ws + L.cPF)};
+  jobs.j[0] = lambda_job(d, L, ws, C, 0);
+  jobs.j[1] = lambda_job(d, L, ws, C, 1);
   jobs.count = 2;
   return jobs;
 }
@@ -1684,7 +1675,7 @@ cudaError_t launch_split_jobs(const SplitJobs& jobs, int Np, double invT, DevHea
   int rmax = 0;
   for (int k = 0; k < jobs.count; ++k)
     if (jobs.j[k].nrows_out > rmax) rmax = jobs.j[k].nrows_out;
-  k_colnorms<<<dim3((rmax + 31) / 32, jobs.count), 1024, 0, s>>>(jobs, invT, hdr);
+  k_colnorms<<<dim3((rmax + 31) / 32, jobs.count), 32 * norm_groups(jobs.j[0].N), 0, s>>>(jobs, invT, hdr);
   k_split_T<<<dim3((Np + 31) / 32, (rmax + 31) / 32, jobs.count), 256, 0, s>>>(jobs, Np);
   count_launch(2);
   return cudaGetLastError();
@@ -2182,9 +2173,17 @@ __device__ __forceinline__ int grp_splits(const Dims& d) { return d.splits < d.Q
 __global__ void __launch_bounds__(1024) k_colsplit_group(const GroupLaunch g, int which) {
   Blk b;
   const InstRec& I = g.inst[group_locate(g, b)];
-  const SplitJobs jobs = which == 0 ? split_c_jobs(I.d, I.L, I.ws, I.C, I.h, true)
-                                    : lambda_jobs(I.d, I.L, I.ws, I.C);
-  k_colsplit_body(b, jobs, intfrac_inv_target(I.d.N), (DevHeader*)(I.ws + I.L.header), I.d.Np);
+  const Dims& d = I.d;
+  const int nC = (d.Ap + 31) / 32, nN = (d.N + 31) / 32;
+  const double invT = intfrac_inv_target(d.N);
+  DevHeader* hdr = (DevHeader*)(I.ws + I.L.header);
+  if (which == 0) {  // blocks: C_act^T (nC), diag(2^s) C_act (nC), h (nN)
+    const int k = b.x < nC ? 0 : (b.x < 2 * nC ? 1 : 2);
+    k_colsplit_body(split_c_job(d, I.L, I.ws, I.C, I.h, k), b.x - k * nC, invT, hdr, d.Np);
+  } else {  // blocks: C (nN), G (nC)
+    const int k = b.x < nN ? 0 : 1;
+    k_colsplit_body(lambda_job(d, I.L, I.ws, I.C, k), b.x - k * nN, invT, hdr, d.Np);
+  }
 }
 __global__ void __launch_bounds__(256) k_gram_part_group(const GroupLaunch g) {
   Blk b;
