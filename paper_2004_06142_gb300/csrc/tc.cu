@@ -328,6 +328,7 @@ constexpr int kThreads = 128 + 128 * kEpiGroups;  // producer, MMA, TMEM, relay 
 // groups), one float2 per column, in shared memory after the barriers
 constexpr int kTabCols = 256 / kEpiGroups;
 constexpr int kMaxSets = 8;  // TMEM accumulator sets at most (narrow tiles)
+constexpr int kMaxStages = 8;  // shared-memory stages at most (16 measured no faster)
 constexpr int kBarTail = 2 * kMaxSets + 4;  // barriers after full/empty, then the TMEM slot
 constexpr int kTabBytes = 4 * kEpiGroups * kTabCols * 8;
 
@@ -1178,7 +1179,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   // the 227 KB opt-in limit, less alignment, barriers and the epilogue's factor tables
   const size_t budget = 232448 - 1024 - 512 - kTabBytes;
   int stages = (int)(budget / stage_bytes);
-  if (stages > 8) stages = 8;
+  if (stages > kMaxStages) stages = kMaxStages;
   if (stages < 2) stages = 2;
   a.stages = stages;
   // TMEM: one or two accumulators per set (kIntFrac keeps h*h apart; of 2 Nn columns each
@@ -2266,7 +2267,7 @@ size_t tc_group_finish(int kind, void* a_recs, int ninst, int* status, int* abor
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)nn * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   int stages = (int)((232448 - 1024 - 512 - kTabBytes) / stage_bytes);
-  stages = stages > 8 ? 8 : (stages < 2 ? 2 : stages);
+  stages = stages > kMaxStages ? kMaxStages : (stages < 2 ? 2 : stages);
   int nbuf, stride, epi_alt;
   cat = 2 * nn <= 128 ? 1 : 0;  // kIntFracCat for every instance of the launch
   tmem_plan(nn, (cat ? 4 : 2) * nn, true, nbuf, stride, epi_alt);
