@@ -145,6 +145,14 @@ __device__ __forceinline__ int group_locate(const GroupLaunch& g, Blk& b) {
   return lo;
 }
 
+// The K and J partials' entries (q, p0..p0+3) on and below the diagonal (p0 <= q, p0 a
+// multiple of 4), row by row: rows 4k .. 4k+3 have k + 1 such quads each, so the rows before
+// 4k hold 2k(k+1) of them.
+__host__ __device__ inline int kpart_quads(int A) {
+  const int kb = A / 4;
+  return 2 * kb * (kb + 1) + (A % 4) * (kb + 1);
+}
+
 // Slices per CTA of k_diag_w (mid.cu): few in a single build, so that the latency-bound kernel
 // has CTAs enough; more in a grouped launch, which has many instances to spread over the SMs.
 constexpr int kDiagWSlices = 4;

@@ -66,18 +66,25 @@ __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int
   k_diag_w_body<kDiagWSlices>(native_blk(), D, np, A, Ap, AcF, W);
 }
 
-// Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread, for the
-// quads with p0 <= q only (K and J are symmetric: every entry with p <= q is formed, read by
+// Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread, a thread
+// per quad with p0 <= q (K and J are symmetric: every entry with p <= q is formed, read by
 // k_jk_eY for its mirror too, so that b is read on and below the diagonal only).
+__device__ __forceinline__ void kpart_quad(int i, int& q, int& p0) {
+  int k = (int)((sqrtf(1.f + 2.f * (float)i) - 1.f) * 0.5f);
+  while (2 * (k + 1) * (k + 2) <= i) ++k;
+  while (2 * k * (k + 1) > i) --k;
+  const int r = i - 2 * k * (k + 1);
+  q = 4 * k + r / (k + 1);
+  p0 = 4 * (r % (k + 1));
+}
 __device__ __forceinline__ void k_kpart_body(const Blk& B_, const float* __restrict__ b,
                                                const float* __restrict__ D, int np, int A,
                                                int Ap, int splits, double* Ksp, double* Jsp) {
-  const int n4 = A * (Ap / 4);
-  const int i4 = B_.x * blockDim.x + threadIdx.x;
+  const int i4 = B_.x * blockDim.x + threadIdx.x;  // a quad on or below the diagonal
   const int sp = B_.y;
-  if (i4 >= n4) return;
-  const int q = i4 / (Ap / 4), p0 = (i4 % (Ap / 4)) * 4;
-  if (p0 > q) return;  // above the diagonal: the mirror's
+  if (i4 >= kpart_quads(A)) return;
+  int q, p0;
+  kpart_quad(i4, q, p0);
   const int P0 = (int)((long long)np * sp / splits), P1 = (int)((long long)np * (sp + 1) / splits);
   double sk[4] = {0.0, 0.0, 0.0, 0.0}, sj[4] = {0.0, 0.0, 0.0, 0.0};
   const float4* b4 = (const float4*)b;
@@ -86,18 +93,32 @@ __device__ __forceinline__ void k_kpart_body(const Blk& B_, const float* __restr
   for (int G0 = P0; G0 < P1; G0 += 16) {
     const int G1 = min(P1, G0 + 16);
     float fk[4] = {0.f, 0.f, 0.f, 0.f}, fj[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int P = G0; P < G1; ++P) {
-      const float4 v = b4[(size_t)P * slice4 + e4];
-      const float* dP = D + (size_t)P * A;
-      const float dq = dP[q];
-      fk[0] = fmaf(v.x, v.x, fk[0]);
-      fk[1] = fmaf(v.y, v.y, fk[1]);
-      fk[2] = fmaf(v.z, v.z, fk[2]);
-      fk[3] = fmaf(v.w, v.w, fk[3]);
+    for (int Pb = G0; Pb < G1; Pb += 8) {
+      // eight slices' loads in flight, then the products added in order of P
+      float4 v[8];
+      float dq[8], dp[8][4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (p0 + j < A) fj[j] = fmaf(dq, dP[p0 + j], fj[j]);
+      for (int u = 0; u < 8; ++u) {
+        const int P = Pb + u;
+        const bool in = P < G1;
+        const float* dP = D + (size_t)(in ? P : Pb) * A;
+        v[u] = in ? b4[(size_t)P * slice4 + e4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dq[u] = in ? dP[q] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dp[u][j] = (in && p0 + j < A) ? dP[p0 + j] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (Pb + u < G1) {
+          fk[0] = fmaf(v[u].x, v[u].x, fk[0]);
+          fk[1] = fmaf(v[u].y, v[u].y, fk[1]);
+          fk[2] = fmaf(v[u].z, v[u].z, fk[2]);
+          fk[3] = fmaf(v[u].w, v[u].w, fk[3]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (p0 + j < A) fj[j] = fmaf(dq[u], dp[u][j], fj[j]);
+        }
+      }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -336,8 +357,7 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   const float* AcF = (const float*)(ws + L.AcF);
   const float* BcF = (const float*)(ws + L.BcF);
   k_diag_w<<<(np + kDiagWSlices - 1) / kDiagWSlices, 256, 0, s>>>(D, np, A, Ap, AcF, W);
-  const int n4 = A * (Ap / 4);
-  k_kpart<<<dim3((n4 + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
+  k_kpart<<<dim3((kpart_quads(A) + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),
                                                          (double*)(ws + L.Jsp));
   const int ncta_e = (splits * Ap + 7) / 8;  // a warp per (split, row) of the exponents
