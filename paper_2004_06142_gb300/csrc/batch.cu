@@ -181,7 +181,7 @@ dim3 kind_grid(int kind, const Dims& d, const donof_instance& x, bool backward) 
     case GK_GRAM_FINAL: return dim3(A, 1, 1);
     case GK_HDIAG: return dim3(ceil_div(A, 8), 1, 1);
     case GK_XEXP: return dim3(std::max(1, ceil_div((long long)sp3 * N, 256)), 2, 1);
-    case GK_DIAGW: return dim3(ceil_div(np, kDiagWGroupSlices), 1, 1);
+    case GK_DIAGW: return dim3(ceil_div(np, kDiagWTileSlices), ceil_div(A, kDiagWTileCols), 1);
     case GK_KPART: return dim3(ceil_div(kpart_quads(A), 256), sp3, 1);
     case GK_JKEY:  // the sums a thread per entry; the exponents a warp per (split, row)
       return dim3(ceil_div((long long)A * A, 256) + ceil_div((long long)sp3 * Ap, 8), 1, 1);

@@ -153,10 +153,8 @@ __host__ __device__ inline int kpart_quads(int A) {
   return 2 * kb * (kb + 1) + (A % 4) * (kb + 1);
 }
 
-// Slices per CTA of k_diag_w (mid.cu): few in a single build, so that the latency-bound kernel
-// has CTAs enough; more in a grouped launch, which has many instances to spread over the SMs.
-constexpr int kDiagWSlices = 4;
-constexpr int kDiagWGroupSlices = 16;
+// Tiles of k_diag_w (mid.cu): a CTA per 32 slices and 64 columns.
+constexpr int kDiagWTileSlices = 32, kDiagWTileCols = 64;
 
 // The grouped launches of one batched build, in order (batch.cu builds their grids).
 enum GroupKind {

@@ -4,7 +4,7 @@
 //   Y^P_qp = Bcoef_qp b^P_qp + delta_qp w^P_p,   w^P_p = sum_r Acoef_pr d^P_r,  d^P_r = b^P_rr,
 // (the J and K coefficient matrices of E applied slice by slice, Eqs. Vee-s, Vee-d), without
 // materialising Y in fp32:
-//   k_diag_w   w^P per slice from d^P (written by the b contraction; fp32, 16 slices per CTA);
+//   k_diag_w   w^P per slice from d^P (written by the b contraction; fp32, W = D Acoef in tiles);
 //   k_kpart    per G split sp: Ksp_qp = sum_{P in sp} (b^P_qp)^2 and Jsp_qp = sum d^P_q d^P_p
 //              (fp32 groups of 16 slices, double across groups), b read once;
 //   k_jk_eY    K += sum_sp Ksp, J += sum_sp Jsp (double, fixed order), and the exponent of
@@ -22,48 +22,52 @@ __device__ __forceinline__ float pow2f_m(int e) {
 }
 
 
-// w^P = Acoef d^P for a group of kDwSlices slices per CTA, from the diagonals d^P of b^P that
-// the b contraction wrote into D: the group's d in shared memory, thread p forms w_p of
-// every slice of the group (Acoef is symmetric, so its column p is read, coalesced across
-// threads).
-template <int kDwSlices>
-__device__ __forceinline__ void k_diag_w_body(const Blk& B_, const float* __restrict__ D, int np, int A,
-                                                int Ap, const float* __restrict__ AcF,
-                                                float* W) {
-  __shared__ float dv[kDwSlices][256];  // A <= 256
-  const int P0 = B_.x * kDwSlices;
-  const int nP = min(kDwSlices, np - P0);
-  for (int i = threadIdx.x; i < kDwSlices * A; i += blockDim.x) {
-    const int sl = i / A, r = i - sl * A;
-    dv[sl][r] = sl < nP ? D[(size_t)(P0 + sl) * A + r] : 0.f;
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < A; p += blockDim.x) {
-    float w[kDwSlices];
+// w^P = Acoef d^P for every slice, from the diagonals d^P of b^P that the b contraction wrote
+// into D, as the product W = D Acoef (Acoef symmetric) in tiles: a CTA of 256 threads per 32
+// slices and 64 columns p, the d and Acoef tiles of 64 r at a time in shared memory; thread
+// (p, g) forms w_p of slices 8g .. 8g+7, the products added in order of r.
+constexpr int kDwS = kDiagWTileSlices, kDwP = kDiagWTileCols, kDwR = 64;
+__device__ __forceinline__ void k_diag_w_body(const Blk& B_, const float* __restrict__ D, int np,
+                                              int A, int Ap, const float* __restrict__ AcF,
+                                              float* W) {
+  __shared__ float dT[kDwS][kDwR + 1];
+  __shared__ float At[kDwR][kDwP];
+  const int P0 = B_.x * kDwS, p0 = B_.y * kDwP;
+  const int tid = threadIdx.x, pl = tid % kDwP, sg = tid / kDwP;
+  float w[8];
 #pragma unroll
-    for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = 0.f;
-    // eight loads of Acoef in flight, the products still added in order of r
-    for (int r0 = 0; r0 < A; r0 += 8) {
-      float a[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = r0 + u < A ? AcF[(size_t)(r0 + u) * Ap + p] : 0.f;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (r0 + u < A) {
-#pragma unroll
-          for (int sl = 0; sl < kDwSlices; ++sl) w[sl] = fmaf(a[u], dv[sl][r0 + u], w[sl]);
-        }
-      }
+  for (int k = 0; k < 8; ++k) w[k] = 0.f;
+  for (int r0 = 0; r0 < A; r0 += kDwR) {
+    const int nr = min(kDwR, A - r0);
+    for (int i = tid; i < kDwS * kDwR; i += blockDim.x) {
+      const int sl = i / kDwR, r = i % kDwR;
+      dT[sl][r] = (P0 + sl < np && r < nr) ? D[(size_t)(P0 + sl) * A + r0 + r] : 0.f;
     }
+    for (int i = tid; i < kDwR * kDwP; i += blockDim.x) {
+      const int r = i / kDwP, c = i % kDwP;
+      At[r][c] = (r < nr && p0 + c < A) ? AcF[(size_t)(r0 + r) * Ap + p0 + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+      const float a = At[r][pl];
 #pragma unroll
-    for (int sl = 0; sl < kDwSlices; ++sl)
-      if (sl < nP) W[(size_t)(P0 + sl) * A + p] = w[sl];
+      for (int k = 0; k < 8; ++k) w[k] = fmaf(a, dT[sg * 8 + k][r], w[k]);
+    }
+    __syncthreads();
+  }
+  const int p = p0 + pl;
+  if (p < A) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int P = P0 + sg * 8 + k;
+      if (P < np) W[(size_t)P * A + p] = w[k];
+    }
   }
 }
 __global__ void __launch_bounds__(256) k_diag_w(const float* __restrict__ D, int np, int A,
                                                 int Ap, const float* __restrict__ AcF,
                                                 float* W) {
-  k_diag_w_body<kDiagWSlices>(native_blk(), D, np, A, Ap, AcF, W);
+  k_diag_w_body(native_blk(), D, np, A, Ap, AcF, W);
 }
 
 // Per split: K and J partials of four consecutive entries (q, p0..p0+3) per thread, a thread
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(256) k_diag_w_group(const GroupLaunch g) {
   const InstRec& I = g.inst[group_locate(g, b)];
   const Dims& d = I.d;
   char* ws = I.ws;
-  k_diag_w_body<kDiagWGroupSlices>(b, (const float*)(ws + I.L.D), d.Q, d.A, d.Ap, (const float*)(ws + I.L.AcF),
+  k_diag_w_body(b, (const float*)(ws + I.L.D), d.Q, d.A, d.Ap, (const float*)(ws + I.L.AcF),
                 (float*)(ws + I.L.W));
 }
 __global__ void __launch_bounds__(256) k_kpart_group(const GroupLaunch g) {
@@ -356,7 +360,8 @@ cudaError_t launch_mid_mixed(const Dims& d, int np, int splits, char* ws, const 
   float* W = (float*)(ws + L.W);
   const float* AcF = (const float*)(ws + L.AcF);
   const float* BcF = (const float*)(ws + L.BcF);
-  k_diag_w<<<(np + kDiagWSlices - 1) / kDiagWSlices, 256, 0, s>>>(D, np, A, Ap, AcF, W);
+  k_diag_w<<<dim3((np + kDwS - 1) / kDwS, (A + kDwP - 1) / kDwP), 256, 0, s>>>(D, np, A, Ap, AcF,
+                                                                           W);
   k_kpart<<<dim3((kpart_quads(A) + 255) / 256, splits), 256, 0, s>>>(b, D, np, A, Ap, splits,
                                                          (double*)(ws + L.Ksp),
                                                          (double*)(ws + L.Jsp));
