@@ -340,6 +340,10 @@ struct TcArgs {
   int kt_per_kb, nkb;
   int a_z_kb;      // A tile z coordinate = kb (else a_z_unit ? the unit's z : 0)
   int a_z_unit;
+  // dense half transform whose last row tile holds at most 64 AO indices: the last tiles of
+  // slices 2p and 2p + 1 share a unit (rows 0-63 and 64-127, A through the 64-row maps ah2,
+  // al2), after the z_count x (m_tiles - 1) units of the full tiles
+  int pack2;
   int b_z_mode;    // 0: 0, 1: z, 2: kb
   int stages;
   int nbuf;        // TMEM accumulator sets: 1, 2, 4, 8, or 3 (three regions in rotation, below)
@@ -388,10 +392,19 @@ struct TcArgs {
   int* abort_flag;
 };
 
-// The four operand maps of one contraction (integer and fraction planes of A and B).
+// The operand maps of one contraction (integer and fraction planes of A and B; ah2, al2: A
+// in boxes of 64 rows, for pack2).
 struct TcMaps {
-  CUtensorMap ah, al, bh, bl;
+  CUtensorMap ah, al, bh, bl, ah2, al2;
 };
+
+// Work units of one problem (PAIR: units of a CTA pair).
+__host__ __device__ inline int tc_units(const TcArgs& A, int pair) {
+  if (A.pack2) return A.z_count * (A.m_tiles - 1) + (A.z_count + 1) / 2;
+  const int zu = (pair && A.sym) ? (A.z_count + 1) / 2 : A.z_count;
+  const int mu = (pair && !A.sym) ? (A.m_tiles + 1) / 2 : A.m_tiles;
+  return zu * mu * A.splits;
+}
 
 // Round-robin (circle method) schedule over the T row tiles of a slice: in round r row
 // tile i works on tile column rr_partner(i, r, T), an involution, so both row tiles that
@@ -499,7 +512,7 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   auto m_units = [&](const TcArgs& A) {
     return (PAIR && !sym_of(A)) ? (A.m_tiles + 1) / 2 : A.m_tiles;
   };
-  const int units = ustart ? ustart[ninst] : z_units(a0) * m_units(a0) * a0.splits;
+  const int units = ustart ? ustart[ninst] : tc_units(a0, PAIR);
   // the problem of unit u and the unit's index lu among that problem's units: every role
   // walks its units in increasing order, so the problem index only moves forward
   struct Walk {
@@ -517,7 +530,21 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
   };
   // consecutive units share the split (and so the B tiles of one K range, which then come
   // from L2 for all M tiles of that split)
-  auto decode = [&](const TcArgs& A, int u, int& z, int& mt, int& sp) {
+  auto decode = [&](const TcArgs& A, int u, int& z, int& mt, int& sp, int& half) {
+    half = 0;
+    if (A.pack2) {  // full tiles, then the shared last tiles of slice pairs
+      const int nf = A.z_count * (A.m_tiles - 1);
+      sp = 0;
+      if (u < nf) {
+        z = u / (A.m_tiles - 1);
+        mt = u % (A.m_tiles - 1);
+      } else {
+        z = 2 * (u - nf);
+        mt = A.m_tiles - 1;
+        half = 1;
+      }
+      return;
+    }
     const int mu_n = m_units(A);
     const int zu = u / (mu_n * A.splits);
     const int r = u % (mu_n * A.splits);
@@ -543,15 +570,23 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     long long issued = 0;  // stages filled so far
     const int b_row0 = (int)rank * nb_rows;
     Walk wk = walk0();
+    // the current problem's arguments, copied into registers when the problem changes (the
+    // table is in global memory, and every asm statement's memory clobber would reload them)
+    int cur = -1;
+    TcArgs acur;
     for (int u = cl; u < units && ok; u += ncl) {
       int lu;
       const int inst = locate(wk, u, lu);
-      const TcArgs& args = targs[inst];
+      if (inst != cur) {
+        acur = targs[inst];
+        cur = inst;
+      }
+      const TcArgs& args = acur;
       const TcMaps& maps = tmaps[inst];
       const uint32_t bu = b_bytes_of(args);
       const uint32_t bl_off = bcat ? bu : b_bytes;  // the fraction plane of B
-      int z, mt, sp;
-      decode(args, lu, z, mt, sp);
+      int z, mt, sp, half;
+      decode(args, lu, z, mt, sp, half);
       if (sym_of(args)) {
         const SymTiles st = args.st;
         const bool a_valid = z < args.z_count;  // PAIR: the odd slice of an odd count is absent
@@ -610,6 +645,11 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
           if (il8) {
             tma_load_4d(base, &maps.ah, fb, 0, mt * BM / 8, kt * BK / 8, az);
             tma_load_4d(base + a_bytes, &maps.al, fb, 0, mt * BM / 8, kt * BK / 8, az);
+          } else if (half) {  // the last row tiles of slices z and z + 1, 64 rows each
+            tma_load_3d(base, &maps.ah2, fb, kt * BK, mt * BM, z);
+            tma_load_3d(base + a_bytes / 2, &maps.ah2, fb, kt * BK, mt * BM, z + 1);
+            tma_load_3d(base + a_bytes, &maps.al2, fb, kt * BK, mt * BM, z);
+            tma_load_3d(base + a_bytes + a_bytes / 2, &maps.al2, fb, kt * BK, mt * BM, z + 1);
           } else if (amn) {
             tma_load_3d(base, &maps.ah, fb, mt * BM, kt * BK, az);
             tma_load_3d(base + a_bytes / 2, &maps.ah, fb, mt * BM + 64, kt * BK, az);
@@ -641,11 +681,20 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     uint32_t phase = 0;
     bool ok = true;
     Walk wk = walk0();
+    // the current problem's arguments, copied into registers when the problem changes (the
+    // table is in global memory, and every asm statement's memory clobber would reload them)
+    int cur = -1;
+    TcArgs acur;
     for (int u = cl; u < units && ok; u += ncl) {
       int lu;
-      const TcArgs& args = targs[locate(wk, u, lu)];
-      int z, mt, sp;
-      decode(args, lu, z, mt, sp);
+      const int inst = locate(wk, u, lu);
+      if (inst != cur) {
+        acur = targs[inst];
+        cur = inst;
+      }
+      const TcArgs& args = acur;
+      int z, mt, sp, half;
+      decode(args, lu, z, mt, sp, half);
       const int iters = unit_iters(args, sp);
       for (int it = 0; it < iters; ++it) {
         if (!mbar_wait(bar(kFull + stage), phase, status, abort_flag)) { ok = false; break; }
@@ -663,16 +712,25 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
     bool ok = true;
     int local = 0;
     Walk wk = walk0();
+    // the current problem's arguments, copied into registers when the problem changes (the
+    // table is in global memory, and every asm statement's memory clobber would reload them)
+    int cur = -1;
+    TcArgs acur;
     for (int u = cl; u < units && ok; u += ncl, ++local) {
       int lu;
-      const TcArgs& args = targs[locate(wk, u, lu)];
+      const int inst = locate(wk, u, lu);
+      if (inst != cur) {
+        acur = targs[inst];
+        cur = inst;
+      }
+      const TcArgs& args = acur;
       const int nn = args.Nn;
       const bool il8 = args.a_il8 != 0, amn = args.a_mn != 0;
       const uint32_t idesc =
           idesc_f16(PAIR ? 2 * BM : BM, bcat ? 2 * nn : nn) | (amn ? (1u << 15) : 0u);
       const int T = args.st.T, rl64 = args.st.Rlast / 64;
-      int z, mt, sp;
-      decode(args, lu, z, mt, sp);
+      int z, mt, sp, half;
+      decode(args, lu, z, mt, sp, half);
       // the accumulator pair (d0: h*h, d1: the cross products) of this unit
       uint32_t d0, d1;
       int tf;
@@ -783,8 +841,8 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       const int nch = args.Nn / 16;
       const int hch = epi_alt ? nch : (nch + kEpiGroups - 1) / kEpiGroups;
       const int ch0 = epi_alt ? 0 : eg * hch, ch1 = ch0 + hch < nch ? ch0 + hch : nch;
-      int z, mt, sp;
-      decode(args, lu, z, mt, sp);
+      int z, mt, sp, half;
+      decode(args, lu, z, mt, sp, half);
       int tf;
       uint32_t tf_phase, c0off, c1off;
       if (nbuf3) {
@@ -800,15 +858,17 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       }
       // everything that needs no accumulator (exponents, the factor table) is looked up
       // before waiting for it, while the tile's MMAs run
-      const int row = mt * BM + q * 32 + lane;
+      // a shared unit (half): lane quadrants 0, 1 hold slice z, quadrants 2, 3 slice z + 1
+      const int zq = (half && q >= 2) ? z + 1 : z;
+      const int row = half ? mt * BM + (q & 1) * 32 + lane : mt * BM + q * 32 + lane;
       // mode 1: slice and AO index of this row, the exponent of its X row in the G
       // contraction and the row of X^T exponents, looked up once per tile
       int rP = 0, rmu = 0;
       bool valid = row < args.M && z < args.z_count;
-      if (args.sym || args.a_z_unit) {  // the unit is one slice z
-        rP = z;
+      if (args.sym || args.a_z_unit) {  // the unit is one slice zq
+        rP = zq;
         rmu = row;
-        valid = row < args.Nrow && z < args.z_count;
+        valid = row < args.Nrow && zq < args.z_count;
       } else if (args.mode == 1) {
         rP = row / args.Nmu;
         rmu = row % args.Nmu;
@@ -825,12 +885,12 @@ __device__ __forceinline__ void tc_body(const TcArgs* __restrict__ targs,
       // 2^-eX3 of its G split) and a column factor, 2^(ecol - eXt) for X^T and 2^ecol for X
       // (mode 1), 2^(ecol + glob) (mode 2); the column factors of this warp's chunks are
       // tabulated once per tile
-      const bool zvalid = z < args.z_count;
+      const bool zvalid = zq < args.z_count;
       const int* ecol =
           (NUM != kSplit3) ? args.eB + z * args.eB_zstride + sp * args.eB_sstride : nullptr;
       __syncwarp();  // every lane is done with the previous tile's table
       if (zvalid) {
-        const int* exz = args.mode == 1 ? args.eXt + (size_t)z * args.Ap : nullptr;
+        const int* exz = args.mode == 1 ? args.eXt + (size_t)zq * args.Ap : nullptr;
         for (int k = lane; k < (ch1 - ch0) * 16; k += 32) {
           const int c = ch0 * 16 + k;
           const int ec = NUM != kSplit3 ? ecol[c] : 0;
@@ -1169,10 +1229,9 @@ bool tmem_plan(int nn, int per_set, bool intfrac, int& nbuf, int& stride, int& e
 }
 
 template <int BK, int NUM, int PAIR>
-cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
-                      const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
+cudaError_t launch_tc(const TcMaps& m, TcArgs a, cudaStream_t s) {
   if constexpr (NUM == kIntFrac && !PAIR) {
-    if (2 * a.Nn <= 128) return launch_tc<BK, kIntFracCat, 0>(ah, al, bh, bl, a, s);
+    if (2 * a.Nn <= 128) return launch_tc<BK, kIntFracCat, 0>(m, a, s);
   }
   const size_t a_bytes = (size_t)BM * BK * 2, b_bytes = (size_t)(PAIR ? a.Nn / 2 : a.Nn) * BK * 2;
   const size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
@@ -1195,10 +1254,7 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BK, NUM, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const bool sym = BK == 64 && a.sym;
-  const int z_units = (PAIR && sym) ? (a.z_count + 1) / 2 : a.z_count;
-  const int m_units = (PAIR && !sym) ? (a.m_tiles + 1) / 2 : a.m_tiles;
-  const int units = z_units * m_units * a.splits;
+  const int units = tc_units(a, PAIR);
   int work = a.grid > 0 ? a.grid : (PAIR ? num_sms() / 2 : num_sms());  // CTAs or CTA pairs
   if (work > units) work = units;
   if (work < 1) work = 1;
@@ -1215,30 +1271,26 @@ cudaError_t launch_tc(const CUtensorMap& ah, const CUtensorMap& al, const CUtens
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BK, NUM, PAIR>, TcMaps{ah, al, bh, bl}, a);
+    e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BK, NUM, PAIR>, m, a);
     count_launch(1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  k_tc_gemm<BK, NUM, PAIR><<<work, kThreads, smem, s>>>(TcMaps{ah, al, bh, bl}, a);
+  k_tc_gemm<BK, NUM, PAIR><<<work, kThreads, smem, s>>>(m, a);
   count_launch(1);
   return cudaGetLastError();
 }
 
 template <int NUM>
-cudaError_t launch_tc_bk(int bk, const CUtensorMap& ah, const CUtensorMap& al,
-                         const CUtensorMap& bh, const CUtensorMap& bl, TcArgs a, cudaStream_t s) {
-  return bk == 32 ? launch_tc<32, NUM, 0>(ah, al, bh, bl, a, s)
-                  : launch_tc<64, NUM, 0>(ah, al, bh, bl, a, s);
+cudaError_t launch_tc_bk(int bk, const TcMaps& m, TcArgs a, cudaStream_t s) {
+  return bk == 32 ? launch_tc<32, NUM, 0>(m, a, s) : launch_tc<64, NUM, 0>(m, a, s);
 }
 
 // The launch of a tuned variant (the B maps must have boxes of Nn / 2 rows for a pair).
 template <int NUM>
-cudaError_t launch_tc_variant(const TuneCode& t, const CUtensorMap& ah, const CUtensorMap& al,
-                              const CUtensorMap& bh, const CUtensorMap& bl, TcArgs a,
-                              cudaStream_t s) {
-  if (t.pair) return launch_tc<64, NUM, 1>(ah, al, bh, bl, a, s);
-  return launch_tc_bk<NUM>(t.bk, ah, al, bh, bl, a, s);
+cudaError_t launch_tc_variant(const TuneCode& t, const TcMaps& m, TcArgs a, cudaStream_t s) {
+  if (t.pair) return launch_tc<64, NUM, 1>(m, a, s);
+  return launch_tc_bk<NUM>(t.bk, m, a, s);
 }
 
 // ------------------------------------------------------------------ split / scale kernels
@@ -1967,7 +2019,7 @@ int run_extended_product(const Dims& d, int M, const int* eU, const int* eV, int
   TcArgs a;
   TcMaps m;
   if (!ext_setup(d, M, eU, eV, ws, L, a, m)) return DONOF_ERR_CUDA;
-  if (launch_tc<64, kIntFrac, 0>(m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
+  if (launch_tc<64, kIntFrac, 0>(m, a, s) != cudaSuccess)
     return DONOF_ERR_CUDA;
   const long long nb = ((long long)M * ncols + 255) / 256;
   k_sum_blocks<<<(int)(nb < num_sms() * 8 ? nb : num_sms() * 8), 256, 0, s>>>(
@@ -2030,6 +2082,12 @@ bool half_setup(const Dims& d, int p0, int np, const TuneCode& tv, char* ws, con
     a.kt_per_kb = (N + bk - 1) / bk;
     a.sym = 0; a.a_z_unit = 1;
     a.grid = work;
+    // a last row tile of at most 64 AO indices: two slices' last tiles share a unit
+    a.pack2 = (!tv.pair && N - BM * (st.T - 1) <= 64) ? 1 : 0;
+    if (a.pack2 &&
+        (!make_map(&m.ah2, bh, N, N, np, (uint64_t)st.ld * h2, (uint64_t)st.perP * h2, bk, 64) ||
+         !make_map(&m.al2, bl, N, N, np, (uint64_t)st.ld * h2, (uint64_t)st.perP * h2, bk, 64)))
+      return false;
   } else {
     m.ah = m.bh;  // unused: the A tiles come from the bulk copies
     m.al = m.bl;
@@ -2131,7 +2189,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   {
     const TuneCode tv = tuned_variant(1, N, Ap, np);
     if (!half_setup(d, p0, np, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
-    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
+    if (launch_tc_variant<kIntFrac>(tv, m, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_HALF_TRANSFORM, s);
@@ -2140,7 +2198,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   {
     const TuneCode tv = tuned_variant(2, N, Ap, np);
     if (!b_setup(d, np, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
-    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
+    if (launch_tc_variant<kIntFrac>(tv, m, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
   }
   prof_end(DONOF_PHASE_MO_3INDEX, s);
@@ -2153,7 +2211,7 @@ int run_tc_block(const Dims& d, int p0, int np, char* ws, const Layout& L, cudaS
   {
     const TuneCode tv = tuned_variant(3, N, Ap, np);
     if (!g_setup(d, np, splits3, tv, ws, L, a, m)) return DONOF_ERR_CUDA;
-    if (launch_tc_variant<kIntFrac>(tv, m.ah, m.al, m.bh, m.bl, a, s) != cudaSuccess)
+    if (launch_tc_variant<kIntFrac>(tv, m, a, s) != cudaSuccess)
       return DONOF_ERR_CUDA;
     Dims d2 = d;
     d2.splits = a.splits;
@@ -2251,7 +2309,7 @@ bool tc_group_setup(int kind, const Dims& d, char* ws, const Layout& L, void* a_
     case GK_TC_G: ok = g_setup(d, np, sp3, TuneCode{32, 0, 0}, ws, L, a, m); break;
     default: return false;
   }
-  units = a.z_count * a.m_tiles * a.splits;
+  units = tc_units(a, 0);
   return ok;
 }
 
@@ -2443,8 +2501,9 @@ extern "C" int donof_testing_tc_gemm_ex(const uint16_t* A_hi, const uint16_t* A_
   a.glob_exp = words + 0; a.status = words + 1; a.abort_flag = words + 2;
   if (cudaMemsetAsync(words + 2, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
     return DONOF_ERR_CUDA;
-  const cudaError_t e = pair ? launch_tc<64, kSplit3, 1>(ah, al, bh, bl, a, (cudaStream_t)stream)
-                             : launch_tc<64, kSplit3, 0>(ah, al, bh, bl, a, (cudaStream_t)stream);
+  const TcMaps m{ah, al, bh, bl, {}, {}};
+  const cudaError_t e = pair ? launch_tc<64, kSplit3, 1>(m, a, (cudaStream_t)stream)
+                             : launch_tc<64, kSplit3, 0>(m, a, (cudaStream_t)stream);
   return e == cudaSuccess ? DONOF_OK : DONOF_ERR_CUDA;
 }
 
