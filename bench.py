@@ -528,6 +528,19 @@ def run_ours(args):
         u1.record()
         torch.cuda.synchronize()
         upd_ms = u0.elapsed_time(u1) / 3
+        # the eigensolver alone on the same F (donof_eigh; eigenvalues and V in place)
+        Fm = torch.randn(N, N, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        Fm = Fm + Fm.T
+        Vm = torch.empty_like(Fm)
+        wse = dn.donof_eigh(Fm, Vm, epsv)
+        torch.cuda.synchronize()
+        u0.record()
+        for _ in range(3):
+            dn.donof_eigh(Fm, Vm, epsv, ws=wse)
+        u1.record()
+        torch.cuda.synchronize()
+        eigh_ms = u0.elapsed_time(u1) / 3
+        del Fm, Vm, wse
         # measured FP64 peak: a cuBLAS DGEMM (library routine, for the denominator only)
         Ad = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
         Bd = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
@@ -559,6 +572,7 @@ def run_ours(args):
             },
             "status": b64.status(),
             "orbital_update_ms": upd_ms,
+            "eigh_ms": eigh_ms,
         }
 
     # ---------------- errors against the FP64 oracle's stored values (large workload)

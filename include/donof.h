@@ -184,18 +184,44 @@ int donof_optimize_occupations(const donof_problem* prob, const int32_t* pair_ma
 /* Hand-off to the orbital update (Sec. III.B).  Builds the symmetric matrix of Eq. Fockian,
  *   F_qp = theta(p - q)[lambda_qp - lambda_pq] + theta(q - p)[lambda_pq - lambda_qp] (q != p),
  *   F_pp = Fdiag[p]   (the paper takes the diagonal from the previous diagonalisation),
- * diagonalises it in double, F = V diag(eps) V^T with eps ascending, and writes the rotated
+ * diagonalises it in double (donof_eigh), F = V diag(eps) V^T with eps ascending, and writes the rotated
  * orbitals C_new = C V after one double Newton-Schulz reorthonormalisation step
  * C_new <- C_new (3 I - C_new^T C_new) / 2.  lam, Fdiag[nbf], C (device, as in
  * donof_energy_lagrangian) in; C_new[nbf*nbf] (column j = new orbital j) and eps[nbf]
- * (device) out.  Workspace: donof_orbital_update_workspace_size bytes (device, 256-byte
- * aligned).  Note: with lambda as defined here (lambda = C^T G, G = dE/dC / 4) the first-order
+ * (device) out; nbf <= 4096.  Workspace: donof_orbital_update_workspace_size bytes (device,
+ * 256-byte aligned).  Note: with lambda as defined here (lambda = C^T G, G = dE/dC / 4) the first-order
  * energy change of this update is 4 sum_{q<p} F_qp^2 / (F_pp - F_qq), so a diagonal that
  * decreases with the orbital index lowers E (the paper's Eq. ene1 prints the opposite sign). */
 int donof_orbital_update_workspace_size(int32_t nbf, size_t* bytes);
 int donof_orbital_update(int32_t nbf, const double* lam, const double* Fdiag, const double* C,
                          void* workspace, size_t workspace_bytes, double* C_new, double* eps,
                          void* stream);
+
+/* Symmetric eigendecomposition in double: the diagonalisation step of Sec. III.B (the new
+ * orbitals are the eigenvectors of the symmetric F of Eq. Fockian; donof_orbital_update and
+ * donof_optimize call it).  A = V diag(w) V^T with w ascending.
+ *   A[n*n]: device, row-major, symmetric (both triangles are read and must agree); not
+ *           modified.
+ *   V[n*n]: device, row-major, column j = eigenvector j (unit norm); may be A's buffer.
+ *   w[n]:   device, eigenvalues in ascending order.
+ * 1 <= n <= 4096.  Workspace: donof_eigh_workspace_size(n) bytes of device memory, 256-byte
+ * aligned, owned by the caller (one call at a time per workspace).  Method: Householder
+ * reduction to tridiagonal T in one cooperative launch (one CTA per SM); T split where an
+ * off-diagonal element is at most 16 n eps ||T||_inf; eigenvalues by bisection on Sturm
+ * counts; eigenvectors of T from twisted factorisations, and by inverse iteration with
+ * modified Gram-Schmidt for eigenvalues of one block closer than 1e-5 ||T||_inf; V = Q Z in
+ * blocks of 64 reflectors.  Each eigenvalue is within a small multiple of n eps ||A|| of the
+ * exact one and each eigenvector within that over its gap; columns of V are orthonormal to
+ * about n eps ||A|| / (smallest gap outside the clusters).
+ * Returns DONOF_ERR_INVALID_ARG (n out of range, NULL pointer), DONOF_ERR_WORKSPACE, or
+ * DONOF_ERR_CUDA (a failed launch, also when the cooperative launch cannot make its grid
+ * co-resident).  Device-side outcomes (A not finite; a grid-barrier wait that ran out after
+ * 2 s, which leaves NaN eigenvalues) are read with donof_eigh_read_status, which waits for
+ * `stream` and writes DONOF_OK, DONOF_ERR_NONFINITE or DONOF_ERR_TIMEOUT to *status. */
+int donof_eigh_workspace_size(int32_t n, size_t* bytes);
+int donof_eigh(int32_t n, const double* A, double* V, double* w, void* workspace,
+               size_t workspace_bytes, void* stream);
+int donof_eigh_read_status(const void* workspace, int32_t* status, void* stream);
 
 /* Batched builds: ninst independent instances (e.g. one molecule at many geometries), each
  * with its own problem description probs[i] and device pointers inst[i].  The workspace

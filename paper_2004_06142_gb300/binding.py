@@ -106,6 +106,9 @@ def lib() -> ctypes.CDLL:
         L.donof_energy_lagrangian_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, ctypes.c_int32, vp]
         L.donof_orbital_update_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_orbital_update.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp, vp, vp]
+        L.donof_eigh_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_eigh.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp]
+        L.donof_eigh_read_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
         L.donof_autotune.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp]
         L.donof_optimize_occupations.argtypes = [P, vp, vp, vp, sz, ctypes.c_int32,
                                                  ctypes.c_double, vp, vp, vp]
@@ -127,7 +130,8 @@ def lib() -> ctypes.CDLL:
                   "donof_energy_lagrangian_partial", "donof_energy_lagrangian_finish",
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
-                  "donof_orbital_update", "donof_autotune", "donof_optimize_occupations",
+                  "donof_orbital_update", "donof_eigh_workspace_size", "donof_eigh",
+                  "donof_eigh_read_status", "donof_autotune", "donof_optimize_occupations",
                   "donof_optimize_workspace_size", "donof_optimize", "donof_nofmp2_static"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -254,6 +258,27 @@ def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):
                                       _ptr(C_new), _ptr(eps), _stream(stream)),
            "donof_orbital_update")
     return ws
+
+
+def donof_eigh(A, V, w, ws=None, stream=None):
+    """A = V diag(w) V^T in double on the device (w ascending, column j of V eigenvector j);
+    V may be A.  Returns the workspace used."""
+    n = A.shape[0]
+    if ws is None:
+        nb = ctypes.c_size_t(0)
+        _check(lib().donof_eigh_workspace_size(n, ctypes.byref(nb)), "donof_eigh_workspace_size")
+        ws = alloc_workspace(nb.value, A.device)
+    _check(lib().donof_eigh(n, _ptr(A), _ptr(V), _ptr(w), _ptr(ws), ws.numel(), _stream(stream)),
+           "donof_eigh")
+    return ws
+
+
+def donof_eigh_read_status(ws, stream=None):
+    """Device-side status of the last donof_eigh on ``ws`` (waits for the stream)."""
+    st = ctypes.c_int32(0)
+    _check(lib().donof_eigh_read_status(_ptr(ws), ctypes.byref(st), _stream(stream)),
+           "donof_eigh_read_status")
+    return st.value
 
 
 def donof_optimize_occupations(prob, pair_map, gamma, ws, max_iter=500, gtol=1e-9, E=None,

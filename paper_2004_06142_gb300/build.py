@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdonof.so")
 SOURCES = ["api.cu", "fp64.cu", "tc.cu", "noalloc.cu", "batch.cu", "orbital.cu", "occopt.cu", "mid.cu",
-           "nofmp2.cu"]
+           "nofmp2.cu", "eigh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,7 +50,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lcusolver"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

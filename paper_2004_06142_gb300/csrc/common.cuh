@@ -304,6 +304,13 @@ struct DgemmArgs {
 cudaError_t launch_dgemm(const DgemmArgs& a, cudaStream_t s);
 // The split count split_k_args uses for an M x N output with contraction length K.
 int splitk_count(int M, int N, int K);
+// Symmetric FP64 eigensolver (eigh.cu): A (N x N, row-major, symmetric; not modified) =
+// V diag(w) V^T with w ascending and V row-major (column j = eigenvector j).  V may share
+// A's storage.  Workspace: eigh_workspace_bytes(N), 256-byte aligned, its first bytes the
+// solver's device header.
+constexpr int kEighMaxN = 4096;
+size_t eigh_workspace_bytes(int N);
+int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_t s);
 int g_splits_fp64(int N, int A, int np);
 // C(m, n) += sum_k A(m, k) B(k, n) with the contraction cut into 64-wide (or 16-wide) chunks
 // shared by enough CTAs to fill the GPU; `part` holds splitk_count(M, N, K) x M x N doubles

@@ -1,0 +1,965 @@
+// Symmetric FP64 eigensolver of the orbital update (Sec. III.B: the new orbitals are the
+// eigenvectors of the symmetric matrix F of Eq. Fockian, and its eigenvalues the next
+// diagonal).  Laid out for this GPU's narrow FP64 pipe and large L2:
+//   1. A = Q T Q^T by Householder reflections in one cooperative launch (one CTA per SM, one
+//      grid barrier per column).  Each step forms the next column of the rank-2-updated
+//      matrix in every CTA (from one row, by symmetry), its reflector, and then every warp
+//      updates its own rows of the trailing matrix and forms their part of the next
+//      matrix-vector product in the same pass; the matrix stays in L2.  A is first scaled by
+//      a power of two (exact) to a largest element in [1/2, 1).
+//   2. T is split where an off-diagonal element is at most 16 N eps ||T||_inf (a perturbation
+//      of that size moves no eigenvalue by more); eigenvalues of each block by bisection on
+//      Sturm counts, one thread per eigenvalue, the counts from the three-term recurrence of
+//      the leading minors with exact power-of-two rescaling (three FP64 operations a step).
+//   3. Eigenvectors of T from twisted factorisations T - lambda I = N_r D_r N_r^T, one thread
+//      per eigenvalue, the twist r where |gamma_r| is smallest; eigenvalues of one block closer
+//      than 1e-5 ||T||_inf form clusters whose vectors come from inverse iteration (LU with
+//      partial pivoting) and modified Gram-Schmidt inside the cluster.
+//   4. V = Q Z by the compact WY form of blocks of 64 reflectors: the blocks' triangular
+//      factors from their Gram matrices, and two FP64 GEMMs per block.
+#include <float.h>
+
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace donof {
+namespace {
+
+constexpr int kTriThreads = 256;
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr int kNb = 64;           // reflectors per WY block
+constexpr int kSlotThreads = 8;   // threads per CTA of the one-thread-per-eigenvalue kernels
+constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
+constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
+constexpr double kClusterTol = 1e-5;
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
+
+struct EighHdr {
+  unsigned int ctr;   // grid-barrier arrivals of the tridiagonal reduction
+  int abort;          // set when a barrier wait ran out
+  int ncl;            // clusters found
+  int nonfinite;      // A holds a NaN or an infinity
+  unsigned long long amax_bits;  // max |A_ij| (bit pattern of a non-negative double)
+  double scale;       // the power of two applied to A
+  double tnorm;       // ||T||_inf of the scaled tridiagonal matrix
+  double pivmin;      // smallest pivot magnitude of the twisted factorisations
+};
+
+struct EighLayout {
+  size_t hdr, A, Yr, Wd, d, e, es, e2, tau, pbuf, lam, glo, ghi, col, bstart, bend, incl, cl, T,
+      G, W1, W2, part, fix, total;
+  int nref, nblk;
+};
+
+EighLayout eigh_layout(int N) {
+  EighLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  };
+  const size_t n = (size_t)N, nn = n * n;
+  L.nref = N > 2 ? N - 2 : 0;
+  L.nblk = (L.nref + kNb - 1) / kNb;
+  L.hdr = take(sizeof(EighHdr));
+  L.A = take(nn * 8);
+  L.Yr = take(nn * 8);
+  L.Wd = take(nn * 8);
+  L.d = take(n * 8);
+  L.e = take(n * 8);
+  L.es = take(n * 8);
+  L.e2 = take(n * 8);
+  L.tau = take(n * 8);
+  L.pbuf = take(2 * n * 8);
+  L.lam = take(n * 8);
+  L.glo = take(n * 8);
+  L.ghi = take(n * 8);
+  L.col = take(n * 4);
+  L.bstart = take(n * 4);
+  L.bend = take(n * 4);
+  L.incl = take(n * 4);
+  L.cl = take(2 * n * 4);
+  L.T = take((size_t)L.nblk * kNb * kNb * 8);
+  L.G = take((size_t)L.nblk * kNb * kNb * 8);
+  L.W1 = take((size_t)kNb * n * 8);
+  L.W2 = take((size_t)kNb * n * 8);
+  size_t ks = 1;
+  for (int b = 0; b < L.nblk; ++b) {
+    const int m = L.nref - b * kNb < kNb ? L.nref - b * kNb : kNb;
+    const size_t k = (size_t)splitk_count(m, N, N - 1 - b * kNb);
+    if (k > ks) ks = k;
+  }
+  L.part = take(ks > 1 ? ks * kNb * n * 8 : 0);
+  L.fix = take((size_t)kFixCTAs * 6 * n * 8);
+  L.total = off;
+  return L;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA in a fixed order (lane 0 of each warp, then the warps in order): every
+// thread gets the same value.
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < kTriWarps; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// Grid barrier of the cooperative launch: arrivals counted in hdr->ctr (zeroed before the
+// launch); the wait gives up after kBarrierLimitNs and raises hdr->abort, which ends every
+// other CTA's wait at once.  Returns false when the CTA must leave.
+__device__ __forceinline__ bool grid_barrier(EighHdr* h, unsigned target, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&h->ctr, 1u);
+    const unsigned long long t0 = gtimer();
+    int ok = 1;
+    while (*(volatile unsigned*)&h->ctr < target) {
+      if (*(volatile int*)&h->abort) { ok = 0; break; }
+      if (gtimer() - t0 > kBarrierLimitNs) {
+        atomicExch(&h->abort, 1);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Reflector H = I - tau u u^T with u[k0] = 1 and H x[k0..N) = beta e_k0; xn2 is the sum of
+// x[j]^2 over j > k0 (the same value in every thread).  x[k0+1..N) becomes u's tail, x[k0] 1.
+__device__ __forceinline__ void householder(double* x, int k0, int N, double xn2, double& tau,
+                                            double& beta) {
+  const double al = x[k0];
+  __syncthreads();  // every thread has read x[k0]
+  if (xn2 == 0.0) {
+    tau = 0.0;
+    beta = al;
+    for (int j = k0 + 1 + threadIdx.x; j < N; j += blockDim.x) x[j] = 0.0;
+  } else {
+    beta = -copysign(sqrt(al * al + xn2), al);
+    tau = (beta - al) / beta;
+    const double s = 1.0 / (al - beta);
+    for (int j = k0 + 1 + threadIdx.x; j < N; j += blockDim.x) x[j] *= s;
+  }
+  if (threadIdx.x == 0) x[k0] = 1.0;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// 0. max |A| (and a non-finite check), then the scaled copy
+// ---------------------------------------------------------------------------
+__global__ void k_eigh_amax(const double* __restrict__ A, long long nn, EighHdr* h) {
+  __shared__ unsigned long long red[8];
+  unsigned long long m = 0;
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = fabs(A[i]);
+    if (!isfinite(a)) bad = 1;
+    else m = max(m, (unsigned long long)__double_as_longlong(a));
+  }
+  for (int o = 16; o; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  if ((threadIdx.x & 31) == 0 && bad) h->nonfinite = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = max(m, red[i]);
+    atomicMax(&h->amax_bits, m);
+  }
+}
+
+__device__ __forceinline__ double eigh_scale(const EighHdr* h) {
+  const double amax = __longlong_as_double((long long)h->amax_bits);
+  if (amax == 0.0 || h->nonfinite) return 1.0;
+  int ex = 0;
+  frexp(amax, &ex);  // amax = f 2^ex, f in [1/2, 1)
+  return ldexp(1.0, -ex);
+}
+
+__global__ void k_eigh_scale_copy(const double* __restrict__ A, long long nn, EighHdr* h,
+                                  double* __restrict__ out) {
+  const double s = eigh_scale(h);
+  if (blockIdx.x == 0 && threadIdx.x == 0) h->scale = s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = A[i] * s;
+}
+
+// ---------------------------------------------------------------------------
+// 1. Householder tridiagonalisation (cooperative launch, kTriThreads threads, one CTA per SM)
+// ---------------------------------------------------------------------------
+struct TriArgs {
+  int N;
+  double* A;     // N x N, row-major, symmetric; trailing rows updated in place
+  double* Yr;    // reflector k in row k, columns k+1 .. N-1 (zero elsewhere)
+  double* d;     // diagonal of T
+  double* e;     // off-diagonal of T (N - 1)
+  double* tau;   // tau of reflector k
+  double* pbuf;  // two N-vectors: p of the current and the next step
+  EighHdr* hdr;
+};
+
+__global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double red[kTriWarps];
+  __shared__ int s_flag;
+  const int N = a.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int G = gridDim.x;
+  double* v = sm;           // reflector of the current step (indices k+1 .. N-1)
+  double* x = sm + N;       // next column, then its reflector
+  double* w = sm + 2 * N;   // p, then w = p - (tau/2)(p.v) v
+  double* A = a.A;
+  const bool writer = blockIdx.x == 0;
+  if (N <= 2) {
+    if (writer && tid == 0) {
+      a.d[0] = __ldcg(A);
+      if (N == 2) {
+        a.e[0] = __ldcg(A + 1);
+        a.d[1] = __ldcg(A + 3);
+      }
+    }
+    return;
+  }
+  // rows are dealt to CTAs cyclically (row i to CTA i mod G), then to the CTA's warps, so the
+  // shrinking trailing matrix stays spread over every SM
+  auto row_of = [&](int t) { return blockIdx.x + G * (wid + kTriWarps * t); };
+  unsigned bar = 0;
+
+  // reflector 0 from row 0 (column 0)
+  double xn = 0.0;
+  for (int j = tid; j < N; j += kTriThreads) {
+    const double xj = __ldcg(A + j);
+    x[j] = xj;
+    if (j >= 2) xn += xj * xj;
+  }
+  double xn2 = block_sum_d(xn, red);
+  double tau_c, beta;
+  householder(x, 1, N, xn2, tau_c, beta);
+  if (writer) {
+    if (tid == 0) {
+      a.d[0] = x[0];
+      a.e[0] = beta;
+      a.tau[0] = tau_c;
+    }
+    for (int j = 1 + tid; j < N; j += kTriThreads) a.Yr[j] = x[j];
+  }
+  for (int t = 0;; ++t) {
+    const int i = row_of(t);
+    if (i >= N) break;
+    if (i < 1) continue;
+    const double* Ar = A + (size_t)i * N;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int j = 1 + lane; j < N; j += 32) acc += __ldcg(Ar + j) * x[j];
+    acc = warp_sum_d(acc);
+    if (lane == 0) a.pbuf[i] = tau_c * acc;
+  }
+  if (!grid_barrier(a.hdr, (++bar) * G, &s_flag)) return;
+  {
+    double* t = v;
+    v = x;
+    x = t;
+  }
+
+  for (int k = 0; k <= N - 3; ++k) {
+    // w = p_k - (tau_k / 2)(p_k . v_k) v_k
+    const double* pk = a.pbuf + (size_t)(k & 1) * N;
+    double acc = 0.0;
+    for (int j = k + 1 + tid; j < N; j += kTriThreads) {
+      const double pj = __ldcg(pk + j);
+      w[j] = pj;
+      acc += pj * v[j];
+    }
+    const double aw = 0.5 * tau_c * block_sum_d(acc, red);
+    for (int j = k + 1 + tid; j < N; j += kTriThreads) w[j] -= aw * v[j];
+    __syncthreads();
+    // row k+1 of the updated matrix (v[k+1] = 1): its column k+1 below the diagonal
+    const double wk1 = w[k + 1];
+    const double* Ak1 = A + (size_t)(k + 1) * N;
+    xn = 0.0;
+    for (int j = k + 1 + tid; j < N; j += kTriThreads) {
+      const double xj = __ldcg(Ak1 + j) - w[j] - wk1 * v[j];
+      x[j] = xj;
+      if (j >= k + 3) xn += xj * xj;
+    }
+    xn2 = block_sum_d(xn, red);
+    if (k + 1 == N - 2) {  // the last 2 x 2 block
+      if (writer && tid == 0) {
+        a.d[N - 2] = x[N - 2];
+        a.e[N - 2] = x[N - 1];
+        a.d[N - 1] = __ldcg(A + (size_t)(N - 1) * N + N - 1) - 2.0 * v[N - 1] * w[N - 1];
+      }
+      break;
+    }
+    double tau_n;
+    householder(x, k + 2, N, xn2, tau_n, beta);
+    if (writer) {
+      if (tid == 0) {
+        a.d[k + 1] = x[k + 1];
+        a.e[k + 1] = beta;
+        a.tau[k + 1] = tau_n;
+      }
+      double* Yk = a.Yr + (size_t)(k + 1) * N;
+      for (int j = k + 2 + tid; j < N; j += kTriThreads) Yk[j] = x[j];
+    }
+    // own rows i >= k+2: A_ij -= v_i w_j + w_i v_j (j >= k+2), and p_{k+1} = tau A u
+    double* pn = a.pbuf + (size_t)((k + 1) & 1) * N;
+    for (int t = 0;; ++t) {
+      const int i = row_of(t);
+      if (i >= N) break;
+      if (i < k + 2) continue;
+      double* Ar = A + (size_t)i * N;
+      const double vi = v[i], wi = w[i];
+      double acc2 = 0.0;
+      int j = k + 2 + lane;
+      for (; j + 96 < N; j += 128) {
+        const double a0 = __ldcg(Ar + j), a1 = __ldcg(Ar + j + 32), a2 = __ldcg(Ar + j + 64),
+                     a3 = __ldcg(Ar + j + 96);
+        const double b0 = a0 - vi * w[j] - wi * v[j];
+        const double b1 = a1 - vi * w[j + 32] - wi * v[j + 32];
+        const double b2 = a2 - vi * w[j + 64] - wi * v[j + 64];
+        const double b3 = a3 - vi * w[j + 96] - wi * v[j + 96];
+        Ar[j] = b0;
+        Ar[j + 32] = b1;
+        Ar[j + 64] = b2;
+        Ar[j + 96] = b3;
+        acc2 += b0 * x[j];
+        acc2 += b1 * x[j + 32];
+        acc2 += b2 * x[j + 64];
+        acc2 += b3 * x[j + 96];
+      }
+      for (; j < N; j += 32) {
+        const double b0 = __ldcg(Ar + j) - vi * w[j] - wi * v[j];
+        Ar[j] = b0;
+        acc2 += b0 * x[j];
+      }
+      acc2 = warp_sum_d(acc2);
+      if (lane == 0) pn[i] = tau_n * acc2;
+    }
+    if (!grid_barrier(a.hdr, (++bar) * G, &s_flag)) return;
+    double* t = v;
+    v = x;
+    x = t;
+    tau_c = tau_n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. splitting, Gershgorin bounds, bisection
+// ---------------------------------------------------------------------------
+// One CTA: ||T||_inf, the split off-diagonal es (and es^2), the blocks (bstart/bend of every
+// row), each block's Gershgorin interval (at its first row) and the pivot floor.
+__global__ void k_tri_prep(int N, const double* __restrict__ d, const double* __restrict__ e,
+                           EighHdr* h, double* es, double* e2, int* bstart, int* bend,
+                           double* glo, double* ghi) {
+  extern __shared__ double sp[];
+  double* sd = sp;       // d
+  double* se = sp + N;   // es
+  __shared__ double red[8];
+  double tn = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double di = d[i];
+    sd[i] = di;
+    const double r = fabs(di) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < N - 1 ? fabs(e[i]) : 0.0);
+    tn = fmax(tn, r);
+  }
+  for (int o = 16; o; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tn;
+  __syncthreads();
+  tn = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tn = fmax(tn, red[i]);
+  if (!(tn > 0.0)) tn = 1.0;  // T = 0 (or NaN: the eigenvalues come out NaN)
+  const double thresh = 16.0 * N * DBL_EPSILON * tn;
+  double emax = 0.0;
+  for (int i = threadIdx.x; i < N - 1; i += blockDim.x) {
+    const double ei = e[i];
+    const double v = fabs(ei) <= thresh ? 0.0 : ei;
+    se[i] = v;
+    es[i] = v;
+    e2[i] = v * v;
+    emax = fmax(emax, v * v);
+  }
+  for (int o = 16; o; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  emax = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) emax = fmax(emax, red[i]);
+  h->tnorm = tn;
+  h->pivmin = DBL_MIN * fmax(1.0, emax);
+  int s0 = 0;
+  double lo = 0.0, hi = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double el = i > s0 ? fabs(se[i - 1]) : 0.0;
+    const double er = i < N - 1 ? fabs(se[i]) : 0.0;
+    const double l = sd[i] - el - er, u = sd[i] + el + er;
+    lo = i == s0 ? l : fmin(lo, l);
+    hi = i == s0 ? u : fmax(hi, u);
+    if (i == N - 1 || se[i] == 0.0) {
+      for (int r = s0; r <= i; ++r) {
+        bstart[r] = s0;
+        bend[r] = i + 1;
+      }
+      glo[s0] = lo;
+      ghi[s0] = hi;
+      s0 = i + 1;
+    }
+  }
+}
+
+// Number of eigenvalues of the block [s0, s1) below sig: sign changes of the leading minors
+// p_i = (d_i - sig) p_{i-1} - e_{i-1}^2 p_{i-2} (a zero minor counts as a tiny negative ratio),
+// the pair (p_{i-1}, p_i) rescaled by 2^-+600 whenever its larger magnitude leaves
+// [2^-600, 2^600].
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
+                                           const double* __restrict__ e2, int s0, int s1,
+                                           double sig) {
+  double p0 = 1.0, p1 = d[s0] - sig;
+  if (p1 == 0.0) p1 = -0x1p-60;
+  int cnt = signbit(p1) ? 1 : 0;
+#pragma unroll 4
+  for (int i = s0 + 1; i < s1; ++i) {
+    double p2 = fma(d[i] - sig, p1, -(e2[i - 1] * p0));
+    if (p2 == 0.0) p2 = -p1 * 0x1p-60;
+    cnt += (signbit(p2) != signbit(p1)) ? 1 : 0;
+    const int ex = max((__double2hiint(p1) >> 20) & 0x7ff, (__double2hiint(p2) >> 20) & 0x7ff);
+    if (ex > 1023 + 600) {
+      p1 *= 0x1p-600;
+      p2 *= 0x1p-600;
+    } else if (ex < 1023 - 600) {
+      p1 *= 0x1p600;
+      p2 *= 0x1p600;
+    }
+    p0 = p1;
+    p1 = p2;
+  }
+  return cnt;
+}
+
+// eigenvalue k = s - bstart[s] of the block holding row s (ascending within the block)
+__global__ void k_bisect(int N, const double* __restrict__ d, const double* __restrict__ e2,
+                         const int* __restrict__ bstart, const int* __restrict__ bend,
+                         const double* __restrict__ glo, const double* __restrict__ ghi,
+                         const EighHdr* h, double* lam) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  if (h->abort) {
+    lam[s] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const int s0 = bstart[s], s1 = bend[s], k = s - s0;
+  if (s1 - s0 == 1) {
+    lam[s] = d[s0];
+    return;
+  }
+  const double tn = h->tnorm;
+  const double pad = 2.0 * N * DBL_EPSILON * tn + 4.0 * h->pivmin;
+  double lo = glo[s0] - pad, hi = ghi[s0] + pad;
+  for (int it = 0; it < 96; ++it) {
+    if (!(hi - lo > fmax(DBL_EPSILON * tn, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))))) break;
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(d, e2, s0, s1, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  lam[s] = 0.5 * (lo + hi);
+}
+
+// Rank of every eigenvalue (ties by slot), eigenvalues of A in ascending order; CTA 0 also
+// lists the clusters: runs of a block's consecutive eigenvalues closer than kClusterTol ||T||.
+__global__ void k_rank_plan(int N, const double* __restrict__ lam, const int* __restrict__ bend,
+                            EighHdr* h, int* col, double* w_out, int* incl, int* cl) {
+  extern __shared__ double sl[];
+  int* sb = (int*)(sl + N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sl[i] = lam[i];
+    sb[i] = bend[i];
+  }
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < N) {
+    const double ls = sl[s];
+    int r = 0;
+    for (int t = 0; t < N; ++t) {
+      const double lt = sl[t];
+      r += (lt < ls || (lt == ls && t < s)) ? 1 : 0;
+    }
+    if (r > N - 1 || ls != ls) r = s;  // NaN (a failed reduction): its own slot
+    col[s] = r;
+    w_out[r] = ls / h->scale;
+  }
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double tol = kClusterTol * h->tnorm;
+  int ncl = 0;
+  for (int s0 = 0; s0 < N;) {
+    int t = s0;
+    while (t + 1 < sb[s0] && sl[t + 1] - sl[t] < tol) ++t;
+    for (int u = s0; u <= t; ++u) incl[u] = t > s0 ? 1 : 0;
+    if (t > s0) {
+      cl[2 * ncl] = s0;
+      cl[2 * ncl + 1] = t - s0 + 1;
+      ++ncl;
+    }
+    s0 = t + 1;
+  }
+  h->ncl = ncl;
+}
+
+// ---------------------------------------------------------------------------
+// 3. eigenvectors of T
+// ---------------------------------------------------------------------------
+// Twisted factorisation of T_b - lambda I for an eigenvalue outside the clusters: forward
+// pivots D+ (kept in Z's column), backward pivots D- (in Wd), gamma_i = D+_i + D-_i - (d_i -
+// lambda), then z_r = 1 and z_i = -e_i z_{i+1} / D+_i above r, z_i = -e_{i-1} z_{i-1} / D-_i
+// below.  Z[i][col] (row-major, column = rank of the eigenvalue), zero outside the block.
+__device__ __forceinline__ double pivot_floor(double v, double pivmin) {
+  return fabs(v) < pivmin ? -pivmin : v;
+}
+
+__global__ void k_twisted(int N, const double* __restrict__ d, const double* __restrict__ es,
+                          const double* __restrict__ e2, const int* __restrict__ bstart,
+                          const int* __restrict__ bend, const double* __restrict__ lam,
+                          const int* __restrict__ col, const int* __restrict__ incl,
+                          const EighHdr* h, double* Z, double* Wd) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int s0 = bstart[s], s1 = bend[s], c = col[s];
+  const size_t ld = (size_t)N;
+  if (s1 - s0 == 1) {
+    Z[s0 * ld + c] = 1.0;
+    return;
+  }
+  if (incl[s]) return;
+  const double lm = lam[s], pm = h->pivmin;
+  double dp = pivot_floor(d[s0] - lm, pm);
+  Z[s0 * ld + c] = dp;
+  for (int i = s0 + 1; i < s1; ++i) {
+    dp = pivot_floor((d[i] - lm) - e2[i - 1] / dp, pm);
+    Z[i * ld + c] = dp;
+  }
+  double dm = pivot_floor(d[s1 - 1] - lm, pm);
+  Wd[(s1 - 1) * ld + c] = dm;
+  double best = fabs(dp);
+  int r = s1 - 1;
+  for (int i = s1 - 2; i >= s0; --i) {
+    const double ci = d[i] - lm;
+    dm = pivot_floor(ci - e2[i] / dm, pm);
+    Wd[i * ld + c] = dm;
+    const double g = fabs(Z[i * ld + c] + dm - ci);
+    if (g <= best) {
+      best = g;
+      r = i;
+    }
+  }
+  Z[r * ld + c] = 1.0;
+  double z = 1.0;
+  for (int i = r - 1; i >= s0; --i) {
+    z = -es[i] * z / Z[i * ld + c];
+    if (fabs(z) > 1e150) {  // rescale what is written (rare: a tiny pivot)
+      for (int u = i + 1; u <= r; ++u) Z[u * ld + c] *= 1e-150;
+      z *= 1e-150;
+    }
+    Z[i * ld + c] = z;
+  }
+  z = Z[r * ld + c];
+  for (int i = r + 1; i < s1; ++i) {
+    z = -es[i - 1] * z / Wd[i * ld + c];
+    if (fabs(z) > 1e150) {
+      for (int u = s0; u < i; ++u) Z[u * ld + c] *= 1e-150;
+      z *= 1e-150;
+    }
+    Z[i * ld + c] = z;
+  }
+  double n2 = 0.0;
+  for (int i = s0; i < s1; ++i) {
+    const double zi = Z[i * ld + c];
+    n2 += zi * zi;
+  }
+  const double sc = 1.0 / sqrt(n2);
+  for (int i = s0; i < s1; ++i) Z[i * ld + c] *= sc;
+}
+
+__device__ __forceinline__ double hash_uniform(unsigned long long key) {
+  // splitmix64 (Steele, Lea and Flood, 2014), mapped to [-1, 1)
+  unsigned long long z = key + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+
+// Clusters: for each member in order, three steps of inverse iteration from a pseudo-random
+// start, (T_b - lambda I) y = x by LU with partial pivoting (pivots below eps ||T|| raised to
+// that size), each followed by modified Gram-Schmidt against the members before it.  One warp
+// per cluster; lane 0 factors and solves, the warp does the vector work.
+__global__ void __launch_bounds__(32) k_cluster_fix(int N, const double* __restrict__ d,
+                                                    const double* __restrict__ es,
+                                                    const int* __restrict__ bstart,
+                                                    const int* __restrict__ bend,
+                                                    const double* __restrict__ lam,
+                                                    const int* __restrict__ col,
+                                                    const int* __restrict__ cl, const EighHdr* h,
+                                                    double* Z, double* scratch) {
+  const int ncl = h->ncl, lane = threadIdx.x;
+  const size_t ld = (size_t)N;
+  double* dl = scratch + (size_t)blockIdx.x * 6 * N;
+  double* dd = dl + N;
+  double* du = dd + N;
+  double* du2 = du + N;
+  double* pv = du2 + N;
+  double* xv = pv + N;
+  const double tiny = DBL_EPSILON * h->tnorm;
+  for (int q = blockIdx.x; q < ncl; q += gridDim.x) {
+    const int s = cl[2 * q], m = cl[2 * q + 1];
+    const int a0 = bstart[s], L = bend[s] - a0;
+    for (int j = 0; j < m; ++j) {
+      const double lm = lam[s + j];
+      if (lane == 0) {
+        for (int i = 0; i < L; ++i) dd[i] = d[a0 + i] - lm;
+        for (int i = 0; i + 1 < L; ++i) {
+          dl[i] = es[a0 + i];
+          du[i] = es[a0 + i];
+          du2[i] = 0.0;
+        }
+        for (int i = 0; i + 1 < L; ++i) {
+          if (fabs(dd[i]) >= fabs(dl[i])) {
+            pv[i] = 0.0;
+            const double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
+            dl[i] = f;
+            dd[i + 1] -= f * du[i];
+          } else {
+            pv[i] = 1.0;
+            const double f = dd[i] / dl[i];
+            dd[i] = dl[i];
+            dl[i] = f;
+            const double t = du[i];
+            du[i] = dd[i + 1];
+            dd[i + 1] = t - f * dd[i + 1];
+            if (i + 2 < L) {
+              du2[i] = du[i + 1];
+              du[i + 1] = -f * du[i + 1];
+            }
+          }
+        }
+        for (int i = 0; i < L; ++i)
+          if (fabs(dd[i]) < tiny) dd[i] = dd[i] < 0.0 ? -tiny : tiny;
+      }
+      for (int i = lane; i < L; i += 32)
+        xv[i] = hash_uniform(((unsigned long long)(s + j) << 32) + (unsigned long long)i);
+      __syncwarp();
+      for (int it = 0; it < 3; ++it) {
+        if (lane == 0) {
+          for (int i = 0; i + 1 < L; ++i) {
+            if (pv[i] == 0.0) {
+              xv[i + 1] -= dl[i] * xv[i];
+            } else {
+              const double t = xv[i];
+              xv[i] = xv[i + 1];
+              xv[i + 1] = t - dl[i] * xv[i];
+            }
+          }
+          for (int i = L - 1; i >= 0; --i) {
+            double b = xv[i];
+            if (i + 1 < L) b -= du[i] * xv[i + 1];
+            if (i + 2 < L) b -= du2[i] * xv[i + 2];
+            b /= dd[i];
+            xv[i] = b;
+            if (fabs(b) > 1e100)
+              for (int u = 0; u < L; ++u) xv[u] *= 1e-100;
+          }
+        }
+        __syncwarp();
+        for (int jj = 0; jj < j; ++jj) {
+          const int cj = col[s + jj];
+          double dot = 0.0;
+          for (int i = lane; i < L; i += 32) dot += Z[(a0 + i) * ld + cj] * xv[i];
+          dot = __shfl_sync(0xffffffffu, warp_sum_d(dot), 0);
+          for (int i = lane; i < L; i += 32) xv[i] -= dot * Z[(a0 + i) * ld + cj];
+          __syncwarp();
+        }
+        double n2 = 0.0;
+        for (int i = lane; i < L; i += 32) n2 += xv[i] * xv[i];
+        n2 = __shfl_sync(0xffffffffu, warp_sum_d(n2), 0);
+        const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+        for (int i = lane; i < L; i += 32) xv[i] *= sc;
+        __syncwarp();
+      }
+      const int cj = col[s + j];
+      for (int i = lane; i < L; i += 32) Z[(a0 + i) * ld + cj] = xv[i];
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. back-transformation V = Q Z, Q = H_0 ... H_{nref-1} in blocks of kNb reflectors
+// ---------------------------------------------------------------------------
+// Gram matrices G_b = Y_b^T Y_b of every block (entries c <= c' only), Y_b's column c the
+// reflector k0 + c: grid (nblk, 4, 4) of 16 x 16 sub-tiles, upper ones only.
+__global__ void __launch_bounds__(256) k_gram(int N, int nref, const double* __restrict__ Yr,
+                                              double* G) {
+  const int b = blockIdx.x, tr = blockIdx.y, tc = blockIdx.z;
+  if (tr > tc) return;
+  __shared__ double Ys[2][16][65];
+  const int k0 = b * kNb;
+  const int m = nref - k0 < kNb ? nref - k0 : kNb;
+  const int r = threadIdx.x / 16, c = threadIdx.x % 16;
+  const int gr = tr * 16 + r, gc = tc * 16 + c;
+  double acc = 0.0;
+  for (int j0 = k0 + 1; j0 < N; j0 += 64) {
+    for (int idx = threadIdx.x; idx < 2 * 16 * 64; idx += 256) {
+      const int which = idx / 1024, rr = (idx / 64) % 16, jj = idx % 64;
+      const int refl = (which == 0 ? tr : tc) * 16 + rr;
+      const int j = j0 + jj;
+      Ys[which][rr][jj] = (refl < m && j < N) ? Yr[(size_t)(k0 + refl) * N + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 64; ++jj) acc += Ys[0][r][jj] * Ys[1][c][jj];
+    __syncthreads();
+  }
+  G[(size_t)b * kNb * kNb + gr * kNb + gc] = acc;
+}
+
+// Triangular factors T_b (upper): T_ii = tau_i, T[r][i] = -tau_i sum_{c=r}^{i-1} T[r][c] G[c][i]
+// (r < i); thread r forms row r.
+__global__ void k_tfactor(int nref, const double* __restrict__ tau, const double* __restrict__ G,
+                          double* T) {
+  const int b = blockIdx.x, r = threadIdx.x;
+  const int k0 = b * kNb;
+  const int m = nref - k0 < kNb ? nref - k0 : kNb;
+  const double* Gb = G + (size_t)b * kNb * kNb;
+  double* Tb = T + (size_t)b * kNb * kNb + (size_t)r * kNb;
+  for (int i = 0; i < kNb; ++i) {
+    double v = 0.0;
+    if (r < m && i < m) {
+      if (r == i) {
+        v = tau[k0 + i];
+      } else if (r < i) {
+        double acc = 0.0;
+        for (int c = r; c < i; ++c) acc += Tb[c] * Gb[c * kNb + i];
+        v = -tau[k0 + i] * acc;
+      }
+    }
+    Tb[i] = v;
+  }
+}
+
+// W2 = T_b W1 (m x N), kApplyCols columns of W1 per CTA, thread r one row.
+__global__ void __launch_bounds__(kNb) k_apply_tfactor(int N, int m, const double* __restrict__ Tb,
+                                                       const double* __restrict__ W1, double* W2) {
+  __shared__ double Ts[kNb][kNb + 1];
+  __shared__ double Ws[kNb][kApplyCols];
+  const int r = threadIdx.x, c0 = blockIdx.x * kApplyCols;
+  for (int i = 0; i < kNb; ++i) Ts[i][r] = Tb[i * kNb + r];
+  for (int cc = 0; cc < kApplyCols; ++cc) {
+    const int c = c0 + cc;
+    Ws[r][cc] = (r < m && c < N) ? W1[(size_t)r * N + c] : 0.0;
+  }
+  __syncthreads();
+  if (r >= m) return;
+  double acc[kApplyCols];
+#pragma unroll
+  for (int cc = 0; cc < kApplyCols; ++cc) acc[cc] = 0.0;
+  for (int c = r; c < m; ++c) {
+    const double t = Ts[r][c];
+#pragma unroll
+    for (int cc = 0; cc < kApplyCols; ++cc) acc[cc] += t * Ws[c][cc];
+  }
+#pragma unroll
+  for (int cc = 0; cc < kApplyCols; ++cc) {
+    const int c = c0 + cc;
+    if (c < N) W2[(size_t)r * N + c] = acc[cc];
+  }
+}
+
+struct DevInfo {
+  int sms = 0;
+};
+std::mutex g_dev_mu;
+std::map<int, DevInfo> g_dev;
+
+int device_sms(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DONOF_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev.find(dev);
+  if (it == g_dev.end()) {
+    DevInfo di;
+    if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return DONOF_ERR_CUDA;
+    it = g_dev.emplace(dev, di).first;
+  }
+  *sms = it->second.sms;
+  return DONOF_OK;
+}
+
+}  // namespace
+
+size_t eigh_workspace_bytes(int N) { return eigh_layout(N).total; }
+
+int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_t s) {
+  if (N < 1 || N > kEighMaxN || !A || !V || !w || !ws) return DONOF_ERR_INVALID_ARG;
+  const EighLayout L = eigh_layout(N);
+  EighHdr* hdr = (EighHdr*)(ws + L.hdr);
+  double* Aw = (double*)(ws + L.A);
+  double* Yr = (double*)(ws + L.Yr);
+  double* Wd = (double*)(ws + L.Wd);
+  double* d = (double*)(ws + L.d);
+  double* e = (double*)(ws + L.e);
+  double* es = (double*)(ws + L.es);
+  double* e2 = (double*)(ws + L.e2);
+  double* tau = (double*)(ws + L.tau);
+  double* lam = (double*)(ws + L.lam);
+  double* glo = (double*)(ws + L.glo);
+  double* ghi = (double*)(ws + L.ghi);
+  int* col = (int*)(ws + L.col);
+  int* bstart = (int*)(ws + L.bstart);
+  int* bend = (int*)(ws + L.bend);
+  int* incl = (int*)(ws + L.incl);
+  int* cl = (int*)(ws + L.cl);
+  double* T = (double*)(ws + L.T);
+  double* G = (double*)(ws + L.G);
+  double* W1 = (double*)(ws + L.W1);
+  double* W2 = (double*)(ws + L.W2);
+  double* part = (double*)(ws + L.part);
+  double* fix = (double*)(ws + L.fix);
+  const long long nn = (long long)N * N;
+  const size_t nnb = (size_t)nn * 8;
+  auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+
+  if (!ok(cudaMemsetAsync(hdr, 0, sizeof(EighHdr), s))) return DONOF_ERR_CUDA;
+  const int gcopy = (int)((nn + 255) / 256 < 152 * 4 ? (nn + 255) / 256 : 152 * 4);
+  k_eigh_amax<<<gcopy, 256, 0, s>>>(A, nn, hdr);
+  k_eigh_scale_copy<<<gcopy, 256, 0, s>>>(A, nn, hdr, Aw);
+  count_launch(2);
+  // V may share A's storage: it is written only after the scaled copy
+  if (!ok(cudaMemsetAsync(Yr, 0, nnb, s)) || !ok(cudaMemsetAsync(V, 0, nnb, s)))
+    return DONOF_ERR_CUDA;
+
+  // 1. tridiagonal reduction, one CTA per SM, co-resident (cooperative launch)
+  int sms = 0;
+  int rc = device_sms(&sms);
+  if (rc != DONOF_OK) return rc;
+  const size_t tri_smem = (size_t)3 * N * 8;
+  if (!ok(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tri_smem)))
+    return DONOF_ERR_CUDA;
+  int occ = 0;
+  if (!ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag, kTriThreads, tri_smem)) ||
+      occ < 1)
+    return DONOF_ERR_CUDA;
+  TriArgs ta{N, Aw, Yr, d, e, tau, (double*)(ws + L.pbuf), hdr};
+  void* targs[] = {&ta};
+  if (!ok(cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(sms), dim3(kTriThreads), targs,
+                                      tri_smem, s)))
+    return DONOF_ERR_CUDA;
+  count_launch(1);
+
+  // 2. eigenvalues
+  const size_t prep_smem = (size_t)2 * N * 8;
+  if (!ok(cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)prep_smem)))
+    return DONOF_ERR_CUDA;
+  k_tri_prep<<<1, 256, prep_smem, s>>>(N, d, e, hdr, es, e2, bstart, bend, glo, ghi);
+  const int gslot = (N + kSlotThreads - 1) / kSlotThreads;
+  k_bisect<<<gslot, kSlotThreads, 0, s>>>(N, d, e2, bstart, bend, glo, ghi, hdr, lam);
+  const size_t rank_smem = (size_t)N * 12;
+  if (!ok(cudaFuncSetAttribute(k_rank_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rank_smem)))
+    return DONOF_ERR_CUDA;
+  k_rank_plan<<<(N + 255) / 256, 256, rank_smem, s>>>(N, lam, bend, hdr, col, w, incl, cl);
+  // 3. eigenvectors of T (into V)
+  k_twisted<<<gslot, kSlotThreads, 0, s>>>(N, d, es, e2, bstart, bend, lam, col, incl, hdr, V,
+                                           Wd);
+  k_cluster_fix<<<kFixCTAs, 32, 0, s>>>(N, d, es, bstart, bend, lam, col, cl, hdr, V, fix);
+  count_launch(5);
+  if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
+
+  // 4. V = Q Z
+  if (L.nblk > 0) {
+    k_gram<<<dim3(L.nblk, 4, 4), 256, 0, s>>>(N, L.nref, Yr, G);
+    k_tfactor<<<L.nblk, kNb, 0, s>>>(L.nref, tau, G, T);
+    count_launch(2);
+  }
+  for (int b = L.nblk - 1; b >= 0; --b) {
+    const int k0 = b * kNb;
+    const int m = L.nref - k0 < kNb ? L.nref - k0 : kNb;
+    const int R0 = k0 + 1, nR = N - R0;
+    // W1 = Y_b^T Z[R0:, :]
+    if (!ok(cudaMemsetAsync(W1, 0, (size_t)m * N * 8, s))) return DONOF_ERR_CUDA;
+    if (!ok(launch_dgemm(split_k_args(m, N, nR, Yr + (size_t)k0 * N + R0, N, 1, V + (size_t)R0 * N,
+                                      N, 1, W1, N, 1, part),
+                         s)))
+      return DONOF_ERR_CUDA;
+    // W2 = T_b W1
+    k_apply_tfactor<<<(N + kApplyCols - 1) / kApplyCols, kNb, 0, s>>>(
+        N, m, T + (size_t)b * kNb * kNb, W1, W2);
+    count_launch(1);
+    // Z[R0:, :] -= Y_b W2
+    DgemmArgs u{};
+    u.M = nR; u.N = N; u.K = m; u.KB = 1; u.batch = 1; u.ksplit = 1;
+    u.A = Yr + (size_t)k0 * N + R0; u.sAm = 1; u.sAk = N;
+    u.B = W2; u.sBk = N; u.sBn = 1;
+    u.C = V + (size_t)R0 * N; u.sCm = N; u.sCn = 1;
+    u.alpha = -1.0; u.beta = 1.0;
+    if (!ok(launch_dgemm(u, s))) return DONOF_ERR_CUDA;
+  }
+  return ok(cudaGetLastError()) ? DONOF_OK : DONOF_ERR_CUDA;
+}
+
+}  // namespace donof
+
+using namespace donof;
+
+extern "C" int donof_eigh_workspace_size(int32_t n, size_t* bytes) {
+  if (n < 1 || n > kEighMaxN || !bytes) return DONOF_ERR_INVALID_ARG;
+  *bytes = eigh_workspace_bytes(n);
+  return DONOF_OK;
+}
+
+extern "C" int donof_eigh(int32_t n, const double* A, double* V, double* w, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (n < 1 || n > kEighMaxN || !A || !V || !w) return DONOF_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < eigh_workspace_bytes(n) ||
+      ((uintptr_t)workspace % kAlign) != 0)
+    return DONOF_ERR_WORKSPACE;
+  return eigh_run(n, A, V, w, (char*)workspace, (cudaStream_t)stream);
+}
+
+extern "C" int donof_eigh_read_status(const void* workspace, int32_t* status, void* stream) {
+  if (!workspace || !status) return DONOF_ERR_INVALID_ARG;
+  EighHdr h{};
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DONOF_ERR_CUDA;
+  *status = h.abort ? DONOF_ERR_TIMEOUT : (h.nonfinite ? DONOF_ERR_NONFINITE : DONOF_OK);
+  return DONOF_OK;
+}

@@ -1,35 +1,13 @@
 // Hand-off to the orbital update (Sec. III.B): the symmetric matrix F of Eq. Fockian from the
 // Lagrangian lambda and a given diagonal, its FP64 eigendecomposition, the rotated orbitals
 // C V and their FP64 reorthonormalisation (one Newton-Schulz step C (3I - C^T C) / 2).
-// The eigensolver is cuSOLVER's divide-and-conquer syevd (a plain library routine, as cuBLAS
-// would be for a plain GEMM); everything else runs in this library's kernels.
-#include <cusolverDn.h>
-
-#include <map>
-#include <mutex>
+// The eigendecomposition is this library's own FP64 solver (eigh.cu).
 #include <vector>
 
 #include "common.cuh"
 
 namespace donof {
 namespace {
-
-std::mutex g_sol_mu;
-std::map<int, cusolverDnHandle_t> g_sol;
-
-int solver(cusolverDnHandle_t* h) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DONOF_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_sol_mu);
-  auto it = g_sol.find(dev);
-  if (it == g_sol.end()) {
-    cusolverDnHandle_t s = nullptr;
-    if (cusolverDnCreate(&s) != CUSOLVER_STATUS_SUCCESS) return DONOF_ERR_CUDA;
-    it = g_sol.emplace(dev, s).first;
-  }
-  *h = it->second;
-  return DONOF_OK;
-}
 
 // F[q][p] per Eq. Fockian (row-major, symmetric), diagonal from Fdiag.
 __global__ void k_fockian(const double* __restrict__ lam, const double* __restrict__ Fdiag, int N,
@@ -93,16 +71,9 @@ int sym_product(DgemmArgs a, cudaStream_t s) {
 using namespace donof;
 
 extern "C" int donof_orbital_update_workspace_size(int32_t nbf, size_t* bytes) {
-  if (nbf < 1 || !bytes) return DONOF_ERR_INVALID_ARG;
-  cusolverDnHandle_t h = nullptr;
-  int rc = solver(&h);
-  if (rc != DONOF_OK) return rc;
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nbf,
-                                  nullptr, nbf, nullptr, &lwork) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
+  if (nbf < 1 || nbf > kEighMaxN || !bytes) return DONOF_ERR_INVALID_ARG;
   const size_t nn = (size_t)nbf * nbf * 8;
-  *bytes = 3 * align_up(nn) + align_up((size_t)lwork * 8) + kAlign;
+  *bytes = 3 * align_up(nn) + eigh_workspace_bytes(nbf);
   return DONOF_OK;
 }
 
@@ -115,35 +86,24 @@ extern "C" int donof_orbital_update(int32_t nbf, const double* lam, const double
   if (rc != DONOF_OK) return rc;
   if (!workspace || workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0)
     return DONOF_ERR_WORKSPACE;
-  cusolverDnHandle_t h = nullptr;
-  rc = solver(&h);
-  if (rc != DONOF_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return DONOF_ERR_CUDA;
   const int N = nbf;
   const size_t nn = align_up((size_t)N * N * 8);
   char* ws = (char*)workspace;
-  double* F = (double*)ws;             // F, then its eigenvectors
+  double* F = (double*)ws;             // F, then its eigenvectors V (row-major)
   double* T = (double*)(ws + nn);      // C V
   double* S = (double*)(ws + 2 * nn);  // T^T T, then (3I - T^T T) / 2
-  int* info = (int*)(ws + 3 * nn);
-  double* work = (double*)(ws + 3 * nn + kAlign);
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, F, N, eps,
-                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
+  char* ews = ws + 3 * nn;             // the eigensolver's workspace
 
   prof_begin(DONOF_PHASE_ORBITAL_UPDATE, s);
   k_fockian<<<152 * 4, 256, 0, s>>>(lam, Fdiag, N, F);
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return DONOF_ERR_CUDA;
-  // F is symmetric, so its row-major storage is also its column-major storage; on return
-  // column j of the column-major result (row j of the row-major view) is eigenvector j.
-  if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, F, N, eps, work,
-                       lwork, info) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
-  // T[mu][j] = sum_i C[mu][i] V[i][j], V[i][j] = F[j * N + i]
-  if (launch_dgemm(plain(N, N, N, C, N, 1, F, 1, N, T), s) != cudaSuccess) return DONOF_ERR_CUDA;
+  // F = V diag(eps) V^T, V over F's storage (row-major, column j = eigenvector j)
+  rc = eigh_run(N, F, F, eps, ews, s);
+  if (rc != DONOF_OK) return rc;
+  // T[mu][j] = sum_i C[mu][i] V[i][j]
+  if (launch_dgemm(plain(N, N, N, C, N, 1, F, N, 1, T), s) != cudaSuccess) return DONOF_ERR_CUDA;
   // S = T^T T;  M = (3I - S) / 2;  C_new = T M
   if (sym_product(plain(N, N, N, T, 1, N, T, N, 1, S), s) != DONOF_OK) return DONOF_ERR_CUDA;
   k_newton_schulz<<<152 * 4, 256, 0, s>>>(S, N, S);
@@ -162,8 +122,7 @@ extern "C" int donof_orbital_update(int32_t nbf, const double* lam, const double
 // its diagonal, its off-diagonal zeta-scaled (Sec. III.B) and DIIS-extrapolated (Sec.
 // III.C); converged when max |lambda_qp - lambda_pq| < delta and the energy of an outer
 // iteration changed by less than eps_energy.  The host drives the loop and reads two
-// device scalars per build; every arithmetic step runs in this library's kernels (and
-// cuSOLVER's eigensolver).
+// device scalars per build; every arithmetic step runs in this library's kernels.
 //
 // Readings: F^j and its error vector e^j = offdiag F^j are taken to the fixed AO basis
 // (C F C^T, C e C^T) so that matrices of different iterations can be combined; with
@@ -185,12 +144,12 @@ struct Slots {
 };
 
 struct OptLayout {
-  size_t lam, Emo, T1, T2, Fbar, hist, eps, scal, B, c, info, work;
+  size_t lam, Emo, T1, T2, Fbar, hist, eps, scal, B, c, work;
   size_t skp;  // split-K partials of R_a C^T (nact x N)
   size_t total;
 };
 
-int opt_layout(int N, int A, int depth, int lwork, OptLayout* o) {
+int opt_layout(int N, int A, int depth, OptLayout* o) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t r = off;
@@ -209,8 +168,7 @@ int opt_layout(int N, int A, int depth, int lwork, OptLayout* o) {
   o->scal = take(8 * 8);                // [0] E, [1] asym bits, [2] E of the occupation step
   o->B = take((size_t)kMaxDepth * kMaxDepth * 8);
   o->c = take((size_t)(kMaxDepth + 2) * 8);  // c[0..n]; the restart flag kept at [kMaxDepth + 1]
-  o->info = take(16);
-  o->work = take((size_t)lwork * 8);
+  o->work = take(eigh_workspace_bytes(N));  // the eigensolver's workspace
   const int ks = splitk_count(A, N, N);
   o->skp = take(ks > 1 ? (size_t)ks * A * N * 8 : 0);
   o->total = off;
@@ -358,15 +316,15 @@ __global__ void k_diis_combine(const double* __restrict__ hist, const double* __
   }
 }
 
-// Eigenvectors (rows of the row-major view of the column-major syevd result) in decreasing
-// eigenvalue order as the columns of C; the eigenvalues in that order as the next diagonal.
+// Eigenvectors (columns of the row-major eigenvector matrix W) in decreasing eigenvalue order
+// as the columns of C; the eigenvalues in that order as the next diagonal.
 __global__ void k_take_descending(const double* __restrict__ W, const double* __restrict__ eps,
                                   int N, double* C, double* Fdiag) {
   const long long tot = (long long)N * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
        i += (long long)gridDim.x * blockDim.x) {
     const int mu = (int)(i / N), p = (int)(i % N);
-    C[i] = W[(size_t)(N - 1 - p) * N + mu];
+    C[i] = W[(size_t)mu * N + (N - 1 - p)];
     if (mu == 0) Fdiag[p] = eps[N - 1 - p];
   }
 }
@@ -394,9 +352,8 @@ struct Loop {
   size_t bbytes;
   char* ows;
   OptLayout L;
-  int N, lwork;
+  int N;
   cudaStream_t s;
-  cusolverDnHandle_t sol;
 };
 
 bool ok(cudaError_t e) { return e == cudaSuccess; }
@@ -511,15 +468,14 @@ int loop_orbital_step(Loop& lp, double zeta, int depth, std::vector<int>& active
   }
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
   // Fbar symmetric: its row-major storage is its column-major storage
-  if (cusolverDnDsyevd(lp.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, Fbar, N,
-                       (double*)(o + lp.L.eps), (double*)(o + lp.L.work), lp.lwork,
-                       (int*)(o + lp.L.info)) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
+  // Fbar = V diag(eps) V^T, V over Fbar's storage (row-major, column j = eigenvector j)
+  int rc = eigh_run(N, Fbar, Fbar, (double*)(o + lp.L.eps), o + lp.L.work, lp.s);
+  if (rc != DONOF_OK) return rc;
   k_take_descending<<<152 * 4, 256, 0, lp.s>>>(Fbar, (const double*)(o + lp.L.eps), N, lp.C,
                                                lp.Fdiag);
   count_launch(1);
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
-  int rc = loop_reorthonormalise(lp);
+  rc = loop_reorthonormalise(lp);
   if (rc != DONOF_OK) return rc;
   prof_end(DONOF_PHASE_ORBITAL_STEP, lp.s);
   // the restart decision is needed before the next step: read it now
@@ -540,12 +496,10 @@ int loop_initial_diagonal(Loop& lp) {
   double* T1 = (double*)(o + lp.L.T1);
   k_symmetrise<<<152 * 4, 256, 0, lp.s>>>((const double*)(o + lp.L.lam), N, S);
   count_launch(1);
-  if (cusolverDnDsyevd(lp.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, S, N,
-                       (double*)(o + lp.L.eps), (double*)(o + lp.L.work), lp.lwork,
-                       (int*)(o + lp.L.info)) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
-  // T1 = C V, V[i][j] = S[j * N + i] (ascending eigenvalues)
-  if (!ok(launch_dgemm(plain(N, N, N, lp.C, N, 1, S, 1, N, T1), lp.s)) ||
+  const int rc = eigh_run(N, S, S, (double*)(o + lp.L.eps), o + lp.L.work, lp.s);
+  if (rc != DONOF_OK) return rc;
+  // T1 = C V, V[i][j] = S[i * N + j] (ascending eigenvalues)
+  if (!ok(launch_dgemm(plain(N, N, N, lp.C, N, 1, S, N, 1, T1), lp.s)) ||
       !ok(cudaMemcpyAsync(lp.C, T1, (size_t)N * N * 8, cudaMemcpyDeviceToDevice, lp.s)))
     return DONOF_ERR_CUDA;
   k_negate<<<8, 256, 0, lp.s>>>((const double*)(o + lp.L.eps), N, lp.Fdiag);
@@ -562,15 +516,9 @@ extern "C" int donof_optimize_workspace_size(const donof_problem* prob, int32_t 
   size_t b = 0;
   int rc = donof_workspace_size(prob, &b);  // validates the problem
   if (rc != DONOF_OK) return rc;
-  cusolverDnHandle_t h = nullptr;
-  rc = solver(&h);
-  if (rc != DONOF_OK) return rc;
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, prob->nbf,
-                                  nullptr, prob->nbf, nullptr, &lwork) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
+  if (prob->nbf > kEighMaxN) return DONOF_ERR_UNSUPPORTED;
   OptLayout L;
-  opt_layout(prob->nbf, prob->npair * (1 + prob->ncwo) + prob->nsingle, diis_depth, lwork, &L);
+  opt_layout(prob->nbf, prob->npair * (1 + prob->ncwo) + prob->nsingle, diis_depth, &L);
   *bytes = L.total;
   return DONOF_OK;
 }
@@ -598,14 +546,7 @@ extern "C" int donof_optimize(const donof_problem* prob, const donof_opt_params*
   lp.ows = (char*)opt_ws;
   lp.N = prob->nbf;
   lp.s = (cudaStream_t)stream;
-  rc = solver(&lp.sol);
-  if (rc != DONOF_OK) return rc;
-  if (cusolverDnSetStream(lp.sol, lp.s) != CUSOLVER_STATUS_SUCCESS) return DONOF_ERR_CUDA;
-  if (cusolverDnDsyevd_bufferSize(lp.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, lp.N,
-                                  nullptr, lp.N, nullptr, &lp.lwork) != CUSOLVER_STATUS_SUCCESS)
-    return DONOF_ERR_CUDA;
-  opt_layout(lp.N, prob->npair * (1 + prob->ncwo) + prob->nsingle, prm->diis_depth, lp.lwork,
-             &lp.L);
+  opt_layout(lp.N, prob->npair * (1 + prob->ncwo) + prob->nsingle, prm->diis_depth, &lp.L);
 
   int nE = 0;
   auto record = [&](double E) {
