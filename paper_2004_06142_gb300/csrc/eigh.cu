@@ -30,9 +30,13 @@ namespace {
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kNb = 64;           // reflectors per WY block
-constexpr int kSlotThreads = 8;   // threads per CTA of the one-thread-per-eigenvalue kernels
 constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
 constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
+// tridiagonal reduction: vector elements per thread held in registers, and the largest n whose
+// trailing rows (one per warp) stay in registers, kTriRowRegs elements per lane
+constexpr int kTriVec = 5;
+constexpr int kTriRegMaxN = 1216;
+constexpr int kTriRowRegs = (kTriRegMaxN - 2 + 31) / 32;
 constexpr double kClusterTol = 1e-5;
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
 
@@ -43,13 +47,14 @@ struct EighHdr {
   int nonfinite;      // A holds a NaN or an infinity
   unsigned long long amax_bits;  // max |A_ij| (bit pattern of a non-negative double)
   double scale;       // the power of two applied to A
-  double tnorm;       // ||T||_inf of the scaled tridiagonal matrix
-  double pivmin;      // smallest pivot magnitude of the twisted factorisations
+  double tscale;      // the power of two applied to T: ||T||_inf * tscale in [1/2, 1)
+  double tnorm;       // ||T||_inf after that scaling
+  double pivmin;      // pivot floor of the twisted factorisations (scaled units)
 };
 
 struct EighLayout {
-  size_t hdr, A, Yr, Wd, d, e, es, e2, tau, pbuf, lam, glo, ghi, col, bstart, bend, incl, cl, T,
-      G, W1, W2, part, fix, total;
+  size_t hdr, A, Yr, Wd, Wp, d, e, ds, es, e2, df, e2f, tau, pbuf, lam, glo, ghi, col, bstart,
+      bend, incl, cl, T, G, W1, W2, part, fix, total;
   int nref, nblk;
 };
 
@@ -68,10 +73,14 @@ EighLayout eigh_layout(int N) {
   L.A = take(nn * 8);
   L.Yr = take(nn * 8);
   L.Wd = take(nn * 8);
+  L.Wp = take(nn * 8);
   L.d = take(n * 8);
   L.e = take(n * 8);
+  L.ds = take(n * 8);
   L.es = take(n * 8);
   L.e2 = take(n * 8);
+  L.df = take(n * 4);
+  L.e2f = take(n * 4);
   L.tau = take(n * 8);
   L.pbuf = take(2 * n * 8);
   L.lam = take(n * 8);
@@ -110,17 +119,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Sum over the CTA in a fixed order (lane 0 of each warp, then the warps in order): every
-// thread gets the same value.
+// Sum over the CTA in a fixed order (a fixed shuffle tree in each warp, then warp 0 adds the
+// warps' sums by a fixed tree): every thread gets the same value.  red holds kTriWarps + 1.
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   v = warp_sum_d(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kTriWarps ? red[threadIdx.x] : 0.0;
 #pragma unroll
-  for (int i = 0; i < kTriWarps; ++i) t += red[i];
+    for (int o = kTriWarps / 2; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[kTriWarps] = t;
+  }
   __syncthreads();
-  return t;
+  return red[kTriWarps];
 }
 
 // Grid barrier of the cooperative launch: arrivals counted in hdr->ctr (zeroed before the
@@ -146,26 +158,6 @@ __device__ __forceinline__ bool grid_barrier(EighHdr* h, unsigned target, int* s
   }
   __syncthreads();
   return *s_flag != 0;
-}
-
-// Reflector H = I - tau u u^T with u[k0] = 1 and H x[k0..N) = beta e_k0; xn2 is the sum of
-// x[j]^2 over j > k0 (the same value in every thread).  x[k0+1..N) becomes u's tail, x[k0] 1.
-__device__ __forceinline__ void householder(double* x, int k0, int N, double xn2, double& tau,
-                                            double& beta) {
-  const double al = x[k0];
-  __syncthreads();  // every thread has read x[k0]
-  if (xn2 == 0.0) {
-    tau = 0.0;
-    beta = al;
-    for (int j = k0 + 1 + threadIdx.x; j < N; j += blockDim.x) x[j] = 0.0;
-  } else {
-    beta = -copysign(sqrt(al * al + xn2), al);
-    tau = (beta - al) / beta;
-    const double s = 1.0 / (al - beta);
-    for (int j = k0 + 1 + threadIdx.x; j < N; j += blockDim.x) x[j] *= s;
-  }
-  if (threadIdx.x == 0) x[k0] = 1.0;
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -227,13 +219,14 @@ struct TriArgs {
 
 __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
   extern __shared__ double sm[];
-  __shared__ double red[kTriWarps];
+  __shared__ double red[kTriWarps + 1];
+  __shared__ double sh[3];
   __shared__ int s_flag;
   const int N = a.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int G = gridDim.x;
   double* v = sm;           // reflector of the current step (indices k+1 .. N-1)
   double* x = sm + N;       // next column, then its reflector
-  double* w = sm + 2 * N;   // p, then w = p - (tau/2)(p.v) v
+  double* w = sm + 2 * N;   // w = p - (tau/2)(p.v) v
   double* A = a.A;
   const bool writer = blockIdx.x == 0;
   if (N <= 2) {
@@ -247,20 +240,45 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     return;
   }
   // rows are dealt to CTAs cyclically (row i to CTA i mod G), then to the CTA's warps, so the
-  // shrinking trailing matrix stays spread over every SM
+  // shrinking trailing matrix stays spread over every SM; with N <= G * kTriWarps each warp
+  // owns one row at most and keeps it in registers while it is updated
   auto row_of = [&](int t) { return blockIdx.x + G * (wid + kTriWarps * t); };
+  const bool reg_rows = N <= kTriRegMaxN && N <= G * kTriWarps;
+  const int myrow = row_of(0);
   unsigned bar = 0;
+
+  // reflector of x[k0..N) (xn2 = sum over j > k0 of x_j^2; the scalars from thread 0)
+  auto householder = [&](int k0, double xn2, double& tau, double& beta) {
+    if (tid == 0) {
+      const double al = x[k0];
+      double t = 0.0, b = al, sc = 0.0;
+      if (xn2 != 0.0) {
+        b = -copysign(sqrt(fma(al, al, xn2)), al);
+        t = (b - al) / b;
+        sc = 1.0 / (al - b);
+      }
+      sh[0] = t;
+      sh[1] = b;
+      sh[2] = sc;
+    }
+    __syncthreads();
+    tau = sh[0];
+    beta = sh[1];
+    const double sc = sh[2];  // 0 when the column is already reduced (u = e_k0)
+    for (int j = k0 + 1 + tid; j < N; j += kTriThreads) x[j] *= sc;
+    if (tid == 0) x[k0] = 1.0;
+    __syncthreads();
+  };
 
   // reflector 0 from row 0 (column 0)
   double xn = 0.0;
   for (int j = tid; j < N; j += kTriThreads) {
     const double xj = __ldcg(A + j);
     x[j] = xj;
-    if (j >= 2) xn += xj * xj;
+    if (j >= 2) xn = fma(xj, xj, xn);
   }
-  double xn2 = block_sum_d(xn, red);
   double tau_c, beta;
-  householder(x, 1, N, xn2, tau_c, beta);
+  householder(1, block_sum_d(xn, red), tau_c, beta);
   if (writer) {
     if (tid == 0) {
       a.d[0] = x[0];
@@ -276,7 +294,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     const double* Ar = A + (size_t)i * N;
     double acc = 0.0;
 #pragma unroll 4
-    for (int j = 1 + lane; j < N; j += 32) acc += __ldcg(Ar + j) * x[j];
+    for (int j = 1 + lane; j < N; j += 32) acc = fma(__ldcg(Ar + j), x[j], acc);
     acc = warp_sum_d(acc);
     if (lane == 0) a.pbuf[i] = tau_c * acc;
   }
@@ -288,27 +306,80 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
   }
 
   for (int k = 0; k <= N - 3; ++k) {
-    // w = p_k - (tau_k / 2)(p_k . v_k) v_k
     const double* pk = a.pbuf + (size_t)(k & 1) * N;
-    double acc = 0.0;
-    for (int j = k + 1 + tid; j < N; j += kTriThreads) {
-      const double pj = __ldcg(pk + j);
-      w[j] = pj;
-      acc += pj * v[j];
+    const double* Ak1 = A + (size_t)(k + 1) * N;
+    // every load of the step at once: p_k, row k+1, and (register path) the warp's own row
+    double pr[kTriVec], ar[kTriVec];
+#pragma unroll
+    for (int r = 0; r < kTriVec; ++r) {
+      const int j = k + 1 + tid + kTriThreads * r;
+      pr[r] = 0.0;
+      ar[r] = 0.0;
+      if (j < N) {
+        pr[r] = __ldcg(pk + j);
+        ar[r] = __ldcg(Ak1 + j);
+      }
     }
+    double rr[kTriRowRegs];
+    const bool has_row = reg_rows && myrow < N && myrow >= k + 2;
+    double* Amy = A + (size_t)myrow * N;
+    if (has_row) {
+#pragma unroll
+      for (int q = 0; q < kTriRowRegs; ++q) {
+        const int j = k + 2 + lane + 32 * q;
+        rr[q] = j < N ? __ldcg(Amy + j) : 0.0;
+      }
+    }
+    // the loads beyond kTriVec per thread (large N only)
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < kTriVec; ++r) {
+      const int j = k + 1 + tid + kTriThreads * r;
+      if (j < N) acc = fma(pr[r], v[j], acc);
+    }
+    for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads)
+      acc = fma(__ldcg(pk + j), v[j], acc);
+    // w = p_k - (tau_k / 2)(p_k . v_k) v_k
     const double aw = 0.5 * tau_c * block_sum_d(acc, red);
-    for (int j = k + 1 + tid; j < N; j += kTriThreads) w[j] -= aw * v[j];
+#pragma unroll
+    for (int r = 0; r < kTriVec; ++r) {
+      const int j = k + 1 + tid + kTriThreads * r;
+      if (j < N) w[j] = fma(-aw, v[j], pr[r]);
+    }
+    for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads)
+      w[j] = fma(-aw, v[j], __ldcg(pk + j));
     __syncthreads();
     // row k+1 of the updated matrix (v[k+1] = 1): its column k+1 below the diagonal
     const double wk1 = w[k + 1];
-    const double* Ak1 = A + (size_t)(k + 1) * N;
     xn = 0.0;
-    for (int j = k + 1 + tid; j < N; j += kTriThreads) {
-      const double xj = __ldcg(Ak1 + j) - w[j] - wk1 * v[j];
-      x[j] = xj;
-      if (j >= k + 3) xn += xj * xj;
+#pragma unroll
+    for (int r = 0; r < kTriVec; ++r) {
+      const int j = k + 1 + tid + kTriThreads * r;
+      if (j < N) {
+        const double xj = fma(-wk1, v[j], ar[r] - w[j]);
+        x[j] = xj;
+        if (j >= k + 3) xn = fma(xj, xj, xn);
+      }
     }
-    xn2 = block_sum_d(xn, red);
+    for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads) {
+      const double xj = fma(-wk1, v[j], __ldcg(Ak1 + j) - w[j]);
+      x[j] = xj;
+      if (j >= k + 3) xn = fma(xj, xj, xn);
+    }
+    // register path: the own row's rank-2 update, while the norm is reduced (not at the last
+    // step, whose 2 x 2 block is formed from the rows as they stand)
+    if (has_row && k + 1 < N - 2) {
+      const double vi = v[myrow], wi = w[myrow];
+#pragma unroll
+      for (int q = 0; q < kTriRowRegs; ++q) {
+        const int j = k + 2 + lane + 32 * q;
+        if (j < N) {
+          rr[q] = fma(-wi, v[j], fma(-vi, w[j], rr[q]));
+          Amy[j] = rr[q];
+        }
+      }
+    }
+    const double xn2 = block_sum_d(xn, red);
     if (k + 1 == N - 2) {  // the last 2 x 2 block
       if (writer && tid == 0) {
         a.d[N - 2] = x[N - 2];
@@ -318,7 +389,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       break;
     }
     double tau_n;
-    householder(x, k + 2, N, xn2, tau_n, beta);
+    householder(k + 2, xn2, tau_n, beta);
     if (writer) {
       if (tid == 0) {
         a.d[k + 1] = x[k + 1];
@@ -328,39 +399,52 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       double* Yk = a.Yr + (size_t)(k + 1) * N;
       for (int j = k + 2 + tid; j < N; j += kTriThreads) Yk[j] = x[j];
     }
-    // own rows i >= k+2: A_ij -= v_i w_j + w_i v_j (j >= k+2), and p_{k+1} = tau A u
+    // p_{k+1} = tau A u over the own rows i >= k+2
     double* pn = a.pbuf + (size_t)((k + 1) & 1) * N;
-    for (int t = 0;; ++t) {
-      const int i = row_of(t);
-      if (i >= N) break;
-      if (i < k + 2) continue;
-      double* Ar = A + (size_t)i * N;
-      const double vi = v[i], wi = w[i];
-      double acc2 = 0.0;
-      int j = k + 2 + lane;
-      for (; j + 96 < N; j += 128) {
-        const double a0 = __ldcg(Ar + j), a1 = __ldcg(Ar + j + 32), a2 = __ldcg(Ar + j + 64),
-                     a3 = __ldcg(Ar + j + 96);
-        const double b0 = a0 - vi * w[j] - wi * v[j];
-        const double b1 = a1 - vi * w[j + 32] - wi * v[j + 32];
-        const double b2 = a2 - vi * w[j + 64] - wi * v[j + 64];
-        const double b3 = a3 - vi * w[j + 96] - wi * v[j + 96];
-        Ar[j] = b0;
-        Ar[j + 32] = b1;
-        Ar[j + 64] = b2;
-        Ar[j + 96] = b3;
-        acc2 += b0 * x[j];
-        acc2 += b1 * x[j + 32];
-        acc2 += b2 * x[j + 64];
-        acc2 += b3 * x[j + 96];
+    if (reg_rows) {
+      if (has_row) {
+        double acc2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < kTriRowRegs; ++q) {
+          const int j = k + 2 + lane + 32 * q;
+          if (j < N) acc2 = fma(rr[q], x[j], acc2);
+        }
+        acc2 = warp_sum_d(acc2);
+        if (lane == 0) pn[myrow] = tau_n * acc2;
       }
-      for (; j < N; j += 32) {
-        const double b0 = __ldcg(Ar + j) - vi * w[j] - wi * v[j];
-        Ar[j] = b0;
-        acc2 += b0 * x[j];
+    } else {
+      for (int t = 0;; ++t) {
+        const int i = row_of(t);
+        if (i >= N) break;
+        if (i < k + 2) continue;
+        double* Ar = A + (size_t)i * N;
+        const double vi = v[i], wi = w[i];
+        double acc2 = 0.0;
+        int j = k + 2 + lane;
+        for (; j + 96 < N; j += 128) {
+          const double a0 = __ldcg(Ar + j), a1 = __ldcg(Ar + j + 32), a2 = __ldcg(Ar + j + 64),
+                       a3 = __ldcg(Ar + j + 96);
+          const double b0 = fma(-wi, v[j], fma(-vi, w[j], a0));
+          const double b1 = fma(-wi, v[j + 32], fma(-vi, w[j + 32], a1));
+          const double b2 = fma(-wi, v[j + 64], fma(-vi, w[j + 64], a2));
+          const double b3 = fma(-wi, v[j + 96], fma(-vi, w[j + 96], a3));
+          Ar[j] = b0;
+          Ar[j + 32] = b1;
+          Ar[j + 64] = b2;
+          Ar[j + 96] = b3;
+          acc2 = fma(b0, x[j], acc2);
+          acc2 = fma(b1, x[j + 32], acc2);
+          acc2 = fma(b2, x[j + 64], acc2);
+          acc2 = fma(b3, x[j + 96], acc2);
+        }
+        for (; j < N; j += 32) {
+          const double b0 = fma(-wi, v[j], fma(-vi, w[j], __ldcg(Ar + j)));
+          Ar[j] = b0;
+          acc2 = fma(b0, x[j], acc2);
+        }
+        acc2 = warp_sum_d(acc2);
+        if (lane == 0) pn[i] = tau_n * acc2;
       }
-      acc2 = warp_sum_d(acc2);
-      if (lane == 0) pn[i] = tau_n * acc2;
     }
     if (!grid_barrier(a.hdr, (++bar) * G, &s_flag)) return;
     double* t = v;
@@ -371,22 +455,32 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// 2. splitting, Gershgorin bounds, bisection
+// 2. splitting, Gershgorin bounds, bisection.  From here on T is scaled by the power of two
+//    ts = 2^-ceil(log2 ||T||_inf), so that ||T||_inf <= 1 (exact), and every kernel reads the
+//    scaled arrays.
 // ---------------------------------------------------------------------------
-// One CTA: ||T||_inf, the split off-diagonal es (and es^2), the blocks (bstart/bend of every
-// row), each block's Gershgorin interval (at its first row) and the pivot floor.
-__global__ void k_tri_prep(int N, const double* __restrict__ d, const double* __restrict__ e,
-                           EighHdr* h, double* es, double* e2, int* bstart, int* bend,
-                           double* glo, double* ghi) {
-  extern __shared__ double sp[];
-  double* sd = sp;       // d
-  double* se = sp + N;   // es
+__device__ __forceinline__ bool dbl_is_zero(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
+}
+__device__ __forceinline__ int dbl_biased_exp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+__device__ __forceinline__ int dbl_sign(double x) { return (int)((unsigned)__double2hiint(x) >> 31); }
+
+// One CTA.  ||T||_inf and the scale ts; the split off-diagonal (es, es^2) and the diagonal
+// scaled by ts (double and float copies); the blocks (bstart/bend of every row, found by one
+// thread from integer flags); each block's Gershgorin interval (at its first row, one warp
+// per block); the twisted factorisations' pivot floor.
+__global__ void __launch_bounds__(256) k_tri_prep(int N, const double* __restrict__ d,
+                                                  const double* __restrict__ e, EighHdr* h,
+                                                  double* ds, double* es, double* e2, float* df,
+                                                  float* e2f, int* bstart, int* bend,
+                                                  double* glo, double* ghi) {
+  extern __shared__ int sflag[];  // [N]: row i ends a block; then the list of block starts
+  int* blist = sflag + N;
   __shared__ double red[8];
+  __shared__ int s_nb;
   double tn = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double di = d[i];
-    sd[i] = di;
-    const double r = fabs(di) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < N - 1 ? fabs(e[i]) : 0.0);
+    const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < N - 1 ? fabs(e[i]) : 0.0);
     tn = fmax(tn, r);
   }
   for (int o = 16; o; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
@@ -394,132 +488,249 @@ __global__ void k_tri_prep(int N, const double* __restrict__ d, const double* __
   __syncthreads();
   tn = 0.0;
   for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tn = fmax(tn, red[i]);
-  if (!(tn > 0.0)) tn = 1.0;  // T = 0 (or NaN: the eigenvalues come out NaN)
+  if (!(tn > 0.0) || !isfinite(tn)) tn = 1.0;  // T = 0 (or not finite: NaN eigenvalues follow)
+  int ex = 0;
+  frexp(tn, &ex);  // tn = f 2^ex, f in [1/2, 1)
+  const double ts = ldexp(1.0, -ex);
   const double thresh = 16.0 * N * DBL_EPSILON * tn;
-  double emax = 0.0;
-  for (int i = threadIdx.x; i < N - 1; i += blockDim.x) {
-    const double ei = e[i];
-    const double v = fabs(ei) <= thresh ? 0.0 : ei;
-    se[i] = v;
-    es[i] = v;
-    e2[i] = v * v;
-    emax = fmax(emax, v * v);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double di = d[i] * ts;
+    ds[i] = di;
+    df[i] = (float)di;
+    int end = i == N - 1 ? 1 : 0;
+    if (i < N - 1) {
+      const double ei = fabs(e[i]) <= thresh ? 0.0 : e[i] * ts;
+      es[i] = ei;
+      e2[i] = ei * ei;
+      e2f[i] = (float)(ei * ei);
+      end = dbl_is_zero(ei) ? 1 : end;
+    }
+    sflag[i] = end;
   }
-  for (int o = 16; o; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  emax = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) emax = fmax(emax, red[i]);
-  h->tnorm = tn;
-  h->pivmin = DBL_MIN * fmax(1.0, emax);
-  int s0 = 0;
-  double lo = 0.0, hi = 0.0;
-  for (int i = 0; i < N; ++i) {
-    const double el = i > s0 ? fabs(se[i - 1]) : 0.0;
-    const double er = i < N - 1 ? fabs(se[i]) : 0.0;
-    const double l = sd[i] - el - er, u = sd[i] + el + er;
-    lo = i == s0 ? l : fmin(lo, l);
-    hi = i == s0 ? u : fmax(hi, u);
-    if (i == N - 1 || se[i] == 0.0) {
-      for (int r = s0; r <= i; ++r) {
-        bstart[r] = s0;
-        bend[r] = i + 1;
+  if (threadIdx.x == 0) {
+    h->tnorm = tn * ts;
+    h->tscale = ts;
+    h->pivmin = 0x1p-100;
+    int s0 = 0, nb = 0;
+    for (int i = 0; i < N; ++i) {
+      if (sflag[i]) {
+        for (int r = s0; r <= i; ++r) {
+          bstart[r] = s0;
+          bend[r] = i + 1;
+        }
+        blist[nb++] = s0;
+        s0 = i + 1;
       }
+    }
+    s_nb = nb;
+  }
+  __syncthreads();
+  const int nb = s_nb, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int b = threadIdx.x >> 5; b < nb; b += nw) {
+    const int s0 = blist[b], s1 = b + 1 < nb ? blist[b + 1] : N;
+    if (s1 - s0 < 2) continue;  // a 1 x 1 block needs no bisection
+    double lo = 0.0, hi = 0.0;
+    bool any = false;
+    for (int i = s0 + lane; i < s1; i += 32) {
+      const double el = i > s0 ? fabs(es[i - 1]) : 0.0;
+      const double er = i < s1 - 1 ? fabs(es[i]) : 0.0;
+      const double l = ds[i] - el - er, u = ds[i] + el + er;
+      lo = any ? fmin(lo, l) : l;
+      hi = any ? fmax(hi, u) : u;
+      any = true;
+    }
+    if (!any) {  // lanes beyond the block: neutral values
+      lo = ds[s0];
+      hi = ds[s0];
+    }
+    for (int o = 16; o; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
       glo[s0] = lo;
       ghi[s0] = hi;
-      s0 = i + 1;
     }
   }
 }
 
-// Number of eigenvalues of the block [s0, s1) below sig: sign changes of the leading minors
-// p_i = (d_i - sig) p_{i-1} - e_{i-1}^2 p_{i-2} (a zero minor counts as a tiny negative ratio),
-// the pair (p_{i-1}, p_i) rescaled by 2^-+600 whenever its larger magnitude leaves
-// [2^-600, 2^600].
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
-                                           const double* __restrict__ e2, int s0, int s1,
-                                           double sig) {
-  double p0 = 1.0, p1 = d[s0] - sig;
-  if (p1 == 0.0) p1 = -0x1p-60;
-  int cnt = signbit(p1) ? 1 : 0;
-#pragma unroll 4
+// Number of eigenvalues of the (scaled) block [s0, s1) below sig in float: the ratio form
+// q_i = (d_i - sig) - e_{i-1}^2 / q_{i-1}, |q_i| floored at piv (a zero pivot counts negative).
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ d,
+                                               const float* __restrict__ e2, int s0, int s1,
+                                               float sig) {
+  constexpr float piv = 1e-30f;
+  float q = d[s0] - sig;
+  if (fabsf(q) < piv) q = -piv;
+  int cnt = q < 0.0f ? 1 : 0;
   for (int i = s0 + 1; i < s1; ++i) {
-    double p2 = fma(d[i] - sig, p1, -(e2[i - 1] * p0));
-    if (p2 == 0.0) p2 = -p1 * 0x1p-60;
-    cnt += (signbit(p2) != signbit(p1)) ? 1 : 0;
-    const int ex = max((__double2hiint(p1) >> 20) & 0x7ff, (__double2hiint(p2) >> 20) & 0x7ff);
-    if (ex > 1023 + 600) {
-      p1 *= 0x1p-600;
-      p2 *= 0x1p-600;
-    } else if (ex < 1023 - 600) {
-      p1 *= 0x1p600;
-      p2 *= 0x1p600;
-    }
-    p0 = p1;
-    p1 = p2;
+    q = (d[i] - sig) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < piv) q = -piv;
+    cnt += q < 0.0f ? 1 : 0;
   }
   return cnt;
 }
 
-// eigenvalue k = s - bstart[s] of the block holding row s (ascending within the block)
-__global__ void k_bisect(int N, const double* __restrict__ d, const double* __restrict__ e2,
-                         const int* __restrict__ bstart, const int* __restrict__ bend,
-                         const double* __restrict__ glo, const double* __restrict__ ghi,
-                         const EighHdr* h, double* lam) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
+// The same count in double: sign changes of the leading minors
+// p_i = (d_i - sig) p_{i-1} - e_{i-1}^2 p_{i-2} (a zero minor counts as a tiny negative ratio),
+// the pair (p_{i-1}, p_i) rescaled by 2^-+300 after every eighth row when its larger magnitude
+// has left [2^-300, 2^300] (with ||T||_inf <= 1 and the split threshold, eight rows move it by
+// at most 2^13 up or 2^-616 down).
+__device__ __forceinline__ int sturm_count_f64(const double* __restrict__ d,
+                                               const double* __restrict__ e2, int s0, int s1,
+                                               double sig) {
+  double p0 = 1.0, p1 = d[s0] - sig;
+  if (dbl_is_zero(p1)) p1 = -0x1p-60;
+  int cnt = dbl_sign(p1);
+  int i = s0 + 1;
+  while (i < s1) {
+    const int iend = min(i + 8, s1);
+#pragma unroll 4
+    for (; i < iend; ++i) {
+      double p2 = fma(d[i] - sig, p1, -(e2[i - 1] * p0));
+      if (dbl_is_zero(p2)) p2 = -p1 * 0x1p-60;
+      cnt += dbl_sign(p2) ^ dbl_sign(p1);
+      p0 = p1;
+      p1 = p2;
+    }
+    const int ex = max(dbl_biased_exp(p0), dbl_biased_exp(p1));
+    if (ex > 1023 + 300) {
+      p0 *= 0x1p-300;
+      p1 *= 0x1p-300;
+    } else if (ex < 1023 - 300) {
+      p0 *= 0x1p300;
+      p1 *= 0x1p300;
+    }
+  }
+  return cnt;
+}
+
+// Eigenvalue k = s - bstart[s] of the block holding row s, by multisection: a half-warp per
+// eigenvalue, its 16 lanes counting at 16 points of the bracket per round.  Five float rounds
+// (brackets of ~2^-20 ||T||), the bracket widened by 4e-6 ||T|| (the float counts are exact
+// for a matrix within a few float roundings of T) and its ends checked by double counts (the
+// Gershgorin interval again if either fails), then double rounds to the width eps ||T||.
+constexpr int kBisThreads = 128;
+__global__ void __launch_bounds__(kBisThreads) k_bisect(int N, const double* __restrict__ ds,
+                                                        const double* __restrict__ e2,
+                                                        const float* __restrict__ df,
+                                                        const float* __restrict__ e2f,
+                                                        const int* __restrict__ bstart,
+                                                        const int* __restrict__ bend,
+                                                        const double* __restrict__ glo,
+                                                        const double* __restrict__ ghi,
+                                                        const EighHdr* h, double* lam) {
+  extern __shared__ double sb[];
+  double* sd = sb;
+  double* se2 = sb + N;
+  float* sdf = (float*)(sb + 2 * N);
+  float* se2f = sdf + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sd[i] = ds[i];
+    sdf[i] = df[i];
+    se2[i] = i < N - 1 ? e2[i] : 0.0;
+    se2f[i] = i < N - 1 ? e2f[i] : 0.0f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, j = lane & 15;
+  const unsigned hm = 0xffffu << (lane & 16);
+  const int s = (blockIdx.x * kBisThreads + threadIdx.x) >> 4;
+  if (s >= N) return;  // uniform over the half-warp
   if (h->abort) {
-    lam[s] = __longlong_as_double(0x7ff8000000000000ll);
+    if (j == 0) lam[s] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
   const int s0 = bstart[s], s1 = bend[s], k = s - s0;
   if (s1 - s0 == 1) {
-    lam[s] = d[s0];
+    if (j == 0) lam[s] = sd[s0];
     return;
   }
   const double tn = h->tnorm;
-  const double pad = 2.0 * N * DBL_EPSILON * tn + 4.0 * h->pivmin;
-  double lo = glo[s0] - pad, hi = ghi[s0] + pad;
-  for (int it = 0; it < 96; ++it) {
-    if (!(hi - lo > fmax(DBL_EPSILON * tn, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))))) break;
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_count(d, e2, s0, s1, mid) > k) hi = mid;
-    else lo = mid;
+  const double pad = 2.0 * N * DBL_EPSILON * tn;
+  const double glo_s = glo[s0] - pad, ghi_s = ghi[s0] + pad;
+  double lo = glo_s, hi = ghi_s;
+  // narrow [lo, hi] to the points of the lanes: jh the first lane whose count exceeds k, jl
+  // the last lane before it whose count does not
+  auto narrow = [&](bool above, double base, double step, int off) {
+    const unsigned ab = (__ballot_sync(hm, above) >> (lane & 16)) & 0xffffu;
+    const unsigned be = (__ballot_sync(hm, !above) >> (lane & 16)) & 0xffffu;
+    const int jh = ab ? __ffs(ab) - 1 : 16;
+    const unsigned bl = be & ((1u << jh) - 1u);
+    const int jl = bl ? 31 - __clz(bl) : -1;
+    const double nhi = jh < 16 ? base + (jh + off) * step : hi;
+    const double nlo = jl >= 0 ? base + (jl + off) * step : lo;
+    hi = nhi;
+    lo = nlo;
+  };
+  for (int r = 0; r < 5; ++r) {
+    const double step = (hi - lo) * (1.0 / 17.0);
+    const double sg = lo + (j + 1) * step;
+    narrow(sturm_count_f32(sdf, se2f, s0, s1, (float)sg) > k, lo, step, 1);
   }
-  lam[s] = 0.5 * (lo + hi);
+  lo -= 4e-6 * tn;
+  hi += 4e-6 * tn;
+  {  // 16 points from lo to hi inclusive: the ends verify the float bracket
+    const double step = (hi - lo) * (1.0 / 15.0);
+    const double sg = lo + j * step;
+    const int c = sturm_count_f64(sd, se2, s0, s1, sg);
+    const int clo = __shfl_sync(hm, c, lane & 16), chi = __shfl_sync(hm, c, (lane & 16) + 15);
+    if (clo <= k && chi > k) {
+      narrow(c > k, lo, step, 0);
+    } else {
+      lo = glo_s;
+      hi = ghi_s;
+    }
+  }
+  for (int r = 0; r < 40; ++r) {
+    if (!(hi - lo > fmax(DBL_EPSILON * tn, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))))) break;
+    const double step = (hi - lo) * (1.0 / 17.0);
+    const double sg = lo + (j + 1) * step;
+    narrow(sturm_count_f64(sd, se2, s0, s1, sg) > k, lo, step, 1);
+  }
+  if (j == 0) lam[s] = 0.5 * (lo + hi);
 }
 
-// Rank of every eigenvalue (ties by slot), eigenvalues of A in ascending order; CTA 0 also
-// lists the clusters: runs of a block's consecutive eigenvalues closer than kClusterTol ||T||.
-__global__ void k_rank_plan(int N, const double* __restrict__ lam, const int* __restrict__ bend,
-                            EighHdr* h, int* col, double* w_out, int* incl, int* cl) {
-  extern __shared__ double sl[];
-  int* sb = (int*)(sl + N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sl[i] = lam[i];
-    sb[i] = bend[i];
-  }
+// Order-preserving integer key of a double (NaN above everything).
+__device__ __forceinline__ long long dbl_key(double x) {
+  const long long u = __double_as_longlong(x);
+  return u >= 0 ? u : (u ^ 0x7fffffffffffffffll);
+}
+
+// Rank of every eigenvalue (integer keys, ties by slot), eigenvalues of A in ascending order;
+// CTA 0 also lists the clusters: runs of a block's consecutive eigenvalues closer than
+// kClusterTol ||T|| (the gaps tested in parallel, the runs found by one thread).
+__global__ void __launch_bounds__(256) k_rank_plan(int N, const double* __restrict__ lam,
+                                                   const int* __restrict__ bend, EighHdr* h,
+                                                   int* col, double* w_out, int* incl, int* cl) {
+  extern __shared__ long long skey[];
+  int* sgap = (int*)(skey + N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) skey[i] = dbl_key(lam[i]);
   __syncthreads();
+  const double unscale = 1.0 / (h->tscale * h->scale);  // a power of two
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < N) {
-    const double ls = sl[s];
+    const long long ks = skey[s];
     int r = 0;
     for (int t = 0; t < N; ++t) {
-      const double lt = sl[t];
-      r += (lt < ls || (lt == ls && t < s)) ? 1 : 0;
+      const long long kt = skey[t];
+      r += (kt < ks || (kt == ks && t < s)) ? 1 : 0;
     }
-    if (r > N - 1 || ls != ls) r = s;  // NaN (a failed reduction): its own slot
+    const double ls = lam[s];
+    if (ls != ls) r = s;  // NaN (a failed reduction): its own slot
     col[s] = r;
-    w_out[r] = ls / h->scale;
+    w_out[r] = ls * unscale;
   }
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   const double tol = kClusterTol * h->tnorm;
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    sgap[i] = (i + 1 < bend[i] && lam[i + 1] - lam[i] < tol) ? 1 : 0;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   int ncl = 0;
   for (int s0 = 0; s0 < N;) {
     int t = s0;
-    while (t + 1 < sb[s0] && sl[t + 1] - sl[t] < tol) ++t;
+    while (sgap[t]) ++t;  // sgap[bend - 1] = 0 ends every run inside its block
     for (int u = s0; u <= t; ++u) incl[u] = t > s0 ? 1 : 0;
     if (t > s0) {
       cl[2 * ncl] = s0;
@@ -534,75 +745,132 @@ __global__ void k_rank_plan(int N, const double* __restrict__ lam, const int* __
 // ---------------------------------------------------------------------------
 // 3. eigenvectors of T
 // ---------------------------------------------------------------------------
-// Twisted factorisation of T_b - lambda I for an eigenvalue outside the clusters: forward
-// pivots D+ (kept in Z's column), backward pivots D- (in Wd), gamma_i = D+_i + D-_i - (d_i -
-// lambda), then z_r = 1 and z_i = -e_i z_{i+1} / D+_i above r, z_i = -e_{i-1} z_{i-1} / D-_i
-// below.  Z[i][col] (row-major, column = rank of the eigenvalue), zero outside the block.
-__device__ __forceinline__ double pivot_floor(double v, double pivmin) {
-  return fabs(v) < pivmin ? -pivmin : v;
+// 1/x to double precision by Newton's iteration r <- r (2 - x r) from a float seed (the error
+// squares each step: 2^-23, 2^-46, then rounding); 2^-126 < |x| < 2^126.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double t = fma(-x, r, 1.0);
+  r = fma(r, t, r);
+  t = fma(-x, r, 1.0);
+  return fma(r, t, r);
+}
+// a pivot of magnitude below 2^-100 (||T|| <= 1) becomes -2^-100
+__device__ __forceinline__ double pivot_floor(double v) {
+  return dbl_biased_exp(v) < 1023 - 100 ? -0x1p-100 : v;
 }
 
-__global__ void k_twisted(int N, const double* __restrict__ d, const double* __restrict__ es,
-                          const double* __restrict__ e2, const int* __restrict__ bstart,
-                          const int* __restrict__ bend, const double* __restrict__ lam,
-                          const int* __restrict__ col, const int* __restrict__ incl,
-                          const EighHdr* h, double* Z, double* Wd) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
+// Twisted factorisation of T_b - lambda I for an eigenvalue outside the clusters, two threads
+// per eigenvalue.  Thread 0 of the pair runs the forward pivots D+_i (stored in Z's column,
+// their reciprocals in Wp), thread 1 the backward pivots D-_i (reciprocals in Wd); then
+// gamma_i = D+_i - e_i^2 / D-_{i+1} (each thread half the rows), the twist r where |gamma_r|
+// is smallest (first such row), z_r = 1, and thread 0 forms z_i = -e_i z_{i+1} / D+_i above r
+// while thread 1 forms z_i = -e_{i-1} z_{i-1} / D-_i below it; normalised to unit length.
+// Z[i][col] (row-major, column = rank of the eigenvalue), zero outside the block.
+__global__ void __launch_bounds__(32) k_twisted(int N, const double* __restrict__ ds,
+                                                const double* __restrict__ es,
+                                                const double* __restrict__ e2,
+                                                const int* __restrict__ bstart,
+                                                const int* __restrict__ bend,
+                                                const double* __restrict__ lam,
+                                                const int* __restrict__ col,
+                                                const int* __restrict__ incl, double* Z,
+                                                double* Wp, double* Wd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = t >> 1, side = t & 1, lane = threadIdx.x;
+  const unsigned pm = 3u << (lane & ~1);
+  if (s >= N) return;  // uniform over the pair
   const int s0 = bstart[s], s1 = bend[s], c = col[s];
   const size_t ld = (size_t)N;
   if (s1 - s0 == 1) {
-    Z[s0 * ld + c] = 1.0;
+    if (side == 0) Z[s0 * ld + c] = 1.0;
     return;
   }
   if (incl[s]) return;
-  const double lm = lam[s], pm = h->pivmin;
-  double dp = pivot_floor(d[s0] - lm, pm);
-  Z[s0 * ld + c] = dp;
-  for (int i = s0 + 1; i < s1; ++i) {
-    dp = pivot_floor((d[i] - lm) - e2[i - 1] / dp, pm);
-    Z[i * ld + c] = dp;
+  const double lm = lam[s];
+  if (side == 0) {
+    double dp = pivot_floor(ds[s0] - lm), rp = rcp_nr(dp);
+    Z[s0 * ld + c] = dp;
+    Wp[s0 * ld + c] = rp;
+    for (int i = s0 + 1; i < s1; ++i) {
+      dp = pivot_floor(fma(-e2[i - 1], rp, ds[i] - lm));
+      rp = rcp_nr(dp);
+      Z[i * ld + c] = dp;
+      Wp[i * ld + c] = rp;
+    }
+  } else {
+    double dm = pivot_floor(ds[s1 - 1] - lm), rm = rcp_nr(dm);
+    Wd[(s1 - 1) * ld + c] = rm;
+    for (int i = s1 - 2; i >= s0; --i) {
+      dm = pivot_floor(fma(-e2[i], rm, ds[i] - lm));
+      rm = rcp_nr(dm);
+      Wd[i * ld + c] = rm;
+    }
   }
-  double dm = pivot_floor(d[s1 - 1] - lm, pm);
-  Wd[(s1 - 1) * ld + c] = dm;
-  double best = fabs(dp);
-  int r = s1 - 1;
-  for (int i = s1 - 2; i >= s0; --i) {
-    const double ci = d[i] - lm;
-    dm = pivot_floor(ci - e2[i] / dm, pm);
-    Wd[i * ld + c] = dm;
-    const double g = fabs(Z[i * ld + c] + dm - ci);
-    if (g <= best) {
+  __syncwarp(pm);
+  // twist: thread 0 the rows [s0, mid), thread 1 [mid, s1)
+  const int mid = (s0 + s1) >> 1;
+  const int a = side == 0 ? s0 : mid, b = side == 0 ? mid : s1;
+  double best = 0.0;
+  int r = -1;
+  for (int i = a; i < b; ++i) {
+    const double g = i < s1 - 1 ? fabs(fma(-e2[i], Wd[(i + 1) * ld + c], Z[i * ld + c]))
+                                : fabs(Z[i * ld + c]);
+    if (r < 0 || g < best) {
       best = g;
       r = i;
     }
   }
-  Z[r * ld + c] = 1.0;
-  double z = 1.0;
-  for (int i = r - 1; i >= s0; --i) {
-    z = -es[i] * z / Z[i * ld + c];
-    if (fabs(z) > 1e150) {  // rescale what is written (rare: a tiny pivot)
-      for (int u = i + 1; u <= r; ++u) Z[u * ld + c] *= 1e-150;
-      z *= 1e-150;
+  {
+    const double ob = __shfl_xor_sync(pm, best, 1);
+    const int orr = __shfl_xor_sync(pm, r, 1);
+    // the lower rows win ties; an empty half (r < 0) never wins
+    const bool take_other = orr >= 0 && (r < 0 || ob < best || (ob == best && orr < r));
+    if (take_other) {
+      best = ob;
+      r = orr;
     }
-    Z[i * ld + c] = z;
   }
-  z = Z[r * ld + c];
-  for (int i = r + 1; i < s1; ++i) {
-    z = -es[i - 1] * z / Wd[i * ld + c];
-    if (fabs(z) > 1e150) {
-      for (int u = s0; u < i; ++u) Z[u * ld + c] *= 1e-150;
-      z *= 1e-150;
+  __syncwarp(pm);
+  // z: thread 0 upwards from r, thread 1 downwards; rescaled by 2^-500 when above 2^500
+  int nres = 0;
+  if (side == 0) {
+    Z[r * ld + c] = 1.0;
+    double z = 1.0;
+    for (int i = r - 1; i >= s0; --i) {
+      z = -es[i] * z * Wp[i * ld + c];
+      if (fabs(z) > 0x1p500) {
+        for (int u = i + 1; u <= r; ++u) Z[u * ld + c] *= 0x1p-500;
+        z *= 0x1p-500;
+        ++nres;
+      }
+      Z[i * ld + c] = z;
     }
-    Z[i * ld + c] = z;
+  } else {
+    double z = 1.0;
+    for (int i = r + 1; i < s1; ++i) {
+      z = -es[i - 1] * z * Wd[i * ld + c];
+      if (fabs(z) > 0x1p500) {
+        for (int u = r + 1; u < i; ++u) Z[u * ld + c] *= 0x1p-500;
+        z *= 0x1p-500;
+        ++nres;
+      }
+      Z[i * ld + c] = z;
+    }
   }
+  __syncwarp(pm);
+  // bring both halves to the same scale, then normalise
+  const int lo_i = side == 0 ? s0 : r + 1, hi_i = side == 0 ? r + 1 : s1;
+  const int other = __shfl_xor_sync(pm, nres, 1);
+  for (int q = nres; q < other; ++q)
+    for (int i = lo_i; i < hi_i; ++i) Z[i * ld + c] *= 0x1p-500;
   double n2 = 0.0;
-  for (int i = s0; i < s1; ++i) {
+  for (int i = lo_i; i < hi_i; ++i) {
     const double zi = Z[i * ld + c];
-    n2 += zi * zi;
+    n2 = fma(zi, zi, n2);
   }
+  n2 += __shfl_xor_sync(pm, n2, 1);
   const double sc = 1.0 / sqrt(n2);
-  for (int i = s0; i < s1; ++i) Z[i * ld + c] *= sc;
+  for (int i = lo_i; i < hi_i; ++i) Z[i * ld + c] *= sc;
 }
 
 __device__ __forceinline__ double hash_uniform(unsigned long long key) {
@@ -831,10 +1099,14 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
   double* Aw = (double*)(ws + L.A);
   double* Yr = (double*)(ws + L.Yr);
   double* Wd = (double*)(ws + L.Wd);
+  double* Wp = (double*)(ws + L.Wp);
   double* d = (double*)(ws + L.d);
   double* e = (double*)(ws + L.e);
+  double* ds = (double*)(ws + L.ds);
   double* es = (double*)(ws + L.es);
   double* e2 = (double*)(ws + L.e2);
+  float* df = (float*)(ws + L.df);
+  float* e2f = (float*)(ws + L.e2f);
   double* tau = (double*)(ws + L.tau);
   double* lam = (double*)(ws + L.lam);
   double* glo = (double*)(ws + L.glo);
@@ -882,23 +1154,27 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
     return DONOF_ERR_CUDA;
   count_launch(1);
 
-  // 2. eigenvalues
-  const size_t prep_smem = (size_t)2 * N * 8;
+  // 2. eigenvalues (of T scaled to ||T||_inf <= 1)
+  const size_t prep_smem = (size_t)2 * N * 4;
   if (!ok(cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)prep_smem)))
     return DONOF_ERR_CUDA;
-  k_tri_prep<<<1, 256, prep_smem, s>>>(N, d, e, hdr, es, e2, bstart, bend, glo, ghi);
-  const int gslot = (N + kSlotThreads - 1) / kSlotThreads;
-  k_bisect<<<gslot, kSlotThreads, 0, s>>>(N, d, e2, bstart, bend, glo, ghi, hdr, lam);
+  k_tri_prep<<<1, 256, prep_smem, s>>>(N, d, e, hdr, ds, es, e2, df, e2f, bstart, bend, glo, ghi);
+  const size_t bis_smem = (size_t)N * 24;
+  if (!ok(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bis_smem)))
+    return DONOF_ERR_CUDA;
+  k_bisect<<<(N * 16 + kBisThreads - 1) / kBisThreads, kBisThreads, bis_smem, s>>>(
+      N, ds, e2, df, e2f, bstart, bend, glo, ghi, hdr, lam);
   const size_t rank_smem = (size_t)N * 12;
   if (!ok(cudaFuncSetAttribute(k_rank_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)rank_smem)))
     return DONOF_ERR_CUDA;
   k_rank_plan<<<(N + 255) / 256, 256, rank_smem, s>>>(N, lam, bend, hdr, col, w, incl, cl);
   // 3. eigenvectors of T (into V)
-  k_twisted<<<gslot, kSlotThreads, 0, s>>>(N, d, es, e2, bstart, bend, lam, col, incl, hdr, V,
-                                           Wd);
-  k_cluster_fix<<<kFixCTAs, 32, 0, s>>>(N, d, es, bstart, bend, lam, col, cl, hdr, V, fix);
+  k_twisted<<<(2 * N + 31) / 32, 32, 0, s>>>(N, ds, es, e2, bstart, bend, lam, col, incl, V, Wp,
+                                            Wd);
+  k_cluster_fix<<<kFixCTAs, 32, 0, s>>>(N, ds, es, bstart, bend, lam, col, cl, hdr, V, fix);
   count_launch(5);
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
 
