@@ -15,7 +15,7 @@
 //      per eigenvalue, the twist r where |gamma_r| is smallest; eigenvalues of one block closer
 //      than 1e-5 ||T||_inf form clusters whose vectors come from inverse iteration (LU with
 //      partial pivoting) and modified Gram-Schmidt inside the cluster.
-//   4. V = Q Z by the compact WY form of blocks of 64 reflectors: the blocks' triangular
+//   4. V = Q Z by the compact WY form of blocks of 128 reflectors: the blocks' triangular
 //      factors from their Gram matrices, and two FP64 GEMMs per block.
 #include <float.h>
 
@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kNb = 64;           // reflectors per WY block
+constexpr int kNb = 128;          // reflectors per WY block
 constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
 constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
 // tridiagonal reduction: vector elements per thread held in registers, and the largest n whose
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
   const int G = gridDim.x;
   double* v = sm;           // reflector of the current step (indices k+1 .. N-1)
   double* x = sm + N;       // next column, then its reflector
-  double* w = sm + 2 * N;   // w = p - (tau/2)(p.v) v
+  double* p = sm + 2 * N;   // p = tau A v of the current step
   double* A = a.A;
   const bool writer = blockIdx.x == 0;
   if (N <= 2) {
@@ -339,42 +339,43 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     }
     for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads)
       acc = fma(__ldcg(pk + j), v[j], acc);
-    // w = p_k - (tau_k / 2)(p_k . v_k) v_k
-    const double aw = 0.5 * tau_c * block_sum_d(acc, red);
+    // alpha = (tau_k / 2)(p_k . v_k); with w = p - alpha v the update A - v w^T - w v^T is
+    // A_ij - v_i p_j - (p_i - 2 alpha v_i) v_j, formed from p and v alone
+    const double al = 0.5 * tau_c * block_sum_d(acc, red);
 #pragma unroll
     for (int r = 0; r < kTriVec; ++r) {
       const int j = k + 1 + tid + kTriThreads * r;
-      if (j < N) w[j] = fma(-aw, v[j], pr[r]);
+      if (j < N) p[j] = pr[r];
     }
     for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads)
-      w[j] = fma(-aw, v[j], __ldcg(pk + j));
+      p[j] = __ldcg(pk + j);
     __syncthreads();
     // row k+1 of the updated matrix (v[k+1] = 1): its column k+1 below the diagonal
-    const double wk1 = w[k + 1];
+    const double ck1 = fma(-2.0, al, p[k + 1]);
     xn = 0.0;
 #pragma unroll
     for (int r = 0; r < kTriVec; ++r) {
       const int j = k + 1 + tid + kTriThreads * r;
       if (j < N) {
-        const double xj = fma(-wk1, v[j], ar[r] - w[j]);
+        const double xj = fma(-ck1, v[j], ar[r] - pr[r]);
         x[j] = xj;
         if (j >= k + 3) xn = fma(xj, xj, xn);
       }
     }
     for (int j = k + 1 + tid + kTriThreads * kTriVec; j < N; j += kTriThreads) {
-      const double xj = fma(-wk1, v[j], __ldcg(Ak1 + j) - w[j]);
+      const double xj = fma(-ck1, v[j], __ldcg(Ak1 + j) - p[j]);
       x[j] = xj;
       if (j >= k + 3) xn = fma(xj, xj, xn);
     }
     // register path: the own row's rank-2 update, while the norm is reduced (not at the last
     // step, whose 2 x 2 block is formed from the rows as they stand)
     if (has_row && k + 1 < N - 2) {
-      const double vi = v[myrow], wi = w[myrow];
+      const double vi = v[myrow], ci = fma(-2.0 * al, vi, p[myrow]);
 #pragma unroll
       for (int q = 0; q < kTriRowRegs; ++q) {
         const int j = k + 2 + lane + 32 * q;
         if (j < N) {
-          rr[q] = fma(-wi, v[j], fma(-vi, w[j], rr[q]));
+          rr[q] = fma(-ci, v[j], fma(-vi, p[j], rr[q]));
           Amy[j] = rr[q];
         }
       }
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       if (writer && tid == 0) {
         a.d[N - 2] = x[N - 2];
         a.e[N - 2] = x[N - 1];
-        a.d[N - 1] = __ldcg(A + (size_t)(N - 1) * N + N - 1) - 2.0 * v[N - 1] * w[N - 1];
+        const double vl = v[N - 1], cl = fma(-2.0 * al, vl, p[N - 1]);
+        a.d[N - 1] = __ldcg(A + (size_t)(N - 1) * N + N - 1) - vl * p[N - 1] - cl * vl;
       }
       break;
     }
@@ -418,16 +420,16 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
         if (i >= N) break;
         if (i < k + 2) continue;
         double* Ar = A + (size_t)i * N;
-        const double vi = v[i], wi = w[i];
+        const double vi = v[i], ci = fma(-2.0 * al, vi, p[i]);
         double acc2 = 0.0;
         int j = k + 2 + lane;
         for (; j + 96 < N; j += 128) {
           const double a0 = __ldcg(Ar + j), a1 = __ldcg(Ar + j + 32), a2 = __ldcg(Ar + j + 64),
                        a3 = __ldcg(Ar + j + 96);
-          const double b0 = fma(-wi, v[j], fma(-vi, w[j], a0));
-          const double b1 = fma(-wi, v[j + 32], fma(-vi, w[j + 32], a1));
-          const double b2 = fma(-wi, v[j + 64], fma(-vi, w[j + 64], a2));
-          const double b3 = fma(-wi, v[j + 96], fma(-vi, w[j + 96], a3));
+          const double b0 = fma(-ci, v[j], fma(-vi, p[j], a0));
+          const double b1 = fma(-ci, v[j + 32], fma(-vi, p[j + 32], a1));
+          const double b2 = fma(-ci, v[j + 64], fma(-vi, p[j + 64], a2));
+          const double b3 = fma(-ci, v[j + 96], fma(-vi, p[j + 96], a3));
           Ar[j] = b0;
           Ar[j + 32] = b1;
           Ar[j + 64] = b2;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
           acc2 = fma(b3, x[j + 96], acc2);
         }
         for (; j < N; j += 32) {
-          const double b0 = fma(-wi, v[j], fma(-vi, w[j], __ldcg(Ar + j)));
+          const double b0 = fma(-ci, v[j], fma(-vi, p[j], __ldcg(Ar + j)));
           Ar[j] = b0;
           acc2 = fma(b0, x[j], acc2);
         }
@@ -989,7 +991,7 @@ __global__ void __launch_bounds__(32) k_cluster_fix(int N, const double* __restr
 // 4. back-transformation V = Q Z, Q = H_0 ... H_{nref-1} in blocks of kNb reflectors
 // ---------------------------------------------------------------------------
 // Gram matrices G_b = Y_b^T Y_b of every block (entries c <= c' only), Y_b's column c the
-// reflector k0 + c: grid (nblk, 4, 4) of 16 x 16 sub-tiles, upper ones only.
+// reflector k0 + c: grid (nblk, kNb / 16, kNb / 16) of 16 x 16 sub-tiles, upper ones only.
 __global__ void __launch_bounds__(256) k_gram(int N, int nref, const double* __restrict__ Yr,
                                               double* G) {
   const int b = blockIdx.x, tr = blockIdx.y, tc = blockIdx.z;
@@ -1040,10 +1042,12 @@ __global__ void k_tfactor(int nref, const double* __restrict__ tau, const double
 }
 
 // W2 = T_b W1 (m x N), kApplyCols columns of W1 per CTA, thread r one row.
+constexpr size_t kApplySmem = (size_t)(kNb * (kNb + 1) + kNb * kApplyCols) * 8;
 __global__ void __launch_bounds__(kNb) k_apply_tfactor(int N, int m, const double* __restrict__ Tb,
                                                        const double* __restrict__ W1, double* W2) {
-  __shared__ double Ts[kNb][kNb + 1];
-  __shared__ double Ws[kNb][kApplyCols];
+  extern __shared__ double sa[];
+  double(*Ts)[kNb + 1] = (double(*)[kNb + 1])sa;                   // [kNb][kNb + 1]
+  double(*Ws)[kApplyCols] = (double(*)[kApplyCols])(sa + kNb * (kNb + 1));  // [kNb][kApplyCols]
   const int r = threadIdx.x, c0 = blockIdx.x * kApplyCols;
   for (int i = 0; i < kNb; ++i) Ts[i][r] = Tb[i * kNb + r];
   for (int cc = 0; cc < kApplyCols; ++cc) {
@@ -1180,7 +1184,10 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
 
   // 4. V = Q Z
   if (L.nblk > 0) {
-    k_gram<<<dim3(L.nblk, 4, 4), 256, 0, s>>>(N, L.nref, Yr, G);
+    if (!ok(cudaFuncSetAttribute(k_apply_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kApplySmem)))
+      return DONOF_ERR_CUDA;
+    k_gram<<<dim3(L.nblk, kNb / 16, kNb / 16), 256, 0, s>>>(N, L.nref, Yr, G);
     k_tfactor<<<L.nblk, kNb, 0, s>>>(L.nref, tau, G, T);
     count_launch(2);
   }
@@ -1195,7 +1202,7 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
                          s)))
       return DONOF_ERR_CUDA;
     // W2 = T_b W1
-    k_apply_tfactor<<<(N + kApplyCols - 1) / kApplyCols, kNb, 0, s>>>(
+    k_apply_tfactor<<<(N + kApplyCols - 1) / kApplyCols, kNb, kApplySmem, s>>>(
         N, m, T + (size_t)b * kNb * kNb, W1, W2);
     count_launch(1);
     // Z[R0:, :] -= Y_b W2
