@@ -15,7 +15,7 @@
 //      per eigenvalue, the twist r where |gamma_r| is smallest; eigenvalues of one block closer
 //      than 1e-5 ||T||_inf form clusters whose vectors come from inverse iteration (LU with
 //      partial pivoting) and modified Gram-Schmidt inside the cluster.
-//   4. V = Q Z by the compact WY form of blocks of 128 reflectors: the blocks' triangular
+//   4. V = Q Z by the compact WY form of blocks of 64 reflectors: the blocks' triangular
 //      factors from their Gram matrices, and two FP64 GEMMs per block.
 #include <float.h>
 
@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kNb = 128;          // reflectors per WY block
+constexpr int kNb = 64;           // reflectors per WY block
 constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
 constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
 // tridiagonal reduction: vector elements per thread held in registers, and the largest n whose
