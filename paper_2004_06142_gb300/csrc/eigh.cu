@@ -27,14 +27,17 @@
 namespace donof {
 namespace {
 
-constexpr int kTriThreads = 256;
-constexpr int kTriWarps = kTriThreads / 32;
+constexpr int kRowWarps = 8;                  // warps of a tridiagonal-reduction CTA that own rows
+constexpr int kTriWarps = kRowWarps + 1;      // ... and the scalar warp
+constexpr int kTriThreads = 32 * kTriWarps;
+constexpr int kScalarTid = 32 * kRowWarps;    // lane 0 of the scalar warp
+static_assert(kTriWarps <= 16, "block_sum_d sums at most 16 warps");
 constexpr int kNb = 64;           // reflectors per WY block
 constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
 constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
 // tridiagonal reduction: vector elements per thread held in registers, and the largest n whose
 // trailing rows (one per warp) stay in registers, kTriRowRegs elements per lane
-constexpr int kTriVec = 5;
+constexpr int kTriVec = 5;  // (kTriRegMaxN + kTriThreads - 1) / kTriThreads
 constexpr int kTriRegMaxN = 1216;
 constexpr int kTriRowRegs = (kTriRegMaxN - 2 + 31) / 32;
 constexpr double kClusterTol = 1e-5;
@@ -128,7 +131,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   if (threadIdx.x < 32) {
     double t = threadIdx.x < kTriWarps ? red[threadIdx.x] : 0.0;
 #pragma unroll
-    for (int o = kTriWarps / 2; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int o = 8; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (threadIdx.x == 0) red[kTriWarps] = t;
   }
   __syncthreads();
@@ -239,17 +242,20 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     }
     return;
   }
-  // rows are dealt to CTAs cyclically (row i to CTA i mod G), then to the CTA's warps, so the
-  // shrinking trailing matrix stays spread over every SM; with N <= G * kTriWarps each warp
-  // owns one row at most and keeps it in registers while it is updated
-  auto row_of = [&](int t) { return blockIdx.x + G * (wid + kTriWarps * t); };
-  const bool reg_rows = N <= kTriRegMaxN && N <= G * kTriWarps;
-  const int myrow = row_of(0);
+  // rows are dealt to CTAs cyclically (row i to CTA i mod G), then to the CTA's row warps, so
+  // the shrinking trailing matrix stays spread over every SM; with N <= G * kRowWarps each row
+  // warp owns one row at most and keeps it in registers while it is updated.  The last warp
+  // owns no row: its lane 0 forms the reflectors' scalars.
+  const bool row_warp = wid < kRowWarps;
+  auto row_of = [&](int t) { return blockIdx.x + G * (wid + kRowWarps * t); };
+  const bool reg_rows = N <= kTriRegMaxN && N <= G * kRowWarps;
+  const int myrow = row_warp ? row_of(0) : N;
   unsigned bar = 0;
 
-  // reflector of x[k0..N) (xn2 = sum over j > k0 of x_j^2; the scalars from thread 0)
-  auto householder = [&](int k0, double xn2, double& tau, double& beta) {
-    if (tid == 0) {
+  // reflector of x[k0..N) (xn2 = sum over j > k0 of x_j^2): the scalars tau, beta and the
+  // scale of u's tail (0 when the column is already reduced: u = e_k0)
+  auto hh_scalars = [&](int k0, double xn2) {
+    if (tid == kScalarTid) {
       const double al = x[k0];
       double t = 0.0, b = al, sc = 0.0;
       if (xn2 != 0.0) {
@@ -261,13 +267,17 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       sh[1] = b;
       sh[2] = sc;
     }
-    __syncthreads();
-    tau = sh[0];
-    beta = sh[1];
-    const double sc = sh[2];  // 0 when the column is already reduced (u = e_k0)
-    for (int j = k0 + 1 + tid; j < N; j += kTriThreads) x[j] *= sc;
-    if (tid == 0) x[k0] = 1.0;
-    __syncthreads();
+  };
+  // after a barrier: x[k0+1..) scaled into u's tail, x[k0] = 1; CTA 0 also stores u as row
+  // `refl` of Yr
+  auto hh_apply = [&](int k0, int refl) {
+    const double sc = sh[2];
+    double* Yk = a.Yr + (size_t)refl * N;
+    for (int j = k0 + tid; j < N; j += kTriThreads) {
+      const double u = j == k0 ? 1.0 : x[j] * sc;
+      x[j] = u;
+      if (writer) Yk[j] = u;
+    }
   };
 
   // reflector 0 from row 0 (column 0)
@@ -277,26 +287,28 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     x[j] = xj;
     if (j >= 2) xn = fma(xj, xj, xn);
   }
-  double tau_c, beta;
-  householder(1, block_sum_d(xn, red), tau_c, beta);
-  if (writer) {
-    if (tid == 0) {
-      a.d[0] = x[0];
-      a.e[0] = beta;
-      a.tau[0] = tau_c;
-    }
-    for (int j = 1 + tid; j < N; j += kTriThreads) a.Yr[j] = x[j];
+  hh_scalars(1, block_sum_d(xn, red));
+  __syncthreads();
+  double tau_c = sh[0], beta = sh[1];
+  if (writer && tid == 0) {
+    a.d[0] = x[0];
+    a.e[0] = beta;
+    a.tau[0] = tau_c;
   }
-  for (int t = 0;; ++t) {
-    const int i = row_of(t);
-    if (i >= N) break;
-    if (i < 1) continue;
-    const double* Ar = A + (size_t)i * N;
-    double acc = 0.0;
+  hh_apply(1, 0);
+  __syncthreads();
+  if (row_warp) {
+    for (int t = 0;; ++t) {
+      const int i = row_of(t);
+      if (i >= N) break;
+      if (i < 1) continue;
+      const double* Ar = A + (size_t)i * N;
+      double acc = 0.0;
 #pragma unroll 4
-    for (int j = 1 + lane; j < N; j += 32) acc = fma(__ldcg(Ar + j), x[j], acc);
-    acc = warp_sum_d(acc);
-    if (lane == 0) a.pbuf[i] = tau_c * acc;
+      for (int j = 1 + lane; j < N; j += 32) acc = fma(__ldcg(Ar + j), x[j], acc);
+      acc = warp_sum_d(acc);
+      if (lane == 0) a.pbuf[i] = tau_c * acc;
+    }
   }
   if (!grid_barrier(a.hdr, (++bar) * G, &s_flag)) return;
   {
@@ -308,6 +320,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
   for (int k = 0; k <= N - 3; ++k) {
     const double* pk = a.pbuf + (size_t)(k & 1) * N;
     const double* Ak1 = A + (size_t)(k + 1) * N;
+    const bool last = k + 1 == N - 2;
     // every load of the step at once: p_k, row k+1, and (register path) the warp's own row
     double pr[kTriVec], ar[kTriVec];
 #pragma unroll
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     }
     double rr[kTriRowRegs];
     const bool has_row = reg_rows && myrow < N && myrow >= k + 2;
-    double* Amy = A + (size_t)myrow * N;
+    double* Amy = A + (size_t)(has_row ? myrow : 0) * N;
     if (has_row) {
 #pragma unroll
       for (int q = 0; q < kTriRowRegs; ++q) {
@@ -330,7 +343,6 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
         rr[q] = j < N ? __ldcg(Amy + j) : 0.0;
       }
     }
-    // the loads beyond kTriVec per thread (large N only)
     double acc = 0.0;
 #pragma unroll
     for (int r = 0; r < kTriVec; ++r) {
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
     }
     // register path: the own row's rank-2 update, while the norm is reduced (not at the last
     // step, whose 2 x 2 block is formed from the rows as they stand)
-    if (has_row && k + 1 < N - 2) {
+    if (has_row && !last) {
       const double vi = v[myrow], ci = fma(-2.0 * al, vi, p[myrow]);
 #pragma unroll
       for (int q = 0; q < kTriRowRegs; ++q) {
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       }
     }
     const double xn2 = block_sum_d(xn, red);
-    if (k + 1 == N - 2) {  // the last 2 x 2 block
+    if (last) {  // the last 2 x 2 block
       if (writer && tid == 0) {
         a.d[N - 2] = x[N - 2];
         a.e[N - 2] = x[N - 1];
@@ -390,32 +402,37 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tridiag(TriArgs a) {
       }
       break;
     }
-    double tau_n;
-    householder(k + 2, xn2, tau_n, beta);
-    if (writer) {
-      if (tid == 0) {
-        a.d[k + 1] = x[k + 1];
-        a.e[k + 1] = beta;
-        a.tau[k + 1] = tau_n;
+    // the scalar warp forms the next reflector while the row warps take the dot of their
+    // updated row with the unscaled column (u_{k+2} = 1, u_j = sc x_j beyond)
+    hh_scalars(k + 2, xn2);
+    double rawdot = 0.0, r0 = 0.0;
+    if (has_row) {
+#pragma unroll
+      for (int q = 0; q < kTriRowRegs; ++q) {
+        const int j = k + 2 + lane + 32 * q;
+        if (j < N) {
+          if (q == 0 && lane == 0) r0 = rr[0];
+          else rawdot = fma(rr[q], x[j], rawdot);
+        }
       }
-      double* Yk = a.Yr + (size_t)(k + 1) * N;
-      for (int j = k + 2 + tid; j < N; j += kTriThreads) Yk[j] = x[j];
+      rawdot = warp_sum_d(rawdot);
     }
+    __syncthreads();
+    const double tau_n = sh[0], sc = sh[2];
+    beta = sh[1];
+    if (writer && tid == 0) {
+      a.d[k + 1] = x[k + 1];
+      a.e[k + 1] = beta;
+      a.tau[k + 1] = tau_n;
+    }
+    hh_apply(k + 2, k + 1);
     // p_{k+1} = tau A u over the own rows i >= k+2
     double* pn = a.pbuf + (size_t)((k + 1) & 1) * N;
     if (reg_rows) {
-      if (has_row) {
-        double acc2 = 0.0;
-#pragma unroll
-        for (int q = 0; q < kTriRowRegs; ++q) {
-          const int j = k + 2 + lane + 32 * q;
-          if (j < N) acc2 = fma(rr[q], x[j], acc2);
-        }
-        acc2 = warp_sum_d(acc2);
-        if (lane == 0) pn[myrow] = tau_n * acc2;
-      }
+      if (has_row && lane == 0) pn[myrow] = tau_n * fma(sc, rawdot, r0);
     } else {
-      for (int t = 0;; ++t) {
+      __syncthreads();  // the scaled reflector
+      for (int t = 0; row_warp; ++t) {
         const int i = row_of(t);
         if (i >= N) break;
         if (i < k + 2) continue;
