@@ -21,6 +21,7 @@
 
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -33,7 +34,10 @@ constexpr int kTriThreads = 32 * kTriWarps;
 constexpr int kScalarTid = 32 * kRowWarps;    // lane 0 of the scalar warp
 static_assert(kTriWarps <= 16, "block_sum_d sums at most 16 warps");
 constexpr int kNb = 64;           // reflectors per WY block
-constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the cluster kernel
+constexpr int kFixCTAs = 32;      // CTAs (one warp each) of the small-cluster kernel
+constexpr int kSmallCl = 32;      // clusters up to this size are orthonormalised by one warp
+constexpr int kClDesc = 5;        // ints per cluster: first slot, members, block start, block
+                                  // length, offset of its vectors in the scratch (large ones)
 constexpr int kApplyCols = 8;     // columns of W1 per CTA in the triangular-factor product
 // tridiagonal reduction: vector elements per thread held in registers, and the largest n whose
 // trailing rows (one per warp) stay in registers, kTriRowRegs elements per lane
@@ -47,7 +51,9 @@ struct EighHdr {
   unsigned int ctr;   // grid-barrier arrivals of the tridiagonal reduction
   int abort;          // set when a barrier wait ran out
   int ncl;            // clusters found
+  int maxcl;          // members of the largest cluster
   int nonfinite;      // A holds a NaN or an infinity
+  int pad;
   unsigned long long amax_bits;  // max |A_ij| (bit pattern of a non-negative double)
   double scale;       // the power of two applied to A
   double tscale;      // the power of two applied to T: ||T||_inf * tscale in [1/2, 1)
@@ -57,7 +63,7 @@ struct EighHdr {
 
 struct EighLayout {
   size_t hdr, A, Yr, Wd, Wp, d, e, ds, es, e2, df, e2f, tau, pbuf, lam, glo, ghi, col, bstart,
-      bend, incl, cl, T, G, W1, W2, part, fix, total;
+      bend, incl, cl, cj, T, G, W1, W2, part, total;
   int nref, nblk;
 };
 
@@ -93,7 +99,8 @@ EighLayout eigh_layout(int N) {
   L.bstart = take(n * 4);
   L.bend = take(n * 4);
   L.incl = take(n * 4);
-  L.cl = take(2 * n * 4);
+  L.cl = take((size_t)kClDesc * n * 4);
+  L.cj = take(n * 4);
   L.T = take((size_t)L.nblk * kNb * kNb * 8);
   L.G = take((size_t)L.nblk * kNb * kNb * 8);
   L.W1 = take((size_t)kNb * n * 8);
@@ -104,8 +111,17 @@ EighLayout eigh_layout(int N) {
     const size_t k = (size_t)splitk_count(m, N, N - 1 - b * kNb);
     if (k > ks) ks = k;
   }
-  L.part = take(ks > 1 ? ks * kNb * n * 8 : 0);
-  L.fix = take((size_t)kFixCTAs * 6 * n * 8);
+  size_t part = ks > 1 ? ks * kNb * n : 0;
+  // the large clusters' panel products: (r0 x 32) and (32 x 32) with contraction length <= N
+  for (int r0 = 32; r0 < N; r0 += 32) {
+    const size_t k = (size_t)splitk_count(r0, 32, N);
+    if (k > 1 && k * r0 * 32 > part) part = k * r0 * 32;
+  }
+  {
+    const size_t k = (size_t)splitk_count(32, 32, N);
+    if (k > 1 && k * 32 * 32 > part) part = k * 32 * 32;
+  }
+  L.part = take(part * 8);
   L.total = off;
   return L;
 }
@@ -721,7 +737,8 @@ __device__ __forceinline__ long long dbl_key(double x) {
 // kClusterTol ||T|| (the gaps tested in parallel, the runs found by one thread).
 __global__ void __launch_bounds__(256) k_rank_plan(int N, const double* __restrict__ lam,
                                                    const int* __restrict__ bend, EighHdr* h,
-                                                   int* col, double* w_out, int* incl, int* cl) {
+                                                   int* col, double* w_out, int* incl, int* cl,
+                                                   int* cj, const int* __restrict__ bstart) {
   extern __shared__ long long skey[];
   int* sgap = (int*)(skey + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) skey[i] = dbl_key(lam[i]);
@@ -746,19 +763,31 @@ __global__ void __launch_bounds__(256) k_rank_plan(int N, const double* __restri
     sgap[i] = (i + 1 < bend[i] && lam[i + 1] - lam[i] < tol) ? 1 : 0;
   __syncthreads();
   if (threadIdx.x != 0) return;
-  int ncl = 0;
+  int ncl = 0, maxcl = 0, off = 0;
   for (int s0 = 0; s0 < N;) {
     int t = s0;
     while (sgap[t]) ++t;  // sgap[bend - 1] = 0 ends every run inside its block
-    for (int u = s0; u <= t; ++u) incl[u] = t > s0 ? 1 : 0;
-    if (t > s0) {
-      cl[2 * ncl] = s0;
-      cl[2 * ncl + 1] = t - s0 + 1;
+    const int m = t - s0 + 1;
+    for (int u = s0; u <= t; ++u) {
+      incl[u] = m > 1 ? ncl + 1 : 0;  // cluster id + 1
+      cj[u] = u - s0;                 // member index
+    }
+    if (m > 1) {
+      const int a0 = bstart[s0], L = bend[s0] - a0;
+      int* c = cl + kClDesc * ncl;
+      c[0] = s0;
+      c[1] = m;
+      c[2] = a0;
+      c[3] = L;
+      c[4] = off;
+      if (m > kSmallCl) off += m * L;  // large clusters keep their vectors in the scratch
+      maxcl = max(maxcl, m);
       ++ncl;
     }
     s0 = t + 1;
   }
   h->ncl = ncl;
+  h->maxcl = maxcl;
 }
 
 // ---------------------------------------------------------------------------
@@ -901,106 +930,154 @@ __device__ __forceinline__ double hash_uniform(unsigned long long key) {
   return (double)(z >> 11) * 0x1p-52 - 1.0;
 }
 
-// Clusters: for each member in order, three steps of inverse iteration from a pseudo-random
-// start, (T_b - lambda I) y = x by LU with partial pivoting (pivots below eps ||T|| raised to
-// that size), each followed by modified Gram-Schmidt against the members before it.  One warp
-// per cluster; lane 0 factors and solves, the warp does the vector work.
-__global__ void __launch_bounds__(32) k_cluster_fix(int N, const double* __restrict__ d,
-                                                    const double* __restrict__ es,
-                                                    const int* __restrict__ bstart,
-                                                    const int* __restrict__ bend,
-                                                    const double* __restrict__ lam,
-                                                    const int* __restrict__ col,
-                                                    const int* __restrict__ cl, const EighHdr* h,
-                                                    double* Z, double* scratch) {
+// Clusters.  Every member first gets two steps of inverse iteration of its own, all members at
+// once (a thread each): (T_b - lambda I) = L D L^T without pivoting (pivots floored at 2^-100
+// as in the twisted factorisations), from a pseudo-random start, normalised after each step.
+// The vectors of a small cluster go to Z's columns and are orthonormalised by one warp (modified
+// Gram-Schmidt, twice); those of a large cluster go to rows of a scratch matrix and are
+// orthonormalised in panels of 32 (block classical Gram-Schmidt and a Cholesky QR of the
+// panel, each twice) on the GEMM kernel, then scattered to Z.  With shifts accurate to eps ||T||
+// a member's vector is its eigenvector up to (eps / gap)^2 of its neighbours, so the
+// orthonormalisation only mixes members whose eigenvalues are equal at working precision.
+__global__ void __launch_bounds__(32) k_cluster_vectors(
+    int N, const double* __restrict__ ds, const double* __restrict__ es,
+    const int* __restrict__ bstart, const int* __restrict__ bend, const double* __restrict__ lam,
+    const int* __restrict__ col, const int* __restrict__ incl, const int* __restrict__ cj,
+    const int* __restrict__ cl, double* Z, double* Yc, double* Wrp, double* Wl) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N || incl[t] == 0) return;
+  const int* c = cl + kClDesc * (incl[t] - 1);
+  const int a0 = bstart[t], L = bend[t] - a0, j = cj[t];
+  const size_t ld = (size_t)N;
+  const bool large = c[1] > kSmallCl;
+  double* y = large ? Yc + (size_t)c[4] + (size_t)j * L : Z + (size_t)a0 * ld + col[t];
+  const size_t ys = large ? 1 : ld;
+  double* rp = Wrp + (size_t)t * ld;  // reciprocal pivots
+  double* lm_ = Wl + (size_t)t * ld;  // multipliers
+  const double lm = lam[t];
+  double r = rcp_nr(pivot_floor(ds[a0] - lm));
+  rp[0] = r;
+  for (int i = 0; i + 1 < L; ++i) {
+    const double li = es[a0 + i] * r;
+    lm_[i] = li;
+    r = rcp_nr(pivot_floor(fma(-li, es[a0 + i], ds[a0 + i + 1] - lm)));
+    rp[i + 1] = r;
+  }
+  for (int i = 0; i < L; ++i)
+    y[i * ys] = hash_uniform(((unsigned long long)t << 32) + (unsigned long long)i);
+  for (int it = 0; it < 2; ++it) {
+    // L u = x (in place), w = D^-1 u, L^T y = w
+    double u = y[0];
+    for (int i = 1; i < L; ++i) {
+      u = fma(-lm_[i - 1], u, y[i * ys]);
+      y[i * ys] = u;
+    }
+    double yy = y[(L - 1) * ys] * rp[L - 1];
+    y[(L - 1) * ys] = yy;
+    double amax = fabs(yy);
+    for (int i = L - 2; i >= 0; --i) {
+      yy = fma(-lm_[i], yy, y[i * ys] * rp[i]);
+      y[i * ys] = yy;
+      amax = fmax(amax, fabs(yy));
+    }
+    const double sa = amax > 0.0 && isfinite(amax) ? 1.0 / amax : 1.0;
+    double n2 = 0.0;
+    for (int i = 0; i < L; ++i) {
+      const double v = y[i * ys] * sa;
+      n2 = fma(v, v, n2);
+    }
+    const double sc = sa / sqrt(n2);
+    for (int i = 0; i < L; ++i) y[i * ys] *= sc;
+  }
+}
+
+// Small clusters (at most kSmallCl members): modified Gram-Schmidt over the members in order,
+// twice, on Z's columns; one warp per cluster.
+__global__ void __launch_bounds__(32) k_cluster_small(int N, const int* __restrict__ col,
+                                                      const int* __restrict__ cl,
+                                                      const EighHdr* h, double* Z) {
   const int ncl = h->ncl, lane = threadIdx.x;
   const size_t ld = (size_t)N;
-  double* dl = scratch + (size_t)blockIdx.x * 6 * N;
-  double* dd = dl + N;
-  double* du = dd + N;
-  double* du2 = du + N;
-  double* pv = du2 + N;
-  double* xv = pv + N;
-  const double tiny = DBL_EPSILON * h->tnorm;
   for (int q = blockIdx.x; q < ncl; q += gridDim.x) {
-    const int s = cl[2 * q], m = cl[2 * q + 1];
-    const int a0 = bstart[s], L = bend[s] - a0;
-    for (int j = 0; j < m; ++j) {
-      const double lm = lam[s + j];
-      if (lane == 0) {
-        for (int i = 0; i < L; ++i) dd[i] = d[a0 + i] - lm;
-        for (int i = 0; i + 1 < L; ++i) {
-          dl[i] = es[a0 + i];
-          du[i] = es[a0 + i];
-          du2[i] = 0.0;
-        }
-        for (int i = 0; i + 1 < L; ++i) {
-          if (fabs(dd[i]) >= fabs(dl[i])) {
-            pv[i] = 0.0;
-            const double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
-            dl[i] = f;
-            dd[i + 1] -= f * du[i];
-          } else {
-            pv[i] = 1.0;
-            const double f = dd[i] / dl[i];
-            dd[i] = dl[i];
-            dl[i] = f;
-            const double t = du[i];
-            du[i] = dd[i + 1];
-            dd[i + 1] = t - f * dd[i + 1];
-            if (i + 2 < L) {
-              du2[i] = du[i + 1];
-              du[i + 1] = -f * du[i + 1];
-            }
-          }
-        }
-        for (int i = 0; i < L; ++i)
-          if (fabs(dd[i]) < tiny) dd[i] = dd[i] < 0.0 ? -tiny : tiny;
-      }
-      for (int i = lane; i < L; i += 32)
-        xv[i] = hash_uniform(((unsigned long long)(s + j) << 32) + (unsigned long long)i);
-      __syncwarp();
-      for (int it = 0; it < 3; ++it) {
-        if (lane == 0) {
-          for (int i = 0; i + 1 < L; ++i) {
-            if (pv[i] == 0.0) {
-              xv[i + 1] -= dl[i] * xv[i];
-            } else {
-              const double t = xv[i];
-              xv[i] = xv[i + 1];
-              xv[i + 1] = t - dl[i] * xv[i];
-            }
-          }
-          for (int i = L - 1; i >= 0; --i) {
-            double b = xv[i];
-            if (i + 1 < L) b -= du[i] * xv[i + 1];
-            if (i + 2 < L) b -= du2[i] * xv[i + 2];
-            b /= dd[i];
-            xv[i] = b;
-            if (fabs(b) > 1e100)
-              for (int u = 0; u < L; ++u) xv[u] *= 1e-100;
-          }
-        }
-        __syncwarp();
+    const int* c = cl + kClDesc * q;
+    const int s = c[0], m = c[1], a0 = c[2], L = c[3];
+    if (m > kSmallCl) continue;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < m; ++j) {
+        double* zj = Z + (size_t)a0 * ld + col[s + j];
         for (int jj = 0; jj < j; ++jj) {
-          const int cj = col[s + jj];
+          const double* zk = Z + (size_t)a0 * ld + col[s + jj];
           double dot = 0.0;
-          for (int i = lane; i < L; i += 32) dot += Z[(a0 + i) * ld + cj] * xv[i];
+          for (int i = lane; i < L; i += 32) dot = fma(zk[i * ld], zj[i * ld], dot);
           dot = __shfl_sync(0xffffffffu, warp_sum_d(dot), 0);
-          for (int i = lane; i < L; i += 32) xv[i] -= dot * Z[(a0 + i) * ld + cj];
+          for (int i = lane; i < L; i += 32) zj[i * ld] = fma(-dot, zk[i * ld], zj[i * ld]);
           __syncwarp();
         }
         double n2 = 0.0;
-        for (int i = lane; i < L; i += 32) n2 += xv[i] * xv[i];
+        for (int i = lane; i < L; i += 32) n2 = fma(zj[i * ld], zj[i * ld], n2);
         n2 = __shfl_sync(0xffffffffu, warp_sum_d(n2), 0);
         const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-        for (int i = lane; i < L; i += 32) xv[i] *= sc;
+        for (int i = lane; i < L; i += 32) zj[i * ld] *= sc;
         __syncwarp();
       }
-      const int cj = col[s + j];
-      for (int i = lane; i < L; i += 32) Z[(a0 + i) * ld + cj] = xv[i];
-      __syncwarp();
     }
+  }
+}
+
+// A panel of b <= 32 rows of length L (row-major, leading dimension L): the Cholesky factor
+// R^T R of its Gram matrix G (b x b, formed by the GEMM), computed by every CTA, then each
+// CTA's columns replaced by R^-T times them (the panel's rows become orthonormal).  A pivot
+// that is not positive (a dependent row) is raised to 1e-300 of the diagonal.
+__global__ void __launch_bounds__(128) k_chol_apply(int b, int L, const double* __restrict__ G,
+                                                    double* P) {
+  __shared__ double R[32][33];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < b * b; i += blockDim.x) R[i / b][i % b] = G[i];
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {  // right-looking Cholesky, R upper triangular in place
+    if (tid == 0) {
+      double d = R[k][k];
+      if (!(d > 1e-300 * fabs(G[k * b + k]))) d = fmax(1e-300 * fabs(G[k * b + k]), 1e-300);
+      R[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    const double rk = R[k][k];
+    for (int jj = k + 1 + tid; jj < b; jj += blockDim.x) R[k][jj] /= rk;
+    __syncthreads();
+    for (int idx = tid; idx < b * b; idx += blockDim.x) {
+      const int i = idx / b, jj = idx % b;
+      if (i > k && jj >= i) R[i][jj] = fma(-R[k][i], R[k][jj], R[i][jj]);
+    }
+    __syncthreads();
+  }
+  const int cidx = blockIdx.x * blockDim.x + tid;
+  if (cidx >= L) return;
+  double y[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) y[i] = i < b ? P[(size_t)i * L + cidx] : 0.0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    if (i < b) {
+      double v = y[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) v = fma(-R[k][i], y[k], v);
+      y[i] = v / R[i][i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < b) P[(size_t)i * L + cidx] = y[i];
+}
+
+// The rows of a large cluster's scratch into Z's columns.
+__global__ void k_cluster_scatter(int N, int s, int m, int a0, int L,
+                                  const double* __restrict__ Y, const int* __restrict__ col,
+                                  double* Z) {
+  const long long tot = (long long)m * L;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / L), r = (int)(i % L);
+    Z[(size_t)(a0 + r) * N + col[s + j]] = Y[i];
   }
 }
 
@@ -1137,12 +1214,12 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
   int* bend = (int*)(ws + L.bend);
   int* incl = (int*)(ws + L.incl);
   int* cl = (int*)(ws + L.cl);
+  int* cj = (int*)(ws + L.cj);
   double* T = (double*)(ws + L.T);
   double* G = (double*)(ws + L.G);
   double* W1 = (double*)(ws + L.W1);
   double* W2 = (double*)(ws + L.W2);
   double* part = (double*)(ws + L.part);
-  double* fix = (double*)(ws + L.fix);
   const long long nn = (long long)N * N;
   const size_t nnb = (size_t)nn * 8;
   auto ok = [](cudaError_t e) { return e == cudaSuccess; };
@@ -1191,13 +1268,68 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
   if (!ok(cudaFuncSetAttribute(k_rank_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)rank_smem)))
     return DONOF_ERR_CUDA;
-  k_rank_plan<<<(N + 255) / 256, 256, rank_smem, s>>>(N, lam, bend, hdr, col, w, incl, cl);
+  k_rank_plan<<<(N + 255) / 256, 256, rank_smem, s>>>(N, lam, bend, hdr, col, w, incl, cl, cj,
+                                                      bstart);
   // 3. eigenvectors of T (into V)
   k_twisted<<<(2 * N + 31) / 32, 32, 0, s>>>(N, ds, es, e2, bstart, bend, lam, col, incl, V, Wp,
                                             Wd);
-  k_cluster_fix<<<kFixCTAs, 32, 0, s>>>(N, ds, es, bstart, bend, lam, col, cl, hdr, V, fix);
-  count_launch(5);
+  count_launch(4);
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
+  // clusters: the plan is read on the host (one wait for the stream)
+  int hp[2] = {0, 0};
+  if (!ok(cudaMemcpyAsync(hp, &hdr->ncl, sizeof(hp), cudaMemcpyDeviceToHost, s)) ||
+      !ok(cudaStreamSynchronize(s)))
+    return DONOF_ERR_CUDA;
+  if (hp[0] > 0) {
+    // the scratch: Aw (free after the reduction) for the large clusters' vectors, Wd and Wp rows
+    // for the members' factorisations (free after the twisted factorisations)
+    k_cluster_vectors<<<(N + 31) / 32, 32, 0, s>>>(N, ds, es, bstart, bend, lam, col, incl, cj, cl,
+                                                   V, Aw, Wd, Wp);
+    k_cluster_small<<<kFixCTAs, 32, 0, s>>>(N, col, cl, hdr, V);
+    count_launch(2);
+    if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
+  }
+  if (hp[1] > kSmallCl) {
+    std::vector<int> hcl((size_t)kClDesc * hp[0]);
+    if (!ok(cudaMemcpyAsync(hcl.data(), cl, hcl.size() * 4, cudaMemcpyDeviceToHost, s)) ||
+        !ok(cudaStreamSynchronize(s)))
+      return DONOF_ERR_CUDA;
+    double* Cc = W1;  // r0 x 32 overlaps of a panel with the rows before it
+    double* Gp = W2;  // 32 x 32 Gram matrix of a panel
+    for (int q = 0; q < hp[0]; ++q) {
+      const int* c = &hcl[(size_t)kClDesc * q];
+      const int m = c[1], L = c[3];
+      if (m <= kSmallCl) continue;
+      double* Y = Aw + c[4];
+      for (int r0 = 0; r0 < m; r0 += 32) {
+        const int b = m - r0 < 32 ? m - r0 : 32;
+        double* P = Y + (size_t)r0 * L;
+        for (int pass = 0; pass < 2; ++pass) {
+          if (r0 > 0) {
+            // Cc = Y[0:r0] P^T, then P -= Cc^T Y[0:r0]
+            if (!ok(cudaMemsetAsync(Cc, 0, (size_t)r0 * b * 8, s)) ||
+                !ok(launch_dgemm(split_k_args(r0, b, L, Y, L, 1, P, 1, L, Cc, b, 1, part), s)))
+              return DONOF_ERR_CUDA;
+            DgemmArgs u{};
+            u.M = b; u.N = L; u.K = r0; u.KB = 1; u.batch = 1; u.ksplit = 1;
+            u.A = Cc; u.sAm = 1; u.sAk = b;
+            u.B = Y; u.sBk = L; u.sBn = 1;
+            u.C = P; u.sCm = L; u.sCn = 1;
+            u.alpha = -1.0; u.beta = 1.0;
+            if (!ok(launch_dgemm(u, s))) return DONOF_ERR_CUDA;
+          }
+          if (!ok(cudaMemsetAsync(Gp, 0, (size_t)b * b * 8, s)) ||
+              !ok(launch_dgemm(split_k_args(b, b, L, P, L, 1, P, 1, L, Gp, b, 1, part), s)))
+            return DONOF_ERR_CUDA;
+          k_chol_apply<<<(L + 127) / 128, 128, 0, s>>>(b, L, Gp, P);
+          count_launch(1);
+        }
+      }
+      k_cluster_scatter<<<152 * 4, 256, 0, s>>>(N, c[0], m, c[2], L, Y, col, V);
+      count_launch(1);
+      if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
+    }
+  }
 
   // 4. V = Q Z
   if (L.nblk > 0) {

@@ -200,3 +200,21 @@ def test_argument_errors():
                         ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(small.data_ptr()), 256,
                         None)
     assert rc == -4  # DONOF_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("spread", [1e-9, 1e-13])
+def test_large_clusters(spread):
+    """A block-sized cluster that does not split: 250 eigenvalues within `spread` of 1, 100
+    with gaps of 1e-7 near 3 (a chain of resolvable close eigenvalues) and 250 spread over
+    [-5, 5], under a random orthogonal similarity: the clusters' members get inverse iteration
+    of their own and a block orthonormalisation (the large-cluster path)."""
+    n = 600
+    rng = np.random.default_rng(13)
+    lam = np.concatenate([1.0 + spread * rng.random(250), 3.0 + 1e-7 * np.arange(100),
+                          rng.uniform(-5.0, 5.0, 250)])
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    w, V, st, _ = _eigh(A)
+    assert st == 0
+    _check(A, w, V, orth_tol=1e-11)
