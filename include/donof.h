@@ -209,10 +209,14 @@ int donof_orbital_update(int32_t nbf, const double* lam, const double* Fdiag, co
  * reduction to tridiagonal T in one cooperative launch (one CTA per SM); T split where an
  * off-diagonal element is at most 16 n eps ||T||_inf; eigenvalues by bisection on Sturm
  * counts; eigenvectors of T from twisted factorisations, and by inverse iteration with
- * modified Gram-Schmidt for eigenvalues of one block closer than 1e-5 ||T||_inf; V = Q Z in
- * blocks of 64 reflectors.  Each eigenvalue is within a small multiple of n eps ||A|| of the
- * exact one and each eigenvector within that over its gap; columns of V are orthonormal to
- * about n eps ||A|| / (smallest gap outside the clusters).
+ * block orthonormalisation for eigenvalues of one block closer than 1e-5 ||T||_inf (every
+ * member's own inverse iteration; clusters of more than 32 members in panels on the GEMM
+ * kernel); V = Q Z in blocks of 64 reflectors.  The call waits once for `stream` (after the
+ * eigenvalues, to read the clusters' layout on the host), so it cannot be captured into a
+ * CUDA graph; donof_orbital_update and donof_optimize inherit that wait.  Each eigenvalue is
+ * within a small multiple of n eps ||A|| of the exact one and each eigenvector within that
+ * over its gap; columns of V are orthonormal to about n eps ||A|| / (smallest gap outside the
+ * clusters).
  * Returns DONOF_ERR_INVALID_ARG (n out of range, NULL pointer), DONOF_ERR_WORKSPACE, or
  * DONOF_ERR_CUDA (a failed launch, also when the cooperative launch cannot make its grid
  * co-resident).  Device-side outcomes (A not finite; a grid-barrier wait that ran out after
