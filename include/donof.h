@@ -124,6 +124,26 @@ int donof_energy_lagrangian(const donof_problem* prob, const double* h, const do
 int donof_energy_backward(const donof_problem* prob, const double* Ebar, const void* workspace,
                           size_t workspace_bytes, double* dE_dC, double* dE_dgamma, void* stream);
 
+/* One build and its adjoint for a caller whose orbitals and occupation parameters live in
+ * host memory (an orbital-optimisation driver on the CPU): copies C_host[nbf*nbf] and
+ * gamma_host[npair*ncwo] to the device, runs donof_energy_lagrangian and, when dE_dC_host is
+ * not NULL, donof_energy_backward with Ebar = 1, copies E (and lambda, dE/dgamma, dE/dC where
+ * their host pointers are not NULL) back to E_host[1], lam_host[nbf*nbf],
+ * dE_dgamma_host[npair*ncwo], dE_dC_host[nbf*nbf], and waits for `stream`.  h, B, pair_map and
+ * the workspace are device memory as for donof_energy_lagrangian (B prepared with
+ * donof_prepare_B); `staging` is a caller-allocated device buffer of
+ * donof_host_staging_size bytes (256-byte aligned) that holds the device copies.  With
+ * page-locked host buffers the copies are DMA transfers at full rate.  Returns a host-side
+ * error code, or else the build's device-side status (as donof_read_status, which it reads
+ * and clears). */
+int donof_host_staging_size(const donof_problem* prob, size_t* bytes);
+int donof_energy_lagrangian_host(const donof_problem* prob, const double* h, const double* B,
+                                 const double* C_host, const double* gamma_host,
+                                 const int32_t* pair_map, void* workspace,
+                                 size_t workspace_bytes, void* staging, size_t staging_bytes,
+                                 double* E_host, double* lam_host, double* dE_dgamma_host,
+                                 double* dE_dC_host, void* stream);
+
 /* A build sharded over the auxiliary index, one shard per GPU (Sec. III.D: J_pq, K_pq of
  * Eq. JKpq and the exchange and Coulomb operators of Eq. Gpmn are sums over the auxiliary
  * functions P of the density-fitted integrals, and so is the two-electron part of the

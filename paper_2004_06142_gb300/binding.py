@@ -106,6 +106,9 @@ def lib() -> ctypes.CDLL:
         L.donof_energy_lagrangian_batched.argtypes = [ctypes.c_int32, P, PI, vp, sz, ctypes.c_int32, vp]
         L.donof_orbital_update_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_orbital_update.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp, vp, vp]
+        L.donof_host_staging_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.donof_energy_lagrangian_host.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp, sz, vp, vp,
+                                                   vp, vp, vp]
         L.donof_eigh_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         L.donof_eigh.argtypes = [ctypes.c_int32, vp, vp, vp, vp, sz, vp]
         L.donof_eigh_read_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
@@ -131,6 +134,7 @@ def lib() -> ctypes.CDLL:
                   "donof_batched_workspace_size", "donof_prepare_B_batched",
                   "donof_energy_lagrangian_batched", "donof_orbital_update_workspace_size",
                   "donof_orbital_update", "donof_eigh_workspace_size", "donof_eigh",
+                  "donof_host_staging_size", "donof_energy_lagrangian_host",
                   "donof_eigh_read_status", "donof_autotune", "donof_optimize_occupations",
                   "donof_optimize_workspace_size", "donof_optimize", "donof_nofmp2_static"):
             getattr(L, f).restype = ctypes.c_int
@@ -258,6 +262,32 @@ def donof_orbital_update(lam, Fdiag, C, C_new, eps, ws=None, stream=None):
                                       _ptr(C_new), _ptr(eps), _stream(stream)),
            "donof_orbital_update")
     return ws
+
+
+def _hptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("contiguous host tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def donof_host_staging_size(prob) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().donof_host_staging_size(ctypes.byref(prob), ctypes.byref(n)),
+           "donof_host_staging_size")
+    return n.value
+
+
+def donof_energy_lagrangian_host(prob, h, B, C_host, gamma_host, pair_map, ws, staging, E_host,
+                                 lam_host=None, dEdg_host=None, dEdC_host=None, stream=None):
+    """One build (and its adjoint when dEdC_host is given) from host C and gamma into host
+    outputs; h, B, pair_map, ws and staging are device tensors.  Returns after the stream is
+    idle; raises DonofError with the build's device-side status when it is not DONOF_OK."""
+    _check(lib().donof_energy_lagrangian_host(
+        ctypes.byref(prob), _ptr(h), _ptr(B), _hptr(C_host), _hptr(gamma_host), _ptr(pair_map),
+        _ptr(ws), ws.numel(), _ptr(staging), staging.numel(), _hptr(E_host), _hptr(lam_host),
+        _hptr(dEdg_host), _hptr(dEdC_host), _stream(stream)), "donof_energy_lagrangian_host")
 
 
 def donof_eigh(A, V, w, ws=None, stream=None):

@@ -579,6 +579,88 @@ extern "C" int donof_read_status(const void* workspace, int32_t* status, void* s
   return DONOF_OK;
 }
 
+// Staging of donof_energy_lagrangian_host: device copies of C, gamma, E, the upstream gradient
+// 1, lambda, dE/dgamma and dE/dC, each 256-byte aligned.
+namespace donof {
+namespace {
+struct Stage {
+  size_t C, g, E, Ebar, lam, dg, dC, total;
+};
+Stage stage_layout(const donof_problem* p) {
+  Stage st{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  };
+  const size_t nn = (size_t)p->nbf * p->nbf * 8, ng = (size_t)p->npair * p->ncwo * 8;
+  st.C = take(nn);
+  st.g = take(ng);
+  st.E = take(8);
+  st.Ebar = take(8);
+  st.lam = take(nn);
+  st.dg = take(ng);
+  st.dC = take(nn);
+  st.total = off;
+  return st;
+}
+}  // namespace
+}  // namespace donof
+
+extern "C" int donof_host_staging_size(const donof_problem* prob, size_t* bytes) {
+  if (!prob || !bytes) return DONOF_ERR_INVALID_ARG;
+  size_t w = 0;
+  const int rc = donof_workspace_size(prob, &w);  // validates the problem
+  if (rc != DONOF_OK) return rc;
+  *bytes = stage_layout(prob).total;
+  return DONOF_OK;
+}
+
+extern "C" int donof_energy_lagrangian_host(const donof_problem* prob, const double* h,
+                                            const double* B, const double* C_host,
+                                            const double* gamma_host, const int32_t* pair_map,
+                                            void* workspace, size_t workspace_bytes,
+                                            void* staging, size_t staging_bytes, double* E_host,
+                                            double* lam_host, double* dE_dgamma_host,
+                                            double* dE_dC_host, void* stream) {
+  if (!prob || !C_host || !gamma_host || !E_host || !staging) return DONOF_ERR_INVALID_ARG;
+  size_t need = 0;
+  int rc = donof_host_staging_size(prob, &need);
+  if (rc != DONOF_OK) return rc;
+  if (staging_bytes < need || ((uintptr_t)staging % kAlign) != 0) return DONOF_ERR_WORKSPACE;
+  const Stage st = stage_layout(prob);
+  char* sg = (char*)staging;
+  double* Cd = (double*)(sg + st.C);
+  double* gd = (double*)(sg + st.g);
+  double* Ed = (double*)(sg + st.E);
+  double* Ebar = (double*)(sg + st.Ebar);
+  double* lamd = (double*)(sg + st.lam);
+  double* dgd = (double*)(sg + st.dg);
+  double* dCd = (double*)(sg + st.dC);
+  const size_t nn = (size_t)prob->nbf * prob->nbf * 8, ng = (size_t)prob->npair * prob->ncwo * 8;
+  cudaStream_t s = (cudaStream_t)stream;
+  static const double kOne = 1.0;
+  CK(cudaMemcpyAsync(Cd, C_host, nn, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(gd, gamma_host, ng, cudaMemcpyHostToDevice, s));
+  if (dE_dC_host) CK(cudaMemcpyAsync(Ebar, &kOne, 8, cudaMemcpyHostToDevice, s));
+  rc = donof_energy_lagrangian(prob, h, B, Cd, gd, pair_map, workspace, workspace_bytes, Ed,
+                               lam_host ? lamd : nullptr, dE_dgamma_host ? dgd : nullptr, stream);
+  if (rc != DONOF_OK) return rc;
+  if (dE_dC_host) {
+    rc = donof_energy_backward(prob, Ebar, workspace, workspace_bytes, dCd, nullptr, stream);
+    if (rc != DONOF_OK) return rc;
+  }
+  CK(cudaMemcpyAsync(E_host, Ed, 8, cudaMemcpyDeviceToHost, s));
+  if (lam_host) CK(cudaMemcpyAsync(lam_host, lamd, nn, cudaMemcpyDeviceToHost, s));
+  if (dE_dgamma_host) CK(cudaMemcpyAsync(dE_dgamma_host, dgd, ng, cudaMemcpyDeviceToHost, s));
+  if (dE_dC_host) CK(cudaMemcpyAsync(dE_dC_host, dCd, nn, cudaMemcpyDeviceToHost, s));
+  int32_t status = DONOF_OK;
+  rc = donof_read_status(workspace, &status, stream);  // waits for the stream
+  if (rc != DONOF_OK) return rc;
+  return status;
+}
+
 extern "C" int donof_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (enable) prof_clear_locked();
