@@ -3,18 +3,21 @@
 // diagonal).  Laid out for this GPU's narrow FP64 pipe and large L2:
 //   1. A = Q T Q^T by Householder reflections in one cooperative launch (one CTA per SM, one
 //      grid barrier per column).  Each step forms the next column of the rank-2-updated
-//      matrix in every CTA (from one row, by symmetry), its reflector, and then every warp
-//      updates its own rows of the trailing matrix and forms their part of the next
-//      matrix-vector product in the same pass; the matrix stays in L2.  A is first scaled by
-//      a power of two (exact) to a largest element in [1/2, 1).
+//      matrix in every CTA (from one row, by symmetry) and its reflector; every row warp
+//      updates its own row of the trailing matrix and takes its part of the next
+//      matrix-vector product while a scalar warp forms the reflector's scalars; the matrix
+//      stays in L2.  A is first scaled by a power of two (exact) to a largest element in
+//      [1/2, 1).
 //   2. T is split where an off-diagonal element is at most 16 N eps ||T||_inf (a perturbation
-//      of that size moves no eigenvalue by more); eigenvalues of each block by bisection on
-//      Sturm counts, one thread per eigenvalue, the counts from the three-term recurrence of
-//      the leading minors with exact power-of-two rescaling (three FP64 operations a step).
-//   3. Eigenvectors of T from twisted factorisations T - lambda I = N_r D_r N_r^T, one thread
+//      of that size moves no eigenvalue by more) and scaled by a power of two to
+//      ||T||_inf <= 1; eigenvalues of each block by multisection on Sturm counts, a half-warp
+//      per eigenvalue: float rounds, then double rounds from the three-term recurrence of the
+//      leading minors with exact power-of-two rescaling.
+//   3. Eigenvectors of T from twisted factorisations T - lambda I = N_r D_r N_r^T, two threads
 //      per eigenvalue, the twist r where |gamma_r| is smallest; eigenvalues of one block closer
-//      than 1e-5 ||T||_inf form clusters whose vectors come from inverse iteration (LU with
-//      partial pivoting) and modified Gram-Schmidt inside the cluster.
+//      than 1e-5 ||T||_inf form clusters: each member's own inverse iteration (all members at
+//      once), then a block orthonormalisation inside the cluster (one warp for small
+//      clusters, panels on the GEMM kernel for large ones).
 //   4. V = Q Z by the compact WY form of blocks of 64 reflectors: the blocks' triangular
 //      factors from their Gram matrices, and two FP64 GEMMs per block.
 #include <float.h>
