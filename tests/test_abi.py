@@ -86,6 +86,36 @@ def test_entry_points_reject_null_workspace(lib):
     assert rc == -1
 
 
+def test_eigensolver_and_host_entry_argument_checks(lib):
+    """Host-side argument checks of the eigensolver and of the host-buffer build: refused
+    before any device work (the pointers here are never dereferenced)."""
+    from paper_2004_06142_gb300 import binding as b
+    nb = ctypes.c_size_t(0)
+    assert lib.donof_eigh_workspace_size(0, ctypes.byref(nb)) == -1
+    assert lib.donof_eigh_workspace_size(4097, ctypes.byref(nb)) == -1
+    assert lib.donof_eigh_workspace_size(10, ctypes.byref(nb)) == 0
+    assert nb.value >= 3 * 10 * 10 * 8
+    assert lib.donof_orbital_update_workspace_size(4097, ctypes.byref(nb)) == -1
+    X = ctypes.c_void_p(256)
+    assert lib.donof_eigh(0, X, X, X, X, 1 << 20, None) == -1
+    assert lib.donof_eigh(10, None, X, X, X, 1 << 20, None) == -1
+    assert lib.donof_eigh(10, X, X, X, None, 0, None) == -4
+    assert lib.donof_eigh(10, X, X, X, X, 16, None) == -4
+    p = b.make_problem(24, 96, 5, 1)
+    assert lib.donof_host_staging_size(ctypes.byref(p), ctypes.byref(nb)) == 0
+    assert nb.value >= 3 * 24 * 24 * 8
+    bad = b.make_problem(0, 96, 5, 1)
+    assert lib.donof_host_staging_size(ctypes.byref(bad), ctypes.byref(nb)) == -1
+    args = [X, X, X, X, X, X, 1 << 20, X, 1 << 20, X, None, None, None, None]
+    # NULL host orbitals; a staging buffer smaller than donof_host_staging_size
+    a1 = list(args)
+    a1[2] = None
+    assert lib.donof_energy_lagrangian_host(ctypes.byref(p), *a1) == -1
+    a2 = list(args)
+    a2[8] = 64
+    assert lib.donof_energy_lagrangian_host(ctypes.byref(p), *a2) == -4
+
+
 def test_injected_workspace_allocation_failure(lib, monkeypatch):
     """Host-side fault injection: with DONOF_INJECT_ALLOC_FAILURE=1 every workspace the
     binding would allocate fails as an allocation failure does, before any device is
