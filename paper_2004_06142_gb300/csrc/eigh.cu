@@ -21,7 +21,6 @@
 //   4. V = Q Z by the compact WY form of blocks of 64 reflectors: the blocks' triangular
 //      factors from their Gram matrices, and two FP64 GEMMs per block.
 #include <float.h>
-#include <limits.h>
 
 #include <map>
 #include <mutex>
@@ -811,235 +810,118 @@ __device__ __forceinline__ double pivot_floor(double v) {
   return dbl_biased_exp(v) < 1023 - 100 ? -0x1p-100 : v;
 }
 
-// Twisted factorisation of T_b - lambda I for an eigenvalue outside the clusters, one warp per
-// eigenvalue.  The block's rows are cut into 32 segments, one per lane.  The forward pivots
-// D+_i = (d_i - lambda) - e_{i-1}^2 / D+_{i-1} are the ratios n_i / m_i of the products of
-// the 2 x 2 (Moebius) matrices [[d_i - lambda, -e_{i-1}^2], [1, 0]]: each lane forms its
-// segment's product, a warp scan gives every lane the state entering its segment, and each
-// lane then runs the recurrence over its own rows (pivots floored at 2^-100, reciprocals by
-// Newton's iteration), storing D+_i in Z's column and 1/D+_i in Wp; the backward pivots D-_i
-// the same way from the other end (1/D-_i in Wd).  The twist r is the row of smallest
-// |gamma_i| = |D+_i - e_i^2 / D-_{i+1}| (the first on ties).  z_r = 1, and the other entries
-// are products of the factors -e_i / D+_i (above r) and -e_{i-1} / D-_i (below r), formed
-// as mantissa-exponent pairs by segment and warp scans, scaled by the largest exponent and
-// normalised.  Z[i][col] (row-major, column = rank of the eigenvalue), zero outside the block.
-constexpr int kTwThreads = 128;  // four eigenvalues per CTA
-
-struct Mx {
-  double a, b, c, d;  // [[a, b], [c, d]]
-};
-__device__ __forceinline__ Mx mx_mul(const Mx& x, const Mx& y) {
-  return Mx{fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c),
-            fma(x.c, y.b, x.d * y.d)};
-}
-// scale by the power of two that brings the largest entry's exponent to 0 (exact)
-__device__ __forceinline__ void mx_norm(Mx& x) {
-  const int ex = max(max(dbl_biased_exp(x.a), dbl_biased_exp(x.b)),
-                     max(dbl_biased_exp(x.c), dbl_biased_exp(x.d)));
-  if (ex == 0 || ex == 2047) return;  // zero (or denormal), or not finite
-  const double sc = __longlong_as_double((long long)(2046 - ex) << 52);
-  x.a *= sc;
-  x.b *= sc;
-  x.c *= sc;
-  x.d *= sc;
-}
-__device__ __forceinline__ Mx mx_shfl_up(const Mx& x, int o) {
-  return Mx{__shfl_up_sync(0xffffffffu, x.a, o), __shfl_up_sync(0xffffffffu, x.b, o),
-            __shfl_up_sync(0xffffffffu, x.c, o), __shfl_up_sync(0xffffffffu, x.d, o)};
-}
-__device__ __forceinline__ Mx mx_shfl_down(const Mx& x, int o) {
-  return Mx{__shfl_down_sync(0xffffffffu, x.a, o), __shfl_down_sync(0xffffffffu, x.b, o),
-            __shfl_down_sync(0xffffffffu, x.c, o), __shfl_down_sync(0xffffffffu, x.d, o)};
-}
-// the pivot n / m of a state (n, m), floored, its magnitude kept below 2^120
-__device__ __forceinline__ double state_pivot(double n, double m) {
-  double p = dbl_is_zero(m) ? -0x1p120 : n / m;
-  if (!(fabs(p) <= 0x1p120)) p = p > 0.0 ? 0x1p120 : -0x1p120;
-  return pivot_floor(p);
-}
-
-// a nonzero finite double as m 2^e with |m| in [1, 2)
-struct Me {
-  double m;
-  int e;
-};
-__device__ __forceinline__ Me me_of(double f) {
-  const long long bits = __double_as_longlong(f);
-  const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
-  return Me{__longlong_as_double((bits & ~(0x7ffll << 52)) | (1023ll << 52)), ex};
-}
-__device__ __forceinline__ Me me_mul(const Me& x, const Me& y) {
-  const Me p = me_of(x.m * y.m);
-  return Me{p.m, x.e + y.e + p.e};
-}
-
-__global__ void __launch_bounds__(kTwThreads) k_twisted(int N, const double* __restrict__ ds,
-                                                        const double* __restrict__ es,
-                                                        const double* __restrict__ e2,
-                                                        const int* __restrict__ bstart,
-                                                        const int* __restrict__ bend,
-                                                        const double* __restrict__ lam,
-                                                        const int* __restrict__ col,
-                                                        const int* __restrict__ incl, double* Z,
-                                                        double* Wp, double* Wd) {
-  const int lane = threadIdx.x & 31;
-  const int s = (blockIdx.x * kTwThreads + threadIdx.x) >> 5;
-  if (s >= N) return;  // uniform over the warp
-  const int s0 = bstart[s], s1 = bend[s], cc = col[s];
+// Twisted factorisation of T_b - lambda I for an eigenvalue outside the clusters, two threads
+// per eigenvalue.  Thread 0 of the pair runs the forward pivots D+_i (stored in Z's column,
+// their reciprocals in Wp), thread 1 the backward pivots D-_i (reciprocals in Wd); then
+// gamma_i = D+_i - e_i^2 / D-_{i+1} (each thread half the rows), the twist r where |gamma_r|
+// is smallest (first such row), z_r = 1, and thread 0 forms z_i = -e_i z_{i+1} / D+_i above r
+// while thread 1 forms z_i = -e_{i-1} z_{i-1} / D-_i below it; normalised to unit length.
+// Z[i][col] (row-major, column = rank of the eigenvalue), zero outside the block.
+__global__ void __launch_bounds__(32) k_twisted(int N, const double* __restrict__ ds,
+                                                const double* __restrict__ es,
+                                                const double* __restrict__ e2,
+                                                const int* __restrict__ bstart,
+                                                const int* __restrict__ bend,
+                                                const double* __restrict__ lam,
+                                                const int* __restrict__ col,
+                                                const int* __restrict__ incl, double* Z,
+                                                double* Wp, double* Wd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = t >> 1, side = t & 1, lane = threadIdx.x;
+  const unsigned pm = 3u << (lane & ~1);
+  if (s >= N) return;  // uniform over the pair
+  const int s0 = bstart[s], s1 = bend[s], c = col[s];
   const size_t ld = (size_t)N;
   if (s1 - s0 == 1) {
-    if (lane == 0) Z[s0 * ld + cc] = 1.0;
+    if (side == 0) Z[s0 * ld + c] = 1.0;
     return;
   }
   if (incl[s]) return;
   const double lm = lam[s];
-  const int seg = (s1 - s0 + 31) >> 5;
-  const int a = min(s0 + lane * seg, s1), b = min(a + seg, s1);
-  const Mx I{1.0, 0.0, 0.0, 1.0};
-
-  // forward pivots
-  {
-    Mx P = I;
-    for (int i = a; i < b; ++i) {
-      const double c = ds[i] - lm, f = i > s0 ? e2[i - 1] : 0.0;
-      P = Mx{fma(c, P.a, -f * P.c), fma(c, P.b, -f * P.d), P.a, P.b};
-      if (((i - a) & 7) == 7) mx_norm(P);
+  if (side == 0) {
+    double dp = pivot_floor(ds[s0] - lm), rp = rcp_nr(dp);
+    Z[s0 * ld + c] = dp;
+    Wp[s0 * ld + c] = rp;
+    for (int i = s0 + 1; i < s1; ++i) {
+      dp = pivot_floor(fma(-e2[i - 1], rp, ds[i] - lm));
+      rp = rcp_nr(dp);
+      Z[i * ld + c] = dp;
+      Wp[i * ld + c] = rp;
     }
-    mx_norm(P);
-    for (int o = 1; o < 32; o <<= 1) {
-      const Mx R = mx_shfl_up(P, o);
-      if (lane >= o) {
-        P = mx_mul(P, R);
-        mx_norm(P);
-      }
-    }
-    Mx S = mx_shfl_up(P, 1);
-    if (lane == 0) S = I;
-    if (a < b) {
-      double rp = a > s0 ? rcp_nr(state_pivot(S.a, S.c)) : 0.0;
-      for (int i = a; i < b; ++i) {
-        const double c = ds[i] - lm;
-        const double D = pivot_floor(i > s0 ? fma(-e2[i - 1], rp, c) : c);
-        rp = rcp_nr(D);
-        Z[i * ld + cc] = D;
-        Wp[i * ld + cc] = rp;
-      }
+  } else {
+    double dm = pivot_floor(ds[s1 - 1] - lm), rm = rcp_nr(dm);
+    Wd[(s1 - 1) * ld + c] = rm;
+    for (int i = s1 - 2; i >= s0; --i) {
+      dm = pivot_floor(fma(-e2[i], rm, ds[i] - lm));
+      rm = rcp_nr(dm);
+      Wd[i * ld + c] = rm;
     }
   }
-  // backward pivots
-  {
-    Mx P = I;
-    for (int i = b - 1; i >= a; --i) {
-      const double c = ds[i] - lm, f = i < s1 - 1 ? e2[i] : 0.0;
-      P = Mx{fma(c, P.a, -f * P.c), fma(c, P.b, -f * P.d), P.a, P.b};
-      if (((b - 1 - i) & 7) == 7) mx_norm(P);
-    }
-    mx_norm(P);
-    for (int o = 1; o < 32; o <<= 1) {
-      const Mx R = mx_shfl_down(P, o);
-      if (lane + o < 32) {
-        P = mx_mul(P, R);
-        mx_norm(P);
-      }
-    }
-    Mx S = mx_shfl_down(P, 1);
-    if (lane == 31) S = I;
-    if (a < b) {
-      double rm = b < s1 ? rcp_nr(state_pivot(S.a, S.c)) : 0.0;
-      for (int i = b - 1; i >= a; --i) {
-        const double c = ds[i] - lm;
-        const double D = pivot_floor(i < s1 - 1 ? fma(-e2[i], rm, c) : c);
-        rm = rcp_nr(D);
-        Wd[i * ld + cc] = rm;
-      }
-    }
-  }
-  __syncwarp();
-  // twist: the first row of smallest |gamma|
-  double best = INFINITY;
-  int r = s1;
+  __syncwarp(pm);
+  // twist: thread 0 the rows [s0, mid), thread 1 [mid, s1)
+  const int mid = (s0 + s1) >> 1;
+  const int a = side == 0 ? s0 : mid, b = side == 0 ? mid : s1;
+  double best = 0.0;
+  int r = -1;
   for (int i = a; i < b; ++i) {
-    const double g = i < s1 - 1 ? fabs(fma(-e2[i], Wd[(i + 1) * ld + cc], Z[i * ld + cc]))
-                                : fabs(Z[i * ld + cc]);
-    if (g < best) {
+    const double g = i < s1 - 1 ? fabs(fma(-e2[i], Wd[(i + 1) * ld + c], Z[i * ld + c]))
+                                : fabs(Z[i * ld + c]);
+    if (r < 0 || g < best) {
       best = g;
       r = i;
     }
   }
-  for (int o = 16; o; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int orr = __shfl_xor_sync(0xffffffffu, r, o);
-    if (ob < best || (ob == best && orr < r)) {
+  {
+    const double ob = __shfl_xor_sync(pm, best, 1);
+    const int orr = __shfl_xor_sync(pm, r, 1);
+    // the lower rows win ties; an empty half (r < 0) never wins
+    const bool take_other = orr >= 0 && (r < 0 || ob < best || (ob == best && orr < r));
+    if (take_other) {
       best = ob;
       r = orr;
     }
   }
-  if (r >= s1) r = s0;  // every |gamma| NaN
-  __syncwarp();
-  // z as mantissa-exponent pairs: above r the suffix products of -e_i / D+_i, below r the
-  // prefix products of -e_{i-1} / D-_i; the mantissas go to Z's column, the exponents to Wp
-  {
-    const int hi = min(b, r);  // this lane's rows above r: [a, hi)
-    Me t{1.0, 0};
-    for (int i = hi - 1; i >= a; --i) {
-      t = me_mul(t, me_of(-es[i] * Wp[i * ld + cc]));
-      Z[i * ld + cc] = t.m;
-      Wp[i * ld + cc] = (double)t.e;
+  __syncwarp(pm);
+  // z: thread 0 upwards from r, thread 1 downwards; rescaled by 2^-500 when above 2^500
+  int nres = 0;
+  if (side == 0) {
+    Z[r * ld + c] = 1.0;
+    double z = 1.0;
+    for (int i = r - 1; i >= s0; --i) {
+      z = -es[i] * z * Wp[i * ld + c];
+      if (fabs(z) > 0x1p500) {
+        for (int u = i + 1; u <= r; ++u) Z[u * ld + c] *= 0x1p-500;
+        z *= 0x1p-500;
+        ++nres;
+      }
+      Z[i * ld + c] = z;
     }
-    // products of the lanes above (their rows above r), lane by lane downwards
-    Me E = t;  // inclusive suffix over lanes
-    for (int o = 1; o < 32; o <<= 1) {
-      const Me R{__shfl_down_sync(0xffffffffu, E.m, o), __shfl_down_sync(0xffffffffu, E.e, o)};
-      if (lane + o < 32) E = me_mul(E, R);
-    }
-    Me X{__shfl_down_sync(0xffffffffu, E.m, 1), __shfl_down_sync(0xffffffffu, E.e, 1)};
-    if (lane == 31) X = Me{1.0, 0};
-    for (int i = a; i < hi; ++i) {
-      const Me z = me_mul(Me{Z[i * ld + cc], (int)Wp[i * ld + cc]}, X);
-      Z[i * ld + cc] = z.m;
-      Wp[i * ld + cc] = (double)z.e;
-    }
-  }
-  {
-    const int lo = max(a, r + 1);  // this lane's rows below r: [lo, b)
-    Me t{1.0, 0};
-    for (int i = lo; i < b; ++i) {
-      t = me_mul(t, me_of(-es[i - 1] * Wd[i * ld + cc]));
-      Z[i * ld + cc] = t.m;
-      Wp[i * ld + cc] = (double)t.e;
-    }
-    Me E = t;  // inclusive prefix over lanes
-    for (int o = 1; o < 32; o <<= 1) {
-      const Me R{__shfl_up_sync(0xffffffffu, E.m, o), __shfl_up_sync(0xffffffffu, E.e, o)};
-      if (lane >= o) E = me_mul(E, R);
-    }
-    Me X{__shfl_up_sync(0xffffffffu, E.m, 1), __shfl_up_sync(0xffffffffu, E.e, 1)};
-    if (lane == 0) X = Me{1.0, 0};
-    for (int i = lo; i < b; ++i) {
-      const Me z = me_mul(Me{Z[i * ld + cc], (int)Wp[i * ld + cc]}, X);
-      Z[i * ld + cc] = z.m;
-      Wp[i * ld + cc] = (double)z.e;
+  } else {
+    double z = 1.0;
+    for (int i = r + 1; i < s1; ++i) {
+      z = -es[i - 1] * z * Wd[i * ld + c];
+      if (fabs(z) > 0x1p500) {
+        for (int u = r + 1; u < i; ++u) Z[u * ld + c] *= 0x1p-500;
+        z *= 0x1p-500;
+        ++nres;
+      }
+      Z[i * ld + c] = z;
     }
   }
-  if (r >= a && r < b) {
-    Z[r * ld + cc] = 1.0;
-    Wp[r * ld + cc] = 0.0;
-  }
-  __syncwarp();
-  // scale by the largest exponent, normalise
-  int emax = INT_MIN;
-  for (int i = a; i < b; ++i) emax = max(emax, (int)Wp[i * ld + cc]);
-  for (int o = 16; o; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  __syncwarp(pm);
+  // bring both halves to the same scale, then normalise
+  const int lo_i = side == 0 ? s0 : r + 1, hi_i = side == 0 ? r + 1 : s1;
+  const int other = __shfl_xor_sync(pm, nres, 1);
+  for (int q = nres; q < other; ++q)
+    for (int i = lo_i; i < hi_i; ++i) Z[i * ld + c] *= 0x1p-500;
   double n2 = 0.0;
-  for (int i = a; i < b; ++i) {
-    const int k = (int)Wp[i * ld + cc] - emax;
-    const double z = k < -1022 ? 0.0 : Z[i * ld + cc] * __longlong_as_double((long long)(k + 1023) << 52);
-    Z[i * ld + cc] = z;
-    n2 = fma(z, z, n2);
+  for (int i = lo_i; i < hi_i; ++i) {
+    const double zi = Z[i * ld + c];
+    n2 = fma(zi, zi, n2);
   }
-  n2 = __shfl_sync(0xffffffffu, warp_sum_d(n2), 0);
+  n2 += __shfl_xor_sync(pm, n2, 1);
   const double sc = 1.0 / sqrt(n2);
-  for (int i = a; i < b; ++i) Z[i * ld + cc] *= sc;
+  for (int i = lo_i; i < hi_i; ++i) Z[i * ld + c] *= sc;
 }
 
 __device__ __forceinline__ double hash_uniform(unsigned long long key) {
@@ -1392,8 +1274,8 @@ int eigh_run(int N, const double* A, double* V, double* w, char* ws, cudaStream_
   k_rank_plan<<<(N + 255) / 256, 256, rank_smem, s>>>(N, lam, bend, hdr, col, w, incl, cl, cj,
                                                       bstart);
   // 3. eigenvectors of T (into V)
-  k_twisted<<<(N + kTwThreads / 32 - 1) / (kTwThreads / 32), kTwThreads, 0, s>>>(
-      N, ds, es, e2, bstart, bend, lam, col, incl, V, Wp, Wd);
+  k_twisted<<<(2 * N + 31) / 32, 32, 0, s>>>(N, ds, es, e2, bstart, bend, lam, col, incl, V, Wp,
+                                            Wd);
   count_launch(4);
   if (!ok(cudaGetLastError())) return DONOF_ERR_CUDA;
   // clusters: the plan is read on the host (one wait for the stream)
